@@ -1,0 +1,74 @@
+"""Pins of the oracle's growth-factor ODEs (Sec. 3, Sec. 4) against closed forms."""
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import growth
+from oracle.background import E
+from workloads import FOFR, LCDM, Model
+
+
+def _eds_powerlaw(mu, a_over_ai):
+    # D'' = kappa mu D in EdS: D ~ a^p, p(p + 1/2) = 3 mu / 2.
+    s = np.sqrt(0.25 + 6.0 * mu)
+    pp, pm = (-0.5 + s) / 2, (-0.5 - s) / 2
+    cp = (1 - pm) / (pp - pm)   # c+ + c- = 1, p+ c+ + p- c- = 1
+    cm = 1 - cp
+    return cp * a_over_ai**pp + cm * a_over_ai**pm
+
+
+def test_eds_lcdm_closed_forms():
+    a = np.linspace(0.02, 1.0, 11)
+    g = growth.solve_growth(Model(kind=LCDM), 1.0, a, np.array([0.1]), lcdm_growth=True)
+    D1 = g["D1"][:, 0]
+    assert np.allclose(D1, a / a[0], rtol=1e-10)
+    assert np.allclose(g["D2"][:, 0], -3.0 / 7.0 * D1**2, rtol=1e-10)
+    # dD1/dtau = a^3 E dD1/da = a^3 a^(-3/2) / a_i in EdS
+    assert np.allclose(g["dD1"][:, 0], a**1.5 / a[0], rtol=1e-10)
+    assert np.allclose(g["ddD1"][:, 0], 1.5 * a * D1, rtol=1e-12)
+
+
+def test_eds_fR_limits_are_powerlaws():
+    """f(R) in EdS: k -> 0 gives mu = 1 (D = a/a_i); k -> inf gives mu = 4/3 power law."""
+    a = np.linspace(0.05, 1.0, 9)
+    k = np.array([1e-9, 1e6])
+    g = growth.solve_growth(Model(kind=FOFR, fR0=1e-2), 1.0, a, k)
+    D1 = g["D1"]
+    assert np.allclose(D1[:, 0], a / a[0], rtol=1e-9)
+    assert np.allclose(g["D2"][:, 0], -3.0 / 7.0 * (a / a[0]) ** 2, rtol=1e-9)
+    assert np.allclose(D1[:, 1], _eds_powerlaw(4.0 / 3.0, a / a[0]), rtol=1e-7)
+
+
+def test_lcdm_growing_mode_integral():
+    """LCDM: D(a)/D(1) equals E(a) int_0^a da/(a E)^3 normalised at a = 1."""
+    Om = 0.3
+    a = np.array([1e-4, 0.05, 0.2, 0.5, 0.8, 1.0])
+    g = growth.solve_growth(Model(kind=LCDM), Om, a, np.array([0.1]), lcdm_growth=True)
+    D = g["D1"][:, 0]
+
+    def Dplus(x):
+        v, _ = integrate.quad(lambda s: 1.0 / (s * float(E(s, Om))) ** 3, 0.0, x,
+                              epsrel=1e-13, epsabs=0)
+        return float(E(x, Om)) * v
+
+    ref = np.array([Dplus(x) for x in a[1:]])
+    assert np.allclose(D[1:] / D[-1], ref / ref[-1], rtol=1e-6)
+
+
+def test_fR_table_low_k_column_is_lcdm():
+    from workloads import F5
+    a = np.linspace(0.05, 1.0, 11)
+    k = np.array([1e-6, 0.05, 1.0])
+    g = growth.solve_growth(F5, 0.3, a, k)
+    gl = growth.solve_growth(F5, 0.3, a, k, lcdm_growth=True)
+    assert np.allclose(g["D1"][:, 0], gl["D1"][:, 0], rtol=1e-9)
+    assert np.allclose(g["D2"][:, 0], gl["D2"][:, 0], rtol=1e-9)
+    # enhanced growth at higher k, ordered in k
+    assert np.all(g["D1"][-1, 2] > g["D1"][-1, 1]) and np.all(g["D1"][-1, 1] > g["D1"][-1, 0])
+
+
+def test_table_interpolation_is_linear_in_lnk():
+    t = growth.growth_table(Model(), 0.3, np.array([0.05, 1.0]), 16, 64.0, nk=64)
+    row = np.log(t.k) * 2.0 + 1.0          # linear in ln k -> interpolated exactly
+    kq = np.array([t.k[3] * 1.3, t.k[10], t.k[40] * 1.01])
+    assert np.allclose(t.interp(row, kq), np.log(kq) * 2.0 + 1.0, rtol=1e-13)
