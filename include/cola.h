@@ -1,0 +1,232 @@
+/*
+ * cola.h - C ABI of libcola: one COLA particle-mesh simulation with
+ * scale-dependent growth and approximate screening on one GB300 (sm_103a).
+ *
+ * Method: Winther, Koyama, Manera, Wright & Zhao, "COLA with scale-dependent
+ * growth: applications to screened modified gravity models" (arXiv:1703.00879).
+ * Section references below are to that paper.
+ *
+ * Conventions shared by every entry point
+ *   - Units: lengths Mpc/h, wavenumbers h/Mpc, time 1/H0 (H0 = 1); the time
+ *     variable is tau with dtau = dt/a^2 (Sec. 1).  Velocities returned by
+ *     cola_snapshot are peculiar velocities in km/s.
+ *   - Particles: Np^3 unit-mass particles, particle p = (z*Np + y)*Np + x sits
+ *     at the Lagrangian lattice point q = (x, y, z) * Lbox/Np.
+ *   - Mesh arrays: Nmesh^3, indexed [z][y][x] with x fastest.  Half spectra:
+ *     [kz][ky][kx], kx = 0..N/2 fastest (N/2+1 entries per row), complex
+ *     numbers as interleaved float pairs.  Forward transforms are
+ *     unnormalised (sum x e^{-ikx}).
+ *   - Return value: COLA_OK (0) on success, a negative COLA_E* code on
+ *     failure; no call aborts or prints.  The message of the last failure is
+ *     returned by cola_last_error (a context-free failure, e.g. in cola_init
+ *     before the context exists, is reported by cola_last_error(NULL)).
+ *   - Memory: every device allocation goes through the alloc/free callbacks
+ *     given to cola_init (NULL callbacks: cudaMallocAsync/cudaFreeAsync on the
+ *     stream).  The context owns what it allocates and releases it in
+ *     cola_free.  Buffers passed in by the caller stay owned by the caller.
+ *   - Streams: all device work is enqueued on the stream given to cola_init
+ *     (borrowed, never destroyed).  Calls that take or return HOST buffers
+ *     synchronise that stream before returning; calls with DEVICE buffers do
+ *     not.
+ *   - No CPU fallback: every step of the method runs in the library's CUDA
+ *     kernels; without a usable GPU cola_init fails with COLA_ECUDA.
+ */
+#ifndef COLA_H
+#define COLA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  COLA_OK = 0,
+  COLA_EINVAL = -1,   /* bad argument or unsupported size */
+  COLA_ENOMEM = -2,   /* the allocator returned NULL */
+  COLA_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+  COLA_ESTATE = -4,   /* calls made in the wrong order */
+  COLA_ETIMEOUT = -5  /* a bounded device-side wait expired */
+};
+
+/* Model kinds. */
+enum { COLA_LCDM = 0, COLA_FOFR = 1, COLA_NDGP = 2 };
+
+/* Where a caller-owned buffer lives. */
+enum { COLA_HOST = 0, COLA_DEVICE = 1 };
+
+/* Precision of the stored k-space LPT potentials (the seed fields). */
+enum { COLA_SEED_FP32 = 0, COLA_SEED_BF16 = 1, COLA_SEED_FP16 = 2 };
+
+typedef struct cola_ctx cola_ctx;
+
+/* Device allocator: return `bytes` of device memory usable on `stream`, or NULL. */
+typedef void* (*cola_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*cola_free_fn)(void* ptr, void* stream, void* user);
+
+/* Run configuration.  Flat LCDM background (Omega_L = 1 - Omega_m, App. B);
+ * Gaussian initial field with the Eisenstein-Hu no-wiggle spectrum
+ * normalised to sigma8 at z = 0 and scaled to z_ini with the LCDM growth
+ * factor; nsteps COLA steps uniform in a from z_ini to z_final. */
+typedef struct {
+  double Omega_m, Omega_b, h, n_s, sigma8;
+  double Lbox;             /* box side [Mpc/h] */
+  int32_t Np;              /* particles per side: power of two, 32..1024 */
+  int32_t Nmesh;           /* PM mesh cells per side: power of two, 32..1024 */
+  double z_ini, z_final;
+  int32_t nsteps;          /* >= 1 */
+  uint64_t seed;           /* Philox-4x32-10 key of the white noise */
+  int32_t seed_precision;  /* COLA_SEED_* */
+  int32_t nk_table;        /* log-k nodes of the growth tables, >= 16 (1024 typical) */
+} cola_config;
+
+/* Gravity model (Sec. 5, Sec. 6, App. B). */
+typedef struct {
+  int32_t kind;            /* COLA_LCDM, COLA_FOFR (Hu-Sawicky n = 1), COLA_NDGP */
+  double fR0;              /* |f_R0| (f(R) only, > 0) */
+  double rcH0;             /* r_c H0 (nDGP only, > 0) */
+  int32_t screening;       /* 1: approximate screening of the fifth force (Sec. 6) */
+  int32_t filter;          /* smoothing window of the Vainshtein density: 0 = Gaussian */
+  double R_smooth;         /* smoothing radius [Mpc/h] (nDGP screening) */
+  int32_t scale_dependent; /* 1: per-k growth D(k,a) (Sec. 4); 0: LCDM growth factors */
+} cola_model;
+
+/* Creates a context: validates the configuration, allocates every device
+ * buffer of the run (particles, LPT grid, PM mesh, tables) through `alloc`,
+ * and computes the background quantities.  `stream` is a cudaStream_t (NULL =
+ * legacy default stream).  On success *out owns the context; on failure
+ * *out is NULL and nothing is leaked.  Errors: COLA_EINVAL (sizes not powers of
+ * two in 32..1024, nsteps < 1, nonsensical cosmology), COLA_ENOMEM, COLA_ECUDA. */
+int cola_init(const cola_config* cfg, cola_alloc_fn alloc, cola_free_fn free_fn, void* user,
+              void* stream, cola_ctx** out);
+
+/* Sets the gravity model and solves, in double precision on the host, the
+ * growth ODEs of Sec. 4.1 (D1'' = kappa mu(k,a) D1) and Eq. fofrapprox
+ * (approximate second-order D2 with gamma_2(k, k/sqrt2, k/sqrt2, a)) on
+ * nk_table log-spaced k nodes at every step boundary; uploads the float
+ * tables.  Must precede cola_ic.  Errors: COLA_EINVAL (unknown kind,
+ * non-positive fR0/rcH0/R_smooth where needed), COLA_ESTATE (after cola_ic). */
+int cola_set_model(cola_ctx* ctx, const cola_model* model);
+
+/* Initial conditions (Sec. 3, Sec. 4.1, App. A): Philox white noise on the Np^3
+ * lattice, delta(k) with P_ini(k), phi1 = delta/k^2, phi2 from the 2LPT
+ * source (Eq. lcdm2lpt); stores phi1(k), phi2(k) (the k-space seed fields),
+ * places particles on the 2LPT trajectory at a_ini and evaluates the initial
+ * force.  Errors: COLA_ESTATE (no model), COLA_ECUDA. */
+int cola_ic(cola_ctx* ctx);
+
+/* Same as cola_ic but with caller-provided potentials phi1(k), phi2(k):
+ * Np*Np*(Np/2+1) complex values each (interleaved float pairs, unnormalised
+ * forward-DFT convention, phi(k=0) ignored), on the host or the device. */
+int cola_ic_from_potentials(cola_ctx* ctx, const float* phi1, const float* phi2, int32_t where);
+
+/* Advances `nsteps` COLA steps (Sec. 2, App. A; -1 = to z_final): per step the
+ * LPT reweight and inverse FFTs of the displacement and acceleration fields,
+ * the drift with CIC deposit, the forward FFT, the screened Poisson solve,
+ * the force inverse FFTs and the CIC gather with the kick.  Asynchronous on
+ * the stream.  Errors: COLA_ESTATE (before cola_ic), COLA_EINVAL (past the
+ * last step), COLA_ECUDA. */
+int cola_step(cola_ctx* ctx, int32_t nsteps);
+
+/* Particle positions (wrapped into [0, Lbox), [Np^3][3] floats, Mpc/h) and
+ * peculiar velocities ([Np^3][3] floats, km/s) at the current scale factor,
+ * written to caller-owned buffers on the host or device; either pointer may
+ * be NULL.  Host buffers synchronise the stream. */
+int cola_snapshot(cola_ctx* ctx, float* pos, float* vel, int32_t where);
+
+/* Matter power spectrum of the current particles: CIC on the Nmesh mesh,
+ * deconvolved by the CIC window, linear bins b = 0..nbins-1 covering
+ * |k| in [(b+1/2) k_F, (b+3/2) k_F), k_F = 2 pi/Lbox, no shot-noise
+ * subtraction.  Host arrays of nbins entries (k = mean |k| of the bin's modes,
+ * pk in (Mpc/h)^3, nmodes = number of modes); any may be NULL.  Synchronises. */
+int cola_pk(cola_ctx* ctx, int32_t nbins, double* k, double* pk, int64_t* nmodes);
+
+/* Current scale factor (NaN for a NULL context) and completed steps. */
+double cola_scale_factor(const cola_ctx* ctx);
+int32_t cola_steps_done(const cola_ctx* ctx);
+
+/* Message of the last failure on ctx (or of the last context-free failure for
+ * NULL); empty string if none.  Owned by the library. */
+const char* cola_last_error(const cola_ctx* ctx);
+
+/* Releases every device buffer of the context through the free callback and
+ * destroys it.  Synchronises the stream first.  NULL is a no-op. */
+void cola_free(cola_ctx* ctx);
+
+/* ---------------------------------------------------------------------
+ * State access (checkpoint/resume and per-stage inspection).
+ * --------------------------------------------------------------------- */
+
+/* Internal arrays that cola_export / cola_import copy.  Layouts:
+ *   COLA_F_DISP, COLA_F_DV, COLA_F_ACC : [3][Np^3] floats (SoA x, y, z): the
+ *       displacement s = x - q, the COLA residual velocity delta_v = dx/dtau
+ *       - dPsi_LPT/dtau, and the last residual acceleration (force - A_LPT).
+ *   COLA_F_RHO     : [Nmesh^3] floats, CIC mass per cell of the last deposit.
+ *   COLA_F_DELTAK  : [Nmesh][Nmesh][Nmesh/2+1] complex, DFT of delta of the
+ *                    last force evaluation (unnormalised).
+ *   COLA_F_FORCE   : [3][Nmesh^3] floats, the last mesh force -grad Phi_tot.
+ *   COLA_F_PHI1, COLA_F_PHI2 : [Np][Np][Np/2+1] complex, the seed potentials.
+ *   COLA_F_LPT_DISP, COLA_F_LPT_ACC : [3][Np^3] floats, the last LPT
+ *       displacement increment and LPT acceleration fields at the lattice. */
+enum {
+  COLA_F_DISP = 0, COLA_F_DV = 1, COLA_F_ACC = 2, COLA_F_RHO = 3, COLA_F_DELTAK = 4,
+  COLA_F_FORCE = 5, COLA_F_PHI1 = 6, COLA_F_PHI2 = 7, COLA_F_LPT_DISP = 8, COLA_F_LPT_ACC = 9
+};
+
+/* Copies internal array `which` to a caller-owned buffer (host or device).
+ * Errors: COLA_EINVAL (unknown array), COLA_ESTATE (array not computed yet). */
+int cola_export(cola_ctx* ctx, int32_t which, void* dst, int32_t where);
+
+/* Restores the particle state (COLA_F_DISP, COLA_F_DV, COLA_F_ACC from the
+ * same step) and the step counter, e.g. from a checkpoint of an identical
+ * run.  cola_ic must have run (the seed potentials are needed). */
+int cola_import_state(cola_ctx* ctx, const float* disp, const float* dv, const float* acc,
+                      int32_t steps_done, int32_t where);
+
+/* ---------------------------------------------------------------------
+ * Stage entry points (the same kernels as cola_step, on caller data).
+ * --------------------------------------------------------------------- */
+
+/* 3-D FFT on the context's Nmesh mesh.  dir = +1: real [N^3] -> half spectrum
+ * [N][N][N/2+1] complex (unnormalised forward); dir = -1: half spectrum ->
+ * real (unnormalised inverse; imaginary parts of the kx = 0 and kx = N/2
+ * entries are ignored after the ky, kz transforms).  in/out on the host or
+ * device (both on the same side). */
+int cola_fft(cola_ctx* ctx, int32_t dir, const void* in, void* out, int32_t where);
+
+/* CIC deposit of n positions ([n][3] floats, Mpc/h, any real values; wrapped
+ * periodically) with unit mass onto the Nmesh mesh; writes [Nmesh^3] floats. */
+int cola_cic_deposit(cola_ctx* ctx, const float* pos, int64_t n, float* rho, int32_t where);
+
+/* Mesh force of App. B for the current model at scale factor a from a given
+ * CIC density (mass per cell, [Nmesh^3] floats, mean Np^3/Nmesh^3): writes
+ * [3][Nmesh^3] floats -grad Phi_tot. */
+int cola_force_from_density(cola_ctx* ctx, const float* rho, double a, float* force,
+                            int32_t where);
+
+/* ---------------------------------------------------------------------
+ * Host-only helpers (no GPU needed): the double-precision quantities the
+ * library computes on the host and uploads.  Same validation as cola_init /
+ * cola_set_model.
+ * --------------------------------------------------------------------- */
+
+/* Growth tables of Sec. 4.1 and Eq. fofrapprox at the nsteps+1 step boundaries
+ * a_n = a_ini + n (a_final - a_ini)/nsteps, on the nk_table log-spaced nodes
+ * k_j = k0 exp(j dlnk), k0 = pi/Lbox, k_last = 1.01 sqrt(3) pi Np/Lbox.
+ * out: [nsteps+1][6][nk_table] doubles = D1, dD1/dtau, d2D1/dtau2, D2,
+ * dD2/dtau, d2D2/dtau2 (D1 = 1, D2 = -3/7 at a_ini).  k_nodes (optional):
+ * [nk_table] wavenumbers in h/Mpc. */
+int cola_host_growth(const cola_config* cfg, const cola_model* model, double* out,
+                     double* k_nodes);
+
+/* Time integrals of the kick-drift-kick step (Sec. 2; dtau = dt/a^2):
+ * out: [nsteps][4] doubles = a_{n+1}, Delta tau(a_n, a_{n+1/2}),
+ * Delta tau(a_n, a_{n+1}), Delta tau(a_{n+1/2}, a_{n+1}), a_{n+1/2} = (a_n + a_{n+1})/2. */
+int cola_host_timesteps(const cola_config* cfg, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COLA_H */

@@ -1,0 +1,276 @@
+"""Python binding of libcola (ctypes): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module
+converts Python records to the C structs of ``include/cola.h``, routes the
+library's device allocations to PyTorch's caching allocator and passes
+PyTorch's current stream.  There is no CPU fallback: if ``libcola.so`` has not
+been built (``paper_1703_00879_gb300.build.build()``) or no GPU is visible,
+every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcola.so")
+
+COLA_OK, COLA_EINVAL, COLA_ENOMEM, COLA_ECUDA, COLA_ESTATE, COLA_ETIMEOUT = 0, -1, -2, -3, -4, -5
+COLA_LCDM, COLA_FOFR, COLA_NDGP = 0, 1, 2
+COLA_HOST, COLA_DEVICE = 0, 1
+COLA_F_DISP, COLA_F_DV, COLA_F_ACC, COLA_F_RHO, COLA_F_DELTAK = 0, 1, 2, 3, 4
+COLA_F_FORCE, COLA_F_PHI1, COLA_F_PHI2, COLA_F_LPT_DISP, COLA_F_LPT_ACC = 5, 6, 7, 8, 9
+
+
+class ColaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libcola error {code}: {msg}")
+        self.code = code
+
+
+class cola_config(ctypes.Structure):
+    _fields_ = [("Omega_m", ctypes.c_double), ("Omega_b", ctypes.c_double), ("h", ctypes.c_double),
+                ("n_s", ctypes.c_double), ("sigma8", ctypes.c_double), ("Lbox", ctypes.c_double),
+                ("Np", ctypes.c_int32), ("Nmesh", ctypes.c_int32), ("z_ini", ctypes.c_double),
+                ("z_final", ctypes.c_double), ("nsteps", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("seed_precision", ctypes.c_int32), ("nk_table", ctypes.c_int32)]
+
+
+class cola_model(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("fR0", ctypes.c_double), ("rcH0", ctypes.c_double),
+                ("screening", ctypes.c_int32), ("filter", ctypes.c_int32), ("R_smooth", ctypes.c_double),
+                ("scale_dependent", ctypes.c_int32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib_handle: Optional[ctypes.CDLL] = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "cola_init": (ctypes.c_int, [ctypes.POINTER(cola_config), ALLOC_FN, FREE_FN, _P, _P, ctypes.POINTER(_P)]),
+    "cola_set_model": (ctypes.c_int, [_P, ctypes.POINTER(cola_model)]),
+    "cola_ic": (ctypes.c_int, [_P]),
+    "cola_ic_from_potentials": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
+    "cola_step": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cola_snapshot": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
+    "cola_pk": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
+    "cola_scale_factor": (ctypes.c_double, [_P]),
+    "cola_steps_done": (ctypes.c_int32, [_P]),
+    "cola_last_error": (ctypes.c_char_p, [_P]),
+    "cola_free": (None, [_P]),
+    "cola_export": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "cola_import_state": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32]),
+    "cola_fft": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
+    "cola_cic_deposit": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32]),
+    "cola_force_from_density": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.c_int32]),
+    "cola_host_growth": (ctypes.c_int, [ctypes.POINTER(cola_config), ctypes.POINTER(cola_model), _P, _P]),
+    "cola_host_timesteps": (ctypes.c_int, [ctypes.POINTER(cola_config), _P]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libcola.so; raises if it has not been built."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        h = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(h, name)
+            f.restype = res
+            f.argtypes = args
+        _lib_handle = h
+    return _lib_handle
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc: int, ctx=None):
+    if rc != COLA_OK:
+        msg = lib().cola_last_error(ctx)
+        raise ColaError(rc, msg.decode() if msg else "")
+
+
+def make_config(run) -> cola_config:
+    """cola_config from a workloads.Run-like record."""
+    c = run.cosmo
+    return cola_config(c.Omega_m, c.Omega_b, c.h, c.n_s, c.sigma8, float(run.Lbox), int(run.Np),
+                       int(run.Nmesh), float(run.z_ini), float(run.z_final), int(run.nsteps),
+                       int(run.seed), int(getattr(run, "seed_precision", 0)), int(run.nk_table))
+
+
+def make_model(m) -> cola_model:
+    return cola_model(int(m.kind), float(m.fR0), float(m.rcH0), int(m.screening), 0,
+                      float(m.R_smooth), int(m.scale_dependent))
+
+
+def cola_host_growth(run):
+    """Host growth tables: array [nsteps+1][6][nk] and the k nodes."""
+    cfg, mdl = make_config(run), make_model(run.model)
+    out = np.zeros((run.nsteps + 1, 6, run.nk_table))
+    k = np.zeros(run.nk_table)
+    _check(lib().cola_host_growth(ctypes.byref(cfg), ctypes.byref(mdl), out.ctypes.data, k.ctypes.data))
+    return out, k
+
+
+def cola_host_timesteps(run):
+    cfg = make_config(run)
+    out = np.zeros((run.nsteps, 4))
+    _check(lib().cola_host_timesteps(ctypes.byref(cfg), out.ctypes.data))
+    return out
+
+
+class Simulation:
+    """One libcola context: cola_init + cola_set_model (+ cola_ic) on the current torch stream."""
+
+    def __init__(self, run, seed_precision: int = 0, ic: bool = True, phi=None, stream=None,
+                 torch_alloc: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libcola needs a CUDA GPU; none is visible")
+        self.torch = torch
+        self.run = run
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        L = lib()
+        cfg = make_config(run)
+        cfg.seed_precision = int(seed_precision)
+        self.cfg = cfg
+        dev = self.device
+
+        def _alloc(nbytes, stream, user):
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+
+        def _free(ptr, stream, user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_cb = ALLOC_FN(_alloc) if torch_alloc else ALLOC_FN()
+        self._free_cb = FREE_FN(_free) if torch_alloc else FREE_FN()
+        h = _P()
+        _check(L.cola_init(ctypes.byref(cfg), self._alloc_cb, self._free_cb, None,
+                           _P(self.stream.cuda_stream), ctypes.byref(h)))
+        self.ctx = h
+        self.P = run.Np ** 3
+        self.M = run.Nmesh ** 3
+        _check(L.cola_set_model(self.ctx, ctypes.byref(make_model(run.model))), self.ctx)
+        if phi is not None:
+            self.ic_from_potentials(*phi)
+        elif ic:
+            self.ic()
+
+    # -- lifecycle --
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().cola_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- C ABI calls --
+    def ic(self):
+        _check(lib().cola_ic(self.ctx), self.ctx)
+
+    def ic_from_potentials(self, phi1: np.ndarray, phi2: np.ndarray):
+        p1 = np.ascontiguousarray(phi1, dtype=np.complex64)
+        p2 = np.ascontiguousarray(phi2, dtype=np.complex64)
+        _check(lib().cola_ic_from_potentials(self.ctx, p1.ctypes.data, p2.ctypes.data, COLA_HOST), self.ctx)
+
+    def step(self, n: int = 1):
+        _check(lib().cola_step(self.ctx, int(n)), self.ctx)
+
+    def run_to_end(self):
+        self.step(-1)
+        return self
+
+    @property
+    def a(self) -> float:
+        return lib().cola_scale_factor(self.ctx)
+
+    @property
+    def steps_done(self) -> int:
+        return lib().cola_steps_done(self.ctx)
+
+    def snapshot(self, pos=True, vel=True):
+        """(positions [P,3], velocities [P,3]) as numpy float32 (host buffers)."""
+        P = self.P
+        p = np.empty((P, 3), np.float32) if pos else None
+        v = np.empty((P, 3), np.float32) if vel else None
+        _check(lib().cola_snapshot(self.ctx, p.ctypes.data if pos else None,
+                                   v.ctypes.data if vel else None, COLA_HOST), self.ctx)
+        return p, v
+
+    def snapshot_device(self, pos_t, vel_t):
+        """Write into device torch tensors (float32, P*3 each, or None)."""
+        _check(lib().cola_snapshot(self.ctx, pos_t.data_ptr() if pos_t is not None else None,
+                                   vel_t.data_ptr() if vel_t is not None else None, COLA_DEVICE), self.ctx)
+
+    def pk(self, nbins: Optional[int] = None):
+        nb = nbins or self.run.Nmesh // 2
+        k = np.empty(nb)
+        pk = np.empty(nb)
+        nm = np.empty(nb, np.int64)
+        _check(lib().cola_pk(self.ctx, nb, k.ctypes.data, pk.ctypes.data, nm.ctypes.data), self.ctx)
+        return k, pk, nm
+
+    def export(self, which: int) -> np.ndarray:
+        Np, Nm = self.run.Np, self.run.Nmesh
+        shapes = {COLA_F_DISP: ((3, Np**3), np.float32), COLA_F_DV: ((3, Np**3), np.float32),
+                  COLA_F_ACC: ((3, Np**3), np.float32), COLA_F_RHO: ((Nm, Nm, Nm), np.float32),
+                  COLA_F_DELTAK: ((Nm, Nm, Nm // 2 + 1), np.complex64),
+                  COLA_F_FORCE: ((3, Nm, Nm, Nm), np.float32),
+                  COLA_F_PHI1: ((Np, Np, Np // 2 + 1), np.complex64),
+                  COLA_F_PHI2: ((Np, Np, Np // 2 + 1), np.complex64),
+                  COLA_F_LPT_DISP: ((3, Np**3), np.float32), COLA_F_LPT_ACC: ((3, Np**3), np.float32)}
+        shape, dt = shapes[which]
+        out = np.empty(shape, dt)
+        _check(lib().cola_export(self.ctx, which, out.ctypes.data, COLA_HOST), self.ctx)
+        return out
+
+    def import_state(self, disp, dv, acc, steps_done: int):
+        arrs = [np.ascontiguousarray(x, dtype=np.float32) for x in (disp, dv, acc)]
+        _check(lib().cola_import_state(self.ctx, arrs[0].ctypes.data, arrs[1].ctypes.data,
+                                       arrs[2].ctypes.data, int(steps_done), COLA_HOST), self.ctx)
+
+    def fft(self, x: np.ndarray, direction: int) -> np.ndarray:
+        N = self.run.Nmesh
+        if direction == 1:
+            src = np.ascontiguousarray(x, dtype=np.float32)
+            out = np.empty((N, N, N // 2 + 1), np.complex64)
+        else:
+            src = np.ascontiguousarray(x, dtype=np.complex64)
+            out = np.empty((N, N, N), np.float32)
+        _check(lib().cola_fft(self.ctx, int(direction), src.ctypes.data, out.ctypes.data, COLA_HOST), self.ctx)
+        return out
+
+    def cic_deposit(self, pos: np.ndarray) -> np.ndarray:
+        N = self.run.Nmesh
+        p = np.ascontiguousarray(pos, dtype=np.float32)
+        out = np.empty((N, N, N), np.float32)
+        _check(lib().cola_cic_deposit(self.ctx, p.ctypes.data, p.shape[0], out.ctypes.data, COLA_HOST), self.ctx)
+        return out
+
+    def force_from_density(self, rho: np.ndarray, a: float) -> np.ndarray:
+        N = self.run.Nmesh
+        r = np.ascontiguousarray(rho, dtype=np.float32)
+        out = np.empty((3, N, N, N), np.float32)
+        _check(lib().cola_force_from_density(self.ctx, r.ctypes.data, float(a), out.ctypes.data, COLA_HOST),
+               self.ctx)
+        return out

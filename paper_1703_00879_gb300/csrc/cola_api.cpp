@@ -1,0 +1,801 @@
+// C ABI of libcola: context, buffers, and the orchestration of the COLA step
+// (Sec. 2, Sec. 4, Sec. 6, App. A, App. B) on one CUDA stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cola.h"
+#include "cola_internal.h"
+#include "host_cosmo.h"
+
+using namespace cola;
+
+namespace {
+thread_local std::string g_err;
+}
+
+struct cola_ctx {
+  cola_config cfg{};
+  cola_model model{};
+  bool model_set = false, ic_done = false, have_force = false, have_lpt = false;
+  cudaStream_t st = nullptr;
+  cola_alloc_fn alloc = nullptr;
+  cola_free_fn freef = nullptr;
+  void* user = nullptr;
+  std::string err;
+  std::vector<void*> allocs;
+  int Np = 0, Nm = 0, lgNp = 0, nk = 0;
+  double L = 0;
+  int64_t P = 0, M = 0;
+  std::vector<double> a, dtk1, dtd, dtk2;
+  int step = 0;
+  double lnk0 = 0, dlnk = 0;
+  // particles (SoA)
+  float* s[3] = {};
+  float* v[3] = {};
+  float* acc[3] = {};
+  // seeds
+  float2* phi[2] = {};
+  void* seedq[2] = {};
+  float seed_scale[2] = {1.f, 1.f};
+  // LPT work
+  float2* lc[6] = {};
+  float* lr[6] = {};
+  // mesh
+  float* rho = nullptr;
+  float2 *Cd = nullptr, *Ck = nullptr, *Cw = nullptr, *Cphi = nullptr, *Cphz = nullptr;
+  float* F[3] = {};
+  float2 *tw_np = nullptr, *tw_nm = nullptr;
+  float4 *tab = nullptr, *vtab = nullptr;
+  double* pk_acc = nullptr;
+  float* scratch = nullptr;
+  EHParams eh{};
+  double Dratio = 1.0;
+};
+
+namespace {
+
+constexpr int kMaxBins = 2000;
+
+int fail(cola_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_err = msg;
+  return code;
+}
+
+#define CK(expr)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, COLA_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+#define CHECK_RC(expr)          \
+  do {                          \
+    int rc_ = (expr);           \
+    if (rc_ != COLA_OK) return rc_; \
+  } while (0)
+
+bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+int ilog2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+void* dev_alloc(cola_ctx* c, size_t bytes) {
+  void* p = nullptr;
+  if (c->alloc) {
+    p = c->alloc(bytes, (void*)c->st, c->user);
+  } else if (cudaMallocAsync(&p, bytes, c->st) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+void dev_free(cola_ctx* c, void* p) {
+  if (!p) return;
+  if (c->freef) c->freef(p, (void*)c->st, c->user);
+  else if (!c->alloc) cudaFreeAsync(p, c->st);
+}
+
+template <class T>
+int alloc_buf(cola_ctx* c, T** out, size_t count) {
+  void* p = dev_alloc(c, count * sizeof(T));
+  if (!p) return fail(c, COLA_ENOMEM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
+  c->allocs.push_back(p);
+  *out = static_cast<T*>(p);
+  return COLA_OK;
+}
+
+// Temporary device buffer released by the destructor (after a stream sync).
+struct Temp {
+  cola_ctx* c;
+  void* p = nullptr;
+  Temp(cola_ctx* cc, size_t bytes) : c(cc) {
+    if (bytes) p = dev_alloc(c, bytes);
+  }
+  ~Temp() {
+    if (p) {
+      cudaStreamSynchronize(c->st);
+      dev_free(c, p);
+    }
+  }
+};
+
+int validate_cfg(const cola_config* cfg, cola_ctx* c) {
+  if (!cfg) return fail(c, COLA_EINVAL, "cfg is NULL");
+  if (!pow2_in(cfg->Np, 32, 1024)) return fail(c, COLA_EINVAL, "Np must be a power of two in 32..1024");
+  if (!pow2_in(cfg->Nmesh, 32, 1024)) return fail(c, COLA_EINVAL, "Nmesh must be a power of two in 32..1024");
+  if (cfg->nsteps < 1) return fail(c, COLA_EINVAL, "nsteps must be >= 1");
+  if (!(cfg->Lbox > 0)) return fail(c, COLA_EINVAL, "Lbox must be > 0");
+  if (!(cfg->Omega_m > 0 && cfg->Omega_m <= 1) || !(cfg->Omega_b >= 0 && cfg->Omega_b < cfg->Omega_m) ||
+      !(cfg->h > 0) || !(cfg->sigma8 > 0))
+    return fail(c, COLA_EINVAL, "cosmological parameters out of range");
+  if (!(cfg->z_ini > cfg->z_final) || !(cfg->z_final >= 0))
+    return fail(c, COLA_EINVAL, "need z_ini > z_final >= 0");
+  if (cfg->nk_table < 16 || cfg->nk_table > (1 << 20)) return fail(c, COLA_EINVAL, "nk_table out of range");
+  if (cfg->seed_precision < 0 || cfg->seed_precision > 2) return fail(c, COLA_EINVAL, "seed_precision must be 0, 1 or 2");
+  return COLA_OK;
+}
+
+int validate_model(const cola_model* m, cola_ctx* c) {
+  if (!m) return fail(c, COLA_EINVAL, "model is NULL");
+  if (m->kind < 0 || m->kind > 2) return fail(c, COLA_EINVAL, "unknown model kind");
+  if (m->kind == COLA_FOFR && !(m->fR0 > 0)) return fail(c, COLA_EINVAL, "f(R) needs fR0 > 0");
+  if (m->kind == COLA_NDGP && !(m->rcH0 > 0)) return fail(c, COLA_EINVAL, "nDGP needs rcH0 > 0");
+  if (m->kind == COLA_NDGP && m->screening && !(m->R_smooth > 0))
+    return fail(c, COLA_EINVAL, "Vainshtein screening needs R_smooth > 0");
+  if (m->filter != 0) return fail(c, COLA_EINVAL, "only the Gaussian filter (0) is available");
+  return COLA_OK;
+}
+
+std::vector<double> a_nodes(const cola_config& cfg) {
+  const double ai = 1.0 / (1.0 + cfg.z_ini), af = 1.0 / (1.0 + cfg.z_final);
+  std::vector<double> a(cfg.nsteps + 1);
+  for (int i = 0; i <= cfg.nsteps; ++i) a[i] = ai + i * (af - ai) / cfg.nsteps;
+  a[cfg.nsteps] = af;
+  return a;
+}
+
+void k_nodes(const cola_config& cfg, double& lnk0, double& dlnk, std::vector<double>& k) {
+  const double kF = 2.0 * kPi / cfg.Lbox;
+  const double kmin = 0.5 * kF, kmax = 1.01 * std::sqrt(3.0) * kPi * cfg.Np / cfg.Lbox;
+  lnk0 = std::log(kmin);
+  dlnk = (std::log(kmax) - lnk0) / (cfg.nk_table - 1);
+  k.resize(cfg.nk_table);
+  for (int j = 0; j < cfg.nk_table; ++j) k[j] = std::exp(lnk0 + dlnk * j);
+}
+
+HModel hmodel(const cola_model& m) {
+  HModel h;
+  h.kind = m.kind;
+  h.fR0 = m.fR0;
+  h.rcH0 = m.rcH0;
+  h.R_smooth = m.R_smooth;
+  h.screening = m.screening;
+  h.scale_dependent = m.scale_dependent;
+  return h;
+}
+
+void growth_for(const cola_config& cfg, const cola_model& m, Growth& g, std::vector<double>* kout,
+                double* lnk0_out, double* dlnk_out) {
+  double lnk0, dlnk;
+  std::vector<double> k;
+  k_nodes(cfg, lnk0, dlnk, k);
+  const bool lcdm = (m.kind == COLA_LCDM) || !m.scale_dependent;
+  solve_growth(hmodel(m), cfg.Omega_m, a_nodes(cfg), k, lcdm, g);
+  if (kout) *kout = k;
+  if (lnk0_out) *lnk0_out = lnk0;
+  if (dlnk_out) *dlnk_out = dlnk;
+}
+
+int upload_twiddles(cola_ctx* ctx, int N, float2** dst) {
+  CHECK_RC(alloc_buf(ctx, dst, N));
+  std::vector<float2> h(N);
+  for (int m = 0; m < N; ++m) {
+    const double ang = -2.0 * kPi * m / N;
+    h[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  CK(cudaMemcpyAsync(*dst, h.data(), N * sizeof(float2), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return COLA_OK;
+}
+
+ForceParams force_params(const cola_ctx* c, double a) {
+  ForceParams fp{};
+  const double Om = c->cfg.Omega_m;
+  const double N3 = (double)c->Nm * c->Nm * c->Nm;
+  fp.kf = (float)(2.0 * kPi / c->L);
+  fp.kappa_norm = (float)(1.5 * Om * a / N3);
+  fp.norm = (float)(1.0 / N3);
+  fp.inv_rhobar = (float)(N3 / ((double)c->Np * c->Np * c->Np));
+  fp.model = c->model.kind;
+  fp.screened = 0;
+  if (c->model.kind == COLA_FOFR) {
+    fp.C = (float)(1.0 / 3.0);
+    fp.a2m2 = (float)(a * a * fr_m2(a, Om, c->model.fR0));
+    fp.fr_thr = (float)(1.5 * fr_fR(a, Om, c->model.fR0) * a * a * kCLight * kCLight);
+    fp.screened = c->model.screening ? 1 : 0;
+  } else if (c->model.kind == COLA_NDGP) {
+    const double b = dgp_beta(a, Om, c->model.rcH0);
+    fp.C = (float)(1.0 / (3.0 * b));
+    fp.a2m2 = 0.f;
+    fp.dgp_coef = (float)(8.0 * c->model.rcH0 * c->model.rcH0 * Om / (9.0 * b * b));
+    fp.R2half = (float)(0.5 * c->model.R_smooth * c->model.R_smooth);
+    fp.screened = c->model.screening ? 1 : 0;
+  }
+  return fp;
+}
+
+// 3-D transforms on the padded half-spectrum layout.
+int r2c3(cola_ctx* ctx, int N, const float* in, float2* out, const float2* tw, float scale,
+         float offset) {
+  CK(fft_xr2c(N, in, out, scale, offset, tw, ctx->st));
+  CK(fft_col(N, out, 1, false, tw, ctx->st));
+  CK(fft_col(N, out, 2, false, tw, ctx->st));
+  return COLA_OK;
+}
+
+int c2r3(cola_ctx* ctx, int N, float2* in, float* out, const float2* tw) {
+  CK(fft_col(N, in, 2, true, tw, ctx->st));
+  CK(fft_col(N, in, 1, true, tw, ctx->st));
+  CK(fft_xc2r(N, in, out, 0.f, tw, ctx->st));
+  return COLA_OK;
+}
+
+// Sec. 4.1 / App. A: LPT fields at the lattice from the k-space seeds and one table row.
+int run_lpt(cola_ctx* ctx, const float4* row) {
+  LptParams lp{};
+  lp.tab = row;
+  lp.lnk0 = (float)ctx->lnk0;
+  lp.inv_dlnk = (float)(1.0 / ctx->dlnk);
+  lp.nk = ctx->nk;
+  lp.kf = (float)(2.0 * kPi / ctx->L);
+  lp.norm = (float)(1.0 / ((double)ctx->Np * ctx->Np * ctx->Np));
+  lp.seed_prec = ctx->cfg.seed_precision;
+  lp.seed_scale1 = ctx->seed_scale[0];
+  lp.seed_scale2 = ctx->seed_scale[1];
+  const void* p1 = lp.seed_prec ? ctx->seedq[0] : (const void*)ctx->phi[0];
+  const void* p2 = lp.seed_prec ? ctx->seedq[1] : (const void*)ctx->phi[1];
+  const int N = ctx->Np;
+  const float kf = lp.kf;
+  auto st = ctx->st;
+  CK(lpt_z(N, p1, p2, ctx->lc[0], ctx->lc[1], ctx->lc[2], ctx->lc[3], lp, ctx->tw_np, st));
+  CK(fft_yinv2(N, ctx->lc[0], ctx->lc[0], ctx->lc[4], kf, ctx->tw_np, st));
+  CK(fft_col(N, ctx->lc[1], 1, true, ctx->tw_np, st));
+  CK(fft_yinv2(N, ctx->lc[2], ctx->lc[2], ctx->lc[5], kf, ctx->tw_np, st));
+  CK(fft_col(N, ctx->lc[3], 1, true, ctx->tw_np, st));
+  CK(fft_xc2r(N, ctx->lc[0], ctx->lr[0], kf, ctx->tw_np, st));
+  CK(fft_xc2r(N, ctx->lc[4], ctx->lr[1], 0.f, ctx->tw_np, st));
+  CK(fft_xc2r(N, ctx->lc[1], ctx->lr[2], 0.f, ctx->tw_np, st));
+  CK(fft_xc2r(N, ctx->lc[2], ctx->lr[3], kf, ctx->tw_np, st));
+  CK(fft_xc2r(N, ctx->lc[5], ctx->lr[4], 0.f, ctx->tw_np, st));
+  CK(fft_xc2r(N, ctx->lc[3], ctx->lr[5], 0.f, ctx->tw_np, st));
+  ctx->have_lpt = true;
+  return COLA_OK;
+}
+
+// App. B: mesh force -grad(Phi_N + phi) at scale factor a from the density in ctx->rho.
+int run_force(cola_ctx* ctx, double a) {
+  const ForceParams fp = force_params(ctx, a);
+  const int N = ctx->Nm;
+  auto st = ctx->st;
+  const float2* tw = ctx->tw_nm;
+  CK(fft_xr2c(N, ctx->rho, ctx->Cd, fp.inv_rhobar, -1.f, tw, st));
+  CK(fft_col(N, ctx->Cd, 1, false, tw, st));
+  if (fp.screened) {
+    CK(mesh_z_screen_field(N, ctx->Cd, ctx->Ck, ctx->Cw, fp, tw, st));
+    CK(fft_col(N, ctx->Cw, 1, true, tw, st));
+    CK(mesh_x_screen_source(N, ctx->Cw, ctx->rho, ctx->Cd, fp, tw, st));
+    CK(fft_col(N, ctx->Cd, 1, false, tw, st));
+    CK(mesh_z_force(N, ctx->Cd, ctx->Ck, ctx->Cphi, ctx->Cphz, nullptr, fp, tw, st));
+  } else {
+    CK(mesh_z_force(N, ctx->Cd, nullptr, ctx->Cphi, ctx->Cphz, nullptr, fp, tw, st));
+  }
+  CK(fft_yinv2(N, ctx->Cphi, ctx->Cphi, ctx->Cw, -fp.kf, tw, st));
+  CK(fft_col(N, ctx->Cphz, 1, true, tw, st));
+  CK(fft_xc2r(N, ctx->Cphi, ctx->F[0], -fp.kf, tw, st));
+  CK(fft_xc2r(N, ctx->Cw, ctx->F[1], 0.f, tw, st));
+  CK(fft_xc2r(N, ctx->Cphz, ctx->F[2], 0.f, tw, st));
+  ctx->have_force = true;
+  return COLA_OK;
+}
+
+PartParams part_params(const cola_ctx* c) {
+  PartParams pp;
+  pp.Np = c->Np;
+  pp.Nm = c->Nm;
+  pp.lgNp = c->lgNp;
+  pp.cellscale = (float)(c->Nm / c->L);
+  pp.L = (float)c->L;
+  return pp;
+}
+
+// Particles on the LPT trajectory at a_ini, initial force and residual acceleration.
+int finish_ic(cola_ctx* ctx) {
+  const int N = ctx->Np;
+  if (ctx->cfg.seed_precision) {
+    for (int f = 0; f < 2; ++f) {
+      CK(seed_absmax(N, ctx->phi[f], ctx->scratch, ctx->st));
+      float amax = 0.f;
+      CK(cudaMemcpyAsync(&amax, ctx->scratch, sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+      CK(cudaStreamSynchronize(ctx->st));
+      // bf16: unit scale of the largest value; fp16: largest value at 2^15.
+      const float target = ctx->cfg.seed_precision == COLA_SEED_FP16 ? 32768.f : 1.f;
+      const float scale = amax > 0.f ? amax / target : 1.f;
+      ctx->seed_scale[f] = scale;
+      CK(seed_quantise(N, ctx->phi[f], ctx->seedq[f], ctx->cfg.seed_precision, 1.f / scale,
+                       ctx->st));
+    }
+  }
+  CHECK_RC(run_lpt(ctx, ctx->tab));
+  CK(ic_particles(ctx->P, ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->s[0], ctx->s[1], ctx->s[2],
+                  ctx->v[0], ctx->v[1], ctx->v[2], ctx->st));
+  const PartParams pp = part_params(ctx);
+  CK(cudaMemsetAsync(ctx->rho, 0, ctx->M * sizeof(float), ctx->st));
+  CK(part_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->rho, ctx->P, ctx->st));
+  CHECK_RC(run_force(ctx, ctx->a[0]));
+  CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
+                      ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[3], ctx->lr[4], ctx->lr[5],
+                      ctx->F[0], ctx->F[1], ctx->F[2], 0.f, ctx->P, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->step = 0;
+  ctx->ic_done = true;
+  return COLA_OK;
+}
+
+int copy_out(cola_ctx* ctx, void* dst, const void* src, size_t bytes, int where) {
+  CK(cudaMemcpyAsync(dst, src, bytes, where == COLA_HOST ? cudaMemcpyDeviceToHost
+                                                         : cudaMemcpyDeviceToDevice, ctx->st));
+  if (where == COLA_HOST) CK(cudaStreamSynchronize(ctx->st));
+  return COLA_OK;
+}
+
+int copy_in(cola_ctx* ctx, void* dst, const void* src, size_t bytes, int where) {
+  CK(cudaMemcpyAsync(dst, src, bytes, where == COLA_HOST ? cudaMemcpyHostToDevice
+                                                         : cudaMemcpyDeviceToDevice, ctx->st));
+  if (where == COLA_HOST) CK(cudaStreamSynchronize(ctx->st));
+  return COLA_OK;
+}
+
+// Dense [N][N][N/2+1] complex copy of a padded half spectrum (tmp: device dense buffer).
+int export_half(cola_ctx* ctx, int N, const float2* padded, float2* tmp, void* dst, int where) {
+  const size_t bytes = (size_t)N * N * (N / 2 + 1) * sizeof(float2);
+  if (where == COLA_DEVICE) {
+    CK(half_unpack(N, padded, static_cast<float2*>(dst), ctx->st));
+    return COLA_OK;
+  }
+  CK(half_unpack(N, padded, tmp, ctx->st));
+  return copy_out(ctx, dst, tmp, bytes, where);
+}
+
+}  // namespace
+
+extern "C" {
+
+int cola_init(const cola_config* cfg, cola_alloc_fn alloc, cola_free_fn free_fn, void* user,
+              void* stream, cola_ctx** out) {
+  if (!out) return fail(nullptr, COLA_EINVAL, "out is NULL");
+  *out = nullptr;
+  {
+    int rc = validate_cfg(cfg, nullptr);
+    if (rc) return rc;
+  }
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(nullptr, COLA_EINVAL, "give both alloc and free callbacks or neither");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(nullptr, COLA_ECUDA, "no CUDA device available");
+  }
+  cola_ctx* ctx = new cola_ctx();
+  ctx->cfg = *cfg;
+  ctx->st = static_cast<cudaStream_t>(stream);
+  ctx->alloc = alloc;
+  ctx->freef = free_fn;
+  ctx->user = user;
+  ctx->Np = cfg->Np;
+  ctx->Nm = cfg->Nmesh;
+  ctx->lgNp = ilog2i(cfg->Np);
+  ctx->L = cfg->Lbox;
+  ctx->nk = cfg->nk_table;
+  ctx->P = (int64_t)cfg->Np * cfg->Np * cfg->Np;
+  ctx->M = (int64_t)cfg->Nmesh * cfg->Nmesh * cfg->Nmesh;
+  ctx->a = a_nodes(*cfg);
+  const double Om = cfg->Omega_m;
+  for (int n = 0; n < cfg->nsteps; ++n) {
+    const double a0 = ctx->a[n], a1 = ctx->a[n + 1], am = 0.5 * (a0 + a1);
+    ctx->dtk1.push_back(hdtau(a0, am, Om));
+    ctx->dtd.push_back(hdtau(a0, a1, Om));
+    ctx->dtk2.push_back(hdtau(am, a1, Om));
+  }
+  std::vector<double> kdummy;
+  k_nodes(*cfg, ctx->lnk0, ctx->dlnk, kdummy);
+  int rc = COLA_OK;
+  const int64_t hp = half_elems(ctx->Np), hm = half_elems(ctx->Nm);
+  for (int d = 0; d < 3 && !rc; ++d) {
+    rc = alloc_buf(ctx, &ctx->s[d], ctx->P);
+    if (!rc) rc = alloc_buf(ctx, &ctx->v[d], ctx->P);
+    if (!rc) rc = alloc_buf(ctx, &ctx->acc[d], ctx->P);
+  }
+  for (int f = 0; f < 2 && !rc; ++f) {
+    rc = alloc_buf(ctx, &ctx->phi[f], hp);
+    if (!rc && cfg->seed_precision) {
+      uint32_t* q = nullptr;
+      rc = alloc_buf(ctx, &q, hp);
+      ctx->seedq[f] = q;
+    }
+  }
+  for (int i = 0; i < 6 && !rc; ++i) {
+    rc = alloc_buf(ctx, &ctx->lc[i], hp);
+    if (!rc) rc = alloc_buf(ctx, &ctx->lr[i], ctx->P);
+  }
+  if (!rc) rc = alloc_buf(ctx, &ctx->rho, ctx->M);
+  if (!rc) rc = alloc_buf(ctx, &ctx->Cd, hm);
+  if (!rc) rc = alloc_buf(ctx, &ctx->Ck, hm);
+  if (!rc) rc = alloc_buf(ctx, &ctx->Cw, hm);
+  if (!rc) rc = alloc_buf(ctx, &ctx->Cphi, hm);
+  if (!rc) rc = alloc_buf(ctx, &ctx->Cphz, hm);
+  for (int d = 0; d < 3 && !rc; ++d) rc = alloc_buf(ctx, &ctx->F[d], ctx->M);
+  if (!rc) rc = alloc_buf(ctx, &ctx->tab, (size_t)(cfg->nsteps + 1) * cfg->nk_table);
+  if (!rc) rc = alloc_buf(ctx, &ctx->vtab, (size_t)(cfg->nsteps + 1) * cfg->nk_table);
+  if (!rc) rc = alloc_buf(ctx, &ctx->pk_acc, 3 * kMaxBins);
+  if (!rc) rc = alloc_buf(ctx, &ctx->scratch, 64);
+  if (!rc) rc = upload_twiddles(ctx, ctx->Np, &ctx->tw_np);
+  if (!rc) rc = upload_twiddles(ctx, ctx->Nm, &ctx->tw_nm);
+  if (rc) {
+    g_err = ctx->err;
+    cola_free(ctx);
+    return rc;
+  }
+  ctx->eh = eh_params(cfg->Omega_m, cfg->Omega_b, cfg->h, cfg->n_s, cfg->sigma8);
+  {
+    HModel lc;
+    Growth g;
+    const double ai = ctx->a[0];
+    std::vector<double> nodes = {ai, 1.0};
+    solve_growth(lc, Om, nodes, std::vector<double>{1.0}, true, g);
+    ctx->Dratio = 1.0 / g.D1[1];
+  }
+  *out = ctx;
+  return COLA_OK;
+}
+
+int cola_set_model(cola_ctx* ctx, const cola_model* model) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  CHECK_RC(validate_model(model, ctx));
+  if (ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_set_model after cola_ic");
+  ctx->model = *model;
+  Growth g;
+  growth_for(ctx->cfg, *model, g, nullptr, nullptr, nullptr);
+  const int nk = ctx->nk, ns = ctx->cfg.nsteps;
+  std::vector<float4> tab((size_t)(ns + 1) * nk), vtab((size_t)(ns + 1) * nk);
+  for (int n = 0; n <= ns; ++n) {
+    for (int j = 0; j < nk; ++j) {
+      const size_t i = (size_t)n * nk + j;
+      float4 t;
+      if (n == 0) {
+        t = make_float4((float)g.D1[i], (float)g.D2[i], (float)g.ddD1[i], (float)g.ddD2[i]);
+      } else {
+        const size_t p = (size_t)(n - 1) * nk + j;
+        t = make_float4((float)(g.D1[i] - g.D1[p]), (float)(g.D2[i] - g.D2[p]), (float)g.ddD1[i],
+                        (float)g.ddD2[i]);
+      }
+      tab[i] = t;
+      vtab[i] = make_float4((float)g.dD1[i], (float)g.dD2[i], 0.f, 0.f);
+    }
+  }
+  CK(cudaMemcpyAsync(ctx->tab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->vtab, vtab.data(), vtab.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->model_set = true;
+  return COLA_OK;
+}
+
+int cola_ic(cola_ctx* ctx) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!ctx->model_set) return fail(ctx, COLA_ESTATE, "cola_ic before cola_set_model");
+  const int N = ctx->Np;
+  auto st = ctx->st;
+  const float kf = (float)(2.0 * kPi / ctx->L);
+  CK(ic_noise(N, ctx->cfg.seed, ctx->lr[0], st));
+  CHECK_RC(r2c3(ctx, N, ctx->lr[0], ctx->phi[0], ctx->tw_np, 1.f, 0.f));
+  EHDev eh;
+  eh.theta2 = ctx->eh.theta2;
+  eh.s = ctx->eh.s;
+  eh.alpha = ctx->eh.alpha;
+  eh.Omh = ctx->eh.Omh;
+  eh.h = ctx->eh.h;
+  eh.ns = ctx->eh.ns;
+  eh.amp = ctx->eh.amp * ctx->Dratio * ctx->Dratio;
+  eh.N3_over_L3 = (double)N * N * N / (ctx->L * ctx->L * ctx->L);
+  CK(ic_phi1(N, ctx->phi[0], kf, eh, st));
+  const int ij[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  for (int h = 0; h < 6; ++h) {
+    CK(ic_hessian(N, ctx->phi[0], ctx->lc[0], ij[h][0], ij[h][1], kf, st));
+    CHECK_RC(c2r3(ctx, N, ctx->lc[0], ctx->lr[h], ctx->tw_np));
+  }
+  float* src = reinterpret_cast<float*>(ctx->lc[1]);
+  CK(ic_source(ctx->P, ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->lr[3], ctx->lr[4], ctx->lr[5], src, st));
+  CHECK_RC(r2c3(ctx, N, src, ctx->phi[1], ctx->tw_np, 1.f, 0.f));
+  CK(ic_phi2(N, ctx->phi[1], kf, st));
+  return finish_ic(ctx);
+}
+
+int cola_ic_from_potentials(cola_ctx* ctx, const float* phi1, const float* phi2, int32_t where) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!phi1 || !phi2) return fail(ctx, COLA_EINVAL, "phi1/phi2 is NULL");
+  if (where != COLA_HOST && where != COLA_DEVICE) return fail(ctx, COLA_EINVAL, "bad where");
+  if (!ctx->model_set) return fail(ctx, COLA_ESTATE, "cola_ic_from_potentials before cola_set_model");
+  const int N = ctx->Np;
+  const size_t bytes = (size_t)N * N * (N / 2 + 1) * sizeof(float2);
+  const float* src[2] = {phi1, phi2};
+  for (int f = 0; f < 2; ++f) {
+    const float2* dense = reinterpret_cast<const float2*>(src[f]);
+    if (where == COLA_HOST) {
+      CHECK_RC(copy_in(ctx, ctx->lc[0], src[f], bytes, where));
+      dense = ctx->lc[0];
+    }
+    CK(half_pack(N, dense, ctx->phi[f], ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  return finish_ic(ctx);
+}
+
+int cola_step(cola_ctx* ctx, int32_t nsteps) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_step before cola_ic");
+  if (nsteps < 0) nsteps = ctx->cfg.nsteps - ctx->step;
+  if (ctx->step + nsteps > ctx->cfg.nsteps) return fail(ctx, COLA_EINVAL, "past the last step");
+  const PartParams pp = part_params(ctx);
+  for (int it = 0; it < nsteps; ++it) {
+    const int n = ctx->step;
+    CHECK_RC(run_lpt(ctx, ctx->tab + (size_t)(n + 1) * ctx->nk));
+    CK(cudaMemsetAsync(ctx->rho, 0, ctx->M * sizeof(float), ctx->st));
+    CK(part_drift_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
+                          ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[0], ctx->lr[1],
+                          ctx->lr[2], ctx->rho, (float)ctx->dtk1[n], (float)ctx->dtd[n], ctx->P,
+                          ctx->st));
+    CHECK_RC(run_force(ctx, ctx->a[n + 1]));
+    CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
+                        ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[3], ctx->lr[4],
+                        ctx->lr[5], ctx->F[0], ctx->F[1], ctx->F[2], (float)ctx->dtk2[n], ctx->P,
+                        ctx->st));
+    ctx->step = n + 1;
+  }
+  return COLA_OK;
+}
+
+int cola_snapshot(cola_ctx* ctx, float* pos, float* vel, int32_t where) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_snapshot before cola_ic");
+  if (where != COLA_HOST && where != COLA_DEVICE) return fail(ctx, COLA_EINVAL, "bad where");
+  if (!pos && !vel) return COLA_OK;
+  const size_t bytes = (size_t)ctx->P * 3 * sizeof(float);
+  if (vel) CHECK_RC(run_lpt(ctx, ctx->vtab + (size_t)ctx->step * ctx->nk));
+  const PartParams pp = part_params(ctx);
+  const float vscale = (float)(100.0 / ctx->a[ctx->step]);
+  if (where == COLA_DEVICE) {
+    CK(part_snapshot(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
+                     ctx->lr[0], ctx->lr[1], ctx->lr[2], vscale, pos, vel, ctx->P, ctx->st));
+    return COLA_OK;
+  }
+  // host: stage through the (step-scratch) mesh force buffers when they are big enough
+  Temp tp(ctx, pos ? bytes : 0), tv(ctx, vel ? bytes : 0);
+  if ((pos && !tp.p) || (vel && !tv.p)) return fail(ctx, COLA_ENOMEM, "snapshot staging allocation failed");
+  CK(part_snapshot(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
+                   ctx->lr[0], ctx->lr[1], ctx->lr[2], vscale, static_cast<float*>(tp.p),
+                   static_cast<float*>(tv.p), ctx->P, ctx->st));
+  if (pos) CK(cudaMemcpyAsync(pos, tp.p, bytes, cudaMemcpyDeviceToHost, ctx->st));
+  if (vel) CK(cudaMemcpyAsync(vel, tv.p, bytes, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return COLA_OK;
+}
+
+int cola_pk(cola_ctx* ctx, int32_t nbins, double* k, double* pk, int64_t* nmodes) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_pk before cola_ic");
+  if (nbins < 1 || nbins > kMaxBins) return fail(ctx, COLA_EINVAL, "nbins out of range 1..2000");
+  const int N = ctx->Nm;
+  const PartParams pp = part_params(ctx);
+  const ForceParams fp = force_params(ctx, ctx->a[ctx->step]);
+  CK(cudaMemsetAsync(ctx->rho, 0, ctx->M * sizeof(float), ctx->st));
+  CK(part_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->rho, ctx->P, ctx->st));
+  CHECK_RC(r2c3(ctx, N, ctx->rho, ctx->Cw, ctx->tw_nm, fp.inv_rhobar, -1.f));
+  CK(cudaMemsetAsync(ctx->pk_acc, 0, 3 * nbins * sizeof(double), ctx->st));
+  const double L = ctx->L, N3 = (double)N * N * N;
+  CK(pk_bin(N, ctx->Cw, nbins, ctx->pk_acc, L * L * L / (N3 * N3), ctx->st));
+  std::vector<double> h(3 * nbins);
+  CK(cudaMemcpyAsync(h.data(), ctx->pk_acc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  const double kf = 2.0 * kPi / L;
+  for (int b = 0; b < nbins; ++b) {
+    const double cnt = h[b];
+    if (k) k[b] = cnt > 0 ? h[2 * nbins + b] / cnt * kf : NAN;
+    if (pk) pk[b] = cnt > 0 ? h[nbins + b] / cnt : NAN;
+    if (nmodes) nmodes[b] = (int64_t)llround(cnt);
+  }
+  return COLA_OK;
+}
+
+double cola_scale_factor(const cola_ctx* ctx) { return ctx ? ctx->a[ctx->step] : NAN; }
+
+int32_t cola_steps_done(const cola_ctx* ctx) { return ctx ? ctx->step : -1; }
+
+const char* cola_last_error(const cola_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+void cola_free(cola_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->st);
+  for (void* p : ctx->allocs) dev_free(ctx, p);
+  if (!ctx->alloc) cudaStreamSynchronize(ctx->st);
+  cudaGetLastError();
+  delete ctx;
+}
+
+int cola_export(cola_ctx* ctx, int32_t which, void* dst, int32_t where) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!dst) return fail(ctx, COLA_EINVAL, "dst is NULL");
+  if (where != COLA_HOST && where != COLA_DEVICE) return fail(ctx, COLA_EINVAL, "bad where");
+  const size_t pb = (size_t)ctx->P * sizeof(float), mb = (size_t)ctx->M * sizeof(float);
+  char* d = static_cast<char*>(dst);
+  switch (which) {
+    case COLA_F_DISP:
+    case COLA_F_DV:
+    case COLA_F_ACC: {
+      if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "no particle state before cola_ic");
+      float* const* arr = which == COLA_F_DISP ? ctx->s : which == COLA_F_DV ? ctx->v : ctx->acc;
+      for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * pb, arr[c], pb, where));
+      return COLA_OK;
+    }
+    case COLA_F_RHO:
+      if (!ctx->have_force) return fail(ctx, COLA_ESTATE, "no deposit yet");
+      return copy_out(ctx, dst, ctx->rho, mb, where);
+    case COLA_F_DELTAK: {
+      if (!ctx->have_force) return fail(ctx, COLA_ESTATE, "no deposit yet");
+      const ForceParams fp = force_params(ctx, ctx->a[ctx->step]);
+      CHECK_RC(r2c3(ctx, ctx->Nm, ctx->rho, ctx->Cw, ctx->tw_nm, fp.inv_rhobar, -1.f));
+      return export_half(ctx, ctx->Nm, ctx->Cw, ctx->Cphi, dst, where);
+    }
+    case COLA_F_FORCE:
+      if (!ctx->have_force) return fail(ctx, COLA_ESTATE, "no force yet");
+      for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * mb, ctx->F[c], mb, where));
+      return COLA_OK;
+    case COLA_F_PHI1:
+    case COLA_F_PHI2:
+      if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "no seeds before cola_ic");
+      return export_half(ctx, ctx->Np, ctx->phi[which - COLA_F_PHI1], ctx->lc[5], dst, where);
+    case COLA_F_LPT_DISP:
+    case COLA_F_LPT_ACC: {
+      if (!ctx->have_lpt) return fail(ctx, COLA_ESTATE, "no LPT fields yet");
+      const int o = which == COLA_F_LPT_DISP ? 0 : 3;
+      for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * pb, ctx->lr[o + c], pb, where));
+      return COLA_OK;
+    }
+    default:
+      return fail(ctx, COLA_EINVAL, "unknown array id");
+  }
+}
+
+int cola_import_state(cola_ctx* ctx, const float* disp, const float* dv, const float* acc,
+                      int32_t steps_done, int32_t where) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_import_state before cola_ic");
+  if (!disp || !dv || !acc) return fail(ctx, COLA_EINVAL, "NULL state array");
+  if (steps_done < 0 || steps_done > ctx->cfg.nsteps) return fail(ctx, COLA_EINVAL, "steps_done out of range");
+  if (where != COLA_HOST && where != COLA_DEVICE) return fail(ctx, COLA_EINVAL, "bad where");
+  const size_t pb = (size_t)ctx->P * sizeof(float);
+  const float* src[3] = {disp, dv, acc};
+  float* const* dstv[3] = {ctx->s, ctx->v, ctx->acc};
+  for (int q = 0; q < 3; ++q)
+    for (int c = 0; c < 3; ++c)
+      CHECK_RC(copy_in(ctx, dstv[q][c], reinterpret_cast<const char*>(src[q]) + c * pb, pb, where));
+  ctx->step = steps_done;
+  return COLA_OK;
+}
+
+int cola_fft(cola_ctx* ctx, int32_t dir, const void* in, void* out, int32_t where) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!in || !out) return fail(ctx, COLA_EINVAL, "NULL buffer");
+  if (where != COLA_HOST && where != COLA_DEVICE) return fail(ctx, COLA_EINVAL, "bad where");
+  const int N = ctx->Nm;
+  const size_t rb = (size_t)ctx->M * sizeof(float);
+  const size_t cb = (size_t)N * N * (N / 2 + 1) * sizeof(float2);
+  if (dir == 1) {
+    const float* src = static_cast<const float*>(in);
+    if (where == COLA_HOST) {
+      CHECK_RC(copy_in(ctx, ctx->F[0], in, rb, where));
+      src = ctx->F[0];
+    }
+    CHECK_RC(r2c3(ctx, N, src, ctx->Cw, ctx->tw_nm, 1.f, 0.f));
+    return export_half(ctx, N, ctx->Cw, ctx->Cphi, out, where);
+  }
+  if (dir == -1) {
+    const float2* dense = static_cast<const float2*>(in);
+    if (where == COLA_HOST) {
+      CHECK_RC(copy_in(ctx, ctx->Cphi, in, cb, where));
+      dense = ctx->Cphi;
+    }
+    CK(half_pack(N, dense, ctx->Cw, ctx->st));
+    float* dst = where == COLA_DEVICE ? static_cast<float*>(out) : ctx->F[0];
+    CHECK_RC(c2r3(ctx, N, ctx->Cw, dst, ctx->tw_nm));
+    if (where == COLA_HOST) return copy_out(ctx, out, ctx->F[0], rb, where);
+    return COLA_OK;
+  }
+  return fail(ctx, COLA_EINVAL, "dir must be +1 or -1");
+}
+
+int cola_cic_deposit(cola_ctx* ctx, const float* pos, int64_t n, float* rho, int32_t where) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if ((!pos && n > 0) || !rho || n < 0) return fail(ctx, COLA_EINVAL, "bad buffers");
+  if (where != COLA_HOST && where != COLA_DEVICE) return fail(ctx, COLA_EINVAL, "bad where");
+  const float* dpos = pos;
+  Temp t(ctx, where == COLA_HOST && n > 0 ? (size_t)n * 3 * sizeof(float) : 0);
+  if (where == COLA_HOST && n > 0) {
+    if (!t.p) return fail(ctx, COLA_ENOMEM, "staging allocation failed");
+    CHECK_RC(copy_in(ctx, t.p, pos, (size_t)n * 3 * sizeof(float), where));
+    dpos = static_cast<const float*>(t.p);
+  }
+  CK(cudaMemsetAsync(ctx->rho, 0, ctx->M * sizeof(float), ctx->st));
+  CK(pos_deposit(ctx->Nm, (float)(ctx->Nm / ctx->L), dpos, n, ctx->rho, ctx->st));
+  return copy_out(ctx, rho, ctx->rho, (size_t)ctx->M * sizeof(float), where);
+}
+
+int cola_force_from_density(cola_ctx* ctx, const float* rho, double a, float* force,
+                            int32_t where) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!rho || !force) return fail(ctx, COLA_EINVAL, "NULL buffer");
+  if (!ctx->model_set) return fail(ctx, COLA_ESTATE, "no model set");
+  if (!(a > 0)) return fail(ctx, COLA_EINVAL, "a must be > 0");
+  if (where != COLA_HOST && where != COLA_DEVICE) return fail(ctx, COLA_EINVAL, "bad where");
+  const size_t mb = (size_t)ctx->M * sizeof(float);
+  CHECK_RC(copy_in(ctx, ctx->rho, rho, mb, where));
+  CHECK_RC(run_force(ctx, a));
+  char* d = reinterpret_cast<char*>(force);
+  for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * mb, ctx->F[c], mb, where));
+  return COLA_OK;
+}
+
+int cola_host_growth(const cola_config* cfg, const cola_model* model, double* out,
+                     double* k_nodes_out) {
+  g_err.clear();
+  int rc = validate_cfg(cfg, nullptr);
+  if (rc) return rc;
+  rc = validate_model(model, nullptr);
+  if (rc) return rc;
+  if (!out) return fail(nullptr, COLA_EINVAL, "out is NULL");
+  Growth g;
+  std::vector<double> k;
+  growth_for(*cfg, *model, g, &k, nullptr, nullptr);
+  const int nk = cfg->nk_table;
+  for (int n = 0; n <= cfg->nsteps; ++n) {
+    const std::vector<double>* cols[6] = {&g.D1, &g.dD1, &g.ddD1, &g.D2, &g.dD2, &g.ddD2};
+    for (int q = 0; q < 6; ++q)
+      std::memcpy(out + ((size_t)n * 6 + q) * nk, cols[q]->data() + (size_t)n * nk, nk * sizeof(double));
+  }
+  if (k_nodes_out) std::memcpy(k_nodes_out, k.data(), nk * sizeof(double));
+  return COLA_OK;
+}
+
+int cola_host_timesteps(const cola_config* cfg, double* out) {
+  g_err.clear();
+  int rc = validate_cfg(cfg, nullptr);
+  if (rc) return rc;
+  if (!out) return fail(nullptr, COLA_EINVAL, "out is NULL");
+  const std::vector<double> a = a_nodes(*cfg);
+  for (int n = 0; n < cfg->nsteps; ++n) {
+    const double a0 = a[n], a1 = a[n + 1], am = 0.5 * (a0 + a1);
+    out[4 * n + 0] = a1;
+    out[4 * n + 1] = hdtau(a0, am, cfg->Omega_m);
+    out[4 * n + 2] = hdtau(a0, a1, cfg->Omega_m);
+    out[4 * n + 3] = hdtau(am, a1, cfg->Omega_m);
+  }
+  return COLA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Internal declarations shared by the host code and the CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cola {
+
+// Row pitch (in complex elements) of every half spectrum: N/2+1 rounded up to
+// 16 so that column tiles of 2..16 elements never straddle a row.
+inline int64_t half_pitch(int N) { return ((N / 2 + 1 + 15) / 16) * 16; }
+inline int64_t half_elems(int N) { return (int64_t)N * N * half_pitch(N); }
+
+// Parameters of one force evaluation (App. B field equation).
+struct ForceParams {
+  float kf;          // 2 pi / L
+  float kappa_norm;  // kappa(a) / N^3 (the inverse transforms are unnormalised)
+  float C;           // fifth-force coupling C(a) (0 for LCDM)
+  float a2m2;        // a^2 m^2(a)  [(h/Mpc)^2]
+  float inv_rhobar;  // Nmesh^3 / Np^3
+  float fr_thr;      // f(R): Phi_crit(a) a^2 c^2, threshold on |Phi_N| in code units
+  float dgp_coef;    // nDGP: 8 (r_c H0)^2 Omega_m / (9 beta^2)
+  float R2half;      // nDGP: R_smooth^2 / 2
+  float norm;        // 1 / N^3
+  int model;         // 0 LCDM, 1 f(R), 2 nDGP
+  int screened;      // 1: screened fifth force
+};
+
+// Parameters of the per-k LPT reweight (Sec. 4.1): table of float4 per log-k node.
+struct LptParams {
+  const float4* tab;  // nk nodes: (c1, c2, e1, e2)
+  float lnk0, inv_dlnk;
+  int nk;
+  float kf;           // 2 pi / L
+  float norm;         // 1 / Np^3
+  float seed_scale1, seed_scale2;  // dequantisation scales of phi1, phi2 (1 for fp32)
+  int seed_prec;      // 0 fp32, 1 bf16, 2 fp16
+};
+
+// Lattice/particle parameters.
+struct PartParams {
+  int Np, Nm, lgNp;
+  float cellscale;  // Nm / L
+  float L;
+};
+
+// ------------------------------------------------------------------ FFT passes
+// All launchers return cudaGetLastError() of their launch.
+cudaError_t fft_xr2c(int N, const float* in, float2* out, float scale, float offset,
+                     const float2* tw, cudaStream_t s);
+cudaError_t fft_xc2r(int N, const float2* in, float* out, float kfs, const float2* tw,
+                     cudaStream_t s);
+// axis 1 = y, 2 = z; in place
+cudaError_t fft_col(int N, float2* data, int axis, bool inv, const float2* tw, cudaStream_t s);
+// y inverse pass producing the plain transform (out_plain may alias in) and the
+// transform of (i kfs f_y) times the input (out_deriv).
+cudaError_t fft_yinv2(int N, const float2* in, float2* out_plain, float2* out_deriv, float kfs,
+                      const float2* tw, cudaStream_t s);
+// Screening field: forward z of delta (after x, y) -> delta(k) stored in dk_out;
+// Phi_N(k) (f(R)) or W(kR) delta(k) (nDGP) -> inverse z -> w_out.
+cudaError_t mesh_z_screen_field(int N, const float2* in, float2* dk_out, float2* w_out,
+                                const ForceParams& fp, const float2* tw, cudaStream_t s);
+// S = delta eps: c2r of the screening field rows, eps, times delta from rho, r2c.
+cudaError_t mesh_x_screen_source(int N, const float2* w_in, const float* rho, float2* s_out,
+                                 const ForceParams& fp, const float2* tw, cudaStream_t s);
+// Forward z of the source (S or delta), Phi_tot(k) and -i kz Phi_tot, inverse z.
+// dk may be null when unscreened; dk_keep (optional) receives the forward
+// spectrum of `in` when unscreened.
+cudaError_t mesh_z_force(int N, const float2* in, const float2* dk, float2* phi_out,
+                         float2* phiz_out, float2* dk_keep, const ForceParams& fp,
+                         const float2* tw, cudaStream_t s);
+// LPT: phi1, phi2 -> (c1 phi1 + c2 phi2), i kz (...), (e1 phi1 + e2 phi2), i kz (...),
+// each inverse-transformed along z.  phi1/phi2 point to float2 (fp32) or
+// 2 x 16-bit pairs (bf16/fp16) according to lp.seed_prec.
+cudaError_t lpt_z(int N, const void* phi1, const void* phi2, float2* o0, float2* o1, float2* o2,
+                  float2* o3, const LptParams& lp, const float2* tw, cudaStream_t s);
+
+// ------------------------------------------------------------------ particles
+cudaError_t part_deposit(const PartParams& pp, const float* sx, const float* sy, const float* sz,
+                         float* rho, int64_t P, cudaStream_t s);
+cudaError_t part_drift_deposit(const PartParams& pp, float* sx, float* sy, float* sz, float* vx,
+                               float* vy, float* vz, const float* ax, const float* ay,
+                               const float* az, const float* dpx, const float* dpy,
+                               const float* dpz, float* rho, float dtk, float dtd, int64_t P,
+                               cudaStream_t s);
+cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float* sy,
+                             const float* sz, float* vx, float* vy, float* vz, float* ax,
+                             float* ay, float* az, const float* Ax, const float* Ay,
+                             const float* Az, const float* Fx, const float* Fy, const float* Fz,
+                             float dtk, int64_t P, cudaStream_t s);
+cudaError_t part_snapshot(const PartParams& pp, const float* sx, const float* sy, const float* sz,
+                          const float* vx, const float* vy, const float* vz, const float* lx,
+                          const float* ly, const float* lz, float vscale, float* pos, float* vel,
+                          int64_t P, cudaStream_t s);
+cudaError_t pos_deposit(int Nm, float cellscale, const float* pos, int64_t n, float* rho,
+                        cudaStream_t s);
+cudaError_t pk_bin(int N, const float2* dk, int nbins, double* acc, double norm,
+                   cudaStream_t s);
+
+// ------------------------------------------------------------------ initial conditions
+struct EHDev {
+  double theta2, s, alpha, Omh, h, ns, amp;  // amp: A (D(a_ini)/D(1))^2
+  double N3_over_L3;
+};
+cudaError_t ic_noise(int N, uint64_t seed, float* out, cudaStream_t s);
+// delta(k) = G(k) sqrt(P(k) N^3/L^3); phi1 = delta/k^2 (k = 0 -> 0), in place on c.
+cudaError_t ic_phi1(int N, float2* c, float kf, const EHDev& eh, cudaStream_t s);
+// out = -k_i k_j / N^3 * phi1 with the Nyquist rule for i != j.
+cudaError_t ic_hessian(int N, const float2* phi1, float2* out, int i, int j, float kf,
+                       cudaStream_t s);
+cudaError_t ic_source(int64_t n, const float* hxx, const float* hyy, const float* hzz,
+                      const float* hxy, const float* hxz, const float* hyz, float* src,
+                      cudaStream_t s);
+// phi2 = -src(k)/k^2 in place.
+cudaError_t ic_phi2(int N, float2* c, float kf, cudaStream_t s);
+cudaError_t ic_particles(int64_t P, const float* px, const float* py, const float* pz, float* sx,
+                         float* sy, float* sz, float* vx, float* vy, float* vz,
+                         cudaStream_t s);
+// pack a dense [N][N][N/2+1] half spectrum into / out of the padded layout
+cudaError_t half_pack(int N, const float2* dense, float2* padded, cudaStream_t s);
+cudaError_t half_unpack(int N, const float2* padded, float2* dense, cudaStream_t s);
+// seed fields in reduced precision
+cudaError_t seed_quantise(int N, const float2* src, void* dst, int prec, float inv_scale,
+                          cudaStream_t s);
+cudaError_t seed_absmax(int N, const float2* src, float* out_absmax, cudaStream_t s);
+
+}  // namespace cola

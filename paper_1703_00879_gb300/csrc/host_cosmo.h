@@ -1,0 +1,41 @@
+// Host-side double-precision background, model functions and growth tables.
+#pragma once
+#include <vector>
+
+namespace cola {
+
+constexpr double kCLight = 2997.92458;  // c in (Mpc/h) H0
+constexpr double kH0OverC = 1.0 / kCLight;
+constexpr double kPi = 3.14159265358979323846;
+
+struct HModel {
+  int kind = 0;  // 0 LCDM, 1 f(R), 2 nDGP
+  double fR0 = 0, rcH0 = 0, R_smooth = 1;
+  int screening = 0, scale_dependent = 1;
+};
+
+double hE(double a, double Om);
+double hdlnE_da(double a, double Om);
+// Delta tau = int_{a1}^{a2} da / (a^3 E(a)) (Sec. 1: dtau = dt/a^2).
+double hdtau(double a1, double a2, double Om);
+
+double fr_m2(double a, double Om, double fR0);       // (h/Mpc)^2
+double fr_fR(double a, double Om, double fR0);       // |f_R(a)|
+double dgp_beta(double a, double Om, double rcH0);
+
+// Growth tables at a-nodes (Sec. 4.1, Eq. fofrapprox), row-major [na][nk].
+struct Growth {
+  int na = 0, nk = 0;
+  std::vector<double> D1, dD1, ddD1, D2, dD2, ddD2;
+};
+void solve_growth(const HModel& m, double Om, const std::vector<double>& a_nodes,
+                  const std::vector<double>& k, bool lcdm_growth, Growth& out);
+
+// Eisenstein-Hu no-wiggle spectrum parameters; amp normalises P(k, z=0) to sigma8.
+struct EHParams {
+  double theta2, s, alpha, Omh, h, ns, amp;
+};
+EHParams eh_params(double Om, double Ob, double h, double ns, double sigma8);
+double eh_T(const EHParams& e, double k);
+
+}  // namespace cola

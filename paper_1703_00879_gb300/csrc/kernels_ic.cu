@@ -1,0 +1,261 @@
+// Initial-condition kernels (run once per simulation, not on the step path):
+// Philox white noise, the Gaussian delta(k), phi1 = delta/k^2 (Sec. 3.1), the
+// Hessian of phi1 and the 2LPT source of Eq. lcdm2lpt (Sec. 3.2), phi2, the
+// initial particle state, layout packing and reduced-precision seed storage.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "cola_internal.h"
+
+namespace cola {
+namespace {
+
+constexpr int NTI = 256;
+
+inline unsigned blocks_for(int64_t n) { return (unsigned)((n + NTI - 1) / NTI); }
+
+// Philox-4x32-10 (Salmon et al., SC'11): ten rounds of the multiply-xor
+// bijection with multipliers 0xD2511F53, 0xCD9E8D57 and Weyl key increments
+// 0x9E3779B9, 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Unit Gaussian per lattice point: counter (idx lo, idx hi, 0, 0), key = seed,
+// u_i = (w_i + 1/2) / 2^32, g = sqrt(-2 ln u1) cos(2 pi u2) in double precision.
+__global__ void k_noise(int64_t n, uint32_t k0, uint32_t k1, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * NTI + threadIdx.x;
+  if (i >= n) return;
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 0u, 0u), k0, k1);
+  const double u1 = ((double)r.x + 0.5) * (1.0 / 4294967296.0);
+  const double u2 = ((double)r.y + 0.5) * (1.0 / 4294967296.0);
+  out[i] = (float)(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
+}
+
+struct Mode {
+  int ix, fy, fz;
+  bool nyx, nyy, nyz;
+};
+
+__device__ __forceinline__ Mode mode_of(int64_t m, int N, int64_t P, bool& valid) {
+  Mode md;
+  const int ix = (int)(m % P);
+  const int64_t rest = m / P;
+  const int iy = (int)(rest % N), iz = (int)(rest / N);
+  valid = ix <= N / 2;
+  md.ix = ix;
+  md.fy = iy < N / 2 ? iy : iy - N;
+  md.fz = iz < N / 2 ? iz : iz - N;
+  md.nyx = ix == N / 2;
+  md.nyy = iy == N / 2;
+  md.nyz = iz == N / 2;
+  return md;
+}
+
+// Eisenstein & Hu (1998) no-wiggle transfer function, k in h/Mpc.
+__device__ double eh_T(const EHDev& e, double k) {
+  const double kmpc = k * e.h;
+  const double x = 0.43 * kmpc * e.s;
+  const double x2 = x * x;
+  const double gamma = e.Omh * (e.alpha + (1.0 - e.alpha) / (1.0 + x2 * x2));
+  const double q = k * e.theta2 / gamma;
+  const double L0 = log(2.0 * 2.718281828459045235 + 1.8 * q);
+  const double C0 = 14.2 + 731.0 / (1.0 + 62.5 * q);
+  return L0 / (L0 + C0 * q * q);
+}
+
+__global__ void k_ic_phi1(int N, int64_t P, float2* __restrict__ c, float kf, EHDev eh) {
+  const int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x;
+  if (m >= (int64_t)N * N * P) return;
+  bool valid;
+  const Mode md = mode_of(m, N, P, valid);
+  if (!valid) return;
+  const double n2 = (double)md.ix * md.ix + (double)md.fy * md.fy + (double)md.fz * md.fz;
+  float2 v = c[m];
+  if (n2 == 0.0) {
+    c[m] = make_float2(0.f, 0.f);
+    return;
+  }
+  const double k = (double)kf * sqrt(n2);
+  const double T = eh_T(eh, k);
+  const double pk = eh.amp * pow(k, eh.ns) * T * T;
+  const double f = sqrt(pk * eh.N3_over_L3) / (k * k);
+  c[m] = make_float2((float)(v.x * f), (float)(v.y * f));
+}
+
+__global__ void k_ic_hessian(int N, int64_t P, const float2* __restrict__ phi1,
+                             float2* __restrict__ out, int i, int j, float kf, float norm) {
+  const int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x;
+  if (m >= (int64_t)N * N * P) return;
+  bool valid;
+  const Mode md = mode_of(m, N, P, valid);
+  if (!valid) return;
+  const float kv[3] = {kf * md.ix, kf * md.fy, kf * md.fz};
+  const bool ny[3] = {md.nyx, md.nyy, md.nyz};
+  float f = -kv[i] * kv[j] * norm;
+  if (i != j && (ny[i] || ny[j])) f = 0.f;
+  const float2 v = phi1[m];
+  out[m] = make_float2(v.x * f, v.y * f);
+}
+
+// sum_{i<j} (phi_ii phi_jj - phi_ij^2) = 1/2 [(lap phi)^2 - (phi_ij)^2]
+__global__ void k_ic_source(int64_t n, const float* __restrict__ hxx,
+                            const float* __restrict__ hyy, const float* __restrict__ hzz,
+                            const float* __restrict__ hxy, const float* __restrict__ hxz,
+                            const float* __restrict__ hyz, float* __restrict__ src) {
+  const int64_t i = (int64_t)blockIdx.x * NTI + threadIdx.x;
+  if (i >= n) return;
+  const float a = hxx[i], b = hyy[i], c = hzz[i], d = hxy[i], e = hxz[i], f = hyz[i];
+  src[i] = (a * b - d * d) + (a * c - e * e) + (b * c - f * f);
+}
+
+__global__ void k_ic_phi2(int N, int64_t P, float2* __restrict__ c, float kf) {
+  const int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x;
+  if (m >= (int64_t)N * N * P) return;
+  bool valid;
+  const Mode md = mode_of(m, N, P, valid);
+  if (!valid) return;
+  const float k2 = kf * kf * ((float)md.ix * md.ix + (float)md.fy * md.fy + (float)md.fz * md.fz);
+  const float2 v = c[m];
+  c[m] = k2 > 0.f ? make_float2(-v.x / k2, -v.y / k2) : make_float2(0.f, 0.f);
+}
+
+__global__ void k_ic_particles(int64_t P, const float* __restrict__ px,
+                               const float* __restrict__ py, const float* __restrict__ pz,
+                               float* __restrict__ sx, float* __restrict__ sy,
+                               float* __restrict__ sz, float* __restrict__ vx,
+                               float* __restrict__ vy, float* __restrict__ vz) {
+  const int64_t i = (int64_t)blockIdx.x * NTI + threadIdx.x;
+  if (i >= P) return;
+  sx[i] = px[i];
+  sy[i] = py[i];
+  sz[i] = pz[i];
+  vx[i] = 0.f;
+  vy[i] = 0.f;
+  vz[i] = 0.f;
+}
+
+__global__ void k_half_pack(int N, int64_t P, const float2* __restrict__ dense,
+                            float2* __restrict__ padded, bool to_padded) {
+  const int64_t W = N / 2 + 1;
+  const int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x;
+  if (m >= (int64_t)N * N * W) return;
+  const int64_t row = m / W, k = m % W;
+  if (to_padded) padded[row * P + k] = dense[m];
+  else const_cast<float2*>(dense)[m] = padded[row * P + k];
+}
+
+__global__ void k_absmax(int64_t n, int N, int64_t P, const float2* __restrict__ src,
+                         unsigned int* __restrict__ out) {
+  float mx = 0.f;
+  for (int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x; m < n;
+       m += (int64_t)gridDim.x * NTI) {
+    if ((int)(m % P) > N / 2) continue;
+    const float2 v = src[m];
+    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
+}
+
+__global__ void k_quantise(int64_t n, const float2* __restrict__ src, uint32_t* __restrict__ dst,
+                           int prec, float inv_scale) {
+  const int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x;
+  if (m >= n) return;
+  const float2 v = src[m];
+  uint32_t lo, hi;
+  if (prec == 1) {
+    lo = __bfloat16_as_ushort(__float2bfloat16_rn(v.x * inv_scale));
+    hi = __bfloat16_as_ushort(__float2bfloat16_rn(v.y * inv_scale));
+  } else {
+    lo = __half_as_ushort(__float2half_rn(v.x * inv_scale));
+    hi = __half_as_ushort(__float2half_rn(v.y * inv_scale));
+  }
+  dst[m] = lo | (hi << 16);
+}
+
+}  // namespace
+
+cudaError_t ic_noise(int N, uint64_t seed, float* out, cudaStream_t s) {
+  const int64_t n = (int64_t)N * N * N;
+  k_noise<<<blocks_for(n), NTI, 0, s>>>(n, (uint32_t)seed, (uint32_t)(seed >> 32), out);
+  return cudaGetLastError();
+}
+
+cudaError_t ic_phi1(int N, float2* c, float kf, const EHDev& eh, cudaStream_t s) {
+  const int64_t n = half_elems(N);
+  k_ic_phi1<<<blocks_for(n), NTI, 0, s>>>(N, half_pitch(N), c, kf, eh);
+  return cudaGetLastError();
+}
+
+cudaError_t ic_hessian(int N, const float2* phi1, float2* out, int i, int j, float kf,
+                       cudaStream_t s) {
+  const int64_t n = half_elems(N);
+  const float norm = (float)(1.0 / ((double)N * N * N));
+  k_ic_hessian<<<blocks_for(n), NTI, 0, s>>>(N, half_pitch(N), phi1, out, i, j, kf, norm);
+  return cudaGetLastError();
+}
+
+cudaError_t ic_source(int64_t n, const float* hxx, const float* hyy, const float* hzz,
+                      const float* hxy, const float* hxz, const float* hyz, float* src,
+                      cudaStream_t s) {
+  k_ic_source<<<blocks_for(n), NTI, 0, s>>>(n, hxx, hyy, hzz, hxy, hxz, hyz, src);
+  return cudaGetLastError();
+}
+
+cudaError_t ic_phi2(int N, float2* c, float kf, cudaStream_t s) {
+  const int64_t n = half_elems(N);
+  k_ic_phi2<<<blocks_for(n), NTI, 0, s>>>(N, half_pitch(N), c, kf);
+  return cudaGetLastError();
+}
+
+cudaError_t ic_particles(int64_t P, const float* px, const float* py, const float* pz, float* sx,
+                         float* sy, float* sz, float* vx, float* vy, float* vz,
+                         cudaStream_t s) {
+  k_ic_particles<<<blocks_for(P), NTI, 0, s>>>(P, px, py, pz, sx, sy, sz, vx, vy, vz);
+  return cudaGetLastError();
+}
+
+cudaError_t half_pack(int N, const float2* dense, float2* padded, cudaStream_t s) {
+  const int64_t n = (int64_t)N * N * (N / 2 + 1);
+  k_half_pack<<<blocks_for(n), NTI, 0, s>>>(N, half_pitch(N), dense, padded, true);
+  return cudaGetLastError();
+}
+
+cudaError_t half_unpack(int N, const float2* padded, float2* dense, cudaStream_t s) {
+  const int64_t n = (int64_t)N * N * (N / 2 + 1);
+  k_half_pack<<<blocks_for(n), NTI, 0, s>>>(N, half_pitch(N), dense, const_cast<float2*>(padded),
+                                            false);
+  return cudaGetLastError();
+}
+
+cudaError_t seed_absmax(int N, const float2* src, float* out_absmax, cudaStream_t s) {
+  const int64_t n = half_elems(N);
+  cudaError_t e = cudaMemsetAsync(out_absmax, 0, sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)std::min<int64_t>((n + NTI - 1) / NTI, 152 * 16);
+  k_absmax<<<grid, NTI, 0, s>>>(n, N, half_pitch(N), src,
+                                reinterpret_cast<unsigned int*>(out_absmax));
+  return cudaGetLastError();
+}
+
+cudaError_t seed_quantise(int N, const float2* src, void* dst, int prec, float inv_scale,
+                          cudaStream_t s) {
+  const int64_t n = half_elems(N);
+  k_quantise<<<blocks_for(n), NTI, 0, s>>>(n, src, static_cast<uint32_t*>(dst), prec, inv_scale);
+  return cudaGetLastError();
+}
+
+}  // namespace cola

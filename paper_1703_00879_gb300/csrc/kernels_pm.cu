@@ -1,0 +1,292 @@
+// Particle kernels of the COLA step: drift with cloud-in-cell deposit, CIC
+// gather with kick, snapshot, and the P(k) binning.
+//
+// Particles stay in Lagrangian order (p = (z Np + y) Np + x), so the lattice
+// point q is implicit and the LPT fields are read at index p (App. A: each
+// particle needs the displacement field at its original lattice point).  The
+// displacement s = x - q is stored instead of x, and the mesh coordinate is
+// formed as integer + fraction (q's cell split exactly, then s Nm/L added to the
+// fractional part), so float positions keep ~1e-6 cell resolution at any box size.
+#include <algorithm>
+
+#include "cola_internal.h"
+
+namespace cola {
+namespace {
+
+constexpr int NTP = 256;
+
+struct Cic {
+  int i0[3], i1[3];
+  float f[3];
+};
+
+// Cell indices and CIC fractions of the particle at lattice (ix, iy, iz) with displacement s.
+__device__ __forceinline__ Cic cic_setup(const PartParams& pp, int ix, int iy, int iz, float sx,
+                                        float sy, float sz) {
+  Cic c;
+  const int li[3] = {ix, iy, iz};
+  const float sv[3] = {sx, sy, sz};
+  const int mask = pp.Nm - 1;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int num = li[d] * pp.Nm;  // q in cells = num / Np
+    const int base = num >> pp.lgNp;
+    const float qf = (float)(num - (base << pp.lgNp)) / (float)pp.Np;
+    const float u = qf + sv[d] * pp.cellscale;
+    const float fl = floorf(u);
+    c.f[d] = u - fl;
+    c.i0[d] = (base + (int)fl) & mask;
+    c.i1[d] = (c.i0[d] + 1) & mask;
+  }
+  return c;
+}
+
+__device__ __forceinline__ void cic_deposit(float* __restrict__ rho, int Nm, const Cic& c) {
+  const float wx0 = 1.f - c.f[0], wx1 = c.f[0];
+  const float wy0 = 1.f - c.f[1], wy1 = c.f[1];
+  const float wz0 = 1.f - c.f[2], wz1 = c.f[2];
+  const int64_t z0 = (int64_t)c.i0[2] * Nm, z1 = (int64_t)c.i1[2] * Nm;
+  const int64_t r00 = (z0 + c.i0[1]) * Nm, r01 = (z0 + c.i1[1]) * Nm;
+  const int64_t r10 = (z1 + c.i0[1]) * Nm, r11 = (z1 + c.i1[1]) * Nm;
+  atomicAdd(rho + r00 + c.i0[0], wz0 * wy0 * wx0);
+  atomicAdd(rho + r00 + c.i1[0], wz0 * wy0 * wx1);
+  atomicAdd(rho + r01 + c.i0[0], wz0 * wy1 * wx0);
+  atomicAdd(rho + r01 + c.i1[0], wz0 * wy1 * wx1);
+  atomicAdd(rho + r10 + c.i0[0], wz1 * wy0 * wx0);
+  atomicAdd(rho + r10 + c.i1[0], wz1 * wy0 * wx1);
+  atomicAdd(rho + r11 + c.i0[0], wz1 * wy1 * wx0);
+  atomicAdd(rho + r11 + c.i1[0], wz1 * wy1 * wx1);
+}
+
+__device__ __forceinline__ float cic_interp(const float* __restrict__ F, int Nm, const Cic& c) {
+  const float wx0 = 1.f - c.f[0], wx1 = c.f[0];
+  const float wy0 = 1.f - c.f[1], wy1 = c.f[1];
+  const float wz0 = 1.f - c.f[2], wz1 = c.f[2];
+  const int64_t z0 = (int64_t)c.i0[2] * Nm, z1 = (int64_t)c.i1[2] * Nm;
+  const int64_t r00 = (z0 + c.i0[1]) * Nm, r01 = (z0 + c.i1[1]) * Nm;
+  const int64_t r10 = (z1 + c.i0[1]) * Nm, r11 = (z1 + c.i1[1]) * Nm;
+  const float a00 = wx0 * __ldg(F + r00 + c.i0[0]) + wx1 * __ldg(F + r00 + c.i1[0]);
+  const float a01 = wx0 * __ldg(F + r01 + c.i0[0]) + wx1 * __ldg(F + r01 + c.i1[0]);
+  const float a10 = wx0 * __ldg(F + r10 + c.i0[0]) + wx1 * __ldg(F + r10 + c.i1[0]);
+  const float a11 = wx0 * __ldg(F + r11 + c.i0[0]) + wx1 * __ldg(F + r11 + c.i1[0]);
+  return wz0 * (wy0 * a00 + wy1 * a01) + wz1 * (wy0 * a10 + wy1 * a11);
+}
+
+__device__ __forceinline__ void lattice(const PartParams& pp, int64_t p, int& ix, int& iy, int& iz) {
+  const int m = pp.Np - 1;
+  ix = (int)(p & m);
+  iy = (int)((p >> pp.lgNp) & m);
+  iz = (int)(p >> (2 * pp.lgNp));
+}
+
+__global__ void __launch_bounds__(NTP) k_deposit(PartParams pp, const float* __restrict__ sx,
+                                                 const float* __restrict__ sy,
+                                                 const float* __restrict__ sz,
+                                                 float* __restrict__ rho, int64_t P) {
+  const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
+  if (p >= P) return;
+  int ix, iy, iz;
+  lattice(pp, p, ix, iy, iz);
+  cic_deposit(rho, pp.Nm, cic_setup(pp, ix, iy, iz, sx[p], sy[p], sz[p]));
+}
+
+// Sec. 2 drift in the LPT frame: delta_v += acc dtk (closing the previous
+// half kick), s += delta_v dtd + dPsi_LPT(q); then CIC deposit of x = q + s.
+__global__ void __launch_bounds__(NTP) k_drift_deposit(
+    PartParams pp, float* __restrict__ sx, float* __restrict__ sy, float* __restrict__ sz,
+    float* __restrict__ vx, float* __restrict__ vy, float* __restrict__ vz,
+    const float* __restrict__ ax, const float* __restrict__ ay, const float* __restrict__ az,
+    const float* __restrict__ dpx, const float* __restrict__ dpy,
+    const float* __restrict__ dpz, float* __restrict__ rho, float dtk, float dtd, int64_t P) {
+  const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
+  if (p >= P) return;
+  const float ux = vx[p] + ax[p] * dtk;
+  const float uy = vy[p] + ay[p] * dtk;
+  const float uz = vz[p] + az[p] * dtk;
+  const float nx = sx[p] + ux * dtd + dpx[p];
+  const float ny = sy[p] + uy * dtd + dpy[p];
+  const float nz = sz[p] + uz * dtd + dpz[p];
+  vx[p] = ux;
+  vy[p] = uy;
+  vz[p] = uz;
+  sx[p] = nx;
+  sy[p] = ny;
+  sz[p] = nz;
+  int ix, iy, iz;
+  lattice(pp, p, ix, iy, iz);
+  cic_deposit(rho, pp.Nm, cic_setup(pp, ix, iy, iz, nx, ny, nz));
+}
+
+// Sec. 2 kick: acc = g(x) - A_LPT(q), delta_v += acc dtk.
+__global__ void __launch_bounds__(NTP) k_gather_kick(
+    PartParams pp, const float* __restrict__ sx, const float* __restrict__ sy,
+    const float* __restrict__ sz, float* __restrict__ vx, float* __restrict__ vy,
+    float* __restrict__ vz, float* __restrict__ ax, float* __restrict__ ay,
+    float* __restrict__ az, const float* __restrict__ Ax, const float* __restrict__ Ay,
+    const float* __restrict__ Az, const float* __restrict__ Fx, const float* __restrict__ Fy,
+    const float* __restrict__ Fz, float dtk, int64_t P) {
+  const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
+  if (p >= P) return;
+  int ix, iy, iz;
+  lattice(pp, p, ix, iy, iz);
+  const Cic c = cic_setup(pp, ix, iy, iz, sx[p], sy[p], sz[p]);
+  const float gx = cic_interp(Fx, pp.Nm, c) - Ax[p];
+  const float gy = cic_interp(Fy, pp.Nm, c) - Ay[p];
+  const float gz = cic_interp(Fz, pp.Nm, c) - Az[p];
+  ax[p] = gx;
+  ay[p] = gy;
+  az[p] = gz;
+  vx[p] += gx * dtk;
+  vy[p] += gy * dtk;
+  vz[p] += gz * dtk;
+}
+
+__global__ void __launch_bounds__(NTP) k_snapshot(
+    PartParams pp, const float* __restrict__ sx, const float* __restrict__ sy,
+    const float* __restrict__ sz, const float* __restrict__ vx, const float* __restrict__ vy,
+    const float* __restrict__ vz, const float* __restrict__ lx, const float* __restrict__ ly,
+    const float* __restrict__ lz, float vscale, float* __restrict__ pos,
+    float* __restrict__ vel, int64_t P) {
+  const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
+  if (p >= P) return;
+  int li[3];
+  lattice(pp, p, li[0], li[1], li[2]);
+  const float sv[3] = {sx[p], sy[p], sz[p]};
+  if (pos) {
+    const double L = pp.L;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double x = (double)li[d] * (L / pp.Np) + (double)sv[d];
+      x -= L * floor(x / L);
+      if (x >= L) x -= L;
+      pos[p * 3 + d] = (float)x;
+    }
+  }
+  if (vel) {
+    vel[p * 3 + 0] = (vx[p] + lx[p]) * vscale;
+    vel[p * 3 + 1] = (vy[p] + ly[p]) * vscale;
+    vel[p * 3 + 2] = (vz[p] + lz[p]) * vscale;
+  }
+}
+
+__global__ void __launch_bounds__(NTP) k_pos_deposit(int Nm, float cellscale,
+                                                     const float* __restrict__ pos, int64_t n,
+                                                     float* __restrict__ rho) {
+  const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
+  if (p >= n) return;
+  Cic c;
+  const int mask = Nm - 1;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float u = pos[p * 3 + d] * cellscale;
+    const float fl = floorf(u);
+    c.f[d] = u - fl;
+    const int64_t ii = (int64_t)fl;
+    c.i0[d] = (int)(ii & mask);
+    c.i1[d] = (c.i0[d] + 1) & mask;
+  }
+  cic_deposit(rho, Nm, c);
+}
+
+// P(k) estimator: per mode of the half spectrum, bin b = floor(|n| - 1/2) (decided
+// in double precision), weight 1 on the kx = 0, N/2 planes and 2 elsewhere,
+// |delta|^2 norm / W_CIC^2 with W_CIC = prod sinc^2(pi n_i/N).  acc holds
+// [count | sum P | sum |k| in units of k_F] per bin.
+__global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, int N,
+                                                int64_t P, int nbins,
+                                                double* __restrict__ acc, double norm) {
+  extern __shared__ double sh[];
+  for (int i = threadIdx.x; i < 3 * nbins; i += NTP) sh[i] = 0.0;
+  __syncthreads();
+  const int64_t nmodes = (int64_t)N * N * (N / 2 + 1);
+  for (int64_t m = (int64_t)blockIdx.x * NTP + threadIdx.x; m < nmodes;
+       m += (int64_t)gridDim.x * NTP) {
+    const int ix = (int)(m % (N / 2 + 1));
+    const int64_t rest = m / (N / 2 + 1);
+    const int iy = (int)(rest % N), iz = (int)(rest / N);
+    const int nx = ix, ny = iy < N / 2 ? iy : iy - N, nz = iz < N / 2 ? iz : iz - N;
+    const double nmag = sqrt((double)nx * nx + (double)ny * ny + (double)nz * nz);
+    if (nmag < 0.5) continue;
+    const int b = (int)floor(nmag - 0.5);
+    if (b >= nbins) continue;
+    const double pi = 3.14159265358979323846;
+    double w = 1.0;
+    const int nn[3] = {nx, ny, nz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (nn[d] != 0) {
+        const double x = pi * nn[d] / N;
+        const double sc = sin(x) / x;
+        w *= sc * sc;
+      }
+    }
+    const float2 v = dk[(int64_t)iz * N * P + (int64_t)iy * P + ix];
+    const double p2 = ((double)v.x * v.x + (double)v.y * v.y) * norm / (w * w);
+    const double wt = (ix == 0 || ix == N / 2) ? 1.0 : 2.0;
+    atomicAdd(&sh[b], wt);
+    atomicAdd(&sh[nbins + b], wt * p2);
+    atomicAdd(&sh[2 * nbins + b], wt * nmag);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * nbins; i += NTP)
+    if (sh[i] != 0.0) atomicAdd(&acc[i], sh[i]);
+}
+
+inline unsigned blocks_for(int64_t n) { return (unsigned)((n + NTP - 1) / NTP); }
+
+}  // namespace
+
+cudaError_t part_deposit(const PartParams& pp, const float* sx, const float* sy, const float* sz,
+                         float* rho, int64_t P, cudaStream_t s) {
+  k_deposit<<<blocks_for(P), NTP, 0, s>>>(pp, sx, sy, sz, rho, P);
+  return cudaGetLastError();
+}
+
+cudaError_t part_drift_deposit(const PartParams& pp, float* sx, float* sy, float* sz, float* vx,
+                               float* vy, float* vz, const float* ax, const float* ay,
+                               const float* az, const float* dpx, const float* dpy,
+                               const float* dpz, float* rho, float dtk, float dtd, int64_t P,
+                               cudaStream_t s) {
+  k_drift_deposit<<<blocks_for(P), NTP, 0, s>>>(pp, sx, sy, sz, vx, vy, vz, ax, ay, az, dpx, dpy,
+                                                dpz, rho, dtk, dtd, P);
+  return cudaGetLastError();
+}
+
+cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float* sy,
+                             const float* sz, float* vx, float* vy, float* vz, float* ax,
+                             float* ay, float* az, const float* Ax, const float* Ay,
+                             const float* Az, const float* Fx, const float* Fy, const float* Fz,
+                             float dtk, int64_t P, cudaStream_t s) {
+  k_gather_kick<<<blocks_for(P), NTP, 0, s>>>(pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az,
+                                              Fx, Fy, Fz, dtk, P);
+  return cudaGetLastError();
+}
+
+cudaError_t part_snapshot(const PartParams& pp, const float* sx, const float* sy, const float* sz,
+                          const float* vx, const float* vy, const float* vz, const float* lx,
+                          const float* ly, const float* lz, float vscale, float* pos, float* vel,
+                          int64_t P, cudaStream_t s) {
+  k_snapshot<<<blocks_for(P), NTP, 0, s>>>(pp, sx, sy, sz, vx, vy, vz, lx, ly, lz, vscale, pos,
+                                           vel, P);
+  return cudaGetLastError();
+}
+
+cudaError_t pos_deposit(int Nm, float cellscale, const float* pos, int64_t n, float* rho,
+                        cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_pos_deposit<<<blocks_for(n), NTP, 0, s>>>(Nm, cellscale, pos, n, rho);
+  return cudaGetLastError();
+}
+
+cudaError_t pk_bin(int N, const float2* dk, int nbins, double* acc, double norm,
+                   cudaStream_t s) {
+  const size_t sm = 3 * (size_t)nbins * sizeof(double);
+  if (sm > 48 * 1024) return cudaErrorInvalidValue;
+  const int64_t nmodes = (int64_t)N * N * (N / 2 + 1);
+  unsigned grid = (unsigned)std::min<int64_t>((nmodes + NTP - 1) / NTP, 152 * 8);
+  k_pk_bin<<<grid, NTP, sm, s>>>(dk, N, half_pitch(N), nbins, acc, norm);
+  return cudaGetLastError();
+}
+
+}  // namespace cola

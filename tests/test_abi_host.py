@@ -1,0 +1,89 @@
+"""C ABI checks that need no GPU: the library loads, exports every function
+declared in include/cola.h, validates its inputs, and its host-side double
+precision tables (growth factors, time integrals) match the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1703_00879_gb300 as pkg
+from oracle import background as bg
+from oracle import growth as og
+from workloads import F5, MAIN_F5, NDGP1, SMALL_F5, Model
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(pkg.LIB_PATH):
+        from paper_1703_00879_gb300.build import build
+        build()
+    return pkg.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "cola.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cola_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(pkg.exported_symbols())
+
+
+def test_init_rejects_bad_config_without_touching_the_gpu(lib):
+    cfg = pkg.make_config(SMALL_F5)
+    cfg.Np = 48   # not a power of two
+    h = ctypes.c_void_p()
+    rc = lib.cola_init(ctypes.byref(cfg), pkg.ALLOC_FN(), pkg.FREE_FN(), None, None, ctypes.byref(h))
+    assert rc == pkg.COLA_EINVAL and not h.value
+    assert b"Np" in lib.cola_last_error(None)
+    cfg = pkg.make_config(SMALL_F5)
+    cfg.nsteps = 0
+    assert lib.cola_init(ctypes.byref(cfg), pkg.ALLOC_FN(), pkg.FREE_FN(), None, None,
+                         ctypes.byref(h)) == pkg.COLA_EINVAL
+
+
+def test_host_growth_rejects_bad_model(lib):
+    cfg = pkg.make_config(SMALL_F5)
+    bad = pkg.make_model(Model(kind=1, fR0=0.0))
+    out = np.zeros((SMALL_F5.nsteps + 1, 6, SMALL_F5.nk_table))
+    assert lib.cola_host_growth(ctypes.byref(cfg), ctypes.byref(bad), out.ctypes.data, None) == pkg.COLA_EINVAL
+
+
+@pytest.mark.parametrize("run", [SMALL_F5, SMALL_F5.with_model(NDGP1), SMALL_F5.with_model(Model()),
+                                 MAIN_F5.with_(nk_table=256)])
+def test_host_growth_tables_match_oracle(lib, run):
+    out, k = pkg.cola_host_growth(run)
+    a = bg.a_nodes(run.a_ini, run.a_final, run.nsteps)
+    t = og.growth_table(run.model, run.cosmo.Omega_m, a, run.Np, run.Lbox, run.nk_table)
+    assert np.allclose(k, t.k, rtol=1e-13)
+    for q, ref in enumerate([t.D1, t.dD1, t.ddD1, t.D2, t.dD2, t.ddD2]):
+        assert np.allclose(out[:, q, :], ref, rtol=2e-9, atol=1e-12 * np.abs(ref).max()), q
+
+
+def test_host_timesteps_match_oracle(lib):
+    run = MAIN_F5
+    out = pkg.cola_host_timesteps(run)
+    a = bg.a_nodes(run.a_ini, run.a_final, run.nsteps)
+    for n in range(run.nsteps):
+        am = 0.5 * (a[n] + a[n + 1])
+        assert out[n, 0] == pytest.approx(a[n + 1], rel=1e-15)
+        assert out[n, 1] == pytest.approx(bg.dtau(a[n], am, 0.3), rel=1e-12)
+        assert out[n, 2] == pytest.approx(bg.dtau(a[n], a[n + 1], 0.3), rel=1e-12)
+        assert out[n, 3] == pytest.approx(bg.dtau(am, a[n + 1], 0.3), rel=1e-12)
+
+
+def test_binding_fails_loudly_without_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    with pytest.raises(RuntimeError):
+        pkg.Simulation(SMALL_F5)
