@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the COLA PM step (scale-dependent growth, screened MG) on GB300.
+
+One "step" is one full COLA PM step of the library (LPT reweight + inverse FFTs,
+drift + CIC deposit, forward FFT, screened Poisson solve, force inverse FFTs,
+CIC gather + kick).  The default workload is nDGP (r_c H0 = 1, Vainshtein
+screening with R = 1 Mpc/h): 512^3 particles, 1024^3 mesh, L = 1024 Mpc/h,
+synthetic Gaussian ICs from a seed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank advances its
+own independent simulation (replicas, weak scaling); there is no collective
+on the data path.  `--impl reference` times the FP64 CPU oracle on a bounded
+sample of the workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "particle-steps/s at 512³ (HBM roofline %); ensemble sims/hour and p50/p99 latency"
+UNIT = "particle-steps/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {"big": W.BIG_NDGP, "main": W.MAIN_F5, "small": W.SMALL_F5}
+
+
+# ---------------------------------------------------------------- distributed helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(x: float, dist=None) -> float:
+    """Maximum of x over ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist=None):
+    if dist is not None:
+        dist.barrier()
+
+
+def whole_job_throughput(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """value = units all ranks processed / max-over-ranks time."""
+    return units_per_rank * world / max_seconds
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock, power and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_selector(local_rank: int) -> str:
+    try:
+        import torch
+        u = getattr(torch.cuda.get_device_properties(local_rank), "uuid", None)
+        if u is not None:
+            s = str(u)
+            return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        return vis.split(",")[local_rank]
+    return str(local_rank)
+
+
+# ---------------------------------------------------------------- roofline helpers
+def hbm_peak():
+    try:
+        d = json.load(open(PEAKS_FILE))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_1703_00879_gb300", "csrc")
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(stage: str, workload: str):
+    """DRAM bytes per launch of `stage` from a committed ncu capture, if the kernels are unchanged."""
+    try:
+        d = json.load(open(TRAFFIC_FILE))
+    except Exception:
+        return None
+    e = d.get(workload, {}).get(stage)
+    if not e or e.get("source_sha") != source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def workload_config(run, world: int):
+    m = run.model
+    grav = {0: "LCDM", 1: f"f(R) Hu-Sawicky n=1 |fR0|={m.fR0:g}", 2: f"nDGP rcH0={m.rcH0:g}"}[m.kind]
+    if m.screening:
+        grav += " + " + ("chameleon" if m.kind == 1 else "Vainshtein R=%g Mpc/h Gaussian" % m.R_smooth) + " screening"
+    return {"workload": run.name, "particles": f"{run.Np}^3", "mesh": f"{run.Nmesh}^3",
+            "box_mpc_h": run.Lbox, "gravity": grav, "growth": "scale-dependent per-k tables (1024 log-k bins)",
+            "z_ini": run.z_ini, "steps_in_run": run.nsteps, "seed": run.seed,
+            "l2": f"inputs larger than L2: each mesh array {run.Nmesh**3 * 4 / 1e9:.1f} GB",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
+# ---------------------------------------------------------------- our implementation
+def bench_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    import paper_1703_00879_gb300 as pkg
+
+    base = WORKLOADS[args.workload]
+    run = base.with_(nsteps=max(base.nsteps, args.warmup + args.steps), seed=base.seed + rank)
+    stream = torch.cuda.current_stream()
+    sim = pkg.Simulation(run)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    sim.profile(True)
+    clocks = ClockSampler(gpu_selector(local))
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(dist)
+    ms = e0.elapsed_time(e1)
+    stages = sim.profile_read()
+    sim.profile(False)
+    sim.close()
+    del sim
+    max_ms = reduce_max(ms, dist)
+    P = run.Np ** 3
+    value = whole_job_throughput(P * args.steps, world, max_ms / 1e3)
+
+    # dominant kernel (largest share of the timed region), its algorithmic bytes / average launch time
+    name, (st_ms, st_n, st_bytes) = max(((k, v) for k, v in stages.items() if v[1] > 0), key=lambda kv: kv[1][0])
+    avg_s = st_ms / st_n / 1e3
+    achieved = st_bytes / avg_s / 1e9
+    peak, peak_src = hbm_peak()
+    launches = sum(v[1] for k, v in stages.items() if k != "rho_zero")   # memset is not a kernel
+    stage_report = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1], "share": v[0] / max(ms, 1e-9),
+                        "GBps": (v[2] / (v[0] / v[1] / 1e3) / 1e9) if v[1] else None}
+                    for k, v in stages.items() if v[1] > 0 or v[0] > 0}
+    # whole-step ledger: algorithmic bytes of every stage per step / step time
+    step_bytes = sum(v[2] * v[1] for v in stages.values()) / args.steps
+    torch.cuda.empty_cache()
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = bench_e2e(args, run, pkg, dist, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(run, args)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(run, world),
+            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                         "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                         else "fallback", "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": ncu_traffic(name, args.workload)},
+            "step_ledger": {"algorithmic_GB_per_step": step_bytes / 1e9,
+                            "achieved_GBps": step_bytes / (max_ms / args.steps / 1e3) / 1e9,
+                            "frac_of_peak": step_bytes / (max_ms / args.steps / 1e3) / 1e9 / peak},
+            "stages": stage_report,
+            "clocks": clk,
+            "gpu_launches": int(launches),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def bench_e2e(args, run, pkg, dist, world):
+    """Whole job through the public C ABI: init from a host config, ICs, K steps, host snapshot and P(k)."""
+    import torch
+    e2e_run = run.with_(nsteps=max(run.nsteps, args.steps))
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = pkg.Simulation(e2e_run)
+    sim.step(args.steps)
+    pos, vel = sim.snapshot()
+    k, pk, nm = sim.pk()
+    t1 = time.perf_counter()
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    dt = reduce_max(t1 - t0, dist)
+    P = run.Np ** 3
+    h2d = (2 * (e2e_run.nsteps + 1) * e2e_run.nk_table * 16 + (run.Np + run.Nmesh) * 8) / args.steps
+    d2h = (pos.nbytes + vel.nbytes + k.nbytes + pk.nbytes + nm.nbytes) / args.steps
+    return {"value": whole_job_throughput(P * args.steps, world, dt), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "what": "cola_init + cola_set_model + cola_ic + cola_step(K) + cola_snapshot(host) + cola_pk(host)"}
+
+
+# ---------------------------------------------------------------- oracle (CPU) timing
+def oracle_sample(run):
+    """Bounded sample of the workload for the CPU oracle: a sub-box with the same cell
+    size, particle spacing, model and time steps (at most 128^3 particles)."""
+    if run.Np <= 128:
+        return run
+    f = run.Np // 128
+    return run.with_(Np=128, Nmesh=run.Nmesh // f, Lbox=run.Lbox / f, name=run.name + "_sample128p")
+
+
+def time_oracle(run, warmup: int, steps: int):
+    from oracle.cola import Simulation as OracleSim
+    sim = OracleSim(run.with_(nsteps=max(run.nsteps, warmup + steps)))
+    for _ in range(warmup):
+        sim.step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.step()
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(run, args):
+    sample = oracle_sample(run)
+    dt = time_oracle(sample, 1, 2)
+    return {"value": sample.Np ** 3 * 2 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"2 oracle PM steps (after 1 warm-up) of {sample.Np}^3 particles / {sample.Nmesh}^3 mesh / "
+                      f"L={sample.Lbox:g} Mpc/h, same model and cell size as the workload; FP64 NumPy/SciPy, "
+                      f"scipy.fft with workers=all cores, CIC via numpy.bincount",
+            "seconds_per_step": dt / 2}
+
+
+def bench_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    base = WORKLOADS[args.workload]
+    sample = oracle_sample(base)
+    dt = time_oracle(sample, args.warmup, args.steps)
+    value = sample.Np ** 3 * args.steps / dt
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": workload_config(base, world),
+           "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value, "unit": UNIT,
+                            "sample": f"each step one oracle PM step of {sample.Np}^3 particles / "
+                                      f"{sample.Nmesh}^3 mesh / L={sample.Lbox:g} Mpc/h (same cell size, "
+                                      f"particle spacing and model as the workload), FP64 NumPy/SciPy"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="big")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -72,7 +72,7 @@ typedef void (*cola_free_fn)(void* ptr, void* stream, void* user);
 typedef struct {
   double Omega_m, Omega_b, h, n_s, sigma8;
   double Lbox;             /* box side [Mpc/h] */
-  int32_t Np;              /* particles per side: power of two, 32..1024 */
+  int32_t Np;              /* particles per side: power of two, 32..512 */
   int32_t Nmesh;           /* PM mesh cells per side: power of two, 32..1024 */
   double z_ini, z_final;
   int32_t nsteps;          /* >= 1 */
@@ -204,6 +204,25 @@ int cola_cic_deposit(cola_ctx* ctx, const float* pos, int64_t n, float* rho, int
  * [3][Nmesh^3] floats -grad Phi_tot. */
 int cola_force_from_density(cola_ctx* ctx, const float* rho, double a, float* force,
                             int32_t where);
+
+/* ---------------------------------------------------------------------
+ * Per-stage device timing: CUDA events recorded on the context's stream
+ * around each launch group of cola_step (and of cola_ic's force evaluation).
+ * --------------------------------------------------------------------- */
+
+/* on = 1 clears the accumulators and starts recording; on = 0 stops. */
+int cola_profile_enable(cola_ctx* ctx, int32_t on);
+
+/* Number of stages and the name of stage i (static strings). */
+int32_t cola_profile_nstages(void);
+const char* cola_profile_stage_name(int32_t i);
+
+/* Synchronises the stream and returns, per stage, the accumulated device
+ * milliseconds, the number of kernel launches, and the algorithmic bytes one
+ * launch moves (each array read once and written once; CIC deposit counts
+ * the mesh read and written once).  Arrays of cola_profile_nstages() entries;
+ * any may be NULL. */
+int cola_profile_read(cola_ctx* ctx, double* ms, int64_t* launches, double* bytes_per_launch);
 
 /* ---------------------------------------------------------------------
  * Host-only helpers (no GPU needed): the double-precision quantities the

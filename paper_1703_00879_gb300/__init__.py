@@ -68,6 +68,10 @@ _SIGS = {
     "cola_fft": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
     "cola_cic_deposit": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32]),
     "cola_force_from_density": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.c_int32]),
+    "cola_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cola_profile_nstages": (ctypes.c_int32, []),
+    "cola_profile_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
+    "cola_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
     "cola_host_growth": (ctypes.c_int, [ctypes.POINTER(cola_config), ctypes.POINTER(cola_model), _P, _P]),
     "cola_host_timesteps": (ctypes.c_int, [ctypes.POINTER(cola_config), _P]),
 }
@@ -243,6 +247,19 @@ class Simulation:
         out = np.empty(shape, dt)
         _check(lib().cola_export(self.ctx, which, out.ctypes.data, COLA_HOST), self.ctx)
         return out
+
+    def profile(self, on: bool = True):
+        _check(lib().cola_profile_enable(self.ctx, int(bool(on))), self.ctx)
+
+    def profile_read(self):
+        """{stage: (ms, launches, algorithmic bytes per launch)} accumulated since profile(True)."""
+        n = lib().cola_profile_nstages()
+        ms = np.zeros(n)
+        nl = np.zeros(n, np.int64)
+        by = np.zeros(n)
+        _check(lib().cola_profile_read(self.ctx, ms.ctypes.data, nl.ctypes.data, by.ctypes.data), self.ctx)
+        return {lib().cola_profile_stage_name(i).decode(): (float(ms[i]), int(nl[i]), float(by[i]))
+                for i in range(n)}
 
     def import_state(self, disp, dv, acc, steps_done: int):
         arrs = [np.ascontiguousarray(x, dtype=np.float32) for x in (disp, dv, acc)]

@@ -54,11 +54,64 @@ struct cola_ctx {
   float* scratch = nullptr;
   EHParams eh{};
   double Dratio = 1.0;
+  // per-stage event timing
+  bool prof = false;
+  struct Stage {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    double ms = 0;
+    int64_t launches = 0;
+    double bytes = 0;
+  };
+  std::vector<Stage> stages;
+  std::vector<cudaEvent_t> event_pool;
 };
 
 namespace {
 
 constexpr int kMaxBins = 2000;
+
+enum Stage {
+  ST_LPT_Z, ST_LPT_Y, ST_LPT_X, ST_RHO_ZERO, ST_DRIFT_DEPOSIT, ST_MESH_XR2C, ST_MESH_Y,
+  ST_Z_SCREEN_FIELD, ST_X_SCREEN_SOURCE, ST_Z_FORCE, ST_MESH_YINV, ST_MESH_XC2R, ST_GATHER_KICK,
+  ST_COUNT
+};
+const char* const kStageNames[ST_COUNT] = {
+    "lpt_z_reweight", "lpt_y_inverse", "lpt_x_c2r", "rho_zero", "drift_deposit", "mesh_x_r2c",
+    "mesh_y_forward", "z_screen_field", "x_screen_source", "z_force", "mesh_y_inverse",
+    "mesh_x_c2r", "gather_kick"};
+
+cudaEvent_t take_event(cola_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Records the start of a launch group; returns the event (null when not profiling).
+cudaEvent_t prof_begin(cola_ctx* c) {
+  if (!c->prof) return nullptr;
+  cudaEvent_t e = take_event(c);
+  if (e) cudaEventRecord(e, c->st);
+  return e;
+}
+
+void prof_end(cola_ctx* c, int stage, cudaEvent_t start, int launches, double bytes) {
+  if (!c->prof || !start) return;
+  cudaEvent_t e = take_event(c);
+  if (!e) return;
+  cudaEventRecord(e, c->st);
+  auto& s = c->stages[stage];
+  s.pending.emplace_back(start, e);
+  s.launches += launches;
+  s.bytes = bytes;
+}
 
 int fail(cola_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -129,7 +182,7 @@ struct Temp {
 
 int validate_cfg(const cola_config* cfg, cola_ctx* c) {
   if (!cfg) return fail(c, COLA_EINVAL, "cfg is NULL");
-  if (!pow2_in(cfg->Np, 32, 1024)) return fail(c, COLA_EINVAL, "Np must be a power of two in 32..1024");
+  if (!pow2_in(cfg->Np, 32, 512)) return fail(c, COLA_EINVAL, "Np must be a power of two in 32..512");
   if (!pow2_in(cfg->Nmesh, 32, 1024)) return fail(c, COLA_EINVAL, "Nmesh must be a power of two in 32..1024");
   if (cfg->nsteps < 1) return fail(c, COLA_EINVAL, "nsteps must be >= 1");
   if (!(cfg->Lbox > 0)) return fail(c, COLA_EINVAL, "Lbox must be > 0");
@@ -265,17 +318,25 @@ int run_lpt(cola_ctx* ctx, const float4* row) {
   const int N = ctx->Np;
   const float kf = lp.kf;
   auto st = ctx->st;
+  const double H = (double)N * N * (N / 2 + 1) * 8.0, R = (double)N * N * N * 4.0;
+  const double seedH = H * (lp.seed_prec ? 0.5 : 1.0);
+  cudaEvent_t e = prof_begin(ctx);
   CK(lpt_z(N, p1, p2, ctx->lc[0], ctx->lc[1], ctx->lc[2], ctx->lc[3], lp, ctx->tw_np, st));
+  prof_end(ctx, ST_LPT_Z, e, 1, 2 * seedH + 4 * H);
+  e = prof_begin(ctx);
   CK(fft_yinv2(N, ctx->lc[0], ctx->lc[0], ctx->lc[4], kf, ctx->tw_np, st));
   CK(fft_col(N, ctx->lc[1], 1, true, ctx->tw_np, st));
   CK(fft_yinv2(N, ctx->lc[2], ctx->lc[2], ctx->lc[5], kf, ctx->tw_np, st));
   CK(fft_col(N, ctx->lc[3], 1, true, ctx->tw_np, st));
-  CK(fft_xc2r(N, ctx->lc[0], ctx->lr[0], kf, ctx->tw_np, st));
-  CK(fft_xc2r(N, ctx->lc[4], ctx->lr[1], 0.f, ctx->tw_np, st));
-  CK(fft_xc2r(N, ctx->lc[1], ctx->lr[2], 0.f, ctx->tw_np, st));
-  CK(fft_xc2r(N, ctx->lc[2], ctx->lr[3], kf, ctx->tw_np, st));
-  CK(fft_xc2r(N, ctx->lc[5], ctx->lr[4], 0.f, ctx->tw_np, st));
-  CK(fft_xc2r(N, ctx->lc[3], ctx->lr[5], 0.f, ctx->tw_np, st));
+  prof_end(ctx, ST_LPT_Y, e, 4, 2.5 * H);
+  e = prof_begin(ctx);
+  {
+    const float2* in6[6] = {ctx->lc[0], ctx->lc[4], ctx->lc[1], ctx->lc[2], ctx->lc[5], ctx->lc[3]};
+    float* out6[6] = {ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->lr[3], ctx->lr[4], ctx->lr[5]};
+    const float kfs6[6] = {kf, 0.f, 0.f, kf, 0.f, 0.f};
+    CK(fft_xc2r_multi(N, 6, in6, out6, kfs6, ctx->tw_np, st));
+  }
+  prof_end(ctx, ST_LPT_X, e, 1, 6 * (H + R));
   ctx->have_lpt = true;
   return COLA_OK;
 }
@@ -286,22 +347,46 @@ int run_force(cola_ctx* ctx, double a) {
   const int N = ctx->Nm;
   auto st = ctx->st;
   const float2* tw = ctx->tw_nm;
+  const double H = (double)N * N * (N / 2 + 1) * 8.0, R = (double)N * N * N * 4.0;
+  cudaEvent_t e = prof_begin(ctx);
   CK(fft_xr2c(N, ctx->rho, ctx->Cd, fp.inv_rhobar, -1.f, tw, st));
+  prof_end(ctx, ST_MESH_XR2C, e, 1, R + H);
+  e = prof_begin(ctx);
   CK(fft_col(N, ctx->Cd, 1, false, tw, st));
+  prof_end(ctx, ST_MESH_Y, e, 1, 2 * H);
   if (fp.screened) {
+    e = prof_begin(ctx);
     CK(mesh_z_screen_field(N, ctx->Cd, ctx->Ck, ctx->Cw, fp, tw, st));
+    prof_end(ctx, ST_Z_SCREEN_FIELD, e, 1, 3 * H);
+    e = prof_begin(ctx);
     CK(fft_col(N, ctx->Cw, 1, true, tw, st));
+    prof_end(ctx, ST_MESH_YINV, e, 1, 2 * H);
+    e = prof_begin(ctx);
     CK(mesh_x_screen_source(N, ctx->Cw, ctx->rho, ctx->Cd, fp, tw, st));
+    prof_end(ctx, ST_X_SCREEN_SOURCE, e, 1, 2 * H + R);
+    e = prof_begin(ctx);
     CK(fft_col(N, ctx->Cd, 1, false, tw, st));
+    prof_end(ctx, ST_MESH_Y, e, 1, 2 * H);
+    e = prof_begin(ctx);
     CK(mesh_z_force(N, ctx->Cd, ctx->Ck, ctx->Cphi, ctx->Cphz, nullptr, fp, tw, st));
+    prof_end(ctx, ST_Z_FORCE, e, 1, 4 * H);
   } else {
+    e = prof_begin(ctx);
     CK(mesh_z_force(N, ctx->Cd, nullptr, ctx->Cphi, ctx->Cphz, nullptr, fp, tw, st));
+    prof_end(ctx, ST_Z_FORCE, e, 1, 3 * H);
   }
+  e = prof_begin(ctx);
   CK(fft_yinv2(N, ctx->Cphi, ctx->Cphi, ctx->Cw, -fp.kf, tw, st));
   CK(fft_col(N, ctx->Cphz, 1, true, tw, st));
-  CK(fft_xc2r(N, ctx->Cphi, ctx->F[0], -fp.kf, tw, st));
-  CK(fft_xc2r(N, ctx->Cw, ctx->F[1], 0.f, tw, st));
-  CK(fft_xc2r(N, ctx->Cphz, ctx->F[2], 0.f, tw, st));
+  prof_end(ctx, ST_MESH_YINV, e, 2, 2.5 * H);
+  e = prof_begin(ctx);
+  {
+    const float2* in3[3] = {ctx->Cphi, ctx->Cw, ctx->Cphz};
+    float* out3[3] = {ctx->F[0], ctx->F[1], ctx->F[2]};
+    const float kfs3[3] = {-fp.kf, 0.f, 0.f};
+    CK(fft_xc2r_multi(N, 3, in3, out3, kfs3, tw, st));
+  }
+  prof_end(ctx, ST_MESH_XC2R, e, 1, 3 * (H + R));
   ctx->have_force = true;
   return COLA_OK;
 }
@@ -555,17 +640,24 @@ int cola_step(cola_ctx* ctx, int32_t nsteps) {
   const PartParams pp = part_params(ctx);
   for (int it = 0; it < nsteps; ++it) {
     const int n = ctx->step;
+    const double Pb = (double)ctx->P, Mb = (double)ctx->M;
     CHECK_RC(run_lpt(ctx, ctx->tab + (size_t)(n + 1) * ctx->nk));
+    cudaEvent_t e = prof_begin(ctx);
     CK(cudaMemsetAsync(ctx->rho, 0, ctx->M * sizeof(float), ctx->st));
+    prof_end(ctx, ST_RHO_ZERO, e, 1, 4.0 * Mb);
+    e = prof_begin(ctx);
     CK(part_drift_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                           ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[0], ctx->lr[1],
                           ctx->lr[2], ctx->rho, (float)ctx->dtk1[n], (float)ctx->dtd[n], ctx->P,
                           ctx->st));
+    prof_end(ctx, ST_DRIFT_DEPOSIT, e, 1, 72.0 * Pb + 8.0 * Mb);
     CHECK_RC(run_force(ctx, ctx->a[n + 1]));
+    e = prof_begin(ctx);
     CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                         ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[3], ctx->lr[4],
                         ctx->lr[5], ctx->F[0], ctx->F[1], ctx->F[2], (float)ctx->dtk2[n], ctx->P,
                         ctx->st));
+    prof_end(ctx, ST_GATHER_KICK, e, 1, 60.0 * Pb + 12.0 * Mb);
     ctx->step = n + 1;
   }
   return COLA_OK;
@@ -632,6 +724,12 @@ const char* cola_last_error(const cola_ctx* ctx) { return ctx ? ctx->err.c_str()
 void cola_free(cola_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->st);
+  for (auto& stg : ctx->stages)
+    for (auto& pr : stg.pending) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   for (void* p : ctx->allocs) dev_free(ctx, p);
   if (!ctx->alloc) cudaStreamSynchronize(ctx->st);
   cudaGetLastError();
@@ -758,6 +856,48 @@ int cola_force_from_density(cola_ctx* ctx, const float* rho, double a, float* fo
   CHECK_RC(run_force(ctx, a));
   char* d = reinterpret_cast<char*>(force);
   for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * mb, ctx->F[c], mb, where));
+  return COLA_OK;
+}
+
+int cola_profile_enable(cola_ctx* ctx, int32_t on) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  CK(cudaStreamSynchronize(ctx->st));
+  if (ctx->stages.empty()) ctx->stages.resize(ST_COUNT);
+  for (auto& stg : ctx->stages) {
+    for (auto& pr : stg.pending) {
+      ctx->event_pool.push_back(pr.first);
+      ctx->event_pool.push_back(pr.second);
+    }
+    stg = cola_ctx::Stage();
+  }
+  ctx->prof = on != 0;
+  return COLA_OK;
+}
+
+int32_t cola_profile_nstages(void) { return ST_COUNT; }
+
+const char* cola_profile_stage_name(int32_t i) {
+  return (i >= 0 && i < ST_COUNT) ? kStageNames[i] : "";
+}
+
+int cola_profile_read(cola_ctx* ctx, double* ms, int64_t* launches, double* bytes_per_launch) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  CK(cudaStreamSynchronize(ctx->st));
+  if (ctx->stages.empty()) ctx->stages.resize(ST_COUNT);
+  for (int i = 0; i < ST_COUNT; ++i) {
+    auto& stg = ctx->stages[i];
+    for (auto& pr : stg.pending) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, pr.first, pr.second));
+      stg.ms += t;
+      ctx->event_pool.push_back(pr.first);
+      ctx->event_pool.push_back(pr.second);
+    }
+    stg.pending.clear();
+    if (ms) ms[i] = stg.ms;
+    if (launches) launches[i] = stg.launches;
+    if (bytes_per_launch) bytes_per_launch[i] = stg.bytes;
+  }
   return COLA_OK;
 }
 

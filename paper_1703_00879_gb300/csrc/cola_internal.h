@@ -49,6 +49,9 @@ cudaError_t fft_xr2c(int N, const float* in, float2* out, float scale, float off
                      const float2* tw, cudaStream_t s);
 cudaError_t fft_xc2r(int N, const float2* in, float* out, float kfs, const float2* tw,
                      cudaStream_t s);
+// up to six independent c2r row passes in one launch
+cudaError_t fft_xc2r_multi(int N, int njobs, const float2* const* in, float* const* out,
+                           const float* kfs, const float2* tw, cudaStream_t s);
 // axis 1 = y, 2 = z; in place
 cudaError_t fft_col(int N, float2* data, int axis, bool inv, const float2* tw, cudaStream_t s);
 // y inverse pass producing the plain transform (out_plain may alias in) and the

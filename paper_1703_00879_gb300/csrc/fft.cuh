@@ -1,13 +1,11 @@
-// Shared-memory Stockham FFT building blocks for sm_103a.
+// Shared-memory FFT building blocks for sm_103a.
 //
 // A tile of TW independent columns of length L (power of two) lives in shared
-// memory as buf[n * PITCH + c] (float2, c = column, n = element).  Each stage is
-// one radix-R Stockham autosort pass (Govindaraju et al., SC'08 formulation):
-// every butterfly j loads elements j + r L/R, applies twiddles w^(r (j mod Ns)),
-// does an in-register radix-R DFT and stores at (j/Ns) Ns R + (j mod Ns) + r Ns.
-// The output is in natural order.  Consecutive threads handle consecutive
-// columns, so every shared-memory access of a half warp is bank-conflict free
-// for PITCH = TW (column tiles) or TW + 1 (row tiles).
+// memory as buf[n * PITCH + c] (float2, c = column, n = element).  A transform
+// is two in-register DFT passes of radix R1, R2 <= 32 (L = R1 R2, the
+// "four-step" factorisation) with one twiddle multiplication between them, so
+// each element makes two round trips through shared memory.  Consecutive
+// threads handle consecutive columns.
 //
 // Twiddles come from a table tw[m] = exp(-2 pi i m / T) of the tile's transform
 // table length T (host-computed in double precision, rounded to float); a
@@ -73,86 +71,162 @@ __device__ __forceinline__ void dft8(float2* v) {
   v[7] = csub(e3, o3);
 }
 
-template <int R, bool INV>
-__device__ __forceinline__ void dftR(float2* v) {
-  if constexpr (R == 2) {
-    dft2<INV>(v[0], v[1]);
-  } else if constexpr (R == 4) {
-    dft4<INV>(v[0], v[1], v[2], v[3]);
+// cos(2 pi m / 32) for m = 0..8 (standard values; sin(2 pi m/32) = cos32(8 - m)).
+__host__ __device__ constexpr float cos32(int m) {
+  return m == 0 ? 1.0f
+       : m == 1 ? 0.98078528040323044913f
+       : m == 2 ? 0.92387953251128675613f
+       : m == 3 ? 0.83146961230254523708f
+       : m == 4 ? 0.70710678118654752440f
+       : m == 5 ? 0.55557023301960222474f
+       : m == 6 ? 0.38268343236508977173f
+       : m == 7 ? 0.19509032201612826785f
+       : 0.0f;
+}
+
+// a * exp(-/+ 2 pi i m / 32), m in [0, 16) a compile-time constant after unrolling.
+template <bool INV>
+__device__ __forceinline__ float2 w32mul(float2 a, int m) {
+  if (m == 0) return a;
+  if (m == 8) return rot_q<INV>(a);
+  const float c = m <= 8 ? cos32(m) : -cos32(16 - m);
+  const float s = m <= 8 ? cos32(8 - m) : cos32(m - 8);
+  return INV ? make_float2(a.x * c - a.y * s, a.y * c + a.x * s)
+             : make_float2(a.x * c + a.y * s, a.y * c - a.x * s);
+}
+
+// In-register DFT of R = 2..32 points on the strided view v[0], v[S], ...,
+// v[(R-1)S], in place.  R <= 8: natural order.  R = 16, 32: radix-2
+// decimation-in-frequency butterflies, so output k sits at position
+// pos_of<R>(k) (resolved at compile time by the caller).
+template <int R>
+__host__ __device__ constexpr int pos_of(int k) {
+  if constexpr (R <= 8) {
+    return k;
   } else {
-    static_assert(R == 8, "radix");
-    dft8<INV>(v);
+    return (k % 2 == 0) ? pos_of<R / 2>(k / 2) : R / 2 + pos_of<R / 2>((k - 1) / 2);
+  }
+}
+
+template <bool INV, int S>
+__device__ __forceinline__ void dft8s(float2* v) {
+  float2 t[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t[i] = v[i * S];
+  dft8<INV>(t);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i * S] = t[i];
+}
+
+template <int R, bool INV, int S = 1>
+__device__ __forceinline__ void dftR(float2* v) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    dft2<INV>(v[0], v[S]);
+  } else if constexpr (R == 4) {
+    dft4<INV>(v[0], v[S], v[2 * S], v[3 * S]);
+  } else if constexpr (R == 8) {
+    dft8s<INV, S>(v);
+  } else {
+    static_assert(R == 16 || R == 32, "radix");
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      const float2 a = v[k * S], b = v[(k + R / 2) * S];
+      v[k * S] = cadd(a, b);
+      v[(k + R / 2) * S] = w32mul<INV>(csub(a, b), k * (32 / R));
+    }
+    dftR<R / 2, INV, S>(v);
+    dftR<R / 2, INV, S>(v + (R / 2) * S);
   }
 }
 
 constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 
-// Radix of stage s for a length-L transform: radix 8 first, one radix 2 or 4 last.
-template <int L, int S>
-struct StageRadix {
+// L = R1 R2 with R1 <= R2 <= 32.
+template <int L>
+struct Split {
   static constexpr int p = ilog2(L);
-  static constexpr int n8 = p / 3;
-  static constexpr int rem = p % 3;
-  static constexpr int value = (S < n8) ? 8 : (rem == 1 ? 2 : 4);
-  static constexpr int nstages = n8 + (rem ? 1 : 0);
+  static constexpr int R1 = 1 << (p / 2);
+  static constexpr int R2 = L / R1;
+  static_assert(R2 <= 32 && R1 * R2 == L, "transform length");
 };
 
-// One Stockham stage on a TW x L shared-memory tile.
-template <int L, int R, int NS, int TW, int PITCH, int NT, bool INV, int TWS>
-__device__ __forceinline__ void fft_stage(float2* __restrict__ buf, const float2* __restrict__ tw) {
-  constexpr int NB = L / R;           // butterflies per column
-  constexpr int TOT = NB * TW;
-  constexpr int PER = (TOT + NT - 1) / NT;
+// Length-L transform of the TW columns of a shared-memory tile (four-step):
+// step 1: for each n2 < R2, DFT_R1 over x[R2 n1 + n2], times w_L^(n2 k1);
+// step 2: for each k1 < R1, DFT_R2 over n2 gives X[k1 + R1 k2].
+// The intermediate Y[n2][k1] is stored at row R2 k1 + ((n2 + k1) mod R2) so that
+// the step-2 reads of adjacent k1 fall in different banks.  tw has L * TWS
+// entries; the caller synchronises before the call; returns after a barrier.
+template <int L, int TW, int PITCH, int NT, bool INV, int TWS = 1>
+__device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2* __restrict__ tw) {
+  constexpr int R1 = Split<L>::R1, R2 = Split<L>::R2;
+  constexpr int U1 = TW * R2, P1 = (U1 + NT - 1) / NT;
+  constexpr int U2 = TW * R1, P2 = (U2 + NT - 1) / NT;
   const int tid = threadIdx.x;
-  float2 v[PER][R];
+  {
+    float2 v[P1][R1];
 #pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int b = tid + i * NT;
-    if ((TOT % NT) == 0 || b < TOT) {
-      const int c = b % TW, j = b / TW;
-      const int k = j & (NS - 1);
+    for (int i = 0; i < P1; ++i) {
+      const int u = tid + i * NT;
+      if ((U1 % NT) == 0 || u < U1) {
+        const int c = u % TW, n2 = u / TW;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = buf[(j + r * NB) * PITCH + c];
-      if (NS > 1) {
+        for (int n1 = 0; n1 < R1; ++n1) v[i][n1] = buf[(R2 * n1 + n2) * PITCH + c];
+        dftR<R1, INV>(v[i]);
+        if (n2 > 0) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = tw[(r * k * (L / (NS * R))) * TWS];
-          if (INV) w.y = -w.y;
-          v[i][r] = cmul(v[i][r], w);
+          for (int k1 = 1; k1 < R1; ++k1) {
+            float2 w = tw[n2 * k1 * TWS];
+            if (INV) w.y = -w.y;
+            v[i][pos_of<R1>(k1)] = cmul(v[i][pos_of<R1>(k1)], w);
+          }
         }
       }
-      dftR<R, INV>(v[i]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < P1; ++i) {
+      const int u = tid + i * NT;
+      if ((U1 % NT) == 0 || u < U1) {
+        const int c = u % TW, n2 = u / TW;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1)
+          buf[(R2 * k1 + ((n2 + k1) & (R2 - 1))) * PITCH + c] = v[i][pos_of<R1>(k1)];
+      }
     }
   }
   __syncthreads();
+  {
+    float2 y[P2][R2];
 #pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int b = tid + i * NT;
-    if ((TOT % NT) == 0 || b < TOT) {
-      const int c = b % TW, j = b / TW;
-      const int k = j & (NS - 1);
-      const int idxD = (j / NS) * NS * R + k;
+    for (int i = 0; i < P2; ++i) {
+      const int u = tid + i * NT;
+      if ((U2 % NT) == 0 || u < U2) {
+        const int c = u % TW, k1 = u / TW;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[(idxD + r * NS) * PITCH + c] = v[i][r];
+        for (int n2 = 0; n2 < R2; ++n2) y[i][n2] = buf[(R2 * k1 + ((n2 + k1) & (R2 - 1))) * PITCH + c];
+        dftR<R2, INV>(y[i]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < P2; ++i) {
+      const int u = tid + i * NT;
+      if ((U2 % NT) == 0 || u < U2) {
+        const int c = u % TW, k1 = u / TW;
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) buf[(k1 + R1 * k2) * PITCH + c] = y[i][pos_of<R2>(k2)];
+      }
     }
   }
   __syncthreads();
 }
 
-template <int L, int S, int NS, int TW, int PITCH, int NT, bool INV, int TWS>
-__device__ __forceinline__ void fft_stages(float2* buf, const float2* tw) {
-  if constexpr (S < StageRadix<L, 0>::nstages) {
-    constexpr int R = StageRadix<L, S>::value;
-    fft_stage<L, R, NS, TW, PITCH, NT, INV, TWS>(buf, tw);
-    fft_stages<L, S + 1, NS * R, TW, PITCH, NT, INV, TWS>(buf, tw);
-  }
-}
-
-// Full length-L transform of all TW columns (caller synchronises before the call).
-// tw is a table of length L * TWS.
+// Out-of-line copy for kernels that run several transforms per tile: each
+// call gets its own register allocation instead of one inlined body per call.
 template <int L, int TW, int PITCH, int NT, bool INV, int TWS = 1>
-__device__ __forceinline__ void fft_tile(float2* buf, const float2* tw) {
-  fft_stages<L, 0, 1, TW, PITCH, NT, INV, TWS>(buf, tw);
+__device__ __noinline__ void fft_tile_call(float2* buf, const float2* tw) {
+  fft_tile<L, TW, PITCH, NT, INV, TWS>(buf, tw);
 }
 
 // Signed frequency index of position n in a length-N transform.

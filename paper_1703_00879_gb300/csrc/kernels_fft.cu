@@ -3,13 +3,21 @@
 //
 // A 3-D real transform is three passes over HBM: rows along x (contiguous,
 // real <-> half spectrum by the two-for-one packing z = x[2j] + i x[2j+1]),
-// then columns along y and along z (tiles of TW adjacent kx columns, so every
-// row segment of a tile is one or more whole 32-byte sectors).  Fusions:
+// then columns along y and along z (tiles of TW >= 4 adjacent kx columns, so
+// every row segment of a tile is at least one whole 32-byte sector).
+//
+// Every pass is a persistent kernel (grid = SMs x resident CTAs) that walks
+// its tiles in a software pipeline: column tiles are staged with cp.async
+// into a second shared-memory buffer while the current tile is transformed;
+// row tiles prefetch the next tile into registers before the transform.
+//
+// Fusions:
 //   * the z pass of a forward transform also applies the Green's function
 //     (and G_eff, screening coupling, gradient) and runs the inverse z pass of
 //     each output before writing it back (Poisson solve, App. B);
 //   * the y inverse pass can emit the y derivative as a second output;
-//   * the x inverse pass can apply the x derivative on load;
+//   * the x inverse pass can apply the x derivative on load, and transforms up
+//     to six independent arrays in one launch;
 //   * the screening source S = delta * eps is formed between an inverse and a
 //     forward x pass in one kernel (Sec. 6.1, Sec. 6.2);
 //   * the LPT reweight by the per-k growth tables (Sec. 4.1, App. A) happens
@@ -25,19 +33,47 @@ namespace {
 
 constexpr int NT = 256;
 
-template <int N>
-struct Tiles {
-  static constexpr int col1 = N <= 512 ? 16 : 8;                                  // 1 buffer
-  static constexpr int col2 = N <= 256 ? 16 : (N == 512 ? 8 : 4);                 // 2 buffers
-  static constexpr int col4 = N <= 128 ? 16 : (N == 256 ? 8 : (N == 512 ? 4 : 2));  // 4 buffers
-  static constexpr int rows = N <= 512 ? 16 : 8;                                  // x pass rows
-};
+// Column tile width: about 4096 complex values per buffer, between 4 and 16
+// columns; 8 columns (64-byte row segments) for single-array 1024-point columns.
+constexpr int col_tw(int N, int NBUF) {
+  return (N == 1024 && NBUF == 1) ? 8
+         : (4096 / (N * NBUF)) < 4 ? 4 : ((4096 / (N * NBUF)) > 16 ? 16 : 4096 / (N * NBUF));
+}
+// Rows per x-pass tile.
+constexpr int row_tw(int N) { return N <= 512 ? 16 : 8; }
+
+// Resident CTAs per SM that the shared memory of a kernel allows (1..3); used
+// as the register bound of __launch_bounds__ so registers never limit occupancy below it.
+constexpr int blocks_for_smem(size_t bytes) {
+  return bytes > 112 * 1024 ? 1 : 2;
+}
+constexpr size_t col_smem_c(int N, int NBUF) {
+  return (N + 2 * (size_t)N * NBUF * col_tw(N, NBUF)) * 8;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
 
 template <class K>
-cudaError_t prep_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t prep(K kernel, size_t smem, int64_t ntiles, unsigned& grid) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
   }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t g = std::min<int64_t>(ntiles, (int64_t)per_sm * sm_count());
+  grid = (unsigned)std::max<int64_t>(g, 1);
   return cudaSuccess;
 }
 
@@ -45,103 +81,59 @@ __device__ __forceinline__ void load_tw(float2* tw, const float2* __restrict__ t
   for (int i = threadIdx.x; i < n; i += NT) tw[i] = twg[i];
 }
 
+// ---------------------------------------------------------------- cp.async helpers
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 16 : 0;  // 0: zero-fill, nothing read
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(sz)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
+}
+
 // ---------------------------------------------------------------- column tiles
 // Tile element (n, c) of sub-block `sub` lives at buf[n * TP + sub * TW + c];
-// global element at g[base + n * sn + c], valid for c0 + c < nvalid.
+// global element at g[base + n * sn + c]; only columns c0 + c < N/2 + 1 exist.
 template <int N, int TW, int TP>
-__device__ __forceinline__ void col_load(float2* buf, int sub, const float2* __restrict__ g,
-                                         int64_t base, int64_t sn, int c0, int nvalid) {
+__device__ __forceinline__ void col_issue(float2* buf, int sub, const float2* __restrict__ g,
+                                          int64_t base, int64_t sn, int c0) {
+  constexpr int CH = TW / 2;  // 16-byte chunks per row segment
 #pragma unroll 4
-  for (int e = threadIdx.x; e < N * TW; e += NT) {
-    const int c = e % TW, n = e / TW;
-    float2 v = make_float2(0.f, 0.f);
-    if (c0 + c < nvalid) v = g[base + (int64_t)n * sn + c];
-    buf[n * TP + sub * TW + c] = v;
+  for (int e = threadIdx.x; e < N * CH; e += NT) {
+    const int j = e % CH, n = e / CH;
+    const bool v = c0 + 2 * j < N / 2 + 1;
+    cp_async16(buf + n * TP + sub * TW + 2 * j, v ? (const void*)(g + base + (int64_t)n * sn + 2 * j)
+                                                   : (const void*)g, v);
+  }
+}
+
+// 16-bit seeds: 4 complex values (uint32 each) per 16-byte chunk.  Field f of
+// row n is staged raw in the sub-block 2/3 area of that row:
+// raw(f, n, c) = ((uint32*)buf)[8 n TW + 4 TW + f TW + c]  (TP = 4 TW).
+template <int N, int TW>
+__device__ __forceinline__ void col_issue_raw(uint32_t* rb, int f, const uint32_t* __restrict__ g,
+                                              int64_t base, int64_t sn, int c0) {
+  constexpr int CH = TW / 4;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < N * CH; e += NT) {
+    const int j = e % CH, n = e / CH;
+    const bool v = c0 + 4 * j < N / 2 + 1;
+    cp_async16(rb + 8 * n * TW + 4 * TW + f * TW + 4 * j,
+               v ? (const void*)(g + base + (int64_t)n * sn + 4 * j) : (const void*)g, v);
   }
 }
 
 template <int N, int TW, int TP>
 __device__ __forceinline__ void col_store(const float2* buf, int sub, float2* __restrict__ g,
-                                          int64_t base, int64_t sn, int c0, int nvalid) {
+                                          int64_t base, int64_t sn, int c0) {
 #pragma unroll 4
   for (int e = threadIdx.x; e < N * TW; e += NT) {
     const int c = e % TW, n = e / TW;
-    if (c0 + c < nvalid) g[base + (int64_t)n * sn + c] = buf[n * TP + sub * TW + c];
+    if (c0 + c < N / 2 + 1) g[base + (int64_t)n * sn + c] = buf[n * TP + sub * TW + c];
   }
-}
-
-// 16-bit seed loads: one 32-bit word holds (re, im).
-template <int PREC>
-__device__ __forceinline__ float2 seed_value(const void* __restrict__ g, int64_t i, float scale) {
-  if constexpr (PREC == 0) {
-    return static_cast<const float2*>(g)[i];
-  } else {
-    const uint32_t w = static_cast<const uint32_t*>(g)[i];
-    float re, im;
-    if constexpr (PREC == 1) {
-      re = __uint_as_float(w << 16);
-      im = __uint_as_float(w & 0xFFFF0000u);
-    } else {
-      re = __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu)));
-      im = __half2float(__ushort_as_half((unsigned short)(w >> 16)));
-    }
-    return make_float2(re * scale, im * scale);
-  }
-}
-
-template <int N, int TW, int TP, int PREC>
-__device__ __forceinline__ void col_load_seed(float2* buf, int sub, const void* __restrict__ g,
-                                              int64_t base, int64_t sn, int c0, int nvalid,
-                                              float scale) {
-#pragma unroll 4
-  for (int e = threadIdx.x; e < N * TW; e += NT) {
-    const int c = e % TW, n = e / TW;
-    float2 v = make_float2(0.f, 0.f);
-    if (c0 + c < nvalid) v = seed_value<PREC>(g, base + (int64_t)n * sn + c, scale);
-    buf[n * TP + sub * TW + c] = v;
-  }
-}
-
-// ---------------------------------------------------------------- plain column pass
-template <int N, int TW, bool INV>
-__global__ void __launch_bounds__(NT) k_col(float2* __restrict__ data, int64_t sn, int64_t so,
-                                            const float2* __restrict__ twg) {
-  extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* buf = sm + N;
-  load_tw(tw, twg, N);
-  const int c0 = blockIdx.x * TW;
-  const int64_t base = (int64_t)blockIdx.y * so + c0;
-  col_load<N, TW, TW>(buf, 0, data, base, sn, c0, N / 2 + 1);
-  __syncthreads();
-  fft_tile<N, TW, TW, NT, INV>(buf, tw);
-  col_store<N, TW, TW>(buf, 0, data, base, sn, c0, N / 2 + 1);
-}
-
-// ---------------------------------------------------------------- y inverse, two outputs
-template <int N, int TW>
-__global__ void __launch_bounds__(NT) k_yinv2(const float2* __restrict__ in,
-                                              float2* __restrict__ outp,
-                                              float2* __restrict__ outd, int64_t P, float kfs,
-                                              const float2* __restrict__ twg) {
-  constexpr int TP = 2 * TW;
-  extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* buf = sm + N;
-  load_tw(tw, twg, N);
-  const int c0 = blockIdx.x * TW;
-  const int64_t base = (int64_t)blockIdx.y * N * P + c0;
-  col_load<N, TW, TP>(buf, 0, in, base, P, c0, N / 2 + 1);
-  __syncthreads();
-  for (int e = threadIdx.x; e < N * TW; e += NT) {
-    const int c = e % TW, n = e / TW;
-    const float f = (n == N / 2) ? 0.f : kfs * (float)freq_index(n, N);
-    buf[n * TP + TW + c] = cscale(cmul_i(buf[n * TP + c]), f);
-  }
-  __syncthreads();
-  fft_tile<N, TP, TP, NT, true>(buf, tw);
-  col_store<N, TW, TP>(buf, 0, outp, base, P, c0, N / 2 + 1);
-  col_store<N, TW, TP>(buf, 1, outd, base, P, c0, N / 2 + 1);
 }
 
 __device__ __forceinline__ float kk2(int ix, int iy, int iz, int N, float kf) {
@@ -149,138 +141,320 @@ __device__ __forceinline__ float kk2(int ix, int iy, int iz, int N, float kf) {
   return kf * kf * (fx * fx + fy * fy + fz * fz);
 }
 
+// Column geometry: tile t -> (outer index o, column block tx); base = o * so + c0.
+template <int N, int TW>
+struct ColGeo {
+  static constexpr int ntx = (N / 2) / TW + 1;
+  int64_t so, sn;
+  __device__ __forceinline__ void tile(int64_t t, int& o, int& c0, int64_t& base) const {
+    o = (int)(t / ntx);
+    c0 = (int)(t % ntx) * TW;
+    base = (int64_t)o * so + c0;
+  }
+};
+
+// Software pipeline over the tiles of one launch.  Op supplies
+//   issue(buf, t): cp.async the inputs of tile t into buf (no commit)
+//   process(buf, tw, t): transform + store (leaves buf free after a final barrier)
+template <int N, int BUFELEMS, class Op>
+__device__ __forceinline__ void col_pipeline(Op op, const float2* __restrict__ twg,
+                                             int64_t ntiles) {
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw = sm;
+  float2* b0 = sm + N;
+  float2* b1 = b0 + BUFELEMS;
+  op.extra = b1 + BUFELEMS;  // optional per-op scratch after the two stage buffers
+  load_tw(tw, twg, N);
+  int64_t t = blockIdx.x;
+  if (t < ntiles) op.issue(b0, t);
+  cp_async_commit();
+  int cur = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) op.issue(cur ? b0 : b1, tn);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    op.process(cur ? b1 : b0, tw, t);
+    __syncthreads();
+    cur ^= 1;
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------- plain column pass
+template <int N, int TW, bool INV>
+struct OpCol {
+  ColGeo<N, TW> geo;
+  float2* data;
+  float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
+  __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
+    int o, c0;
+    int64_t base;
+    geo.tile(t, o, c0, base);
+    col_issue<N, TW, TW>(buf, 0, data, base, geo.sn, c0);
+  }
+  __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
+    int o, c0;
+    int64_t base;
+    geo.tile(t, o, c0, base);
+    fft_tile<N, TW, TW, NT, INV>(buf, tw);
+    col_store<N, TW, TW>(buf, 0, data, base, geo.sn, c0);
+  }
+};
+
+template <int N, int TW, bool INV>
+__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1))) k_col(OpCol<N, TW, INV> op, const float2* __restrict__ twg,
+                                            int64_t ntiles) {
+  col_pipeline<N, N * TW>(op, twg, ntiles);
+}
+
+// ---------------------------------------------------------------- y inverse, two outputs
+template <int N, int TW>
+struct OpYinv2 {
+  ColGeo<N, TW> geo;
+  const float2* in;
+  float2 *outp, *outd;
+  float kfs;
+  float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
+  __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
+    int o, c0;
+    int64_t base;
+    geo.tile(t, o, c0, base);
+    col_issue<N, TW, 2 * TW>(buf, 0, in, base, geo.sn, c0);
+  }
+  __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
+    constexpr int TP = 2 * TW;
+    int o, c0;
+    int64_t base;
+    geo.tile(t, o, c0, base);
+    for (int e = threadIdx.x; e < N * TW; e += NT) {
+      const int c = e % TW, n = e / TW;
+      const float f = (n == N / 2) ? 0.f : kfs * (float)freq_index(n, N);
+      buf[n * TP + TW + c] = cscale(cmul_i(buf[n * TP + c]), f);
+    }
+    __syncthreads();
+    fft_tile<N, TP, TP, NT, true>(buf, tw);
+    col_store<N, TW, TP>(buf, 0, outp, base, geo.sn, c0);
+    col_store<N, TW, TP>(buf, 1, outd, base, geo.sn, c0);
+  }
+};
+
+template <int N, int TW>
+__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 2))) k_yinv2(OpYinv2<N, TW> op, const float2* __restrict__ twg,
+                                              int64_t ntiles) {
+  col_pipeline<N, N * 2 * TW>(op, twg, ntiles);
+}
+
 // ---------------------------------------------------------------- screening field (z pass)
 template <int N, int TW, int MODEL>
-__global__ void __launch_bounds__(NT) k_z_screen_field(const float2* __restrict__ in,
-                                                       float2* __restrict__ dk_out,
-                                                       float2* __restrict__ w_out, int64_t P,
-                                                       ForceParams fp,
-                                                       const float2* __restrict__ twg) {
-  extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* buf = sm + N;
-  load_tw(tw, twg, N);
-  const int c0 = blockIdx.x * TW;
-  const int iy = blockIdx.y;
-  const int64_t base = (int64_t)iy * P + c0;
-  const int64_t sn = (int64_t)N * P;
-  col_load<N, TW, TW>(buf, 0, in, base, sn, c0, N / 2 + 1);
-  __syncthreads();
-  fft_tile<N, TW, TW, NT, false>(buf, tw);
-  for (int e = threadIdx.x; e < N * TW; e += NT) {
-    const int c = e % TW, n = e / TW;
-    const float2 v = buf[n * TW + c];
-    if (c0 + c < N / 2 + 1) dk_out[base + (int64_t)n * sn + c] = v;
-    const float k2 = kk2(c0 + c, iy, n, N, fp.kf);
-    float m = 0.f;
-    if (k2 > 0.f) {
-      if (MODEL == 1) m = -fp.kappa_norm / k2;
-      else m = __expf(-k2 * fp.R2half) * fp.norm;
-    }
-    buf[n * TW + c] = cscale(v, m);
+struct OpZScreenField {
+  ColGeo<N, TW> geo;
+  const float2* in;
+  float2 *dk_out, *w_out;
+  ForceParams fp;
+  float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
+  __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
+    int o, c0;
+    int64_t base;
+    geo.tile(t, o, c0, base);
+    col_issue<N, TW, TW>(buf, 0, in, base, geo.sn, c0);
   }
-  __syncthreads();
-  fft_tile<N, TW, TW, NT, true>(buf, tw);
-  col_store<N, TW, TW>(buf, 0, w_out, base, sn, c0, N / 2 + 1);
+  __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
+    int iy, c0;
+    int64_t base;
+    geo.tile(t, iy, c0, base);
+    fft_tile_call<N, TW, TW, NT, false>(buf, tw);
+#pragma unroll 2
+    for (int e = threadIdx.x; e < N * TW; e += NT) {
+      const int c = e % TW, n = e / TW;
+      const float2 v = buf[n * TW + c];
+      if (c0 + c < N / 2 + 1) dk_out[base + (int64_t)n * geo.sn + c] = v;
+      const float k2 = kk2(c0 + c, iy, n, N, fp.kf);
+      float m = 0.f;
+      if (k2 > 0.f) {
+        if (MODEL == 1) m = -fp.kappa_norm / k2;
+        else m = __expf(-k2 * fp.R2half) * fp.norm;
+      }
+      buf[n * TW + c] = cscale(v, m);
+    }
+    __syncthreads();
+    fft_tile_call<N, TW, TW, NT, true>(buf, tw);
+    col_store<N, TW, TW>(buf, 0, w_out, base, geo.sn, c0);
+  }
+};
+
+template <int N, int TW, int MODEL>
+__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1))) k_z_screen_field(OpZScreenField<N, TW, MODEL> op,
+                                                       const float2* __restrict__ twg,
+                                                       int64_t ntiles) {
+  col_pipeline<N, N * TW>(op, twg, ntiles);
 }
 
 // ---------------------------------------------------------------- force (z pass)
+// One staged buffer per tile: the source (S, or delta when unscreened) is
+// transformed forward; delta(k) is read straight from global memory; Phi_tot(k)
+// is kept in registers while the two outputs (Phi and -i kz Phi) are inverse
+// transformed one after the other in the same buffer.
 template <int N, int TW, bool SCREENED, bool KEEP>
-__global__ void __launch_bounds__(NT) k_z_force(const float2* __restrict__ in,
-                                                const float2* __restrict__ dk,
-                                                float2* __restrict__ phi_out,
-                                                float2* __restrict__ phiz_out,
-                                                float2* __restrict__ dk_keep, int64_t P,
-                                                ForceParams fp, const float2* __restrict__ twg) {
-  constexpr int TP = 2 * TW;
-  extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* buf = sm + N;
-  load_tw(tw, twg, N);
-  const int c0 = blockIdx.x * TW;
-  const int iy = blockIdx.y;
-  const int64_t base = (int64_t)iy * P + c0;
-  const int64_t sn = (int64_t)N * P;
-  col_load<N, TW, TP>(buf, 0, in, base, sn, c0, N / 2 + 1);
-  if (SCREENED) col_load<N, TW, TP>(buf, 1, dk, base, sn, c0, N / 2 + 1);
-  __syncthreads();
-  fft_tile<N, TW, TP, NT, false>(buf, tw);
-  if (KEEP) col_store<N, TW, TP>(buf, 0, dk_keep, base, sn, c0, N / 2 + 1);
-  for (int e = threadIdx.x; e < N * TW; e += NT) {
-    const int c = e % TW, n = e / TW;
-    const float k2 = kk2(c0 + c, iy, n, N, fp.kf);
-    float2 phi = make_float2(0.f, 0.f);
-    if (k2 > 0.f) {
-      const float yuk = k2 / (k2 + fp.a2m2);
-      const float g = -fp.kappa_norm / k2;
-      const float2 src = buf[n * TP + c];
-      if (SCREENED) {
-        const float2 d = buf[n * TP + TW + c];
-        phi = cscale(cadd(d, cscale(src, fp.C * yuk)), g);
-      } else {
-        phi = cscale(src, g * (1.f + fp.C * yuk));
-      }
-    }
-    const float kzs = (n == N / 2) ? 0.f : -fp.kf * (float)freq_index(n, N);
-    buf[n * TP + c] = phi;
-    buf[n * TP + TW + c] = cscale(cmul_i(phi), kzs);
+struct OpZForce {
+  static constexpr int E = (N * TW) / NT;  // elements per thread
+  ColGeo<N, TW> geo;
+  const float2 *in, *dk;
+  float2 *phi_out, *phiz_out, *dk_keep;
+  ForceParams fp;
+  float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
+  __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
+    int o, c0;
+    int64_t base;
+    geo.tile(t, o, c0, base);
+    col_issue<N, TW, TW>(buf, 0, in, base, geo.sn, c0);
   }
-  __syncthreads();
-  fft_tile<N, TP, TP, NT, true>(buf, tw);
-  col_store<N, TW, TP>(buf, 0, phi_out, base, sn, c0, N / 2 + 1);
-  col_store<N, TW, TP>(buf, 1, phiz_out, base, sn, c0, N / 2 + 1);
+  __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
+    int iy, c0;
+    int64_t base;
+    geo.tile(t, iy, c0, base);
+    float2* ph = extra;  // delta(k) of the tile, then Phi_tot(k), N x TW
+    if (SCREENED) {
+      col_issue<N, TW, TW>(ph, 0, dk, base, geo.sn, c0);  // lands while S is transformed
+      cp_async_commit();
+    }
+    fft_tile_call<N, TW, TW, NT, false>(buf, tw);
+    if (KEEP) col_store<N, TW, TW>(buf, 0, dk_keep, base, geo.sn, c0);
+    if (SCREENED) {
+      cp_async_wait<0>();
+      __syncthreads();
+    }
+#pragma unroll 2
+    for (int i = 0; i < E; ++i) {
+      const int e = threadIdx.x + i * NT;
+      const int c = e % TW, n = e / TW;
+      const float k2 = kk2(c0 + c, iy, n, N, fp.kf);
+      float2 phi = make_float2(0.f, 0.f);
+      if (k2 > 0.f) {
+        const float yuk = k2 / (k2 + fp.a2m2);
+        const float g = -fp.kappa_norm / k2;
+        const float2 src = buf[n * TW + c];
+        if (SCREENED) {
+          phi = cscale(cadd(ph[n * TW + c], cscale(src, fp.C * yuk)), g);
+        } else {
+          phi = cscale(src, g * (1.f + fp.C * yuk));
+        }
+      }
+      ph[n * TW + c] = phi;
+      buf[n * TW + c] = phi;
+    }
+    __syncthreads();
+    fft_tile_call<N, TW, TW, NT, true>(buf, tw);
+    col_store<N, TW, TW>(buf, 0, phi_out, base, geo.sn, c0);
+    __syncthreads();
+#pragma unroll 2
+    for (int i = 0; i < E; ++i) {
+      const int e = threadIdx.x + i * NT;
+      const int c = e % TW, n = e / TW;
+      const float kzs = (n == N / 2) ? 0.f : -fp.kf * (float)freq_index(n, N);
+      buf[n * TW + c] = cscale(cmul_i(ph[n * TW + c]), kzs);
+    }
+    __syncthreads();
+    fft_tile_call<N, TW, TW, NT, true>(buf, tw);
+    col_store<N, TW, TW>(buf, 0, phiz_out, base, geo.sn, c0);
+  }
+};
+
+template <int N, int TW, bool SCREENED, bool KEEP>
+__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1) + (size_t)N * TW * 8)) k_z_force(
+    OpZForce<N, TW, SCREENED, KEEP> op, const float2* __restrict__ twg, int64_t ntiles) {
+  col_pipeline<N, N * TW>(op, twg, ntiles);
 }
 
 // ---------------------------------------------------------------- LPT reweight (z pass)
-template <int N, int TW, int PREC>
-__global__ void __launch_bounds__(NT) k_lpt_z(const void* __restrict__ phi1,
-                                              const void* __restrict__ phi2,
-                                              float2* __restrict__ o0, float2* __restrict__ o1,
-                                              float2* __restrict__ o2, float2* __restrict__ o3,
-                                              int64_t P, LptParams lp,
-                                              const float2* __restrict__ twg) {
-  constexpr int TP = 4 * TW;
-  extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* buf = sm + N;
-  load_tw(tw, twg, N);
-  const int c0 = blockIdx.x * TW;
-  const int iy = blockIdx.y;
-  const int64_t base = (int64_t)iy * P + c0;
-  const int64_t sn = (int64_t)N * P;
-  col_load_seed<N, TW, TP, PREC>(buf, 0, phi1, base, sn, c0, N / 2 + 1, lp.seed_scale1);
-  col_load_seed<N, TW, TP, PREC>(buf, 1, phi2, base, sn, c0, N / 2 + 1, lp.seed_scale2);
-  __syncthreads();
-  for (int e = threadIdx.x; e < N * TW; e += NT) {
-    const int c = e % TW, n = e / TW;
-    const float k2 = kk2(c0 + c, iy, n, N, lp.kf);
-    float2 d = make_float2(0.f, 0.f), A = make_float2(0.f, 0.f);
-    if (k2 > 0.f) {
-      const float u = (0.5f * __logf(k2) - lp.lnk0) * lp.inv_dlnk;
-      int i = (int)floorf(u);
-      i = min(max(i, 0), lp.nk - 2);
-      const float f = u - (float)i;
-      const float4 t0 = lp.tab[i], t1 = lp.tab[i + 1];
-      const float c1 = t0.x * (1.f - f) + t1.x * f;
-      const float c2 = t0.y * (1.f - f) + t1.y * f;
-      const float e1 = t0.z * (1.f - f) + t1.z * f;
-      const float e2 = t0.w * (1.f - f) + t1.w * f;
-      const float2 p1 = buf[n * TP + c], p2 = buf[n * TP + TW + c];
-      d = cscale(cadd(cscale(p1, c1), cscale(p2, c2)), lp.norm);
-      A = cscale(cadd(cscale(p1, e1), cscale(p2, e2)), lp.norm);
-    }
-    const float kz = (n == N / 2) ? 0.f : lp.kf * (float)freq_index(n, N);
-    buf[n * TP + c] = d;
-    buf[n * TP + TW + c] = cscale(cmul_i(d), kz);
-    buf[n * TP + 2 * TW + c] = A;
-    buf[n * TP + 3 * TW + c] = cscale(cmul_i(A), kz);
+template <int PREC>
+__device__ __forceinline__ float2 dequant(uint32_t w, float scale) {
+  float re, im;
+  if constexpr (PREC == 1) {
+    re = __uint_as_float(w << 16);
+    im = __uint_as_float(w & 0xFFFF0000u);
+  } else {
+    re = __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu)));
+    im = __half2float(__ushort_as_half((unsigned short)(w >> 16)));
   }
-  __syncthreads();
-  fft_tile<N, TP, TP, NT, true>(buf, tw);
-  col_store<N, TW, TP>(buf, 0, o0, base, sn, c0, N / 2 + 1);
-  col_store<N, TW, TP>(buf, 1, o1, base, sn, c0, N / 2 + 1);
-  col_store<N, TW, TP>(buf, 2, o2, base, sn, c0, N / 2 + 1);
-  col_store<N, TW, TP>(buf, 3, o3, base, sn, c0, N / 2 + 1);
+  return make_float2(re * scale, im * scale);
+}
+
+template <int N, int TW, int PREC>
+struct OpLptZ {
+  ColGeo<N, TW> geo;
+  const void *phi1, *phi2;
+  float2 *o0, *o1, *o2, *o3;
+  LptParams lp;
+  float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
+  __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
+    int o, c0;
+    int64_t base;
+    geo.tile(t, o, c0, base);
+    if constexpr (PREC == 0) {
+      col_issue<N, TW, 4 * TW>(buf, 0, static_cast<const float2*>(phi1), base, geo.sn, c0);
+      col_issue<N, TW, 4 * TW>(buf, 1, static_cast<const float2*>(phi2), base, geo.sn, c0);
+    } else {
+      // raw 16-bit pairs staged in the (still unused) output sub-blocks 2 and 3
+      uint32_t* rb = reinterpret_cast<uint32_t*>(buf);
+      col_issue_raw<N, TW>(rb, 0, static_cast<const uint32_t*>(phi1), base, geo.sn, c0);
+      col_issue_raw<N, TW>(rb, 1, static_cast<const uint32_t*>(phi2), base, geo.sn, c0);
+    }
+  }
+  __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
+    constexpr int TP = 4 * TW;
+    int iy, c0;
+    int64_t base;
+    geo.tile(t, iy, c0, base);
+    if constexpr (PREC != 0) {
+      const uint32_t* rb = reinterpret_cast<const uint32_t*>(buf);
+      for (int e = threadIdx.x; e < N * TW; e += NT) {
+        const int c = e % TW, n = e / TW;
+        const float2 a = dequant<PREC>(rb[8 * n * TW + 4 * TW + c], lp.seed_scale1);
+        const float2 b = dequant<PREC>(rb[8 * n * TW + 5 * TW + c], lp.seed_scale2);
+        buf[n * TP + c] = a;
+        buf[n * TP + TW + c] = b;
+      }
+      __syncthreads();  // the raw staging (sub-blocks 2, 3) is consumed
+    }
+    for (int e = threadIdx.x; e < N * TW; e += NT) {
+      const int c = e % TW, n = e / TW;
+      const float k2 = kk2(c0 + c, iy, n, N, lp.kf);
+      float2 d = make_float2(0.f, 0.f), A = make_float2(0.f, 0.f);
+      if (k2 > 0.f) {
+        const float u = (0.5f * __logf(k2) - lp.lnk0) * lp.inv_dlnk;
+        int i0 = (int)floorf(u);
+        i0 = min(max(i0, 0), lp.nk - 2);
+        const float f = u - (float)i0;
+        const float4 t0 = lp.tab[i0], t1 = lp.tab[i0 + 1];
+        const float c1 = t0.x * (1.f - f) + t1.x * f;
+        const float c2 = t0.y * (1.f - f) + t1.y * f;
+        const float e1 = t0.z * (1.f - f) + t1.z * f;
+        const float e2 = t0.w * (1.f - f) + t1.w * f;
+        const float2 p1 = buf[n * TP + c], p2 = buf[n * TP + TW + c];
+        d = cscale(cadd(cscale(p1, c1), cscale(p2, c2)), lp.norm);
+        A = cscale(cadd(cscale(p1, e1), cscale(p2, e2)), lp.norm);
+      }
+      const float kz = (n == N / 2) ? 0.f : lp.kf * (float)freq_index(n, N);
+      buf[n * TP + c] = d;
+      buf[n * TP + TW + c] = cscale(cmul_i(d), kz);
+      buf[n * TP + 2 * TW + c] = A;
+      buf[n * TP + 3 * TW + c] = cscale(cmul_i(A), kz);
+    }
+    __syncthreads();
+    fft_tile<N, TP, TP, NT, true>(buf, tw);
+    col_store<N, TW, TP>(buf, 0, o0, base, geo.sn, c0);
+    col_store<N, TW, TP>(buf, 1, o1, base, geo.sn, c0);
+    col_store<N, TW, TP>(buf, 2, o2, base, geo.sn, c0);
+    col_store<N, TW, TP>(buf, 3, o3, base, geo.sn, c0);
+  }
+};
+
+template <int N, int TW, int PREC>
+__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 4))) k_lpt_z(OpLptZ<N, TW, PREC> op,
+                                              const float2* __restrict__ twg, int64_t ntiles) {
+  col_pipeline<N, N * 4 * TW>(op, twg, ntiles);
 }
 
 // ---------------------------------------------------------------- x passes (rows)
@@ -302,77 +476,167 @@ __device__ __forceinline__ void row_r2c_store(const float2* buf, const float2* t
   }
 }
 
-// c2r pre-processing (unnormalised inverse, 2x folded in):
-// E = X[k] + conj X[M-k], O = w^-k (X[k] - conj X[M-k]), Z[k] = E + i O,
-// Z[M-k] = conj E + i conj O.  Imaginary parts of X[0], X[M] are dropped.
+// c2r pre-processing (unnormalised inverse, 2x folded in), on a tile already in
+// buf[k * PITCH + r], k = 0..M: E = X[k] + conj X[M-k], O = w^-k (X[k] - conj X[M-k]),
+// Z[k] = E + i O, Z[M-k] = conj E + i conj O.
 template <int N, int TWX, int PITCH>
-__device__ __forceinline__ void row_c2r_load(float2* buf, const float2* tw,
-                                             const float2* __restrict__ in, int64_t row0,
-                                             int64_t P, float kfs) {
+__device__ __forceinline__ void row_c2r_combine(float2* buf, const float2* tw) {
   constexpr int M = N / 2;
-#pragma unroll 2
-  for (int e = threadIdx.x; e < TWX * (M + 1); e += NT) {
-    const int r = e / (M + 1), k = e - r * (M + 1);
-    float2 v = in[(row0 + r) * P + k];
-    if (kfs != 0.f) v = (k == M) ? make_float2(0.f, 0.f) : cscale(cmul_i(v), kfs * (float)k);
-    if (k == 0 || k == M) v.y = 0.f;
-    buf[k * PITCH + r] = v;
-  }
-  __syncthreads();
   for (int e = threadIdx.x; e < TWX * (M / 2 + 1); e += NT) {
     const int r = e / (M / 2 + 1), k = e - r * (M / 2 + 1);
     const float2 a = buf[k * PITCH + r];
     const float2 b = cconj(buf[(M - k) * PITCH + r]);
     const float2 E = cadd(a, b);
     const float2 O = cmul(cconj(tw[k]), csub(a, b));
-    const float2 Z = cadd(E, cmul_i(O));
-    buf[k * PITCH + r] = Z;
+    buf[k * PITCH + r] = cadd(E, cmul_i(O));
     if (k != 0 && k != M - k) buf[(M - k) * PITCH + r] = cadd(cconj(E), cmul_i(cconj(O)));
   }
   __syncthreads();
 }
 
+// Up to six independent row transforms per launch (job = tile / tiles_per_job).
+struct RowJobs {
+  const void* in[6];
+  void* out[6];
+  float kfs[6];
+  int njobs;
+};
+
+// Row tiles are staged raw with cp.async (double-buffered, row-major), then
+// transposed in shared memory into the transform layout buf[k * (TWX+1) + r].
+// Complex half rows are staged as M + 2 values (the pitch leaves room for the
+// padding value, and M + 2 keeps 16-byte chunks); real rows as N floats.
 template <int N, int TWX>
-__global__ void __launch_bounds__(NT) k_xr2c(const float* __restrict__ in,
-                                             float2* __restrict__ out, int64_t P, float scale,
-                                             float offset, const float2* __restrict__ twg) {
-  constexpr int M = N / 2, PITCH = TWX + 1;
-  extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* buf = sm + N;
-  load_tw(tw, twg, N);
-  const int64_t row0 = (int64_t)blockIdx.x * TWX;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < TWX * M; e += NT) {
-    const int r = e / M, j = e % M;
-    float2 v = reinterpret_cast<const float2*>(in + (row0 + r) * N)[j];
-    v.x = v.x * scale + offset;
-    v.y = v.y * scale + offset;
-    buf[j * PITCH + r] = v;
+struct RowCfg {
+  static constexpr int M = N / 2;
+  static constexpr int PITCH = TWX + 1;
+  static constexpr int CW = M + 2;                       // staged complex values per row
+  static constexpr size_t fftbuf = (size_t)(M + 1) * PITCH;  // float2
+  static constexpr size_t stage = (size_t)TWX * CW;          // float2 (>= TWX * N floats)
+  static constexpr size_t smem = (N + fftbuf + 2 * stage) * sizeof(float2);
+};
+
+template <int N, int TWX>
+__device__ __forceinline__ void stage_complex_rows(float2* st, const float2* __restrict__ in,
+                                                   int64_t row0, int64_t P) {
+  using C = RowCfg<N, TWX>;
+  constexpr int CH = C::CW / 2;
+  for (int e = threadIdx.x; e < TWX * CH; e += NT) {
+    const int r = e / CH, j = e - r * CH;
+    cp_async16(st + r * C::CW + 2 * j, in + (row0 + r) * P + 2 * j, true);
   }
-  __syncthreads();
-  fft_tile<M, TWX, PITCH, NT, false, 2>(buf, tw);
-  row_r2c_store<N, TWX, PITCH>(buf, tw, out, row0, P);
 }
 
 template <int N, int TWX>
-__global__ void __launch_bounds__(NT) k_xc2r(const float2* __restrict__ in,
-                                             float* __restrict__ out, int64_t P, float kfs,
-                                             const float2* __restrict__ twg) {
-  constexpr int M = N / 2, PITCH = TWX + 1;
-  extern __shared__ float2 sm[];
+__device__ __forceinline__ void stage_real_rows(float2* st, const float* __restrict__ in,
+                                                int64_t row0) {
+  constexpr int CH = N / 4;
+  float* s = reinterpret_cast<float*>(st);
+  for (int e = threadIdx.x; e < TWX * CH; e += NT) {
+    const int r = e / CH, j = e - r * CH;
+    cp_async16(s + r * N + 4 * j, in + (row0 + r) * N + 4 * j, true);
+  }
+}
+
+// staged complex rows -> transform layout, with the i kfs k multiplier and the
+// imaginary parts of X[0], X[M] dropped (c2r input convention)
+template <int N, int TWX>
+__device__ __forceinline__ void put_c2r(float2* buf, const float2* st, float kfs) {
+  using C = RowCfg<N, TWX>;
+  constexpr int M = N / 2;
+  for (int e = threadIdx.x; e < TWX * (M + 1); e += NT) {
+    const int r = e / (M + 1), k = e - r * (M + 1);
+    float2 x = st[r * C::CW + k];
+    if (kfs != 0.f) x = (k == M) ? make_float2(0.f, 0.f) : cscale(cmul_i(x), kfs * (float)k);
+    if (k == 0 || k == M) x.y = 0.f;
+    buf[k * C::PITCH + r] = x;
+  }
+}
+
+template <int N, int TWX>
+__device__ __forceinline__ void put_r2c(float2* buf, const float2* st, float scale, float offset) {
+  using C = RowCfg<N, TWX>;
+  constexpr int M = N / 2;
+  for (int e = threadIdx.x; e < TWX * M; e += NT) {
+    const int r = e / M, j = e - r * M;
+    const float2 v = st[r * M + j];  // row r holds N floats = M float2
+    buf[j * C::PITCH + r] = make_float2(v.x * scale + offset, v.y * scale + offset);
+  }
+}
+
+template <int N, int TWX>
+__global__ void __launch_bounds__(NT, 2) k_xr2c(const float* __restrict__ in, float2* __restrict__ out,
+                                                int64_t P, float scale, float offset,
+                                                const float2* __restrict__ twg, int64_t ntiles) {
+  using C = RowCfg<N, TWX>;
+  constexpr int M = N / 2;
+  extern __shared__ __align__(16) float2 sm[];
   float2* tw = sm;
   float2* buf = sm + N;
+  float2* st0 = buf + C::fftbuf + (C::fftbuf & 1);
+  float2* st1 = st0 + C::stage;
   load_tw(tw, twg, N);
-  const int64_t row0 = (int64_t)blockIdx.x * TWX;
-  __syncthreads();
-  row_c2r_load<N, TWX, PITCH>(buf, tw, in, row0, P, kfs);
-  fft_tile<M, TWX, PITCH, NT, true, 2>(buf, tw);
-#pragma unroll 4
-  for (int e = threadIdx.x; e < TWX * M; e += NT) {
-    const int r = e / M, j = e % M;
-    reinterpret_cast<float2*>(out + (row0 + r) * N)[j] = buf[j * PITCH + r];
+  int64_t t = blockIdx.x;
+  if (t < ntiles) stage_real_rows<N, TWX>(st0, in, t * TWX);
+  cp_async_commit();
+  int cur = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) stage_real_rows<N, TWX>(cur ? st0 : st1, in, tn * TWX);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    put_r2c<N, TWX>(buf, cur ? st1 : st0, scale, offset);
+    __syncthreads();
+    fft_tile<M, TWX, C::PITCH, NT, false, 2>(buf, tw);
+    row_r2c_store<N, TWX, C::PITCH>(buf, tw, out, t * TWX, P);
+    __syncthreads();
+    cur ^= 1;
   }
+  cp_async_wait<0>();
+}
+
+template <int N, int TWX>
+__global__ void __launch_bounds__(NT, 2) k_xc2r(RowJobs jobs, int64_t P,
+                                                const float2* __restrict__ twg, int64_t tiles_per_job) {
+  using C = RowCfg<N, TWX>;
+  constexpr int M = N / 2;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw = sm;
+  float2* buf = sm + N;
+  float2* st0 = buf + C::fftbuf + (C::fftbuf & 1);
+  float2* st1 = st0 + C::stage;
+  load_tw(tw, twg, N);
+  const int64_t ntiles = tiles_per_job * jobs.njobs;
+  int64_t t = blockIdx.x;
+  if (t < ntiles)
+    stage_complex_rows<N, TWX>(st0, static_cast<const float2*>(jobs.in[t / tiles_per_job]),
+                               (t % tiles_per_job) * TWX, P);
+  cp_async_commit();
+  int cur = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const int job = (int)(t / tiles_per_job);
+    const int64_t row0 = (t % tiles_per_job) * TWX;
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles)
+      stage_complex_rows<N, TWX>(cur ? st0 : st1, static_cast<const float2*>(jobs.in[tn / tiles_per_job]),
+                                 (tn % tiles_per_job) * TWX, P);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    put_c2r<N, TWX>(buf, cur ? st1 : st0, jobs.kfs[job]);
+    __syncthreads();
+    row_c2r_combine<N, TWX, C::PITCH>(buf, tw);
+    fft_tile<M, TWX, C::PITCH, NT, true, 2>(buf, tw);
+    float* out = static_cast<float*>(jobs.out[job]);
+    for (int e = threadIdx.x; e < TWX * M; e += NT) {
+      const int r = e / M, j = e % M;
+      reinterpret_cast<float2*>(out + (row0 + r) * N)[j] = buf[j * C::PITCH + r];
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  cp_async_wait<0>();
 }
 
 template <int MODEL>
@@ -387,31 +651,81 @@ __device__ __forceinline__ float screen_eps(float w, const ForceParams& fp) {
 }
 
 template <int N, int TWX, int MODEL>
-__global__ void __launch_bounds__(NT) k_x_screen(const float2* __restrict__ w_in,
-                                                 const float* __restrict__ rho,
-                                                 float2* __restrict__ s_out, int64_t P,
-                                                 ForceParams fp,
-                                                 const float2* __restrict__ twg) {
-  constexpr int M = N / 2, PITCH = TWX + 1;
-  extern __shared__ float2 sm[];
+__global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w_in,
+                                                    const float* __restrict__ rho,
+                                                    float2* __restrict__ s_out, int64_t P,
+                                                    ForceParams fp, const float2* __restrict__ twg,
+                                                    int64_t ntiles) {
+  using C = RowCfg<N, TWX>;
+  constexpr int M = N / 2;
+  extern __shared__ __align__(16) float2 sm[];
   float2* tw = sm;
   float2* buf = sm + N;
+  float2* st0 = buf + C::fftbuf + (C::fftbuf & 1);
+  float2* st1 = st0 + C::stage;
   load_tw(tw, twg, N);
-  const int64_t row0 = (int64_t)blockIdx.x * TWX;
-  __syncthreads();
-  row_c2r_load<N, TWX, PITCH>(buf, tw, w_in, row0, P, 0.f);
-  fft_tile<M, TWX, PITCH, NT, true, 2>(buf, tw);
-#pragma unroll 4
-  for (int e = threadIdx.x; e < TWX * M; e += NT) {
-    const int r = e / M, j = e % M;
-    const float2 w = buf[j * PITCH + r];
-    const float2 rr = reinterpret_cast<const float2*>(rho + (row0 + r) * N)[j];
-    const float d0 = rr.x * fp.inv_rhobar - 1.f, d1 = rr.y * fp.inv_rhobar - 1.f;
-    buf[j * PITCH + r] = make_float2(d0 * screen_eps<MODEL>(w.x, fp), d1 * screen_eps<MODEL>(w.y, fp));
+  int64_t t = blockIdx.x;
+  if (t < ntiles) stage_complex_rows<N, TWX>(st0, w_in, t * TWX, P);
+  cp_async_commit();
+  int cur = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const int64_t row0 = t * TWX;
+    const int64_t tn = t + gridDim.x;
+    float2* stc = cur ? st1 : st0;
+    if (tn < ntiles) stage_complex_rows<N, TWX>(cur ? st0 : st1, w_in, tn * TWX, P);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    put_c2r<N, TWX>(buf, stc, 0.f);
+    __syncthreads();
+    // the current staging buffer is free again: bring in the density rows of this tile
+    stage_real_rows<N, TWX>(stc, rho, row0);
+    cp_async_commit();
+    row_c2r_combine<N, TWX, C::PITCH>(buf, tw);
+    fft_tile_call<M, TWX, C::PITCH, NT, true, 2>(buf, tw);
+    cp_async_wait<0>();
+    __syncthreads();
+    const float2* rr = stc;  // row r holds N floats = M float2
+    for (int e = threadIdx.x; e < TWX * M; e += NT) {
+      const int r = e / M, j = e % M;
+      const float2 w = buf[j * C::PITCH + r];
+      const float2 rv = rr[r * M + j];
+      const float d0 = rv.x * fp.inv_rhobar - 1.f, d1 = rv.y * fp.inv_rhobar - 1.f;
+      buf[j * C::PITCH + r] = make_float2(d0 * screen_eps<MODEL>(w.x, fp), d1 * screen_eps<MODEL>(w.y, fp));
+    }
+    __syncthreads();
+    fft_tile_call<M, TWX, C::PITCH, NT, false, 2>(buf, tw);
+    row_r2c_store<N, TWX, C::PITCH>(buf, tw, s_out, row0, P);
+    __syncthreads();
+    cur ^= 1;
   }
-  __syncthreads();
-  fft_tile<M, TWX, PITCH, NT, false, 2>(buf, tw);
-  row_r2c_store<N, TWX, PITCH>(buf, tw, s_out, row0, P);
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------- launch helpers
+template <int N, int NBUF>
+constexpr size_t col_smem() {
+  return (N + 2 * (size_t)N * NBUF * col_tw(N, NBUF)) * sizeof(float2);
+}
+
+template <int N>
+constexpr size_t row_smem(bool) {
+  return RowCfg<N, row_tw(N)>::smem + sizeof(float2);
+}
+
+template <int N, int TW>
+ColGeo<N, TW> geo_y() {
+  const int64_t P = half_pitch(N);
+  return ColGeo<N, TW>{(int64_t)N * P, P};
+}
+template <int N, int TW>
+ColGeo<N, TW> geo_z() {
+  const int64_t P = half_pitch(N);
+  return ColGeo<N, TW>{P, (int64_t)N * P};
+}
+template <int N, int TW>
+constexpr int64_t col_tiles() {
+  return (int64_t)N * ((N / 2) / TW + 1);
 }
 
 }  // namespace
@@ -430,12 +744,14 @@ __global__ void __launch_bounds__(NT) k_x_screen(const float2* __restrict__ w_in
 template <int N>
 static cudaError_t launch_xr2c(const float* in, float2* out, float scale, float offset,
                                const float2* tw, cudaStream_t s) {
-  constexpr int TWX = Tiles<N>::rows;
-  const size_t sm = (N + (N / 2) * (TWX + 1)) * sizeof(float2);
+  constexpr int TWX = row_tw(N);
+  const size_t sm = row_smem<N>(false);
+  const int64_t ntiles = (int64_t)N * N / TWX;
   auto k = k_xr2c<N, TWX>;
-  cudaError_t e = prep_smem(k, sm);
+  unsigned grid;
+  cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)((int64_t)N * N / TWX), NT, sm, s>>>(in, out, half_pitch(N), scale, offset, tw);
+  k<<<grid, NT, sm, s>>>(in, out, half_pitch(N), scale, offset, tw, ntiles);
   return cudaGetLastError();
 }
 
@@ -446,42 +762,56 @@ cudaError_t fft_xr2c(int Nv, const float* in, float2* out, float scale, float of
 }
 
 template <int N>
-static cudaError_t launch_xc2r(const float2* in, float* out, float kfs, const float2* tw,
-                               cudaStream_t s) {
-  constexpr int TWX = Tiles<N>::rows;
-  const size_t sm = (N + (N / 2 + 1) * (TWX + 1)) * sizeof(float2);
+static cudaError_t launch_xc2r_multi(int njobs, const float2* const* in, float* const* out,
+                                     const float* kfs, const float2* tw, cudaStream_t s) {
+  constexpr int TWX = row_tw(N);
+  const size_t sm = row_smem<N>(true);
+  RowJobs jobs{};
+  jobs.njobs = njobs;
+  for (int i = 0; i < njobs; ++i) {
+    jobs.in[i] = in[i];
+    jobs.out[i] = out[i];
+    jobs.kfs[i] = kfs[i];
+  }
+  const int64_t tpj = (int64_t)N * N / TWX;
   auto k = k_xc2r<N, TWX>;
-  cudaError_t e = prep_smem(k, sm);
+  unsigned grid;
+  cudaError_t e = prep(k, sm, tpj * njobs, grid);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)((int64_t)N * N / TWX), NT, sm, s>>>(in, out, half_pitch(N), kfs, tw);
+  k<<<grid, NT, sm, s>>>(jobs, half_pitch(N), tw, tpj);
   return cudaGetLastError();
+}
+
+cudaError_t fft_xc2r_multi(int Nv, int njobs, const float2* const* in, float* const* out,
+                           const float* kfs, const float2* tw, cudaStream_t s) {
+  if (njobs < 1 || njobs > 6) return cudaErrorInvalidValue;
+  COLA_SWITCH_N(Nv, return launch_xc2r_multi<N>(njobs, in, out, kfs, tw, s));
+  return cudaSuccess;
 }
 
 cudaError_t fft_xc2r(int Nv, const float2* in, float* out, float kfs, const float2* tw,
                      cudaStream_t s) {
-  COLA_SWITCH_N(Nv, return launch_xc2r<N>(in, out, kfs, tw, s));
-  return cudaSuccess;
+  return fft_xc2r_multi(Nv, 1, &in, &out, &kfs, tw, s);
 }
 
 template <int N>
 static cudaError_t launch_col(float2* data, int axis, bool inv, const float2* tw,
                               cudaStream_t s) {
-  constexpr int TW = Tiles<N>::col1;
-  const int64_t P = half_pitch(N);
-  const int64_t sn = axis == 1 ? P : (int64_t)N * P;
-  const int64_t so = axis == 1 ? (int64_t)N * P : P;
-  const size_t sm = (N + (size_t)N * TW) * sizeof(float2);
-  dim3 grid((N / 2) / TW + 1, N);
+  constexpr int TW = col_tw(N, 1);
+  constexpr size_t sm = col_smem<N, 1>();
+  constexpr int64_t ntiles = col_tiles<N, TW>();
+  const ColGeo<N, TW> geo = axis == 1 ? geo_y<N, TW>() : geo_z<N, TW>();
+  unsigned grid;
   if (inv) {
     auto k = k_col<N, TW, true>;
-    cudaError_t e = prep_smem(k, sm);
+    cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(data, sn, so, tw);
+    k<<<grid, NT, sm, s>>>(OpCol<N, TW, true>{geo, data}, tw, ntiles);
   } else {
     auto k = k_col<N, TW, false>;
-    cudaError_t e = prep_smem(k, sm);
+    cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(data, sn, so, tw);
+    k<<<grid, NT, sm, s>>>(OpCol<N, TW, false>{geo, data}, tw, ntiles);
   }
   return cudaGetLastError();
 }
@@ -494,13 +824,14 @@ cudaError_t fft_col(int Nv, float2* data, int axis, bool inv, const float2* tw, 
 template <int N>
 static cudaError_t launch_yinv2(const float2* in, float2* outp, float2* outd, float kfs,
                                 const float2* tw, cudaStream_t s) {
-  constexpr int TW = Tiles<N>::col2;
-  const size_t sm = (N + (size_t)N * 2 * TW) * sizeof(float2);
+  constexpr int TW = col_tw(N, 2);
+  constexpr size_t sm = col_smem<N, 2>();
+  constexpr int64_t ntiles = col_tiles<N, TW>();
   auto k = k_yinv2<N, TW>;
-  cudaError_t e = prep_smem(k, sm);
+  unsigned grid;
+  cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  dim3 grid((N / 2) / TW + 1, N);
-  k<<<grid, NT, sm, s>>>(in, outp, outd, half_pitch(N), kfs, tw);
+  k<<<grid, NT, sm, s>>>(OpYinv2<N, TW>{geo_y<N, TW>(), in, outp, outd, kfs}, tw, ntiles);
   return cudaGetLastError();
 }
 
@@ -513,19 +844,20 @@ cudaError_t fft_yinv2(int Nv, const float2* in, float2* outp, float2* outd, floa
 template <int N>
 static cudaError_t launch_zsf(const float2* in, float2* dk_out, float2* w_out,
                               const ForceParams& fp, const float2* tw, cudaStream_t s) {
-  constexpr int TW = Tiles<N>::col1;
-  const size_t sm = (N + (size_t)N * TW) * sizeof(float2);
-  dim3 grid((N / 2) / TW + 1, N);
+  constexpr int TW = col_tw(N, 1);
+  constexpr size_t sm = col_smem<N, 1>();
+  constexpr int64_t ntiles = col_tiles<N, TW>();
+  unsigned grid;
   if (fp.model == 1) {
     auto k = k_z_screen_field<N, TW, 1>;
-    cudaError_t e = prep_smem(k, sm);
+    cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(in, dk_out, w_out, half_pitch(N), fp, tw);
+    k<<<grid, NT, sm, s>>>(OpZScreenField<N, TW, 1>{geo_z<N, TW>(), in, dk_out, w_out, fp}, tw, ntiles);
   } else {
     auto k = k_z_screen_field<N, TW, 2>;
-    cudaError_t e = prep_smem(k, sm);
+    cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(in, dk_out, w_out, half_pitch(N), fp, tw);
+    k<<<grid, NT, sm, s>>>(OpZScreenField<N, TW, 2>{geo_z<N, TW>(), in, dk_out, w_out, fp}, tw, ntiles);
   }
   return cudaGetLastError();
 }
@@ -540,19 +872,20 @@ cudaError_t mesh_z_screen_field(int Nv, const float2* in, float2* dk_out, float2
 template <int N>
 static cudaError_t launch_xscreen(const float2* w_in, const float* rho, float2* s_out,
                                   const ForceParams& fp, const float2* tw, cudaStream_t s) {
-  constexpr int TWX = Tiles<N>::rows;
-  const size_t sm = (N + (N / 2 + 1) * (TWX + 1)) * sizeof(float2);
-  const unsigned grid = (unsigned)((int64_t)N * N / TWX);
+  constexpr int TWX = row_tw(N);
+  const size_t sm = row_smem<N>(true);
+  const int64_t ntiles = (int64_t)N * N / TWX;
+  unsigned grid;
   if (fp.model == 1) {
     auto k = k_x_screen<N, TWX, 1>;
-    cudaError_t e = prep_smem(k, sm);
+    cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, half_pitch(N), fp, tw);
+    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, half_pitch(N), fp, tw, ntiles);
   } else {
     auto k = k_x_screen<N, TWX, 2>;
-    cudaError_t e = prep_smem(k, sm);
+    cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, half_pitch(N), fp, tw);
+    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, half_pitch(N), fp, tw, ntiles);
   }
   return cudaGetLastError();
 }
@@ -568,13 +901,15 @@ template <int N, bool SCR, bool KEEP>
 static cudaError_t launch_zforce_t(const float2* in, const float2* dk, float2* phi,
                                    float2* phiz, float2* keep, const ForceParams& fp,
                                    const float2* tw, cudaStream_t s) {
-  constexpr int TW = Tiles<N>::col2;
-  const size_t sm = (N + (size_t)N * 2 * TW) * sizeof(float2);
+  constexpr int TW = col_tw(N, 1);
+  constexpr size_t sm = col_smem<N, 1>() + (size_t)N * TW * sizeof(float2);
+  constexpr int64_t ntiles = col_tiles<N, TW>();
   auto k = k_z_force<N, TW, SCR, KEEP>;
-  cudaError_t e = prep_smem(k, sm);
+  unsigned grid;
+  cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  dim3 grid((N / 2) / TW + 1, N);
-  k<<<grid, NT, sm, s>>>(in, dk, phi, phiz, keep, half_pitch(N), fp, tw);
+  k<<<grid, NT, sm, s>>>(OpZForce<N, TW, SCR, KEEP>{geo_z<N, TW>(), in, dk, phi, phiz, keep, fp}, tw,
+                         ntiles);
   return cudaGetLastError();
 }
 
@@ -599,13 +934,14 @@ template <int N, int PREC>
 static cudaError_t launch_lpt_t(const void* p1, const void* p2, float2* o0, float2* o1,
                                 float2* o2, float2* o3, const LptParams& lp, const float2* tw,
                                 cudaStream_t s) {
-  constexpr int TW = Tiles<N>::col4;
-  const size_t sm = (N + (size_t)N * 4 * TW) * sizeof(float2);
+  constexpr int TW = col_tw(N, 4);
+  constexpr size_t sm = col_smem<N, 4>();
+  constexpr int64_t ntiles = col_tiles<N, TW>();
   auto k = k_lpt_z<N, TW, PREC>;
-  cudaError_t e = prep_smem(k, sm);
+  unsigned grid;
+  cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  dim3 grid((N / 2) / TW + 1, N);
-  k<<<grid, NT, sm, s>>>(p1, p2, o0, o1, o2, o3, half_pitch(N), lp, tw);
+  k<<<grid, NT, sm, s>>>(OpLptZ<N, TW, PREC>{geo_z<N, TW>(), p1, p2, o0, o1, o2, o3, lp}, tw, ntiles);
   return cudaGetLastError();
 }
 
@@ -620,6 +956,7 @@ static cudaError_t launch_lpt(const void* p1, const void* p2, float2* o0, float2
 
 cudaError_t lpt_z(int Nv, const void* phi1, const void* phi2, float2* o0, float2* o1, float2* o2,
                   float2* o3, const LptParams& lp, const float2* tw, cudaStream_t s) {
+  if (Nv > 512) return cudaErrorInvalidValue;  // four double-buffered 4-column tiles exceed shared memory
   COLA_SWITCH_N(Nv, return launch_lpt<N>(phi1, phi2, o0, o1, o2, o3, lp, tw, s));
   return cudaSuccess;
 }
