@@ -225,6 +225,38 @@ const char* cola_profile_stage_name(int32_t i);
 int cola_profile_read(cola_ctx* ctx, double* ms, int64_t* launches, double* bytes_per_launch);
 
 /* ---------------------------------------------------------------------
+ * Allocation-free power spectrum.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they need
+ * a P(k) - cudaFree (and cudaMalloc when a pool grows) synchronises the whole
+ * device and would stall the other streams of a latency-bound serving loop,
+ * a process whose device memory is held by another allocator may get no
+ * fresh memory, and a diagnostic inside a long run must not fail on an
+ * allocation.
+ *
+ * It computes what cola_pk computes (CIC deposit, CIC-deconvolved |delta(k)|^2,
+ * the same bins) for caller-given positions, using only a file-scope device
+ * scratch array of fixed size that every GPU loading the library holds until
+ * the process exits (about 18.6 MB: room for a COLA_PK_NOALLOC_MAX_NMESH^3
+ * mesh, its half spectrum, twiddles and 2000 bins).
+ *   pos    : DEVICE pointer, [n][3] floats, Mpc/h (wrapped periodically), n > 0
+ *   nmesh  : power of two in 32..COLA_PK_NOALLOC_MAX_NMESH; larger meshes are
+ *            rejected with COLA_EINVAL
+ *   Lbox   : box side [Mpc/h];  nbins: 1..2000
+ *   k, pk, nmodes : HOST arrays of nbins entries (any may be NULL), as cola_pk
+ *   stream : cudaStream_t for the work; the call synchronises it.
+ * No cudaMalloc, cudaFree or allocating library routine is called.  The
+ * first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the scratch and
+ * it keeps the last call's contents (each call clears what must start at
+ * zero), so calls whose device work could overlap race and must not be
+ * issued.  Errors: COLA_EINVAL, COLA_ECUDA; message in cola_last_error(NULL).
+ * --------------------------------------------------------------------- */
+#define COLA_PK_NOALLOC_MAX_NMESH 128
+int cola_pk_noalloc(const float* pos, int64_t n, int32_t nmesh, double Lbox, int32_t nbins,
+                    double* k, double* pk, int64_t* nmodes, void* stream);
+
+/* ---------------------------------------------------------------------
  * Host-only helpers (no GPU needed): the double-precision quantities the
  * library computes on the host and uploads.  Same validation as cola_init /
  * cola_set_model.

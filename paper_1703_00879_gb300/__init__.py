@@ -72,6 +72,8 @@ _SIGS = {
     "cola_profile_nstages": (ctypes.c_int32, []),
     "cola_profile_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
     "cola_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
+    "cola_pk_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                       _P, _P, _P, _P]),
     "cola_host_growth": (ctypes.c_int, [ctypes.POINTER(cola_config), ctypes.POINTER(cola_model), _P, _P]),
     "cola_host_timesteps": (ctypes.c_int, [ctypes.POINTER(cola_config), _P]),
 }
@@ -123,6 +125,25 @@ def cola_host_growth(run):
     k = np.zeros(run.nk_table)
     _check(lib().cola_host_growth(ctypes.byref(cfg), ctypes.byref(mdl), out.ctypes.data, k.ctypes.data))
     return out, k
+
+
+COLA_PK_NOALLOC_MAX_NMESH = 128
+
+
+def cola_pk_noalloc(pos_ptr: int, n: int, nmesh: int, Lbox: float, nbins: int, stream_ptr: int = 0):
+    """P(k) of n device positions ([n][3] float32 at pos_ptr) without device allocation.
+
+    For callers that cannot allocate device memory at that point (see
+    include/cola.h); scratch is the library's fixed static device array, so
+    nmesh is limited to COLA_PK_NOALLOC_MAX_NMESH and calls must not overlap.
+    Returns (k, P(k), nmodes) as numpy arrays.
+    """
+    k = np.empty(nbins)
+    pk = np.empty(nbins)
+    nm = np.empty(nbins, np.int64)
+    _check(lib().cola_pk_noalloc(_P(pos_ptr), int(n), int(nmesh), float(Lbox), int(nbins),
+                                 k.ctypes.data, pk.ctypes.data, nm.ctypes.data, _P(stream_ptr)))
+    return k, pk, nm
 
 
 def cola_host_timesteps(run):

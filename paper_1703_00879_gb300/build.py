@@ -11,7 +11,8 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libcola.so")
-SOURCES = ["kernels_fft.cu", "kernels_pm.cu", "kernels_ic.cu", "host_cosmo.cpp", "cola_api.cpp"]
+SOURCES = ["kernels_fft.cu", "kernels_pm.cu", "kernels_ic.cu", "host_cosmo.cpp", "cola_api.cpp",
+           "pk_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -17,6 +17,8 @@ namespace {
 thread_local std::string g_err;
 }
 
+void cola::set_context_free_error(const std::string& msg) { g_err = msg; }
+
 struct cola_ctx {
   cola_config cfg{};
   cola_model model{};

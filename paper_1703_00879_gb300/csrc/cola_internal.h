@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace cola {
 
 // Row pitch (in complex elements) of every half spectrum: N/2+1 rounded up to
@@ -125,5 +127,8 @@ cudaError_t half_unpack(int N, const float2* padded, float2* dense, cudaStream_t
 cudaError_t seed_quantise(int N, const float2* src, void* dst, int prec, float inv_scale,
                           cudaStream_t s);
 cudaError_t seed_absmax(int N, const float2* src, float* out_absmax, cudaStream_t s);
+
+// Sets the message cola_last_error(NULL) returns (calling thread).
+void set_context_free_error(const std::string& msg);
 
 }  // namespace cola
