@@ -345,6 +345,89 @@ def bench_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------- ensemble and serving
+def _run_one(pkg, run):
+    with pkg.Simulation(run) as sim:
+        sim.run_to_end()
+        return sim.pk()
+
+
+def bench_ensemble(args):
+    """256 sims of 64^3 / 128^3, models cycled: batched graph launches vs one at a time."""
+    import torch
+    import paper_1703_00879_gb300 as pkg
+    n = args.ensemble_size
+    runs = [W.ensemble_run(seed) for seed in range(n)]
+    for r in runs[:6]:          # warm the library (kernel attributes, growth-table cache)
+        _run_one(pkg, r.with_(nsteps=r.nsteps))
+    torch.cuda.synchronize()
+    # one at a time: a bounded prefix, as a rate
+    n1 = min(n, args.ensemble_solo)
+    t0 = time.perf_counter()
+    for r in runs[:n1]:
+        _run_one(pkg, r)
+    torch.cuda.synchronize()
+    t_solo = time.perf_counter() - t0
+    solo_rate = n1 / t_solo * 3600.0
+    # batched: contexts created on a pool of streams (their ICs overlap on the
+    # device), then every sim advanced by one graph launch per step
+    t0 = time.perf_counter()
+    pool = [torch.cuda.Stream() for _ in range(min(32, n))]
+    sims = []
+    for i, r in enumerate(runs):
+        with torch.cuda.stream(pool[i % len(pool)]):
+            sims.append(pkg.Simulation(r, stream=pool[i % len(pool)]))
+    torch.cuda.synchronize()
+    t_init = time.perf_counter() - t0
+    b = pkg.Batch(sims)
+    chains, cap = b.autotune(max_steps=args.autotune_steps)
+    b.step(-1)
+    torch.cuda.synchronize()
+    t_steps = time.perf_counter() - t0 - t_init
+    for s in sims:
+        s.pk()
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    b.close()
+    for s in sims:
+        s.close()
+    out = {"metric": "ensemble sims/hour", "unit": "sims/hour", "value": n / t_batch * 3600.0,
+           "one_at_a_time_sims_per_hour": solo_rate, "speedup_vs_one_at_a_time": (n / t_batch * 3600.0) / solo_rate,
+           "n_sims": n, "steps": runs[0].nsteps, "config": {"workload": "ensemble 64^3 particles / 128^3 mesh, "
+           "L=128 Mpc/h, 20 steps, models cycled over LCDM, F6, F5, F4, nDGP rcH0=1, nDGP rcH0=5, seeds 0..%d" % (n - 1)},
+           "autotune": {"chains": chains, "grid_cap": cap, "steps_used": args.autotune_steps},
+           "seconds": {"init_and_ic": t_init, "steps": t_steps, "total": t_batch, "one_at_a_time_prefix": t_solo,
+                       "one_at_a_time_sims": n1}}
+    print(json.dumps(out), flush=True)
+
+
+def bench_serve(args):
+    """Poisson arrivals (mean 20/s) of mixed sims under an 80 GB HBM budget: p50/p99 latency, sims/hour."""
+    import torch
+    import paper_1703_00879_gb300 as pkg
+    from paper_1703_00879_gb300.serve import Server
+    reqs = W.serving_requests(args.serve_requests, rate_hz=20.0, seed=0)
+    for _, r in reqs[:8]:
+        _run_one(pkg, r.with_(nsteps=2))
+    torch.cuda.synchronize()
+    st = Server(80 * 10**9, max_slots=64).run(reqs, realtime=True)
+    summ = st.summary()
+    # one at a time over the same requests (no overlap; arrivals ignored), bounded prefix
+    n1 = min(len(reqs), args.serve_solo)
+    t0 = time.perf_counter()
+    for _, r in reqs[:n1]:
+        _run_one(pkg, r)
+    torch.cuda.synchronize()
+    solo_rate = n1 / (time.perf_counter() - t0) * 3600.0
+    out = {"metric": "served sims/hour", "unit": "sims/hour", "value": summ["sims_per_hour"],
+           "p50_latency_s": summ["p50_latency_s"], "p99_latency_s": summ["p99_latency_s"],
+           "one_at_a_time_sims_per_hour": solo_rate, "speedup_vs_one_at_a_time": summ["sims_per_hour"] / solo_rate,
+           "requests": len(reqs), "peak_active": summ["peak_active"], "peak_bytes": summ["peak_bytes"],
+           "config": {"workload": "Poisson arrivals mean 20/s, particles^(1/3) in {32,64,128,256}, mesh 2x, "
+                      "L = 2 Np Mpc/h, 10-30 steps, models from the ensemble set, 80 GB HBM budget"}}
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,7 +437,18 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="big")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ensemble", action="store_true", help="batched ensemble benchmark instead")
+    ap.add_argument("--ensemble-size", type=int, default=256)
+    ap.add_argument("--ensemble-solo", type=int, default=48)
+    ap.add_argument("--autotune-steps", type=int, default=6)
+    ap.add_argument("--serve", action="store_true", help="serving benchmark instead")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-solo", type=int, default=60)
     args = ap.parse_args(argv)
+    if args.ensemble:
+        return bench_ensemble(args)
+    if args.serve:
+        return bench_serve(args)
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -206,6 +206,31 @@ int cola_force_from_density(cola_ctx* ctx, const float* rho, double a, float* fo
                             int32_t where);
 
 /* ---------------------------------------------------------------------
+ * Batches: many simulations of one shape advanced together (ensembles).
+ * --------------------------------------------------------------------- */
+typedef struct cola_batch cola_batch;
+
+/* Groups n contexts that completed cola_ic, have equal nsteps and steps done,
+ * and live on the current device.  Each step of cola_batch_step is ONE CUDA
+ * graph launch on `stream` that advances every context by one step.  The
+ * graph of step k is captured on first use from `chains` forked streams
+ * (chain c advances contexts c, c + chains, ... in turn, chains run
+ * concurrently), instantiated and kept; chains <= 0 picks min(n, 32).
+ * Contexts whose own stream differs from `stream` get ordered behind each
+ * batch step.  The batch borrows the contexts (free the batch before them).
+ * Errors: COLA_EINVAL, COLA_ESTATE, COLA_ECUDA (message via cola_last_error(NULL)). */
+int cola_batch_create(cola_ctx* const* ctxs, int32_t n, int32_t chains, void* stream,
+                      cola_batch** out);
+int cola_batch_step(cola_batch* b, int32_t nsteps);  /* -1: to the last step */
+/* Autotuner: times up to max_steps real steps (they advance the batch) with
+ * different (chains, grid cap) candidates - the grid cap bounds the
+ * persistent grid of every FFT pass so that concurrent simulations share the
+ * SMs - and keeps the fastest for later steps. */
+int cola_batch_autotune(cola_batch* b, int32_t max_steps, int32_t* chains_out, int32_t* cap_out);
+int32_t cola_batch_steps_done(const cola_batch* b);
+void cola_batch_free(cola_batch* b);
+
+/* ---------------------------------------------------------------------
  * Per-stage device timing: CUDA events recorded on the context's stream
  * around each launch group of cola_step (and of cola_ic's force evaluation).
  * --------------------------------------------------------------------- */
@@ -270,6 +295,10 @@ int cola_pk_noalloc(const float* pos, int64_t n, int32_t nmesh, double Lbox, int
  * [nk_table] wavenumbers in h/Mpc. */
 int cola_host_growth(const cola_config* cfg, const cola_model* model, double* out,
                      double* k_nodes);
+
+/* Device bytes cola_init would allocate for cfg (for admission control);
+ * -1 if cfg is invalid. */
+int64_t cola_device_bytes(const cola_config* cfg);
 
 /* Time integrals of the kick-drift-kick step (Sec. 2; dtau = dt/a^2):
  * out: [nsteps][4] doubles = a_{n+1}, Delta tau(a_n, a_{n+1/2}),

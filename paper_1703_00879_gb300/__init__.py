@@ -68,6 +68,11 @@ _SIGS = {
     "cola_fft": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
     "cola_cic_deposit": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32]),
     "cola_force_from_density": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.c_int32]),
+    "cola_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.POINTER(_P)]),
+    "cola_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cola_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "cola_batch_steps_done": (ctypes.c_int32, [_P]),
+    "cola_batch_free": (None, [_P]),
     "cola_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cola_profile_nstages": (ctypes.c_int32, []),
     "cola_profile_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
@@ -76,6 +81,7 @@ _SIGS = {
                                        _P, _P, _P, _P]),
     "cola_host_growth": (ctypes.c_int, [ctypes.POINTER(cola_config), ctypes.POINTER(cola_model), _P, _P]),
     "cola_host_timesteps": (ctypes.c_int, [ctypes.POINTER(cola_config), _P]),
+    "cola_device_bytes": (ctypes.c_int64, [ctypes.POINTER(cola_config)]),
 }
 
 
@@ -144,6 +150,13 @@ def cola_pk_noalloc(pos_ptr: int, n: int, nmesh: int, Lbox: float, nbins: int, s
     _check(lib().cola_pk_noalloc(_P(pos_ptr), int(n), int(nmesh), float(Lbox), int(nbins),
                                  k.ctypes.data, pk.ctypes.data, nm.ctypes.data, _P(stream_ptr)))
     return k, pk, nm
+
+
+def cola_device_bytes(run, seed_precision: int = 0) -> int:
+    """Device bytes one context of this run needs (no GPU needed)."""
+    cfg = make_config(run)
+    cfg.seed_precision = int(seed_precision)
+    return int(lib().cola_device_bytes(ctypes.byref(cfg)))
 
 
 def cola_host_timesteps(run):
@@ -312,3 +325,47 @@ class Simulation:
         _check(lib().cola_force_from_density(self.ctx, r.ctypes.data, float(a), out.ctypes.data, COLA_HOST),
                self.ctx)
         return out
+
+
+class Batch:
+    """cola_batch over Simulations of one shape: one CUDA graph launch per step for all of them."""
+
+    def __init__(self, sims, chains: int = 0, stream=None):
+        import torch
+        self.sims = list(sims)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (_P * len(self.sims))(*[s.ctx for s in self.sims])
+        h = _P()
+        _check(lib().cola_batch_create(arr, len(self.sims), int(chains), _P(self.stream.cuda_stream),
+                                       ctypes.byref(h)))
+        self.h = h
+
+    def step(self, n: int = 1):
+        _check(lib().cola_batch_step(self.h, int(n)))
+
+    def autotune(self, max_steps: int = 4):
+        c = ctypes.c_int32()
+        k = ctypes.c_int32()
+        _check(lib().cola_batch_autotune(self.h, int(max_steps), ctypes.byref(c), ctypes.byref(k)))
+        return int(c.value), int(k.value)
+
+    @property
+    def steps_done(self) -> int:
+        return lib().cola_batch_steps_done(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cola_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

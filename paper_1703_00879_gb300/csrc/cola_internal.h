@@ -128,6 +128,10 @@ cudaError_t seed_quantise(int N, const float2* src, void* dst, int prec, float i
                           cudaStream_t s);
 cudaError_t seed_absmax(int N, const float2* src, float* out_absmax, cudaStream_t s);
 
+// Caps the persistent grid of the FFT-pass kernels launched by the calling
+// thread (0 = no cap: resident CTAs x SMs).
+void set_grid_cap(int max_ctas);
+
 // Sets the message cola_last_error(NULL) returns (calling thread).
 void set_context_free_error(const std::string& msg);
 

@@ -25,6 +25,10 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include "cola_internal.h"
 #include "fft.cuh"
 
@@ -62,17 +66,45 @@ int sm_count() {
   return n;
 }
 
+thread_local int g_grid_cap = 0;  // 0: no cap (see set_grid_cap)
+
+struct KernelInfo {
+  const void* fn;
+  size_t smem;
+  int per_sm;
+};
+std::mutex g_kinfo_mu;
+std::vector<KernelInfo> g_kinfo;
+
+// Sets the shared-memory limit of a kernel once and caches its resident CTAs per SM.
 template <class K>
-cudaError_t prep(K kernel, size_t smem, int64_t ntiles, unsigned& grid) {
+cudaError_t resident_ctas(K kernel, size_t smem, int& per_sm) {
+  std::lock_guard<std::mutex> lk(g_kinfo_mu);
+  for (const KernelInfo& k : g_kinfo)
+    if (k.fn == (const void*)kernel && k.smem == smem) {
+      per_sm = k.per_sm;
+      return cudaSuccess;
+    }
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem);
   if (e != cudaSuccess) return e;
+  g_kinfo.push_back({(const void*)kernel, smem, per_sm});
+  return cudaSuccess;
+}
+
+// Persistent grid: resident CTAs x SMs, at most one CTA per tile, at most the
+// calling thread's grid cap (used when many small simulations run concurrently).
+template <class K>
+cudaError_t prep(K kernel, size_t smem, int64_t ntiles, unsigned& grid) {
+  int per_sm = 0;
+  cudaError_t e = resident_ctas(kernel, smem, per_sm);
+  if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int64_t g = std::min<int64_t>(ntiles, (int64_t)per_sm * sm_count());
+  int64_t g = std::min<int64_t>(ntiles, (int64_t)per_sm * sm_count());
+  if (g_grid_cap > 0) g = std::min<int64_t>(g, g_grid_cap);
   grid = (unsigned)std::max<int64_t>(g, 1);
   return cudaSuccess;
 }
@@ -729,6 +761,8 @@ constexpr int64_t col_tiles() {
 }
 
 }  // namespace
+
+void set_grid_cap(int max_ctas) { g_grid_cap = max_ctas > 0 ? max_ctas : 0; }
 
 #define COLA_SWITCH_N(NVAL, ...)                 \
   switch (NVAL) {                                \

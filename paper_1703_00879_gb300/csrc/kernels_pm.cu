@@ -42,6 +42,23 @@ __device__ __forceinline__ Cic cic_setup(const PartParams& pp, int ix, int iy, i
   return c;
 }
 
+// Adds a0 at row[i0] and a1 at row[i1] (i1 = i0 + 1 unless the row wraps).
+// Adjacent cells inside one 16-byte group go out as a single vector atomic
+// (red.global.add.v4.f32, zeros in the other lanes).
+__device__ __forceinline__ void row_add(float* __restrict__ row, int i0, int i1, float a0, float a1) {
+  const int q = i0 & 3;
+  if (i1 == i0 + 1 && q < 3) {
+    float4* p4 = reinterpret_cast<float4*>(row + (i0 - q));
+    const float4 v = q == 0 ? make_float4(a0, a1, 0.f, 0.f)
+                   : q == 1 ? make_float4(0.f, a0, a1, 0.f)
+                            : make_float4(0.f, 0.f, a0, a1);
+    atomicAdd(p4, v);
+  } else {
+    atomicAdd(row + i0, a0);
+    atomicAdd(row + i1, a1);
+  }
+}
+
 __device__ __forceinline__ void cic_deposit(float* __restrict__ rho, int Nm, const Cic& c) {
   const float wx0 = 1.f - c.f[0], wx1 = c.f[0];
   const float wy0 = 1.f - c.f[1], wy1 = c.f[1];
@@ -49,14 +66,11 @@ __device__ __forceinline__ void cic_deposit(float* __restrict__ rho, int Nm, con
   const int64_t z0 = (int64_t)c.i0[2] * Nm, z1 = (int64_t)c.i1[2] * Nm;
   const int64_t r00 = (z0 + c.i0[1]) * Nm, r01 = (z0 + c.i1[1]) * Nm;
   const int64_t r10 = (z1 + c.i0[1]) * Nm, r11 = (z1 + c.i1[1]) * Nm;
-  atomicAdd(rho + r00 + c.i0[0], wz0 * wy0 * wx0);
-  atomicAdd(rho + r00 + c.i1[0], wz0 * wy0 * wx1);
-  atomicAdd(rho + r01 + c.i0[0], wz0 * wy1 * wx0);
-  atomicAdd(rho + r01 + c.i1[0], wz0 * wy1 * wx1);
-  atomicAdd(rho + r10 + c.i0[0], wz1 * wy0 * wx0);
-  atomicAdd(rho + r10 + c.i1[0], wz1 * wy0 * wx1);
-  atomicAdd(rho + r11 + c.i0[0], wz1 * wy1 * wx0);
-  atomicAdd(rho + r11 + c.i1[0], wz1 * wy1 * wx1);
+  const float w00 = wz0 * wy0, w01 = wz0 * wy1, w10 = wz1 * wy0, w11 = wz1 * wy1;
+  row_add(rho + r00, c.i0[0], c.i1[0], w00 * wx0, w00 * wx1);
+  row_add(rho + r01, c.i0[0], c.i1[0], w01 * wx0, w01 * wx1);
+  row_add(rho + r10, c.i0[0], c.i1[0], w10 * wx0, w10 * wx1);
+  row_add(rho + r11, c.i0[0], c.i1[0], w11 * wx0, w11 * wx1);
 }
 
 __device__ __forceinline__ float cic_interp(const float* __restrict__ F, int Nm, const Cic& c) {
@@ -118,7 +132,11 @@ __global__ void __launch_bounds__(NTP) k_drift_deposit(
   cic_deposit(rho, pp.Nm, cic_setup(pp, ix, iy, iz, nx, ny, nz));
 }
 
-// Sec. 2 kick: acc = g(x) - A_LPT(q), delta_v += acc dtk.
+// Sec. 2 kick: acc = g(x) - A_LPT(q), delta_v += acc dtk.  Each thread handles
+// PPT particles (p, p + NTP, ...) of its block so that the dependent chains
+// (displacement load -> cell index -> 24 mesh loads) of different particles overlap.
+constexpr int PPT = 2;
+
 __global__ void __launch_bounds__(NTP) k_gather_kick(
     PartParams pp, const float* __restrict__ sx, const float* __restrict__ sy,
     const float* __restrict__ sz, float* __restrict__ vx, float* __restrict__ vy,
@@ -126,20 +144,43 @@ __global__ void __launch_bounds__(NTP) k_gather_kick(
     float* __restrict__ az, const float* __restrict__ Ax, const float* __restrict__ Ay,
     const float* __restrict__ Az, const float* __restrict__ Fx, const float* __restrict__ Fy,
     const float* __restrict__ Fz, float dtk, int64_t P) {
-  const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
-  if (p >= P) return;
-  int ix, iy, iz;
-  lattice(pp, p, ix, iy, iz);
-  const Cic c = cic_setup(pp, ix, iy, iz, sx[p], sy[p], sz[p]);
-  const float gx = cic_interp(Fx, pp.Nm, c) - Ax[p];
-  const float gy = cic_interp(Fy, pp.Nm, c) - Ay[p];
-  const float gz = cic_interp(Fz, pp.Nm, c) - Az[p];
-  ax[p] = gx;
-  ay[p] = gy;
-  az[p] = gz;
-  vx[p] += gx * dtk;
-  vy[p] += gy * dtk;
-  vz[p] += gz * dtk;
+  const int64_t p0 = (int64_t)blockIdx.x * NTP * PPT + threadIdx.x;
+  float px[PPT], py[PPT], pz[PPT];
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) {
+    const int64_t p = p0 + u * NTP;
+    if (p < P) {
+      px[u] = sx[p];
+      py[u] = sy[p];
+      pz[u] = sz[p];
+    }
+  }
+  float gx[PPT], gy[PPT], gz[PPT];
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) {
+    const int64_t p = p0 + u * NTP;
+    if (p < P) {
+      int ix, iy, iz;
+      lattice(pp, p, ix, iy, iz);
+      const Cic c = cic_setup(pp, ix, iy, iz, px[u], py[u], pz[u]);
+      gx[u] = cic_interp(Fx, pp.Nm, c);
+      gy[u] = cic_interp(Fy, pp.Nm, c);
+      gz[u] = cic_interp(Fz, pp.Nm, c);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) {
+    const int64_t p = p0 + u * NTP;
+    if (p < P) {
+      const float ex = gx[u] - Ax[p], ey = gy[u] - Ay[p], ez = gz[u] - Az[p];
+      ax[p] = ex;
+      ay[p] = ey;
+      az[p] = ez;
+      vx[p] += ex * dtk;
+      vy[p] += ey * dtk;
+      vz[p] += ez * dtk;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(NTP) k_snapshot(
@@ -258,8 +299,8 @@ cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float*
                              float* ay, float* az, const float* Ax, const float* Ay,
                              const float* Az, const float* Fx, const float* Fy, const float* Fz,
                              float dtk, int64_t P, cudaStream_t s) {
-  k_gather_kick<<<blocks_for(P), NTP, 0, s>>>(pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az,
-                                              Fx, Fy, Fz, dtk, P);
+  k_gather_kick<<<(unsigned)((P + NTP * PPT - 1) / (NTP * PPT)), NTP, 0, s>>>(
+      pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, Fx, Fy, Fz, dtk, P);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,81 @@
+"""Batched ensembles (one CUDA graph launch per step) and the serving loop on the GPU.
+
+A simulation's result must not depend on whether it runs alone, in a batch,
+or in the serving mix: displacements within 1e-4 of a mesh cell of the solo
+run (the parity tolerance; only the order of the float atomics differs) and
+P(k) within 1e-4.
+"""
+import numpy as np
+import pytest
+
+from workloads import ENSEMBLE_MODELS, ensemble_run
+
+pytestmark = pytest.mark.gpu
+
+
+def _runs(n, Np=32, Nmesh=64, steps=4):
+    return [ensemble_run(seed, Np=Np, Nmesh=Nmesh, Lbox=2.0 * Np, nsteps=steps) for seed in range(n)]
+
+
+def _solo(pkg, run):
+    with pkg.Simulation(run) as s:
+        s.run_to_end()
+        return s.export(pkg.COLA_F_DISP), s.pk()
+
+
+@pytest.mark.parametrize("chains", [1, 3, 0])
+def test_batch_equals_solo(chains):
+    import paper_1703_00879_gb300 as pkg
+    runs = _runs(len(ENSEMBLE_MODELS))
+    solo = [_solo(pkg, r) for r in runs]
+    sims = [pkg.Simulation(r) for r in runs]
+    with pkg.Batch(sims, chains=chains) as b:
+        b.step(-1)
+        assert b.steps_done == runs[0].nsteps
+    for r, s, (d0, _) in zip(runs, sims, solo):
+        d = s.export(pkg.COLA_F_DISP)
+        assert s.steps_done == r.nsteps
+        assert np.max(np.abs(d - d0)) / (r.Lbox / r.Nmesh) <= 1e-4
+        s.close()
+
+
+def test_batch_autotune_keeps_results():
+    import paper_1703_00879_gb300 as pkg
+    runs = _runs(8, steps=6)
+    solo = [_solo(pkg, r) for r in runs]
+    sims = [pkg.Simulation(r) for r in runs]
+    with pkg.Batch(sims) as b:
+        chains, cap = b.autotune(max_steps=3)
+        assert 1 <= chains <= 8 and cap >= 0
+        b.step(-1)
+    for r, s, (d0, _) in zip(runs, sims, solo):
+        assert np.max(np.abs(s.export(pkg.COLA_F_DISP) - d0)) / (r.Lbox / r.Nmesh) <= 1e-4
+        s.close()
+
+
+def test_batch_rejects_mismatched_steps():
+    import paper_1703_00879_gb300 as pkg
+    runs = _runs(2)
+    a, b = pkg.Simulation(runs[0]), pkg.Simulation(runs[1])
+    a.step(1)
+    with pytest.raises(pkg.ColaError):
+        pkg.Batch([a, b])
+    a.close()
+    b.close()
+
+
+def test_serving_results_equal_solo_runs():
+    import paper_1703_00879_gb300 as pkg
+    from paper_1703_00879_gb300.serve import Server
+    from workloads import serving_requests
+    reqs = serving_requests(10, rate_hz=200.0, seed=3, sizes=(32, 64), steps=(3, 5))
+    budget = 3 * max(pkg.cola_device_bytes(r) for _, r in reqs)   # forces staggered admission
+    st = Server(budget, max_slots=4).run(reqs, realtime=True)
+    assert len(st.results) == 10 and st.peak_bytes <= budget and st.peak_active >= 2
+    for res in st.results:
+        _, (k, P, nm) = _solo(pkg, res.run)
+        ok = nm > 0
+        assert np.array_equal(res.nmodes, nm)
+        assert np.max(np.abs(res.pk[ok] / P[ok] - 1)) <= 1e-4
+    s = st.summary()
+    assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
