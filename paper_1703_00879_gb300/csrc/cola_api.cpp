@@ -60,6 +60,12 @@ struct cola_ctx {
   float* scratch = nullptr;
   EHParams eh{};
   double Dratio = 1.0;
+  // device-resident step state: current step and per-step parameters, so the
+  // launch sequence of a step does not depend on which step it is
+  int* dstep = nullptr;
+  ForceParams* dfp = nullptr;  // [nsteps]: force parameters at a_{n+1}
+  float* ddt = nullptr;        // [nsteps][3]: half kick, drift, half kick
+  int h_step = 0;              // staging for uploads of the step counter
   // per-stage event timing
   bool prof = false;
   struct Stage {
@@ -82,7 +88,7 @@ struct cola_batch {
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;           // one per chain stream (owned)
   int chains = 1, cap = 0, step = 0;
-  std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (step, chains, cap)
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (chains, cap): one graph serves every step
   std::string err;
 };
 
@@ -346,9 +352,11 @@ int c2r3(cola_ctx* ctx, int N, float2* in, float* out, const float2* tw) {
 }
 
 // Sec. 4.1 / App. A: LPT fields at the lattice from the k-space seeds and one table row.
-int run_lpt(cola_ctx* ctx, const float4* row) {
+int run_lpt(cola_ctx* ctx, const float4* table, int row0, const int* step) {
   LptParams lp{};
-  lp.tab = row;
+  lp.tab = table;
+  lp.row0 = row0;
+  lp.step = step;
   lp.lnk0 = (float)ctx->lnk0;
   lp.inv_dlnk = (float)(1.0 / ctx->dlnk);
   lp.nk = ctx->nk;
@@ -386,8 +394,12 @@ int run_lpt(cola_ctx* ctx, const float4* row) {
 }
 
 // App. B: mesh force -grad(Phi_N + phi) at scale factor a from the density in ctx->rho.
-int run_force(cola_ctx* ctx, double a) {
-  const ForceParams fp = force_params(ctx, a);
+int run_force(cola_ctx* ctx, double a, bool device_params = false) {
+  ForceParams fp = force_params(ctx, a);
+  if (device_params) {  // the values come from dfp[*dstep]; fp's model flags decide the kernels
+    fp.src = ctx->dfp;
+    fp.step = ctx->dstep;
+  }
   const int N = ctx->Nm;
   auto st = ctx->st;
   const float2* tw = ctx->tw_nm;
@@ -462,7 +474,7 @@ int finish_ic(cola_ctx* ctx) {
                        ctx->st));
     }
   }
-  CHECK_RC(run_lpt(ctx, ctx->tab));
+  CHECK_RC(run_lpt(ctx, ctx->tab, 0, nullptr));
   CK(ic_particles(ctx->P, ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->s[0], ctx->s[1], ctx->s[2],
                   ctx->v[0], ctx->v[1], ctx->v[2], ctx->st));
   const PartParams pp = part_params(ctx);
@@ -471,7 +483,9 @@ int finish_ic(cola_ctx* ctx) {
   CHECK_RC(run_force(ctx, ctx->a[0]));
   CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                       ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[3], ctx->lr[4], ctx->lr[5],
-                      ctx->F[0], ctx->F[1], ctx->F[2], 0.f, ctx->P, ctx->st));
+                      ctx->F[0], ctx->F[1], ctx->F[2], StepDt{nullptr, nullptr, 0.f, 0.f}, ctx->P,
+                      ctx->st));
+  CK(cudaMemsetAsync(ctx->dstep, 0, sizeof(int), ctx->st));
   ctx->step = 0;
   ctx->ic_done = true;
   return COLA_OK;
@@ -503,26 +517,29 @@ int export_half(cola_ctx* ctx, int N, const float2* padded, float2* tmp, void* d
 }
 
 // Enqueues step n (a_n -> a_{n+1}) of Sec. 2 on ctx->st without touching ctx->step.
+// Enqueues the next step (from the device step counter) on ctx->st; the
+// launch sequence is the same for every step.  n is the host's step index,
+// used only to pick the model branch (constant over the run).
 int enqueue_step(cola_ctx* ctx, int n) {
   const PartParams pp = part_params(ctx);
   const double Pb = (double)ctx->P, Mb = (double)ctx->M;
-  CHECK_RC(run_lpt(ctx, ctx->tab + (size_t)(n + 1) * ctx->nk));
+  const StepDt dt{ctx->ddt, ctx->dstep, 0.f, 0.f};
+  CHECK_RC(run_lpt(ctx, ctx->tab, 1, ctx->dstep));
   cudaEvent_t e = prof_begin(ctx);
   CK(cudaMemsetAsync(ctx->rho, 0, ctx->M * sizeof(float), ctx->st));
   prof_end(ctx, ST_RHO_ZERO, e, 1, 4.0 * Mb);
   e = prof_begin(ctx);
   CK(part_drift_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                         ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[0], ctx->lr[1],
-                        ctx->lr[2], ctx->rho, (float)ctx->dtk1[n], (float)ctx->dtd[n], ctx->P,
-                        ctx->st));
+                        ctx->lr[2], ctx->rho, dt, ctx->P, ctx->st));
   prof_end(ctx, ST_DRIFT_DEPOSIT, e, 1, 72.0 * Pb + 8.0 * Mb);
-  CHECK_RC(run_force(ctx, ctx->a[n + 1]));
+  CHECK_RC(run_force(ctx, ctx->a[n + 1], true));
   e = prof_begin(ctx);
   CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                       ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[3], ctx->lr[4],
-                      ctx->lr[5], ctx->F[0], ctx->F[1], ctx->F[2], (float)ctx->dtk2[n], ctx->P,
-                      ctx->st));
+                      ctx->lr[5], ctx->F[0], ctx->F[1], ctx->F[2], dt, ctx->P, ctx->st));
   prof_end(ctx, ST_GATHER_KICK, e, 1, 60.0 * Pb + 12.0 * Mb);
+  CK(step_advance(ctx->dstep, ctx->st));
   return COLA_OK;
 }
 
@@ -597,6 +614,9 @@ int cola_init(const cola_config* cfg, cola_alloc_fn alloc, cola_free_fn free_fn,
   if (!rc) rc = alloc_buf(ctx, &ctx->tab, (size_t)(cfg->nsteps + 1) * cfg->nk_table);
   if (!rc) rc = alloc_buf(ctx, &ctx->vtab, (size_t)(cfg->nsteps + 1) * cfg->nk_table);
   if (!rc) rc = alloc_buf(ctx, &ctx->pk_acc, 3 * kMaxBins);
+  if (!rc) rc = alloc_buf(ctx, &ctx->dstep, 4);
+  if (!rc) rc = alloc_buf(ctx, &ctx->dfp, (size_t)cfg->nsteps);
+  if (!rc) rc = alloc_buf(ctx, &ctx->ddt, (size_t)3 * cfg->nsteps);
   if (!rc) rc = alloc_buf(ctx, &ctx->scratch, 64);
   if (!rc) rc = upload_twiddles(ctx, ctx->Np, &ctx->tw_np);
   if (!rc) rc = upload_twiddles(ctx, ctx->Nm, &ctx->tw_nm);
@@ -655,8 +675,18 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
   }
   CK(cudaMemcpyAsync(ctx->tab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->vtab, vtab.data(), vtab.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->st));
+  ctx->model_set = true;  // force_params below reads the model
+  std::vector<ForceParams> hfp(ns);
+  std::vector<float> hdt(3 * (size_t)ns);
+  for (int n = 0; n < ns; ++n) {
+    hfp[n] = force_params(ctx, ctx->a[n + 1]);
+    hdt[3 * n + 0] = (float)ctx->dtk1[n];
+    hdt[3 * n + 1] = (float)ctx->dtd[n];
+    hdt[3 * n + 2] = (float)ctx->dtk2[n];
+  }
+  CK(cudaMemcpyAsync(ctx->dfp, hfp.data(), hfp.size() * sizeof(ForceParams), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->ddt, hdt.data(), hdt.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
-  ctx->model_set = true;
   return COLA_OK;
 }
 
@@ -728,7 +758,7 @@ int cola_snapshot(cola_ctx* ctx, float* pos, float* vel, int32_t where) {
   if (where != COLA_HOST && where != COLA_DEVICE) return fail(ctx, COLA_EINVAL, "bad where");
   if (!pos && !vel) return COLA_OK;
   const size_t bytes = (size_t)ctx->P * 3 * sizeof(float);
-  if (vel) CHECK_RC(run_lpt(ctx, ctx->vtab + (size_t)ctx->step * ctx->nk));
+  if (vel) CHECK_RC(run_lpt(ctx, ctx->vtab, ctx->step, nullptr));
   const PartParams pp = part_params(ctx);
   const float vscale = (float)(100.0 / ctx->a[ctx->step]);
   if (where == COLA_DEVICE) {
@@ -852,6 +882,8 @@ int cola_import_state(cola_ctx* ctx, const float* disp, const float* dv, const f
   for (int q = 0; q < 3; ++q)
     for (int c = 0; c < 3; ++c)
       CHECK_RC(copy_in(ctx, dstv[q][c], reinterpret_cast<const char*>(src[q]) + c * pb, pb, where));
+  ctx->h_step = steps_done;
+  CHECK_RC(copy_in(ctx, ctx->dstep, &ctx->h_step, sizeof(int), COLA_HOST));
   ctx->step = steps_done;
   return COLA_OK;
 }
@@ -931,7 +963,9 @@ static int bfail(cola_batch* b, int code, const std::string& m) {
     if (e_ != cudaSuccess) return bfail(b, COLA_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-// Captures step n of every context: chain c advances contexts c, c + C, ... in turn.
+// Captures one step of every context (the step index comes from each context's
+// device counter, so the graph serves every step): chain c advances contexts
+// c, c + C, ... in turn.
 static int batch_capture(cola_batch* b, int n, int C, int cap, cudaGraphExec_t* out) {
   cudaGraph_t graph = nullptr;
   BCK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeRelaxed));
@@ -972,7 +1006,7 @@ static int batch_capture(cola_batch* b, int n, int C, int cap, cudaGraphExec_t* 
 
 static int batch_launch(cola_batch* b, int C, int cap) {
   const int n = b->step;
-  auto key = std::make_tuple(n, C, cap);
+  auto key = std::make_pair(C, cap);
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
     cudaGraphExec_t ex = nullptr;
@@ -1078,7 +1112,7 @@ int cola_batch_autotune(cola_batch* b, int32_t max_steps, int32_t* chains_out, i
     if (used >= budget) break;
     // capture outside the timed region, then time one launch (one real step)
     cudaGraphExec_t ex = nullptr;
-    auto key = std::make_tuple(b->step, ck.first, ck.second);
+    auto key = std::make_pair(ck.first, ck.second);
     if (!b->graphs.count(key)) {
       int rc = batch_capture(b, b->step, ck.first, ck.second, &ex);
       if (rc != COLA_OK) return rc;

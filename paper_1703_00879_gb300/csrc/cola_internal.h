@@ -25,11 +25,22 @@ struct ForceParams {
   float norm;        // 1 / N^3
   int model;         // 0 LCDM, 1 f(R), 2 nDGP
   int screened;      // 1: screened fifth force
+  // When src is set, kernels replace every value above by src[*step] (the
+  // parameters of the current step, kept on the device so one captured
+  // launch sequence serves every step).
+  const ForceParams* src;
+  const int* step;
 };
+
+__device__ __forceinline__ void resolve(ForceParams& fp) {
+  if (fp.src) fp = fp.src[*fp.step];
+}
 
 // Parameters of the per-k LPT reweight (Sec. 4.1): table of float4 per log-k node.
 struct LptParams {
-  const float4* tab;  // nk nodes: (c1, c2, e1, e2)
+  const float4* tab;  // row 0 of the table; the row used is row0 + (*step if step)
+  const int* step;
+  int row0;
   float lnk0, inv_dlnk;
   int nk;
   float kf;           // 2 pi / L
@@ -82,16 +93,25 @@ cudaError_t lpt_z(int N, const void* phi1, const void* phi2, float2* o0, float2*
 // ------------------------------------------------------------------ particles
 cudaError_t part_deposit(const PartParams& pp, const float* sx, const float* sy, const float* sz,
                          float* rho, int64_t P, cudaStream_t s);
+// Kick/drift time integrals: dt[3 * (*step) + j] when dt is set (j = 0 first
+// half kick, 1 drift, 2 second half kick), else the given values.
+struct StepDt {
+  const float* dt;
+  const int* step;
+  float dtk, dtd;
+};
 cudaError_t part_drift_deposit(const PartParams& pp, float* sx, float* sy, float* sz, float* vx,
                                float* vy, float* vz, const float* ax, const float* ay,
                                const float* az, const float* dpx, const float* dpy,
-                               const float* dpz, float* rho, float dtk, float dtd, int64_t P,
+                               const float* dpz, float* rho, StepDt dt, int64_t P,
                                cudaStream_t s);
 cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float* sy,
                              const float* sz, float* vx, float* vy, float* vz, float* ax,
                              float* ay, float* az, const float* Ax, const float* Ay,
                              const float* Az, const float* Fx, const float* Fy, const float* Fz,
-                             float dtk, int64_t P, cudaStream_t s);
+                             StepDt dt, int64_t P, cudaStream_t s);
+// *step += 1 (end of a step)
+cudaError_t step_advance(int* step, cudaStream_t s);
 cudaError_t part_snapshot(const PartParams& pp, const float* sx, const float* sy, const float* sz,
                           const float* vx, const float* vy, const float* vz, const float* lx,
                           const float* ly, const float* lz, float vscale, float* pos, float* vel,

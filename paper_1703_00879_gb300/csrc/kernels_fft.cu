@@ -320,6 +320,7 @@ template <int N, int TW, int MODEL>
 __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1))) k_z_screen_field(OpZScreenField<N, TW, MODEL> op,
                                                        const float2* __restrict__ twg,
                                                        int64_t ntiles) {
+  resolve(op.fp);
   col_pipeline<N, N * TW>(op, twg, ntiles);
 }
 
@@ -396,6 +397,7 @@ struct OpZForce {
 template <int N, int TW, bool SCREENED, bool KEEP>
 __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1) + (size_t)N * TW * 8)) k_z_force(
     OpZForce<N, TW, SCREENED, KEEP> op, const float2* __restrict__ twg, int64_t ntiles) {
+  resolve(op.fp);
   col_pipeline<N, N * TW>(op, twg, ntiles);
 }
 
@@ -486,6 +488,7 @@ struct OpLptZ {
 template <int N, int TW, int PREC>
 __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 4))) k_lpt_z(OpLptZ<N, TW, PREC> op,
                                               const float2* __restrict__ twg, int64_t ntiles) {
+  op.lp.tab += (size_t)(op.lp.row0 + (op.lp.step ? *op.lp.step : 0)) * op.lp.nk;
   col_pipeline<N, N * 4 * TW>(op, twg, ntiles);
 }
 
@@ -688,6 +691,7 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
                                                     float2* __restrict__ s_out, int64_t P,
                                                     ForceParams fp, const float2* __restrict__ twg,
                                                     int64_t ntiles) {
+  resolve(fp);
   using C = RowCfg<N, TWX>;
   constexpr int M = N / 2;
   extern __shared__ __align__(16) float2 sm[];

@@ -112,9 +112,11 @@ __global__ void __launch_bounds__(NTP) k_drift_deposit(
     float* __restrict__ vx, float* __restrict__ vy, float* __restrict__ vz,
     const float* __restrict__ ax, const float* __restrict__ ay, const float* __restrict__ az,
     const float* __restrict__ dpx, const float* __restrict__ dpy,
-    const float* __restrict__ dpz, float* __restrict__ rho, float dtk, float dtd, int64_t P) {
+    const float* __restrict__ dpz, float* __restrict__ rho, StepDt dt, int64_t P) {
   const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
   if (p >= P) return;
+  const float dtk = dt.dt ? dt.dt[3 * *dt.step] : dt.dtk;
+  const float dtd = dt.dt ? dt.dt[3 * *dt.step + 1] : dt.dtd;
   const float ux = vx[p] + ax[p] * dtk;
   const float uy = vy[p] + ay[p] * dtk;
   const float uz = vz[p] + az[p] * dtk;
@@ -143,8 +145,9 @@ __global__ void __launch_bounds__(NTP) k_gather_kick(
     float* __restrict__ vz, float* __restrict__ ax, float* __restrict__ ay,
     float* __restrict__ az, const float* __restrict__ Ax, const float* __restrict__ Ay,
     const float* __restrict__ Az, const float* __restrict__ Fx, const float* __restrict__ Fy,
-    const float* __restrict__ Fz, float dtk, int64_t P) {
+    const float* __restrict__ Fz, StepDt dt, int64_t P) {
   const int64_t p0 = (int64_t)blockIdx.x * NTP * PPT + threadIdx.x;
+  const float dtk = dt.dt ? dt.dt[3 * *dt.step + 2] : dt.dtk;
   float px[PPT], py[PPT], pz[PPT];
 #pragma unroll
   for (int u = 0; u < PPT; ++u) {
@@ -276,6 +279,8 @@ __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, i
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + NTP - 1) / NTP); }
 
+__global__ void k_step_advance(int* step) { *step += 1; }
+
 }  // namespace
 
 cudaError_t part_deposit(const PartParams& pp, const float* sx, const float* sy, const float* sz,
@@ -287,10 +292,10 @@ cudaError_t part_deposit(const PartParams& pp, const float* sx, const float* sy,
 cudaError_t part_drift_deposit(const PartParams& pp, float* sx, float* sy, float* sz, float* vx,
                                float* vy, float* vz, const float* ax, const float* ay,
                                const float* az, const float* dpx, const float* dpy,
-                               const float* dpz, float* rho, float dtk, float dtd, int64_t P,
+                               const float* dpz, float* rho, StepDt dt, int64_t P,
                                cudaStream_t s) {
   k_drift_deposit<<<blocks_for(P), NTP, 0, s>>>(pp, sx, sy, sz, vx, vy, vz, ax, ay, az, dpx, dpy,
-                                                dpz, rho, dtk, dtd, P);
+                                                dpz, rho, dt, P);
   return cudaGetLastError();
 }
 
@@ -298,9 +303,9 @@ cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float*
                              const float* sz, float* vx, float* vy, float* vz, float* ax,
                              float* ay, float* az, const float* Ax, const float* Ay,
                              const float* Az, const float* Fx, const float* Fy, const float* Fz,
-                             float dtk, int64_t P, cudaStream_t s) {
+                             StepDt dt, int64_t P, cudaStream_t s) {
   k_gather_kick<<<(unsigned)((P + NTP * PPT - 1) / (NTP * PPT)), NTP, 0, s>>>(
-      pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, Fx, Fy, Fz, dtk, P);
+      pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, Fx, Fy, Fz, dt, P);
   return cudaGetLastError();
 }
 
@@ -310,6 +315,11 @@ cudaError_t part_snapshot(const PartParams& pp, const float* sx, const float* sy
                           int64_t P, cudaStream_t s) {
   k_snapshot<<<blocks_for(P), NTP, 0, s>>>(pp, sx, sy, sz, vx, vy, vz, lx, ly, lz, vscale, pos,
                                            vel, P);
+  return cudaGetLastError();
+}
+
+cudaError_t step_advance(int* step, cudaStream_t s) {
+  k_step_advance<<<1, 1, 0, s>>>(step);
   return cudaGetLastError();
 }
 
