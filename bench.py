@@ -380,13 +380,11 @@ def bench_ensemble(args):
     torch.cuda.synchronize()
     t_init = time.perf_counter() - t0
     b = pkg.Batch(sims)
-    chains, cap = b.autotune(max_steps=args.autotune_steps)
+    plan = b.autotune(max_steps=args.autotune_steps)
     b.step(-1)
     torch.cuda.synchronize()
     t_steps = time.perf_counter() - t0 - t_init
-    for s in sims:
-        s.pk()
-    torch.cuda.synchronize()
+    b.pk()
     t_batch = time.perf_counter() - t0
     b.close()
     for s in sims:
@@ -395,7 +393,8 @@ def bench_ensemble(args):
            "one_at_a_time_sims_per_hour": solo_rate, "speedup_vs_one_at_a_time": (n / t_batch * 3600.0) / solo_rate,
            "n_sims": n, "steps": runs[0].nsteps, "config": {"workload": "ensemble 64^3 particles / 128^3 mesh, "
            "L=128 Mpc/h, 20 steps, models cycled over LCDM, F6, F5, F4, nDGP rcH0=1, nDGP rcH0=5, seeds 0..%d" % (n - 1)},
-           "autotune": {"chains": chains, "grid_cap": cap, "steps_used": args.autotune_steps},
+           "autotune": {"group": plan[0], "chains": plan[1], "grid_cap": plan[2],
+                        "steps_used": args.autotune_steps},
            "seconds": {"init_and_ic": t_init, "steps": t_steps, "total": t_batch, "one_at_a_time_prefix": t_solo,
                        "one_at_a_time_sims": n1}}
     print(json.dumps(out), flush=True)

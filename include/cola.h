@@ -20,10 +20,14 @@
  *     failure; no call aborts or prints.  The message of the last failure is
  *     returned by cola_last_error (a context-free failure, e.g. in cola_init
  *     before the context exists, is reported by cola_last_error(NULL)).
- *   - Memory: every device allocation goes through the alloc/free callbacks
- *     given to cola_init (NULL callbacks: cudaMallocAsync/cudaFreeAsync on the
- *     stream).  The context owns what it allocates and releases it in
- *     cola_free.  Buffers passed in by the caller stay owned by the caller.
+ *   - Memory: the per-context buffers are one allocation made through the
+ *     alloc/free callbacks given to cola_init (NULL callbacks:
+ *     cudaMallocAsync/cudaFreeAsync on the stream); the context owns it and
+ *     releases it in cola_free.  Read-only tables that depend only on the
+ *     configuration and model (twiddles, growth tables, per-step parameters)
+ *     are library-owned (cudaMalloc), uploaded once per distinct key and
+ *     shared by every context with that key.  Buffers passed in by the
+ *     caller stay owned by the caller.
  *   - Streams: all device work is enqueued on the stream given to cola_init
  *     (borrowed, never destroyed).  Calls that take or return HOST buffers
  *     synchronise that stream before returning; calls with DEVICE buffers do
@@ -93,7 +97,7 @@ typedef struct {
 } cola_model;
 
 /* Creates a context: validates the configuration, allocates every device
- * buffer of the run (particles, LPT grid, PM mesh, tables) through `alloc`,
+ * buffer of the run (particles, LPT grid, PM mesh) in one call of `alloc`,
  * and computes the background quantities.  `stream` is a cudaStream_t (NULL =
  * legacy default stream).  On success *out owns the context; on failure
  * *out is NULL and nothing is leaked.  Errors: COLA_EINVAL (sizes not powers of
@@ -105,7 +109,9 @@ int cola_init(const cola_config* cfg, cola_alloc_fn alloc, cola_free_fn free_fn,
  * growth ODEs of Sec. 4.1 (D1'' = kappa mu(k,a) D1) and Eq. fofrapprox
  * (approximate second-order D2 with gamma_2(k, k/sqrt2, k/sqrt2, a)) on
  * nk_table log-spaced k nodes at every step boundary; uploads the float
- * tables.  Must precede cola_ic.  Errors: COLA_EINVAL (unknown kind,
+ * tables (once per distinct configuration and model: later contexts with
+ * the same key share that copy and this call then copies nothing and does
+ * not synchronise).  Must precede cola_ic.  Errors: COLA_EINVAL (unknown kind,
  * non-positive fR0/rcH0/R_smooth where needed), COLA_ESTATE (after cola_ic). */
 int cola_set_model(cola_ctx* ctx, const cola_model* model);
 
@@ -210,23 +216,49 @@ int cola_force_from_density(cola_ctx* ctx, const float* rho, double a, float* fo
  * --------------------------------------------------------------------- */
 typedef struct cola_batch cola_batch;
 
-/* Groups n contexts that completed cola_ic, have equal nsteps and steps done,
- * and live on the current device.  Each step of cola_batch_step is ONE CUDA
- * graph launch on `stream` that advances every context by one step.  The
- * graph of step k is captured on first use from `chains` forked streams
- * (chain c advances contexts c, c + chains, ... in turn, chains run
- * concurrently), instantiated and kept; chains <= 0 picks min(n, 32).
+/* How one batch step is launched.  The contexts, in batch order, are split
+ * into groups of `group` consecutive contexts; every kernel of the step runs
+ * ONCE per group over all of its contexts (a tile index that spans the
+ * group's simulations; the model-dependent force stages run once per model
+ * subset of the group).  Multi-simulation groups need contexts of one shape:
+ * equal Np, Nmesh, Lbox, nsteps, nk_table and seed_precision (seeds, models
+ * and cosmologies may differ); otherwise groups have one context.  Groups are
+ * spread round-robin over `chains` concurrent streams; `grid_cap` > 0 bounds
+ * the persistent grid of every FFT pass so concurrent groups share the SMs. */
+typedef struct {
+  int32_t group;    /* contexts per group; <= 0: all (one shape) or 1 */
+  int32_t chains;   /* concurrent streams, >= 1 */
+  int32_t grid_cap; /* CTAs per FFT pass, 0 = no cap */
+} cola_batch_plan;
+
+/* Groups 1..65535 distinct contexts that completed cola_ic, have equal nsteps
+ * and steps done, and live on the current device.  Each step of
+ * cola_batch_step is ONE CUDA graph launch on `stream` that advances every
+ * context by one step: the launch sequence of the plan (NULL: one group over
+ * all contexts of one shape, else one context per group on one chain) is
+ * captured once, instantiated and replayed for every step (the step index
+ * and each simulation's per-step parameters are read on the device).
  * Contexts whose own stream differs from `stream` get ordered behind each
  * batch step.  The batch borrows the contexts (free the batch before them).
  * Errors: COLA_EINVAL, COLA_ESTATE, COLA_ECUDA (message via cola_last_error(NULL)). */
-int cola_batch_create(cola_ctx* const* ctxs, int32_t n, int32_t chains, void* stream,
+int cola_batch_create(cola_ctx* const* ctxs, int32_t n, const cola_batch_plan* plan, void* stream,
                       cola_batch** out);
-int cola_batch_step(cola_batch* b, int32_t nsteps);  /* -1: to the last step */
-/* Autotuner: times up to max_steps real steps (they advance the batch) with
- * different (chains, grid cap) candidates - the grid cap bounds the
- * persistent grid of every FFT pass so that concurrent simulations share the
- * SMs - and keeps the fastest for later steps. */
-int cola_batch_autotune(cola_batch* b, int32_t max_steps, int32_t* chains_out, int32_t* cap_out);
+int cola_batch_set_plan(cola_batch* b, const cola_batch_plan* plan);
+int cola_batch_get_plan(const cola_batch* b, cola_batch_plan* out);
+/* Advances every context by nsteps (-1: to the last step).  When stage timing
+ * is enabled on the first context (cola_profile_enable), the steps are
+ * launched without a graph, group after group on one stream, so that the
+ * first group's stage timings (covering all of its simulations) are recorded. */
+int cola_batch_step(cola_batch* b, int32_t nsteps);
+/* Autotuner: times up to max_steps real steps (they advance the batch), one
+ * per candidate plan (one group over everything; halves and quarters on
+ * concurrent chains; small groups on many chains with a capped grid), and
+ * keeps the fastest for later steps; *best_out receives it (may be NULL). */
+int cola_batch_autotune(cola_batch* b, int32_t max_steps, cola_batch_plan* best_out);
+/* Matter power spectrum of every context (same estimator and bins as
+ * cola_pk), computed by multi-simulation launches with one synchronisation:
+ * k, pk, nmodes are host arrays [n][nbins] in batch order (each may be NULL). */
+int cola_batch_pk(cola_batch* b, int32_t nbins, double* k, double* pk, int64_t* nmodes);
 int32_t cola_batch_steps_done(const cola_batch* b);
 void cola_batch_free(cola_batch* b);
 
@@ -296,8 +328,11 @@ int cola_pk_noalloc(const float* pos, int64_t n, int32_t nmesh, double Lbox, int
 int cola_host_growth(const cola_config* cfg, const cola_model* model, double* out,
                      double* k_nodes);
 
-/* Device bytes cola_init would allocate for cfg (for admission control);
- * -1 if cfg is invalid. */
+/* Device bytes cola_init allocates for cfg: one allocation holding every
+ * per-context buffer (for admission control); -1 if cfg is invalid.  Not
+ * counted: the read-only tables shared by all contexts of one configuration
+ * and model (twiddles, growth tables, per-step parameters; about
+ * 2 (nsteps+1) nk_table 16 bytes per distinct configuration and model). */
 int64_t cola_device_bytes(const cola_config* cfg);
 
 /* Time integrals of the kick-drift-kick step (Sec. 2; dtau = dt/a^2):

@@ -45,6 +45,10 @@ class cola_model(ctypes.Structure):
                 ("scale_dependent", ctypes.c_int32)]
 
 
+class cola_batch_plan(ctypes.Structure):
+    _fields_ = [("group", ctypes.c_int32), ("chains", ctypes.c_int32), ("grid_cap", ctypes.c_int32)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -68,9 +72,13 @@ _SIGS = {
     "cola_fft": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
     "cola_cic_deposit": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int32]),
     "cola_force_from_density": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, ctypes.c_int32]),
-    "cola_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.POINTER(_P)]),
+    "cola_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(cola_batch_plan), _P,
+                                         ctypes.POINTER(_P)]),
+    "cola_batch_set_plan": (ctypes.c_int, [_P, ctypes.POINTER(cola_batch_plan)]),
+    "cola_batch_get_plan": (ctypes.c_int, [_P, ctypes.POINTER(cola_batch_plan)]),
     "cola_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
-    "cola_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "cola_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(cola_batch_plan)]),
+    "cola_batch_pk": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "cola_batch_steps_done": (ctypes.c_int32, [_P]),
     "cola_batch_free": (None, [_P]),
     "cola_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
@@ -328,26 +336,50 @@ class Simulation:
 
 
 class Batch:
-    """cola_batch over Simulations of one shape: one CUDA graph launch per step for all of them."""
+    """cola_batch over Simulations: one CUDA graph launch per step for all of them.
 
-    def __init__(self, sims, chains: int = 0, stream=None):
+    plan = (group, chains, grid_cap) as in cola_batch_plan; None: one group over
+    all simulations when they share a shape, else one per group on one chain.
+    """
+
+    def __init__(self, sims, plan=None, stream=None):
         import torch
         self.sims = list(sims)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         arr = (_P * len(self.sims))(*[s.ctx for s in self.sims])
         h = _P()
-        _check(lib().cola_batch_create(arr, len(self.sims), int(chains), _P(self.stream.cuda_stream),
-                                       ctypes.byref(h)))
+        p = ctypes.byref(cola_batch_plan(*plan)) if plan is not None else None
+        _check(lib().cola_batch_create(arr, len(self.sims), p, _P(self.stream.cuda_stream), ctypes.byref(h)))
         self.h = h
 
     def step(self, n: int = 1):
         _check(lib().cola_batch_step(self.h, int(n)))
 
     def autotune(self, max_steps: int = 4):
-        c = ctypes.c_int32()
-        k = ctypes.c_int32()
-        _check(lib().cola_batch_autotune(self.h, int(max_steps), ctypes.byref(c), ctypes.byref(k)))
-        return int(c.value), int(k.value)
+        """Times candidate plans on real steps; returns the kept (group, chains, grid_cap)."""
+        p = cola_batch_plan()
+        _check(lib().cola_batch_autotune(self.h, int(max_steps), ctypes.byref(p)))
+        return int(p.group), int(p.chains), int(p.grid_cap)
+
+    @property
+    def plan(self):
+        p = cola_batch_plan()
+        _check(lib().cola_batch_get_plan(self.h, ctypes.byref(p)))
+        return int(p.group), int(p.chains), int(p.grid_cap)
+
+    @plan.setter
+    def plan(self, value):
+        _check(lib().cola_batch_set_plan(self.h, ctypes.byref(cola_batch_plan(*value))))
+
+    def pk(self, nbins: Optional[int] = None):
+        """(k, P, nmodes), each [n_sims, nbins], for every simulation in batch order."""
+        nb = nbins or self.sims[0].run.Nmesh // 2
+        n = len(self.sims)
+        k = np.empty((n, nb))
+        pk = np.empty((n, nb))
+        nm = np.empty((n, nb), np.int64)
+        _check(lib().cola_batch_pk(self.h, nb, k.ctypes.data, pk.ctypes.data, nm.ctypes.data))
+        return k, pk, nm
 
     @property
     def steps_done(self) -> int:

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -33,6 +34,7 @@ struct cola_ctx {
   void* user = nullptr;
   std::string err;
   std::vector<void*> allocs;
+  std::vector<std::vector<double>> const_keys;  // shared device constants this context holds
   int Np = 0, Nm = 0, lgNp = 0, nk = 0;
   double L = 0;
   int64_t P = 0, M = 0;
@@ -62,10 +64,10 @@ struct cola_ctx {
   double Dratio = 1.0;
   // device-resident step state: current step and per-step parameters, so the
   // launch sequence of a step does not depend on which step it is
-  int* dstep = nullptr;
-  ForceParams* dfp = nullptr;  // [nsteps]: force parameters at a_{n+1}
-  float* ddt = nullptr;        // [nsteps][3]: half kick, drift, half kick
-  int h_step = 0;              // staging for uploads of the step counter
+  SimHeader* hdr = nullptr;    // device header (in the context's allocation)
+  SimHeader hh{};              // host copy of what was last written to it
+  ForceParams* dfp = nullptr;  // [nsteps]: force parameters at a_{n+1} (shared)
+  float* ddt = nullptr;        // [nsteps][3]: half kick, drift, half kick (shared)
   // per-stage event timing
   bool prof = false;
   struct Stage {
@@ -81,14 +83,21 @@ struct cola_ctx {
 // A batch of contexts advanced together, one CUDA graph launch per step.
 struct cola_batch {
   std::vector<cola_ctx*> ctx;
+  bool uniform = false;                    // one shape: multi-simulation launches possible
   cudaStream_t st = nullptr;               // caller's stream (may be the legacy stream)
   cudaStream_t cap_st = nullptr;           // owned: graphs are captured and launched here
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  std::vector<cudaStream_t> chain_st;      // forked capture streams (owned)
+  std::vector<cudaStream_t> chain_st;      // forked capture streams (owned, created on demand)
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;           // one per chain stream (owned)
-  int chains = 1, cap = 0, step = 0;
-  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (chains, cap): one graph serves every step
+  cola_batch_plan plan{1, 1, 0};
+  int step = 0;
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    void* shifts = nullptr;                // device shift arrays the graph's launches read
+  };
+  std::map<std::tuple<int, int, int>, Graph> graphs;  // plan -> graph serving every step
+  double* pk_acc = nullptr;                // [n][3 * kMaxBins] (batch P(k))
   std::string err;
 };
 
@@ -297,16 +306,130 @@ void growth_for(const cola_config& cfg, const cola_model& m, Growth& g, std::vec
   if (dlnk_out) *dlnk_out = dlnk;
 }
 
-int upload_twiddles(cola_ctx* ctx, int N, float2** dst) {
-  CHECK_RC(alloc_buf(ctx, dst, N));
-  std::vector<float2> h(N);
-  for (int m = 0; m < N; ++m) {
-    const double ang = -2.0 * kPi * m / N;
-    h[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+// ---------------------------------------------------------------- shared device constants
+// Read-only device data that depends only on a key: the twiddle table of a
+// transform length, and per (configuration without the seed, model) the LPT
+// growth tables, the per-step force parameters and the time integrals.  Every
+// context with the same key on the same device points at one copy, so once a
+// key has been seen cola_init and cola_set_model copy nothing to the device.
+// The copies are library-owned (cudaMalloc), uploaded on a library stream and
+// published only after that upload has completed; entries that no context
+// holds are released once the cache grows past kMaxConstEntries.
+constexpr size_t kMaxConstEntries = 512;
+struct ConstEntry {
+  void* mem = nullptr;
+  int refs = 0;
+};
+std::mutex g_const_mu;
+std::map<std::vector<double>, ConstEntry> g_consts;
+std::map<int, cudaStream_t> g_const_stream;
+
+int acquire_consts(cola_ctx* ctx, std::vector<double> key, size_t bytes,
+                   const std::function<void(char*)>& fill, void** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  key.insert(key.begin(), (double)dev);
+  std::lock_guard<std::mutex> lk(g_const_mu);
+  auto it = g_consts.find(key);
+  if (it == g_consts.end()) {
+    if (g_consts.size() >= kMaxConstEntries) {
+      for (auto e = g_consts.begin(); e != g_consts.end();) {
+        if (e->second.refs == 0) {
+          cudaFree(e->second.mem);
+          e = g_consts.erase(e);
+        } else {
+          ++e;
+        }
+      }
+    }
+    cudaStream_t& cs = g_const_stream[dev];
+    if (!cs) CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    std::vector<char> h(bytes);
+    fill(h.data());
+    void* mem = nullptr;
+    CK(cudaMalloc(&mem, bytes));
+    cudaError_t e = cudaMemcpyAsync(mem, h.data(), bytes, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) {
+      cudaFree(mem);
+      return fail(ctx, COLA_ECUDA, std::string("constant upload: ") + cudaGetErrorString(e));
+    }
+    it = g_consts.emplace(key, ConstEntry{mem, 0}).first;
   }
-  CK(cudaMemcpyAsync(*dst, h.data(), N * sizeof(float2), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
+  it->second.refs += 1;
+  ctx->const_keys.push_back(key);
+  *out = it->second.mem;
   return COLA_OK;
+}
+
+void release_consts(cola_ctx* ctx) {
+  std::lock_guard<std::mutex> lk(g_const_mu);
+  for (const auto& k : ctx->const_keys) {
+    auto it = g_consts.find(k);
+    if (it != g_consts.end() && it->second.refs > 0) it->second.refs -= 1;
+  }
+  ctx->const_keys.clear();
+}
+
+int shared_twiddles(cola_ctx* ctx, int N, float2** dst) {
+  void* p = nullptr;
+  CHECK_RC(acquire_consts(ctx, {0.0, (double)N}, (size_t)N * sizeof(float2), [N](char* h) {
+    float2* t = reinterpret_cast<float2*>(h);
+    for (int m = 0; m < N; ++m) {
+      const double ang = -2.0 * kPi * m / N;
+      t[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  }, &p));
+  *dst = static_cast<float2*>(p);
+  return COLA_OK;
+}
+
+// ---------------------------------------------------------------- context memory
+// Every per-context device buffer lives in one allocation (one call of the
+// allocator per context); each buffer starts on a 256-byte boundary.
+struct Layout {
+  struct Item {
+    void** dst;
+    size_t off;
+  };
+  std::vector<Item> items;
+  size_t size = 0;
+  template <class T>
+  void add(T** p, size_t count) {
+    items.push_back({reinterpret_cast<void**>(p), size});
+    size += (count * sizeof(T) + 255) / 256 * 256;
+  }
+  void place(char* base) const {
+    for (const auto& it : items) *it.dst = base + it.off;
+  }
+};
+
+void context_layout(cola_ctx* c, const cola_config& cfg, Layout& L) {
+  const int64_t P = (int64_t)cfg.Np * cfg.Np * cfg.Np, M = (int64_t)cfg.Nmesh * cfg.Nmesh * cfg.Nmesh;
+  const int64_t hp = half_elems(cfg.Np), hm = half_elems(cfg.Nmesh);
+  for (int d = 0; d < 3; ++d) {
+    L.add(&c->s[d], P);
+    L.add(&c->v[d], P);
+    L.add(&c->acc[d], P);
+  }
+  for (int f = 0; f < 2; ++f) {
+    L.add(&c->phi[f], hp);
+    if (cfg.seed_precision) L.add(reinterpret_cast<uint32_t**>(&c->seedq[f]), hp);
+  }
+  for (int i = 0; i < 6; ++i) {
+    L.add(&c->lc[i], hp);
+    L.add(&c->lr[i], P);
+  }
+  L.add(&c->rho, M);
+  L.add(&c->Cd, hm);
+  L.add(&c->Ck, hm);
+  L.add(&c->Cw, hm);
+  L.add(&c->Cphi, hm);
+  L.add(&c->Cphz, hm);
+  for (int d = 0; d < 3; ++d) L.add(&c->F[d], M);
+  L.add(&c->pk_acc, 3 * kMaxBins);
+  L.add(&c->hdr, 1);
+  L.add(&c->scratch, 64);
 }
 
 ForceParams force_params(const cola_ctx* c, double a) {
@@ -351,20 +474,21 @@ int c2r3(cola_ctx* ctx, int N, float2* in, float* out, const float2* tw) {
   return COLA_OK;
 }
 
-// Sec. 4.1 / App. A: LPT fields at the lattice from the k-space seeds and one table row.
-int run_lpt(cola_ctx* ctx, const float4* table, int row0, const int* step) {
+// Sec. 4.1 / App. A: LPT fields at the lattice from the k-space seeds and one
+// row of table `vel` (0 displacement/acceleration, 1 velocity): row0, plus the
+// device step counter when add_step; over m's simulations (ctx is the first).
+int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}) {
   LptParams lp{};
-  lp.tab = table;
+  lp.hdr = ctx->hdr;
+  lp.vel = vel;
   lp.row0 = row0;
-  lp.step = step;
+  lp.add_step = add_step ? 1 : 0;
   lp.lnk0 = (float)ctx->lnk0;
   lp.inv_dlnk = (float)(1.0 / ctx->dlnk);
   lp.nk = ctx->nk;
   lp.kf = (float)(2.0 * kPi / ctx->L);
   lp.norm = (float)(1.0 / ((double)ctx->Np * ctx->Np * ctx->Np));
   lp.seed_prec = ctx->cfg.seed_precision;
-  lp.seed_scale1 = ctx->seed_scale[0];
-  lp.seed_scale2 = ctx->seed_scale[1];
   const void* p1 = lp.seed_prec ? ctx->seedq[0] : (const void*)ctx->phi[0];
   const void* p2 = lp.seed_prec ? ctx->seedq[1] : (const void*)ctx->phi[1];
   const int N = ctx->Np;
@@ -373,78 +497,121 @@ int run_lpt(cola_ctx* ctx, const float4* table, int row0, const int* step) {
   const double H = (double)N * N * (N / 2 + 1) * 8.0, R = (double)N * N * N * 4.0;
   const double seedH = H * (lp.seed_prec ? 0.5 : 1.0);
   cudaEvent_t e = prof_begin(ctx);
-  CK(lpt_z(N, p1, p2, ctx->lc[0], ctx->lc[1], ctx->lc[2], ctx->lc[3], lp, ctx->tw_np, st));
-  prof_end(ctx, ST_LPT_Z, e, 1, 2 * seedH + 4 * H);
+  CK(lpt_z(N, p1, p2, ctx->lc[0], ctx->lc[1], ctx->lc[2], ctx->lc[3], lp, ctx->tw_np, st, m));
+  prof_end(ctx, ST_LPT_Z, e, 1, m.nb * (2 * seedH + 4 * H));
   e = prof_begin(ctx);
-  CK(fft_yinv2(N, ctx->lc[0], ctx->lc[0], ctx->lc[4], kf, ctx->tw_np, st));
-  CK(fft_col(N, ctx->lc[1], 1, true, ctx->tw_np, st));
-  CK(fft_yinv2(N, ctx->lc[2], ctx->lc[2], ctx->lc[5], kf, ctx->tw_np, st));
-  CK(fft_col(N, ctx->lc[3], 1, true, ctx->tw_np, st));
-  prof_end(ctx, ST_LPT_Y, e, 4, 2.5 * H);
+  CK(fft_yinv2(N, ctx->lc[0], ctx->lc[0], ctx->lc[4], kf, ctx->tw_np, st, m));
+  CK(fft_col(N, ctx->lc[1], 1, true, ctx->tw_np, st, m));
+  CK(fft_yinv2(N, ctx->lc[2], ctx->lc[2], ctx->lc[5], kf, ctx->tw_np, st, m));
+  CK(fft_col(N, ctx->lc[3], 1, true, ctx->tw_np, st, m));
+  prof_end(ctx, ST_LPT_Y, e, 4, m.nb * 2.5 * H);
   e = prof_begin(ctx);
   {
     const float2* in6[6] = {ctx->lc[0], ctx->lc[4], ctx->lc[1], ctx->lc[2], ctx->lc[5], ctx->lc[3]};
     float* out6[6] = {ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->lr[3], ctx->lr[4], ctx->lr[5]};
     const float kfs6[6] = {kf, 0.f, 0.f, kf, 0.f, 0.f};
-    CK(fft_xc2r_multi(N, 6, in6, out6, kfs6, ctx->tw_np, st));
+    CK(fft_xc2r_multi(N, 6, in6, out6, kfs6, ctx->tw_np, st, m));
   }
-  prof_end(ctx, ST_LPT_X, e, 1, 6 * (H + R));
+  prof_end(ctx, ST_LPT_X, e, 1, m.nb * 6 * (H + R));
   ctx->have_lpt = true;
   return COLA_OK;
 }
 
-// App. B: mesh force -grad(Phi_N + phi) at scale factor a from the density in ctx->rho.
-int run_force(cola_ctx* ctx, double a, bool device_params = false) {
-  ForceParams fp = force_params(ctx, a);
-  if (device_params) {  // the values come from dfp[*dstep]; fp's model flags decide the kernels
-    fp.src = ctx->dfp;
-    fp.step = ctx->dstep;
-  }
+// Simulations advanced by one launch sequence: `all` moves the pointers of
+// `lead` to every one of them; the model-dependent force stages run over the
+// subsets (each with its own first context and shifts).
+struct Group {
+  struct Sub {
+    cola_ctx* lead = nullptr;
+    Multi m;
+  };
+  cola_ctx* lead = nullptr;
+  Multi all;
+  Sub unscreened, fr_screened, dgp_screened, screened;
+};
+
+Group single_group(cola_ctx* ctx) {
+  Group g;
+  g.lead = ctx;
+  const Group::Sub me{ctx, Multi{}};
+  const bool scr = ctx->model.kind != COLA_LCDM && ctx->model.screening;
+  if (!scr) g.unscreened = me;
+  else if (ctx->model.kind == COLA_FOFR) g.fr_screened = g.screened = me;
+  else g.dgp_screened = g.screened = me;
+  return g;
+}
+
+// App. B: mesh force -grad(Phi_N + phi) at scale factor a from the density in
+// rho, for every simulation of g.  device_params: each simulation's values of
+// its current step come from its header (a is then only used for the model
+// flags); otherwise the values at a (single simulation).
+int force_group(const Group& g, double a, bool device_params) {
+  cola_ctx* ctx = g.lead;
+  const Multi all = g.all;
+  auto fp_of = [&](cola_ctx* c) {
+    ForceParams fp = force_params(c, a);
+    if (device_params) fp.hdr = c->hdr;
+    return fp;
+  };
+  const ForceParams fp = fp_of(ctx);
   const int N = ctx->Nm;
   auto st = ctx->st;
   const float2* tw = ctx->tw_nm;
   const double H = (double)N * N * (N / 2 + 1) * 8.0, R = (double)N * N * N * 4.0;
   cudaEvent_t e = prof_begin(ctx);
-  CK(fft_xr2c(N, ctx->rho, ctx->Cd, fp.inv_rhobar, -1.f, tw, st));
-  prof_end(ctx, ST_MESH_XR2C, e, 1, R + H);
+  CK(fft_xr2c(N, ctx->rho, ctx->Cd, fp.inv_rhobar, -1.f, tw, st, all));
+  prof_end(ctx, ST_MESH_XR2C, e, 1, all.nb * (R + H));
   e = prof_begin(ctx);
-  CK(fft_col(N, ctx->Cd, 1, false, tw, st));
-  prof_end(ctx, ST_MESH_Y, e, 1, 2 * H);
-  if (fp.screened) {
+  CK(fft_col(N, ctx->Cd, 1, false, tw, st, all));
+  prof_end(ctx, ST_MESH_Y, e, 1, all.nb * 2 * H);
+  if (const Group::Sub& sc = g.screened; sc.lead) {
     e = prof_begin(ctx);
-    CK(mesh_z_screen_field(N, ctx->Cd, ctx->Ck, ctx->Cw, fp, tw, st));
-    prof_end(ctx, ST_Z_SCREEN_FIELD, e, 1, 3 * H);
+    for (const Group::Sub* sub : {&g.fr_screened, &g.dgp_screened})
+      if (sub->lead)
+        CK(mesh_z_screen_field(N, sub->lead->Cd, sub->lead->Ck, sub->lead->Cw, fp_of(sub->lead), tw, st,
+                               sub->m));
+    prof_end(ctx, ST_Z_SCREEN_FIELD, e, 1, sc.m.nb * 3 * H);
     e = prof_begin(ctx);
-    CK(fft_col(N, ctx->Cw, 1, true, tw, st));
-    prof_end(ctx, ST_MESH_YINV, e, 1, 2 * H);
+    CK(fft_col(N, sc.lead->Cw, 1, true, tw, st, sc.m));
+    prof_end(ctx, ST_MESH_YINV, e, 1, sc.m.nb * 2 * H);
     e = prof_begin(ctx);
-    CK(mesh_x_screen_source(N, ctx->Cw, ctx->rho, ctx->Cd, fp, tw, st));
-    prof_end(ctx, ST_X_SCREEN_SOURCE, e, 1, 2 * H + R);
+    for (const Group::Sub* sub : {&g.fr_screened, &g.dgp_screened})
+      if (sub->lead)
+        CK(mesh_x_screen_source(N, sub->lead->Cw, sub->lead->rho, sub->lead->Cd, fp_of(sub->lead), tw,
+                                st, sub->m));
+    prof_end(ctx, ST_X_SCREEN_SOURCE, e, 1, sc.m.nb * (2 * H + R));
     e = prof_begin(ctx);
-    CK(fft_col(N, ctx->Cd, 1, false, tw, st));
-    prof_end(ctx, ST_MESH_Y, e, 1, 2 * H);
+    CK(fft_col(N, sc.lead->Cd, 1, false, tw, st, sc.m));
+    prof_end(ctx, ST_MESH_Y, e, 1, sc.m.nb * 2 * H);
     e = prof_begin(ctx);
-    CK(mesh_z_force(N, ctx->Cd, ctx->Ck, ctx->Cphi, ctx->Cphz, nullptr, fp, tw, st));
-    prof_end(ctx, ST_Z_FORCE, e, 1, 4 * H);
-  } else {
+    CK(mesh_z_force(N, sc.lead->Cd, sc.lead->Ck, sc.lead->Cphi, sc.lead->Cphz, nullptr, fp_of(sc.lead), tw,
+                    st, sc.m));
+    prof_end(ctx, ST_Z_FORCE, e, 1, sc.m.nb * 4 * H);
+  }
+  if (const Group::Sub& un = g.unscreened; un.lead) {
     e = prof_begin(ctx);
-    CK(mesh_z_force(N, ctx->Cd, nullptr, ctx->Cphi, ctx->Cphz, nullptr, fp, tw, st));
-    prof_end(ctx, ST_Z_FORCE, e, 1, 3 * H);
+    CK(mesh_z_force(N, un.lead->Cd, nullptr, un.lead->Cphi, un.lead->Cphz, nullptr, fp_of(un.lead), tw,
+                    st, un.m));
+    prof_end(ctx, ST_Z_FORCE, e, 1, un.m.nb * 3 * H);
   }
   e = prof_begin(ctx);
-  CK(fft_yinv2(N, ctx->Cphi, ctx->Cphi, ctx->Cw, -fp.kf, tw, st));
-  CK(fft_col(N, ctx->Cphz, 1, true, tw, st));
-  prof_end(ctx, ST_MESH_YINV, e, 2, 2.5 * H);
+  CK(fft_yinv2(N, ctx->Cphi, ctx->Cphi, ctx->Cw, -fp.kf, tw, st, all));
+  CK(fft_col(N, ctx->Cphz, 1, true, tw, st, all));
+  prof_end(ctx, ST_MESH_YINV, e, 2, all.nb * 2.5 * H);
   e = prof_begin(ctx);
   {
     const float2* in3[3] = {ctx->Cphi, ctx->Cw, ctx->Cphz};
     float* out3[3] = {ctx->F[0], ctx->F[1], ctx->F[2]};
     const float kfs3[3] = {-fp.kf, 0.f, 0.f};
-    CK(fft_xc2r_multi(N, 3, in3, out3, kfs3, tw, st));
+    CK(fft_xc2r_multi(N, 3, in3, out3, kfs3, tw, st, all));
   }
-  prof_end(ctx, ST_MESH_XC2R, e, 1, 3 * (H + R));
+  prof_end(ctx, ST_MESH_XC2R, e, 1, all.nb * 3 * (H + R));
   ctx->have_force = true;
   return COLA_OK;
+}
+
+int run_force(cola_ctx* ctx, double a, bool device_params = false) {
+  return force_group(single_group(ctx), a, device_params);
 }
 
 PartParams part_params(const cola_ctx* c) {
@@ -474,7 +641,11 @@ int finish_ic(cola_ctx* ctx) {
                        ctx->st));
     }
   }
-  CHECK_RC(run_lpt(ctx, ctx->tab, 0, nullptr));
+  ctx->hh.seed_scale[0] = ctx->seed_scale[0];
+  ctx->hh.seed_scale[1] = ctx->seed_scale[1];
+  ctx->hh.step = 0;
+  CK(set_header(ctx->hdr, ctx->hh, ctx->st));
+  CHECK_RC(run_lpt(ctx, 0, 0, false));
   CK(ic_particles(ctx->P, ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->s[0], ctx->s[1], ctx->s[2],
                   ctx->v[0], ctx->v[1], ctx->v[2], ctx->st));
   const PartParams pp = part_params(ctx);
@@ -483,9 +654,8 @@ int finish_ic(cola_ctx* ctx) {
   CHECK_RC(run_force(ctx, ctx->a[0]));
   CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                       ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[3], ctx->lr[4], ctx->lr[5],
-                      ctx->F[0], ctx->F[1], ctx->F[2], StepDt{nullptr, nullptr, 0.f, 0.f}, ctx->P,
+                      ctx->F[0], ctx->F[1], ctx->F[2], StepDt{nullptr, 0.f, 0.f}, ctx->P,
                       ctx->st));
-  CK(cudaMemsetAsync(ctx->dstep, 0, sizeof(int), ctx->st));
   ctx->step = 0;
   ctx->ic_done = true;
   return COLA_OK;
@@ -516,32 +686,36 @@ int export_half(cola_ctx* ctx, int N, const float2* padded, float2* tmp, void* d
   return copy_out(ctx, dst, tmp, bytes, where);
 }
 
-// Enqueues step n (a_n -> a_{n+1}) of Sec. 2 on ctx->st without touching ctx->step.
-// Enqueues the next step (from the device step counter) on ctx->st; the
-// launch sequence is the same for every step.  n is the host's step index,
-// used only to pick the model branch (constant over the run).
-int enqueue_step(cola_ctx* ctx, int n) {
+// Enqueues the next step (Sec. 2, a_n -> a_{n+1}) of every simulation of g on
+// g.lead->st without touching the host step counters.  The step index comes
+// from each simulation's device header, so the launch sequence is the same for
+// every step.  n is the host's step index, used only for the model flags.
+int enqueue_group_step(const Group& g, int n) {
+  cola_ctx* ctx = g.lead;
+  const Multi m = g.all;
   const PartParams pp = part_params(ctx);
   const double Pb = (double)ctx->P, Mb = (double)ctx->M;
-  const StepDt dt{ctx->ddt, ctx->dstep, 0.f, 0.f};
-  CHECK_RC(run_lpt(ctx, ctx->tab, 1, ctx->dstep));
+  const StepDt dt{ctx->hdr, 0.f, 0.f};
+  CHECK_RC(run_lpt(ctx, 0, 1, true, m));
   cudaEvent_t e = prof_begin(ctx);
-  CK(cudaMemsetAsync(ctx->rho, 0, ctx->M * sizeof(float), ctx->st));
-  prof_end(ctx, ST_RHO_ZERO, e, 1, 4.0 * Mb);
+  CK(zero_f32(ctx->rho, ctx->M, ctx->st, m));
+  prof_end(ctx, ST_RHO_ZERO, e, 1, m.nb * 4.0 * Mb);
   e = prof_begin(ctx);
   CK(part_drift_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                         ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[0], ctx->lr[1],
-                        ctx->lr[2], ctx->rho, dt, ctx->P, ctx->st));
-  prof_end(ctx, ST_DRIFT_DEPOSIT, e, 1, 72.0 * Pb + 8.0 * Mb);
-  CHECK_RC(run_force(ctx, ctx->a[n + 1], true));
+                        ctx->lr[2], ctx->rho, dt, ctx->P, ctx->st, m));
+  prof_end(ctx, ST_DRIFT_DEPOSIT, e, 1, m.nb * (72.0 * Pb + 8.0 * Mb));
+  CHECK_RC(force_group(g, ctx->a[n + 1], true));
   e = prof_begin(ctx);
   CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                       ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[3], ctx->lr[4],
-                      ctx->lr[5], ctx->F[0], ctx->F[1], ctx->F[2], dt, ctx->P, ctx->st));
-  prof_end(ctx, ST_GATHER_KICK, e, 1, 60.0 * Pb + 12.0 * Mb);
-  CK(step_advance(ctx->dstep, ctx->st));
+                      ctx->lr[5], ctx->F[0], ctx->F[1], ctx->F[2], dt, ctx->P, ctx->st, m));
+  prof_end(ctx, ST_GATHER_KICK, e, 1, m.nb * (60.0 * Pb + 12.0 * Mb));
+  CK(step_advance(ctx->hdr, ctx->st, m));
   return COLA_OK;
 }
+
+int enqueue_step(cola_ctx* ctx, int n) { return enqueue_group_step(single_group(ctx), n); }
 
 }  // namespace
 
@@ -577,49 +751,50 @@ int cola_init(const cola_config* cfg, cola_alloc_fn alloc, cola_free_fn free_fn,
   ctx->M = (int64_t)cfg->Nmesh * cfg->Nmesh * cfg->Nmesh;
   ctx->a = a_nodes(*cfg);
   const double Om = cfg->Omega_m;
-  for (int n = 0; n < cfg->nsteps; ++n) {
-    const double a0 = ctx->a[n], a1 = ctx->a[n + 1], am = 0.5 * (a0 + a1);
-    ctx->dtk1.push_back(hdtau(a0, am, Om));
-    ctx->dtd.push_back(hdtau(a0, a1, Om));
-    ctx->dtk2.push_back(hdtau(am, a1, Om));
+  {
+    // the time integrals depend only on (Omega_m, z_ini, z_final, nsteps): computed once per key
+    static std::mutex mu;
+    static std::map<std::vector<double>, std::vector<double>> cache;
+    const std::vector<double> key = {Om, cfg->z_ini, cfg->z_final, (double)cfg->nsteps};
+    std::vector<double> tau;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto it = cache.find(key);
+      if (it != cache.end()) tau = it->second;
+    }
+    if (tau.empty()) {
+      for (int n = 0; n < cfg->nsteps; ++n) {
+        const double a0 = ctx->a[n], a1 = ctx->a[n + 1], am = 0.5 * (a0 + a1);
+        tau.push_back(hdtau(a0, am, Om));
+        tau.push_back(hdtau(a0, a1, Om));
+        tau.push_back(hdtau(am, a1, Om));
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      if (cache.size() > 4096) cache.clear();
+      cache.emplace(key, tau);
+    }
+    for (int n = 0; n < cfg->nsteps; ++n) {
+      ctx->dtk1.push_back(tau[3 * n]);
+      ctx->dtd.push_back(tau[3 * n + 1]);
+      ctx->dtk2.push_back(tau[3 * n + 2]);
+    }
   }
   std::vector<double> kdummy;
   k_nodes(*cfg, ctx->lnk0, ctx->dlnk, kdummy);
   int rc = COLA_OK;
-  const int64_t hp = half_elems(ctx->Np), hm = half_elems(ctx->Nm);
-  for (int d = 0; d < 3 && !rc; ++d) {
-    rc = alloc_buf(ctx, &ctx->s[d], ctx->P);
-    if (!rc) rc = alloc_buf(ctx, &ctx->v[d], ctx->P);
-    if (!rc) rc = alloc_buf(ctx, &ctx->acc[d], ctx->P);
-  }
-  for (int f = 0; f < 2 && !rc; ++f) {
-    rc = alloc_buf(ctx, &ctx->phi[f], hp);
-    if (!rc && cfg->seed_precision) {
-      uint32_t* q = nullptr;
-      rc = alloc_buf(ctx, &q, hp);
-      ctx->seedq[f] = q;
+  {
+    Layout lay;
+    context_layout(ctx, *cfg, lay);
+    void* slab = dev_alloc(ctx, lay.size);
+    if (!slab) {
+      rc = fail(ctx, COLA_ENOMEM, "device allocation of " + std::to_string(lay.size) + " bytes failed");
+    } else {
+      ctx->allocs.push_back(slab);
+      lay.place(static_cast<char*>(slab));
     }
   }
-  for (int i = 0; i < 6 && !rc; ++i) {
-    rc = alloc_buf(ctx, &ctx->lc[i], hp);
-    if (!rc) rc = alloc_buf(ctx, &ctx->lr[i], ctx->P);
-  }
-  if (!rc) rc = alloc_buf(ctx, &ctx->rho, ctx->M);
-  if (!rc) rc = alloc_buf(ctx, &ctx->Cd, hm);
-  if (!rc) rc = alloc_buf(ctx, &ctx->Ck, hm);
-  if (!rc) rc = alloc_buf(ctx, &ctx->Cw, hm);
-  if (!rc) rc = alloc_buf(ctx, &ctx->Cphi, hm);
-  if (!rc) rc = alloc_buf(ctx, &ctx->Cphz, hm);
-  for (int d = 0; d < 3 && !rc; ++d) rc = alloc_buf(ctx, &ctx->F[d], ctx->M);
-  if (!rc) rc = alloc_buf(ctx, &ctx->tab, (size_t)(cfg->nsteps + 1) * cfg->nk_table);
-  if (!rc) rc = alloc_buf(ctx, &ctx->vtab, (size_t)(cfg->nsteps + 1) * cfg->nk_table);
-  if (!rc) rc = alloc_buf(ctx, &ctx->pk_acc, 3 * kMaxBins);
-  if (!rc) rc = alloc_buf(ctx, &ctx->dstep, 4);
-  if (!rc) rc = alloc_buf(ctx, &ctx->dfp, (size_t)cfg->nsteps);
-  if (!rc) rc = alloc_buf(ctx, &ctx->ddt, (size_t)3 * cfg->nsteps);
-  if (!rc) rc = alloc_buf(ctx, &ctx->scratch, 64);
-  if (!rc) rc = upload_twiddles(ctx, ctx->Np, &ctx->tw_np);
-  if (!rc) rc = upload_twiddles(ctx, ctx->Nm, &ctx->tw_nm);
+  if (!rc) rc = shared_twiddles(ctx, ctx->Np, &ctx->tw_np);
+  if (!rc) rc = shared_twiddles(ctx, ctx->Nm, &ctx->tw_nm);
   if (rc) {
     g_err = ctx->err;
     cola_free(ctx);
@@ -654,39 +829,68 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
   CHECK_RC(validate_model(model, ctx));
   if (ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_set_model after cola_ic");
   ctx->model = *model;
-  Growth g;
-  growth_for(ctx->cfg, *model, g, nullptr, nullptr, nullptr);
-  const int nk = ctx->nk, ns = ctx->cfg.nsteps;
-  std::vector<float4> tab((size_t)(ns + 1) * nk), vtab((size_t)(ns + 1) * nk);
-  for (int n = 0; n <= ns; ++n) {
-    for (int j = 0; j < nk; ++j) {
-      const size_t i = (size_t)n * nk + j;
-      float4 t;
-      if (n == 0) {
-        t = make_float4((float)g.D1[i], (float)g.D2[i], (float)g.ddD1[i], (float)g.ddD2[i]);
-      } else {
-        const size_t p = (size_t)(n - 1) * nk + j;
-        t = make_float4((float)(g.D1[i] - g.D1[p]), (float)(g.D2[i] - g.D2[p]), (float)g.ddD1[i],
-                        (float)g.ddD2[i]);
-      }
-      tab[i] = t;
-      vtab[i] = make_float4((float)g.dD1[i], (float)g.dD2[i], 0.f, 0.f);
+  ctx->model_set = true;  // force_params reads the model
+  // a second cola_set_model before cola_ic drops the first model's tables
+  if (ctx->tab) {
+    std::vector<std::vector<double>> keep;
+    for (auto& k : ctx->const_keys)
+      if (k.size() > 2 && k[1] != 1.0) keep.push_back(k);
+    std::lock_guard<std::mutex> lk(g_const_mu);
+    for (auto& k : ctx->const_keys) {
+      auto it = g_consts.find(k);
+      if (k.size() > 2 && k[1] == 1.0 && it != g_consts.end() && it->second.refs > 0) it->second.refs -= 1;
     }
+    ctx->const_keys = keep;
   }
-  CK(cudaMemcpyAsync(ctx->tab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->vtab, vtab.data(), vtab.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->st));
-  ctx->model_set = true;  // force_params below reads the model
-  std::vector<ForceParams> hfp(ns);
-  std::vector<float> hdt(3 * (size_t)ns);
-  for (int n = 0; n < ns; ++n) {
-    hfp[n] = force_params(ctx, ctx->a[n + 1]);
-    hdt[3 * n + 0] = (float)ctx->dtk1[n];
-    hdt[3 * n + 1] = (float)ctx->dtd[n];
-    hdt[3 * n + 2] = (float)ctx->dtk2[n];
-  }
-  CK(cudaMemcpyAsync(ctx->dfp, hfp.data(), hfp.size() * sizeof(ForceParams), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(ctx->ddt, hdt.data(), hdt.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
+  const cola_config& cfg = ctx->cfg;
+  const int nk = ctx->nk, ns = cfg.nsteps;
+  const size_t tab_b = (size_t)(ns + 1) * nk * sizeof(float4);
+  const size_t fp_off = 2 * tab_b, fp_b = ((size_t)ns * sizeof(ForceParams) + 255) / 256 * 256;
+  const size_t dt_off = fp_off + fp_b, bytes = dt_off + 3 * (size_t)ns * sizeof(float);
+  // kind 1: (every configuration field but the seed and the seed precision, the model)
+  const std::vector<double> key = {1.0, (double)cfg.Np, (double)cfg.Nmesh, cfg.Lbox, (double)ns,
+                                   cfg.z_ini, cfg.z_final, cfg.Omega_m, cfg.Omega_b, cfg.h, cfg.n_s,
+                                   cfg.sigma8, (double)nk, (double)model->kind, model->fR0, model->rcH0,
+                                   model->R_smooth, (double)model->screening,
+                                   (double)model->scale_dependent, (double)model->filter};
+  void* mem = nullptr;
+  CHECK_RC(acquire_consts(ctx, key, bytes, [&](char* h) {
+    Growth g;
+    growth_for(cfg, *model, g, nullptr, nullptr, nullptr);
+    float4* tab = reinterpret_cast<float4*>(h);
+    float4* vtab = reinterpret_cast<float4*>(h + tab_b);
+    for (int n = 0; n <= ns; ++n) {
+      for (int j = 0; j < nk; ++j) {
+        const size_t i = (size_t)n * nk + j;
+        if (n == 0) {
+          tab[i] = make_float4((float)g.D1[i], (float)g.D2[i], (float)g.ddD1[i], (float)g.ddD2[i]);
+        } else {
+          const size_t q = (size_t)(n - 1) * nk + j;
+          tab[i] = make_float4((float)(g.D1[i] - g.D1[q]), (float)(g.D2[i] - g.D2[q]),
+                               (float)g.ddD1[i], (float)g.ddD2[i]);
+        }
+        vtab[i] = make_float4((float)g.dD1[i], (float)g.dD2[i], 0.f, 0.f);
+      }
+    }
+    ForceParams* fp = reinterpret_cast<ForceParams*>(h + fp_off);
+    float* dt = reinterpret_cast<float*>(h + dt_off);
+    for (int n = 0; n < ns; ++n) {
+      fp[n] = force_params(ctx, ctx->a[n + 1]);
+      dt[3 * n + 0] = (float)ctx->dtk1[n];
+      dt[3 * n + 1] = (float)ctx->dtd[n];
+      dt[3 * n + 2] = (float)ctx->dtk2[n];
+    }
+  }, &mem));
+  char* base = static_cast<char*>(mem);
+  ctx->tab = reinterpret_cast<float4*>(base);
+  ctx->vtab = reinterpret_cast<float4*>(base + tab_b);
+  ctx->dfp = reinterpret_cast<ForceParams*>(base + fp_off);
+  ctx->ddt = reinterpret_cast<float*>(base + dt_off);
+  ctx->hh.dfp = ctx->dfp;
+  ctx->hh.ddt = ctx->ddt;
+  ctx->hh.tab = ctx->tab;
+  ctx->hh.vtab = ctx->vtab;
+  CK(set_header(ctx->hdr, ctx->hh, ctx->st));
   return COLA_OK;
 }
 
@@ -758,7 +962,7 @@ int cola_snapshot(cola_ctx* ctx, float* pos, float* vel, int32_t where) {
   if (where != COLA_HOST && where != COLA_DEVICE) return fail(ctx, COLA_EINVAL, "bad where");
   if (!pos && !vel) return COLA_OK;
   const size_t bytes = (size_t)ctx->P * 3 * sizeof(float);
-  if (vel) CHECK_RC(run_lpt(ctx, ctx->vtab, ctx->step, nullptr));
+  if (vel) CHECK_RC(run_lpt(ctx, 1, ctx->step, false));
   const PartParams pp = part_params(ctx);
   const float vscale = (float)(100.0 / ctx->a[ctx->step]);
   if (where == COLA_DEVICE) {
@@ -821,6 +1025,7 @@ void cola_free(cola_ctx* ctx) {
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   for (void* p : ctx->allocs) dev_free(ctx, p);
   if (!ctx->alloc) cudaStreamSynchronize(ctx->st);
+  release_consts(ctx);
   cudaGetLastError();
   delete ctx;
 }
@@ -882,8 +1087,8 @@ int cola_import_state(cola_ctx* ctx, const float* disp, const float* dv, const f
   for (int q = 0; q < 3; ++q)
     for (int c = 0; c < 3; ++c)
       CHECK_RC(copy_in(ctx, dstv[q][c], reinterpret_cast<const char*>(src[q]) + c * pb, pb, where));
-  ctx->h_step = steps_done;
-  CHECK_RC(copy_in(ctx, ctx->dstep, &ctx->h_step, sizeof(int), COLA_HOST));
+  ctx->hh.step = steps_done;
+  CK(set_header(ctx->hdr, ctx->hh, ctx->st));
   ctx->step = steps_done;
   return COLA_OK;
 }
@@ -963,26 +1168,114 @@ static int bfail(cola_batch* b, int code, const std::string& m) {
     if (e_ != cudaSuccess) return bfail(b, COLA_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-// Captures one step of every context (the step index comes from each context's
-// device counter, so the graph serves every step): chain c advances contexts
-// c, c + C, ... in turn.
-static int batch_capture(cola_batch* b, int n, int C, int cap, cudaGraphExec_t* out) {
+static bool same_shape(const cola_ctx* a, const cola_ctx* c) {
+  return a->cfg.Np == c->cfg.Np && a->cfg.Nmesh == c->cfg.Nmesh && a->cfg.Lbox == c->cfg.Lbox &&
+         a->cfg.nsteps == c->cfg.nsteps && a->cfg.nk_table == c->cfg.nk_table &&
+         a->cfg.seed_precision == c->cfg.seed_precision;
+}
+
+static cola_batch_plan normal_plan(const cola_batch* b, cola_batch_plan p) {
+  const int n = (int)b->ctx.size();
+  if (!b->uniform || p.group < 1) p.group = b->uniform ? n : 1;
+  p.group = std::min(p.group, n);
+  const int groups = (n + p.group - 1) / p.group;
+  p.chains = std::max(1, std::min(p.chains < 1 ? 1 : p.chains, groups));
+  p.grid_cap = std::max(0, p.grid_cap);
+  return p;
+}
+
+static int chain_streams(cola_batch* b, int C) {
+  while ((int)b->chain_st.size() < C) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    BCK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    b->chain_st.push_back(s);
+    BCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    b->join.push_back(ev);
+  }
+  return COLA_OK;
+}
+
+// Groups of a plan: consecutive runs of plan.group contexts.  Shift arrays
+// (byte offsets of each member's allocation from its subset's first member)
+// are gathered into `hsh`; the Multi pointers are fixed up once the device
+// copy of hsh exists.
+struct GroupPlan {
+  Group g;
+  size_t off[5];  // offsets into hsh of all, unscreened, fr_screened, dgp_screened, screened
+};
+
+static void plan_groups(const cola_batch* b, const cola_batch_plan& p, std::vector<GroupPlan>& out,
+                        std::vector<int64_t>& hsh) {
+  const int n = (int)b->ctx.size();
+  for (int j0 = 0; j0 < n; j0 += p.group) {
+    const int j1 = std::min(n, j0 + p.group);
+    GroupPlan gp;
+    std::vector<cola_ctx*> lists[5];
+    for (int i = j0; i < j1; ++i) {
+      cola_ctx* c = b->ctx[i];
+      const bool scr = c->model.kind != COLA_LCDM && c->model.screening;
+      lists[0].push_back(c);
+      if (!scr) lists[1].push_back(c);
+      else if (c->model.kind == COLA_FOFR) lists[2].push_back(c);
+      else lists[3].push_back(c);
+      if (scr) lists[4].push_back(c);
+    }
+    Group::Sub* subs[5] = {nullptr, &gp.g.unscreened, &gp.g.fr_screened, &gp.g.dgp_screened, &gp.g.screened};
+    for (int q = 0; q < 5; ++q) {
+      gp.off[q] = hsh.size();
+      if (lists[q].empty()) continue;
+      const char* base = static_cast<const char*>(lists[q][0]->allocs[0]);
+      for (cola_ctx* c : lists[q]) hsh.push_back(static_cast<const char*>(c->allocs[0]) - base);
+      Multi m;
+      m.nb = (int)lists[q].size();
+      if (q == 0) {
+        gp.g.lead = lists[q][0];
+        gp.g.all = m;
+      } else {
+        subs[q]->lead = lists[q][0];
+        subs[q]->m = m;
+      }
+    }
+    out.push_back(gp);
+  }
+}
+
+// Captures one step of every context under plan p (the step index comes from
+// each context's device header, so the graph serves every step).
+static int batch_capture(cola_batch* b, int n, const cola_batch_plan& p, cola_batch::Graph* out) {
+  std::vector<GroupPlan> groups;
+  std::vector<int64_t> hsh;
+  plan_groups(b, p, groups, hsh);
+  CHECK_RC(chain_streams(b, p.chains));
+  int64_t* dsh = nullptr;
+  if (!hsh.empty()) {
+    BCK(cudaMalloc(&dsh, hsh.size() * sizeof(int64_t)));
+    out->shifts = dsh;
+    BCK(cudaMemcpy(dsh, hsh.data(), hsh.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  }
+  for (GroupPlan& gp : groups) {
+    Multi* ms[5] = {&gp.g.all, &gp.g.unscreened.m, &gp.g.fr_screened.m, &gp.g.dgp_screened.m,
+                    &gp.g.screened.m};
+    for (int q = 0; q < 5; ++q) ms[q]->shift = ms[q]->nb > 1 ? dsh + gp.off[q] : nullptr;
+  }
   cudaGraph_t graph = nullptr;
   BCK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeRelaxed));
   int rc = COLA_OK;
+  const int C = p.chains;
   cudaError_t e = cudaEventRecord(b->fork, b->cap_st);
   for (int c = 0; c < C && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(b->chain_st[c], b->fork, 0);
-  set_grid_cap(cap);
-  for (size_t i = 0; i < b->ctx.size() && e == cudaSuccess && rc == COLA_OK; ++i) {
-    cola_ctx* ctx = b->ctx[i];
-    cudaStream_t saved = ctx->st;
-    const bool prof = ctx->prof;
-    ctx->st = b->chain_st[i % C];
-    ctx->prof = false;
-    rc = enqueue_step(ctx, n);
-    ctx->st = saved;
-    ctx->prof = prof;
-    if (rc != COLA_OK) b->err = ctx->err;
+  set_grid_cap(p.grid_cap);
+  for (size_t j = 0; j < groups.size() && e == cudaSuccess && rc == COLA_OK; ++j) {
+    cola_ctx* lead = groups[j].g.lead;
+    cudaStream_t saved = lead->st;
+    const bool prof = lead->prof;
+    lead->st = b->chain_st[j % C];
+    lead->prof = false;
+    rc = enqueue_group_step(groups[j].g, n);
+    lead->st = saved;
+    lead->prof = prof;
+    if (rc != COLA_OK) b->err = lead->err;
   }
   set_grid_cap(0);
   for (int c = 0; c < C && e == cudaSuccess; ++c) {
@@ -998,54 +1291,105 @@ static int batch_capture(cola_batch* b, int n, int C, int cap, cudaGraphExec_t* 
     if (graph) cudaGraphDestroy(graph);
     return bfail(b, COLA_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
   }
-  e = cudaGraphInstantiate(out, graph, 0);
+  e = cudaGraphInstantiate(&out->exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return bfail(b, COLA_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
   return COLA_OK;
 }
 
-static int batch_launch(cola_batch* b, int C, int cap) {
-  const int n = b->step;
-  auto key = std::make_pair(C, cap);
+static int batch_graph(cola_batch* b, const cola_batch_plan& p, cudaGraphExec_t* ex) {
+  const auto key = std::make_tuple(p.group, p.chains, p.grid_cap);
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
-    cudaGraphExec_t ex = nullptr;
-    int rc = batch_capture(b, n, C, cap, &ex);
-    if (rc != COLA_OK) return rc;
-    it = b->graphs.emplace(key, ex).first;
+    cola_batch::Graph g;
+    int rc = batch_capture(b, b->step, p, &g);
+    if (rc != COLA_OK) {
+      if (g.shifts) cudaFree(g.shifts);
+      return rc;
+    }
+    it = b->graphs.emplace(key, g).first;
   }
+  *ex = it->second.exec;
+  return COLA_OK;
+}
+
+// Profiling: when the first context has stage timing enabled, the groups of
+// the plan are launched directly (no graph) one after another on the batch's
+// stream, so the first group's stage events cover its multi-simulation launches.
+static int batch_eager(cola_batch* b, const cola_batch_plan& p, int n) {
+  std::vector<GroupPlan> groups;
+  std::vector<int64_t> hsh;
+  plan_groups(b, p, groups, hsh);
+  int64_t* dsh = nullptr;
+  if (!hsh.empty()) {
+    BCK(cudaMallocAsync(&dsh, hsh.size() * sizeof(int64_t), b->cap_st));
+    BCK(cudaMemcpyAsync(dsh, hsh.data(), hsh.size() * sizeof(int64_t), cudaMemcpyHostToDevice, b->cap_st));
+  }
+  int rc = COLA_OK;
+  for (GroupPlan& gp : groups) {
+    Multi* ms[5] = {&gp.g.all, &gp.g.unscreened.m, &gp.g.fr_screened.m, &gp.g.dgp_screened.m,
+                    &gp.g.screened.m};
+    for (int q = 0; q < 5; ++q) ms[q]->shift = ms[q]->nb > 1 ? dsh + gp.off[q] : nullptr;
+    cola_ctx* lead = gp.g.lead;
+    cudaStream_t saved = lead->st;
+    lead->st = b->cap_st;
+    set_grid_cap(p.grid_cap);
+    rc = enqueue_group_step(gp.g, n);
+    set_grid_cap(0);
+    lead->st = saved;
+    if (rc != COLA_OK) {
+      b->err = lead->err;
+      break;
+    }
+  }
+  if (dsh) BCK(cudaFreeAsync(dsh, b->cap_st));
+  return rc == COLA_OK ? COLA_OK : bfail(b, rc, "batch step: " + b->err);
+}
+
+static int batch_launch(cola_batch* b, const cola_batch_plan& p) {
+  const int n = b->step;
+  const bool eager = b->ctx[0]->prof;
+  cudaGraphExec_t ex = nullptr;
+  if (!eager) CHECK_RC(batch_graph(b, p, &ex));
   // ordered after earlier work on the caller's stream, and before later work on it
   BCK(cudaEventRecord(b->ev_in, b->st));
   BCK(cudaStreamWaitEvent(b->cap_st, b->ev_in, 0));
-  BCK(cudaGraphLaunch(it->second, b->cap_st));
+  if (eager) CHECK_RC(batch_eager(b, p, n));
+  else BCK(cudaGraphLaunch(ex, b->cap_st));
   BCK(cudaEventRecord(b->ev_out, b->cap_st));
   BCK(cudaStreamWaitEvent(b->st, b->ev_out, 0));
   b->step = n + 1;
-  for (cola_ctx* ctx : b->ctx) ctx->step = n + 1;
+  for (cola_ctx* ctx : b->ctx) {
+    ctx->step = n + 1;
+    ctx->hh.step = n + 1;
+  }
   // later per-context calls on the contexts' own streams see the step
   for (cola_ctx* ctx : b->ctx)
     if (ctx->st != b->st) BCK(cudaStreamWaitEvent(ctx->st, b->ev_out, 0));
   return COLA_OK;
 }
 
-int cola_batch_create(cola_ctx* const* ctxs, int32_t n, int32_t chains, void* stream,
+int cola_batch_create(cola_ctx* const* ctxs, int32_t n, const cola_batch_plan* plan, void* stream,
                       cola_batch** out) {
   if (!out) return fail(nullptr, COLA_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!ctxs || n < 1) return fail(nullptr, COLA_EINVAL, "need n >= 1 contexts");
+  if (!ctxs || n < 1 || n > 65535) return fail(nullptr, COLA_EINVAL, "need 1 <= n <= 65535 contexts");
   for (int i = 0; i < n; ++i) {
     const cola_ctx* c = ctxs[i];
     if (!c) return fail(nullptr, COLA_EINVAL, "NULL context in batch");
     if (!c->ic_done) return fail(nullptr, COLA_ESTATE, "every context of a batch needs cola_ic");
     if (c->cfg.nsteps != ctxs[0]->cfg.nsteps || c->step != ctxs[0]->step)
       return fail(nullptr, COLA_EINVAL, "contexts of a batch need equal nsteps and steps done");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return fail(nullptr, COLA_EINVAL, "a context appears twice in the batch");
   }
   cola_batch* b = new cola_batch();
   b->ctx.assign(ctxs, ctxs + n);
   b->st = static_cast<cudaStream_t>(stream);
   b->step = ctxs[0]->step;
-  b->chains = chains > 0 ? std::min<int>(chains, n) : std::min(n, 32);
-  const int maxc = n;
+  b->uniform = true;
+  for (int i = 1; i < n; ++i) b->uniform = b->uniform && same_shape(ctxs[0], ctxs[i]);
+  b->plan = normal_plan(b, plan ? *plan : cola_batch_plan{0, 1, 0});
   auto bail = [&](cudaError_t e) {
     g_err = std::string("cola_batch_create: ") + cudaGetErrorString(e);
     cola_batch_free(b);
@@ -1059,16 +1403,6 @@ int cola_batch_create(cola_ctx* const* ctxs, int32_t n, int32_t chains, void* st
   if (e != cudaSuccess) return bail(e);
   e = cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking);
   if (e != cudaSuccess) return bail(e);
-  for (int c = 0; c < maxc; ++c) {
-    cudaStream_t s = nullptr;
-    cudaEvent_t ev = nullptr;
-    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return bail(e);
-    b->chain_st.push_back(s);
-    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e != cudaSuccess) return bail(e);
-    b->join.push_back(ev);
-  }
   // work already queued on the contexts' own streams precedes the first batch step
   for (cola_ctx* ctx : b->ctx) {
     if (ctx->st == b->st) continue;
@@ -1080,64 +1414,139 @@ int cola_batch_create(cola_ctx* const* ctxs, int32_t n, int32_t chains, void* st
   return COLA_OK;
 }
 
+int cola_batch_set_plan(cola_batch* b, const cola_batch_plan* plan) {
+  if (!b || !plan) return fail(nullptr, COLA_EINVAL, "batch or plan is NULL");
+  b->plan = normal_plan(b, *plan);
+  return COLA_OK;
+}
+
+int cola_batch_get_plan(const cola_batch* b, cola_batch_plan* out) {
+  if (!b || !out) return fail(nullptr, COLA_EINVAL, "batch or out is NULL");
+  *out = b->plan;
+  return COLA_OK;
+}
+
 int cola_batch_step(cola_batch* b, int32_t nsteps) {
   if (!b) return fail(nullptr, COLA_EINVAL, "batch is NULL");
   const int total = b->ctx[0]->cfg.nsteps;
   if (nsteps < 0) nsteps = total - b->step;
   if (b->step + nsteps > total) return bfail(b, COLA_EINVAL, "past the last step");
-  for (int i = 0; i < nsteps; ++i) {
-    int rc = batch_launch(b, b->chains, b->cap);
-    if (rc != COLA_OK) return rc;
-  }
+  for (int i = 0; i < nsteps; ++i) CHECK_RC(batch_launch(b, b->plan));
   return COLA_OK;
 }
 
-int cola_batch_autotune(cola_batch* b, int32_t max_steps, int32_t* chains_out, int32_t* cap_out) {
+int cola_batch_autotune(cola_batch* b, int32_t max_steps, cola_batch_plan* best_out) {
   if (!b) return fail(nullptr, COLA_EINVAL, "batch is NULL");
   const int n = (int)b->ctx.size();
   const int total = b->ctx[0]->cfg.nsteps;
-  // (chains, grid cap): capped grids let kernels of different chains share the SMs
-  std::vector<std::pair<int, int>> cand;
   const int sms = 152;
-  for (auto ck : std::vector<std::pair<int, int>>{{32, sms}, {64, sms / 2}, {16, 2 * sms},
-                                                   {128, sms / 4}, {8, 0}, {32, 0}})
-    cand.push_back({std::min(n, ck.first), ck.second});
+  std::vector<cola_batch_plan> cand;
+  if (b->uniform) {
+    // one group over everything; halves and quarters on concurrent chains;
+    // small groups on many chains with a capped grid (more on-chip reuse)
+    cand = {{n, 1, 0}, {(n + 1) / 2, 2, 0}, {(n + 3) / 4, 4, 0}, {(n + 7) / 8, 4, 0},
+            {std::max(1, n / 32), 8, sms}, {1, 32, sms}};
+  } else {
+    cand = {{1, 32, sms}, {1, 64, sms / 2}, {1, 16, 2 * sms}, {1, 128, sms / 4}, {1, 8, 0}, {1, 32, 0}};
+  }
+  std::vector<cola_batch_plan> plans;
+  for (const auto& c : cand) {
+    const cola_batch_plan p = normal_plan(b, c);
+    bool dup = false;
+    for (const auto& q : plans) dup = dup || (q.group == p.group && q.chains == p.chains && q.grid_cap == p.grid_cap);
+    if (!dup) plans.push_back(p);
+  }
   const int budget = std::min<int>(max_steps > 0 ? max_steps : total, total - b->step);
   double best = 1e300;
-  int bestC = b->chains, bestK = b->cap, used = 0;
+  cola_batch_plan bestp = b->plan;
+  int used = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
-  for (const auto& ck : cand) {
+  int rc = COLA_OK;
+  for (const auto& p : plans) {
     if (used >= budget) break;
     // capture outside the timed region, then time one launch (one real step)
     cudaGraphExec_t ex = nullptr;
-    auto key = std::make_pair(ck.first, ck.second);
-    if (!b->graphs.count(key)) {
-      int rc = batch_capture(b, b->step, ck.first, ck.second, &ex);
-      if (rc != COLA_OK) return rc;
-      b->graphs.emplace(key, ex);
-    }
-    BCK(cudaEventRecord(e0, b->st));
-    int rc = batch_launch(b, ck.first, ck.second);
-    if (rc != COLA_OK) return rc;
-    BCK(cudaEventRecord(e1, b->st));  // the caller's stream waits for the graph
-    BCK(cudaEventSynchronize(e1));
+    rc = batch_graph(b, p, &ex);
+    if (rc != COLA_OK) break;
+    cudaError_t e = cudaEventRecord(e0, b->st);
+    if (e == cudaSuccess) rc = batch_launch(b, p);
+    if (rc != COLA_OK) break;
+    if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);  // the caller's stream waits for the graph
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
-    BCK(cudaEventElapsedTime(&ms, e0, e1));
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rc = bfail(b, COLA_ECUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
+      break;
+    }
     ++used;
     if (ms < best) {
       best = ms;
-      bestC = ck.first;
-      bestK = ck.second;
+      bestp = p;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->chains = bestC;
-  b->cap = bestK;
-  if (chains_out) *chains_out = bestC;
-  if (cap_out) *cap_out = bestK;
+  if (rc != COLA_OK) return rc;
+  b->plan = bestp;
+  if (best_out) *best_out = bestp;
+  return COLA_OK;
+}
+
+int cola_batch_pk(cola_batch* b, int32_t nbins, double* k, double* pk, int64_t* nmodes) {
+  if (!b) return fail(nullptr, COLA_EINVAL, "batch is NULL");
+  if (nbins < 1 || nbins > kMaxBins) return bfail(b, COLA_EINVAL, "nbins out of range 1..2000");
+  const int n = (int)b->ctx.size();
+  if (!b->uniform) {
+    for (int i = 0; i < n; ++i) {
+      cola_ctx* c = b->ctx[i];
+      int rc = cola_pk(c, nbins, k ? k + (size_t)i * nbins : nullptr, pk ? pk + (size_t)i * nbins : nullptr,
+                       nmodes ? nmodes + (size_t)i * nbins : nullptr);
+      if (rc != COLA_OK) return bfail(b, rc, c->err);
+    }
+    return COLA_OK;
+  }
+  cola_ctx* lead = b->ctx[0];
+  const int N = lead->Nm;
+  const int64_t stride = 3 * (int64_t)kMaxBins;
+  // [n][stride] accumulators, then the n shifts
+  if (!b->pk_acc) BCK(cudaMalloc(&b->pk_acc, ((size_t)n * stride + n) * sizeof(double)));
+  std::vector<int64_t> hsh(n);
+  const char* base = static_cast<const char*>(lead->allocs[0]);
+  for (int i = 0; i < n; ++i) hsh[i] = static_cast<const char*>(b->ctx[i]->allocs[0]) - base;
+  int64_t* dsh = n > 1 ? reinterpret_cast<int64_t*>(b->pk_acc + (size_t)n * stride) : nullptr;
+  cudaStream_t st = b->st;
+  if (dsh) BCK(cudaMemcpyAsync(dsh, hsh.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  Multi m;
+  m.shift = dsh;
+  m.nb = n;
+  const PartParams pp = part_params(lead);
+  const ForceParams fp = force_params(lead, lead->a[lead->step]);
+  BCK(zero_f32(lead->rho, lead->M, st, m));
+  BCK(part_deposit(pp, lead->s[0], lead->s[1], lead->s[2], lead->rho, lead->P, st, m));
+  BCK(fft_xr2c(N, lead->rho, lead->Cw, fp.inv_rhobar, -1.f, lead->tw_nm, st, m));
+  BCK(fft_col(N, lead->Cw, 1, false, lead->tw_nm, st, m));
+  BCK(fft_col(N, lead->Cw, 2, false, lead->tw_nm, st, m));
+  BCK(cudaMemset2DAsync(b->pk_acc, stride * sizeof(double), 0, 3 * nbins * sizeof(double), n, st));
+  const double L = lead->L, N3 = (double)N * N * N;
+  BCK(pk_bin(N, lead->Cw, nbins, b->pk_acc, L * L * L / (N3 * N3), st, m, stride));
+  std::vector<double> h((size_t)n * 3 * nbins);
+  BCK(cudaMemcpy2DAsync(h.data(), 3 * nbins * sizeof(double), b->pk_acc, stride * sizeof(double),
+                        3 * nbins * sizeof(double), n, cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  const double kf = 2.0 * kPi / L;
+  for (int i = 0; i < n; ++i) {
+    const double* r = h.data() + (size_t)i * 3 * nbins;
+    for (int q = 0; q < nbins; ++q) {
+      const double cnt = r[q];
+      const size_t o = (size_t)i * nbins + q;
+      if (k) k[o] = cnt > 0 ? r[2 * nbins + q] / cnt * kf : NAN;
+      if (pk) pk[o] = cnt > 0 ? r[nbins + q] / cnt : NAN;
+      if (nmodes) nmodes[o] = (int64_t)llround(cnt);
+    }
+  }
   return COLA_OK;
 }
 
@@ -1147,7 +1556,11 @@ void cola_batch_free(cola_batch* b) {
   if (!b) return;
   if (b->cap_st) cudaStreamSynchronize(b->cap_st);
   cudaStreamSynchronize(b->st);
-  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : b->graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.shifts) cudaFree(kv.second.shifts);
+  }
+  if (b->pk_acc) cudaFree(b->pk_acc);
   if (b->cap_st) cudaStreamDestroy(b->cap_st);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
@@ -1223,15 +1636,10 @@ int cola_host_growth(const cola_config* cfg, const cola_model* model, double* ou
 
 int64_t cola_device_bytes(const cola_config* cfg) {
   if (validate_cfg(cfg, nullptr) != COLA_OK) return -1;
-  const int64_t P = (int64_t)cfg->Np * cfg->Np * cfg->Np, M = (int64_t)cfg->Nmesh * cfg->Nmesh * cfg->Nmesh;
-  const int64_t hp = half_elems(cfg->Np), hm = half_elems(cfg->Nmesh);
-  int64_t b = 9 * P * 4;                                      // s, dv, acc
-  b += 2 * hp * 8 + (cfg->seed_precision ? 2 * hp * 4 : 0);  // seeds
-  b += 6 * hp * 8 + 6 * P * 4;                                // LPT work
-  b += M * 4 + 5 * hm * 8 + 3 * M * 4;                        // mesh
-  b += 2 * (int64_t)(cfg->nsteps + 1) * cfg->nk_table * 16;   // tables
-  b += 3 * (int64_t)kMaxBins * 8 + 64 * 4 + (cfg->Np + cfg->Nmesh) * 8;
-  return b;
+  cola_ctx probe;
+  Layout lay;
+  context_layout(&probe, *cfg, lay);
+  return (int64_t)lay.size;
 }
 
 int cola_host_timesteps(const cola_config* cfg, double* out) {

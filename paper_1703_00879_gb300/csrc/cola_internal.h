@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <vector_types.h>
 
 #include <string>
 
@@ -11,6 +12,36 @@ namespace cola {
 // 16 so that column tiles of 2..16 elements never straddle a row.
 inline int64_t half_pitch(int N) { return ((N / 2 + 1 + 15) / 16) * 16; }
 inline int64_t half_elems(int N) { return (int64_t)N * N * half_pitch(N); }
+
+struct ForceParams;
+
+// Per-simulation device header: where its per-step parameters live and how many
+// steps it has done.  Kernels that serve every step read their parameters
+// through it, so one captured launch sequence serves every step.
+struct SimHeader {
+  const ForceParams* dfp;  // [nsteps]: force parameters at a_{n+1}
+  const float* ddt;        // [nsteps][3]: half kick, drift, half kick time integrals
+  const float4* tab;       // [nsteps+1][nk] LPT reweight table (row 0: a_ini, row n+1: step n)
+  const float4* vtab;      // [nsteps+1][nk] velocity table
+  int step;                // steps done
+  float seed_scale[2];     // dequantisation scales of the 16-bit seeds
+};
+
+// One launch over several simulations of one shape.  Each simulation's
+// buffers sit at the same offsets of its own allocation, so simulation b's
+// pointers are simulation 0's moved by shift[b] bytes.  shift == nullptr: a
+// single simulation.  Shared read-only tables (twiddles) are never moved;
+// per-simulation parameters are reached through the moved SimHeader.
+struct Multi {
+  const int64_t* shift = nullptr;
+  int nb = 1;
+};
+
+template <class T>
+__host__ __device__ __forceinline__ T* moved(T* p, int64_t by) {
+  return p ? reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(p) + by) : p;
+}
+__device__ __forceinline__ int64_t shift_of(const Multi& m, int b) { return m.shift ? m.shift[b] : 0; }
 
 // Parameters of one force evaluation (App. B field equation).
 struct ForceParams {
@@ -25,29 +56,43 @@ struct ForceParams {
   float norm;        // 1 / N^3
   int model;         // 0 LCDM, 1 f(R), 2 nDGP
   int screened;      // 1: screened fifth force
-  // When src is set, kernels replace every value above by src[*step] (the
-  // parameters of the current step, kept on the device so one captured
-  // launch sequence serves every step).
-  const ForceParams* src;
-  const int* step;
+  // When hdr is set, kernels replace every value above by the current step's
+  // entry hdr->dfp[hdr->step] of the simulation (hdr moved by its shift).
+  const SimHeader* hdr;
 };
 
-__device__ __forceinline__ void resolve(ForceParams& fp) {
-  if (fp.src) fp = fp.src[*fp.step];
+__device__ __forceinline__ void resolve(ForceParams& fp, int64_t by) {
+  if (fp.hdr) {
+    const SimHeader* h = moved(fp.hdr, by);
+    fp = h->dfp[h->step];
+  }
 }
+
 
 // Parameters of the per-k LPT reweight (Sec. 4.1): table of float4 per log-k node.
 struct LptParams {
-  const float4* tab;  // row 0 of the table; the row used is row0 + (*step if step)
-  const int* step;
-  int row0;
+  const SimHeader* hdr;  // table and seed scales of the simulation (moved per simulation)
+  int vel;               // 0: hdr->tab, 1: hdr->vtab
+  int row0;              // table row; plus hdr->step when add_step
+  int add_step;
+  const float4* row;     // resolved table row (set on the device when hdr is resolved)
+  float scale[2];        // resolved seed scales
   float lnk0, inv_dlnk;
   int nk;
   float kf;           // 2 pi / L
   float norm;         // 1 / Np^3
-  float seed_scale1, seed_scale2;  // dequantisation scales of phi1, phi2 (1 for fp32)
   int seed_prec;      // 0 fp32, 1 bf16, 2 fp16
 };
+
+__device__ __forceinline__ void resolve(LptParams& lp, int64_t by) {
+  if (lp.hdr) {
+    const SimHeader* h = moved(lp.hdr, by);
+    lp.row = (lp.vel ? h->vtab : h->tab) + (size_t)(lp.row0 + (lp.add_step ? h->step : 0)) * lp.nk;
+    lp.scale[0] = h->seed_scale[0];
+    lp.scale[1] = h->seed_scale[1];
+    lp.hdr = nullptr;
+  }
+}
 
 // Lattice/particle parameters.
 struct PartParams {
@@ -59,67 +104,77 @@ struct PartParams {
 // ------------------------------------------------------------------ FFT passes
 // All launchers return cudaGetLastError() of their launch.
 cudaError_t fft_xr2c(int N, const float* in, float2* out, float scale, float offset,
-                     const float2* tw, cudaStream_t s);
+                     const float2* tw, cudaStream_t s, Multi m = {});
 cudaError_t fft_xc2r(int N, const float2* in, float* out, float kfs, const float2* tw,
-                     cudaStream_t s);
+                     cudaStream_t s, Multi m = {});
 // up to six independent c2r row passes in one launch
 cudaError_t fft_xc2r_multi(int N, int njobs, const float2* const* in, float* const* out,
-                           const float* kfs, const float2* tw, cudaStream_t s);
+                           const float* kfs, const float2* tw, cudaStream_t s, Multi m = {});
 // axis 1 = y, 2 = z; in place
-cudaError_t fft_col(int N, float2* data, int axis, bool inv, const float2* tw, cudaStream_t s);
+cudaError_t fft_col(int N, float2* data, int axis, bool inv, const float2* tw, cudaStream_t s,
+                    Multi m = {});
 // y inverse pass producing the plain transform (out_plain may alias in) and the
 // transform of (i kfs f_y) times the input (out_deriv).
 cudaError_t fft_yinv2(int N, const float2* in, float2* out_plain, float2* out_deriv, float kfs,
-                      const float2* tw, cudaStream_t s);
+                      const float2* tw, cudaStream_t s, Multi m = {});
 // Screening field: forward z of delta (after x, y) -> delta(k) stored in dk_out;
 // Phi_N(k) (f(R)) or W(kR) delta(k) (nDGP) -> inverse z -> w_out.
 cudaError_t mesh_z_screen_field(int N, const float2* in, float2* dk_out, float2* w_out,
-                                const ForceParams& fp, const float2* tw, cudaStream_t s);
+                                const ForceParams& fp, const float2* tw, cudaStream_t s,
+                                Multi m = {});
 // S = delta eps: c2r of the screening field rows, eps, times delta from rho, r2c.
 cudaError_t mesh_x_screen_source(int N, const float2* w_in, const float* rho, float2* s_out,
-                                 const ForceParams& fp, const float2* tw, cudaStream_t s);
+                                 const ForceParams& fp, const float2* tw, cudaStream_t s,
+                                 Multi m = {});
 // Forward z of the source (S or delta), Phi_tot(k) and -i kz Phi_tot, inverse z.
 // dk may be null when unscreened; dk_keep (optional) receives the forward
 // spectrum of `in` when unscreened.
 cudaError_t mesh_z_force(int N, const float2* in, const float2* dk, float2* phi_out,
                          float2* phiz_out, float2* dk_keep, const ForceParams& fp,
-                         const float2* tw, cudaStream_t s);
+                         const float2* tw, cudaStream_t s, Multi m = {});
 // LPT: phi1, phi2 -> (c1 phi1 + c2 phi2), i kz (...), (e1 phi1 + e2 phi2), i kz (...),
 // each inverse-transformed along z.  phi1/phi2 point to float2 (fp32) or
 // 2 x 16-bit pairs (bf16/fp16) according to lp.seed_prec.
 cudaError_t lpt_z(int N, const void* phi1, const void* phi2, float2* o0, float2* o1, float2* o2,
-                  float2* o3, const LptParams& lp, const float2* tw, cudaStream_t s);
+                  float2* o3, const LptParams& lp, const float2* tw, cudaStream_t s,
+                  Multi m = {});
 
 // ------------------------------------------------------------------ particles
 cudaError_t part_deposit(const PartParams& pp, const float* sx, const float* sy, const float* sz,
-                         float* rho, int64_t P, cudaStream_t s);
-// Kick/drift time integrals: dt[3 * (*step) + j] when dt is set (j = 0 first
-// half kick, 1 drift, 2 second half kick), else the given values.
+                         float* rho, int64_t P, cudaStream_t s, Multi m = {});
+// Kick/drift time integrals: hdr->ddt[3 hdr->step + j] of the simulation when
+// hdr is set (j = 0 first half kick, 1 drift, 2 second half kick), else the
+// given values.
 struct StepDt {
-  const float* dt;
-  const int* step;
+  const SimHeader* hdr;
   float dtk, dtd;
 };
 cudaError_t part_drift_deposit(const PartParams& pp, float* sx, float* sy, float* sz, float* vx,
                                float* vy, float* vz, const float* ax, const float* ay,
                                const float* az, const float* dpx, const float* dpy,
                                const float* dpz, float* rho, StepDt dt, int64_t P,
-                               cudaStream_t s);
+                               cudaStream_t s, Multi m = {});
 cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float* sy,
                              const float* sz, float* vx, float* vy, float* vz, float* ax,
                              float* ay, float* az, const float* Ax, const float* Ay,
                              const float* Az, const float* Fx, const float* Fy, const float* Fz,
-                             StepDt dt, int64_t P, cudaStream_t s);
-// *step += 1 (end of a step)
-cudaError_t step_advance(int* step, cudaStream_t s);
+                             StepDt dt, int64_t P, cudaStream_t s, Multi m = {});
+// hdr->step += 1 (end of a step)
+cudaError_t step_advance(SimHeader* hdr, cudaStream_t s, Multi m = {});
+// hdr = v (one simulation)
+cudaError_t set_header(SimHeader* hdr, const SimHeader& v, cudaStream_t s);
+// n floats at p set to zero in every simulation
+cudaError_t zero_f32(float* p, int64_t n, cudaStream_t s, Multi m = {});
 cudaError_t part_snapshot(const PartParams& pp, const float* sx, const float* sy, const float* sz,
                           const float* vx, const float* vy, const float* vz, const float* lx,
                           const float* ly, const float* lz, float vscale, float* pos, float* vel,
                           int64_t P, cudaStream_t s);
 cudaError_t pos_deposit(int Nm, float cellscale, const float* pos, int64_t n, float* rho,
                         cudaStream_t s);
+// acc_stride > 0: simulation b accumulates into acc + b acc_stride (acc not
+// moved); 0: into acc moved by its shift.
 cudaError_t pk_bin(int N, const float2* dk, int nbins, double* acc, double norm,
-                   cudaStream_t s);
+                   cudaStream_t s, Multi m = {}, int64_t acc_stride = 0);
 
 // ------------------------------------------------------------------ initial conditions
 struct EHDev {

@@ -43,13 +43,16 @@ constexpr int col_tw(int N, int NBUF) {
   return (N == 1024 && NBUF == 1) ? 8
          : (4096 / (N * NBUF)) < 4 ? 4 : ((4096 / (N * NBUF)) > 16 ? 16 : 4096 / (N * NBUF));
 }
-// Rows per x-pass tile.
-constexpr int row_tw(int N) { return N <= 512 ? 16 : 8; }
+// Rows per x-pass tile: about 8192 staged values per tile (~64 KB in flight
+// per CTA pair), 8..64 rows.
+constexpr int row_tw(int N) { return 8192 / N < 8 ? 8 : (8192 / N > 64 ? 64 : 8192 / N); }
 
 // Resident CTAs per SM that the shared memory of a kernel allows (1..3); used
-// as the register bound of __launch_bounds__ so registers never limit occupancy below it.
-constexpr int blocks_for_smem(size_t bytes) {
-  return bytes > 112 * 1024 ? 1 : 2;
+// as the register bound of __launch_bounds__ so registers never limit occupancy
+// below it.  Transforms of 512 points and more, and the force-side z passes
+// (two transforms per tile), would spill at 3 and take at most 2.
+constexpr int blocks_for_smem(size_t bytes, int N) {
+  return bytes > 112 * 1024 ? 1 : (bytes > 72 * 1024 || N >= 512 ? 2 : 3);
 }
 constexpr size_t col_smem_c(int N, int NBUF) {
   return (N + 2 * (size_t)N * NBUF * col_tw(N, NBUF)) * 8;
@@ -173,12 +176,18 @@ __device__ __forceinline__ float kk2(int ix, int iy, int iz, int N, float kf) {
   return kf * kf * (fx * fx + fy * fy + fz * fz);
 }
 
-// Column geometry: tile t -> (outer index o, column block tx); base = o * so + c0.
+// Column geometry: tile t -> (simulation b, outer index o, column block tx);
+// base = o * so + c0 and `by` = the byte shift of simulation b's buffers.
 template <int N, int TW>
 struct ColGeo {
   static constexpr int ntx = (N / 2) / TW + 1;
+  static constexpr int64_t tps = (int64_t)N * ntx;  // tiles per simulation
   int64_t so, sn;
-  __device__ __forceinline__ void tile(int64_t t, int& o, int& c0, int64_t& base) const {
+  Multi m;
+  __device__ __forceinline__ void tile(int64_t t, int& o, int& c0, int64_t& base, int64_t& by) const {
+    const int b = (int)(t / tps);
+    t -= (int64_t)b * tps;
+    by = shift_of(m, b);
     o = (int)(t / ntx);
     c0 = (int)(t % ntx) * TW;
     base = (int64_t)o * so + c0;
@@ -222,21 +231,21 @@ struct OpCol {
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
     int o, c0;
-    int64_t base;
-    geo.tile(t, o, c0, base);
-    col_issue<N, TW, TW>(buf, 0, data, base, geo.sn, c0);
+    int64_t base, by;
+    geo.tile(t, o, c0, base, by);
+    col_issue<N, TW, TW>(buf, 0, moved(data, by), base, geo.sn, c0);
   }
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
     int o, c0;
-    int64_t base;
-    geo.tile(t, o, c0, base);
+    int64_t base, by;
+    geo.tile(t, o, c0, base, by);
     fft_tile<N, TW, TW, NT, INV>(buf, tw);
-    col_store<N, TW, TW>(buf, 0, data, base, geo.sn, c0);
+    col_store<N, TW, TW>(buf, 0, moved(data, by), base, geo.sn, c0);
   }
 };
 
 template <int N, int TW, bool INV>
-__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1))) k_col(OpCol<N, TW, INV> op, const float2* __restrict__ twg,
+__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1), N)) k_col(OpCol<N, TW, INV> op, const float2* __restrict__ twg,
                                             int64_t ntiles) {
   col_pipeline<N, N * TW>(op, twg, ntiles);
 }
@@ -251,15 +260,15 @@ struct OpYinv2 {
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
     int o, c0;
-    int64_t base;
-    geo.tile(t, o, c0, base);
-    col_issue<N, TW, 2 * TW>(buf, 0, in, base, geo.sn, c0);
+    int64_t base, by;
+    geo.tile(t, o, c0, base, by);
+    col_issue<N, TW, 2 * TW>(buf, 0, moved(in, by), base, geo.sn, c0);
   }
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
     constexpr int TP = 2 * TW;
     int o, c0;
-    int64_t base;
-    geo.tile(t, o, c0, base);
+    int64_t base, by;
+    geo.tile(t, o, c0, base, by);
     for (int e = threadIdx.x; e < N * TW; e += NT) {
       const int c = e % TW, n = e / TW;
       const float f = (n == N / 2) ? 0.f : kfs * (float)freq_index(n, N);
@@ -267,13 +276,13 @@ struct OpYinv2 {
     }
     __syncthreads();
     fft_tile<N, TP, TP, NT, true>(buf, tw);
-    col_store<N, TW, TP>(buf, 0, outp, base, geo.sn, c0);
-    col_store<N, TW, TP>(buf, 1, outd, base, geo.sn, c0);
+    col_store<N, TW, TP>(buf, 0, moved(outp, by), base, geo.sn, c0);
+    col_store<N, TW, TP>(buf, 1, moved(outd, by), base, geo.sn, c0);
   }
 };
 
 template <int N, int TW>
-__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 2))) k_yinv2(OpYinv2<N, TW> op, const float2* __restrict__ twg,
+__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 2), N)) k_yinv2(OpYinv2<N, TW> op, const float2* __restrict__ twg,
                                               int64_t ntiles) {
   col_pipeline<N, N * 2 * TW>(op, twg, ntiles);
 }
@@ -288,20 +297,23 @@ struct OpZScreenField {
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
     int o, c0;
-    int64_t base;
-    geo.tile(t, o, c0, base);
-    col_issue<N, TW, TW>(buf, 0, in, base, geo.sn, c0);
+    int64_t base, by;
+    geo.tile(t, o, c0, base, by);
+    col_issue<N, TW, TW>(buf, 0, moved(in, by), base, geo.sn, c0);
   }
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
     int iy, c0;
-    int64_t base;
-    geo.tile(t, iy, c0, base);
+    int64_t base, by;
+    geo.tile(t, iy, c0, base, by);
+    ForceParams fp = this->fp;
+    resolve(fp, by);
+    float2* dko = moved(dk_out, by);
     fft_tile_call<N, TW, TW, NT, false>(buf, tw);
 #pragma unroll 2
     for (int e = threadIdx.x; e < N * TW; e += NT) {
       const int c = e % TW, n = e / TW;
       const float2 v = buf[n * TW + c];
-      if (c0 + c < N / 2 + 1) dk_out[base + (int64_t)n * geo.sn + c] = v;
+      if (c0 + c < N / 2 + 1) dko[base + (int64_t)n * geo.sn + c] = v;
       const float k2 = kk2(c0 + c, iy, n, N, fp.kf);
       float m = 0.f;
       if (k2 > 0.f) {
@@ -312,15 +324,15 @@ struct OpZScreenField {
     }
     __syncthreads();
     fft_tile_call<N, TW, TW, NT, true>(buf, tw);
-    col_store<N, TW, TW>(buf, 0, w_out, base, geo.sn, c0);
+    col_store<N, TW, TW>(buf, 0, moved(w_out, by), base, geo.sn, c0);
   }
 };
 
 template <int N, int TW, int MODEL>
-__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1))) k_z_screen_field(OpZScreenField<N, TW, MODEL> op,
+__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1), N) < 2 ? 1 : 2) k_z_screen_field(OpZScreenField<N, TW, MODEL> op,
                                                        const float2* __restrict__ twg,
                                                        int64_t ntiles) {
-  resolve(op.fp);
+  if (!op.geo.m.shift) resolve(op.fp, 0);  // one simulation: once per launch
   col_pipeline<N, N * TW>(op, twg, ntiles);
 }
 
@@ -339,21 +351,23 @@ struct OpZForce {
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
     int o, c0;
-    int64_t base;
-    geo.tile(t, o, c0, base);
-    col_issue<N, TW, TW>(buf, 0, in, base, geo.sn, c0);
+    int64_t base, by;
+    geo.tile(t, o, c0, base, by);
+    col_issue<N, TW, TW>(buf, 0, moved(in, by), base, geo.sn, c0);
   }
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
     int iy, c0;
-    int64_t base;
-    geo.tile(t, iy, c0, base);
+    int64_t base, by;
+    geo.tile(t, iy, c0, base, by);
+    ForceParams fp = this->fp;
+    resolve(fp, by);
     float2* ph = extra;  // delta(k) of the tile, then Phi_tot(k), N x TW
     if (SCREENED) {
-      col_issue<N, TW, TW>(ph, 0, dk, base, geo.sn, c0);  // lands while S is transformed
+      col_issue<N, TW, TW>(ph, 0, moved(dk, by), base, geo.sn, c0);  // lands while S is transformed
       cp_async_commit();
     }
     fft_tile_call<N, TW, TW, NT, false>(buf, tw);
-    if (KEEP) col_store<N, TW, TW>(buf, 0, dk_keep, base, geo.sn, c0);
+    if (KEEP) col_store<N, TW, TW>(buf, 0, moved(dk_keep, by), base, geo.sn, c0);
     if (SCREENED) {
       cp_async_wait<0>();
       __syncthreads();
@@ -379,7 +393,7 @@ struct OpZForce {
     }
     __syncthreads();
     fft_tile_call<N, TW, TW, NT, true>(buf, tw);
-    col_store<N, TW, TW>(buf, 0, phi_out, base, geo.sn, c0);
+    col_store<N, TW, TW>(buf, 0, moved(phi_out, by), base, geo.sn, c0);
     __syncthreads();
 #pragma unroll 2
     for (int i = 0; i < E; ++i) {
@@ -390,14 +404,14 @@ struct OpZForce {
     }
     __syncthreads();
     fft_tile_call<N, TW, TW, NT, true>(buf, tw);
-    col_store<N, TW, TW>(buf, 0, phiz_out, base, geo.sn, c0);
+    col_store<N, TW, TW>(buf, 0, moved(phiz_out, by), base, geo.sn, c0);
   }
 };
 
 template <int N, int TW, bool SCREENED, bool KEEP>
-__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1) + (size_t)N * TW * 8)) k_z_force(
+__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1) + (size_t)N * TW * 8, N) < 2 ? 1 : 2) k_z_force(
     OpZForce<N, TW, SCREENED, KEEP> op, const float2* __restrict__ twg, int64_t ntiles) {
-  resolve(op.fp);
+  if (!op.geo.m.shift) resolve(op.fp, 0);  // one simulation: once per launch
   col_pipeline<N, N * TW>(op, twg, ntiles);
 }
 
@@ -424,29 +438,33 @@ struct OpLptZ {
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
     int o, c0;
-    int64_t base;
-    geo.tile(t, o, c0, base);
+    int64_t base, by;
+    geo.tile(t, o, c0, base, by);
     if constexpr (PREC == 0) {
-      col_issue<N, TW, 4 * TW>(buf, 0, static_cast<const float2*>(phi1), base, geo.sn, c0);
-      col_issue<N, TW, 4 * TW>(buf, 1, static_cast<const float2*>(phi2), base, geo.sn, c0);
+      col_issue<N, TW, 4 * TW>(buf, 0, moved(static_cast<const float2*>(phi1), by), base, geo.sn, c0);
+      col_issue<N, TW, 4 * TW>(buf, 1, moved(static_cast<const float2*>(phi2), by), base, geo.sn, c0);
     } else {
       // raw 16-bit pairs staged in the (still unused) output sub-blocks 2 and 3
       uint32_t* rb = reinterpret_cast<uint32_t*>(buf);
-      col_issue_raw<N, TW>(rb, 0, static_cast<const uint32_t*>(phi1), base, geo.sn, c0);
-      col_issue_raw<N, TW>(rb, 1, static_cast<const uint32_t*>(phi2), base, geo.sn, c0);
+      col_issue_raw<N, TW>(rb, 0, moved(static_cast<const uint32_t*>(phi1), by), base, geo.sn, c0);
+      col_issue_raw<N, TW>(rb, 1, moved(static_cast<const uint32_t*>(phi2), by), base, geo.sn, c0);
     }
   }
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
     constexpr int TP = 4 * TW;
     int iy, c0;
-    int64_t base;
-    geo.tile(t, iy, c0, base);
+    int64_t base, by;
+    geo.tile(t, iy, c0, base, by);
+    LptParams lp = this->lp;
+    resolve(lp, by);  // no-op when resolved once for the launch
+    const float4* tab = lp.row;
     if constexpr (PREC != 0) {
       const uint32_t* rb = reinterpret_cast<const uint32_t*>(buf);
+      const float sc1 = lp.scale[0], sc2 = lp.scale[1];
       for (int e = threadIdx.x; e < N * TW; e += NT) {
         const int c = e % TW, n = e / TW;
-        const float2 a = dequant<PREC>(rb[8 * n * TW + 4 * TW + c], lp.seed_scale1);
-        const float2 b = dequant<PREC>(rb[8 * n * TW + 5 * TW + c], lp.seed_scale2);
+        const float2 a = dequant<PREC>(rb[8 * n * TW + 4 * TW + c], sc1);
+        const float2 b = dequant<PREC>(rb[8 * n * TW + 5 * TW + c], sc2);
         buf[n * TP + c] = a;
         buf[n * TP + TW + c] = b;
       }
@@ -461,7 +479,7 @@ struct OpLptZ {
         int i0 = (int)floorf(u);
         i0 = min(max(i0, 0), lp.nk - 2);
         const float f = u - (float)i0;
-        const float4 t0 = lp.tab[i0], t1 = lp.tab[i0 + 1];
+        const float4 t0 = tab[i0], t1 = tab[i0 + 1];
         const float c1 = t0.x * (1.f - f) + t1.x * f;
         const float c2 = t0.y * (1.f - f) + t1.y * f;
         const float e1 = t0.z * (1.f - f) + t1.z * f;
@@ -478,17 +496,17 @@ struct OpLptZ {
     }
     __syncthreads();
     fft_tile<N, TP, TP, NT, true>(buf, tw);
-    col_store<N, TW, TP>(buf, 0, o0, base, geo.sn, c0);
-    col_store<N, TW, TP>(buf, 1, o1, base, geo.sn, c0);
-    col_store<N, TW, TP>(buf, 2, o2, base, geo.sn, c0);
-    col_store<N, TW, TP>(buf, 3, o3, base, geo.sn, c0);
+    col_store<N, TW, TP>(buf, 0, moved(o0, by), base, geo.sn, c0);
+    col_store<N, TW, TP>(buf, 1, moved(o1, by), base, geo.sn, c0);
+    col_store<N, TW, TP>(buf, 2, moved(o2, by), base, geo.sn, c0);
+    col_store<N, TW, TP>(buf, 3, moved(o3, by), base, geo.sn, c0);
   }
 };
 
 template <int N, int TW, int PREC>
-__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 4))) k_lpt_z(OpLptZ<N, TW, PREC> op,
+__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 4), N)) k_lpt_z(OpLptZ<N, TW, PREC> op,
                                               const float2* __restrict__ twg, int64_t ntiles) {
-  op.lp.tab += (size_t)(op.lp.row0 + (op.lp.step ? *op.lp.step : 0)) * op.lp.nk;
+  if (!op.geo.m.shift) resolve(op.lp, 0);  // one simulation: once per launch
   col_pipeline<N, N * 4 * TW>(op, twg, ntiles);
 }
 
@@ -599,10 +617,21 @@ __device__ __forceinline__ void put_r2c(float2* buf, const float2* st, float sca
   }
 }
 
+// Row tile t of a multi-simulation launch: simulation t / tps, first row (t mod tps) TWX.
+struct RowTile {
+  int64_t row0, by;
+};
+template <int TWX>
+__device__ __forceinline__ RowTile row_tile(int64_t t, int64_t tps, const Multi& m) {
+  const int b = (int)(t / tps);
+  return RowTile{(t - (int64_t)b * tps) * TWX, shift_of(m, b)};
+}
+
 template <int N, int TWX>
 __global__ void __launch_bounds__(NT, 2) k_xr2c(const float* __restrict__ in, float2* __restrict__ out,
                                                 int64_t P, float scale, float offset,
-                                                const float2* __restrict__ twg, int64_t ntiles) {
+                                                const float2* __restrict__ twg, int64_t ntiles,
+                                                int64_t tps, Multi m) {
   using C = RowCfg<N, TWX>;
   constexpr int M = N / 2;
   extern __shared__ __align__(16) float2 sm[];
@@ -612,28 +641,49 @@ __global__ void __launch_bounds__(NT, 2) k_xr2c(const float* __restrict__ in, fl
   float2* st1 = st0 + C::stage;
   load_tw(tw, twg, N);
   int64_t t = blockIdx.x;
-  if (t < ntiles) stage_real_rows<N, TWX>(st0, in, t * TWX);
+  if (t < ntiles) {
+    const RowTile r = row_tile<TWX>(t, tps, m);
+    stage_real_rows<N, TWX>(st0, moved(in, r.by), r.row0);
+  }
   cp_async_commit();
   int cur = 0;
   for (; t < ntiles; t += gridDim.x) {
     const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) stage_real_rows<N, TWX>(cur ? st0 : st1, in, tn * TWX);
+    if (tn < ntiles) {
+      const RowTile r = row_tile<TWX>(tn, tps, m);
+      stage_real_rows<N, TWX>(cur ? st0 : st1, moved(in, r.by), r.row0);
+    }
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
     put_r2c<N, TWX>(buf, cur ? st1 : st0, scale, offset);
     __syncthreads();
     fft_tile<M, TWX, C::PITCH, NT, false, 2>(buf, tw);
-    row_r2c_store<N, TWX, C::PITCH>(buf, tw, out, t * TWX, P);
+    const RowTile r = row_tile<TWX>(t, tps, m);
+    row_r2c_store<N, TWX, C::PITCH>(buf, tw, moved(out, r.by), r.row0, P);
     __syncthreads();
     cur ^= 1;
   }
   cp_async_wait<0>();
 }
 
+// Tile t of a multi-job, multi-simulation c2r launch: simulation, job, first row.
+struct JobTile {
+  int job;
+  int64_t row0, by;
+};
+__device__ __forceinline__ JobTile job_tile(int64_t t, int64_t tpj, int njobs, int twx,
+                                            const Multi& m) {
+  const int64_t per_sim = tpj * njobs;
+  const int b = (int)(t / per_sim);
+  t -= (int64_t)b * per_sim;
+  return JobTile{(int)(t / tpj), (t % tpj) * twx, shift_of(m, b)};
+}
+
 template <int N, int TWX>
 __global__ void __launch_bounds__(NT, 2) k_xc2r(RowJobs jobs, int64_t P,
-                                                const float2* __restrict__ twg, int64_t tiles_per_job) {
+                                                const float2* __restrict__ twg, int64_t tiles_per_job,
+                                                Multi m) {
   using C = RowCfg<N, TWX>;
   constexpr int M = N / 2;
   extern __shared__ __align__(16) float2 sm[];
@@ -642,20 +692,24 @@ __global__ void __launch_bounds__(NT, 2) k_xc2r(RowJobs jobs, int64_t P,
   float2* st0 = buf + C::fftbuf + (C::fftbuf & 1);
   float2* st1 = st0 + C::stage;
   load_tw(tw, twg, N);
-  const int64_t ntiles = tiles_per_job * jobs.njobs;
+  const int64_t ntiles = tiles_per_job * jobs.njobs * m.nb;
   int64_t t = blockIdx.x;
-  if (t < ntiles)
-    stage_complex_rows<N, TWX>(st0, static_cast<const float2*>(jobs.in[t / tiles_per_job]),
-                               (t % tiles_per_job) * TWX, P);
+  if (t < ntiles) {
+    const JobTile j = job_tile(t, tiles_per_job, jobs.njobs, TWX, m);
+    stage_complex_rows<N, TWX>(st0, moved(static_cast<const float2*>(jobs.in[j.job]), j.by), j.row0, P);
+  }
   cp_async_commit();
   int cur = 0;
   for (; t < ntiles; t += gridDim.x) {
-    const int job = (int)(t / tiles_per_job);
-    const int64_t row0 = (t % tiles_per_job) * TWX;
+    const JobTile j = job_tile(t, tiles_per_job, jobs.njobs, TWX, m);
+    const int job = j.job;
+    const int64_t row0 = j.row0;
     const int64_t tn = t + gridDim.x;
-    if (tn < ntiles)
-      stage_complex_rows<N, TWX>(cur ? st0 : st1, static_cast<const float2*>(jobs.in[tn / tiles_per_job]),
-                                 (tn % tiles_per_job) * TWX, P);
+    if (tn < ntiles) {
+      const JobTile jn = job_tile(tn, tiles_per_job, jobs.njobs, TWX, m);
+      stage_complex_rows<N, TWX>(cur ? st0 : st1, moved(static_cast<const float2*>(jobs.in[jn.job]), jn.by),
+                                 jn.row0, P);
+    }
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
@@ -663,7 +717,7 @@ __global__ void __launch_bounds__(NT, 2) k_xc2r(RowJobs jobs, int64_t P,
     __syncthreads();
     row_c2r_combine<N, TWX, C::PITCH>(buf, tw);
     fft_tile<M, TWX, C::PITCH, NT, true, 2>(buf, tw);
-    float* out = static_cast<float*>(jobs.out[job]);
+    float* out = moved(static_cast<float*>(jobs.out[job]), j.by);
     for (int e = threadIdx.x; e < TWX * M; e += NT) {
       const int r = e / M, j = e % M;
       reinterpret_cast<float2*>(out + (row0 + r) * N)[j] = buf[j * C::PITCH + r];
@@ -689,9 +743,9 @@ template <int N, int TWX, int MODEL>
 __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w_in,
                                                     const float* __restrict__ rho,
                                                     float2* __restrict__ s_out, int64_t P,
-                                                    ForceParams fp, const float2* __restrict__ twg,
-                                                    int64_t ntiles) {
-  resolve(fp);
+                                                    ForceParams fp0, const float2* __restrict__ twg,
+                                                    int64_t ntiles, int64_t tps, Multi m) {
+  if (!m.shift) resolve(fp0, 0);  // one simulation: once per launch
   using C = RowCfg<N, TWX>;
   constexpr int M = N / 2;
   extern __shared__ __align__(16) float2 sm[];
@@ -701,21 +755,30 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
   float2* st1 = st0 + C::stage;
   load_tw(tw, twg, N);
   int64_t t = blockIdx.x;
-  if (t < ntiles) stage_complex_rows<N, TWX>(st0, w_in, t * TWX, P);
+  if (t < ntiles) {
+    const RowTile r = row_tile<TWX>(t, tps, m);
+    stage_complex_rows<N, TWX>(st0, moved(w_in, r.by), r.row0, P);
+  }
   cp_async_commit();
   int cur = 0;
   for (; t < ntiles; t += gridDim.x) {
-    const int64_t row0 = t * TWX;
+    const RowTile r = row_tile<TWX>(t, tps, m);
+    const int64_t row0 = r.row0;
+    ForceParams fp = fp0;
+    resolve(fp, r.by);
     const int64_t tn = t + gridDim.x;
     float2* stc = cur ? st1 : st0;
-    if (tn < ntiles) stage_complex_rows<N, TWX>(cur ? st0 : st1, w_in, tn * TWX, P);
+    if (tn < ntiles) {
+      const RowTile rn = row_tile<TWX>(tn, tps, m);
+      stage_complex_rows<N, TWX>(cur ? st0 : st1, moved(w_in, rn.by), rn.row0, P);
+    }
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
     put_c2r<N, TWX>(buf, stc, 0.f);
     __syncthreads();
     // the current staging buffer is free again: bring in the density rows of this tile
-    stage_real_rows<N, TWX>(stc, rho, row0);
+    stage_real_rows<N, TWX>(stc, moved(rho, r.by), row0);
     cp_async_commit();
     row_c2r_combine<N, TWX, C::PITCH>(buf, tw);
     fft_tile_call<M, TWX, C::PITCH, NT, true, 2>(buf, tw);
@@ -731,7 +794,7 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
     }
     __syncthreads();
     fft_tile_call<M, TWX, C::PITCH, NT, false, 2>(buf, tw);
-    row_r2c_store<N, TWX, C::PITCH>(buf, tw, s_out, row0, P);
+    row_r2c_store<N, TWX, C::PITCH>(buf, tw, moved(s_out, r.by), row0, P);
     __syncthreads();
     cur ^= 1;
   }
@@ -750,14 +813,14 @@ constexpr size_t row_smem(bool) {
 }
 
 template <int N, int TW>
-ColGeo<N, TW> geo_y() {
+ColGeo<N, TW> geo_y(Multi m) {
   const int64_t P = half_pitch(N);
-  return ColGeo<N, TW>{(int64_t)N * P, P};
+  return ColGeo<N, TW>{(int64_t)N * P, P, m};
 }
 template <int N, int TW>
-ColGeo<N, TW> geo_z() {
+ColGeo<N, TW> geo_z(Multi m) {
   const int64_t P = half_pitch(N);
-  return ColGeo<N, TW>{P, (int64_t)N * P};
+  return ColGeo<N, TW>{P, (int64_t)N * P, m};
 }
 template <int N, int TW>
 constexpr int64_t col_tiles() {
@@ -781,27 +844,28 @@ void set_grid_cap(int max_ctas) { g_grid_cap = max_ctas > 0 ? max_ctas : 0; }
 
 template <int N>
 static cudaError_t launch_xr2c(const float* in, float2* out, float scale, float offset,
-                               const float2* tw, cudaStream_t s) {
+                               const float2* tw, cudaStream_t s, Multi m) {
   constexpr int TWX = row_tw(N);
   const size_t sm = row_smem<N>(false);
-  const int64_t ntiles = (int64_t)N * N / TWX;
+  const int64_t tps = (int64_t)N * N / TWX;
+  const int64_t ntiles = tps * m.nb;
   auto k = k_xr2c<N, TWX>;
   unsigned grid;
   cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, sm, s>>>(in, out, half_pitch(N), scale, offset, tw, ntiles);
+  k<<<grid, NT, sm, s>>>(in, out, half_pitch(N), scale, offset, tw, ntiles, tps, m);
   return cudaGetLastError();
 }
 
 cudaError_t fft_xr2c(int Nv, const float* in, float2* out, float scale, float offset,
-                     const float2* tw, cudaStream_t s) {
-  COLA_SWITCH_N(Nv, return launch_xr2c<N>(in, out, scale, offset, tw, s));
+                     const float2* tw, cudaStream_t s, Multi m) {
+  COLA_SWITCH_N(Nv, return launch_xr2c<N>(in, out, scale, offset, tw, s, m));
   return cudaSuccess;
 }
 
 template <int N>
 static cudaError_t launch_xc2r_multi(int njobs, const float2* const* in, float* const* out,
-                                     const float* kfs, const float2* tw, cudaStream_t s) {
+                                     const float* kfs, const float2* tw, cudaStream_t s, Multi m) {
   constexpr int TWX = row_tw(N);
   const size_t sm = row_smem<N>(true);
   RowJobs jobs{};
@@ -814,31 +878,31 @@ static cudaError_t launch_xc2r_multi(int njobs, const float2* const* in, float* 
   const int64_t tpj = (int64_t)N * N / TWX;
   auto k = k_xc2r<N, TWX>;
   unsigned grid;
-  cudaError_t e = prep(k, sm, tpj * njobs, grid);
+  cudaError_t e = prep(k, sm, tpj * njobs * m.nb, grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, sm, s>>>(jobs, half_pitch(N), tw, tpj);
+  k<<<grid, NT, sm, s>>>(jobs, half_pitch(N), tw, tpj, m);
   return cudaGetLastError();
 }
 
 cudaError_t fft_xc2r_multi(int Nv, int njobs, const float2* const* in, float* const* out,
-                           const float* kfs, const float2* tw, cudaStream_t s) {
+                           const float* kfs, const float2* tw, cudaStream_t s, Multi m) {
   if (njobs < 1 || njobs > 6) return cudaErrorInvalidValue;
-  COLA_SWITCH_N(Nv, return launch_xc2r_multi<N>(njobs, in, out, kfs, tw, s));
+  COLA_SWITCH_N(Nv, return launch_xc2r_multi<N>(njobs, in, out, kfs, tw, s, m));
   return cudaSuccess;
 }
 
 cudaError_t fft_xc2r(int Nv, const float2* in, float* out, float kfs, const float2* tw,
-                     cudaStream_t s) {
-  return fft_xc2r_multi(Nv, 1, &in, &out, &kfs, tw, s);
+                     cudaStream_t s, Multi m) {
+  return fft_xc2r_multi(Nv, 1, &in, &out, &kfs, tw, s, m);
 }
 
 template <int N>
 static cudaError_t launch_col(float2* data, int axis, bool inv, const float2* tw,
-                              cudaStream_t s) {
+                              cudaStream_t s, Multi m) {
   constexpr int TW = col_tw(N, 1);
   constexpr size_t sm = col_smem<N, 1>();
-  constexpr int64_t ntiles = col_tiles<N, TW>();
-  const ColGeo<N, TW> geo = axis == 1 ? geo_y<N, TW>() : geo_z<N, TW>();
+  const int64_t ntiles = col_tiles<N, TW>() * m.nb;
+  const ColGeo<N, TW> geo = axis == 1 ? geo_y<N, TW>(m) : geo_z<N, TW>(m);
   unsigned grid;
   if (inv) {
     auto k = k_col<N, TW, true>;
@@ -854,99 +918,101 @@ static cudaError_t launch_col(float2* data, int axis, bool inv, const float2* tw
   return cudaGetLastError();
 }
 
-cudaError_t fft_col(int Nv, float2* data, int axis, bool inv, const float2* tw, cudaStream_t s) {
-  COLA_SWITCH_N(Nv, return launch_col<N>(data, axis, inv, tw, s));
+cudaError_t fft_col(int Nv, float2* data, int axis, bool inv, const float2* tw, cudaStream_t s,
+                    Multi m) {
+  COLA_SWITCH_N(Nv, return launch_col<N>(data, axis, inv, tw, s, m));
   return cudaSuccess;
 }
 
 template <int N>
 static cudaError_t launch_yinv2(const float2* in, float2* outp, float2* outd, float kfs,
-                                const float2* tw, cudaStream_t s) {
+                                const float2* tw, cudaStream_t s, Multi m) {
   constexpr int TW = col_tw(N, 2);
   constexpr size_t sm = col_smem<N, 2>();
-  constexpr int64_t ntiles = col_tiles<N, TW>();
+  const int64_t ntiles = col_tiles<N, TW>() * m.nb;
   auto k = k_yinv2<N, TW>;
   unsigned grid;
   cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, sm, s>>>(OpYinv2<N, TW>{geo_y<N, TW>(), in, outp, outd, kfs}, tw, ntiles);
+  k<<<grid, NT, sm, s>>>(OpYinv2<N, TW>{geo_y<N, TW>(m), in, outp, outd, kfs}, tw, ntiles);
   return cudaGetLastError();
 }
 
 cudaError_t fft_yinv2(int Nv, const float2* in, float2* outp, float2* outd, float kfs,
-                      const float2* tw, cudaStream_t s) {
-  COLA_SWITCH_N(Nv, return launch_yinv2<N>(in, outp, outd, kfs, tw, s));
+                      const float2* tw, cudaStream_t s, Multi m) {
+  COLA_SWITCH_N(Nv, return launch_yinv2<N>(in, outp, outd, kfs, tw, s, m));
   return cudaSuccess;
 }
 
 template <int N>
 static cudaError_t launch_zsf(const float2* in, float2* dk_out, float2* w_out,
-                              const ForceParams& fp, const float2* tw, cudaStream_t s) {
+                              const ForceParams& fp, const float2* tw, cudaStream_t s, Multi m) {
   constexpr int TW = col_tw(N, 1);
   constexpr size_t sm = col_smem<N, 1>();
-  constexpr int64_t ntiles = col_tiles<N, TW>();
+  const int64_t ntiles = col_tiles<N, TW>() * m.nb;
   unsigned grid;
   if (fp.model == 1) {
     auto k = k_z_screen_field<N, TW, 1>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(OpZScreenField<N, TW, 1>{geo_z<N, TW>(), in, dk_out, w_out, fp}, tw, ntiles);
+    k<<<grid, NT, sm, s>>>(OpZScreenField<N, TW, 1>{geo_z<N, TW>(m), in, dk_out, w_out, fp}, tw, ntiles);
   } else {
     auto k = k_z_screen_field<N, TW, 2>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(OpZScreenField<N, TW, 2>{geo_z<N, TW>(), in, dk_out, w_out, fp}, tw, ntiles);
+    k<<<grid, NT, sm, s>>>(OpZScreenField<N, TW, 2>{geo_z<N, TW>(m), in, dk_out, w_out, fp}, tw, ntiles);
   }
   return cudaGetLastError();
 }
 
 cudaError_t mesh_z_screen_field(int Nv, const float2* in, float2* dk_out, float2* w_out,
-                                const ForceParams& fp, const float2* tw, cudaStream_t s) {
+                                const ForceParams& fp, const float2* tw, cudaStream_t s, Multi m) {
   if (fp.model != 1 && fp.model != 2) return cudaErrorInvalidValue;
-  COLA_SWITCH_N(Nv, return launch_zsf<N>(in, dk_out, w_out, fp, tw, s));
+  COLA_SWITCH_N(Nv, return launch_zsf<N>(in, dk_out, w_out, fp, tw, s, m));
   return cudaSuccess;
 }
 
 template <int N>
 static cudaError_t launch_xscreen(const float2* w_in, const float* rho, float2* s_out,
-                                  const ForceParams& fp, const float2* tw, cudaStream_t s) {
+                                  const ForceParams& fp, const float2* tw, cudaStream_t s, Multi m) {
   constexpr int TWX = row_tw(N);
   const size_t sm = row_smem<N>(true);
-  const int64_t ntiles = (int64_t)N * N / TWX;
+  const int64_t tps = (int64_t)N * N / TWX;
+  const int64_t ntiles = tps * m.nb;
   unsigned grid;
   if (fp.model == 1) {
     auto k = k_x_screen<N, TWX, 1>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, half_pitch(N), fp, tw, ntiles);
+    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, half_pitch(N), fp, tw, ntiles, tps, m);
   } else {
     auto k = k_x_screen<N, TWX, 2>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, half_pitch(N), fp, tw, ntiles);
+    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, half_pitch(N), fp, tw, ntiles, tps, m);
   }
   return cudaGetLastError();
 }
 
 cudaError_t mesh_x_screen_source(int Nv, const float2* w_in, const float* rho, float2* s_out,
-                                 const ForceParams& fp, const float2* tw, cudaStream_t s) {
+                                 const ForceParams& fp, const float2* tw, cudaStream_t s, Multi m) {
   if (fp.model != 1 && fp.model != 2) return cudaErrorInvalidValue;
-  COLA_SWITCH_N(Nv, return launch_xscreen<N>(w_in, rho, s_out, fp, tw, s));
+  COLA_SWITCH_N(Nv, return launch_xscreen<N>(w_in, rho, s_out, fp, tw, s, m));
   return cudaSuccess;
 }
 
 template <int N, bool SCR, bool KEEP>
 static cudaError_t launch_zforce_t(const float2* in, const float2* dk, float2* phi,
                                    float2* phiz, float2* keep, const ForceParams& fp,
-                                   const float2* tw, cudaStream_t s) {
+                                   const float2* tw, cudaStream_t s, Multi m) {
   constexpr int TW = col_tw(N, 1);
   constexpr size_t sm = col_smem<N, 1>() + (size_t)N * TW * sizeof(float2);
-  constexpr int64_t ntiles = col_tiles<N, TW>();
+  const int64_t ntiles = col_tiles<N, TW>() * m.nb;
   auto k = k_z_force<N, TW, SCR, KEEP>;
   unsigned grid;
   cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, sm, s>>>(OpZForce<N, TW, SCR, KEEP>{geo_z<N, TW>(), in, dk, phi, phiz, keep, fp}, tw,
+  k<<<grid, NT, sm, s>>>(OpZForce<N, TW, SCR, KEEP>{geo_z<N, TW>(m), in, dk, phi, phiz, keep, fp}, tw,
                          ntiles);
   return cudaGetLastError();
 }
@@ -954,48 +1020,48 @@ static cudaError_t launch_zforce_t(const float2* in, const float2* dk, float2* p
 template <int N>
 static cudaError_t launch_zforce(const float2* in, const float2* dk, float2* phi, float2* phiz,
                                  float2* keep, const ForceParams& fp, const float2* tw,
-                                 cudaStream_t s) {
-  if (fp.screened) return launch_zforce_t<N, true, false>(in, dk, phi, phiz, keep, fp, tw, s);
-  if (keep) return launch_zforce_t<N, false, true>(in, dk, phi, phiz, keep, fp, tw, s);
-  return launch_zforce_t<N, false, false>(in, dk, phi, phiz, keep, fp, tw, s);
+                                 cudaStream_t s, Multi m) {
+  if (fp.screened) return launch_zforce_t<N, true, false>(in, dk, phi, phiz, keep, fp, tw, s, m);
+  if (keep) return launch_zforce_t<N, false, true>(in, dk, phi, phiz, keep, fp, tw, s, m);
+  return launch_zforce_t<N, false, false>(in, dk, phi, phiz, keep, fp, tw, s, m);
 }
 
 cudaError_t mesh_z_force(int Nv, const float2* in, const float2* dk, float2* phi_out,
                          float2* phiz_out, float2* dk_keep, const ForceParams& fp,
-                         const float2* tw, cudaStream_t s) {
+                         const float2* tw, cudaStream_t s, Multi m) {
   if (fp.screened && dk == nullptr) return cudaErrorInvalidValue;
-  COLA_SWITCH_N(Nv, return launch_zforce<N>(in, dk, phi_out, phiz_out, dk_keep, fp, tw, s));
+  COLA_SWITCH_N(Nv, return launch_zforce<N>(in, dk, phi_out, phiz_out, dk_keep, fp, tw, s, m));
   return cudaSuccess;
 }
 
 template <int N, int PREC>
 static cudaError_t launch_lpt_t(const void* p1, const void* p2, float2* o0, float2* o1,
                                 float2* o2, float2* o3, const LptParams& lp, const float2* tw,
-                                cudaStream_t s) {
+                                cudaStream_t s, Multi m) {
   constexpr int TW = col_tw(N, 4);
   constexpr size_t sm = col_smem<N, 4>();
-  constexpr int64_t ntiles = col_tiles<N, TW>();
+  const int64_t ntiles = col_tiles<N, TW>() * m.nb;
   auto k = k_lpt_z<N, TW, PREC>;
   unsigned grid;
   cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, sm, s>>>(OpLptZ<N, TW, PREC>{geo_z<N, TW>(), p1, p2, o0, o1, o2, o3, lp}, tw, ntiles);
+  k<<<grid, NT, sm, s>>>(OpLptZ<N, TW, PREC>{geo_z<N, TW>(m), p1, p2, o0, o1, o2, o3, lp}, tw, ntiles);
   return cudaGetLastError();
 }
 
 template <int N>
 static cudaError_t launch_lpt(const void* p1, const void* p2, float2* o0, float2* o1, float2* o2,
                               float2* o3, const LptParams& lp, const float2* tw,
-                              cudaStream_t s) {
-  if (lp.seed_prec == 1) return launch_lpt_t<N, 1>(p1, p2, o0, o1, o2, o3, lp, tw, s);
-  if (lp.seed_prec == 2) return launch_lpt_t<N, 2>(p1, p2, o0, o1, o2, o3, lp, tw, s);
-  return launch_lpt_t<N, 0>(p1, p2, o0, o1, o2, o3, lp, tw, s);
+                              cudaStream_t s, Multi m) {
+  if (lp.seed_prec == 1) return launch_lpt_t<N, 1>(p1, p2, o0, o1, o2, o3, lp, tw, s, m);
+  if (lp.seed_prec == 2) return launch_lpt_t<N, 2>(p1, p2, o0, o1, o2, o3, lp, tw, s, m);
+  return launch_lpt_t<N, 0>(p1, p2, o0, o1, o2, o3, lp, tw, s, m);
 }
 
 cudaError_t lpt_z(int Nv, const void* phi1, const void* phi2, float2* o0, float2* o1, float2* o2,
-                  float2* o3, const LptParams& lp, const float2* tw, cudaStream_t s) {
+                  float2* o3, const LptParams& lp, const float2* tw, cudaStream_t s, Multi m) {
   if (Nv > 512) return cudaErrorInvalidValue;  // four double-buffered 4-column tiles exceed shared memory
-  COLA_SWITCH_N(Nv, return launch_lpt<N>(phi1, phi2, o0, o1, o2, o3, lp, tw, s));
+  COLA_SWITCH_N(Nv, return launch_lpt<N>(phi1, phi2, o0, o1, o2, o3, lp, tw, s, m));
   return cudaSuccess;
 }
 

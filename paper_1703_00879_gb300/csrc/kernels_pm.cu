@@ -94,12 +94,19 @@ __device__ __forceinline__ void lattice(const PartParams& pp, int64_t p, int& ix
   iz = (int)(p >> (2 * pp.lgNp));
 }
 
+// Multi-simulation kernels take the simulation from blockIdx.y and move every
+// buffer pointer by its shift.
 __global__ void __launch_bounds__(NTP) k_deposit(PartParams pp, const float* __restrict__ sx,
                                                  const float* __restrict__ sy,
                                                  const float* __restrict__ sz,
-                                                 float* __restrict__ rho, int64_t P) {
+                                                 float* __restrict__ rho, int64_t P, Multi m) {
   const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
   if (p >= P) return;
+  const int64_t by = shift_of(m, blockIdx.y);
+  sx = moved(sx, by);
+  sy = moved(sy, by);
+  sz = moved(sz, by);
+  rho = moved(rho, by);
   int ix, iy, iz;
   lattice(pp, p, ix, iy, iz);
   cic_deposit(rho, pp.Nm, cic_setup(pp, ix, iy, iz, sx[p], sy[p], sz[p]));
@@ -112,11 +119,29 @@ __global__ void __launch_bounds__(NTP) k_drift_deposit(
     float* __restrict__ vx, float* __restrict__ vy, float* __restrict__ vz,
     const float* __restrict__ ax, const float* __restrict__ ay, const float* __restrict__ az,
     const float* __restrict__ dpx, const float* __restrict__ dpy,
-    const float* __restrict__ dpz, float* __restrict__ rho, StepDt dt, int64_t P) {
+    const float* __restrict__ dpz, float* __restrict__ rho, StepDt dt, int64_t P, Multi m) {
   const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
   if (p >= P) return;
-  const float dtk = dt.dt ? dt.dt[3 * *dt.step] : dt.dtk;
-  const float dtd = dt.dt ? dt.dt[3 * *dt.step + 1] : dt.dtd;
+  const int64_t by = shift_of(m, blockIdx.y);
+  sx = moved(sx, by);
+  sy = moved(sy, by);
+  sz = moved(sz, by);
+  vx = moved(vx, by);
+  vy = moved(vy, by);
+  vz = moved(vz, by);
+  ax = moved(ax, by);
+  ay = moved(ay, by);
+  az = moved(az, by);
+  dpx = moved(dpx, by);
+  dpy = moved(dpy, by);
+  dpz = moved(dpz, by);
+  rho = moved(rho, by);
+  float dtk = dt.dtk, dtd = dt.dtd;
+  if (dt.hdr) {
+    const SimHeader* h = moved(dt.hdr, by);
+    dtk = h->ddt[3 * h->step];
+    dtd = h->ddt[3 * h->step + 1];
+  }
   const float ux = vx[p] + ax[p] * dtk;
   const float uy = vy[p] + ay[p] * dtk;
   const float uz = vz[p] + az[p] * dtk;
@@ -145,9 +170,29 @@ __global__ void __launch_bounds__(NTP) k_gather_kick(
     float* __restrict__ vz, float* __restrict__ ax, float* __restrict__ ay,
     float* __restrict__ az, const float* __restrict__ Ax, const float* __restrict__ Ay,
     const float* __restrict__ Az, const float* __restrict__ Fx, const float* __restrict__ Fy,
-    const float* __restrict__ Fz, StepDt dt, int64_t P) {
+    const float* __restrict__ Fz, StepDt dt, int64_t P, Multi m) {
   const int64_t p0 = (int64_t)blockIdx.x * NTP * PPT + threadIdx.x;
-  const float dtk = dt.dt ? dt.dt[3 * *dt.step + 2] : dt.dtk;
+  const int64_t by = shift_of(m, blockIdx.y);
+  sx = moved(sx, by);
+  sy = moved(sy, by);
+  sz = moved(sz, by);
+  vx = moved(vx, by);
+  vy = moved(vy, by);
+  vz = moved(vz, by);
+  ax = moved(ax, by);
+  ay = moved(ay, by);
+  az = moved(az, by);
+  Ax = moved(Ax, by);
+  Ay = moved(Ay, by);
+  Az = moved(Az, by);
+  Fx = moved(Fx, by);
+  Fy = moved(Fy, by);
+  Fz = moved(Fz, by);
+  float dtk = dt.dtk;
+  if (dt.hdr) {
+    const SimHeader* h = moved(dt.hdr, by);
+    dtk = h->ddt[3 * h->step + 2];
+  }
   float px[PPT], py[PPT], pz[PPT];
 #pragma unroll
   for (int u = 0; u < PPT; ++u) {
@@ -239,8 +284,12 @@ __global__ void __launch_bounds__(NTP) k_pos_deposit(int Nm, float cellscale,
 // [count | sum P | sum |k| in units of k_F] per bin.
 __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, int N,
                                                 int64_t P, int nbins,
-                                                double* __restrict__ acc, double norm) {
+                                                double* __restrict__ acc, double norm, Multi m,
+                                                int64_t acc_stride) {
   extern __shared__ double sh[];
+  const int64_t by = shift_of(m, blockIdx.y);
+  dk = moved(dk, by);
+  acc = acc_stride > 0 ? acc + blockIdx.y * acc_stride : moved(acc, by);
   for (int i = threadIdx.x; i < 3 * nbins; i += NTP) sh[i] = 0.0;
   __syncthreads();
   const int64_t nmodes = (int64_t)N * N * (N / 2 + 1);
@@ -279,13 +328,24 @@ __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, i
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + NTP - 1) / NTP); }
 
-__global__ void k_step_advance(int* step) { *step += 1; }
+__global__ void k_step_advance(SimHeader* hdr, Multi m) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < m.nb) moved(hdr, shift_of(m, b))->step += 1;
+}
+
+__global__ void k_set_header(SimHeader* hdr, SimHeader v) { *hdr = v; }
+
+__global__ void __launch_bounds__(NTP) k_zero(float4* __restrict__ p, int64_t n4, Multi m) {
+  p = moved(p, shift_of(m, blockIdx.y));
+  for (int64_t i = (int64_t)blockIdx.x * NTP + threadIdx.x; i < n4; i += (int64_t)gridDim.x * NTP)
+    p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
 
 }  // namespace
 
 cudaError_t part_deposit(const PartParams& pp, const float* sx, const float* sy, const float* sz,
-                         float* rho, int64_t P, cudaStream_t s) {
-  k_deposit<<<blocks_for(P), NTP, 0, s>>>(pp, sx, sy, sz, rho, P);
+                         float* rho, int64_t P, cudaStream_t s, Multi m) {
+  k_deposit<<<dim3(blocks_for(P), m.nb), NTP, 0, s>>>(pp, sx, sy, sz, rho, P, m);
   return cudaGetLastError();
 }
 
@@ -293,9 +353,9 @@ cudaError_t part_drift_deposit(const PartParams& pp, float* sx, float* sy, float
                                float* vy, float* vz, const float* ax, const float* ay,
                                const float* az, const float* dpx, const float* dpy,
                                const float* dpz, float* rho, StepDt dt, int64_t P,
-                               cudaStream_t s) {
-  k_drift_deposit<<<blocks_for(P), NTP, 0, s>>>(pp, sx, sy, sz, vx, vy, vz, ax, ay, az, dpx, dpy,
-                                                dpz, rho, dt, P);
+                               cudaStream_t s, Multi m) {
+  k_drift_deposit<<<dim3(blocks_for(P), m.nb), NTP, 0, s>>>(pp, sx, sy, sz, vx, vy, vz, ax, ay, az,
+                                                            dpx, dpy, dpz, rho, dt, P, m);
   return cudaGetLastError();
 }
 
@@ -303,9 +363,9 @@ cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float*
                              const float* sz, float* vx, float* vy, float* vz, float* ax,
                              float* ay, float* az, const float* Ax, const float* Ay,
                              const float* Az, const float* Fx, const float* Fy, const float* Fz,
-                             StepDt dt, int64_t P, cudaStream_t s) {
-  k_gather_kick<<<(unsigned)((P + NTP * PPT - 1) / (NTP * PPT)), NTP, 0, s>>>(
-      pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, Fx, Fy, Fz, dt, P);
+                             StepDt dt, int64_t P, cudaStream_t s, Multi m) {
+  k_gather_kick<<<dim3((unsigned)((P + NTP * PPT - 1) / (NTP * PPT)), m.nb), NTP, 0, s>>>(
+      pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, Fx, Fy, Fz, dt, P, m);
   return cudaGetLastError();
 }
 
@@ -318,8 +378,22 @@ cudaError_t part_snapshot(const PartParams& pp, const float* sx, const float* sy
   return cudaGetLastError();
 }
 
-cudaError_t step_advance(int* step, cudaStream_t s) {
-  k_step_advance<<<1, 1, 0, s>>>(step);
+cudaError_t step_advance(SimHeader* hdr, cudaStream_t s, Multi m) {
+  k_step_advance<<<(m.nb + 127) / 128, 128, 0, s>>>(hdr, m);
+  return cudaGetLastError();
+}
+
+cudaError_t set_header(SimHeader* hdr, const SimHeader& v, cudaStream_t s) {
+  k_set_header<<<1, 1, 0, s>>>(hdr, v);
+  return cudaGetLastError();
+}
+
+cudaError_t zero_f32(float* p, int64_t n, cudaStream_t s, Multi m) {
+  if (m.nb == 1 && !m.shift) return cudaMemsetAsync(p, 0, n * sizeof(float), s);
+  if (n % 4 != 0 || (reinterpret_cast<uintptr_t>(p) & 15)) return cudaErrorInvalidValue;
+  const int64_t n4 = n / 4;
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n4 + NTP - 1) / NTP, 1024));
+  k_zero<<<dim3(gx, m.nb), NTP, 0, s>>>(reinterpret_cast<float4*>(p), n4, m);
   return cudaGetLastError();
 }
 
@@ -331,12 +405,13 @@ cudaError_t pos_deposit(int Nm, float cellscale, const float* pos, int64_t n, fl
 }
 
 cudaError_t pk_bin(int N, const float2* dk, int nbins, double* acc, double norm,
-                   cudaStream_t s) {
+                   cudaStream_t s, Multi m, int64_t acc_stride) {
   const size_t sm = 3 * (size_t)nbins * sizeof(double);
   if (sm > 48 * 1024) return cudaErrorInvalidValue;
   const int64_t nmodes = (int64_t)N * N * (N / 2 + 1);
   unsigned grid = (unsigned)std::min<int64_t>((nmodes + NTP - 1) / NTP, 152 * 8);
-  k_pk_bin<<<grid, NTP, sm, s>>>(dk, N, half_pitch(N), nbins, acc, norm);
+  if (m.nb > 1) grid = std::max<unsigned>(1, grid / (unsigned)std::min(m.nb, 8));
+  k_pk_bin<<<dim3(grid, m.nb), NTP, sm, s>>>(dk, N, half_pitch(N), nbins, acc, norm, m, acc_stride);
   return cudaGetLastError();
 }
 

@@ -23,30 +23,74 @@ def _solo(pkg, run):
         return s.export(pkg.COLA_F_DISP), s.pk()
 
 
-@pytest.mark.parametrize("chains", [1, 3, 0])
-def test_batch_equals_solo(chains):
+@pytest.mark.parametrize("plan", [None, (2, 1, 0), (4, 2, 0), (3, 2, 76), (1, 3, 0)],
+                         ids=["one_group", "pairs", "quads_2chains", "triples_capped", "singles_3chains"])
+def test_batch_equals_solo(plan):
+    """Every model of the ensemble set (LCDM, f(R) x3, nDGP x2) in one batch:
+    the model-dependent force stages run per model subset of each group."""
     import paper_1703_00879_gb300 as pkg
     runs = _runs(len(ENSEMBLE_MODELS))
     solo = [_solo(pkg, r) for r in runs]
     sims = [pkg.Simulation(r) for r in runs]
-    with pkg.Batch(sims, chains=chains) as b:
+    with pkg.Batch(sims, plan=plan) as b:
         b.step(-1)
         assert b.steps_done == runs[0].nsteps
-    for r, s, (d0, _) in zip(runs, sims, solo):
+        k, P, nm = b.pk()
+    for i, (r, s, (d0, (k0, P0, nm0))) in enumerate(zip(runs, sims, solo)):
         d = s.export(pkg.COLA_F_DISP)
         assert s.steps_done == r.nsteps
         assert np.max(np.abs(d - d0)) / (r.Lbox / r.Nmesh) <= 1e-4
+        ok = nm0 > 0
+        assert np.array_equal(nm[i], nm0)
+        assert np.allclose(k[i][ok], k0[ok], rtol=1e-12)
+        assert np.max(np.abs(P[i][ok] / P0[ok] - 1)) <= 1e-4
+        s.close()
+
+
+def test_batch_of_mixed_shapes_runs_one_context_per_group():
+    import paper_1703_00879_gb300 as pkg
+    runs = [ensemble_run(0, Np=32, Nmesh=64, Lbox=64.0, nsteps=3),
+            ensemble_run(1, Np=64, Nmesh=64, Lbox=64.0, nsteps=3),
+            ensemble_run(2, Np=32, Nmesh=32, Lbox=64.0, nsteps=3)]
+    solo = [_solo(pkg, r) for r in runs]
+    sims = [pkg.Simulation(r) for r in runs]
+    with pkg.Batch(sims, plan=(3, 1, 0)) as b:
+        assert b.plan[0] == 1
+        b.step(-1)
+        _, P, _ = b.pk(16)
+    for i, (r, s, (d0, _)) in enumerate(zip(runs, sims, solo)):
+        assert np.max(np.abs(s.export(pkg.COLA_F_DISP) - d0)) / (r.Lbox / r.Nmesh) <= 1e-4
+        _, P0, nm0 = s.pk(16)
+        ok = nm0 > 0
+        assert np.max(np.abs(P[i][ok] / P0[ok] - 1)) <= 1e-4
+        s.close()
+
+
+def test_batch_of_reduced_precision_seeds_equals_solo():
+    import paper_1703_00879_gb300 as pkg
+    runs = _runs(4, steps=3)
+    solo = []
+    for r in runs:
+        with pkg.Simulation(r, seed_precision=1) as s:
+            s.run_to_end()
+            solo.append(s.export(pkg.COLA_F_DISP))
+    sims = [pkg.Simulation(r, seed_precision=1) for r in runs]
+    with pkg.Batch(sims) as b:
+        b.step(-1)
+    for r, s, d0 in zip(runs, sims, solo):
+        assert np.max(np.abs(s.export(pkg.COLA_F_DISP) - d0)) / (r.Lbox / r.Nmesh) <= 1e-4
         s.close()
 
 
 def test_batch_autotune_keeps_results():
     import paper_1703_00879_gb300 as pkg
-    runs = _runs(8, steps=6)
+    runs = _runs(8, steps=8)
     solo = [_solo(pkg, r) for r in runs]
     sims = [pkg.Simulation(r) for r in runs]
     with pkg.Batch(sims) as b:
-        chains, cap = b.autotune(max_steps=3)
-        assert 1 <= chains <= 8 and cap >= 0
+        group, chains, cap = b.autotune(max_steps=6)
+        assert 1 <= group <= 8 and 1 <= chains <= 8 and cap >= 0
+        assert b.plan == (group, chains, cap)
         b.step(-1)
     for r, s, (d0, _) in zip(runs, sims, solo):
         assert np.max(np.abs(s.export(pkg.COLA_F_DISP) - d0)) / (r.Lbox / r.Nmesh) <= 1e-4
