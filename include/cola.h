@@ -148,6 +148,21 @@ int cola_snapshot(cola_ctx* ctx, float* pos, float* vel, int32_t where);
  * pk in (Mpc/h)^3, nmodes = number of modes); any may be NULL.  Synchronises. */
 int cola_pk(cola_ctx* ctx, int32_t nbins, double* k, double* pk, int64_t* nmodes);
 
+/* Non-blocking P(k): cola_pk_async enqueues the same computation and a copy
+ * of the bin sums into a pinned host buffer owned by the context, and returns
+ * at once; cola_pk_ready returns 1 when that copy has landed (0 while pending);
+ * cola_pk_result waits for it if needed and fills k, pk, nmodes like cola_pk.
+ * One request per context may be pending.  Errors: COLA_EINVAL, COLA_ESTATE
+ * (no ICs; a request already pending / none pending), COLA_ECUDA. */
+int cola_pk_async(cola_ctx* ctx, int32_t nbins);
+int cola_pk_ready(cola_ctx* ctx);
+int cola_pk_result(cola_ctx* ctx, double* k, double* pk, int64_t* nmodes);
+
+/* Moves the context to another stream: work already queued on the old stream
+ * runs before anything later enqueued on the new one (an event wait, no host
+ * synchronisation).  Errors: COLA_EINVAL, COLA_ECUDA. */
+int cola_set_stream(cola_ctx* ctx, void* stream);
+
 /* Current scale factor (NaN for a NULL context) and completed steps. */
 double cola_scale_factor(const cola_ctx* ctx);
 int32_t cola_steps_done(const cola_ctx* ctx);
@@ -221,8 +236,8 @@ typedef struct cola_batch cola_batch;
  * ONCE per group over all of its contexts (a tile index that spans the
  * group's simulations; the model-dependent force stages run once per model
  * subset of the group).  Multi-simulation groups need contexts of one shape:
- * equal Np, Nmesh, Lbox, nsteps, nk_table and seed_precision (seeds, models
- * and cosmologies may differ); otherwise groups have one context.  Groups are
+ * equal Np, Nmesh, Lbox, nk_table and seed_precision (seeds, models and
+ * cosmologies may differ); otherwise groups have one context.  Groups are
  * spread round-robin over `chains` concurrent streams; `grid_cap` > 0 bounds
  * the persistent grid of every FFT pass so concurrent groups share the SMs. */
 typedef struct {
@@ -261,6 +276,19 @@ int cola_batch_autotune(cola_batch* b, int32_t max_steps, cola_batch_plan* best_
 int cola_batch_pk(cola_batch* b, int32_t nbins, double* k, double* pk, int64_t* nmodes);
 int32_t cola_batch_steps_done(const cola_batch* b);
 void cola_batch_free(cola_batch* b);
+
+/* Continuous batching: advances each of n distinct contexts (each after
+ * cola_ic and before its last step) by ONE step, enqueued on `stream`.
+ * Contexts of one shape (equal Np, Nmesh, Lbox, nk_table, seed_precision;
+ * their models, seeds, step counts and progress may differ) share one
+ * multi-simulation launch sequence.  No graph, no device allocation beyond
+ * a stream-ordered shift array, no host synchronisation: a serving loop
+ * calls it once per tick over whatever requests are in flight.  Work queued
+ * on a context's own stream before the call runs before its step, work
+ * queued after the call runs after it.  Errors: COLA_EINVAL (NULL, duplicate,
+ * finished or too many contexts), COLA_ESTATE (no ICs), COLA_ECUDA;
+ * message via cola_last_error(NULL). */
+int cola_step_many(cola_ctx* const* ctxs, int32_t n, void* stream);
 
 /* ---------------------------------------------------------------------
  * Per-stage device timing: CUDA events recorded on the context's stream

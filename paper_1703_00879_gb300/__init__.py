@@ -79,6 +79,11 @@ _SIGS = {
     "cola_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cola_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(cola_batch_plan)]),
     "cola_batch_pk": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
+    "cola_step_many": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "cola_pk_async": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cola_pk_ready": (ctypes.c_int, [_P]),
+    "cola_pk_result": (ctypes.c_int, [_P, _P, _P, _P]),
+    "cola_set_stream": (ctypes.c_int, [_P, _P]),
     "cola_batch_steps_done": (ctypes.c_int32, [_P]),
     "cola_batch_free": (None, [_P]),
     "cola_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
@@ -268,6 +273,28 @@ class Simulation:
         _check(lib().cola_snapshot(self.ctx, pos_t.data_ptr() if pos_t is not None else None,
                                    vel_t.data_ptr() if vel_t is not None else None, COLA_DEVICE), self.ctx)
 
+    def pk_async(self, nbins: Optional[int] = None):
+        """Starts a non-blocking P(k); fetch it with pk_result() (pk_ready() polls)."""
+        self._pk_nbins = nbins or self.run.Nmesh // 2
+        _check(lib().cola_pk_async(self.ctx, self._pk_nbins), self.ctx)
+
+    def pk_ready(self) -> bool:
+        rc = lib().cola_pk_ready(self.ctx)
+        if rc < 0:
+            _check(rc, self.ctx)
+        return rc == 1
+
+    def pk_result(self):
+        nb = self._pk_nbins
+        k, pk, nm = np.empty(nb), np.empty(nb), np.empty(nb, np.int64)
+        _check(lib().cola_pk_result(self.ctx, k.ctypes.data, pk.ctypes.data, nm.ctypes.data), self.ctx)
+        return k, pk, nm
+
+    def set_stream(self, stream):
+        """Moves the context to another torch stream (ordered after its queued work)."""
+        _check(lib().cola_set_stream(self.ctx, _P(stream.cuda_stream)), self.ctx)
+        self.stream = stream
+
     def pk(self, nbins: Optional[int] = None):
         nb = nbins or self.run.Nmesh // 2
         k = np.empty(nb)
@@ -333,6 +360,14 @@ class Simulation:
         _check(lib().cola_force_from_density(self.ctx, r.ctypes.data, float(a), out.ctypes.data, COLA_HOST),
                self.ctx)
         return out
+
+
+def step_many(sims, stream=None):
+    """cola_step_many: one step of every Simulation in `sims`, multi-simulation launches per shape."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    arr = (_P * len(sims))(*[s.ctx for s in sims])
+    _check(lib().cola_step_many(arr, len(sims), _P(st.cuda_stream)))
 
 
 class Batch:

@@ -35,6 +35,10 @@ struct cola_ctx {
   std::string err;
   std::vector<void*> allocs;
   std::vector<std::vector<double>> const_keys;  // shared device constants this context holds
+  cudaEvent_t ev_order = nullptr;  // orders the context's stream with cola_step_many's stream
+  double* pk_host = nullptr;       // pinned [3 * kMaxBins] (cola_pk_async)
+  cudaEvent_t pk_event = nullptr;
+  int pk_nbins = 0;                // bins of the pending cola_pk_async, 0: none
   int Np = 0, Nm = 0, lgNp = 0, nk = 0;
   double L = 0;
   int64_t P = 0, M = 0;
@@ -982,10 +986,9 @@ int cola_snapshot(cola_ctx* ctx, float* pos, float* vel, int32_t where) {
   return COLA_OK;
 }
 
-int cola_pk(cola_ctx* ctx, int32_t nbins, double* k, double* pk, int64_t* nmodes) {
-  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
-  if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_pk before cola_ic");
-  if (nbins < 1 || nbins > kMaxBins) return fail(ctx, COLA_EINVAL, "nbins out of range 1..2000");
+// Deposit, forward transform and binning of the current particles into
+// ctx->pk_acc (Sec. 7 estimator), enqueued on ctx->st.
+static int enqueue_pk(cola_ctx* ctx, int32_t nbins) {
   const int N = ctx->Nm;
   const PartParams pp = part_params(ctx);
   const ForceParams fp = force_params(ctx, ctx->a[ctx->step]);
@@ -995,16 +998,75 @@ int cola_pk(cola_ctx* ctx, int32_t nbins, double* k, double* pk, int64_t* nmodes
   CK(cudaMemsetAsync(ctx->pk_acc, 0, 3 * nbins * sizeof(double), ctx->st));
   const double L = ctx->L, N3 = (double)N * N * N;
   CK(pk_bin(N, ctx->Cw, nbins, ctx->pk_acc, L * L * L / (N3 * N3), ctx->st));
-  std::vector<double> h(3 * nbins);
-  CK(cudaMemcpyAsync(h.data(), ctx->pk_acc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
-  const double kf = 2.0 * kPi / L;
+  return COLA_OK;
+}
+
+// Bin sums [count | sum P | sum |k|/k_F] -> mean k, mean P, mode counts.
+static void finish_pk(const cola_ctx* ctx, const double* h, int32_t nbins, double* k, double* pk,
+                      int64_t* nmodes) {
+  const double kf = 2.0 * kPi / ctx->L;
   for (int b = 0; b < nbins; ++b) {
     const double cnt = h[b];
     if (k) k[b] = cnt > 0 ? h[2 * nbins + b] / cnt * kf : NAN;
     if (pk) pk[b] = cnt > 0 ? h[nbins + b] / cnt : NAN;
     if (nmodes) nmodes[b] = (int64_t)llround(cnt);
   }
+}
+
+int cola_pk(cola_ctx* ctx, int32_t nbins, double* k, double* pk, int64_t* nmodes) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_pk before cola_ic");
+  if (nbins < 1 || nbins > kMaxBins) return fail(ctx, COLA_EINVAL, "nbins out of range 1..2000");
+  CHECK_RC(enqueue_pk(ctx, nbins));
+  std::vector<double> h(3 * nbins);
+  CK(cudaMemcpyAsync(h.data(), ctx->pk_acc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  finish_pk(ctx, h.data(), nbins, k, pk, nmodes);
+  return COLA_OK;
+}
+
+int cola_pk_async(cola_ctx* ctx, int32_t nbins) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_pk_async before cola_ic");
+  if (nbins < 1 || nbins > kMaxBins) return fail(ctx, COLA_EINVAL, "nbins out of range 1..2000");
+  if (ctx->pk_nbins) return fail(ctx, COLA_ESTATE, "a cola_pk_async result is still pending");
+  if (!ctx->pk_host) CK(cudaMallocHost(&ctx->pk_host, 3 * (size_t)kMaxBins * sizeof(double)));
+  if (!ctx->pk_event) CK(cudaEventCreateWithFlags(&ctx->pk_event, cudaEventDisableTiming));
+  CHECK_RC(enqueue_pk(ctx, nbins));
+  CK(cudaMemcpyAsync(ctx->pk_host, ctx->pk_acc, 3 * (size_t)nbins * sizeof(double), cudaMemcpyDeviceToHost,
+                     ctx->st));
+  CK(cudaEventRecord(ctx->pk_event, ctx->st));
+  ctx->pk_nbins = nbins;
+  return COLA_OK;
+}
+
+int cola_pk_ready(cola_ctx* ctx) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!ctx->pk_nbins) return fail(ctx, COLA_ESTATE, "no cola_pk_async pending");
+  const cudaError_t e = cudaEventQuery(ctx->pk_event);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  return fail(ctx, COLA_ECUDA, std::string("cudaEventQuery: ") + cudaGetErrorString(e));
+}
+
+int cola_pk_result(cola_ctx* ctx, double* k, double* pk, int64_t* nmodes) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!ctx->pk_nbins) return fail(ctx, COLA_ESTATE, "no cola_pk_async pending");
+  CK(cudaEventSynchronize(ctx->pk_event));
+  finish_pk(ctx, ctx->pk_host, ctx->pk_nbins, k, pk, nmodes);
+  ctx->pk_nbins = 0;
+  return COLA_OK;
+}
+
+int cola_set_stream(cola_ctx* ctx, void* stream) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (st == ctx->st) return COLA_OK;
+  // work already queued on the old stream precedes later work on the new one
+  if (!ctx->ev_order) CK(cudaEventCreateWithFlags(&ctx->ev_order, cudaEventDisableTiming));
+  CK(cudaEventRecord(ctx->ev_order, ctx->st));
+  CK(cudaStreamWaitEvent(st, ctx->ev_order, 0));
+  ctx->st = st;
   return COLA_OK;
 }
 
@@ -1023,6 +1085,9 @@ void cola_free(cola_ctx* ctx) {
       cudaEventDestroy(pr.second);
     }
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  if (ctx->ev_order) cudaEventDestroy(ctx->ev_order);
+  if (ctx->pk_event) cudaEventDestroy(ctx->pk_event);
+  if (ctx->pk_host) cudaFreeHost(ctx->pk_host);
   for (void* p : ctx->allocs) dev_free(ctx, p);
   if (!ctx->alloc) cudaStreamSynchronize(ctx->st);
   release_consts(ctx);
@@ -1168,10 +1233,12 @@ static int bfail(cola_batch* b, int code, const std::string& m) {
     if (e_ != cudaSuccess) return bfail(b, COLA_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// Contexts one multi-simulation launch can serve: the same buffer layout and
+// the same launch-time constants (time grids, cosmologies, models and step
+// counts may differ: those are read through each simulation's header).
 static bool same_shape(const cola_ctx* a, const cola_ctx* c) {
   return a->cfg.Np == c->cfg.Np && a->cfg.Nmesh == c->cfg.Nmesh && a->cfg.Lbox == c->cfg.Lbox &&
-         a->cfg.nsteps == c->cfg.nsteps && a->cfg.nk_table == c->cfg.nk_table &&
-         a->cfg.seed_precision == c->cfg.seed_precision;
+         a->cfg.nk_table == c->cfg.nk_table && a->cfg.seed_precision == c->cfg.seed_precision;
 }
 
 static cola_batch_plan normal_plan(const cola_batch* b, cola_batch_plan p) {
@@ -1205,15 +1272,15 @@ struct GroupPlan {
   size_t off[5];  // offsets into hsh of all, unscreened, fr_screened, dgp_screened, screened
 };
 
-static void plan_groups(const cola_batch* b, const cola_batch_plan& p, std::vector<GroupPlan>& out,
+static void plan_groups(const std::vector<cola_ctx*>& ctxs, int group, std::vector<GroupPlan>& out,
                         std::vector<int64_t>& hsh) {
-  const int n = (int)b->ctx.size();
-  for (int j0 = 0; j0 < n; j0 += p.group) {
-    const int j1 = std::min(n, j0 + p.group);
+  const int n = (int)ctxs.size();
+  for (int j0 = 0; j0 < n; j0 += group) {
+    const int j1 = std::min(n, j0 + group);
     GroupPlan gp;
     std::vector<cola_ctx*> lists[5];
     for (int i = j0; i < j1; ++i) {
-      cola_ctx* c = b->ctx[i];
+      cola_ctx* c = ctxs[i];
       const bool scr = c->model.kind != COLA_LCDM && c->model.screening;
       lists[0].push_back(c);
       if (!scr) lists[1].push_back(c);
@@ -1246,7 +1313,7 @@ static void plan_groups(const cola_batch* b, const cola_batch_plan& p, std::vect
 static int batch_capture(cola_batch* b, int n, const cola_batch_plan& p, cola_batch::Graph* out) {
   std::vector<GroupPlan> groups;
   std::vector<int64_t> hsh;
-  plan_groups(b, p, groups, hsh);
+  plan_groups(b->ctx, p.group, groups, hsh);
   CHECK_RC(chain_streams(b, p.chains));
   int64_t* dsh = nullptr;
   if (!hsh.empty()) {
@@ -1319,7 +1386,7 @@ static int batch_graph(cola_batch* b, const cola_batch_plan& p, cudaGraphExec_t*
 static int batch_eager(cola_batch* b, const cola_batch_plan& p, int n) {
   std::vector<GroupPlan> groups;
   std::vector<int64_t> hsh;
-  plan_groups(b, p, groups, hsh);
+  plan_groups(b->ctx, p.group, groups, hsh);
   int64_t* dsh = nullptr;
   if (!hsh.empty()) {
     BCK(cudaMallocAsync(&dsh, hsh.size() * sizeof(int64_t), b->cap_st));
@@ -1546,6 +1613,79 @@ int cola_batch_pk(cola_batch* b, int32_t nbins, double* k, double* pk, int64_t* 
       if (pk) pk[o] = cnt > 0 ? r[nbins + q] / cnt : NAN;
       if (nmodes) nmodes[o] = (int64_t)llround(cnt);
     }
+  }
+  return COLA_OK;
+}
+
+int cola_step_many(cola_ctx* const* ctxs, int32_t n, void* stream) {
+  if (!ctxs || n < 1 || n > 65535) return fail(nullptr, COLA_EINVAL, "need 1 <= n <= 65535 contexts");
+  for (int i = 0; i < n; ++i) {
+    const cola_ctx* c = ctxs[i];
+    if (!c) return fail(nullptr, COLA_EINVAL, "NULL context");
+    if (!c->ic_done) return fail(nullptr, COLA_ESTATE, "cola_step_many before cola_ic");
+    if (c->step >= c->cfg.nsteps) return fail(nullptr, COLA_EINVAL, "a context is past its last step");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return fail(nullptr, COLA_EINVAL, "a context appears twice");
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto ck = [](cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return COLA_OK;
+    g_err = std::string("cola_step_many: ") + what + ": " + cudaGetErrorString(e);
+    return COLA_ECUDA;
+  };
+  // after the work already queued on each context's own stream
+  for (int i = 0; i < n; ++i) {
+    cola_ctx* c = ctxs[i];
+    if (c->st == st) continue;
+    if (!c->ev_order) CHECK_RC(ck(cudaEventCreateWithFlags(&c->ev_order, cudaEventDisableTiming), "event"));
+    CHECK_RC(ck(cudaEventRecord(c->ev_order, c->st), "event record"));
+    CHECK_RC(ck(cudaStreamWaitEvent(st, c->ev_order, 0), "stream wait"));
+  }
+  // one multi-simulation launch sequence per shape (order of first appearance)
+  std::vector<std::vector<cola_ctx*>> buckets;
+  for (int i = 0; i < n; ++i) {
+    bool placed = false;
+    for (auto& bk : buckets)
+      if (same_shape(bk[0], ctxs[i])) {
+        bk.push_back(ctxs[i]);
+        placed = true;
+        break;
+      }
+    if (!placed) buckets.push_back({ctxs[i]});
+  }
+  std::vector<GroupPlan> groups;
+  std::vector<int64_t> hsh;
+  for (const auto& bk : buckets) plan_groups(bk, (int)bk.size(), groups, hsh);
+  int64_t* dsh = nullptr;
+  if (!hsh.empty()) {
+    CHECK_RC(ck(cudaMallocAsync(&dsh, hsh.size() * sizeof(int64_t), st), "shift buffer"));
+    CHECK_RC(ck(write_words(dsh, hsh.data(), (int64_t)hsh.size(), st), "shift upload"));
+  }
+  int rc = COLA_OK;
+  for (GroupPlan& gp : groups) {
+    Multi* ms[5] = {&gp.g.all, &gp.g.unscreened.m, &gp.g.fr_screened.m, &gp.g.dgp_screened.m,
+                    &gp.g.screened.m};
+    for (int q = 0; q < 5; ++q) ms[q]->shift = ms[q]->nb > 1 ? dsh + gp.off[q] : nullptr;
+    cola_ctx* lead = gp.g.lead;
+    cudaStream_t saved = lead->st;
+    lead->st = st;
+    rc = enqueue_group_step(gp.g, lead->step);
+    lead->st = saved;
+    if (rc != COLA_OK) {
+      g_err = "cola_step_many: " + lead->err;
+      break;
+    }
+  }
+  if (dsh) cudaFreeAsync(dsh, st);
+  if (rc != COLA_OK) return rc;
+  for (int i = 0; i < n; ++i) {
+    cola_ctx* c = ctxs[i];
+    c->step += 1;
+    c->hh.step = c->step;
+    if (c->st == st) continue;
+    // later work on the context's own stream follows this step
+    CHECK_RC(ck(cudaEventRecord(c->ev_order, st), "event record"));
+    CHECK_RC(ck(cudaStreamWaitEvent(c->st, c->ev_order, 0), "stream wait"));
   }
   return COLA_OK;
 }

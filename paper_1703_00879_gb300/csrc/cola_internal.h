@@ -163,6 +163,9 @@ cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float*
 cudaError_t step_advance(SimHeader* hdr, cudaStream_t s, Multi m = {});
 // hdr = v (one simulation)
 cudaError_t set_header(SimHeader* hdr, const SimHeader& v, cudaStream_t s);
+// dst[0..n) = src[0..n) (host values) by kernels whose launch parameters carry
+// the values: stream-ordered, without a host synchronisation
+cudaError_t write_words(int64_t* dst, const int64_t* src, int64_t n, cudaStream_t s);
 // n floats at p set to zero in every simulation
 cudaError_t zero_f32(float* p, int64_t n, cudaStream_t s, Multi m = {});
 cudaError_t part_snapshot(const PartParams& pp, const float* sx, const float* sy, const float* sz,

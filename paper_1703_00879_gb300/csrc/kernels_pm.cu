@@ -335,6 +335,17 @@ __global__ void k_step_advance(SimHeader* hdr, Multi m) {
 
 __global__ void k_set_header(SimHeader* hdr, SimHeader v) { *hdr = v; }
 
+// Up to kParamWords int64 values carried in the launch parameters (a host to
+// device copy that neither synchronises nor needs pinned memory).
+constexpr int kParamWords = 480;
+struct ParamWords {
+  int64_t v[kParamWords];
+};
+__global__ void k_write_words(int64_t* __restrict__ dst, int n, const __grid_constant__ ParamWords w) {
+  const int i = threadIdx.x + blockIdx.x * blockDim.x;
+  if (i < n) dst[i] = w.v[i];
+}
+
 __global__ void __launch_bounds__(NTP) k_zero(float4* __restrict__ p, int64_t n4, Multi m) {
   p = moved(p, shift_of(m, blockIdx.y));
   for (int64_t i = (int64_t)blockIdx.x * NTP + threadIdx.x; i < n4; i += (int64_t)gridDim.x * NTP)
@@ -386,6 +397,18 @@ cudaError_t step_advance(SimHeader* hdr, cudaStream_t s, Multi m) {
 cudaError_t set_header(SimHeader* hdr, const SimHeader& v, cudaStream_t s) {
   k_set_header<<<1, 1, 0, s>>>(hdr, v);
   return cudaGetLastError();
+}
+
+cudaError_t write_words(int64_t* dst, const int64_t* src, int64_t n, cudaStream_t s) {
+  for (int64_t o = 0; o < n; o += kParamWords) {
+    ParamWords w;
+    const int c = (int)std::min<int64_t>(kParamWords, n - o);
+    for (int i = 0; i < c; ++i) w.v[i] = src[o + i];
+    k_write_words<<<(c + 127) / 128, 128, 0, s>>>(dst + o, c, w);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t zero_f32(float* p, int64_t n, cudaStream_t s, Multi m) {

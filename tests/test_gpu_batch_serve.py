@@ -108,6 +108,41 @@ def test_batch_rejects_mismatched_steps():
     b.close()
 
 
+def test_step_many_mixes_shapes_models_step_counts_and_progress():
+    """cola_step_many over runs of two shapes, every model, different step
+    counts, started at different times: each run ends where its solo run does."""
+    import paper_1703_00879_gb300 as pkg
+    runs = [ensemble_run(seed, Np=32, Nmesh=64, Lbox=64.0, nsteps=3 + seed % 3) for seed in range(6)]
+    runs += [ensemble_run(10 + seed, Np=32, Nmesh=32, Lbox=64.0, nsteps=4) for seed in range(2)]
+    solo = [_solo(pkg, r) for r in runs]
+    sims = [pkg.Simulation(r) for r in runs]
+    sims[1].step(2)                      # ahead of the others
+    sims[4].step(1)
+    while True:
+        live = [s for s in sims if s.steps_done < s.run.nsteps]
+        if not live:
+            break
+        pkg.step_many(live)
+    for r, s, (d0, (k0, P0, nm0)) in zip(runs, sims, solo):
+        assert s.steps_done == r.nsteps
+        assert np.max(np.abs(s.export(pkg.COLA_F_DISP) - d0)) / (r.Lbox / r.Nmesh) <= 1e-4
+        _, P, nm = s.pk()
+        ok = nm0 > 0
+        assert np.max(np.abs(P[ok] / P0[ok] - 1)) <= 1e-4
+        s.close()
+
+
+def test_step_many_rejects_finished_and_duplicate_contexts():
+    import paper_1703_00879_gb300 as pkg
+    r = ensemble_run(0, Np=32, Nmesh=32, Lbox=64.0, nsteps=1)
+    with pkg.Simulation(r) as a, pkg.Simulation(r.with_(seed=5)) as b:
+        with pytest.raises(pkg.ColaError):
+            pkg.step_many([a, a])
+        pkg.step_many([a, b])
+        with pytest.raises(pkg.ColaError):
+            pkg.step_many([a])
+
+
 def test_serving_results_equal_solo_runs():
     import paper_1703_00879_gb300 as pkg
     from paper_1703_00879_gb300.serve import Server
