@@ -179,6 +179,24 @@ def cola_host_timesteps(run):
     return out
 
 
+_ALLOCATORS: dict = {}
+
+
+def _torch_allocator(dev: int):
+    """(alloc, free) C callbacks into PyTorch's caching allocator for device `dev` (one pair per device)."""
+    if dev not in _ALLOCATORS:
+        import torch
+
+        def _alloc(nbytes, stream, user):
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+
+        def _free(ptr, stream, user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        _ALLOCATORS[dev] = (ALLOC_FN(_alloc), FREE_FN(_free))
+    return _ALLOCATORS[dev]
+
+
 class Simulation:
     """One libcola context: cola_init + cola_set_model (+ cola_ic) on the current torch stream."""
 
@@ -197,14 +215,7 @@ class Simulation:
         self.cfg = cfg
         dev = self.device
 
-        def _alloc(nbytes, stream, user):
-            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
-
-        def _free(ptr, stream, user):
-            torch.cuda.caching_allocator_delete(ptr)
-
-        self._alloc_cb = ALLOC_FN(_alloc) if torch_alloc else ALLOC_FN()
-        self._free_cb = FREE_FN(_free) if torch_alloc else FREE_FN()
+        self._alloc_cb, self._free_cb = _torch_allocator(dev) if torch_alloc else (ALLOC_FN(), FREE_FN())
         h = _P()
         _check(L.cola_init(ctypes.byref(cfg), self._alloc_cb, self._free_cb, None,
                            _P(self.stream.cuda_stream), ctypes.byref(h)))

@@ -140,7 +140,7 @@ __device__ __forceinline__ void dftR(float2* v) {
   }
 }
 
-constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 
 // L = R1 R2 with R1 <= R2 <= 32.
 template <int L>
@@ -151,17 +151,30 @@ struct Split {
   static_assert(R2 <= 32 && R1 * R2 == L, "transform length");
 };
 
+// Rows of shared memory a length-L tile transform needs: L, plus R2 padding
+// rows for the intermediate of tiles whose row pitch is a multiple of 8.
+template <int L>
+__host__ __device__ constexpr int fft_rows() {
+  return L + Split<L>::R2;
+}
+
 // Length-L transform of the TW columns of a shared-memory tile (four-step):
 // step 1: for each n2 < R2, DFT_R1 over x[R2 n1 + n2], times w_L^(n2 k1);
 // step 2: for each k1 < R1, DFT_R2 over n2 gives X[k1 + R1 k2].
-// The intermediate Y[n2][k1] is stored at row R2 k1 + ((n2 + k1) mod R2) so that
-// the step-2 reads of adjacent k1 fall in different banks.  tw has L * TWS
-// entries; the caller synchronises before the call; returns after a barrier.
+// Where the intermediate Y[n2][k1] goes, so that the 16 lanes of a half-warp
+// hit 16 different bank pairs:
+//  * row pitch a multiple of 8 (column tiles): row n2 (R1 + 1) + k1, one
+//    padding row per R1 (the tile needs fft_rows<L>() rows); every address is
+//    then a per-thread base plus a compile-time offset;
+//  * odd row pitch (row tiles): row R2 k1 + ((n2 + k1) mod R2), in place.
+// tw has L * TWS entries; the caller synchronises before the call; returns
+// after a barrier.
 template <int L, int TW, int PITCH, int NT, bool INV, int TWS = 1>
 __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2* __restrict__ tw) {
   constexpr int R1 = Split<L>::R1, R2 = Split<L>::R2;
   constexpr int U1 = TW * R2, P1 = (U1 + NT - 1) / NT;
   constexpr int U2 = TW * R1, P2 = (U2 + NT - 1) / NT;
+  constexpr bool PAD = (PITCH % 8) == 0;
   const int tid = threadIdx.x;
   {
     float2 v[P1][R1];
@@ -189,9 +202,15 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
       const int u = tid + i * NT;
       if ((U1 % NT) == 0 || u < U1) {
         const int c = u % TW, n2 = u / TW;
+        if constexpr (PAD) {
+          float2* y = buf + n2 * (R1 + 1) * PITCH + c;
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1)
-          buf[(R2 * k1 + ((n2 + k1) & (R2 - 1))) * PITCH + c] = v[i][pos_of<R1>(k1)];
+          for (int k1 = 0; k1 < R1; ++k1) y[k1 * PITCH] = v[i][pos_of<R1>(k1)];
+        } else {
+#pragma unroll
+          for (int k1 = 0; k1 < R1; ++k1)
+            buf[(R2 * k1 + ((n2 + k1) & (R2 - 1))) * PITCH + c] = v[i][pos_of<R1>(k1)];
+        }
       }
     }
   }
@@ -203,8 +222,14 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
       const int u = tid + i * NT;
       if ((U2 % NT) == 0 || u < U2) {
         const int c = u % TW, k1 = u / TW;
+        if constexpr (PAD) {
+          const float2* yr = buf + k1 * PITCH + c;
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) y[i][n2] = buf[(R2 * k1 + ((n2 + k1) & (R2 - 1))) * PITCH + c];
+          for (int n2 = 0; n2 < R2; ++n2) y[i][n2] = yr[n2 * (R1 + 1) * PITCH];
+        } else {
+#pragma unroll
+          for (int n2 = 0; n2 < R2; ++n2) y[i][n2] = buf[(R2 * k1 + ((n2 + k1) & (R2 - 1))) * PITCH + c];
+        }
         dftR<R2, INV>(y[i]);
       }
     }

@@ -54,8 +54,11 @@ constexpr int row_tw(int N) { return 8192 / N < 8 ? 8 : (8192 / N > 64 ? 64 : 81
 constexpr int blocks_for_smem(size_t bytes, int N) {
   return bytes > 112 * 1024 ? 1 : (bytes > 72 * 1024 || N >= 512 ? 2 : 3);
 }
+// Stage buffer of a column tile: fft_rows rows (the transform's padding rows
+// follow the N data rows) of NBUF arrays x TW columns.
+constexpr int col_rows(int N) { return N + (1 << (ilog2(N) - ilog2(N) / 2)); }
 constexpr size_t col_smem_c(int N, int NBUF) {
-  return (N + 2 * (size_t)N * NBUF * col_tw(N, NBUF)) * 8;
+  return (N + 2 * (size_t)col_rows(N) * NBUF * col_tw(N, NBUF)) * 8;
 }
 
 int sm_count() {
@@ -196,6 +199,10 @@ struct ColGeo {
 
 // Software pipeline over the tiles of one launch.  Op supplies
 //   issue(buf, t): cp.async the inputs of tile t into buf (no commit)
+//   issue_side(t): cp.async of a second input of tile t into op.extra (no commit;
+//     may do nothing); its group is committed BEFORE the next tile's prefetch,
+//     so process() can wait for it with cp_async_wait<1>() while the prefetch
+//     of tile t + grid stays in flight
 //   process(buf, tw, t): transform + store (leaves buf free after a final barrier)
 template <int N, int BUFELEMS, class Op>
 __device__ __forceinline__ void col_pipeline(Op op, const float2* __restrict__ twg,
@@ -211,10 +218,12 @@ __device__ __forceinline__ void col_pipeline(Op op, const float2* __restrict__ t
   cp_async_commit();
   int cur = 0;
   for (; t < ntiles; t += gridDim.x) {
+    op.issue_side(t);  // op.extra is free: the previous tile ended with a barrier
+    cp_async_commit();
     const int64_t tn = t + gridDim.x;
     if (tn < ntiles) op.issue(cur ? b0 : b1, tn);
     cp_async_commit();
-    cp_async_wait<1>();
+    cp_async_wait<2>();  // tile t's main input has landed
     __syncthreads();
     op.process(cur ? b1 : b0, tw, t);
     __syncthreads();
@@ -229,6 +238,7 @@ struct OpCol {
   ColGeo<N, TW> geo;
   float2* data;
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
+  __device__ __forceinline__ void issue_side(int64_t) const {}
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
     int o, c0;
     int64_t base, by;
@@ -247,7 +257,7 @@ struct OpCol {
 template <int N, int TW, bool INV>
 __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1), N)) k_col(OpCol<N, TW, INV> op, const float2* __restrict__ twg,
                                             int64_t ntiles) {
-  col_pipeline<N, N * TW>(op, twg, ntiles);
+  col_pipeline<N, fft_rows<N>() * TW>(op, twg, ntiles);
 }
 
 // ---------------------------------------------------------------- y inverse, two outputs
@@ -258,6 +268,7 @@ struct OpYinv2 {
   float2 *outp, *outd;
   float kfs;
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
+  __device__ __forceinline__ void issue_side(int64_t) const {}
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
     int o, c0;
     int64_t base, by;
@@ -284,7 +295,7 @@ struct OpYinv2 {
 template <int N, int TW>
 __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 2), N)) k_yinv2(OpYinv2<N, TW> op, const float2* __restrict__ twg,
                                               int64_t ntiles) {
-  col_pipeline<N, N * 2 * TW>(op, twg, ntiles);
+  col_pipeline<N, fft_rows<N>() * 2 * TW>(op, twg, ntiles);
 }
 
 // ---------------------------------------------------------------- screening field (z pass)
@@ -295,6 +306,7 @@ struct OpZScreenField {
   float2 *dk_out, *w_out;
   ForceParams fp;
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
+  __device__ __forceinline__ void issue_side(int64_t) const {}
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
     int o, c0;
     int64_t base, by;
@@ -333,7 +345,7 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1), N) < 2 ?
                                                        const float2* __restrict__ twg,
                                                        int64_t ntiles) {
   if (!op.geo.m.shift) resolve(op.fp, 0);  // one simulation: once per launch
-  col_pipeline<N, N * TW>(op, twg, ntiles);
+  col_pipeline<N, fft_rows<N>() * TW>(op, twg, ntiles);
 }
 
 // ---------------------------------------------------------------- force (z pass)
@@ -355,6 +367,15 @@ struct OpZForce {
     geo.tile(t, o, c0, base, by);
     col_issue<N, TW, TW>(buf, 0, moved(in, by), base, geo.sn, c0);
   }
+  // delta(k) of the tile into extra; lands while S is transformed
+  __device__ __forceinline__ void issue_side(int64_t t) const {
+    if (SCREENED) {
+      int o, c0;
+      int64_t base, by;
+      geo.tile(t, o, c0, base, by);
+      col_issue<N, TW, TW>(extra, 0, moved(dk, by), base, geo.sn, c0);
+    }
+  }
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
     int iy, c0;
     int64_t base, by;
@@ -362,14 +383,10 @@ struct OpZForce {
     ForceParams fp = this->fp;
     resolve(fp, by);
     float2* ph = extra;  // delta(k) of the tile, then Phi_tot(k), N x TW
-    if (SCREENED) {
-      col_issue<N, TW, TW>(ph, 0, moved(dk, by), base, geo.sn, c0);  // lands while S is transformed
-      cp_async_commit();
-    }
     fft_tile_call<N, TW, TW, NT, false>(buf, tw);
     if (KEEP) col_store<N, TW, TW>(buf, 0, moved(dk_keep, by), base, geo.sn, c0);
     if (SCREENED) {
-      cp_async_wait<0>();
+      cp_async_wait<1>();  // delta(k) of this tile; the next tile's prefetch may still be in flight
       __syncthreads();
     }
 #pragma unroll 2
@@ -412,7 +429,7 @@ template <int N, int TW, bool SCREENED, bool KEEP>
 __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1) + (size_t)N * TW * 8, N) < 2 ? 1 : 2) k_z_force(
     OpZForce<N, TW, SCREENED, KEEP> op, const float2* __restrict__ twg, int64_t ntiles) {
   if (!op.geo.m.shift) resolve(op.fp, 0);  // one simulation: once per launch
-  col_pipeline<N, N * TW>(op, twg, ntiles);
+  col_pipeline<N, fft_rows<N>() * TW>(op, twg, ntiles);
 }
 
 // ---------------------------------------------------------------- LPT reweight (z pass)
@@ -436,6 +453,7 @@ struct OpLptZ {
   float2 *o0, *o1, *o2, *o3;
   LptParams lp;
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
+  __device__ __forceinline__ void issue_side(int64_t) const {}
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
     int o, c0;
     int64_t base, by;
@@ -507,7 +525,7 @@ template <int N, int TW, int PREC>
 __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 4), N)) k_lpt_z(OpLptZ<N, TW, PREC> op,
                                               const float2* __restrict__ twg, int64_t ntiles) {
   if (!op.geo.m.shift) resolve(op.lp, 0);  // one simulation: once per launch
-  col_pipeline<N, N * 4 * TW>(op, twg, ntiles);
+  col_pipeline<N, fft_rows<N>() * 4 * TW>(op, twg, ntiles);
 }
 
 // ---------------------------------------------------------------- x passes (rows)
@@ -768,21 +786,22 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
     resolve(fp, r.by);
     const int64_t tn = t + gridDim.x;
     float2* stc = cur ? st1 : st0;
+    cp_async_wait<0>();  // w rows of this tile (the only group in flight)
+    __syncthreads();
+    put_c2r<N, TWX>(buf, stc, 0.f);
+    __syncthreads();
+    // the current staging buffer is free again: the density rows of this tile,
+    // then the next tile's w rows into the other buffer (landing during this tile)
+    stage_real_rows<N, TWX>(stc, moved(rho, r.by), row0);
+    cp_async_commit();
     if (tn < ntiles) {
       const RowTile rn = row_tile<TWX>(tn, tps, m);
       stage_complex_rows<N, TWX>(cur ? st0 : st1, moved(w_in, rn.by), rn.row0, P);
     }
     cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    put_c2r<N, TWX>(buf, stc, 0.f);
-    __syncthreads();
-    // the current staging buffer is free again: bring in the density rows of this tile
-    stage_real_rows<N, TWX>(stc, moved(rho, r.by), row0);
-    cp_async_commit();
     row_c2r_combine<N, TWX, C::PITCH>(buf, tw);
     fft_tile_call<M, TWX, C::PITCH, NT, true, 2>(buf, tw);
-    cp_async_wait<0>();
+    cp_async_wait<1>();  // the density rows; the next tile's prefetch may still be in flight
     __syncthreads();
     const float2* rr = stc;  // row r holds N floats = M float2
     for (int e = threadIdx.x; e < TWX * M; e += NT) {
@@ -804,7 +823,8 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
 // ---------------------------------------------------------------- launch helpers
 template <int N, int NBUF>
 constexpr size_t col_smem() {
-  return (N + 2 * (size_t)N * NBUF * col_tw(N, NBUF)) * sizeof(float2);
+  static_assert(col_rows(N) == fft_rows<N>(), "column stage rows");
+  return col_smem_c(N, NBUF);
 }
 
 template <int N>
