@@ -247,6 +247,101 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
   __syncthreads();
 }
 
+// Row pitch (complex values) of a row-major tile transformed in place by
+// fft_rowtile<L>: at least L + R2 - 1 (room for the padded intermediate) and
+// 8 mod 16, so that the half-warps of both steps hit distinct bank pairs.
+template <int L>
+__host__ __device__ constexpr int rowtile_pitch() {
+  return ((L + Split<L>::R2 - 1 - 8 + 15) / 16) * 16 + 8;
+}
+
+struct NoPre {
+  __device__ __forceinline__ float2 operator()(float2 v) const { return v; }
+};
+
+// Length-L transforms of the TW rows of a row-major shared-memory tile, in
+// place: row c holds x[n] at buf[c * CW + n] (CW = rowtile_pitch<L>()).  Same
+// four-step factorisation as fft_tile, with the element index as the fast
+// thread index (consecutive lanes touch consecutive elements of one row):
+// step 1 (thread = (c, n2)): DFT_R1 over x[R2 n1 + n2] (each value passed
+// through pre() as it is loaded), times w_L^(n2 k1), intermediate at
+// n2 (R1 + 1) + k1; step 2 (thread = (c, k1)): DFT_R2 gives X[k1 + R1 k2].
+// The caller synchronises before the call; returns after a barrier.
+template <int L, int TW, int CW, int NT, bool INV, int TWS = 1, class Pre = NoPre>
+__device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const float2* __restrict__ tw,
+                                            Pre pre = Pre()) {
+  constexpr int R1 = Split<L>::R1, R2 = Split<L>::R2;
+  constexpr int U1 = TW * R2, P1 = (U1 + NT - 1) / NT;
+  constexpr int U2 = TW * R1, P2 = (U2 + NT - 1) / NT;
+  static_assert(CW >= L + R2 - 1, "row pitch too small for the intermediate");
+  const int tid = threadIdx.x;
+  {
+    float2 v[P1][R1];
+#pragma unroll
+    for (int i = 0; i < P1; ++i) {
+      const int u = tid + i * NT;
+      if ((U1 % NT) == 0 || u < U1) {
+        const int c = u / R2, n2 = u % R2;
+        const float2* x = buf + c * CW + n2;
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) v[i][n1] = pre(x[R2 * n1]);
+        dftR<R1, INV>(v[i]);
+        if (n2 > 0) {
+#pragma unroll
+          for (int k1 = 1; k1 < R1; ++k1) {
+            float2 w = tw[n2 * k1 * TWS];
+            if (INV) w.y = -w.y;
+            v[i][pos_of<R1>(k1)] = cmul(v[i][pos_of<R1>(k1)], w);
+          }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < P1; ++i) {
+      const int u = tid + i * NT;
+      if ((U1 % NT) == 0 || u < U1) {
+        const int c = u / R2, n2 = u % R2;
+        float2* y = buf + c * CW + n2 * (R1 + 1);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) y[k1] = v[i][pos_of<R1>(k1)];
+      }
+    }
+  }
+  __syncthreads();
+  {
+    float2 y[P2][R2];
+#pragma unroll
+    for (int i = 0; i < P2; ++i) {
+      const int u = tid + i * NT;
+      if ((U2 % NT) == 0 || u < U2) {
+        const int c = u / R1, k1 = u % R1;
+        const float2* yr = buf + c * CW + k1;
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) y[i][n2] = yr[n2 * (R1 + 1)];
+        dftR<R2, INV>(y[i]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < P2; ++i) {
+      const int u = tid + i * NT;
+      if ((U2 % NT) == 0 || u < U2) {
+        const int c = u / R1, k1 = u % R1;
+        float2* X = buf + c * CW + k1;
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) X[R1 * k2] = y[i][pos_of<R2>(k2)];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int L, int TW, int CW, int NT, bool INV, int TWS = 1, class Pre = NoPre>
+__device__ __noinline__ void fft_rowtile_call(float2* buf, const float2* tw, Pre pre = Pre()) {
+  fft_rowtile<L, TW, CW, NT, INV, TWS, Pre>(buf, tw, pre);
+}
+
 // Out-of-line copy for kernels that run several transforms per tile: each
 // call gets its own register allocation instead of one inlined body per call.
 template <int L, int TW, int PITCH, int NT, bool INV, int TWS = 1>

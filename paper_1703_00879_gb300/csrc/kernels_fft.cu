@@ -529,17 +529,55 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 4), N)) k_lp
 }
 
 // ---------------------------------------------------------------- x passes (rows)
+// A row tile holds TWX rows of the half-length complex transform (M = N/2)
+// row-major in shared memory, row r at st[r * CW + k] (CW = rowtile_pitch<M>),
+// exactly as cp.async staged them; the transform runs in place
+// (fft_rowtile).  Tiles are double-buffered: the next tile is staged into the
+// other buffer while the current one is transformed.
+template <int N, int TWX>
+struct RowCfg {
+  static constexpr int M = N / 2;
+  static constexpr int CW = rowtile_pitch<M>();    // complex values per staged row (>= M + 2)
+  static constexpr size_t stage = (size_t)TWX * CW;  // float2 per buffer
+  static constexpr size_t smem = (N + 2 * stage) * sizeof(float2);
+};
+
+// complex half rows (M + 1 values, staged as M + 2 to keep 16-byte chunks)
+template <int N, int TWX>
+__device__ __forceinline__ void stage_complex_rows(float2* st, const float2* __restrict__ in,
+                                                   int64_t row0, int64_t P) {
+  using C = RowCfg<N, TWX>;
+  constexpr int CH = (C::M + 2) / 2;
+  for (int e = threadIdx.x; e < TWX * CH; e += NT) {
+    const int r = e / CH, j = e - r * CH;
+    cp_async16(st + r * C::CW + 2 * j, in + (row0 + r) * P + 2 * j, true);
+  }
+}
+
+// real rows of N floats: row r at floats [2 CW r, 2 CW r + N), i.e. the M
+// complex values z[j] = x[2j] + i x[2j+1] at st[r * CW + j]
+template <int N, int TWX>
+__device__ __forceinline__ void stage_real_rows(float* st, const float* __restrict__ in, int64_t row0,
+                                                int pitch_floats) {
+  constexpr int CH = N / 4;
+  for (int e = threadIdx.x; e < TWX * CH; e += NT) {
+    const int r = e / CH, j = e - r * CH;
+    cp_async16(st + r * pitch_floats + 4 * j, in + (row0 + r) * N + 4 * j, true);
+  }
+}
+
 // r2c post-processing: X[k] = (Z[k] + conj Z[M-k])/2 - i/2 w^k (Z[k] - conj Z[M-k]).
-template <int N, int TWX, int PITCH>
+template <int N, int TWX>
 __device__ __forceinline__ void row_r2c_store(const float2* buf, const float2* tw,
-                                              float2* __restrict__ out, int64_t row0,
-                                              int64_t P) {
+                                              float2* __restrict__ out, int64_t row0, int64_t P) {
+  using C = RowCfg<N, TWX>;
   constexpr int M = N / 2;
 #pragma unroll 2
   for (int e = threadIdx.x; e < TWX * (M + 1); e += NT) {
     const int r = e / (M + 1), k = e - r * (M + 1);
-    const float2 a = buf[(k & (M - 1)) * PITCH + r];
-    const float2 b = cconj(buf[((M - k) & (M - 1)) * PITCH + r]);
+    const float2* z = buf + r * C::CW;
+    const float2 a = z[k & (M - 1)];
+    const float2 b = cconj(z[(M - k) & (M - 1)]);
     const float2 E = cscale(cadd(a, b), 0.5f);
     const float2 D = csub(a, b);
     const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);  // (-i/2) D
@@ -547,93 +585,42 @@ __device__ __forceinline__ void row_r2c_store(const float2* buf, const float2* t
   }
 }
 
-// c2r pre-processing (unnormalised inverse, 2x folded in), on a tile already in
-// buf[k * PITCH + r], k = 0..M: E = X[k] + conj X[M-k], O = w^-k (X[k] - conj X[M-k]),
+// The c2r input convention on a staged spectrum value X[k] (k = 0..M): the
+// optional derivative i kfs k (zero at the Nyquist k = M), and the imaginary
+// parts of X[0], X[M] dropped.
+template <int M>
+__device__ __forceinline__ float2 c2r_in(float2 x, int k, float kfs) {
+  if (kfs != 0.f) x = (k == M) ? make_float2(0.f, 0.f) : cscale(cmul_i(x), kfs * (float)k);
+  if (k == 0 || k == M) x.y = 0.f;
+  return x;
+}
+
+// c2r pre-processing in place on each staged row (unnormalised inverse, 2x
+// folded in): E = X[k] + conj X[M-k], O = w^-k (X[k] - conj X[M-k]),
 // Z[k] = E + i O, Z[M-k] = conj E + i conj O.
-template <int N, int TWX, int PITCH>
-__device__ __forceinline__ void row_c2r_combine(float2* buf, const float2* tw) {
+template <int N, int TWX>
+__device__ __forceinline__ void row_c2r_combine(float2* buf, const float2* tw, float kfs) {
+  using C = RowCfg<N, TWX>;
   constexpr int M = N / 2;
   for (int e = threadIdx.x; e < TWX * (M / 2 + 1); e += NT) {
     const int r = e / (M / 2 + 1), k = e - r * (M / 2 + 1);
-    const float2 a = buf[k * PITCH + r];
-    const float2 b = cconj(buf[(M - k) * PITCH + r]);
+    float2* z = buf + r * C::CW;
+    const float2 a = c2r_in<M>(z[k], k, kfs);
+    const float2 b = cconj(c2r_in<M>(z[M - k], M - k, kfs));
     const float2 E = cadd(a, b);
     const float2 O = cmul(cconj(tw[k]), csub(a, b));
-    buf[k * PITCH + r] = cadd(E, cmul_i(O));
-    if (k != 0 && k != M - k) buf[(M - k) * PITCH + r] = cadd(cconj(E), cmul_i(cconj(O)));
+    z[k] = cadd(E, cmul_i(O));
+    if (k != 0 && k != M - k) z[M - k] = cadd(cconj(E), cmul_i(cconj(O)));
   }
   __syncthreads();
 }
 
-// Up to six independent row transforms per launch (job = tile / tiles_per_job).
-struct RowJobs {
-  const void* in[6];
-  void* out[6];
-  float kfs[6];
-  int njobs;
+struct ScaleOffset {
+  float scale, offset;
+  __device__ __forceinline__ float2 operator()(float2 v) const {
+    return make_float2(fmaf(v.x, scale, offset), fmaf(v.y, scale, offset));
+  }
 };
-
-// Row tiles are staged raw with cp.async (double-buffered, row-major), then
-// transposed in shared memory into the transform layout buf[k * (TWX+1) + r].
-// Complex half rows are staged as M + 2 values (the pitch leaves room for the
-// padding value, and M + 2 keeps 16-byte chunks); real rows as N floats.
-template <int N, int TWX>
-struct RowCfg {
-  static constexpr int M = N / 2;
-  static constexpr int PITCH = TWX + 1;
-  static constexpr int CW = M + 2;                       // staged complex values per row
-  static constexpr size_t fftbuf = (size_t)(M + 1) * PITCH;  // float2
-  static constexpr size_t stage = (size_t)TWX * CW;          // float2 (>= TWX * N floats)
-  static constexpr size_t smem = (N + fftbuf + 2 * stage) * sizeof(float2);
-};
-
-template <int N, int TWX>
-__device__ __forceinline__ void stage_complex_rows(float2* st, const float2* __restrict__ in,
-                                                   int64_t row0, int64_t P) {
-  using C = RowCfg<N, TWX>;
-  constexpr int CH = C::CW / 2;
-  for (int e = threadIdx.x; e < TWX * CH; e += NT) {
-    const int r = e / CH, j = e - r * CH;
-    cp_async16(st + r * C::CW + 2 * j, in + (row0 + r) * P + 2 * j, true);
-  }
-}
-
-template <int N, int TWX>
-__device__ __forceinline__ void stage_real_rows(float2* st, const float* __restrict__ in,
-                                                int64_t row0) {
-  constexpr int CH = N / 4;
-  float* s = reinterpret_cast<float*>(st);
-  for (int e = threadIdx.x; e < TWX * CH; e += NT) {
-    const int r = e / CH, j = e - r * CH;
-    cp_async16(s + r * N + 4 * j, in + (row0 + r) * N + 4 * j, true);
-  }
-}
-
-// staged complex rows -> transform layout, with the i kfs k multiplier and the
-// imaginary parts of X[0], X[M] dropped (c2r input convention)
-template <int N, int TWX>
-__device__ __forceinline__ void put_c2r(float2* buf, const float2* st, float kfs) {
-  using C = RowCfg<N, TWX>;
-  constexpr int M = N / 2;
-  for (int e = threadIdx.x; e < TWX * (M + 1); e += NT) {
-    const int r = e / (M + 1), k = e - r * (M + 1);
-    float2 x = st[r * C::CW + k];
-    if (kfs != 0.f) x = (k == M) ? make_float2(0.f, 0.f) : cscale(cmul_i(x), kfs * (float)k);
-    if (k == 0 || k == M) x.y = 0.f;
-    buf[k * C::PITCH + r] = x;
-  }
-}
-
-template <int N, int TWX>
-__device__ __forceinline__ void put_r2c(float2* buf, const float2* st, float scale, float offset) {
-  using C = RowCfg<N, TWX>;
-  constexpr int M = N / 2;
-  for (int e = threadIdx.x; e < TWX * M; e += NT) {
-    const int r = e / M, j = e - r * M;
-    const float2 v = st[r * M + j];  // row r holds N floats = M float2
-    buf[j * C::PITCH + r] = make_float2(v.x * scale + offset, v.y * scale + offset);
-  }
-}
 
 // Row tile t of a multi-simulation launch: simulation t / tps, first row (t mod tps) TWX.
 struct RowTile {
@@ -654,14 +641,13 @@ __global__ void __launch_bounds__(NT, 2) k_xr2c(const float* __restrict__ in, fl
   constexpr int M = N / 2;
   extern __shared__ __align__(16) float2 sm[];
   float2* tw = sm;
-  float2* buf = sm + N;
-  float2* st0 = buf + C::fftbuf + (C::fftbuf & 1);
+  float2* st0 = sm + N;
   float2* st1 = st0 + C::stage;
   load_tw(tw, twg, N);
   int64_t t = blockIdx.x;
   if (t < ntiles) {
     const RowTile r = row_tile<TWX>(t, tps, m);
-    stage_real_rows<N, TWX>(st0, moved(in, r.by), r.row0);
+    stage_real_rows<N, TWX>(reinterpret_cast<float*>(st0), moved(in, r.by), r.row0, 2 * C::CW);
   }
   cp_async_commit();
   int cur = 0;
@@ -669,21 +655,28 @@ __global__ void __launch_bounds__(NT, 2) k_xr2c(const float* __restrict__ in, fl
     const int64_t tn = t + gridDim.x;
     if (tn < ntiles) {
       const RowTile r = row_tile<TWX>(tn, tps, m);
-      stage_real_rows<N, TWX>(cur ? st0 : st1, moved(in, r.by), r.row0);
+      stage_real_rows<N, TWX>(reinterpret_cast<float*>(cur ? st0 : st1), moved(in, r.by), r.row0, 2 * C::CW);
     }
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    put_r2c<N, TWX>(buf, cur ? st1 : st0, scale, offset);
-    __syncthreads();
-    fft_tile<M, TWX, C::PITCH, NT, false, 2>(buf, tw);
+    float2* buf = cur ? st1 : st0;
+    fft_rowtile<M, TWX, C::CW, NT, false, 2>(buf, tw, ScaleOffset{scale, offset});
     const RowTile r = row_tile<TWX>(t, tps, m);
-    row_r2c_store<N, TWX, C::PITCH>(buf, tw, moved(out, r.by), r.row0, P);
+    row_r2c_store<N, TWX>(buf, tw, moved(out, r.by), r.row0, P);
     __syncthreads();
     cur ^= 1;
   }
   cp_async_wait<0>();
 }
+
+// Up to six independent row transforms per launch (job = tile / tiles_per_job).
+struct RowJobs {
+  const void* in[6];
+  void* out[6];
+  float kfs[6];
+  int njobs;
+};
 
 // Tile t of a multi-job, multi-simulation c2r launch: simulation, job, first row.
 struct JobTile {
@@ -699,15 +692,14 @@ __device__ __forceinline__ JobTile job_tile(int64_t t, int64_t tpj, int njobs, i
 }
 
 template <int N, int TWX>
-__global__ void __launch_bounds__(NT, 2) k_xc2r(RowJobs jobs, int64_t P,
+__global__ void __launch_bounds__(NT, 2) k_xc2r(const __grid_constant__ RowJobs jobs, int64_t P,
                                                 const float2* __restrict__ twg, int64_t tiles_per_job,
                                                 Multi m) {
   using C = RowCfg<N, TWX>;
   constexpr int M = N / 2;
   extern __shared__ __align__(16) float2 sm[];
   float2* tw = sm;
-  float2* buf = sm + N;
-  float2* st0 = buf + C::fftbuf + (C::fftbuf & 1);
+  float2* st0 = sm + N;
   float2* st1 = st0 + C::stage;
   load_tw(tw, twg, N);
   const int64_t ntiles = tiles_per_job * jobs.njobs * m.nb;
@@ -720,8 +712,6 @@ __global__ void __launch_bounds__(NT, 2) k_xc2r(RowJobs jobs, int64_t P,
   int cur = 0;
   for (; t < ntiles; t += gridDim.x) {
     const JobTile j = job_tile(t, tiles_per_job, jobs.njobs, TWX, m);
-    const int job = j.job;
-    const int64_t row0 = j.row0;
     const int64_t tn = t + gridDim.x;
     if (tn < ntiles) {
       const JobTile jn = job_tile(tn, tiles_per_job, jobs.njobs, TWX, m);
@@ -731,14 +721,13 @@ __global__ void __launch_bounds__(NT, 2) k_xc2r(RowJobs jobs, int64_t P,
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    put_c2r<N, TWX>(buf, cur ? st1 : st0, jobs.kfs[job]);
-    __syncthreads();
-    row_c2r_combine<N, TWX, C::PITCH>(buf, tw);
-    fft_tile<M, TWX, C::PITCH, NT, true, 2>(buf, tw);
-    float* out = moved(static_cast<float*>(jobs.out[job]), j.by);
+    float2* buf = cur ? st1 : st0;
+    row_c2r_combine<N, TWX>(buf, tw, jobs.kfs[j.job]);
+    fft_rowtile<M, TWX, C::CW, NT, true, 2>(buf, tw);
+    float* out = moved(static_cast<float*>(jobs.out[j.job]), j.by);
     for (int e = threadIdx.x; e < TWX * M; e += NT) {
-      const int r = e / M, j = e % M;
-      reinterpret_cast<float2*>(out + (row0 + r) * N)[j] = buf[j * C::PITCH + r];
+      const int r = e / M, q = e % M;
+      reinterpret_cast<float2*>(out + (j.row0 + r) * N)[q] = buf[r * C::CW + q];
     }
     __syncthreads();
     cur ^= 1;
@@ -757,6 +746,14 @@ __device__ __forceinline__ float screen_eps(float w, const ForceParams& fp) {
   }
 }
 
+// Screening source S = delta eps: c2r of the screening field rows, eps from the
+// field and delta from rho in the same tile, r2c.  Shared memory: twiddles, two
+// row tiles (double-buffered field rows), one tile of density rows.
+template <int N, int TWX>
+constexpr size_t xscreen_smem() {
+  return RowCfg<N, TWX>::smem + (size_t)TWX * N * sizeof(float);
+}
+
 template <int N, int TWX, int MODEL>
 __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w_in,
                                                     const float* __restrict__ rho,
@@ -768,9 +765,9 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
   constexpr int M = N / 2;
   extern __shared__ __align__(16) float2 sm[];
   float2* tw = sm;
-  float2* buf = sm + N;
-  float2* st0 = buf + C::fftbuf + (C::fftbuf & 1);
+  float2* st0 = sm + N;
   float2* st1 = st0 + C::stage;
+  float* rr = reinterpret_cast<float*>(st1 + C::stage);  // density rows, TWX x N floats
   load_tw(tw, twg, N);
   int64_t t = blockIdx.x;
   if (t < ntiles) {
@@ -785,35 +782,33 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
     ForceParams fp = fp0;
     resolve(fp, r.by);
     const int64_t tn = t + gridDim.x;
-    float2* stc = cur ? st1 : st0;
+    float2* buf = cur ? st1 : st0;
     cp_async_wait<0>();  // w rows of this tile (the only group in flight)
     __syncthreads();
-    put_c2r<N, TWX>(buf, stc, 0.f);
-    __syncthreads();
-    // the current staging buffer is free again: the density rows of this tile,
-    // then the next tile's w rows into the other buffer (landing during this tile)
-    stage_real_rows<N, TWX>(stc, moved(rho, r.by), row0);
+    // the density rows of this tile, then the next tile's w rows into the other
+    // buffer; both land while this tile's field is transformed
+    stage_real_rows<N, TWX>(rr, moved(rho, r.by), row0, N);
     cp_async_commit();
     if (tn < ntiles) {
       const RowTile rn = row_tile<TWX>(tn, tps, m);
       stage_complex_rows<N, TWX>(cur ? st0 : st1, moved(w_in, rn.by), rn.row0, P);
     }
     cp_async_commit();
-    row_c2r_combine<N, TWX, C::PITCH>(buf, tw);
-    fft_tile_call<M, TWX, C::PITCH, NT, true, 2>(buf, tw);
+    row_c2r_combine<N, TWX>(buf, tw, 0.f);
+    fft_rowtile_call<M, TWX, C::CW, NT, true, 2>(buf, tw);
     cp_async_wait<1>();  // the density rows; the next tile's prefetch may still be in flight
     __syncthreads();
-    const float2* rr = stc;  // row r holds N floats = M float2
+    const float2* rv2 = reinterpret_cast<const float2*>(rr);  // row r holds N floats = M float2
     for (int e = threadIdx.x; e < TWX * M; e += NT) {
-      const int r = e / M, j = e % M;
-      const float2 w = buf[j * C::PITCH + r];
-      const float2 rv = rr[r * M + j];
+      const int r2 = e / M, j = e % M;
+      const float2 w = buf[r2 * C::CW + j];
+      const float2 rv = rv2[r2 * M + j];
       const float d0 = rv.x * fp.inv_rhobar - 1.f, d1 = rv.y * fp.inv_rhobar - 1.f;
-      buf[j * C::PITCH + r] = make_float2(d0 * screen_eps<MODEL>(w.x, fp), d1 * screen_eps<MODEL>(w.y, fp));
+      buf[r2 * C::CW + j] = make_float2(d0 * screen_eps<MODEL>(w.x, fp), d1 * screen_eps<MODEL>(w.y, fp));
     }
     __syncthreads();
-    fft_tile_call<M, TWX, C::PITCH, NT, false, 2>(buf, tw);
-    row_r2c_store<N, TWX, C::PITCH>(buf, tw, moved(s_out, r.by), row0, P);
+    fft_rowtile_call<M, TWX, C::CW, NT, false, 2>(buf, tw);
+    row_r2c_store<N, TWX>(buf, tw, moved(s_out, r.by), row0, P);
     __syncthreads();
     cur ^= 1;
   }
@@ -828,8 +823,8 @@ constexpr size_t col_smem() {
 }
 
 template <int N>
-constexpr size_t row_smem(bool) {
-  return RowCfg<N, row_tw(N)>::smem + sizeof(float2);
+constexpr size_t row_smem() {
+  return RowCfg<N, row_tw(N)>::smem;
 }
 
 template <int N, int TW>
@@ -866,7 +861,7 @@ template <int N>
 static cudaError_t launch_xr2c(const float* in, float2* out, float scale, float offset,
                                const float2* tw, cudaStream_t s, Multi m) {
   constexpr int TWX = row_tw(N);
-  const size_t sm = row_smem<N>(false);
+  const size_t sm = row_smem<N>();
   const int64_t tps = (int64_t)N * N / TWX;
   const int64_t ntiles = tps * m.nb;
   auto k = k_xr2c<N, TWX>;
@@ -887,7 +882,7 @@ template <int N>
 static cudaError_t launch_xc2r_multi(int njobs, const float2* const* in, float* const* out,
                                      const float* kfs, const float2* tw, cudaStream_t s, Multi m) {
   constexpr int TWX = row_tw(N);
-  const size_t sm = row_smem<N>(true);
+  const size_t sm = row_smem<N>();
   RowJobs jobs{};
   jobs.njobs = njobs;
   for (int i = 0; i < njobs; ++i) {
@@ -996,7 +991,7 @@ template <int N>
 static cudaError_t launch_xscreen(const float2* w_in, const float* rho, float2* s_out,
                                   const ForceParams& fp, const float2* tw, cudaStream_t s, Multi m) {
   constexpr int TWX = row_tw(N);
-  const size_t sm = row_smem<N>(true);
+  constexpr size_t sm = xscreen_smem<N, TWX>();
   const int64_t tps = (int64_t)N * N / TWX;
   const int64_t ntiles = tps * m.nb;
   unsigned grid;
