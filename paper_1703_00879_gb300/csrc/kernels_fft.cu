@@ -233,24 +233,36 @@ __device__ __forceinline__ void col_pipeline(Op op, const float2* __restrict__ t
 }
 
 // ---------------------------------------------------------------- plain column pass
+// out = transform of (i kfs f_n) in along the tile axis (kfs = 0: of in itself;
+// f_n the signed frequency, zero on the Nyquist row); out may alias in.
 template <int N, int TW, bool INV>
 struct OpCol {
   ColGeo<N, TW> geo;
-  float2* data;
+  const float2* in;
+  float2* out;
+  float kfs;
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
   __device__ __forceinline__ void issue_side(int64_t) const {}
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
     int o, c0;
     int64_t base, by;
     geo.tile(t, o, c0, base, by);
-    col_issue<N, TW, TW>(buf, 0, moved(data, by), base, geo.sn, c0);
+    col_issue<N, TW, TW>(buf, 0, moved(in, by), base, geo.sn, c0);
   }
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
     int o, c0;
     int64_t base, by;
     geo.tile(t, o, c0, base, by);
+    if (kfs != 0.f) {
+      for (int e = threadIdx.x; e < N * TW; e += NT) {
+        const int c = e % TW, n = e / TW;
+        const float f = (n == N / 2) ? 0.f : kfs * (float)freq_index(n, N);
+        buf[n * TW + c] = cscale(cmul_i(buf[n * TW + c]), f);
+      }
+      __syncthreads();
+    }
     fft_tile<N, TW, TW, NT, INV>(buf, tw);
-    col_store<N, TW, TW>(buf, 0, moved(data, by), base, geo.sn, c0);
+    col_store<N, TW, TW>(buf, 0, moved(out, by), base, geo.sn, c0);
   }
 };
 
@@ -615,6 +627,14 @@ __device__ __forceinline__ void row_c2r_combine(float2* buf, const float2* tw, f
   __syncthreads();
 }
 
+// Resident CTAs per SM for the plain row passes: 3 when three tiles fit in
+// shared memory and the transform is short enough (<= 256 points) to stay in
+// 85 registers, else 2.
+template <int N, int TWX>
+constexpr int row_blocks() {
+  return (N <= 512 && RowCfg<N, TWX>::smem <= 74 * 1024) ? 3 : 2;
+}
+
 struct ScaleOffset {
   float scale, offset;
   __device__ __forceinline__ float2 operator()(float2 v) const {
@@ -633,7 +653,7 @@ __device__ __forceinline__ RowTile row_tile(int64_t t, int64_t tps, const Multi&
 }
 
 template <int N, int TWX>
-__global__ void __launch_bounds__(NT, 2) k_xr2c(const float* __restrict__ in, float2* __restrict__ out,
+__global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xr2c(const float* __restrict__ in, float2* __restrict__ out,
                                                 int64_t P, float scale, float offset,
                                                 const float2* __restrict__ twg, int64_t ntiles,
                                                 int64_t tps, Multi m) {
@@ -692,7 +712,7 @@ __device__ __forceinline__ JobTile job_tile(int64_t t, int64_t tpj, int njobs, i
 }
 
 template <int N, int TWX>
-__global__ void __launch_bounds__(NT, 2) k_xc2r(const __grid_constant__ RowJobs jobs, int64_t P,
+__global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_constant__ RowJobs jobs, int64_t P,
                                                 const float2* __restrict__ twg, int64_t tiles_per_job,
                                                 Multi m) {
   using C = RowCfg<N, TWX>;
@@ -923,12 +943,12 @@ static cudaError_t launch_col(float2* data, int axis, bool inv, const float2* tw
     auto k = k_col<N, TW, true>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(OpCol<N, TW, true>{geo, data}, tw, ntiles);
+    k<<<grid, NT, sm, s>>>(OpCol<N, TW, true>{geo, data, data, 0.f}, tw, ntiles);
   } else {
     auto k = k_col<N, TW, false>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(OpCol<N, TW, false>{geo, data}, tw, ntiles);
+    k<<<grid, NT, sm, s>>>(OpCol<N, TW, false>{geo, data, data, 0.f}, tw, ntiles);
   }
   return cudaGetLastError();
 }
@@ -942,15 +962,33 @@ cudaError_t fft_col(int Nv, float2* data, int axis, bool inv, const float2* tw, 
 template <int N>
 static cudaError_t launch_yinv2(const float2* in, float2* outp, float2* outd, float kfs,
                                 const float2* tw, cudaStream_t s, Multi m) {
-  constexpr int TW = col_tw(N, 2);
-  constexpr size_t sm = col_smem<N, 2>();
-  const int64_t ntiles = col_tiles<N, TW>() * m.nb;
-  auto k = k_yinv2<N, TW>;
-  unsigned grid;
-  cudaError_t e = prep(k, sm, ntiles, grid);
-  if (e != cudaSuccess) return e;
-  k<<<grid, NT, sm, s>>>(OpYinv2<N, TW>{geo_y<N, TW>(m), in, outp, outd, kfs}, tw, ntiles);
-  return cudaGetLastError();
+  if constexpr (N >= 512) {
+    // two single-array passes with 64-byte tile rows (the two-array tile would
+    // need 32-byte rows at this size): the derivative out of place first, then
+    // the plain transform (in place when outp aliases in)
+    constexpr int TW = col_tw(N, 1);
+    constexpr size_t sm = col_smem<N, 1>();
+    const int64_t ntiles = col_tiles<N, TW>() * m.nb;
+    auto k = k_col<N, TW, true>;
+    unsigned grid;
+    cudaError_t e = prep(k, sm, ntiles, grid);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NT, sm, s>>>(OpCol<N, TW, true>{geo_y<N, TW>(m), in, outd, kfs}, tw, ntiles);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k<<<grid, NT, sm, s>>>(OpCol<N, TW, true>{geo_y<N, TW>(m), in, outp, 0.f}, tw, ntiles);
+    return cudaGetLastError();
+  } else {
+    constexpr int TW = col_tw(N, 2);
+    constexpr size_t sm = col_smem<N, 2>();
+    const int64_t ntiles = col_tiles<N, TW>() * m.nb;
+    auto k = k_yinv2<N, TW>;
+    unsigned grid;
+    cudaError_t e = prep(k, sm, ntiles, grid);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NT, sm, s>>>(OpYinv2<N, TW>{geo_y<N, TW>(m), in, outp, outd, kfs}, tw, ntiles);
+    return cudaGetLastError();
+  }
 }
 
 cudaError_t fft_yinv2(int Nv, const float2* in, float2* outp, float2* outd, float kfs,
