@@ -303,10 +303,12 @@ int32_t cola_profile_nstages(void);
 const char* cola_profile_stage_name(int32_t i);
 
 /* Synchronises the stream and returns, per stage, the accumulated device
- * milliseconds, the number of kernel launches, and the algorithmic bytes one
- * launch moves (each array read once and written once; CIC deposit counts
- * the mesh read and written once).  Arrays of cola_profile_nstages() entries;
- * any may be NULL. */
+ * milliseconds, the number of kernel launches, and the mean algorithmic
+ * bytes per launch: the stage's algorithmic bytes (each array the stage
+ * needs read once and written once, whatever the number of kernels it takes;
+ * CIC deposit counts the mesh read and written once) divided by its launches,
+ * so launches x bytes_per_launch is the stage's algorithmic traffic.  Arrays
+ * of cola_profile_nstages() entries; any may be NULL. */
 int cola_profile_read(cola_ctx* ctx, double* ms, int64_t* launches, double* bytes_per_launch);
 
 /* ---------------------------------------------------------------------

@@ -141,6 +141,8 @@ cudaEvent_t prof_begin(cola_ctx* c) {
   return e;
 }
 
+// Closes a launch group of `launches` kernels that moves `bytes` algorithmic
+// bytes in total.
 void prof_end(cola_ctx* c, int stage, cudaEvent_t start, int launches, double bytes) {
   if (!c->prof || !start) return;
   cudaEvent_t e = take_event(c);
@@ -149,7 +151,7 @@ void prof_end(cola_ctx* c, int stage, cudaEvent_t start, int launches, double by
   auto& s = c->stages[stage];
   s.pending.emplace_back(start, e);
   s.launches += launches;
-  s.bytes = bytes;
+  s.bytes += bytes;
 }
 
 int fail(cola_ctx* c, int code, const std::string& msg) {
@@ -508,7 +510,7 @@ int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}) {
   CK(fft_col(N, ctx->lc[1], 1, true, ctx->tw_np, st, m));
   CK(fft_yinv2(N, ctx->lc[2], ctx->lc[2], ctx->lc[5], kf, ctx->tw_np, st, m));
   CK(fft_col(N, ctx->lc[3], 1, true, ctx->tw_np, st, m));
-  prof_end(ctx, ST_LPT_Y, e, 2 + 2 * yinv2_launches(N), m.nb * 2.5 * H);
+  prof_end(ctx, ST_LPT_Y, e, 2 + 2 * yinv2_launches(N), m.nb * 10.0 * H);
   e = prof_begin(ctx);
   {
     const float2* in6[6] = {ctx->lc[0], ctx->lc[4], ctx->lc[1], ctx->lc[2], ctx->lc[5], ctx->lc[3]};
@@ -574,7 +576,8 @@ int force_group(const Group& g, double a, bool device_params) {
       if (sub->lead)
         CK(mesh_z_screen_field(N, sub->lead->Cd, sub->lead->Ck, sub->lead->Cw, fp_of(sub->lead), tw, st,
                                sub->m));
-    prof_end(ctx, ST_Z_SCREEN_FIELD, e, 1, sc.m.nb * 3 * H);
+    prof_end(ctx, ST_Z_SCREEN_FIELD, e, (g.fr_screened.lead ? 1 : 0) + (g.dgp_screened.lead ? 1 : 0),
+             sc.m.nb * 3 * H);
     e = prof_begin(ctx);
     CK(fft_col(N, sc.lead->Cw, 1, true, tw, st, sc.m));
     prof_end(ctx, ST_MESH_YINV, e, 1, sc.m.nb * 2 * H);
@@ -583,7 +586,8 @@ int force_group(const Group& g, double a, bool device_params) {
       if (sub->lead)
         CK(mesh_x_screen_source(N, sub->lead->Cw, sub->lead->rho, sub->lead->Cd, fp_of(sub->lead), tw,
                                 st, sub->m));
-    prof_end(ctx, ST_X_SCREEN_SOURCE, e, 1, sc.m.nb * (2 * H + R));
+    prof_end(ctx, ST_X_SCREEN_SOURCE, e, (g.fr_screened.lead ? 1 : 0) + (g.dgp_screened.lead ? 1 : 0),
+             sc.m.nb * (2 * H + R));
     e = prof_begin(ctx);
     CK(fft_col(N, sc.lead->Cd, 1, false, tw, st, sc.m));
     prof_end(ctx, ST_MESH_Y, e, 1, sc.m.nb * 2 * H);
@@ -601,7 +605,7 @@ int force_group(const Group& g, double a, bool device_params) {
   e = prof_begin(ctx);
   CK(fft_yinv2(N, ctx->Cphi, ctx->Cphi, ctx->Cw, -fp.kf, tw, st, all));
   CK(fft_col(N, ctx->Cphz, 1, true, tw, st, all));
-  prof_end(ctx, ST_MESH_YINV, e, 1 + yinv2_launches(N), all.nb * 2.5 * H);
+  prof_end(ctx, ST_MESH_YINV, e, 1 + yinv2_launches(N), all.nb * 5.0 * H);
   e = prof_begin(ctx);
   {
     const float2* in3[3] = {ctx->Cphi, ctx->Cw, ctx->Cphz};
@@ -1748,7 +1752,7 @@ int cola_profile_read(cola_ctx* ctx, double* ms, int64_t* launches, double* byte
     stg.pending.clear();
     if (ms) ms[i] = stg.ms;
     if (launches) launches[i] = stg.launches;
-    if (bytes_per_launch) bytes_per_launch[i] = stg.bytes;
+    if (bytes_per_launch) bytes_per_launch[i] = stg.launches ? stg.bytes / (double)stg.launches : 0.0;
   }
   return COLA_OK;
 }
