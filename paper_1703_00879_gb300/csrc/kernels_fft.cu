@@ -60,6 +60,12 @@ constexpr int col_rows(int N) { return N + (1 << (ilog2(N) - ilog2(N) / 2)); }
 constexpr size_t col_smem_c(int N, int NBUF) {
   return (N + 2 * (size_t)col_rows(N) * NBUF * col_tw(N, NBUF)) * 8;
 }
+// the same for an explicit tile width
+constexpr size_t col_smem_tw(int N, int TW) { return (N + 2 * (size_t)col_rows(N) * TW) * 8; }
+// Tile width of the fused force-side z passes: 128-byte tile rows at N = 512
+// (the z stride is N P 8 bytes; longer contiguous rows per DRAM page), the
+// column default elsewhere.
+constexpr int ztw(int N) { return N == 512 ? 16 : col_tw(N, 1); }
 
 int sm_count() {
   static int n = 0;
@@ -353,7 +359,7 @@ struct OpZScreenField {
 };
 
 template <int N, int TW, int MODEL>
-__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1), N) < 2 ? 1 : 2) k_z_screen_field(OpZScreenField<N, TW, MODEL> op,
+__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_tw(N, TW), N) < 2 ? 1 : 2) k_z_screen_field(OpZScreenField<N, TW, MODEL> op,
                                                        const float2* __restrict__ twg,
                                                        int64_t ntiles) {
   if (!op.geo.m.shift) resolve(op.fp, 0);  // one simulation: once per launch
@@ -438,7 +444,7 @@ struct OpZForce {
 };
 
 template <int N, int TW, bool SCREENED, bool KEEP>
-__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1) + (size_t)N * TW * 8, N) < 2 ? 1 : 2) k_z_force(
+__global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_tw(N, TW) + (size_t)N * TW * 8, N) < 2 ? 1 : 2) k_z_force(
     OpZForce<N, TW, SCREENED, KEEP> op, const float2* __restrict__ twg, int64_t ntiles) {
   if (!op.geo.m.shift) resolve(op.fp, 0);  // one simulation: once per launch
   col_pipeline<N, fft_rows<N>() * TW>(op, twg, ntiles);
@@ -1000,8 +1006,8 @@ cudaError_t fft_yinv2(int Nv, const float2* in, float2* outp, float2* outd, floa
 template <int N>
 static cudaError_t launch_zsf(const float2* in, float2* dk_out, float2* w_out,
                               const ForceParams& fp, const float2* tw, cudaStream_t s, Multi m) {
-  constexpr int TW = col_tw(N, 1);
-  constexpr size_t sm = col_smem<N, 1>();
+  constexpr int TW = ztw(N);
+  constexpr size_t sm = col_smem_tw(N, TW);
   const int64_t ntiles = col_tiles<N, TW>() * m.nb;
   unsigned grid;
   if (fp.model == 1) {
@@ -1058,8 +1064,8 @@ template <int N, bool SCR, bool KEEP>
 static cudaError_t launch_zforce_t(const float2* in, const float2* dk, float2* phi,
                                    float2* phiz, float2* keep, const ForceParams& fp,
                                    const float2* tw, cudaStream_t s, Multi m) {
-  constexpr int TW = col_tw(N, 1);
-  constexpr size_t sm = col_smem<N, 1>() + (size_t)N * TW * sizeof(float2);
+  constexpr int TW = ztw(N);
+  constexpr size_t sm = col_smem_tw(N, TW) + (size_t)N * TW * sizeof(float2);
   const int64_t ntiles = col_tiles<N, TW>() * m.nb;
   auto k = k_z_force<N, TW, SCR, KEEP>;
   unsigned grid;
