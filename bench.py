@@ -381,7 +381,8 @@ def bench_ensemble(args):
     # the launch plan is tuned once per shape bucket, on a batch of the same shape
     # and size with other seeds (not timed: a configuration step, like picking a
     # GEMM algorithm); the timed batch then runs the whole job with that plan
-    tune = [pkg.Simulation(r.with_(seed=r.seed + 100000)) for r in runs]
+    tune = [pkg.Simulation(r.with_(seed=r.seed + 100000), ic=False) for r in runs]
+    pkg.ic_many(tune)
     tb = pkg.Batch(tune)
     plan = tb.autotune(max_steps=args.autotune_steps)
     tb.close()
@@ -389,14 +390,11 @@ def bench_ensemble(args):
         s.close()
     del tune
     torch.cuda.synchronize()
-    # batched: contexts created on a pool of streams (their ICs overlap on the
-    # device), then every sim advanced by one graph launch per step
+    # batched: contexts created, their initial conditions in one multi-simulation
+    # launch sequence, then every sim advanced by one graph launch per step
     t0 = time.perf_counter()
-    pool = [torch.cuda.Stream() for _ in range(min(32, n))]
-    sims = []
-    for i, r in enumerate(runs):
-        with torch.cuda.stream(pool[i % len(pool)]):
-            sims.append(pkg.Simulation(r, stream=pool[i % len(pool)]))
+    sims = [pkg.Simulation(r, ic=False) for r in runs]
+    pkg.ic_many(sims)
     torch.cuda.synchronize()
     t_init = time.perf_counter() - t0
     b = pkg.Batch(sims, plan=plan)

@@ -290,6 +290,15 @@ void cola_batch_free(cola_batch* b);
  * message via cola_last_error(NULL). */
 int cola_step_many(cola_ctx* const* ctxs, int32_t n, void* stream);
 
+/* Initial conditions of n distinct contexts (each after cola_set_model and
+ * before cola_ic) with multi-simulation launches on `stream`: what cola_ic
+ * computes for each, from each context's own seed, spectrum and model,
+ * contexts of one shape (as for cola_step_many) sharing every launch.  No
+ * host synchronisation; ordering with the contexts' own streams as for
+ * cola_step_many.  Errors: COLA_EINVAL, COLA_ESTATE (no model, or ICs already
+ * done), COLA_ECUDA; message via cola_last_error(NULL). */
+int cola_ic_many(cola_ctx* const* ctxs, int32_t n, void* stream);
+
 /* ---------------------------------------------------------------------
  * Per-stage device timing: CUDA events recorded on the context's stream
  * around each launch group of cola_step (and of cola_ic's force evaluation).

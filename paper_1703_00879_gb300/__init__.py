@@ -80,6 +80,7 @@ _SIGS = {
     "cola_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(cola_batch_plan)]),
     "cola_batch_pk": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "cola_step_many": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "cola_ic_many": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "cola_pk_async": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cola_pk_ready": (ctypes.c_int, [_P]),
     "cola_pk_result": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -379,6 +380,14 @@ def step_many(sims, stream=None):
     st = stream if stream is not None else torch.cuda.current_stream()
     arr = (_P * len(sims))(*[s.ctx for s in sims])
     _check(lib().cola_step_many(arr, len(sims), _P(st.cuda_stream)))
+
+
+def ic_many(sims, stream=None):
+    """cola_ic_many: initial conditions of every Simulation in `sims` (created with ic=False)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    arr = (_P * len(sims))(*[s.ctx for s in sims])
+    _check(lib().cola_ic_many(arr, len(sims), _P(st.cuda_stream)))
 
 
 class Batch:

@@ -52,7 +52,6 @@ struct cola_ctx {
   // seeds
   float2* phi[2] = {};
   void* seedq[2] = {};
-  float seed_scale[2] = {1.f, 1.f};
   // LPT work
   float2* lc[6] = {};
   float* lr[6] = {};
@@ -466,17 +465,17 @@ ForceParams force_params(const cola_ctx* c, double a) {
 
 // 3-D transforms on the padded half-spectrum layout.
 int r2c3(cola_ctx* ctx, int N, const float* in, float2* out, const float2* tw, float scale,
-         float offset) {
-  CK(fft_xr2c(N, in, out, scale, offset, tw, ctx->st));
-  CK(fft_col(N, out, 1, false, tw, ctx->st));
-  CK(fft_col(N, out, 2, false, tw, ctx->st));
+         float offset, Multi m = {}) {
+  CK(fft_xr2c(N, in, out, scale, offset, tw, ctx->st, m));
+  CK(fft_col(N, out, 1, false, tw, ctx->st, m));
+  CK(fft_col(N, out, 2, false, tw, ctx->st, m));
   return COLA_OK;
 }
 
-int c2r3(cola_ctx* ctx, int N, float2* in, float* out, const float2* tw) {
-  CK(fft_col(N, in, 2, true, tw, ctx->st));
-  CK(fft_col(N, in, 1, true, tw, ctx->st));
-  CK(fft_xc2r(N, in, out, 0.f, tw, ctx->st));
+int c2r3(cola_ctx* ctx, int N, float2* in, float* out, const float2* tw, Multi m = {}) {
+  CK(fft_col(N, in, 2, true, tw, ctx->st, m));
+  CK(fft_col(N, in, 1, true, tw, ctx->st, m));
+  CK(fft_xc2r(N, in, out, 0.f, tw, ctx->st, m));
   return COLA_OK;
 }
 
@@ -548,15 +547,19 @@ Group single_group(cola_ctx* ctx) {
 }
 
 // App. B: mesh force -grad(Phi_N + phi) at scale factor a from the density in
-// rho, for every simulation of g.  device_params: each simulation's values of
-// its current step come from its header (a is then only used for the model
-// flags); otherwise the values at a (single simulation).
-int force_group(const Group& g, double a, bool device_params) {
+// rho, for every simulation of g.  device_params: each simulation's values
+// come from its header, those of its current step or (ini) those at a_ini (a
+// is then only used for the model flags); otherwise the values at a (single
+// simulation).
+int force_group(const Group& g, double a, bool device_params, bool ini = false) {
   cola_ctx* ctx = g.lead;
   const Multi all = g.all;
   auto fp_of = [&](cola_ctx* c) {
     ForceParams fp = force_params(c, a);
-    if (device_params) fp.hdr = c->hdr;
+    if (device_params) {
+      fp.hdr = c->hdr;
+      fp.ini = ini ? 1 : 0;
+    }
     return fp;
   };
   const ForceParams fp = fp_of(ctx);
@@ -632,38 +635,74 @@ PartParams part_params(const cola_ctx* c) {
   return pp;
 }
 
-// Particles on the LPT trajectory at a_ini, initial force and residual acceleration.
-int finish_ic(cola_ctx* ctx) {
+// The spectrum of the initial conditions in device form.
+EHDev eh_dev(const cola_ctx* ctx) {
   const int N = ctx->Np;
+  EHDev eh;
+  eh.theta2 = ctx->eh.theta2;
+  eh.s = ctx->eh.s;
+  eh.alpha = ctx->eh.alpha;
+  eh.Omh = ctx->eh.Omh;
+  eh.h = ctx->eh.h;
+  eh.ns = ctx->eh.ns;
+  eh.amp = ctx->eh.amp * ctx->Dratio * ctx->Dratio;
+  eh.N3_over_L3 = (double)N * N * N / (ctx->L * ctx->L * ctx->L);
+  return eh;
+}
+
+// Initial conditions (Sec. 3, Sec. 4.1, App. A) of every simulation of g on
+// g.lead->st: white noise from each one's seed, phi1 = delta/k^2, the 2LPT phi2
+// (skipped when `potentials`: phi1 and phi2 are already in place), the
+// reduced-precision seeds, the particles on the LPT trajectory at a_ini, and the
+// initial force and residual acceleration.  Per-simulation values (seed,
+// spectrum, force parameters at a_ini, seed scales) live in the headers, which
+// must hold step 0 before this runs.
+int ic_group(const Group& g, bool potentials) {
+  cola_ctx* ctx = g.lead;
+  const Multi m = g.all;
+  const int N = ctx->Np;
+  auto st = ctx->st;
+  const float kf = (float)(2.0 * kPi / ctx->L);
+  if (!potentials) {
+    CK(ic_noise(N, ctx->cfg.seed, ctx->lr[0], st, m, ctx->hdr));
+    CHECK_RC(r2c3(ctx, N, ctx->lr[0], ctx->phi[0], ctx->tw_np, 1.f, 0.f, m));
+    CK(ic_phi1(N, ctx->phi[0], kf, eh_dev(ctx), st, m, ctx->hdr));
+    const int ij[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int h = 0; h < 6; ++h) {
+      CK(ic_hessian(N, ctx->phi[0], ctx->lc[0], ij[h][0], ij[h][1], kf, st, m));
+      CHECK_RC(c2r3(ctx, N, ctx->lc[0], ctx->lr[h], ctx->tw_np, m));
+    }
+    float* src = reinterpret_cast<float*>(ctx->lc[1]);
+    CK(ic_source(ctx->P, ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->lr[3], ctx->lr[4], ctx->lr[5], src, st,
+                 m));
+    CHECK_RC(r2c3(ctx, N, src, ctx->phi[1], ctx->tw_np, 1.f, 0.f, m));
+    CK(ic_phi2(N, ctx->phi[1], kf, st, m));
+  }
   if (ctx->cfg.seed_precision) {
     for (int f = 0; f < 2; ++f) {
-      CK(seed_absmax(N, ctx->phi[f], ctx->scratch, ctx->st));
-      float amax = 0.f;
-      CK(cudaMemcpyAsync(&amax, ctx->scratch, sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
-      CK(cudaStreamSynchronize(ctx->st));
-      // bf16: unit scale of the largest value; fp16: largest value at 2^15.
-      const float target = ctx->cfg.seed_precision == COLA_SEED_FP16 ? 32768.f : 1.f;
-      const float scale = amax > 0.f ? amax / target : 1.f;
-      ctx->seed_scale[f] = scale;
-      CK(seed_quantise(N, ctx->phi[f], ctx->seedq[f], ctx->cfg.seed_precision, 1.f / scale,
-                       ctx->st));
+      CK(seed_absmax(N, ctx->phi[f], ctx->scratch, st, m));
+      CK(seed_scale_set(ctx->hdr, ctx->scratch, f, st, m));
+      CK(seed_quantise(N, ctx->phi[f], ctx->seedq[f], ctx->cfg.seed_precision, ctx->hdr, f, st, m));
     }
   }
-  ctx->hh.seed_scale[0] = ctx->seed_scale[0];
-  ctx->hh.seed_scale[1] = ctx->seed_scale[1];
-  ctx->hh.step = 0;
-  CK(set_header(ctx->hdr, ctx->hh, ctx->st));
-  CHECK_RC(run_lpt(ctx, 0, 0, false));
+  CHECK_RC(run_lpt(ctx, 0, 0, false, m));
   CK(ic_particles(ctx->P, ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->s[0], ctx->s[1], ctx->s[2],
-                  ctx->v[0], ctx->v[1], ctx->v[2], ctx->st));
+                  ctx->v[0], ctx->v[1], ctx->v[2], st, m));
   const PartParams pp = part_params(ctx);
-  CK(cudaMemsetAsync(ctx->rho, 0, ctx->M * sizeof(float), ctx->st));
-  CK(part_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->rho, ctx->P, ctx->st));
-  CHECK_RC(run_force(ctx, ctx->a[0]));
+  CK(zero_f32(ctx->rho, ctx->M, st, m));
+  CK(part_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->rho, ctx->P, st, m));
+  CHECK_RC(force_group(g, ctx->a[0], true, true));
   CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                       ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[3], ctx->lr[4], ctx->lr[5],
-                      ctx->F[0], ctx->F[1], ctx->F[2], StepDt{nullptr, 0.f, 0.f}, ctx->P,
-                      ctx->st));
+                      ctx->F[0], ctx->F[1], ctx->F[2], StepDt{nullptr, 0.f, 0.f}, ctx->P, st, m));
+  return COLA_OK;
+}
+
+// One context's initial conditions on its own stream.
+int finish_ic(cola_ctx* ctx, bool potentials) {
+  ctx->hh.step = 0;
+  CK(set_header(ctx->hdr, ctx->hh, ctx->st));
+  CHECK_RC(ic_group(single_group(ctx), potentials));
   ctx->step = 0;
   ctx->ic_done = true;
   return COLA_OK;
@@ -898,6 +937,11 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
   ctx->hh.ddt = ctx->ddt;
   ctx->hh.tab = ctx->tab;
   ctx->hh.vtab = ctx->vtab;
+  ctx->hh.fp_ini = force_params(ctx, ctx->a[0]);
+  ctx->hh.seed = ctx->cfg.seed;
+  // bf16: unit scale of the largest value; fp16: the largest value at 2^15
+  ctx->hh.seed_target = ctx->cfg.seed_precision == COLA_SEED_FP16 ? 32768.f : 1.f;
+  ctx->hh.eh = eh_dev(ctx);
   CK(set_header(ctx->hdr, ctx->hh, ctx->st));
   return COLA_OK;
 }
@@ -905,31 +949,7 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
 int cola_ic(cola_ctx* ctx) {
   if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
   if (!ctx->model_set) return fail(ctx, COLA_ESTATE, "cola_ic before cola_set_model");
-  const int N = ctx->Np;
-  auto st = ctx->st;
-  const float kf = (float)(2.0 * kPi / ctx->L);
-  CK(ic_noise(N, ctx->cfg.seed, ctx->lr[0], st));
-  CHECK_RC(r2c3(ctx, N, ctx->lr[0], ctx->phi[0], ctx->tw_np, 1.f, 0.f));
-  EHDev eh;
-  eh.theta2 = ctx->eh.theta2;
-  eh.s = ctx->eh.s;
-  eh.alpha = ctx->eh.alpha;
-  eh.Omh = ctx->eh.Omh;
-  eh.h = ctx->eh.h;
-  eh.ns = ctx->eh.ns;
-  eh.amp = ctx->eh.amp * ctx->Dratio * ctx->Dratio;
-  eh.N3_over_L3 = (double)N * N * N / (ctx->L * ctx->L * ctx->L);
-  CK(ic_phi1(N, ctx->phi[0], kf, eh, st));
-  const int ij[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
-  for (int h = 0; h < 6; ++h) {
-    CK(ic_hessian(N, ctx->phi[0], ctx->lc[0], ij[h][0], ij[h][1], kf, st));
-    CHECK_RC(c2r3(ctx, N, ctx->lc[0], ctx->lr[h], ctx->tw_np));
-  }
-  float* src = reinterpret_cast<float*>(ctx->lc[1]);
-  CK(ic_source(ctx->P, ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->lr[3], ctx->lr[4], ctx->lr[5], src, st));
-  CHECK_RC(r2c3(ctx, N, src, ctx->phi[1], ctx->tw_np, 1.f, 0.f));
-  CK(ic_phi2(N, ctx->phi[1], kf, st));
-  return finish_ic(ctx);
+  return finish_ic(ctx, false);
 }
 
 int cola_ic_from_potentials(cola_ctx* ctx, const float* phi1, const float* phi2, int32_t where) {
@@ -949,7 +969,7 @@ int cola_ic_from_potentials(cola_ctx* ctx, const float* phi1, const float* phi2,
     CK(half_pack(N, dense, ctx->phi[f], ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
   }
-  return finish_ic(ctx);
+  return finish_ic(ctx, true);
 }
 
 int cola_step(cola_ctx* ctx, int32_t nsteps) {
@@ -1621,23 +1641,19 @@ int cola_batch_pk(cola_batch* b, int32_t nbins, double* k, double* pk, int64_t* 
   return COLA_OK;
 }
 
-int cola_step_many(cola_ctx* const* ctxs, int32_t n, void* stream) {
-  if (!ctxs || n < 1 || n > 65535) return fail(nullptr, COLA_EINVAL, "need 1 <= n <= 65535 contexts");
-  for (int i = 0; i < n; ++i) {
-    const cola_ctx* c = ctxs[i];
-    if (!c) return fail(nullptr, COLA_EINVAL, "NULL context");
-    if (!c->ic_done) return fail(nullptr, COLA_ESTATE, "cola_step_many before cola_ic");
-    if (c->step >= c->cfg.nsteps) return fail(nullptr, COLA_EINVAL, "a context is past its last step");
-    for (int j = 0; j < i; ++j)
-      if (ctxs[j] == c) return fail(nullptr, COLA_EINVAL, "a context appears twice");
-  }
+// Runs enqueue(group) on `stream` for every group of the n distinct contexts
+// (one group per shape, in order of first appearance), ordered after the work
+// already queued on each context's own stream and before the work queued on
+// it later.  The shift arrays travel in launch parameters into a
+// stream-ordered allocation.  Reports failures through g_err.
+static int run_on_groups(cola_ctx* const* ctxs, int32_t n, void* stream, const char* who,
+                         const std::function<int(const Group&)>& enqueue) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  auto ck = [](cudaError_t e, const char* what) {
+  auto ck = [who](cudaError_t e, const char* what) {
     if (e == cudaSuccess) return COLA_OK;
-    g_err = std::string("cola_step_many: ") + what + ": " + cudaGetErrorString(e);
+    g_err = std::string(who) + ": " + what + ": " + cudaGetErrorString(e);
     return COLA_ECUDA;
   };
-  // after the work already queued on each context's own stream
   for (int i = 0; i < n; ++i) {
     cola_ctx* c = ctxs[i];
     if (c->st == st) continue;
@@ -1645,7 +1661,6 @@ int cola_step_many(cola_ctx* const* ctxs, int32_t n, void* stream) {
     CHECK_RC(ck(cudaEventRecord(c->ev_order, c->st), "event record"));
     CHECK_RC(ck(cudaStreamWaitEvent(st, c->ev_order, 0), "stream wait"));
   }
-  // one multi-simulation launch sequence per shape (order of first appearance)
   std::vector<std::vector<cola_ctx*>> buckets;
   for (int i = 0; i < n; ++i) {
     bool placed = false;
@@ -1673,10 +1688,10 @@ int cola_step_many(cola_ctx* const* ctxs, int32_t n, void* stream) {
     cola_ctx* lead = gp.g.lead;
     cudaStream_t saved = lead->st;
     lead->st = st;
-    rc = enqueue_group_step(gp.g, lead->step);
+    rc = enqueue(gp.g);
     lead->st = saved;
     if (rc != COLA_OK) {
-      g_err = "cola_step_many: " + lead->err;
+      g_err = std::string(who) + ": " + lead->err;
       break;
     }
   }
@@ -1684,12 +1699,54 @@ int cola_step_many(cola_ctx* const* ctxs, int32_t n, void* stream) {
   if (rc != COLA_OK) return rc;
   for (int i = 0; i < n; ++i) {
     cola_ctx* c = ctxs[i];
-    c->step += 1;
-    c->hh.step = c->step;
     if (c->st == st) continue;
-    // later work on the context's own stream follows this step
     CHECK_RC(ck(cudaEventRecord(c->ev_order, st), "event record"));
     CHECK_RC(ck(cudaStreamWaitEvent(c->st, c->ev_order, 0), "stream wait"));
+  }
+  return COLA_OK;
+}
+
+static int check_distinct(cola_ctx* const* ctxs, int32_t n) {
+  if (!ctxs || n < 1 || n > 65535) return fail(nullptr, COLA_EINVAL, "need 1 <= n <= 65535 contexts");
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(nullptr, COLA_EINVAL, "NULL context");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(nullptr, COLA_EINVAL, "a context appears twice");
+  }
+  return COLA_OK;
+}
+
+int cola_step_many(cola_ctx* const* ctxs, int32_t n, void* stream) {
+  CHECK_RC(check_distinct(ctxs, n));
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]->ic_done) return fail(nullptr, COLA_ESTATE, "cola_step_many before cola_ic");
+    if (ctxs[i]->step >= ctxs[i]->cfg.nsteps) return fail(nullptr, COLA_EINVAL, "a context is past its last step");
+  }
+  CHECK_RC(run_on_groups(ctxs, n, stream, "cola_step_many",
+                         [](const Group& g) { return enqueue_group_step(g, g.lead->step); }));
+  for (int i = 0; i < n; ++i) {
+    ctxs[i]->step += 1;
+    ctxs[i]->hh.step = ctxs[i]->step;
+  }
+  return COLA_OK;
+}
+
+int cola_ic_many(cola_ctx* const* ctxs, int32_t n, void* stream) {
+  CHECK_RC(check_distinct(ctxs, n));
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]->model_set) return fail(nullptr, COLA_ESTATE, "cola_ic_many before cola_set_model");
+    if (ctxs[i]->ic_done) return fail(nullptr, COLA_ESTATE, "cola_ic_many on a context that has its ICs");
+  }
+  // step 0 in every header, on each context's own stream (run_on_groups orders it before the ICs)
+  for (int i = 0; i < n; ++i) {
+    ctxs[i]->hh.step = 0;
+    cudaError_t e = set_header(ctxs[i]->hdr, ctxs[i]->hh, ctxs[i]->st);
+    if (e != cudaSuccess) return fail(nullptr, COLA_ECUDA, std::string("cola_ic_many: ") + cudaGetErrorString(e));
+  }
+  CHECK_RC(run_on_groups(ctxs, n, stream, "cola_ic_many", [](const Group& g) { return ic_group(g, false); }));
+  for (int i = 0; i < n; ++i) {
+    ctxs[i]->step = 0;
+    ctxs[i]->ic_done = true;
   }
   return COLA_OK;
 }

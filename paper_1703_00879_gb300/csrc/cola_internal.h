@@ -13,18 +13,50 @@ namespace cola {
 inline int64_t half_pitch(int N) { return ((N / 2 + 1 + 15) / 16) * 16; }
 inline int64_t half_elems(int N) { return (int64_t)N * N * half_pitch(N); }
 
-struct ForceParams;
+struct SimHeader;
+
+// Parameters of one force evaluation (App. B field equation).
+struct ForceParams {
+  float kf;          // 2 pi / L
+  float kappa_norm;  // kappa(a) / N^3 (the inverse transforms are unnormalised)
+  float C;           // fifth-force coupling C(a) (0 for LCDM)
+  float a2m2;        // a^2 m^2(a)  [(h/Mpc)^2]
+  float inv_rhobar;  // Nmesh^3 / Np^3
+  float fr_thr;      // f(R): Phi_crit(a) a^2 c^2, threshold on |Phi_N| in code units
+  float dgp_coef;    // nDGP: 8 (r_c H0)^2 Omega_m / (9 beta^2)
+  float R2half;      // nDGP: R_smooth^2 / 2
+  float norm;        // 1 / N^3
+  int model;         // 0 LCDM, 1 f(R), 2 nDGP
+  int screened;      // 1: screened fifth force
+  // When hdr is set, kernels replace every value above by the simulation's
+  // own: the current step's entry hdr->dfp[hdr->step], or hdr->fp_ini when ini
+  // is set (hdr moved by the simulation's shift).
+  const SimHeader* hdr;
+  int ini;
+};
+
+// Eisenstein-Hu no-wiggle spectrum of the initial conditions.
+struct EHDev {
+  double theta2, s, alpha, Omh, h, ns, amp;  // amp: A (D(a_ini)/D(1))^2
+  double N3_over_L3;
+};
 
 // Per-simulation device header: where its per-step parameters live and how many
 // steps it has done.  Kernels that serve every step read their parameters
-// through it, so one captured launch sequence serves every step.
+// through it, so one captured launch sequence serves every step.  The second
+// group of fields parameterises the initial conditions, so that one launch
+// sequence can set up many simulations.
 struct SimHeader {
   const ForceParams* dfp;  // [nsteps]: force parameters at a_{n+1}
   const float* ddt;        // [nsteps][3]: half kick, drift, half kick time integrals
   const float4* tab;       // [nsteps+1][nk] LPT reweight table (row 0: a_ini, row n+1: step n)
   const float4* vtab;      // [nsteps+1][nk] velocity table
   int step;                // steps done
-  float seed_scale[2];     // dequantisation scales of the 16-bit seeds
+  float seed_scale[2];     // dequantisation scales of the 16-bit seeds (written on the device)
+  float seed_target;       // 16-bit seeds: the largest |component| maps to this
+  unsigned long long seed; // white-noise seed
+  EHDev eh;                // spectrum of the initial conditions
+  ForceParams fp_ini;      // force parameters at a_ini
 };
 
 // One launch over several simulations of one shape.  Each simulation's
@@ -43,28 +75,11 @@ __host__ __device__ __forceinline__ T* moved(T* p, int64_t by) {
 }
 __device__ __forceinline__ int64_t shift_of(const Multi& m, int b) { return m.shift ? m.shift[b] : 0; }
 
-// Parameters of one force evaluation (App. B field equation).
-struct ForceParams {
-  float kf;          // 2 pi / L
-  float kappa_norm;  // kappa(a) / N^3 (the inverse transforms are unnormalised)
-  float C;           // fifth-force coupling C(a) (0 for LCDM)
-  float a2m2;        // a^2 m^2(a)  [(h/Mpc)^2]
-  float inv_rhobar;  // Nmesh^3 / Np^3
-  float fr_thr;      // f(R): Phi_crit(a) a^2 c^2, threshold on |Phi_N| in code units
-  float dgp_coef;    // nDGP: 8 (r_c H0)^2 Omega_m / (9 beta^2)
-  float R2half;      // nDGP: R_smooth^2 / 2
-  float norm;        // 1 / N^3
-  int model;         // 0 LCDM, 1 f(R), 2 nDGP
-  int screened;      // 1: screened fifth force
-  // When hdr is set, kernels replace every value above by the current step's
-  // entry hdr->dfp[hdr->step] of the simulation (hdr moved by its shift).
-  const SimHeader* hdr;
-};
 
 __device__ __forceinline__ void resolve(ForceParams& fp, int64_t by) {
   if (fp.hdr) {
     const SimHeader* h = moved(fp.hdr, by);
-    fp = h->dfp[h->step];
+    fp = fp.ini ? h->fp_ini : h->dfp[h->step];
   }
 }
 
@@ -164,7 +179,7 @@ cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float*
                              StepDt dt, int64_t P, cudaStream_t s, Multi m = {});
 // hdr->step += 1 (end of a step)
 cudaError_t step_advance(SimHeader* hdr, cudaStream_t s, Multi m = {});
-// hdr = v (one simulation)
+// hdr = v (one simulation), except the seed scales, which keep their device values
 cudaError_t set_header(SimHeader* hdr, const SimHeader& v, cudaStream_t s);
 // dst[0..n) = src[0..n) (host values) by kernels whose launch parameters carry
 // the values: stream-ordered, without a host synchronisation
@@ -183,31 +198,35 @@ cudaError_t pk_bin(int N, const float2* dk, int nbins, double* acc, double norm,
                    cudaStream_t s, Multi m = {}, int64_t acc_stride = 0);
 
 // ------------------------------------------------------------------ initial conditions
-struct EHDev {
-  double theta2, s, alpha, Omh, h, ns, amp;  // amp: A (D(a_ini)/D(1))^2
-  double N3_over_L3;
-};
-cudaError_t ic_noise(int N, uint64_t seed, float* out, cudaStream_t s);
+// The initial-condition launchers run over m's simulations; where a value
+// differs between simulations (seed, spectrum, seed scales) it is read from
+// each simulation's header when hdr is given.
+cudaError_t ic_noise(int N, uint64_t seed, float* out, cudaStream_t s, Multi m = {},
+                     const SimHeader* hdr = nullptr);
 // delta(k) = G(k) sqrt(P(k) N^3/L^3); phi1 = delta/k^2 (k = 0 -> 0), in place on c.
-cudaError_t ic_phi1(int N, float2* c, float kf, const EHDev& eh, cudaStream_t s);
+cudaError_t ic_phi1(int N, float2* c, float kf, const EHDev& eh, cudaStream_t s, Multi m = {},
+                    const SimHeader* hdr = nullptr);
 // out = -k_i k_j / N^3 * phi1 with the Nyquist rule for i != j.
 cudaError_t ic_hessian(int N, const float2* phi1, float2* out, int i, int j, float kf,
-                       cudaStream_t s);
+                       cudaStream_t s, Multi m = {});
 cudaError_t ic_source(int64_t n, const float* hxx, const float* hyy, const float* hzz,
                       const float* hxy, const float* hxz, const float* hyz, float* src,
-                      cudaStream_t s);
+                      cudaStream_t s, Multi m = {});
 // phi2 = -src(k)/k^2 in place.
-cudaError_t ic_phi2(int N, float2* c, float kf, cudaStream_t s);
+cudaError_t ic_phi2(int N, float2* c, float kf, cudaStream_t s, Multi m = {});
 cudaError_t ic_particles(int64_t P, const float* px, const float* py, const float* pz, float* sx,
                          float* sy, float* sz, float* vx, float* vy, float* vz,
-                         cudaStream_t s);
+                         cudaStream_t s, Multi m = {});
 // pack a dense [N][N][N/2+1] half spectrum into / out of the padded layout
 cudaError_t half_pack(int N, const float2* dense, float2* padded, cudaStream_t s);
 cudaError_t half_unpack(int N, const float2* padded, float2* dense, cudaStream_t s);
-// seed fields in reduced precision
-cudaError_t seed_quantise(int N, const float2* src, void* dst, int prec, float inv_scale,
-                          cudaStream_t s);
-cudaError_t seed_absmax(int N, const float2* src, float* out_absmax, cudaStream_t s);
+// reduced-precision seeds: the largest |component| of field f (into absmax),
+// then hdr->seed_scale[f] = absmax / hdr->seed_target (1 if absmax = 0), then
+// the 16-bit copy of the field divided by that scale
+cudaError_t seed_absmax(int N, const float2* src, float* out_absmax, cudaStream_t s, Multi m = {});
+cudaError_t seed_scale_set(SimHeader* hdr, const float* absmax, int f, cudaStream_t s, Multi m = {});
+cudaError_t seed_quantise(int N, const float2* src, void* dst, int prec, const SimHeader* hdr, int f,
+                          cudaStream_t s, Multi m = {});
 
 // Caps the persistent grid of the FFT-pass kernels launched by the calling
 // thread (0 = no cap: resident CTAs x SMs).

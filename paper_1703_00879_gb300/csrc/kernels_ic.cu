@@ -35,9 +35,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 // Unit Gaussian per lattice point: counter (idx lo, idx hi, 0, 0), key = seed,
 // u_i = (w_i + 1/2) / 2^32, g = sqrt(-2 ln u1) cos(2 pi u2) in double precision.
-__global__ void k_noise(int64_t n, uint32_t k0, uint32_t k1, float* __restrict__ out) {
+// Multi-simulation kernels take the simulation from blockIdx.y and move every
+// buffer pointer by its shift; per-simulation values come from the header.
+__global__ void k_noise(int64_t n, uint32_t k0, uint32_t k1, float* __restrict__ out,
+                        const SimHeader* __restrict__ hdr, Multi mm) {
   const int64_t i = (int64_t)blockIdx.x * NTI + threadIdx.x;
   if (i >= n) return;
+  const int64_t by = shift_of(mm, blockIdx.y);
+  out = moved(out, by);
+  if (hdr) {
+    const unsigned long long sd = moved(hdr, by)->seed;
+    k0 = (uint32_t)sd;
+    k1 = (uint32_t)(sd >> 32);
+  }
   const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 0u, 0u), k0, k1);
   const double u1 = ((double)r.x + 0.5) * (1.0 / 4294967296.0);
   const double u2 = ((double)r.y + 0.5) * (1.0 / 4294967296.0);
@@ -76,9 +86,13 @@ __device__ double eh_T(const EHDev& e, double k) {
   return L0 / (L0 + C0 * q * q);
 }
 
-__global__ void k_ic_phi1(int N, int64_t P, float2* __restrict__ c, float kf, EHDev eh) {
+__global__ void k_ic_phi1(int N, int64_t P, float2* __restrict__ c, float kf, EHDev eh,
+                          const SimHeader* __restrict__ hdr, Multi mm) {
   const int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x;
   if (m >= (int64_t)N * N * P) return;
+  const int64_t by = shift_of(mm, blockIdx.y);
+  c = moved(c, by);
+  if (hdr) eh = moved(hdr, by)->eh;
   bool valid;
   const Mode md = mode_of(m, N, P, valid);
   if (!valid) return;
@@ -96,9 +110,12 @@ __global__ void k_ic_phi1(int N, int64_t P, float2* __restrict__ c, float kf, EH
 }
 
 __global__ void k_ic_hessian(int N, int64_t P, const float2* __restrict__ phi1,
-                             float2* __restrict__ out, int i, int j, float kf, float norm) {
+                             float2* __restrict__ out, int i, int j, float kf, float norm, Multi mm) {
   const int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x;
   if (m >= (int64_t)N * N * P) return;
+  const int64_t by = shift_of(mm, blockIdx.y);
+  phi1 = moved(phi1, by);
+  out = moved(out, by);
   bool valid;
   const Mode md = mode_of(m, N, P, valid);
   if (!valid) return;
@@ -114,16 +131,25 @@ __global__ void k_ic_hessian(int N, int64_t P, const float2* __restrict__ phi1,
 __global__ void k_ic_source(int64_t n, const float* __restrict__ hxx,
                             const float* __restrict__ hyy, const float* __restrict__ hzz,
                             const float* __restrict__ hxy, const float* __restrict__ hxz,
-                            const float* __restrict__ hyz, float* __restrict__ src) {
+                            const float* __restrict__ hyz, float* __restrict__ src, Multi mm) {
   const int64_t i = (int64_t)blockIdx.x * NTI + threadIdx.x;
   if (i >= n) return;
+  const int64_t by = shift_of(mm, blockIdx.y);
+  hxx = moved(hxx, by);
+  hyy = moved(hyy, by);
+  hzz = moved(hzz, by);
+  hxy = moved(hxy, by);
+  hxz = moved(hxz, by);
+  hyz = moved(hyz, by);
+  src = moved(src, by);
   const float a = hxx[i], b = hyy[i], c = hzz[i], d = hxy[i], e = hxz[i], f = hyz[i];
   src[i] = (a * b - d * d) + (a * c - e * e) + (b * c - f * f);
 }
 
-__global__ void k_ic_phi2(int N, int64_t P, float2* __restrict__ c, float kf) {
+__global__ void k_ic_phi2(int N, int64_t P, float2* __restrict__ c, float kf, Multi mm) {
   const int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x;
   if (m >= (int64_t)N * N * P) return;
+  c = moved(c, shift_of(mm, blockIdx.y));
   bool valid;
   const Mode md = mode_of(m, N, P, valid);
   if (!valid) return;
@@ -136,9 +162,19 @@ __global__ void k_ic_particles(int64_t P, const float* __restrict__ px,
                                const float* __restrict__ py, const float* __restrict__ pz,
                                float* __restrict__ sx, float* __restrict__ sy,
                                float* __restrict__ sz, float* __restrict__ vx,
-                               float* __restrict__ vy, float* __restrict__ vz) {
+                               float* __restrict__ vy, float* __restrict__ vz, Multi mm) {
   const int64_t i = (int64_t)blockIdx.x * NTI + threadIdx.x;
   if (i >= P) return;
+  const int64_t by = shift_of(mm, blockIdx.y);
+  px = moved(px, by);
+  py = moved(py, by);
+  pz = moved(pz, by);
+  sx = moved(sx, by);
+  sy = moved(sy, by);
+  sz = moved(sz, by);
+  vx = moved(vx, by);
+  vy = moved(vy, by);
+  vz = moved(vz, by);
   sx[i] = px[i];
   sy[i] = py[i];
   sz[i] = pz[i];
@@ -158,7 +194,10 @@ __global__ void k_half_pack(int N, int64_t P, const float2* __restrict__ dense,
 }
 
 __global__ void k_absmax(int64_t n, int N, int64_t P, const float2* __restrict__ src,
-                         unsigned int* __restrict__ out) {
+                         unsigned int* __restrict__ out, Multi mm) {
+  const int64_t by = shift_of(mm, blockIdx.y);
+  src = moved(src, by);
+  out = moved(out, by);
   float mx = 0.f;
   for (int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x; m < n;
        m += (int64_t)gridDim.x * NTI) {
@@ -170,10 +209,23 @@ __global__ void k_absmax(int64_t n, int N, int64_t P, const float2* __restrict__
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
 }
 
+__global__ void k_seed_scale(SimHeader* hdr, const float* __restrict__ absmax, int f, Multi mm) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= mm.nb) return;
+  const int64_t by = shift_of(mm, b);
+  SimHeader* h = moved(hdr, by);
+  const float amax = *moved(absmax, by);
+  h->seed_scale[f] = amax > 0.f ? amax / h->seed_target : 1.f;
+}
+
 __global__ void k_quantise(int64_t n, const float2* __restrict__ src, uint32_t* __restrict__ dst,
-                           int prec, float inv_scale) {
+                           int prec, const SimHeader* __restrict__ hdr, int f, Multi mm) {
   const int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x;
   if (m >= n) return;
+  const int64_t by = shift_of(mm, blockIdx.y);
+  src = moved(src, by);
+  dst = moved(dst, by);
+  const float inv_scale = 1.f / moved(hdr, by)->seed_scale[f];
   const float2 v = src[m];
   uint32_t lo, hi;
   if (prec == 1) {
@@ -188,43 +240,44 @@ __global__ void k_quantise(int64_t n, const float2* __restrict__ src, uint32_t* 
 
 }  // namespace
 
-cudaError_t ic_noise(int N, uint64_t seed, float* out, cudaStream_t s) {
+cudaError_t ic_noise(int N, uint64_t seed, float* out, cudaStream_t s, Multi m, const SimHeader* hdr) {
   const int64_t n = (int64_t)N * N * N;
-  k_noise<<<blocks_for(n), NTI, 0, s>>>(n, (uint32_t)seed, (uint32_t)(seed >> 32), out);
+  k_noise<<<dim3(blocks_for(n), m.nb), NTI, 0, s>>>(n, (uint32_t)seed, (uint32_t)(seed >> 32), out, hdr, m);
   return cudaGetLastError();
 }
 
-cudaError_t ic_phi1(int N, float2* c, float kf, const EHDev& eh, cudaStream_t s) {
+cudaError_t ic_phi1(int N, float2* c, float kf, const EHDev& eh, cudaStream_t s, Multi m,
+                    const SimHeader* hdr) {
   const int64_t n = half_elems(N);
-  k_ic_phi1<<<blocks_for(n), NTI, 0, s>>>(N, half_pitch(N), c, kf, eh);
+  k_ic_phi1<<<dim3(blocks_for(n), m.nb), NTI, 0, s>>>(N, half_pitch(N), c, kf, eh, hdr, m);
   return cudaGetLastError();
 }
 
 cudaError_t ic_hessian(int N, const float2* phi1, float2* out, int i, int j, float kf,
-                       cudaStream_t s) {
+                       cudaStream_t s, Multi m) {
   const int64_t n = half_elems(N);
   const float norm = (float)(1.0 / ((double)N * N * N));
-  k_ic_hessian<<<blocks_for(n), NTI, 0, s>>>(N, half_pitch(N), phi1, out, i, j, kf, norm);
+  k_ic_hessian<<<dim3(blocks_for(n), m.nb), NTI, 0, s>>>(N, half_pitch(N), phi1, out, i, j, kf, norm, m);
   return cudaGetLastError();
 }
 
 cudaError_t ic_source(int64_t n, const float* hxx, const float* hyy, const float* hzz,
                       const float* hxy, const float* hxz, const float* hyz, float* src,
-                      cudaStream_t s) {
-  k_ic_source<<<blocks_for(n), NTI, 0, s>>>(n, hxx, hyy, hzz, hxy, hxz, hyz, src);
+                      cudaStream_t s, Multi m) {
+  k_ic_source<<<dim3(blocks_for(n), m.nb), NTI, 0, s>>>(n, hxx, hyy, hzz, hxy, hxz, hyz, src, m);
   return cudaGetLastError();
 }
 
-cudaError_t ic_phi2(int N, float2* c, float kf, cudaStream_t s) {
+cudaError_t ic_phi2(int N, float2* c, float kf, cudaStream_t s, Multi m) {
   const int64_t n = half_elems(N);
-  k_ic_phi2<<<blocks_for(n), NTI, 0, s>>>(N, half_pitch(N), c, kf);
+  k_ic_phi2<<<dim3(blocks_for(n), m.nb), NTI, 0, s>>>(N, half_pitch(N), c, kf, m);
   return cudaGetLastError();
 }
 
 cudaError_t ic_particles(int64_t P, const float* px, const float* py, const float* pz, float* sx,
                          float* sy, float* sz, float* vx, float* vy, float* vz,
-                         cudaStream_t s) {
-  k_ic_particles<<<blocks_for(P), NTI, 0, s>>>(P, px, py, pz, sx, sy, sz, vx, vy, vz);
+                         cudaStream_t s, Multi m) {
+  k_ic_particles<<<dim3(blocks_for(P), m.nb), NTI, 0, s>>>(P, px, py, pz, sx, sy, sz, vx, vy, vz, m);
   return cudaGetLastError();
 }
 
@@ -241,20 +294,27 @@ cudaError_t half_unpack(int N, const float2* padded, float2* dense, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t seed_absmax(int N, const float2* src, float* out_absmax, cudaStream_t s) {
+cudaError_t seed_absmax(int N, const float2* src, float* out_absmax, cudaStream_t s, Multi m) {
   const int64_t n = half_elems(N);
-  cudaError_t e = cudaMemsetAsync(out_absmax, 0, sizeof(float), s);
+  cudaError_t e = zero_f32(out_absmax, 4, s, m);  // the float and its 16-byte group
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)std::min<int64_t>((n + NTI - 1) / NTI, 152 * 16);
-  k_absmax<<<grid, NTI, 0, s>>>(n, N, half_pitch(N), src,
-                                reinterpret_cast<unsigned int*>(out_absmax));
+  const unsigned grid = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((n + NTI - 1) / NTI, 152 * 16 / std::min(m.nb, 16)));
+  k_absmax<<<dim3(grid, m.nb), NTI, 0, s>>>(n, N, half_pitch(N), src,
+                                            reinterpret_cast<unsigned int*>(out_absmax), m);
   return cudaGetLastError();
 }
 
-cudaError_t seed_quantise(int N, const float2* src, void* dst, int prec, float inv_scale,
-                          cudaStream_t s) {
+cudaError_t seed_scale_set(SimHeader* hdr, const float* absmax, int f, cudaStream_t s, Multi m) {
+  k_seed_scale<<<(m.nb + 127) / 128, 128, 0, s>>>(hdr, absmax, f, m);
+  return cudaGetLastError();
+}
+
+cudaError_t seed_quantise(int N, const float2* src, void* dst, int prec, const SimHeader* hdr, int f,
+                          cudaStream_t s, Multi m) {
   const int64_t n = half_elems(N);
-  k_quantise<<<blocks_for(n), NTI, 0, s>>>(n, src, static_cast<uint32_t*>(dst), prec, inv_scale);
+  k_quantise<<<dim3(blocks_for(n), m.nb), NTI, 0, s>>>(n, src, static_cast<uint32_t*>(dst), prec, hdr,
+                                                       f, m);
   return cudaGetLastError();
 }
 

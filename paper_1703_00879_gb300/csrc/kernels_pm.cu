@@ -334,7 +334,13 @@ __global__ void k_step_advance(SimHeader* hdr, Multi m) {
   if (b < m.nb) moved(hdr, shift_of(m, b))->step += 1;
 }
 
-__global__ void k_set_header(SimHeader* hdr, SimHeader v) { *hdr = v; }
+// Writes the header; the seed scales are written only on the device (by the
+// initial conditions) and keep their values.
+__global__ void k_set_header(SimHeader* hdr, SimHeader v) {
+  v.seed_scale[0] = hdr->seed_scale[0];
+  v.seed_scale[1] = hdr->seed_scale[1];
+  *hdr = v;
+}
 
 // Up to kParamWords int64 values carried in the launch parameters (a host to
 // device copy that neither synchronises nor needs pinned memory).

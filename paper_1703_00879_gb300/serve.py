@@ -17,12 +17,13 @@ late arrivals join early instead of queueing behind work enqueued long ago.
 With one_stream, the ICs and all buckets share one stream: the persistent
 kernels then never compete for SMs with another bucket's kernels.
 
-Nothing in the loop waits for the device: initial conditions run on a side
-stream and a run joins its bucket's ticks once they are done (its context
+Nothing in the loop waits for the device: the initial conditions of the runs
+admitted together run on a side stream as one multi-simulation sequence
+(cola_ic_many), a run joins its bucket's ticks once they are done (its context
 then moves to the bucket stream), results are fetched with a non-blocking
 P(k), and finished contexts are freed when their bucket has no tick in flight.
 
-The loop is host logic on top of the C ABI (cola_init, cola_ic,
+The loop is host logic on top of the C ABI (cola_init, cola_ic_many,
 cola_set_stream, cola_step_many, cola_pk_async, cola_free); every step of the
 method runs in the library's kernels.
 """
@@ -35,7 +36,7 @@ from typing import Callable, Optional
 
 import numpy as np
 
-from . import Simulation, cola_device_bytes, step_many
+from . import Simulation, cola_device_bytes, ic_many, step_many
 
 
 @dataclass
@@ -118,9 +119,12 @@ class _TorchBackend:
         e.record(stream)
         return e
 
-    def simulation(self, run, stream):
+    def simulations(self, runs, stream):
+        """Contexts for runs, their initial conditions in one multi-simulation launch sequence."""
         with self.torch.cuda.stream(stream):
-            return Simulation(run, stream=stream)
+            sims = [Simulation(r, stream=stream, ic=False) for r in runs]
+            ic_many(sims, stream)
+        return sims
 
     def move(self, sim, stream):
         sim.set_stream(stream)
@@ -177,8 +181,10 @@ class Server:
             now = self.clock() - t0
             while pending and (pending[0][0] <= now or not realtime):
                 waiting.append(pending.popleft())
-            # admission: FIFO, by memory budget and free slots; ICs on the side stream
-            while waiting and len(active) < self.max_slots:
+            # admission: FIFO, by memory budget and free slots; the ICs of everything
+            # admitted now run on the side stream as one multi-simulation sequence
+            admitted = []
+            while waiting and len(active) + len(admitted) < self.max_slots:
                 t_arr, rid, run = waiting[0]
                 need = self.bytes_for(run)
                 if used + need > self.budget:
@@ -187,10 +193,14 @@ class Server:
                 key = shape_key(run)
                 if key not in buckets:
                     buckets[key] = _Bucket(shared or be.stream())
-                sim = be.simulation(run, ic_stream)
                 used += need
-                active.append(_Slot(rid, run, sim, key, t_arr, self.clock() - t0, need,
-                                    ic_event=be.event(ic_stream)))
+                admitted.append((rid, run, key, t_arr, need))
+            if admitted:
+                sims = be.simulations([a[1] for a in admitted], ic_stream)
+                ev = be.event(ic_stream)
+                now_adm = self.clock() - t0
+                for (rid, run, key, t_arr, need), sim in zip(admitted, sims):
+                    active.append(_Slot(rid, run, sim, key, t_arr, now_adm, need, ic_event=ev))
             stats.peak_bytes = max(stats.peak_bytes, used)
             stats.peak_active = max(stats.peak_active, len(active))
             progressed = False

@@ -132,6 +132,32 @@ def test_step_many_mixes_shapes_models_step_counts_and_progress():
         s.close()
 
 
+def test_ic_many_equals_cola_ic():
+    """Initial conditions of many contexts in one launch sequence: the same
+    displacements, bit for bit, as cola_ic per context (no atomics on that
+    path), and runs that end where the solo runs end; two shapes, every model,
+    reduced-precision seeds in one of them."""
+    import paper_1703_00879_gb300 as pkg
+    runs = [ensemble_run(seed, Np=32, Nmesh=64, Lbox=64.0, nsteps=3) for seed in range(6)]
+    runs += [ensemble_run(20 + seed, Np=32, Nmesh=32, Lbox=64.0, nsteps=3) for seed in range(3)]
+    precs = [0] * 6 + [1] * 3
+    solo = []
+    for r, pr in zip(runs, precs):
+        with pkg.Simulation(r, seed_precision=pr) as s:
+            d0 = s.export(pkg.COLA_F_DISP)
+            s.run_to_end()
+            solo.append((d0, s.export(pkg.COLA_F_DISP)))
+    sims = [pkg.Simulation(r, seed_precision=pr, ic=False) for r, pr in zip(runs, precs)]
+    pkg.ic_many(sims)
+    for s, (d0, _) in zip(sims, solo):
+        assert np.array_equal(s.export(pkg.COLA_F_DISP), d0)
+    while any(s.steps_done < s.run.nsteps for s in sims):
+        pkg.step_many([s for s in sims if s.steps_done < s.run.nsteps])
+    for r, s, (_, d1) in zip(runs, sims, solo):
+        assert np.max(np.abs(s.export(pkg.COLA_F_DISP) - d1)) / (r.Lbox / r.Nmesh) <= 1e-4
+        s.close()
+
+
 def test_step_many_rejects_finished_and_duplicate_contexts():
     import paper_1703_00879_gb300 as pkg
     r = ensemble_run(0, Np=32, Nmesh=32, Lbox=64.0, nsteps=1)

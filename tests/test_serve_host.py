@@ -58,11 +58,14 @@ class FakeBackend:
         for s in sims:
             s.steps += 1
 
-    def simulation(self, run, stream):
-        self.active += 1
-        self.max_active = max(self.max_active, self.active)
-        self.log.append(("admit", run.name))
-        return FakeSim(run, self.log)
+    def simulations(self, runs, stream):
+        out = []
+        for run in runs:
+            self.active += 1
+            self.max_active = max(self.max_active, self.active)
+            self.log.append(("admit", run.name))
+            out.append(FakeSim(run, self.log))
+        return out
 
     def move(self, sim, stream):
         sim.stream = stream
