@@ -79,6 +79,12 @@ def whole_job_throughput(units_per_rank: float, world: int, max_seconds: float) 
     return units_per_rank * world / max_seconds
 
 
+def replica_run(base, rank: int, total_steps: int):
+    """The simulation rank `rank` runs: the workload with its own seed (replicas only:
+    independent simulations, no data exchanged between ranks)."""
+    return base.with_(nsteps=max(base.nsteps, total_steps), seed=base.seed + rank)
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock, power and throttle reasons during the timed region."""
@@ -202,7 +208,7 @@ def bench_ours(args):
     import paper_1703_00879_gb300 as pkg
 
     base = WORKLOADS[args.workload]
-    run = base.with_(nsteps=max(base.nsteps, args.warmup + args.steps), seed=base.seed + rank)
+    run = replica_run(base, rank, args.warmup + args.steps)
     stream = torch.cuda.current_stream()
     sim = pkg.Simulation(run)
     sim.step(args.warmup)
