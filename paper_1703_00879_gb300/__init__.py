@@ -365,6 +365,11 @@ class Simulation:
         _check(lib().cola_cic_deposit(self.ctx, p.ctypes.data, p.shape[0], out.ctypes.data, COLA_HOST), self.ctx)
         return out
 
+    def force_from_density_device(self, rho_t, a: float, out_t):
+        """cola_force_from_density on device torch tensors: rho [Nm^3] float32, out [3, Nm^3] float32."""
+        _check(lib().cola_force_from_density(self.ctx, rho_t.data_ptr(), float(a), out_t.data_ptr(),
+                                             COLA_DEVICE), self.ctx)
+
     def force_from_density(self, rho: np.ndarray, a: float) -> np.ndarray:
         N = self.run.Nmesh
         r = np.ascontiguousarray(rho, dtype=np.float32)

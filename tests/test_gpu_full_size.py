@@ -109,3 +109,106 @@ def test_big_ndgp_reduced_seeds(prec, u):
     assert e0 <= 1.5 * bound0
     assert e1 <= bound1
     assert perr <= 4 * u
+
+
+# ------------------------------------------------------------------ 1024^3 mesh force against closed forms
+# A density made of a few Fourier modes, delta = sum_i A_i cos(k_i.x + phi_i),
+# has Phi_tot(k) = -kappa g(k) delta(k) / k^2 exactly on the grid (continuous k,
+# spectral gradient, no window): F = -grad Phi = -kappa g(k) A k sin(k.x + phi)/|k|^2
+# per mode, with g = 1 (LCDM), 1 + C yuk(k) (f(R) with |f_R0| so large that the
+# chameleon never screens: eps = 1), 1 + C (nDGP with r_c H0 so small that the
+# Vainshtein eps = 1 to 1e-9).  The modes avoid Nyquist planes and cover low and
+# high frequencies on every axis.
+MODES = [((3, 5, 7), 0.10, 0.3), ((1, 2, 700), 0.08, 1.1), ((511, 0, 5), 0.06, 2.0),
+         ((0, 300, 511), 0.07, 0.7), ((17, 1000, 33), 0.05, 4.0)]
+
+
+def _closed_form_force(modes, idx, N, L, a, Om, g_of_k):
+    """F[3, len(idx)] at flat mesh indices idx ([z][y][x] order)."""
+    from oracle.background import kappa
+    iz, rem = np.divmod(idx, N * N)
+    iy, ix = np.divmod(rem, N)
+    x = np.stack([ix, iy, iz]).astype(np.float64) * (L / N)
+    F = np.zeros((3, idx.size))
+    for n, A, ph in modes:
+        nv = np.array([q if q < N // 2 else q - N for q in n], np.float64)
+        k = 2 * np.pi * nv / L
+        k2 = float(k @ k)
+        s = np.sin(k @ x + ph)
+        F -= float(kappa(a, Om)) * g_of_k(k2) * A * np.outer(k, s) / k2
+    return F
+
+
+def _model_cases():
+    from oracle import models as om
+    from workloads import Model
+    a, Om = 0.6, 0.3
+    fr = Model(kind=1, fR0=0.5, screening=1)
+    m2 = float(om.fr_m2(a, Om, fr.fR0))
+    nd = Model(kind=2, rcH0=1e-4, screening=1, R_smooth=1.0)
+    C = 1.0 / (3.0 * float(om.dgp_beta(a, Om, nd.rcH0)))
+    return [("lcdm", LCDM_MODEL, lambda k2: 1.0),
+            ("fR_unscreened_limit", fr, lambda k2: 1.0 + (1.0 / 3.0) * k2 / (k2 + a * a * m2)),
+            ("nDGP_eps1_limit", nd, lambda k2: 1.0 + C)], a, Om
+
+
+def _density_from_modes(modes, N, L, rho_bar):
+    x = np.arange(N) * (L / N)
+    d = np.zeros((N, N, N))
+    for n, A, ph in modes:
+        k = [2 * np.pi * (q if q < N // 2 else q - N) / L for q in n]
+        d += A * np.cos(k[0] * x[None, None, :] + k[1] * x[None, :, None] + k[2] * x[:, None, None] + ph)
+    return rho_bar * (1.0 + d)
+
+
+def test_closed_form_force_matches_oracle_at_small_size():
+    """Pins the closed form used at 1024^3 against oracle.pm.force_mesh (N = 32)."""
+    from oracle import pm
+    N, L = 32, 64.0
+    modes = [((3, 5, 7), 0.10, 0.3), ((1, 2, 29), 0.08, 1.1), ((15, 0, 5), 0.06, 2.0)]
+    cases, a, Om = _model_cases()
+    idx = np.arange(N ** 3)
+    rho = _density_from_modes(modes, N, L, 1.0)
+    for name, model, g in cases:
+        ref = np.stack([f.ravel() for f in pm.force_mesh(rho, 1.0, N, L, a, Om, model)])
+        cf = _closed_form_force(modes, idx, N, L, a, Om, g)
+        assert np.max(np.abs(ref - cf)) <= 1e-6 * np.max(np.abs(cf)), name
+
+
+@pytest.mark.parametrize("case", [0, 1, 2], ids=["lcdm", "fR_unscreened_limit", "nDGP_eps1_limit"])
+def test_big_mesh_force_vs_closed_form(case):
+    """The 1024^3 force path the bench times (screened and unscreened 1024-point
+    z passes, x passes of 512-point rows) at 65536 sampled cells plus one full z
+    line."""
+    import torch
+
+    import paper_1703_00879_gb300 as pkg
+    cases, a, Om = _model_cases()
+    name, model, g = cases[case]
+    N, L = 1024, 1024.0
+    run = BIG_NDGP.with_(Np=32, model=model)
+    rho_bar = (run.Np / N) ** 3
+    dev = torch.device("cuda")
+    # the density, built with plain PyTorch on the device
+    xs = torch.arange(N, device=dev, dtype=torch.float64) * (L / N)
+    rho = torch.zeros((N, N, N), device=dev, dtype=torch.float32)
+    for n, A, ph in MODES:
+        k = [2 * np.pi * (q if q < N // 2 else q - N) / L for q in n]
+        for iz in range(0, N, 64):
+            z = xs[iz:iz + 64]
+            arg = k[0] * xs[None, None, :] + k[1] * xs[None, :, None] + k[2] * z[:, None, None] + ph
+            rho[iz:iz + 64] += (A * torch.cos(arg)).to(torch.float32)
+    rho = (rho + 1.0) * rho_bar
+    out = torch.empty((3, N ** 3), device=dev, dtype=torch.float32)
+    with pkg.Simulation(run, ic=False) as s:
+        s.force_from_density_device(rho.view(-1), a, out)
+    torch.cuda.synchronize()
+    del rho
+    rng = np.random.default_rng(7)
+    idx = np.concatenate([rng.integers(0, N ** 3, size=65536),
+                          (np.arange(N) * N + 123) * N + 77])            # the z line at (x=77, y=123)
+    F = out[:, torch.as_tensor(idx, device=dev)].double().cpu().numpy()
+    ref = _closed_form_force(MODES, idx, N, L, a, Om, g)
+    err = np.max(np.abs(F - ref)) / np.max(np.abs(ref))
+    print(f"\n{name}: max |F - closed form| / max |F| = {err:.2e}")
+    assert err <= 5e-5
