@@ -595,14 +595,14 @@ int force_group(const Group& g, double a, bool device_params, bool ini = false) 
     CK(fft_col(N, sc.lead->Cd, 1, false, tw, st, sc.m));
     prof_end(ctx, ST_MESH_Y, e, 1, sc.m.nb * 2 * H);
     e = prof_begin(ctx);
-    CK(mesh_z_force(N, sc.lead->Cd, sc.lead->Ck, sc.lead->Cphi, sc.lead->Cphz, nullptr, fp_of(sc.lead), tw,
-                    st, sc.m));
+    CK(mesh_z_force(N, sc.lead->Cd, sc.lead->Ck, sc.lead->Cphi, sc.lead->Cphz, fp_of(sc.lead), tw, st,
+                    sc.m));
     prof_end(ctx, ST_Z_FORCE, e, 1, sc.m.nb * 4 * H);
   }
   if (const Group::Sub& un = g.unscreened; un.lead) {
     e = prof_begin(ctx);
-    CK(mesh_z_force(N, un.lead->Cd, nullptr, un.lead->Cphi, un.lead->Cphz, nullptr, fp_of(un.lead), tw,
-                    st, un.m));
+    CK(mesh_z_force(N, un.lead->Cd, nullptr, un.lead->Cphi, un.lead->Cphz, fp_of(un.lead), tw, st,
+                    un.m));
     prof_end(ctx, ST_Z_FORCE, e, 1, un.m.nb * 3 * H);
   }
   e = prof_begin(ctx);

@@ -145,11 +145,10 @@ cudaError_t mesh_x_screen_source(int N, const float2* w_in, const float* rho, fl
                                  const ForceParams& fp, const float2* tw, cudaStream_t s,
                                  Multi m = {});
 // Forward z of the source (S or delta), Phi_tot(k) and -i kz Phi_tot, inverse z.
-// dk may be null when unscreened; dk_keep (optional) receives the forward
-// spectrum of `in` when unscreened.
+// dk (delta(k) after the forward z pass) is read when screened, may be null otherwise.
 cudaError_t mesh_z_force(int N, const float2* in, const float2* dk, float2* phi_out,
-                         float2* phiz_out, float2* dk_keep, const ForceParams& fp,
-                         const float2* tw, cudaStream_t s, Multi m = {});
+                         float2* phiz_out, const ForceParams& fp, const float2* tw, cudaStream_t s,
+                         Multi m = {});
 // LPT: phi1, phi2 -> (c1 phi1 + c2 phi2), i kz (...), (e1 phi1 + e2 phi2), i kz (...),
 // each inverse-transformed along z.  phi1/phi2 point to float2 (fp32) or
 // 2 x 16-bit pairs (bf16/fp16) according to lp.seed_prec.

@@ -151,8 +151,8 @@ struct Split {
   static_assert(R2 <= 32 && R1 * R2 == L, "transform length");
 };
 
-// Rows of shared memory a length-L tile transform needs: L, plus R2 padding
-// rows for the intermediate of tiles whose row pitch is a multiple of 8.
+// Rows of shared memory a length-L column-tile transform needs: L, plus R2
+// padding rows for the intermediate.
 template <int L>
 __host__ __device__ constexpr int fft_rows() {
   return L + Split<L>::R2;
@@ -161,20 +161,18 @@ __host__ __device__ constexpr int fft_rows() {
 // Length-L transform of the TW columns of a shared-memory tile (four-step):
 // step 1: for each n2 < R2, DFT_R1 over x[R2 n1 + n2], times w_L^(n2 k1);
 // step 2: for each k1 < R1, DFT_R2 over n2 gives X[k1 + R1 k2].
-// Where the intermediate Y[n2][k1] goes, so that the 16 lanes of a half-warp
-// hit 16 different bank pairs:
-//  * row pitch a multiple of 8 (column tiles): row n2 (R1 + 1) + k1, one
-//    padding row per R1 (the tile needs fft_rows<L>() rows); every address is
-//    then a per-thread base plus a compile-time offset;
-//  * odd row pitch (row tiles): row R2 k1 + ((n2 + k1) mod R2), in place.
-// tw has L * TWS entries; the caller synchronises before the call; returns
-// after a barrier.
+// The intermediate Y[n2][k1] goes to row n2 (R1 + 1) + k1, one padding row
+// per R1 (the tile needs fft_rows<L>() rows): with a row pitch that is a
+// multiple of 8 the 16 lanes of a half-warp hit 16 different bank pairs, and
+// every address is a per-thread base plus a compile-time offset.  tw has
+// L * TWS entries; the caller synchronises before the call; returns after a
+// barrier.
 template <int L, int TW, int PITCH, int NT, bool INV, int TWS = 1>
 __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2* __restrict__ tw) {
   constexpr int R1 = Split<L>::R1, R2 = Split<L>::R2;
   constexpr int U1 = TW * R2, P1 = (U1 + NT - 1) / NT;
   constexpr int U2 = TW * R1, P2 = (U2 + NT - 1) / NT;
-  constexpr bool PAD = (PITCH % 8) == 0;
+  static_assert(PITCH % 8 == 0, "column tiles: row pitch a multiple of 8");
   const int tid = threadIdx.x;
   {
     float2 v[P1][R1];
@@ -202,15 +200,9 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
       const int u = tid + i * NT;
       if ((U1 % NT) == 0 || u < U1) {
         const int c = u % TW, n2 = u / TW;
-        if constexpr (PAD) {
-          float2* y = buf + n2 * (R1 + 1) * PITCH + c;
+        float2* y = buf + n2 * (R1 + 1) * PITCH + c;
 #pragma unroll
-          for (int k1 = 0; k1 < R1; ++k1) y[k1 * PITCH] = v[i][pos_of<R1>(k1)];
-        } else {
-#pragma unroll
-          for (int k1 = 0; k1 < R1; ++k1)
-            buf[(R2 * k1 + ((n2 + k1) & (R2 - 1))) * PITCH + c] = v[i][pos_of<R1>(k1)];
-        }
+        for (int k1 = 0; k1 < R1; ++k1) y[k1 * PITCH] = v[i][pos_of<R1>(k1)];
       }
     }
   }
@@ -222,14 +214,9 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
       const int u = tid + i * NT;
       if ((U2 % NT) == 0 || u < U2) {
         const int c = u % TW, k1 = u / TW;
-        if constexpr (PAD) {
-          const float2* yr = buf + k1 * PITCH + c;
+        const float2* yr = buf + k1 * PITCH + c;
 #pragma unroll
-          for (int n2 = 0; n2 < R2; ++n2) y[i][n2] = yr[n2 * (R1 + 1) * PITCH];
-        } else {
-#pragma unroll
-          for (int n2 = 0; n2 < R2; ++n2) y[i][n2] = buf[(R2 * k1 + ((n2 + k1) & (R2 - 1))) * PITCH + c];
-        }
+        for (int n2 = 0; n2 < R2; ++n2) y[i][n2] = yr[n2 * (R1 + 1) * PITCH];
         dftR<R2, INV>(y[i]);
       }
     }

@@ -371,12 +371,12 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_tw(N, TW), N) < 2
 // transformed forward; delta(k) is read straight from global memory; Phi_tot(k)
 // is kept in registers while the two outputs (Phi and -i kz Phi) are inverse
 // transformed one after the other in the same buffer.
-template <int N, int TW, bool SCREENED, bool KEEP>
+template <int N, int TW, bool SCREENED>
 struct OpZForce {
   static constexpr int E = (N * TW) / NT;  // elements per thread
   ColGeo<N, TW> geo;
   const float2 *in, *dk;
-  float2 *phi_out, *phiz_out, *dk_keep;
+  float2 *phi_out, *phiz_out;
   ForceParams fp;
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
@@ -402,7 +402,6 @@ struct OpZForce {
     resolve(fp, by);
     float2* ph = extra;  // delta(k) of the tile, then Phi_tot(k), N x TW
     fft_tile_call<N, TW, TW, NT, false>(buf, tw);
-    if (KEEP) col_store<N, TW, TW>(buf, 0, moved(dk_keep, by), base, geo.sn, c0);
     if (SCREENED) {
       cp_async_wait<1>();  // delta(k) of this tile; the next tile's prefetch may still be in flight
       __syncthreads();
@@ -443,9 +442,9 @@ struct OpZForce {
   }
 };
 
-template <int N, int TW, bool SCREENED, bool KEEP>
+template <int N, int TW, bool SCREENED>
 __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_tw(N, TW) + (size_t)N * TW * 8, N) < 2 ? 1 : 2) k_z_force(
-    OpZForce<N, TW, SCREENED, KEEP> op, const float2* __restrict__ twg, int64_t ntiles) {
+    OpZForce<N, TW, SCREENED> op, const float2* __restrict__ twg, int64_t ntiles) {
   if (!op.geo.m.shift) resolve(op.fp, 0);  // one simulation: once per launch
   col_pipeline<N, fft_rows<N>() * TW>(op, twg, ntiles);
 }
@@ -1060,36 +1059,27 @@ cudaError_t mesh_x_screen_source(int Nv, const float2* w_in, const float* rho, f
   return cudaSuccess;
 }
 
-template <int N, bool SCR, bool KEEP>
+template <int N, bool SCR>
 static cudaError_t launch_zforce_t(const float2* in, const float2* dk, float2* phi,
-                                   float2* phiz, float2* keep, const ForceParams& fp,
+                                   float2* phiz, const ForceParams& fp,
                                    const float2* tw, cudaStream_t s, Multi m) {
   constexpr int TW = ztw(N);
   constexpr size_t sm = col_smem_tw(N, TW) + (size_t)N * TW * sizeof(float2);
   const int64_t ntiles = col_tiles<N, TW>() * m.nb;
-  auto k = k_z_force<N, TW, SCR, KEEP>;
+  auto k = k_z_force<N, TW, SCR>;
   unsigned grid;
   cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, sm, s>>>(OpZForce<N, TW, SCR, KEEP>{geo_z<N, TW>(m), in, dk, phi, phiz, keep, fp}, tw,
-                         ntiles);
+  k<<<grid, NT, sm, s>>>(OpZForce<N, TW, SCR>{geo_z<N, TW>(m), in, dk, phi, phiz, fp}, tw, ntiles);
   return cudaGetLastError();
 }
 
-template <int N>
-static cudaError_t launch_zforce(const float2* in, const float2* dk, float2* phi, float2* phiz,
-                                 float2* keep, const ForceParams& fp, const float2* tw,
-                                 cudaStream_t s, Multi m) {
-  if (fp.screened) return launch_zforce_t<N, true, false>(in, dk, phi, phiz, keep, fp, tw, s, m);
-  if (keep) return launch_zforce_t<N, false, true>(in, dk, phi, phiz, keep, fp, tw, s, m);
-  return launch_zforce_t<N, false, false>(in, dk, phi, phiz, keep, fp, tw, s, m);
-}
-
 cudaError_t mesh_z_force(int Nv, const float2* in, const float2* dk, float2* phi_out,
-                         float2* phiz_out, float2* dk_keep, const ForceParams& fp,
-                         const float2* tw, cudaStream_t s, Multi m) {
+                         float2* phiz_out, const ForceParams& fp, const float2* tw, cudaStream_t s,
+                         Multi m) {
   if (fp.screened && dk == nullptr) return cudaErrorInvalidValue;
-  COLA_SWITCH_N(Nv, return launch_zforce<N>(in, dk, phi_out, phiz_out, dk_keep, fp, tw, s, m));
+  COLA_SWITCH_N(Nv, return fp.screened ? launch_zforce_t<N, true>(in, dk, phi_out, phiz_out, fp, tw, s, m)
+                                       : launch_zforce_t<N, false>(in, dk, phi_out, phiz_out, fp, tw, s, m));
   return cudaSuccess;
 }
 
