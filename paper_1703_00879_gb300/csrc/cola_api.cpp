@@ -463,7 +463,8 @@ ForceParams force_params(const cola_ctx* c, double a) {
   return fp;
 }
 
-// 3-D transforms on the padded half-spectrum layout.
+// 3-D transforms on the internal half-spectrum layout (plane pairs interleaved
+// in 64-byte chunks, cola_internal.h).
 int r2c3(cola_ctx* ctx, int N, const float* in, float2* out, const float2* tw, float scale,
          float offset, Multi m = {}) {
   CK(fft_xr2c(N, in, out, scale, offset, tw, ctx->st, m));

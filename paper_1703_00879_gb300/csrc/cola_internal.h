@@ -10,8 +10,30 @@ namespace cola {
 
 // Row pitch (in complex elements) of every half spectrum: N/2+1 rounded up to
 // 16 so that column tiles of 2..16 elements never straddle a row.
-inline int64_t half_pitch(int N) { return ((N / 2 + 1 + 15) / 16) * 16; }
+__host__ __device__ constexpr int64_t half_pitch(int N) { return ((N / 2 + 1 + 15) / 16) * 16; }
 inline int64_t half_elems(int N) { return (int64_t)N * N * half_pitch(N); }
+
+// Half-spectrum layout.  The rows (z, y) of the planes z = 2j and 2j + 1 are
+// interleaved in chunks of 8 complex values (64 bytes):
+//   element (z, y, kx) at ((z >> 1) N + y) 2P + (kx >> 3) 16 + (z & 1) 8 + (kx & 7),
+// P = half_pitch(N).  A pass along z then reads 128 contiguous bytes per pair of
+// planes where the plain [z][y][kx] order gives 64-byte pieces one plane
+// (N P 8 bytes) apart.  Rows are also numbered pair-major,
+// q = ((z >> 1) N + y) 2 + (z & 1), so that TW consecutive rows q (TW even)
+// fill a contiguous block of TW P elements.
+__host__ __device__ inline int64_t hcol(int kx) { return (int64_t)(kx >> 3) * 16 + (kx & 7); }
+__host__ __device__ inline int64_t hrow(int z, int y, int N, int64_t P) {
+  return ((int64_t)(z >> 1) * N + y) * 2 * P + (z & 1) * 8;
+}
+__host__ __device__ inline int64_t hidx(int z, int y, int kx, int N, int64_t P) {
+  return hrow(z, y, N, P) + hcol(kx);
+}
+// start of pair-major row q, and the index z N + y of the real-space row it belongs to
+__host__ __device__ inline int64_t hrow_q(int64_t q, int64_t P) { return (q >> 1) * 2 * P + (q & 1) * 8; }
+__host__ __device__ inline int64_t real_row_q(int64_t q, int N) {
+  const int64_t pr = q >> 1;  // (z >> 1) N + y
+  return ((pr / N) * 2 + (q & 1)) * N + pr % N;
+}
 
 struct SimHeader;
 

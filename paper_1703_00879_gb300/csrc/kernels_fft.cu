@@ -140,17 +140,25 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // ---------------------------------------------------------------- column tiles
 // Tile element (n, c) of sub-block `sub` lives at buf[n * TP + sub * TW + c];
-// global element at g[base + n * sn + c]; only columns c0 + c < N/2 + 1 exist.
+// global element at g[base + row(n) + hcol(c)] with row(n) = (n >> 1) ra +
+// (n & 1) rb (the half-spectrum layout of cola_internal.h); only columns
+// c0 + c < N/2 + 1 exist.  Each thread keeps one 16-byte piece (or one column)
+// and walks rows n0, n0 + step, ... (step even, so n & 1 stays fixed).
 template <int N, int TW, int TP>
 __device__ __forceinline__ void col_issue(float2* buf, int sub, const float2* __restrict__ g,
-                                          int64_t base, int64_t sn, int c0) {
-  constexpr int CH = TW / 2;  // 16-byte chunks per row segment
+                                          int64_t base, int64_t ra, int64_t rb, int c0) {
+  constexpr int CH = TW / 2;  // 16-byte pieces per row segment
+  constexpr int STEP = NT / CH;
+  static_assert(STEP % 2 == 0, "row step must be even");
+  const int j = threadIdx.x % CH, n0 = threadIdx.x / CH;
+  const bool v = c0 + 2 * j < N / 2 + 1;
+  const float2* src = g + base + (n0 >> 1) * ra + (n0 & 1) * rb + hcol(2 * j);
+  float2* dst = buf + n0 * TP + sub * TW + 2 * j;
 #pragma unroll 4
-  for (int e = threadIdx.x; e < N * CH; e += NT) {
-    const int j = e % CH, n = e / CH;
-    const bool v = c0 + 2 * j < N / 2 + 1;
-    cp_async16(buf + n * TP + sub * TW + 2 * j, v ? (const void*)(g + base + (int64_t)n * sn + 2 * j)
-                                                   : (const void*)g, v);
+  for (int n = n0; n < N; n += STEP) {
+    cp_async16(dst, v ? (const void*)src : (const void*)g, v);
+    src += (STEP / 2) * ra;
+    dst += STEP * TP;
   }
 }
 
@@ -158,25 +166,37 @@ __device__ __forceinline__ void col_issue(float2* buf, int sub, const float2* __
 // row n is staged raw in the sub-block 2/3 area of that row:
 // raw(f, n, c) = ((uint32*)buf)[8 n TW + 4 TW + f TW + c]  (TP = 4 TW).
 template <int N, int TW>
-__device__ __forceinline__ void col_issue_raw(uint32_t* rb, int f, const uint32_t* __restrict__ g,
-                                              int64_t base, int64_t sn, int c0) {
+__device__ __forceinline__ void col_issue_raw(uint32_t* rb_, int f, const uint32_t* __restrict__ g,
+                                              int64_t base, int64_t ra, int64_t rb, int c0) {
   constexpr int CH = TW / 4;
+  constexpr int STEP = NT / CH;
+  static_assert(STEP % 2 == 0, "row step must be even");
+  const int j = threadIdx.x % CH, n0 = threadIdx.x / CH;
+  const bool v = c0 + 4 * j < N / 2 + 1;
+  const uint32_t* src = g + base + (n0 >> 1) * ra + (n0 & 1) * rb + hcol(4 * j);
+  uint32_t* dst = rb_ + 8 * n0 * TW + 4 * TW + f * TW + 4 * j;
 #pragma unroll 4
-  for (int e = threadIdx.x; e < N * CH; e += NT) {
-    const int j = e % CH, n = e / CH;
-    const bool v = c0 + 4 * j < N / 2 + 1;
-    cp_async16(rb + 8 * n * TW + 4 * TW + f * TW + 4 * j,
-               v ? (const void*)(g + base + (int64_t)n * sn + 4 * j) : (const void*)g, v);
+  for (int n = n0; n < N; n += STEP) {
+    cp_async16(dst, v ? (const void*)src : (const void*)g, v);
+    src += (STEP / 2) * ra;
+    dst += 8 * STEP * TW;
   }
 }
 
 template <int N, int TW, int TP>
 __device__ __forceinline__ void col_store(const float2* buf, int sub, float2* __restrict__ g,
-                                          int64_t base, int64_t sn, int c0) {
+                                          int64_t base, int64_t ra, int64_t rb, int c0) {
+  constexpr int STEP = NT / TW;
+  static_assert(STEP % 2 == 0, "row step must be even");
+  const int c = threadIdx.x % TW, n0 = threadIdx.x / TW;
+  if (c0 + c >= N / 2 + 1) return;
+  float2* dst = g + base + (n0 >> 1) * ra + (n0 & 1) * rb + hcol(c);
+  const float2* src = buf + n0 * TP + sub * TW + c;
 #pragma unroll 4
-  for (int e = threadIdx.x; e < N * TW; e += NT) {
-    const int c = e % TW, n = e / TW;
-    if (c0 + c < N / 2 + 1) g[base + (int64_t)n * sn + c] = buf[n * TP + sub * TW + c];
+  for (int n = n0; n < N; n += STEP) {
+    *dst = *src;
+    dst += (STEP / 2) * ra;
+    src += STEP * TP;
   }
 }
 
@@ -185,21 +205,32 @@ __device__ __forceinline__ float kk2(int ix, int iy, int iz, int N, float kf) {
   return kf * kf * (fx * fx + fy * fy + fz * fz);
 }
 
-// Column geometry: tile t -> (simulation b, outer index o, column block tx);
-// base = o * so + c0 and `by` = the byte shift of simulation b's buffers.
+// Column geometry: tile t -> (simulation b, outer index o, column block c0);
+// base = the element offset of (o, row 0, c0) and `by` = the byte shift of
+// simulation b's buffers.  Outer index o sits at (o >> 1) oa + (o & 1) ob and
+// tile row n at (n >> 1) ra + (n & 1) rb.  With pair_tiles, consecutive tiles
+// take o = 2i and 2i + 1 of the same column block (the two halves of each
+// 128-byte chunk pair of the y pass are read by neighbouring CTAs together).
 template <int N, int TW>
 struct ColGeo {
   static constexpr int ntx = (N / 2) / TW + 1;
   static constexpr int64_t tps = (int64_t)N * ntx;  // tiles per simulation
-  int64_t so, sn;
+  int64_t oa, ob, ra, rb;
+  int pair_tiles;
   Multi m;
   __device__ __forceinline__ void tile(int64_t t, int& o, int& c0, int64_t& base, int64_t& by) const {
     const int b = (int)(t / tps);
     t -= (int64_t)b * tps;
     by = shift_of(m, b);
-    o = (int)(t / ntx);
-    c0 = (int)(t % ntx) * TW;
-    base = (int64_t)o * so + c0;
+    if (pair_tiles) {
+      const int r = (int)(t % (2 * ntx));
+      o = (int)(t / (2 * ntx)) * 2 + (r & 1);
+      c0 = (r >> 1) * TW;
+    } else {
+      o = (int)(t / ntx);
+      c0 = (int)(t % ntx) * TW;
+    }
+    base = (o >> 1) * oa + (o & 1) * ob + hcol(c0);
   }
 };
 
@@ -253,7 +284,7 @@ struct OpCol {
     int o, c0;
     int64_t base, by;
     geo.tile(t, o, c0, base, by);
-    col_issue<N, TW, TW>(buf, 0, moved(in, by), base, geo.sn, c0);
+    col_issue<N, TW, TW>(buf, 0, moved(in, by), base, geo.ra, geo.rb, c0);
   }
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
     int o, c0;
@@ -268,7 +299,7 @@ struct OpCol {
       __syncthreads();
     }
     fft_tile<N, TW, TW, NT, INV>(buf, tw);
-    col_store<N, TW, TW>(buf, 0, moved(out, by), base, geo.sn, c0);
+    col_store<N, TW, TW>(buf, 0, moved(out, by), base, geo.ra, geo.rb, c0);
   }
 };
 
@@ -291,7 +322,7 @@ struct OpYinv2 {
     int o, c0;
     int64_t base, by;
     geo.tile(t, o, c0, base, by);
-    col_issue<N, TW, 2 * TW>(buf, 0, moved(in, by), base, geo.sn, c0);
+    col_issue<N, TW, 2 * TW>(buf, 0, moved(in, by), base, geo.ra, geo.rb, c0);
   }
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
     constexpr int TP = 2 * TW;
@@ -305,8 +336,8 @@ struct OpYinv2 {
     }
     __syncthreads();
     fft_tile<N, TP, TP, NT, true>(buf, tw);
-    col_store<N, TW, TP>(buf, 0, moved(outp, by), base, geo.sn, c0);
-    col_store<N, TW, TP>(buf, 1, moved(outd, by), base, geo.sn, c0);
+    col_store<N, TW, TP>(buf, 0, moved(outp, by), base, geo.ra, geo.rb, c0);
+    col_store<N, TW, TP>(buf, 1, moved(outd, by), base, geo.ra, geo.rb, c0);
   }
 };
 
@@ -329,7 +360,7 @@ struct OpZScreenField {
     int o, c0;
     int64_t base, by;
     geo.tile(t, o, c0, base, by);
-    col_issue<N, TW, TW>(buf, 0, moved(in, by), base, geo.sn, c0);
+    col_issue<N, TW, TW>(buf, 0, moved(in, by), base, geo.ra, geo.rb, c0);
   }
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
     int iy, c0;
@@ -343,7 +374,7 @@ struct OpZScreenField {
     for (int e = threadIdx.x; e < N * TW; e += NT) {
       const int c = e % TW, n = e / TW;
       const float2 v = buf[n * TW + c];
-      if (c0 + c < N / 2 + 1) dko[base + (int64_t)n * geo.sn + c] = v;
+      if (c0 + c < N / 2 + 1) dko[base + (n >> 1) * geo.ra + (n & 1) * geo.rb + hcol(c)] = v;
       const float k2 = kk2(c0 + c, iy, n, N, fp.kf);
       float m = 0.f;
       if (k2 > 0.f) {
@@ -354,7 +385,7 @@ struct OpZScreenField {
     }
     __syncthreads();
     fft_tile_call<N, TW, TW, NT, true>(buf, tw);
-    col_store<N, TW, TW>(buf, 0, moved(w_out, by), base, geo.sn, c0);
+    col_store<N, TW, TW>(buf, 0, moved(w_out, by), base, geo.ra, geo.rb, c0);
   }
 };
 
@@ -383,7 +414,7 @@ struct OpZForce {
     int o, c0;
     int64_t base, by;
     geo.tile(t, o, c0, base, by);
-    col_issue<N, TW, TW>(buf, 0, moved(in, by), base, geo.sn, c0);
+    col_issue<N, TW, TW>(buf, 0, moved(in, by), base, geo.ra, geo.rb, c0);
   }
   // delta(k) of the tile into extra; lands while S is transformed
   __device__ __forceinline__ void issue_side(int64_t t) const {
@@ -391,7 +422,7 @@ struct OpZForce {
       int o, c0;
       int64_t base, by;
       geo.tile(t, o, c0, base, by);
-      col_issue<N, TW, TW>(extra, 0, moved(dk, by), base, geo.sn, c0);
+      col_issue<N, TW, TW>(extra, 0, moved(dk, by), base, geo.ra, geo.rb, c0);
     }
   }
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
@@ -427,7 +458,7 @@ struct OpZForce {
     }
     __syncthreads();
     fft_tile_call<N, TW, TW, NT, true>(buf, tw);
-    col_store<N, TW, TW>(buf, 0, moved(phi_out, by), base, geo.sn, c0);
+    col_store<N, TW, TW>(buf, 0, moved(phi_out, by), base, geo.ra, geo.rb, c0);
     __syncthreads();
 #pragma unroll 2
     for (int i = 0; i < E; ++i) {
@@ -438,7 +469,7 @@ struct OpZForce {
     }
     __syncthreads();
     fft_tile_call<N, TW, TW, NT, true>(buf, tw);
-    col_store<N, TW, TW>(buf, 0, moved(phiz_out, by), base, geo.sn, c0);
+    col_store<N, TW, TW>(buf, 0, moved(phiz_out, by), base, geo.ra, geo.rb, c0);
   }
 };
 
@@ -476,13 +507,13 @@ struct OpLptZ {
     int64_t base, by;
     geo.tile(t, o, c0, base, by);
     if constexpr (PREC == 0) {
-      col_issue<N, TW, 4 * TW>(buf, 0, moved(static_cast<const float2*>(phi1), by), base, geo.sn, c0);
-      col_issue<N, TW, 4 * TW>(buf, 1, moved(static_cast<const float2*>(phi2), by), base, geo.sn, c0);
+      col_issue<N, TW, 4 * TW>(buf, 0, moved(static_cast<const float2*>(phi1), by), base, geo.ra, geo.rb, c0);
+      col_issue<N, TW, 4 * TW>(buf, 1, moved(static_cast<const float2*>(phi2), by), base, geo.ra, geo.rb, c0);
     } else {
       // raw 16-bit pairs staged in the (still unused) output sub-blocks 2 and 3
       uint32_t* rb = reinterpret_cast<uint32_t*>(buf);
-      col_issue_raw<N, TW>(rb, 0, moved(static_cast<const uint32_t*>(phi1), by), base, geo.sn, c0);
-      col_issue_raw<N, TW>(rb, 1, moved(static_cast<const uint32_t*>(phi2), by), base, geo.sn, c0);
+      col_issue_raw<N, TW>(rb, 0, moved(static_cast<const uint32_t*>(phi1), by), base, geo.ra, geo.rb, c0);
+      col_issue_raw<N, TW>(rb, 1, moved(static_cast<const uint32_t*>(phi2), by), base, geo.ra, geo.rb, c0);
     }
   }
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
@@ -531,10 +562,10 @@ struct OpLptZ {
     }
     __syncthreads();
     fft_tile<N, TP, TP, NT, true>(buf, tw);
-    col_store<N, TW, TP>(buf, 0, moved(o0, by), base, geo.sn, c0);
-    col_store<N, TW, TP>(buf, 1, moved(o1, by), base, geo.sn, c0);
-    col_store<N, TW, TP>(buf, 2, moved(o2, by), base, geo.sn, c0);
-    col_store<N, TW, TP>(buf, 3, moved(o3, by), base, geo.sn, c0);
+    col_store<N, TW, TP>(buf, 0, moved(o0, by), base, geo.ra, geo.rb, c0);
+    col_store<N, TW, TP>(buf, 1, moved(o1, by), base, geo.ra, geo.rb, c0);
+    col_store<N, TW, TP>(buf, 2, moved(o2, by), base, geo.ra, geo.rb, c0);
+    col_store<N, TW, TP>(buf, 3, moved(o3, by), base, geo.ra, geo.rb, c0);
   }
 };
 
@@ -559,47 +590,94 @@ struct RowCfg {
   static constexpr size_t smem = (N + 2 * stage) * sizeof(float2);
 };
 
-// complex half rows (M + 1 values, staged as M + 2 to keep 16-byte chunks)
+// The rows of a row tile (first pair-major row q0, TWX even) are the pairs
+// (z, y) and (z + 1, y) of TWX/2 consecutive y: in the half spectrum one
+// contiguous block of TWX/2 interleaved row pairs (2P complex values each), in
+// real space two blocks of TWX/2 consecutive rows (even tile rows from real row
+// real_row_q(q0), odd ones from real_row_q(q0 + 1)).  Tile row r is staged at
+// st[r * CW ...].
+//
+// Walk over the NPAIR row pairs of a tile in memory order, LEN positions per
+// pair: warps take whole pairs, or split each pair into NW / NPAIR segments
+// when there are fewer pairs than warps; f(pair, p0, p1) visits p = p0, p0 +
+// 32, ... < p1 with p0 = segment start + lane (segment starts are multiples of
+// 32, so each warp reads or writes whole lines).
+template <int NPAIR, int LEN, class F>
+__device__ __forceinline__ void for_pairs(F f) {
+  constexpr int NW = NT / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if constexpr (NPAIR >= NW) {
+    for (int pr = warp; pr < NPAIR; pr += NW) f(pr, lane, LEN);
+  } else {
+    constexpr int S = NW / NPAIR;
+    constexpr int SEG = (LEN + 32 * S - 1) / (32 * S) * 32;
+    const int s = warp % S;
+    f(warp / S, s * SEG + lane, (s + 1) * SEG < LEN ? (s + 1) * SEG : LEN);
+  }
+}
+
+// Complex half rows (M + 1 values, staged as M + 2 to keep 16-byte pieces).
+// Piece p of a row pair holds values 2p, 2p + 1 of the pair: row (p >> 2) & 1,
+// columns k = (p >> 3) 8 + 2 (p & 3), k + 1; p + 32 is the same row, k + 32.
 template <int N, int TWX>
 __device__ __forceinline__ void stage_complex_rows(float2* st, const float2* __restrict__ in,
-                                                   int64_t row0, int64_t P) {
+                                                   int64_t q0) {
   using C = RowCfg<N, TWX>;
-  constexpr int CH = (C::M + 2) / 2;
-  for (int e = threadIdx.x; e < TWX * CH; e += NT) {
-    const int r = e / CH, j = e - r * CH;
-    cp_async16(st + r * C::CW + 2 * j, in + (row0 + r) * P + 2 * j, true);
-  }
+  constexpr int P = (int)half_pitch(N);  // 16-byte pieces per row pair
+  const float2* src = in + hrow_q(q0, P);
+  for_pairs<TWX / 2, P>([&](int pr, int p0, int p1) {
+    int k = (p0 >> 3) * 8 + 2 * (p0 & 3);
+    float2* d = st + (2 * pr + ((p0 >> 2) & 1)) * C::CW + k;
+    const float2* g = src + (int64_t)pr * 2 * P + 2 * p0;
+    for (int p = p0; p < p1; p += 32, k += 32, d += 32, g += 64)
+      if (k < C::M + 2) cp_async16(d, g, true);
+  });
 }
 
-// real rows of N floats: row r at floats [2 CW r, 2 CW r + N), i.e. the M
-// complex values z[j] = x[2j] + i x[2j+1] at st[r * CW + j]
+// real rows of N floats: row r at floats [pitch r, pitch r + N), i.e. the M
+// complex values z[j] = x[2j] + i x[2j+1] at st[r * CW + j] when pitch = 2 CW
 template <int N, int TWX>
-__device__ __forceinline__ void stage_real_rows(float* st, const float* __restrict__ in, int64_t row0,
+__device__ __forceinline__ void stage_real_rows(float* st, const float* __restrict__ in, int64_t q0,
                                                 int pitch_floats) {
-  constexpr int CH = N / 4;
-  for (int e = threadIdx.x; e < TWX * CH; e += NT) {
-    const int r = e / CH, j = e - r * CH;
-    cp_async16(st + r * pitch_floats + 4 * j, in + (row0 + r) * N + 4 * j, true);
+  constexpr int CH = N / 4;           // 16-byte pieces per row
+  constexpr int HALF = TWX / 2 * CH;  // pieces per block of one parity
+  static_assert(HALF % NT == 0, "a parity block is whole iterations");
+  const float* src0 = in + real_row_q(q0, N) * N;
+  const float* src1 = in + real_row_q(q0 + 1, N) * N;
+#pragma unroll
+  for (int i = 0; i < 2 * HALF / NT; ++i) {
+    const int h = i * NT / HALF;  // constant per iteration
+    const int e2 = threadIdx.x + i * NT - h * HALF;
+    cp_async16(st + (2 * (e2 / CH) + h) * pitch_floats + 4 * (e2 % CH), (h ? src1 : src0) + 4 * e2, true);
   }
 }
 
-// r2c post-processing: X[k] = (Z[k] + conj Z[M-k])/2 - i/2 w^k (Z[k] - conj Z[M-k]).
+// r2c post-processing: X[k] = (Z[k] + conj Z[M-k])/2 - i/2 w^k (Z[k] - conj Z[M-k]),
+// written in memory order; position w of a row pair is row (w >> 3) & 1,
+// column k = (w >> 4) 8 + (w & 7); w + 32 is the same row, k + 16.  Padding
+// columns k > M are not written.
 template <int N, int TWX>
 __device__ __forceinline__ void row_r2c_store(const float2* buf, const float2* tw,
-                                              float2* __restrict__ out, int64_t row0, int64_t P) {
+                                              float2* __restrict__ out, int64_t q0) {
   using C = RowCfg<N, TWX>;
   constexpr int M = N / 2;
+  constexpr int P = (int)half_pitch(N);
+  float2* dst = out + hrow_q(q0, P);
+  for_pairs<TWX / 2, 2 * P>([&](int pr, int w0, int w1) {
+    int k = (w0 >> 4) * 8 + (w0 & 7);
+    const float2* z = buf + (2 * pr + ((w0 >> 3) & 1)) * C::CW;
+    float2* o = dst + (int64_t)pr * 2 * P + w0;
 #pragma unroll 2
-  for (int e = threadIdx.x; e < TWX * (M + 1); e += NT) {
-    const int r = e / (M + 1), k = e - r * (M + 1);
-    const float2* z = buf + r * C::CW;
-    const float2 a = z[k & (M - 1)];
-    const float2 b = cconj(z[(M - k) & (M - 1)]);
-    const float2 E = cscale(cadd(a, b), 0.5f);
-    const float2 D = csub(a, b);
-    const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);  // (-i/2) D
-    out[(row0 + r) * P + k] = cadd(E, cmul(tw[k], O));
-  }
+    for (int w = w0; w < w1; w += 32, k += 16, o += 32) {
+      if (k > M) continue;
+      const float2 a = z[k & (M - 1)];
+      const float2 b = cconj(z[(M - k) & (M - 1)]);
+      const float2 E = cscale(cadd(a, b), 0.5f);
+      const float2 D = csub(a, b);
+      const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);  // (-i/2) D
+      *o = cadd(E, cmul(tw[k], O));
+    }
+  });
 }
 
 // The c2r input convention on a staged spectrum value X[k] (k = 0..M): the
@@ -647,7 +725,8 @@ struct ScaleOffset {
   }
 };
 
-// Row tile t of a multi-simulation launch: simulation t / tps, first row (t mod tps) TWX.
+// Row tile t of a multi-simulation launch: simulation t / tps, first row (t mod tps) TWX
+// in the pair-major row order q of the half-spectrum layout (TWX even).
 struct RowTile {
   int64_t row0, by;
 };
@@ -659,7 +738,7 @@ __device__ __forceinline__ RowTile row_tile(int64_t t, int64_t tps, const Multi&
 
 template <int N, int TWX>
 __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xr2c(const float* __restrict__ in, float2* __restrict__ out,
-                                                int64_t P, float scale, float offset,
+                                                float scale, float offset,
                                                 const float2* __restrict__ twg, int64_t ntiles,
                                                 int64_t tps, Multi m) {
   using C = RowCfg<N, TWX>;
@@ -688,7 +767,7 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xr2c(const float* 
     float2* buf = cur ? st1 : st0;
     fft_rowtile<M, TWX, C::CW, NT, false, 2>(buf, tw, ScaleOffset{scale, offset});
     const RowTile r = row_tile<TWX>(t, tps, m);
-    row_r2c_store<N, TWX>(buf, tw, moved(out, r.by), r.row0, P);
+    row_r2c_store<N, TWX>(buf, tw, moved(out, r.by), r.row0);
     __syncthreads();
     cur ^= 1;
   }
@@ -717,7 +796,7 @@ __device__ __forceinline__ JobTile job_tile(int64_t t, int64_t tpj, int njobs, i
 }
 
 template <int N, int TWX>
-__global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_constant__ RowJobs jobs, int64_t P,
+__global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_constant__ RowJobs jobs,
                                                 const float2* __restrict__ twg, int64_t tiles_per_job,
                                                 Multi m) {
   using C = RowCfg<N, TWX>;
@@ -731,7 +810,7 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
   int64_t t = blockIdx.x;
   if (t < ntiles) {
     const JobTile j = job_tile(t, tiles_per_job, jobs.njobs, TWX, m);
-    stage_complex_rows<N, TWX>(st0, moved(static_cast<const float2*>(jobs.in[j.job]), j.by), j.row0, P);
+    stage_complex_rows<N, TWX>(st0, moved(static_cast<const float2*>(jobs.in[j.job]), j.by), j.row0);
   }
   cp_async_commit();
   int cur = 0;
@@ -741,7 +820,7 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
     if (tn < ntiles) {
       const JobTile jn = job_tile(tn, tiles_per_job, jobs.njobs, TWX, m);
       stage_complex_rows<N, TWX>(cur ? st0 : st1, moved(static_cast<const float2*>(jobs.in[jn.job]), jn.by),
-                                 jn.row0, P);
+                                 jn.row0);
     }
     cp_async_commit();
     cp_async_wait<1>();
@@ -749,10 +828,17 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
     float2* buf = cur ? st1 : st0;
     row_c2r_combine<N, TWX>(buf, tw, jobs.kfs[j.job]);
     fft_rowtile<M, TWX, C::CW, NT, true, 2>(buf, tw);
+    // even tile rows to one block of consecutive real rows, odd ones to another
     float* out = moved(static_cast<float*>(jobs.out[j.job]), j.by);
-    for (int e = threadIdx.x; e < TWX * M; e += NT) {
-      const int r = e / M, q = e % M;
-      reinterpret_cast<float2*>(out + (j.row0 + r) * N)[q] = buf[r * C::CW + q];
+    float2* o0 = reinterpret_cast<float2*>(out + real_row_q(j.row0, N) * N);
+    float2* o1 = reinterpret_cast<float2*>(out + real_row_q(j.row0 + 1, N) * N);
+    constexpr int HALF = TWX / 2 * M;
+    static_assert(HALF % NT == 0, "a parity block is whole iterations");
+#pragma unroll
+    for (int i = 0; i < 2 * HALF / NT; ++i) {
+      const int h = i * NT / HALF;  // constant per iteration
+      const int e2 = threadIdx.x + i * NT - h * HALF;
+      (h ? o1 : o0)[e2] = buf[(2 * (e2 / M) + h) * C::CW + e2 % M];
     }
     __syncthreads();
     cur ^= 1;
@@ -782,7 +868,7 @@ constexpr size_t xscreen_smem() {
 template <int N, int TWX, int MODEL>
 __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w_in,
                                                     const float* __restrict__ rho,
-                                                    float2* __restrict__ s_out, int64_t P,
+                                                    float2* __restrict__ s_out,
                                                     ForceParams fp0, const float2* __restrict__ twg,
                                                     int64_t ntiles, int64_t tps, Multi m) {
   if (!m.shift) resolve(fp0, 0);  // one simulation: once per launch
@@ -797,7 +883,7 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
   int64_t t = blockIdx.x;
   if (t < ntiles) {
     const RowTile r = row_tile<TWX>(t, tps, m);
-    stage_complex_rows<N, TWX>(st0, moved(w_in, r.by), r.row0, P);
+    stage_complex_rows<N, TWX>(st0, moved(w_in, r.by), r.row0);
   }
   cp_async_commit();
   int cur = 0;
@@ -816,7 +902,7 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
     cp_async_commit();
     if (tn < ntiles) {
       const RowTile rn = row_tile<TWX>(tn, tps, m);
-      stage_complex_rows<N, TWX>(cur ? st0 : st1, moved(w_in, rn.by), rn.row0, P);
+      stage_complex_rows<N, TWX>(cur ? st0 : st1, moved(w_in, rn.by), rn.row0);
     }
     cp_async_commit();
     row_c2r_combine<N, TWX>(buf, tw, 0.f);
@@ -833,7 +919,7 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
     }
     __syncthreads();
     fft_rowtile_call<M, TWX, C::CW, NT, false, 2>(buf, tw);
-    row_r2c_store<N, TWX>(buf, tw, moved(s_out, r.by), row0, P);
+    row_r2c_store<N, TWX>(buf, tw, moved(s_out, r.by), row0);
     __syncthreads();
     cur ^= 1;
   }
@@ -852,15 +938,16 @@ constexpr size_t row_smem() {
   return RowCfg<N, row_tw(N)>::smem;
 }
 
+// Along y: o = z, n = y.  Along z: o = y, n = z (rows of a plane pair 8 elements apart).
 template <int N, int TW>
 ColGeo<N, TW> geo_y(Multi m) {
   const int64_t P = half_pitch(N);
-  return ColGeo<N, TW>{(int64_t)N * P, P, m};
+  return ColGeo<N, TW>{2 * N * P, 8, 4 * P, 2 * P, 1, m};
 }
 template <int N, int TW>
 ColGeo<N, TW> geo_z(Multi m) {
   const int64_t P = half_pitch(N);
-  return ColGeo<N, TW>{P, (int64_t)N * P, m};
+  return ColGeo<N, TW>{4 * P, 2 * P, 2 * N * P, 8, 0, m};
 }
 template <int N, int TW>
 constexpr int64_t col_tiles() {
@@ -893,7 +980,7 @@ static cudaError_t launch_xr2c(const float* in, float2* out, float scale, float 
   unsigned grid;
   cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, sm, s>>>(in, out, half_pitch(N), scale, offset, tw, ntiles, tps, m);
+  k<<<grid, NT, sm, s>>>(in, out, scale, offset, tw, ntiles, tps, m);
   return cudaGetLastError();
 }
 
@@ -920,7 +1007,7 @@ static cudaError_t launch_xc2r_multi(int njobs, const float2* const* in, float* 
   unsigned grid;
   cudaError_t e = prep(k, sm, tpj * njobs * m.nb, grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, sm, s>>>(jobs, half_pitch(N), tw, tpj, m);
+  k<<<grid, NT, sm, s>>>(jobs, tw, tpj, m);
   return cudaGetLastError();
 }
 
@@ -1042,12 +1129,12 @@ static cudaError_t launch_xscreen(const float2* w_in, const float* rho, float2* 
     auto k = k_x_screen<N, TWX, 1>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, half_pitch(N), fp, tw, ntiles, tps, m);
+    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, fp, tw, ntiles, tps, m);
   } else {
     auto k = k_x_screen<N, TWX, 2>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, half_pitch(N), fp, tw, ntiles, tps, m);
+    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, fp, tw, ntiles, tps, m);
   }
   return cudaGetLastError();
 }

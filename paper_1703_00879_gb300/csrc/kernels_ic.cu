@@ -59,11 +59,14 @@ struct Mode {
   bool nyx, nyy, nyz;
 };
 
+// Mode of element m of a half spectrum (layout of cola_internal.h); padding
+// elements (kx > N/2) are not valid.
 __device__ __forceinline__ Mode mode_of(int64_t m, int N, int64_t P, bool& valid) {
   Mode md;
-  const int ix = (int)(m % P);
-  const int64_t rest = m / P;
-  const int iy = (int)(rest % N), iz = (int)(rest / N);
+  const int64_t pr = m / (2 * P);            // (z >> 1) N + y
+  const int w = (int)(m - pr * 2 * P);       // position in the interleaved row pair
+  const int ix = (w >> 4) * 8 + (w & 7);
+  const int iy = (int)(pr % N), iz = (int)(pr / N) * 2 + ((w >> 3) & 1);
   valid = ix <= N / 2;
   md.ix = ix;
   md.fy = iy < N / 2 ? iy : iy - N;
@@ -188,9 +191,10 @@ __global__ void k_half_pack(int N, int64_t P, const float2* __restrict__ dense,
   const int64_t W = N / 2 + 1;
   const int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x;
   if (m >= (int64_t)N * N * W) return;
-  const int64_t row = m / W, k = m % W;
-  if (to_padded) padded[row * P + k] = dense[m];
-  else const_cast<float2*>(dense)[m] = padded[row * P + k];
+  const int64_t row = m / W;  // z N + y of the dense [z][y][kx] array
+  const int64_t at = hidx((int)(row / N), (int)(row % N), (int)(m % W), N, P);
+  if (to_padded) padded[at] = dense[m];
+  else const_cast<float2*>(dense)[m] = padded[at];
 }
 
 __global__ void k_absmax(int64_t n, int N, int64_t P, const float2* __restrict__ src,
@@ -201,7 +205,8 @@ __global__ void k_absmax(int64_t n, int N, int64_t P, const float2* __restrict__
   float mx = 0.f;
   for (int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x; m < n;
        m += (int64_t)gridDim.x * NTI) {
-    if ((int)(m % P) > N / 2) continue;
+    const int w = (int)(m % (2 * P));
+    if ((w >> 4) * 8 + (w & 7) > N / 2) continue;  // padding (kx > N/2)
     const float2 v = src[m];
     mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
   }

@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, i
       }
     }
     const double w = wf;
-    const float2 v = dk[(int64_t)iz * N * P + (int64_t)iy * P + ix];
+    const float2 v = dk[hidx(iz, iy, ix, N, P)];
     const double p2 = ((double)v.x * v.x + (double)v.y * v.y) * norm / (w * w);
     const double wt = (ix == 0 || ix == N / 2) ? 1.0 : 2.0;
     atomicAdd(&sh[b], wt);
