@@ -378,7 +378,7 @@ struct OpZScreenField {
       const float k2 = kk2(c0 + c, iy, n, N, fp.kf);
       float m = 0.f;
       if (k2 > 0.f) {
-        if (MODEL == 1) m = -fp.kappa_norm / k2;
+        if (MODEL == 1) m = __fdividef(-fp.kappa_norm, k2);
         else m = __expf(-k2 * fp.R2half) * fp.norm;
       }
       buf[n * TW + c] = cscale(v, m);
@@ -444,8 +444,8 @@ struct OpZForce {
       const float k2 = kk2(c0 + c, iy, n, N, fp.kf);
       float2 phi = make_float2(0.f, 0.f);
       if (k2 > 0.f) {
-        const float yuk = k2 / (k2 + fp.a2m2);
-        const float g = -fp.kappa_norm / k2;
+        const float yuk = __fdividef(k2, k2 + fp.a2m2);
+        const float g = __fdividef(-fp.kappa_norm, k2);
         const float2 src = buf[n * TW + c];
         if (SCREENED) {
           phi = cscale(cadd(ph[n * TW + c], cscale(src, fp.C * yuk)), g);
@@ -846,14 +846,17 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
   cp_async_wait<0>();
 }
 
+// Screening factor eps(w) (Sec. 6.1, Sec. 6.2).  The divisions and the square
+// root use the fast intrinsics (a few ulp), well below the FP32 rounding of
+// the transforms the factor feeds.
 template <int MODEL>
 __device__ __forceinline__ float screen_eps(float w, const ForceParams& fp) {
   if (MODEL == 1) {
     const float aw = fabsf(w);
-    return aw > fp.fr_thr ? fp.fr_thr / aw : 1.f;
+    return aw > fp.fr_thr ? __fdividef(fp.fr_thr, aw) : 1.f;
   } else {
-    const float x = fp.dgp_coef * fmaxf(1.f + w, 0.f);
-    return 2.f / (sqrtf(1.f + x) + 1.f);
+    const float u = 1.f + fp.dgp_coef * fmaxf(1.f + w, 0.f);  // >= 1
+    return __fdividef(2.f, u * rsqrtf(u) + 1.f);
   }
 }
 

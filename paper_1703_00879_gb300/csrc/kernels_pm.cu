@@ -32,7 +32,9 @@ __device__ __forceinline__ Cic cic_setup(const PartParams& pp, int ix, int iy, i
   for (int d = 0; d < 3; ++d) {
     const int num = li[d] * pp.Nm;  // q in cells = num / Np
     const int base = num >> pp.lgNp;
-    const float qf = (float)(num - (base << pp.lgNp)) / (float)pp.Np;
+    // (num mod Np) / Np, exact: the division by Np = 2^lgNp is a multiplication
+    // by the float with exponent field 127 - lgNp (lgNp <= 12)
+    const float qf = (float)(num - (base << pp.lgNp)) * __int_as_float((127 - pp.lgNp) << 23);
     const float u = qf + sv[d] * pp.cellscale;
     const float fl = floorf(u);
     c.f[d] = u - fl;
