@@ -510,7 +510,7 @@ int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}) {
   CK(fft_col(N, ctx->lc[1], 1, true, ctx->tw_np, st, m));
   CK(fft_yinv2(N, ctx->lc[2], ctx->lc[2], ctx->lc[5], kf, ctx->tw_np, st, m));
   CK(fft_col(N, ctx->lc[3], 1, true, ctx->tw_np, st, m));
-  prof_end(ctx, ST_LPT_Y, e, 2 + 2 * yinv2_launches(N), m.nb * 10.0 * H);
+  prof_end(ctx, ST_LPT_Y, e, 4, m.nb * 10.0 * H);
   e = prof_begin(ctx);
   {
     const float2* in6[6] = {ctx->lc[0], ctx->lc[4], ctx->lc[1], ctx->lc[2], ctx->lc[5], ctx->lc[3]};
@@ -609,7 +609,7 @@ int force_group(const Group& g, double a, bool device_params, bool ini = false) 
   e = prof_begin(ctx);
   CK(fft_yinv2(N, ctx->Cphi, ctx->Cphi, ctx->Cw, -fp.kf, tw, st, all));
   CK(fft_col(N, ctx->Cphz, 1, true, tw, st, all));
-  prof_end(ctx, ST_MESH_YINV, e, 1 + yinv2_launches(N), all.nb * 5.0 * H);
+  prof_end(ctx, ST_MESH_YINV, e, 2, all.nb * 5.0 * H);
   e = prof_begin(ctx);
   {
     const float2* in3[3] = {ctx->Cphi, ctx->Cw, ctx->Cphz};

@@ -154,9 +154,6 @@ cudaError_t fft_col(int N, float2* data, int axis, bool inv, const float2* tw, c
 // transform of (i kfs f_y) times the input (out_deriv).
 cudaError_t fft_yinv2(int N, const float2* in, float2* out_plain, float2* out_deriv, float kfs,
                       const float2* tw, cudaStream_t s, Multi m = {});
-// kernel launches fft_yinv2 makes: one two-array pass, or (N >= 512, where a
-// two-array tile would have 32-byte rows) two single-array passes
-inline int yinv2_launches(int N) { return N >= 512 ? 2 : 1; }
 // Screening field: forward z of delta (after x, y) -> delta(k) stored in dk_out;
 // Phi_N(k) (f(R)) or W(kR) delta(k) (nDGP) -> inverse z -> w_out.
 cudaError_t mesh_z_screen_field(int N, const float2* in, float2* dk_out, float2* w_out,

@@ -347,6 +347,68 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 2), N)) k_yi
   col_pipeline<N, fft_rows<N>() * 2 * TW>(op, twg, ntiles);
 }
 
+// y inverse with the y derivative as a second output, for long columns (512
+// and 1024 points) where a two-array tile would need 32-byte rows: three tile
+// buffers of TW columns rotate between the input (transformed in place for the
+// plain output), the derivative and the prefetch of the next input, so the
+// input is read from HBM once with TW-column (64-byte) rows.  Given input
+// buffer I, the derivative goes to (I + 1) mod 3 and the prefetch to (I + 2)
+// mod 3, which holds the next tile's input.
+template <int N, int TW>
+constexpr size_t yinv2r_smem() {
+  return (N + 3 * (size_t)fft_rows<N>() * TW) * sizeof(float2);
+}
+
+template <int N, int TW>
+__global__ void __launch_bounds__(NT, blocks_for_smem(yinv2r_smem<N, TW>(), N)) k_yinv2r(
+    ColGeo<N, TW> geo, const float2* __restrict__ in, float2* __restrict__ outp,
+    float2* __restrict__ outd, float kfs, const float2* __restrict__ twg, int64_t ntiles) {
+  constexpr int B = fft_rows<N>() * TW;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw = sm;
+  load_tw(tw, twg, N);
+  int64_t t = blockIdx.x;
+  if (t < ntiles) {
+    int o, c0;
+    int64_t base, by;
+    geo.tile(t, o, c0, base, by);
+    col_issue<N, TW, TW>(sm + N, 0, moved(in, by), base, geo.ra, geo.rb, c0);
+  }
+  cp_async_commit();
+  int I = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const int D = I == 2 ? 0 : I + 1, F = I == 0 ? 2 : I - 1;
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) {
+      int o, c0;
+      int64_t base, by;
+      geo.tile(tn, o, c0, base, by);
+      col_issue<N, TW, TW>(sm + N + F * B, 0, moved(in, by), base, geo.ra, geo.rb, c0);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();  // tile t's input has landed
+    __syncthreads();
+    float2* bi = sm + N + I * B;
+    float2* bd = sm + N + D * B;
+    int o, c0;
+    int64_t base, by;
+    geo.tile(t, o, c0, base, by);
+    for (int e = threadIdx.x; e < N * TW; e += NT) {
+      const int n = e / TW;
+      const float f = (n == N / 2) ? 0.f : kfs * (float)freq_index(n, N);
+      bd[e] = cscale(cmul_i(bi[e]), f);
+    }
+    __syncthreads();
+    fft_tile_call<N, TW, TW, NT, true>(bi, tw);
+    col_store<N, TW, TW>(bi, 0, moved(outp, by), base, geo.ra, geo.rb, c0);
+    fft_tile_call<N, TW, TW, NT, true>(bd, tw);
+    col_store<N, TW, TW>(bd, 0, moved(outd, by), base, geo.ra, geo.rb, c0);
+    __syncthreads();  // both buffers are free for later prefetches
+    I = F;
+  }
+  cp_async_wait<0>();
+}
+
 // ---------------------------------------------------------------- screening field (z pass)
 template <int N, int TW, int MODEL>
 struct OpZScreenField {
@@ -1058,20 +1120,15 @@ template <int N>
 static cudaError_t launch_yinv2(const float2* in, float2* outp, float2* outd, float kfs,
                                 const float2* tw, cudaStream_t s, Multi m) {
   if constexpr (N >= 512) {
-    // two single-array passes with 64-byte tile rows (the two-array tile would
-    // need 32-byte rows at this size): the derivative out of place first, then
-    // the plain transform (in place when outp aliases in)
+    // one pass with three rotating single-array tile buffers (k_yinv2r)
     constexpr int TW = col_tw(N, 1);
-    constexpr size_t sm = col_smem<N, 1>();
+    constexpr size_t sm = yinv2r_smem<N, TW>();
     const int64_t ntiles = col_tiles<N, TW>() * m.nb;
-    auto k = k_col<N, TW, true>;
+    auto k = k_yinv2r<N, TW>;
     unsigned grid;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(OpCol<N, TW, true>{geo_y<N, TW>(m), in, outd, kfs}, tw, ntiles);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(OpCol<N, TW, true>{geo_y<N, TW>(m), in, outp, 0.f}, tw, ntiles);
+    k<<<grid, NT, sm, s>>>(geo_y<N, TW>(m), in, outp, outd, kfs, tw, ntiles);
     return cudaGetLastError();
   } else {
     constexpr int TW = col_tw(N, 2);
