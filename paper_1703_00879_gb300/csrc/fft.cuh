@@ -140,6 +140,25 @@ __device__ __forceinline__ void dftR(float2* v) {
   }
 }
 
+// 32-point DFT shared by a thread pair (lanes l and l ^ 16 of a full warp):
+// the thread with half = 0 holds x[0..15] in v, its partner x[16..31].  One
+// radix-2 decimation-in-frequency step exchanges the halves by shuffle (half 0
+// forms a[n] = x[n] + x[n + 16], half 1 b[n] = (x[n] - x[n + 16]) w32^n), then
+// each runs a 16-point DFT: half h ends with X[2k + h] at v[pos_of<16>(k)].
+template <bool INV>
+__device__ __forceinline__ void dft32_pair(float2 (&v)[16], int half) {
+  const float sg = half ? -1.f : 1.f;
+#pragma unroll
+  for (int n = 0; n < 16; ++n) {
+    const float ox = __shfl_xor_sync(0xffffffffu, v[n].x, 16);
+    const float oy = __shfl_xor_sync(0xffffffffu, v[n].y, 16);
+    const float2 t = make_float2(fmaf(sg, v[n].x, ox), fmaf(sg, v[n].y, oy));
+    const float2 tw = w32mul<INV>(t, n);
+    v[n] = half ? tw : t;
+  }
+  dftR<16, INV>(v);
+}
+
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 
 // L = R1 R2 with R1 <= R2 <= 32.
@@ -253,8 +272,10 @@ struct NoPre {
 // step 1 (thread = (c, n2)): DFT_R1 over x[R2 n1 + n2] (each value passed
 // through pre() as it is loaded), times w_L^(n2 k1), intermediate at
 // n2 (R1 + 1) + k1; step 2 (thread = (c, k1)): DFT_R2 gives X[k1 + R1 k2].
+// PAIR32: for L = 16 x 32 with half as many step-2 items as threads, step 2
+// runs on thread pairs (dft32_pair), halving its registers per thread.
 // The caller synchronises before the call; returns after a barrier.
-template <int L, int TW, int CW, int NT, bool INV, int TWS = 1, class Pre = NoPre>
+template <int L, int TW, int CW, int NT, bool INV, int TWS = 1, class Pre = NoPre, bool PAIR32 = false>
 __device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const float2* __restrict__ tw,
                                             Pre pre = Pre()) {
   constexpr int R1 = Split<L>::R1, R2 = Split<L>::R2;
@@ -296,7 +317,21 @@ __device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const floa
     }
   }
   __syncthreads();
-  {
+  if constexpr (PAIR32 && R1 == 16 && R2 == 32 && 2 * U2 == NT) {
+    // step 2 on thread pairs (dft32_pair): U2 items would leave half the threads
+    // idle; half the registers per thread
+    const int half = (tid >> 4) & 1, u = (tid >> 5) * 16 + (tid & 15);
+    const int c = u / R1, k1 = u % R1;
+    float2 y[16];
+    const float2* yr = buf + c * CW + k1 + 16 * half * (R1 + 1);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) y[j] = yr[j * (R1 + 1)];
+    dft32_pair<INV>(y, half);
+    __syncthreads();
+    float2* X = buf + c * CW + k1 + R1 * half;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) X[2 * R1 * k] = y[pos_of<16>(k)];
+  } else {
     float2 y[P2][R2];
 #pragma unroll
     for (int i = 0; i < P2; ++i) {
@@ -324,9 +359,9 @@ __device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const floa
   __syncthreads();
 }
 
-template <int L, int TW, int CW, int NT, bool INV, int TWS = 1, class Pre = NoPre>
+template <int L, int TW, int CW, int NT, bool INV, int TWS = 1, class Pre = NoPre, bool PAIR32 = false>
 __device__ __noinline__ void fft_rowtile_call(float2* buf, const float2* tw, Pre pre = Pre()) {
-  fft_rowtile<L, TW, CW, NT, INV, TWS, Pre>(buf, tw, pre);
+  fft_rowtile<L, TW, CW, NT, INV, TWS, Pre, PAIR32>(buf, tw, pre);
 }
 
 // Out-of-line copy for kernels that run several transforms per tile: each

@@ -971,7 +971,7 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
     }
     cp_async_commit();
     row_c2r_combine<N, TWX>(buf, tw, 0.f);
-    fft_rowtile_call<M, TWX, C::CW, NT, true, 2>(buf, tw);
+    fft_rowtile_call<M, TWX, C::CW, NT, true, 2, NoPre, true>(buf, tw);
     cp_async_wait<1>();  // the density rows; the next tile's prefetch may still be in flight
     __syncthreads();
     const float2* rv2 = reinterpret_cast<const float2*>(rr);  // row r holds N floats = M float2
@@ -983,7 +983,7 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
       buf[r2 * C::CW + j] = make_float2(d0 * screen_eps<MODEL>(w.x, fp), d1 * screen_eps<MODEL>(w.y, fp));
     }
     __syncthreads();
-    fft_rowtile_call<M, TWX, C::CW, NT, false, 2>(buf, tw);
+    fft_rowtile_call<M, TWX, C::CW, NT, false, 2, NoPre, true>(buf, tw);
     row_r2c_store<N, TWX>(buf, tw, moved(s_out, r.by), row0);
     __syncthreads();
     cur ^= 1;
