@@ -111,6 +111,7 @@ cudaError_t resident_ctas(K kernel, size_t smem, int& per_sm) {
 // calling thread's grid cap (used when many small simulations run concurrently).
 template <class K>
 cudaError_t prep(K kernel, size_t smem, int64_t ntiles, unsigned& grid) {
+  if (ntiles >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;  // tile indices are 32-bit
   int per_sm = 0;
   cudaError_t e = resident_ctas(kernel, smem, per_sm);
   if (e != cudaSuccess) return e;
@@ -218,17 +219,20 @@ struct ColGeo {
   int64_t oa, ob, ra, rb;
   int pair_tiles;
   Multi m;
-  __device__ __forceinline__ void tile(int64_t t, int& o, int& c0, int64_t& base, int64_t& by) const {
-    const int b = (int)(t / tps);
-    t -= (int64_t)b * tps;
-    by = shift_of(m, b);
+  // t < 2^31 (prep checks the tile count); divisions by compile-time constants
+  __device__ __forceinline__ void tile(int64_t t64, int& o, int& c0, int64_t& base, int64_t& by) const {
+    uint32_t t = (uint32_t)t64;
+    const uint32_t b = t / (uint32_t)tps;
+    t -= b * (uint32_t)tps;
+    by = shift_of(m, (int)b);
     if (pair_tiles) {
-      const int r = (int)(t % (2 * ntx));
-      o = (int)(t / (2 * ntx)) * 2 + (r & 1);
-      c0 = (r >> 1) * TW;
+      const uint32_t q = t / (2 * ntx), r = t - q * (2 * ntx);
+      o = (int)(q * 2 + (r & 1));
+      c0 = (int)(r >> 1) * TW;
     } else {
-      o = (int)(t / ntx);
-      c0 = (int)(t % ntx) * TW;
+      const uint32_t q = t / ntx;
+      o = (int)q;
+      c0 = (int)(t - q * ntx) * TW;
     }
     base = (o >> 1) * oa + (o & 1) * ob + hcol(c0);
   }
@@ -792,17 +796,18 @@ struct ScaleOffset {
 struct RowTile {
   int64_t row0, by;
 };
-template <int TWX>
-__device__ __forceinline__ RowTile row_tile(int64_t t, int64_t tps, const Multi& m) {
-  const int b = (int)(t / tps);
-  return RowTile{(t - (int64_t)b * tps) * TWX, shift_of(m, b)};
+template <int N, int TWX>
+__device__ __forceinline__ RowTile row_tile(int64_t t64, const Multi& m) {
+  constexpr uint32_t TPS = (uint32_t)N * N / TWX;  // tiles per simulation
+  const uint32_t t = (uint32_t)t64, b = t / TPS;     // t < 2^31 (checked by prep)
+  return RowTile{(int64_t)(t - b * TPS) * TWX, shift_of(m, (int)b)};
 }
 
 template <int N, int TWX>
 __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xr2c(const float* __restrict__ in, float2* __restrict__ out,
                                                 float scale, float offset,
                                                 const float2* __restrict__ twg, int64_t ntiles,
-                                                int64_t tps, Multi m) {
+                                                Multi m) {
   using C = RowCfg<N, TWX>;
   constexpr int M = N / 2;
   extern __shared__ __align__(16) float2 sm[];
@@ -812,7 +817,7 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xr2c(const float* 
   load_tw(tw, twg, N);
   int64_t t = blockIdx.x;
   if (t < ntiles) {
-    const RowTile r = row_tile<TWX>(t, tps, m);
+    const RowTile r = row_tile<N, TWX>(t, m);
     stage_real_rows<N, TWX>(reinterpret_cast<float*>(st0), moved(in, r.by), r.row0, 2 * C::CW);
   }
   cp_async_commit();
@@ -820,7 +825,7 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xr2c(const float* 
   for (; t < ntiles; t += gridDim.x) {
     const int64_t tn = t + gridDim.x;
     if (tn < ntiles) {
-      const RowTile r = row_tile<TWX>(tn, tps, m);
+      const RowTile r = row_tile<N, TWX>(tn, m);
       stage_real_rows<N, TWX>(reinterpret_cast<float*>(cur ? st0 : st1), moved(in, r.by), r.row0, 2 * C::CW);
     }
     cp_async_commit();
@@ -828,7 +833,7 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xr2c(const float* 
     __syncthreads();
     float2* buf = cur ? st1 : st0;
     fft_rowtile<M, TWX, C::CW, NT, false, 2>(buf, tw, ScaleOffset{scale, offset});
-    const RowTile r = row_tile<TWX>(t, tps, m);
+    const RowTile r = row_tile<N, TWX>(t, m);
     row_r2c_store<N, TWX>(buf, tw, moved(out, r.by), r.row0);
     __syncthreads();
     cur ^= 1;
@@ -842,19 +847,34 @@ struct RowJobs {
   void* out[6];
   float kfs[6];
   int njobs;
+  uint32_t jmul, jshift;  // q / njobs = (umulhi(q, jmul) + q) >> jshift for q < 2^31
 };
+
+// Division by an invariant integer d >= 1 through a multiply-high (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", PLDI 1994):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, q = (umulhi(n, m) + n) >> l,
+// exact for every n < 2^31.
+inline void fast_div_magic(uint32_t d, uint32_t& mul, uint32_t& shift) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  mul = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+  shift = l;
+}
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, uint32_t mul, uint32_t shift) {
+  return (__umulhi(n, mul) + n) >> shift;
+}
 
 // Tile t of a multi-job, multi-simulation c2r launch: simulation, job, first row.
 struct JobTile {
   int job;
   int64_t row0, by;
 };
-__device__ __forceinline__ JobTile job_tile(int64_t t, int64_t tpj, int njobs, int twx,
-                                            const Multi& m) {
-  const int64_t per_sim = tpj * njobs;
-  const int b = (int)(t / per_sim);
-  t -= (int64_t)b * per_sim;
-  return JobTile{(int)(t / tpj), (t % tpj) * twx, shift_of(m, b)};
+template <int N, int TWX>
+__device__ __forceinline__ JobTile job_tile(int64_t t64, const RowJobs& jobs, const Multi& m) {
+  constexpr uint32_t TPJ = (uint32_t)N * N / TWX;  // tiles per job
+  const uint32_t t = (uint32_t)t64, q = t / TPJ;     // q = simulation * njobs + job
+  const uint32_t b = fast_div(q, jobs.jmul, jobs.jshift);
+  return JobTile{(int)(q - b * (uint32_t)jobs.njobs), (int64_t)(t - q * TPJ) * TWX, shift_of(m, (int)b)};
 }
 
 template <int N, int TWX>
@@ -871,16 +891,16 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
   const int64_t ntiles = tiles_per_job * jobs.njobs * m.nb;
   int64_t t = blockIdx.x;
   if (t < ntiles) {
-    const JobTile j = job_tile(t, tiles_per_job, jobs.njobs, TWX, m);
+    const JobTile j = job_tile<N, TWX>(t, jobs, m);
     stage_complex_rows<N, TWX>(st0, moved(static_cast<const float2*>(jobs.in[j.job]), j.by), j.row0);
   }
   cp_async_commit();
   int cur = 0;
   for (; t < ntiles; t += gridDim.x) {
-    const JobTile j = job_tile(t, tiles_per_job, jobs.njobs, TWX, m);
+    const JobTile j = job_tile<N, TWX>(t, jobs, m);
     const int64_t tn = t + gridDim.x;
     if (tn < ntiles) {
-      const JobTile jn = job_tile(tn, tiles_per_job, jobs.njobs, TWX, m);
+      const JobTile jn = job_tile<N, TWX>(tn, jobs, m);
       stage_complex_rows<N, TWX>(cur ? st0 : st1, moved(static_cast<const float2*>(jobs.in[jn.job]), jn.by),
                                  jn.row0);
     }
@@ -935,7 +955,7 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
                                                     const float* __restrict__ rho,
                                                     float2* __restrict__ s_out,
                                                     ForceParams fp0, const float2* __restrict__ twg,
-                                                    int64_t ntiles, int64_t tps, Multi m) {
+                                                    int64_t ntiles, Multi m) {
   if (!m.shift) resolve(fp0, 0);  // one simulation: once per launch
   using C = RowCfg<N, TWX>;
   constexpr int M = N / 2;
@@ -947,13 +967,13 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
   load_tw(tw, twg, N);
   int64_t t = blockIdx.x;
   if (t < ntiles) {
-    const RowTile r = row_tile<TWX>(t, tps, m);
+    const RowTile r = row_tile<N, TWX>(t, m);
     stage_complex_rows<N, TWX>(st0, moved(w_in, r.by), r.row0);
   }
   cp_async_commit();
   int cur = 0;
   for (; t < ntiles; t += gridDim.x) {
-    const RowTile r = row_tile<TWX>(t, tps, m);
+    const RowTile r = row_tile<N, TWX>(t, m);
     const int64_t row0 = r.row0;
     ForceParams fp = fp0;
     resolve(fp, r.by);
@@ -966,7 +986,7 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
     stage_real_rows<N, TWX>(rr, moved(rho, r.by), row0, N);
     cp_async_commit();
     if (tn < ntiles) {
-      const RowTile rn = row_tile<TWX>(tn, tps, m);
+      const RowTile rn = row_tile<N, TWX>(tn, m);
       stage_complex_rows<N, TWX>(cur ? st0 : st1, moved(w_in, rn.by), rn.row0);
     }
     cp_async_commit();
@@ -1045,7 +1065,7 @@ static cudaError_t launch_xr2c(const float* in, float2* out, float scale, float 
   unsigned grid;
   cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, sm, s>>>(in, out, scale, offset, tw, ntiles, tps, m);
+  k<<<grid, NT, sm, s>>>(in, out, scale, offset, tw, ntiles, m);
   return cudaGetLastError();
 }
 
@@ -1062,6 +1082,7 @@ static cudaError_t launch_xc2r_multi(int njobs, const float2* const* in, float* 
   const size_t sm = row_smem<N>();
   RowJobs jobs{};
   jobs.njobs = njobs;
+  fast_div_magic((uint32_t)njobs, jobs.jmul, jobs.jshift);
   for (int i = 0; i < njobs; ++i) {
     jobs.in[i] = in[i];
     jobs.out[i] = out[i];
@@ -1189,12 +1210,12 @@ static cudaError_t launch_xscreen(const float2* w_in, const float* rho, float2* 
     auto k = k_x_screen<N, TWX, 1>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, fp, tw, ntiles, tps, m);
+    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, fp, tw, ntiles, m);
   } else {
     auto k = k_x_screen<N, TWX, 2>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, fp, tw, ntiles, tps, m);
+    k<<<grid, NT, sm, s>>>(w_in, rho, s_out, fp, tw, ntiles, m);
   }
   return cudaGetLastError();
 }
