@@ -201,10 +201,26 @@ __device__ __forceinline__ void col_store(const float2* buf, int sub, float2* __
   }
 }
 
-__device__ __forceinline__ float kk2(int ix, int iy, int iz, int N, float kf) {
-  const float fx = (float)ix, fy = (float)freq_index(iy, N), fz = (float)freq_index(iz, N);
-  return kf * kf * (fx * fx + fy * fy + fz * fz);
-}
+// The elements of an N x TW column tile that a thread owns: column c = tid mod
+// TW and rows n = n0 + i STEP, i < E (STEP = NT / TW, n0 = tid / TW).  |n|^2
+// of element (kx, ky, n) is sxy + fz(n)^2 with sxy = kx^2 + ky^2 kept per
+// thread; the integer sum is exact, so k^2 = kf^2 |n|^2 rounds once.
+template <int N, int TW>
+struct TileLane {
+  static constexpr int STEP = NT / TW, E = N * TW / NT;
+  int c, n0, sxy;
+  __device__ __forceinline__ TileLane(int c0, int iy) {
+    c = threadIdx.x % TW;
+    n0 = threadIdx.x / TW;
+    const int fx = c0 + c, fy = freq_index(iy, N);
+    sxy = fx * fx + fy * fy;
+  }
+  __device__ __forceinline__ int row(int i) const { return n0 + i * STEP; }
+  __device__ __forceinline__ float k2(int n, float kf2) const {
+    const int fz = freq_index(n, N);
+    return kf2 * (float)(sxy + fz * fz);
+  }
+};
 
 // Column geometry: tile t -> (simulation b, outer index o, column block c0);
 // base = the element offset of (o, row 0, c0) and `by` = the byte shift of
@@ -436,18 +452,23 @@ struct OpZScreenField {
     resolve(fp, by);
     float2* dko = moved(dk_out, by);
     fft_tile_call<N, TW, TW, NT, false>(buf, tw);
-#pragma unroll 2
-    for (int e = threadIdx.x; e < N * TW; e += NT) {
-      const int c = e % TW, n = e / TW;
-      const float2 v = buf[n * TW + c];
-      if (c0 + c < N / 2 + 1) dko[base + (n >> 1) * geo.ra + (n & 1) * geo.rb + hcol(c)] = v;
-      const float k2 = kk2(c0 + c, iy, n, N, fp.kf);
+    const TileLane<N, TW> ln(c0, iy);
+    const float kf2 = fp.kf * fp.kf;
+    const bool live = c0 + ln.c < N / 2 + 1;
+    // delta(k) out: rows n0 + i STEP (STEP even) sit (STEP / 2) ra apart
+    float2* dkp = dko + base + (ln.n0 >> 1) * geo.ra + (ln.n0 & 1) * geo.rb + hcol(ln.c);
+#pragma unroll 4
+    for (int i = 0; i < ln.E; ++i) {
+      const int n = ln.row(i);
+      const float2 v = buf[n * TW + ln.c];
+      if (live) dkp[(int64_t)i * (ln.STEP / 2) * geo.ra] = v;
+      const float k2 = ln.k2(n, kf2);
       float m = 0.f;
       if (k2 > 0.f) {
         if (MODEL == 1) m = __fdividef(-fp.kappa_norm, k2);
         else m = __expf(-k2 * fp.R2half) * fp.norm;
       }
-      buf[n * TW + c] = cscale(v, m);
+      buf[n * TW + ln.c] = cscale(v, m);
     }
     __syncthreads();
     fft_tile_call<N, TW, TW, NT, true>(buf, tw);
@@ -503,35 +524,35 @@ struct OpZForce {
       cp_async_wait<1>();  // delta(k) of this tile; the next tile's prefetch may still be in flight
       __syncthreads();
     }
-#pragma unroll 2
+    const TileLane<N, TW> ln(c0, iy);
+    const float kf2 = fp.kf * fp.kf;
+#pragma unroll 4
     for (int i = 0; i < E; ++i) {
-      const int e = threadIdx.x + i * NT;
-      const int c = e % TW, n = e / TW;
-      const float k2 = kk2(c0 + c, iy, n, N, fp.kf);
+      const int n = ln.row(i), at = n * TW + ln.c;
+      const float k2 = ln.k2(n, kf2);
       float2 phi = make_float2(0.f, 0.f);
       if (k2 > 0.f) {
         const float yuk = __fdividef(k2, k2 + fp.a2m2);
         const float g = __fdividef(-fp.kappa_norm, k2);
-        const float2 src = buf[n * TW + c];
+        const float2 src = buf[at];
         if (SCREENED) {
-          phi = cscale(cadd(ph[n * TW + c], cscale(src, fp.C * yuk)), g);
+          phi = cscale(cadd(ph[at], cscale(src, fp.C * yuk)), g);
         } else {
           phi = cscale(src, g * (1.f + fp.C * yuk));
         }
       }
-      ph[n * TW + c] = phi;
-      buf[n * TW + c] = phi;
+      ph[at] = phi;
+      buf[at] = phi;
     }
     __syncthreads();
     fft_tile_call<N, TW, TW, NT, true>(buf, tw);
     col_store<N, TW, TW>(buf, 0, moved(phi_out, by), base, geo.ra, geo.rb, c0);
     __syncthreads();
-#pragma unroll 2
+#pragma unroll 4
     for (int i = 0; i < E; ++i) {
-      const int e = threadIdx.x + i * NT;
-      const int c = e % TW, n = e / TW;
+      const int n = ln.row(i), at = n * TW + ln.c;
       const float kzs = (n == N / 2) ? 0.f : -fp.kf * (float)freq_index(n, N);
-      buf[n * TW + c] = cscale(cmul_i(ph[n * TW + c]), kzs);
+      buf[at] = cscale(cmul_i(ph[at]), kzs);
     }
     __syncthreads();
     fft_tile_call<N, TW, TW, NT, true>(buf, tw);
@@ -602,9 +623,13 @@ struct OpLptZ {
       }
       __syncthreads();  // the raw staging (sub-blocks 2, 3) is consumed
     }
-    for (int e = threadIdx.x; e < N * TW; e += NT) {
-      const int c = e % TW, n = e / TW;
-      const float k2 = kk2(c0 + c, iy, n, N, lp.kf);
+    const TileLane<N, TW> ln(c0, iy);
+    const float kf2 = lp.kf * lp.kf;
+    const int c = ln.c;
+#pragma unroll 2
+    for (int i = 0; i < ln.E; ++i) {
+      const int n = ln.row(i);
+      const float k2 = ln.k2(n, kf2);
       float2 d = make_float2(0.f, 0.f), A = make_float2(0.f, 0.f);
       if (k2 > 0.f) {
         const float u = (0.5f * __logf(k2) - lp.lnk0) * lp.inv_dlnk;
