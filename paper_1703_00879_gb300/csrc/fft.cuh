@@ -186,8 +186,24 @@ __host__ __device__ constexpr int fft_rows() {
 // every address is a per-thread base plus a compile-time offset.  tw has
 // L * TWS entries; the caller synchronises before the call; returns after a
 // barrier.
-template <int L, int TW, int PITCH, int NT, bool INV, int TWS = 1>
-__device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2* __restrict__ tw) {
+//
+// Hooks (defaults: the tile itself): step 1 reads element n of column c as
+// ld(buf, n, c, at) and step 2 writes X[n] as st(X[n], n, c, at), at = n PITCH
+// + c, so a k-space operation fuses into the first load or the last store
+// (reading or writing another array at the same offset); st.ready() runs in
+// every thread before the barrier between the steps.
+struct TileLoad {
+  __device__ __forceinline__ float2 operator()(const float2* buf, int, int, int at) const { return buf[at]; }
+};
+struct TileStore {
+  __device__ __forceinline__ float2 operator()(float2 v, int, int, int) const { return v; }
+  __device__ __forceinline__ void ready() const {}
+};
+
+template <int L, int TW, int PITCH, int NT, bool INV, int TWS = 1, class Load = TileLoad,
+          class Store = TileStore>
+__device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2* __restrict__ tw,
+                                         Load ld = Load(), Store st = Store()) {
   constexpr int R1 = Split<L>::R1, R2 = Split<L>::R2;
   constexpr int U1 = TW * R2, P1 = (U1 + NT - 1) / NT;
   constexpr int U2 = TW * R1, P2 = (U2 + NT - 1) / NT;
@@ -201,7 +217,7 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
       if ((U1 % NT) == 0 || u < U1) {
         const int c = u % TW, n2 = u / TW;
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) v[i][n1] = buf[(R2 * n1 + n2) * PITCH + c];
+        for (int n1 = 0; n1 < R1; ++n1) v[i][n1] = ld(buf, R2 * n1 + n2, c, (R2 * n1 + n2) * PITCH + c);
         dftR<R1, INV>(v[i]);
         if (n2 > 0) {
 #pragma unroll
@@ -225,6 +241,7 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
       }
     }
   }
+  st.ready();
   __syncthreads();
   {
     float2 y[P2][R2];
@@ -246,7 +263,10 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
       if ((U2 % NT) == 0 || u < U2) {
         const int c = u % TW, k1 = u / TW;
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) buf[(k1 + R1 * k2) * PITCH + c] = y[i][pos_of<R2>(k2)];
+        for (int k2 = 0; k2 < R2; ++k2) {
+          const int n = k1 + R1 * k2;
+          buf[n * PITCH + c] = st(y[i][pos_of<R2>(k2)], n, c, n * PITCH + c);
+        }
       }
     }
   }
@@ -366,9 +386,11 @@ __device__ __noinline__ void fft_rowtile_call(float2* buf, const float2* tw, Pre
 
 // Out-of-line copy for kernels that run several transforms per tile: each
 // call gets its own register allocation instead of one inlined body per call.
-template <int L, int TW, int PITCH, int NT, bool INV, int TWS = 1>
-__device__ __noinline__ void fft_tile_call(float2* buf, const float2* tw) {
-  fft_tile<L, TW, PITCH, NT, INV, TWS>(buf, tw);
+template <int L, int TW, int PITCH, int NT, bool INV, int TWS = 1, class Load = TileLoad,
+          class Store = TileStore>
+__device__ __noinline__ void fft_tile_call(float2* buf, const float2* tw, Load ld = Load(),
+                                           Store st = Store()) {
+  fft_tile<L, TW, PITCH, NT, INV, TWS, Load, Store>(buf, tw, ld, st);
 }
 
 // Signed frequency index of position n in a length-N transform.

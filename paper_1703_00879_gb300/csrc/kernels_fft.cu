@@ -432,6 +432,26 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(yinv2r_smem<N, TW>(), N)) 
 // ---------------------------------------------------------------- screening field (z pass)
 template <int N, int TW, int MODEL>
 struct OpZScreenField {
+  // Store hook of the forward transform: delta(k) out to HBM, the field's
+  // multiplier (f(R): -kappa/k^2; nDGP: the Gaussian filter) applied in place.
+  struct Field {
+    float2* dk;  // delta(k) of the tile: element (n, c) at dk[(n >> 1) ra + (n & 1) rb + hcol(c)]
+    int64_t ra, rb;
+    int c0, fy2;
+    float kf2, kappa_norm, R2half, norm;
+    __device__ __forceinline__ float2 operator()(float2 v, int n, int c, int) const {
+      if (c0 + c < N / 2 + 1) dk[(n >> 1) * ra + (n & 1) * rb + hcol(c)] = v;
+      const int fx = c0 + c, fz = freq_index(n, N);
+      const float k2 = kf2 * (float)(fx * fx + fy2 + fz * fz);
+      float m = 0.f;
+      if (k2 > 0.f) {
+        if (MODEL == 1) m = __fdividef(-kappa_norm, k2);
+        else m = __expf(-k2 * R2half) * norm;
+      }
+      return cscale(v, m);
+    }
+    __device__ __forceinline__ void ready() const {}
+  };
   ColGeo<N, TW> geo;
   const float2* in;
   float2 *dk_out, *w_out;
@@ -450,27 +470,10 @@ struct OpZScreenField {
     geo.tile(t, iy, c0, base, by);
     ForceParams fp = this->fp;
     resolve(fp, by);
-    float2* dko = moved(dk_out, by);
-    fft_tile_call<N, TW, TW, NT, false>(buf, tw);
-    const TileLane<N, TW> ln(c0, iy);
-    const float kf2 = fp.kf * fp.kf;
-    const bool live = c0 + ln.c < N / 2 + 1;
-    // delta(k) out: rows n0 + i STEP (STEP even) sit (STEP / 2) ra apart
-    float2* dkp = dko + base + (ln.n0 >> 1) * geo.ra + (ln.n0 & 1) * geo.rb + hcol(ln.c);
-#pragma unroll 4
-    for (int i = 0; i < ln.E; ++i) {
-      const int n = ln.row(i);
-      const float2 v = buf[n * TW + ln.c];
-      if (live) dkp[(int64_t)i * (ln.STEP / 2) * geo.ra] = v;
-      const float k2 = ln.k2(n, kf2);
-      float m = 0.f;
-      if (k2 > 0.f) {
-        if (MODEL == 1) m = __fdividef(-fp.kappa_norm, k2);
-        else m = __expf(-k2 * fp.R2half) * fp.norm;
-      }
-      buf[n * TW + ln.c] = cscale(v, m);
-    }
-    __syncthreads();
+    const int fy = freq_index(iy, N);
+    const Field f{moved(dk_out, by) + base, geo.ra, geo.rb, c0, fy * fy, fp.kf * fp.kf, fp.kappa_norm,
+                  fp.R2half, fp.norm};
+    fft_tile_call<N, TW, TW, NT, false, 1, TileLoad, Field>(buf, tw, TileLoad{}, f);
     fft_tile_call<N, TW, TW, NT, true>(buf, tw);
     col_store<N, TW, TW>(buf, 0, moved(w_out, by), base, geo.ra, geo.rb, c0);
   }
@@ -491,7 +494,43 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_tw(N, TW), N) < 2
 // transformed one after the other in the same buffer.
 template <int N, int TW, bool SCREENED>
 struct OpZForce {
-  static constexpr int E = (N * TW) / NT;  // elements per thread
+  // One CTA per SM (N >= 512, up to 255 registers): Phi_tot(k) is formed in the
+  // forward transform's last store; with two CTAs (128 registers) that spills,
+  // and a separate pass over the tile forms it instead.
+  static constexpr bool FUSED = blocks_for_smem(col_smem_tw(N, TW) + (size_t)N * TW * 8, N) < 2;
+  // Store hook of the forward transform of S: Phi_tot(k) (App. B), written to
+  // the buffer for the Phi inverse and to `ph` (which held delta(k)) for the
+  // gradient; ready() waits for this tile's delta(k) between the two steps.
+  struct Combine {
+    float2* ph;
+    int c0, fy2;
+    float kf2, a2m2, kappa_norm, C;
+    __device__ __forceinline__ float2 operator()(float2 src, int n, int c, int at) const {
+      const int fx = c0 + c, fz = freq_index(n, N);
+      const float k2 = kf2 * (float)(fx * fx + fy2 + fz * fz);
+      float2 phi = make_float2(0.f, 0.f);
+      if (k2 > 0.f) {
+        const float yuk = __fdividef(k2, k2 + a2m2);
+        const float g = __fdividef(-kappa_norm, k2);
+        if (SCREENED) phi = cscale(cadd(ph[at], cscale(src, C * yuk)), g);
+        else phi = cscale(src, g * (1.f + C * yuk));
+      }
+      ph[at] = phi;
+      return phi;
+    }
+    __device__ __forceinline__ void ready() const {
+      if (SCREENED) cp_async_wait<1>();  // delta(k); the next tile's prefetch may stay in flight
+    }
+  };
+  // Load hook of the gradient transform: -i kz Phi_tot(k), zero on the Nyquist row.
+  struct GradZ {
+    const float2* ph;
+    float mkf;
+    __device__ __forceinline__ float2 operator()(const float2*, int n, int, int at) const {
+      const float kzs = (n == N / 2) ? 0.f : mkf * (float)freq_index(n, N);
+      return cscale(cmul_i(ph[at]), kzs);
+    }
+  };
   ColGeo<N, TW> geo;
   const float2 *in, *dk;
   float2 *phi_out, *phiz_out;
@@ -519,43 +558,40 @@ struct OpZForce {
     ForceParams fp = this->fp;
     resolve(fp, by);
     float2* ph = extra;  // delta(k) of the tile, then Phi_tot(k), N x TW
-    fft_tile_call<N, TW, TW, NT, false>(buf, tw);
-    if (SCREENED) {
-      cp_async_wait<1>();  // delta(k) of this tile; the next tile's prefetch may still be in flight
+    const int fy = freq_index(iy, N);
+    const Combine cmb{ph, c0, fy * fy, fp.kf * fp.kf, fp.a2m2, fp.kappa_norm, fp.C};
+    if constexpr (FUSED) {
+      fft_tile_call<N, TW, TW, NT, false, 1, TileLoad, Combine>(buf, tw, TileLoad{}, cmb);
+    } else {
+      fft_tile_call<N, TW, TW, NT, false>(buf, tw);
+      cmb.ready();
+      __syncthreads();
+      const TileLane<N, TW> ln(c0, iy);
+#pragma unroll 4
+      for (int i = 0; i < ln.E; ++i) {
+        const int n = ln.row(i), at = n * TW + ln.c;
+        buf[at] = cmb(buf[at], n, ln.c, at);
+      }
       __syncthreads();
     }
-    const TileLane<N, TW> ln(c0, iy);
-    const float kf2 = fp.kf * fp.kf;
-#pragma unroll 4
-    for (int i = 0; i < E; ++i) {
-      const int n = ln.row(i), at = n * TW + ln.c;
-      const float k2 = ln.k2(n, kf2);
-      float2 phi = make_float2(0.f, 0.f);
-      if (k2 > 0.f) {
-        const float yuk = __fdividef(k2, k2 + fp.a2m2);
-        const float g = __fdividef(-fp.kappa_norm, k2);
-        const float2 src = buf[at];
-        if (SCREENED) {
-          phi = cscale(cadd(ph[at], cscale(src, fp.C * yuk)), g);
-        } else {
-          phi = cscale(src, g * (1.f + fp.C * yuk));
-        }
-      }
-      ph[at] = phi;
-      buf[at] = phi;
-    }
-    __syncthreads();
     fft_tile_call<N, TW, TW, NT, true>(buf, tw);
     col_store<N, TW, TW>(buf, 0, moved(phi_out, by), base, geo.ra, geo.rb, c0);
-    __syncthreads();
+    const GradZ grad{ph, -fp.kf};
+    if constexpr (FUSED) {
+      // the gradient transform reads ph; its first barrier (before step 1
+      // writes the buffer) orders those writes after every thread's col_store
+      fft_tile_call<N, TW, TW, NT, true, 1, GradZ>(buf, tw, grad);
+    } else {
+      __syncthreads();
+      const TileLane<N, TW> ln(c0, iy);
 #pragma unroll 4
-    for (int i = 0; i < E; ++i) {
-      const int n = ln.row(i), at = n * TW + ln.c;
-      const float kzs = (n == N / 2) ? 0.f : -fp.kf * (float)freq_index(n, N);
-      buf[at] = cscale(cmul_i(ph[at]), kzs);
+      for (int i = 0; i < ln.E; ++i) {
+        const int n = ln.row(i), at = n * TW + ln.c;
+        buf[at] = grad(buf, n, ln.c, at);
+      }
+      __syncthreads();
+      fft_tile_call<N, TW, TW, NT, true>(buf, tw);
     }
-    __syncthreads();
-    fft_tile_call<N, TW, TW, NT, true>(buf, tw);
     col_store<N, TW, TW>(buf, 0, moved(phiz_out, by), base, geo.ra, geo.rb, c0);
   }
 };
