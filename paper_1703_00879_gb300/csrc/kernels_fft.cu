@@ -332,6 +332,19 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 1), N)) k_co
 // ---------------------------------------------------------------- y inverse, two outputs
 template <int N, int TW>
 struct OpYinv2 {
+  // Load hook of the two-array transform: columns c < TW are the staged input,
+  // columns TW + c its y derivative i kfs f_n (zero on the Nyquist row), formed
+  // from column c as the first step loads it.
+  struct PairLoad {
+    float kfs;
+    __device__ __forceinline__ float2 operator()(const float2* buf, int n, int c, int at) const {
+      const bool d = c >= TW;
+      const float2 v = buf[d ? at - TW : at];
+      const float f = (n == N / 2) ? 0.f : kfs * (float)freq_index(n, N);
+      const float a = d ? 0.f : 1.f, b = d ? f : 0.f;  // v (a + i b)
+      return make_float2(a * v.x - b * v.y, a * v.y + b * v.x);
+    }
+  };
   ColGeo<N, TW> geo;
   const float2* in;
   float2 *outp, *outd;
@@ -349,13 +362,7 @@ struct OpYinv2 {
     int o, c0;
     int64_t base, by;
     geo.tile(t, o, c0, base, by);
-    for (int e = threadIdx.x; e < N * TW; e += NT) {
-      const int c = e % TW, n = e / TW;
-      const float f = (n == N / 2) ? 0.f : kfs * (float)freq_index(n, N);
-      buf[n * TP + TW + c] = cscale(cmul_i(buf[n * TP + c]), f);
-    }
-    __syncthreads();
-    fft_tile<N, TP, TP, NT, true>(buf, tw);
+    fft_tile<N, TP, TP, NT, true, 1, PairLoad>(buf, tw, PairLoad{kfs});
     col_store<N, TW, TP>(buf, 0, moved(outp, by), base, geo.ra, geo.rb, c0);
     col_store<N, TW, TP>(buf, 1, moved(outd, by), base, geo.ra, geo.rb, c0);
   }
@@ -374,10 +381,25 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 2), N)) k_yi
 // input is read from HBM once with TW-column (64-byte) rows.  Given input
 // buffer I, the derivative goes to (I + 1) mod 3 and the prefetch to (I + 2)
 // mod 3, which holds the next tile's input.
+// Load hook: i kfs f_n times element (n, c) of another tile (zero on the Nyquist row).
+template <int N>
+struct DerivLoad {
+  const float2* src;
+  float kfs;
+  __device__ __forceinline__ float2 operator()(const float2*, int n, int, int at) const {
+    const float f = (n == N / 2) ? 0.f : kfs * (float)freq_index(n, N);
+    return cscale(cmul_i(src[at]), f);
+  }
+};
+
 template <int N, int TW>
 constexpr size_t yinv2r_smem() {
   return (N + 3 * (size_t)fft_rows<N>() * TW) * sizeof(float2);
 }
+template <int N, int TW>
+struct Yinv2rCfg {
+  static constexpr bool ONE_CTA = blocks_for_smem(yinv2r_smem<N, TW>(), N) < 2;
+};
 
 template <int N, int TW>
 __global__ void __launch_bounds__(NT, blocks_for_smem(yinv2r_smem<N, TW>(), N)) k_yinv2r(
@@ -413,16 +435,21 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(yinv2r_smem<N, TW>(), N)) 
     int o, c0;
     int64_t base, by;
     geo.tile(t, o, c0, base, by);
-    for (int e = threadIdx.x; e < N * TW; e += NT) {
-      const int n = e / TW;
-      const float f = (n == N / 2) ? 0.f : kfs * (float)freq_index(n, N);
-      bd[e] = cscale(cmul_i(bi[e]), f);
+    if constexpr (Yinv2rCfg<N, TW>::ONE_CTA) {
+      // one CTA per SM: the derivative transform runs first, its first step
+      // reading the input (times i kfs f_n) from bi, which the plain transform
+      // then overwrites
+      fft_tile_call<N, TW, TW, NT, true, 1, DerivLoad<N>>(bd, tw, DerivLoad<N>{bi, kfs});
+    } else {
+      // two CTAs per SM (128 registers, where the load hook spills): a pass over the tile
+      const DerivLoad<N> dl{bi, kfs};
+      for (int e = threadIdx.x; e < N * TW; e += NT) bd[e] = dl(bd, e / TW, 0, e);
+      __syncthreads();
+      fft_tile_call<N, TW, TW, NT, true>(bd, tw);
     }
-    __syncthreads();
+    col_store<N, TW, TW>(bd, 0, moved(outd, by), base, geo.ra, geo.rb, c0);
     fft_tile_call<N, TW, TW, NT, true>(bi, tw);
     col_store<N, TW, TW>(bi, 0, moved(outp, by), base, geo.ra, geo.rb, c0);
-    fft_tile_call<N, TW, TW, NT, true>(bd, tw);
-    col_store<N, TW, TW>(bd, 0, moved(outd, by), base, geo.ra, geo.rb, c0);
     __syncthreads();  // both buffers are free for later prefetches
     I = F;
   }
