@@ -191,11 +191,14 @@ __host__ __device__ constexpr int fft_rows() {
 // ld(buf, n, c, at) and step 2 writes X[n] as st(X[n], n, c, at), at = n PITCH
 // + c, so a k-space operation fuses into the first load or the last store
 // (reading or writing another array at the same offset); st.ready() runs in
-// every thread before the barrier between the steps.
+// every thread before the barrier between the steps.  A store hook with
+// kSmem = false writes the outputs itself (e.g. straight to HBM) and the tile
+// is left holding the intermediate.
 struct TileLoad {
   __device__ __forceinline__ float2 operator()(const float2* buf, int, int, int at) const { return buf[at]; }
 };
 struct TileStore {
+  static constexpr bool kSmem = true;
   __device__ __forceinline__ float2 operator()(float2 v, int, int, int) const { return v; }
   __device__ __forceinline__ void ready() const {}
 };
@@ -265,7 +268,8 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) {
           const int n = k1 + R1 * k2;
-          buf[n * PITCH + c] = st(y[i][pos_of<R2>(k2)], n, c, n * PITCH + c);
+          const float2 o = st(y[i][pos_of<R2>(k2)], n, c, n * PITCH + c);
+          if constexpr (Store::kSmem) buf[n * PITCH + c] = o;
         }
       }
     }

@@ -222,6 +222,22 @@ struct TileLane {
   }
 };
 
+// Store hook of a column transform that writes element (n, c) straight to
+// g[(n >> 1) ra + (n & 1) rb + hcol(c)] (g = the tile's base, columns c < live
+// exist) instead of through the tile and col_store: a warp's stores cover whole
+// 128-byte chunk pairs.
+struct ColOut {
+  static constexpr bool kSmem = false;
+  float2* g;
+  int64_t ra, rb;
+  int live;
+  __device__ __forceinline__ float2 operator()(float2 v, int n, int c, int) const {
+    if (c < live) g[(n >> 1) * ra + (n & 1) * rb + hcol(c)] = v;
+    return v;
+  }
+  __device__ __forceinline__ void ready() const {}
+};
+
 // Column geometry: tile t -> (simulation b, outer index o, column block c0);
 // base = the element offset of (o, row 0, c0) and `by` = the byte shift of
 // simulation b's buffers.  Outer index o sits at (o >> 1) oa + (o & 1) ob and
@@ -294,6 +310,7 @@ __device__ __forceinline__ void col_pipeline(Op op, const float2* __restrict__ t
 // f_n the signed frequency, zero on the Nyquist row); out may alias in.
 template <int N, int TW, bool INV>
 struct OpCol {
+  static constexpr bool ONE_CTA = blocks_for_smem(col_smem_c(N, 1), N) < 2;
   ColGeo<N, TW> geo;
   const float2* in;
   float2* out;
@@ -318,8 +335,14 @@ struct OpCol {
       }
       __syncthreads();
     }
-    fft_tile<N, TW, TW, NT, INV>(buf, tw);
-    col_store<N, TW, TW>(buf, 0, moved(out, by), base, geo.ra, geo.rb, c0);
+    if constexpr (ONE_CTA) {
+      // one CTA per SM: outputs go to HBM from the last step's registers
+      fft_tile<N, TW, TW, NT, INV, 1, TileLoad, ColOut>(
+          buf, tw, TileLoad{}, ColOut{moved(out, by) + base, geo.ra, geo.rb, N / 2 + 1 - c0});
+    } else {
+      fft_tile<N, TW, TW, NT, INV>(buf, tw);
+      col_store<N, TW, TW>(buf, 0, moved(out, by), base, geo.ra, geo.rb, c0);
+    }
   }
 };
 
@@ -438,18 +461,23 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(yinv2r_smem<N, TW>(), N)) 
     if constexpr (Yinv2rCfg<N, TW>::ONE_CTA) {
       // one CTA per SM: the derivative transform runs first, its first step
       // reading the input (times i kfs f_n) from bi, which the plain transform
-      // then overwrites
-      fft_tile_call<N, TW, TW, NT, true, 1, DerivLoad<N>>(bd, tw, DerivLoad<N>{bi, kfs});
+      // then overwrites; both store straight to HBM
+      const ColOut o{nullptr, geo.ra, geo.rb, N / 2 + 1 - c0};
+      ColOut od = o, op = o;
+      od.g = moved(outd, by) + base;
+      op.g = moved(outp, by) + base;
+      fft_tile_call<N, TW, TW, NT, true, 1, DerivLoad<N>, ColOut>(bd, tw, DerivLoad<N>{bi, kfs}, od);
+      fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(bi, tw, TileLoad{}, op);
     } else {
       // two CTAs per SM (128 registers, where the load hook spills): a pass over the tile
       const DerivLoad<N> dl{bi, kfs};
       for (int e = threadIdx.x; e < N * TW; e += NT) bd[e] = dl(bd, e / TW, 0, e);
       __syncthreads();
       fft_tile_call<N, TW, TW, NT, true>(bd, tw);
+      col_store<N, TW, TW>(bd, 0, moved(outd, by), base, geo.ra, geo.rb, c0);
+      fft_tile_call<N, TW, TW, NT, true>(bi, tw);
+      col_store<N, TW, TW>(bi, 0, moved(outp, by), base, geo.ra, geo.rb, c0);
     }
-    col_store<N, TW, TW>(bd, 0, moved(outd, by), base, geo.ra, geo.rb, c0);
-    fft_tile_call<N, TW, TW, NT, true>(bi, tw);
-    col_store<N, TW, TW>(bi, 0, moved(outp, by), base, geo.ra, geo.rb, c0);
     __syncthreads();  // both buffers are free for later prefetches
     I = F;
   }
@@ -459,9 +487,11 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(yinv2r_smem<N, TW>(), N)) 
 // ---------------------------------------------------------------- screening field (z pass)
 template <int N, int TW, int MODEL>
 struct OpZScreenField {
+  static constexpr bool ONE_CTA = blocks_for_smem(col_smem_tw(N, TW), N) < 2;
   // Store hook of the forward transform: delta(k) out to HBM, the field's
   // multiplier (f(R): -kappa/k^2; nDGP: the Gaussian filter) applied in place.
   struct Field {
+    static constexpr bool kSmem = true;
     float2* dk;  // delta(k) of the tile: element (n, c) at dk[(n >> 1) ra + (n & 1) rb + hcol(c)]
     int64_t ra, rb;
     int c0, fy2;
@@ -501,8 +531,13 @@ struct OpZScreenField {
     const Field f{moved(dk_out, by) + base, geo.ra, geo.rb, c0, fy * fy, fp.kf * fp.kf, fp.kappa_norm,
                   fp.R2half, fp.norm};
     fft_tile_call<N, TW, TW, NT, false, 1, TileLoad, Field>(buf, tw, TileLoad{}, f);
-    fft_tile_call<N, TW, TW, NT, true>(buf, tw);
-    col_store<N, TW, TW>(buf, 0, moved(w_out, by), base, geo.ra, geo.rb, c0);
+    if constexpr (ONE_CTA) {
+      fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(
+          buf, tw, TileLoad{}, ColOut{moved(w_out, by) + base, geo.ra, geo.rb, N / 2 + 1 - c0});
+    } else {
+      fft_tile_call<N, TW, TW, NT, true>(buf, tw);
+      col_store<N, TW, TW>(buf, 0, moved(w_out, by), base, geo.ra, geo.rb, c0);
+    }
   }
 };
 
@@ -529,6 +564,7 @@ struct OpZForce {
   // the buffer for the Phi inverse and to `ph` (which held delta(k)) for the
   // gradient; ready() waits for this tile's delta(k) between the two steps.
   struct Combine {
+    static constexpr bool kSmem = true;
     float2* ph;
     int c0, fy2;
     float kf2, a2m2, kappa_norm, C;
@@ -601,14 +637,19 @@ struct OpZForce {
       }
       __syncthreads();
     }
-    fft_tile_call<N, TW, TW, NT, true>(buf, tw);
-    col_store<N, TW, TW>(buf, 0, moved(phi_out, by), base, geo.ra, geo.rb, c0);
     const GradZ grad{ph, -fp.kf};
     if constexpr (FUSED) {
-      // the gradient transform reads ph; its first barrier (before step 1
-      // writes the buffer) orders those writes after every thread's col_store
-      fft_tile_call<N, TW, TW, NT, true, 1, GradZ>(buf, tw, grad);
+      // both inverse transforms store straight to HBM; the gradient transform
+      // reads ph, not the tile
+      const ColOut o{nullptr, geo.ra, geo.rb, N / 2 + 1 - c0};
+      ColOut op = o, oz = o;
+      op.g = moved(phi_out, by) + base;
+      oz.g = moved(phiz_out, by) + base;
+      fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(buf, tw, TileLoad{}, op);
+      fft_tile_call<N, TW, TW, NT, true, 1, GradZ, ColOut>(buf, tw, grad, oz);
     } else {
+      fft_tile_call<N, TW, TW, NT, true>(buf, tw);
+      col_store<N, TW, TW>(buf, 0, moved(phi_out, by), base, geo.ra, geo.rb, c0);
       __syncthreads();
       const TileLane<N, TW> ln(c0, iy);
 #pragma unroll 4
@@ -618,8 +659,8 @@ struct OpZForce {
       }
       __syncthreads();
       fft_tile_call<N, TW, TW, NT, true>(buf, tw);
+      col_store<N, TW, TW>(buf, 0, moved(phiz_out, by), base, geo.ra, geo.rb, c0);
     }
-    col_store<N, TW, TW>(buf, 0, moved(phiz_out, by), base, geo.ra, geo.rb, c0);
   }
 };
 
