@@ -299,9 +299,18 @@ struct NoPre {
 // PAIR32: for L = 16 x 32 with half as many step-2 items as threads, step 2
 // runs on thread pairs (dft32_pair), halving its registers per thread.
 // The caller synchronises before the call; returns after a barrier.
-template <int L, int TW, int CW, int NT, bool INV, int TWS = 1, class Pre = NoPre, bool PAIR32 = false>
+// Store hook of fft_rowtile's last step: output k of row c as st(X[k], c, k);
+// with kSmem = false the hook writes the output itself and the tile keeps the
+// intermediate.
+struct RowStore {
+  static constexpr bool kSmem = true;
+  __device__ __forceinline__ float2 operator()(float2 v, int, int) const { return v; }
+};
+
+template <int L, int TW, int CW, int NT, bool INV, int TWS = 1, class Pre = NoPre, bool PAIR32 = false,
+          class Store = RowStore>
 __device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const float2* __restrict__ tw,
-                                            Pre pre = Pre()) {
+                                            Pre pre = Pre(), Store st = Store()) {
   constexpr int R1 = Split<L>::R1, R2 = Split<L>::R2;
   constexpr int U1 = TW * R2, P1 = (U1 + NT - 1) / NT;
   constexpr int U2 = TW * R1, P2 = (U2 + NT - 1) / NT;
@@ -354,7 +363,10 @@ __device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const floa
     __syncthreads();
     float2* X = buf + c * CW + k1 + R1 * half;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) X[2 * R1 * k] = y[pos_of<16>(k)];
+    for (int k = 0; k < 16; ++k) {
+      const float2 o = st(y[pos_of<16>(k)], c, k1 + R1 * (2 * k + half));
+      if constexpr (Store::kSmem) X[2 * R1 * k] = o;
+    }
   } else {
     float2 y[P2][R2];
 #pragma unroll
@@ -376,16 +388,21 @@ __device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const floa
         const int c = u / R1, k1 = u % R1;
         float2* X = buf + c * CW + k1;
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) X[R1 * k2] = y[i][pos_of<R2>(k2)];
+        for (int k2 = 0; k2 < R2; ++k2) {
+          const float2 o = st(y[i][pos_of<R2>(k2)], c, k1 + R1 * k2);
+          if constexpr (Store::kSmem) X[R1 * k2] = o;
+        }
       }
     }
   }
   __syncthreads();
 }
 
-template <int L, int TW, int CW, int NT, bool INV, int TWS = 1, class Pre = NoPre, bool PAIR32 = false>
-__device__ __noinline__ void fft_rowtile_call(float2* buf, const float2* tw, Pre pre = Pre()) {
-  fft_rowtile<L, TW, CW, NT, INV, TWS, Pre, PAIR32>(buf, tw, pre);
+template <int L, int TW, int CW, int NT, bool INV, int TWS = 1, class Pre = NoPre, bool PAIR32 = false,
+          class Store = RowStore>
+__device__ __noinline__ void fft_rowtile_call(float2* buf, const float2* tw, Pre pre = Pre(),
+                                              Store st = Store()) {
+  fft_rowtile<L, TW, CW, NT, INV, TWS, Pre, PAIR32, Store>(buf, tw, pre, st);
 }
 
 // Out-of-line copy for kernels that run several transforms per tile: each

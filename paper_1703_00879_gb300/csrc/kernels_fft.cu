@@ -1006,6 +1006,18 @@ __device__ __forceinline__ JobTile job_tile(int64_t t64, const RowJobs& jobs, co
   return JobTile{(int)(q - b * (uint32_t)jobs.njobs), (int64_t)(t - q * TPJ) * TWX, shift_of(m, (int)b)};
 }
 
+// Store hook of the c2r row transform: tile row r's M complex outputs (2M
+// reals) to real row r / 2 of the even (o0) or odd (o1) block.
+template <int M>
+struct RealRowOut {
+  static constexpr bool kSmem = false;
+  float2 *o0, *o1;
+  __device__ __forceinline__ float2 operator()(float2 v, int r, int k) const {
+    ((r & 1) ? o1 : o0)[(r >> 1) * M + k] = v;
+    return v;
+  }
+};
+
 template <int N, int TWX>
 __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_constant__ RowJobs jobs,
                                                 const float2* __restrict__ twg, int64_t tiles_per_job,
@@ -1038,19 +1050,12 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
     __syncthreads();
     float2* buf = cur ? st1 : st0;
     row_c2r_combine<N, TWX>(buf, tw, jobs.kfs[j.job]);
-    fft_rowtile<M, TWX, C::CW, NT, true, 2>(buf, tw);
-    // even tile rows to one block of consecutive real rows, odd ones to another
+    // even tile rows go to one block of consecutive real rows, odd ones to
+    // another, straight from the transform's last step
     float* out = moved(static_cast<float*>(jobs.out[j.job]), j.by);
-    float2* o0 = reinterpret_cast<float2*>(out + real_row_q(j.row0, N) * N);
-    float2* o1 = reinterpret_cast<float2*>(out + real_row_q(j.row0 + 1, N) * N);
-    constexpr int HALF = TWX / 2 * M;
-    static_assert(HALF % NT == 0, "a parity block is whole iterations");
-#pragma unroll
-    for (int i = 0; i < 2 * HALF / NT; ++i) {
-      const int h = i * NT / HALF;  // constant per iteration
-      const int e2 = threadIdx.x + i * NT - h * HALF;
-      (h ? o1 : o0)[e2] = buf[(2 * (e2 / M) + h) * C::CW + e2 % M];
-    }
+    const RealRowOut<M> o{reinterpret_cast<float2*>(out + real_row_q(j.row0, N) * N),
+                          reinterpret_cast<float2*>(out + real_row_q(j.row0 + 1, N) * N)};
+    fft_rowtile<M, TWX, C::CW, NT, true, 2, NoPre, false, RealRowOut<M>>(buf, tw, NoPre{}, o);
     __syncthreads();
     cur ^= 1;
   }
