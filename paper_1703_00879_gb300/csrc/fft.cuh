@@ -285,8 +285,9 @@ __host__ __device__ constexpr int rowtile_pitch() {
   return ((L + Split<L>::R2 - 1 - 8 + 15) / 16) * 16 + 8;
 }
 
+// Load hook of fft_rowtile's first step: element n of row c as pre(x, c, n).
 struct NoPre {
-  __device__ __forceinline__ float2 operator()(float2 v) const { return v; }
+  __device__ __forceinline__ float2 operator()(float2 v, int, int) const { return v; }
 };
 
 // Length-L transforms of the TW rows of a row-major shared-memory tile, in
@@ -325,7 +326,7 @@ __device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const floa
         const int c = u / R2, n2 = u % R2;
         const float2* x = buf + c * CW + n2;
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) v[i][n1] = pre(x[R2 * n1]);
+        for (int n1 = 0; n1 < R1; ++n1) v[i][n1] = pre(x[R2 * n1], c, R2 * n1 + n2);
         dftR<R1, INV>(v[i]);
         if (n2 > 0) {
 #pragma unroll

@@ -915,7 +915,7 @@ constexpr int row_blocks() {
 
 struct ScaleOffset {
   float scale, offset;
-  __device__ __forceinline__ float2 operator()(float2 v) const {
+  __device__ __forceinline__ float2 operator()(float2 v, int, int) const {
     return make_float2(fmaf(v.x, scale, offset), fmaf(v.y, scale, offset));
   }
 };
@@ -1065,16 +1065,31 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
 // Screening factor eps(w) (Sec. 6.1, Sec. 6.2).  The divisions and the square
 // root use the fast intrinsics (a few ulp), well below the FP32 rounding of
 // the transforms the factor feeds.
+// p: f(R) the threshold fr_thr on |Phi_N|; nDGP the coefficient dgp_coef.
 template <int MODEL>
-__device__ __forceinline__ float screen_eps(float w, const ForceParams& fp) {
+__device__ __forceinline__ float screen_eps(float w, float p) {
   if (MODEL == 1) {
     const float aw = fabsf(w);
-    return aw > fp.fr_thr ? __fdividef(fp.fr_thr, aw) : 1.f;
+    return aw > p ? __fdividef(p, aw) : 1.f;
   } else {
-    const float u = 1.f + fp.dgp_coef * fmaxf(1.f + w, 0.f);  // >= 1
+    const float u = 1.f + p * fmaxf(1.f + w, 0.f);  // >= 1
     return __fdividef(2.f, u * rsqrtf(u) + 1.f);
   }
 }
+
+// Load hook of the forward transform of the screening x pass: element j of
+// tile row r is S = delta eps(w), w the screening field (the tile value) and
+// delta = rho / rho_bar - 1 from the staged density row (M float2 per row).
+template <int M, int MODEL>
+struct ScreenSource {
+  const float2* rho;
+  float inv_rhobar, p;
+  __device__ __forceinline__ float2 operator()(float2 w, int r, int j) const {
+    const float2 rv = rho[r * M + j];
+    const float d0 = rv.x * inv_rhobar - 1.f, d1 = rv.y * inv_rhobar - 1.f;
+    return make_float2(d0 * screen_eps<MODEL>(w.x, p), d1 * screen_eps<MODEL>(w.y, p));
+  }
+};
 
 // Screening source S = delta eps: c2r of the screening field rows, eps from the
 // field and delta from rho in the same tile, r2c.  Shared memory: twiddles, two
@@ -1128,16 +1143,10 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
     fft_rowtile_call<M, TWX, C::CW, NT, true, 2, NoPre, true>(buf, tw);
     cp_async_wait<1>();  // the density rows; the next tile's prefetch may still be in flight
     __syncthreads();
-    const float2* rv2 = reinterpret_cast<const float2*>(rr);  // row r holds N floats = M float2
-    for (int e = threadIdx.x; e < TWX * M; e += NT) {
-      const int r2 = e / M, j = e % M;
-      const float2 w = buf[r2 * C::CW + j];
-      const float2 rv = rv2[r2 * M + j];
-      const float d0 = rv.x * fp.inv_rhobar - 1.f, d1 = rv.y * fp.inv_rhobar - 1.f;
-      buf[r2 * C::CW + j] = make_float2(d0 * screen_eps<MODEL>(w.x, fp), d1 * screen_eps<MODEL>(w.y, fp));
-    }
-    __syncthreads();
-    fft_rowtile_call<M, TWX, C::CW, NT, false, 2, NoPre, true>(buf, tw);
+    // S = delta eps(w) is formed as the forward transform loads it
+    const ScreenSource<M, MODEL> src{reinterpret_cast<const float2*>(rr), fp.inv_rhobar,
+                                     MODEL == 1 ? fp.fr_thr : fp.dgp_coef};
+    fft_rowtile_call<M, TWX, C::CW, NT, false, 2, ScreenSource<M, MODEL>, true>(buf, tw, src);
     row_r2c_store<N, TWX>(buf, tw, moved(s_out, r.by), row0);
     __syncthreads();
     cur ^= 1;
