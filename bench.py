@@ -239,7 +239,9 @@ def bench_ours(args):
     avg_s = st_ms / st_n / 1e3
     achieved = st_bytes / avg_s / 1e9
     peak, peak_src = hbm_peak()
-    launches = sum(v[1] for k, v in stages.items() if k != "rho_zero")   # memset is not a kernel
+    # kernels of the profiled stages (the density memset is not a kernel) plus the
+    # one step-advance kernel that ends every step
+    launches = sum(v[1] for k, v in stages.items() if k != "rho_zero") + args.steps
     stage_report = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1], "share": v[0] / max(ms, 1e-9),
                         "GBps": (v[2] / (v[0] / v[1] / 1e3) / 1e9) if v[1] else None}
                     for k, v in stages.items() if v[1] > 0 or v[0] > 0}
