@@ -306,15 +306,12 @@ __device__ __forceinline__ void col_pipeline(Op op, const float2* __restrict__ t
 }
 
 // ---------------------------------------------------------------- plain column pass
-// out = transform of (i kfs f_n) in along the tile axis (kfs = 0: of in itself;
-// f_n the signed frequency, zero on the Nyquist row); out may alias in.
+// out = transform of in along the tile axis; out may alias in.
 template <int N, int TW, bool INV>
 struct OpCol {
-  static constexpr bool ONE_CTA = blocks_for_smem(col_smem_c(N, 1), N) < 2;
   ColGeo<N, TW> geo;
   const float2* in;
   float2* out;
-  float kfs;
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
   __device__ __forceinline__ void issue_side(int64_t) const {}
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
@@ -323,26 +320,13 @@ struct OpCol {
     geo.tile(t, o, c0, base, by);
     col_issue<N, TW, TW>(buf, 0, moved(in, by), base, geo.ra, geo.rb, c0);
   }
+  // outputs go to HBM from the last step's registers (ColOut)
   __device__ __forceinline__ void process(float2* buf, const float2* tw, int64_t t) const {
     int o, c0;
     int64_t base, by;
     geo.tile(t, o, c0, base, by);
-    if (kfs != 0.f) {
-      for (int e = threadIdx.x; e < N * TW; e += NT) {
-        const int c = e % TW, n = e / TW;
-        const float f = (n == N / 2) ? 0.f : kfs * (float)freq_index(n, N);
-        buf[n * TW + c] = cscale(cmul_i(buf[n * TW + c]), f);
-      }
-      __syncthreads();
-    }
-    if constexpr (ONE_CTA) {
-      // one CTA per SM: outputs go to HBM from the last step's registers
-      fft_tile<N, TW, TW, NT, INV, 1, TileLoad, ColOut>(
-          buf, tw, TileLoad{}, ColOut{moved(out, by) + base, geo.ra, geo.rb, N / 2 + 1 - c0});
-    } else {
-      fft_tile<N, TW, TW, NT, INV>(buf, tw);
-      col_store<N, TW, TW>(buf, 0, moved(out, by), base, geo.ra, geo.rb, c0);
-    }
+    fft_tile<N, TW, TW, NT, INV, 1, TileLoad, ColOut>(
+        buf, tw, TileLoad{}, ColOut{moved(out, by) + base, geo.ra, geo.rb, N / 2 + 1 - c0});
   }
 };
 
@@ -1264,12 +1248,12 @@ static cudaError_t launch_col(float2* data, int axis, bool inv, const float2* tw
     auto k = k_col<N, TW, true>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(OpCol<N, TW, true>{geo, data, data, 0.f}, tw, ntiles);
+    k<<<grid, NT, sm, s>>>(OpCol<N, TW, true>{geo, data, data}, tw, ntiles);
   } else {
     auto k = k_col<N, TW, false>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(OpCol<N, TW, false>{geo, data, data, 0.f}, tw, ntiles);
+    k<<<grid, NT, sm, s>>>(OpCol<N, TW, false>{geo, data, data}, tw, ntiles);
   }
   return cudaGetLastError();
 }
