@@ -352,6 +352,21 @@ struct OpYinv2 {
       return make_float2(a * v.x - b * v.y, a * v.y + b * v.x);
     }
   };
+  // Store hook: columns c < TW to the plain output, TW + c to the derivative,
+  // straight from the last step's registers.
+  struct PairOut {
+    static constexpr bool kSmem = false;
+    float2 *gp, *gd;
+    int64_t ra, rb;
+    int live;
+    __device__ __forceinline__ float2 operator()(float2 v, int n, int c, int) const {
+      const bool d = c >= TW;
+      const int cc = d ? c - TW : c;
+      if (cc < live) (d ? gd : gp)[(n >> 1) * ra + (n & 1) * rb + hcol(cc)] = v;
+      return v;
+    }
+    __device__ __forceinline__ void ready() const {}
+  };
   ColGeo<N, TW> geo;
   const float2* in;
   float2 *outp, *outd;
@@ -369,9 +384,9 @@ struct OpYinv2 {
     int o, c0;
     int64_t base, by;
     geo.tile(t, o, c0, base, by);
-    fft_tile<N, TP, TP, NT, true, 1, PairLoad>(buf, tw, PairLoad{kfs});
-    col_store<N, TW, TP>(buf, 0, moved(outp, by), base, geo.ra, geo.rb, c0);
-    col_store<N, TW, TP>(buf, 1, moved(outd, by), base, geo.ra, geo.rb, c0);
+    fft_tile<N, TP, TP, NT, true, 1, PairLoad, PairOut>(
+        buf, tw, PairLoad{kfs},
+        PairOut{moved(outp, by) + base, moved(outd, by) + base, geo.ra, geo.rb, N / 2 + 1 - c0});
   }
 };
 
@@ -457,10 +472,12 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(yinv2r_smem<N, TW>(), N)) 
       const DerivLoad<N> dl{bi, kfs};
       for (int e = threadIdx.x; e < N * TW; e += NT) bd[e] = dl(bd, e / TW, 0, e);
       __syncthreads();
-      fft_tile_call<N, TW, TW, NT, true>(bd, tw);
-      col_store<N, TW, TW>(bd, 0, moved(outd, by), base, geo.ra, geo.rb, c0);
-      fft_tile_call<N, TW, TW, NT, true>(bi, tw);
-      col_store<N, TW, TW>(bi, 0, moved(outp, by), base, geo.ra, geo.rb, c0);
+      const ColOut o{nullptr, geo.ra, geo.rb, N / 2 + 1 - c0};
+      ColOut od = o, op = o;
+      od.g = moved(outd, by) + base;
+      op.g = moved(outp, by) + base;
+      fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(bd, tw, TileLoad{}, od);
+      fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(bi, tw, TileLoad{}, op);
     }
     __syncthreads();  // both buffers are free for later prefetches
     I = F;
@@ -471,7 +488,6 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(yinv2r_smem<N, TW>(), N)) 
 // ---------------------------------------------------------------- screening field (z pass)
 template <int N, int TW, int MODEL>
 struct OpZScreenField {
-  static constexpr bool ONE_CTA = blocks_for_smem(col_smem_tw(N, TW), N) < 2;
   // Store hook of the forward transform: delta(k) out to HBM, the field's
   // multiplier (f(R): -kappa/k^2; nDGP: the Gaussian filter) applied in place.
   struct Field {
@@ -515,13 +531,8 @@ struct OpZScreenField {
     const Field f{moved(dk_out, by) + base, geo.ra, geo.rb, c0, fy * fy, fp.kf * fp.kf, fp.kappa_norm,
                   fp.R2half, fp.norm};
     fft_tile_call<N, TW, TW, NT, false, 1, TileLoad, Field>(buf, tw, TileLoad{}, f);
-    if constexpr (ONE_CTA) {
-      fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(
-          buf, tw, TileLoad{}, ColOut{moved(w_out, by) + base, geo.ra, geo.rb, N / 2 + 1 - c0});
-    } else {
-      fft_tile_call<N, TW, TW, NT, true>(buf, tw);
-      col_store<N, TW, TW>(buf, 0, moved(w_out, by), base, geo.ra, geo.rb, c0);
-    }
+    fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(
+        buf, tw, TileLoad{}, ColOut{moved(w_out, by) + base, geo.ra, geo.rb, N / 2 + 1 - c0});
   }
 };
 
@@ -632,9 +643,11 @@ struct OpZForce {
       fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(buf, tw, TileLoad{}, op);
       fft_tile_call<N, TW, TW, NT, true, 1, GradZ, ColOut>(buf, tw, grad, oz);
     } else {
-      fft_tile_call<N, TW, TW, NT, true>(buf, tw);
-      col_store<N, TW, TW>(buf, 0, moved(phi_out, by), base, geo.ra, geo.rb, c0);
-      __syncthreads();
+      const ColOut o{nullptr, geo.ra, geo.rb, N / 2 + 1 - c0};
+      ColOut op = o, oz = o;
+      op.g = moved(phi_out, by) + base;
+      oz.g = moved(phiz_out, by) + base;
+      fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(buf, tw, TileLoad{}, op);
       const TileLane<N, TW> ln(c0, iy);
 #pragma unroll 4
       for (int i = 0; i < ln.E; ++i) {
@@ -642,8 +655,7 @@ struct OpZForce {
         buf[at] = grad(buf, n, ln.c, at);
       }
       __syncthreads();
-      fft_tile_call<N, TW, TW, NT, true>(buf, tw);
-      col_store<N, TW, TW>(buf, 0, moved(phiz_out, by), base, geo.ra, geo.rb, c0);
+      fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(buf, tw, TileLoad{}, oz);
     }
   }
 };
