@@ -687,6 +687,7 @@ struct OpLptZ {
   const void *phi1, *phi2;
   float2 *o0, *o1, *o2, *o3;
   LptParams lp;
+  int tab_smem;             // 1: the (single) table row is staged in extra once per CTA
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
   __device__ __forceinline__ void issue_side(int64_t) const {}
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
@@ -711,6 +712,14 @@ struct OpLptZ {
     LptParams lp = this->lp;
     resolve(lp, by);  // no-op when resolved once for the launch
     const float4* tab = lp.row;
+    if (tab_smem) {
+      float4* st = reinterpret_cast<float4*>(extra);
+      if (t == blockIdx.x) {  // this CTA's first tile: stage the row
+        for (int i = threadIdx.x; i < lp.nk; i += NT) st[i] = tab[i];
+        __syncthreads();
+      }
+      tab = st;
+    }
     if constexpr (PREC != 0) {
       const uint32_t* rb = reinterpret_cast<const uint32_t*>(buf);
       const float sc1 = lp.scale[0], sc2 = lp.scale[1];
@@ -1395,13 +1404,17 @@ static cudaError_t launch_lpt_t(const void* p1, const void* p2, float2* o0, floa
                                 float2* o2, float2* o3, const LptParams& lp, const float2* tw,
                                 cudaStream_t s, Multi m) {
   constexpr int TW = col_tw(N, 4);
-  constexpr size_t sm = col_smem<N, 4>();
+  // one simulation at N >= 512 (one CTA per SM either way): the table row also
+  // goes to shared memory
+  const int tab_smem = (N >= 512 && !m.shift) ? 1 : 0;
+  const size_t sm = col_smem<N, 4>() + (tab_smem ? (size_t)lp.nk * sizeof(float4) : 0);
   const int64_t ntiles = col_tiles<N, TW>() * m.nb;
   auto k = k_lpt_z<N, TW, PREC>;
   unsigned grid;
   cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, sm, s>>>(OpLptZ<N, TW, PREC>{geo_z<N, TW>(m), p1, p2, o0, o1, o2, o3, lp}, tw, ntiles);
+  k<<<grid, NT, sm, s>>>(OpLptZ<N, TW, PREC>{geo_z<N, TW>(m), p1, p2, o0, o1, o2, o3, lp, tab_smem}, tw,
+                          ntiles);
   return cudaGetLastError();
 }
 
