@@ -7,9 +7,14 @@
 // every row segment of a tile is at least one whole 32-byte sector).
 //
 // Every pass is a persistent kernel (grid = SMs x resident CTAs) that walks
-// its tiles in a software pipeline: column tiles are staged with cp.async
-// into a second shared-memory buffer while the current tile is transformed;
-// row tiles prefetch the next tile into registers before the transform.
+// its tiles in a software pipeline: the next tile is staged with cp.async into
+// a second shared-memory buffer while the current tile is transformed.  The
+// half spectra use the plane-pair interleaved layout of cola_internal.h.
+//
+// Most k-space operations and output stores run inside the tile transforms,
+// through their load hook (first step) and store hook (last step), so a tile
+// makes one round trip through shared memory per transform step and outputs
+// leave for HBM from registers.
 //
 // Fusions:
 //   * the z pass of a forward transform also applies the Green's function
