@@ -167,11 +167,16 @@ KERNEL_SOURCES = ("kernels_fft.cu", "kernels_pm.cu", "kernels_ic.cu", "fft.cuh",
 
 
 def source_sha() -> str:
-    """Hash of the device-code sources (the kernels whose DRAM traffic a capture measured)."""
+    """Hash of the device-code sources (the kernels whose DRAM traffic a capture
+    measured), with // comments and blank lines left out so that a comment edit
+    keeps the hash."""
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_1703_00879_gb300", "csrc")
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(src, f), "rb").read())
+        for line in open(os.path.join(src, f), encoding="utf-8"):
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
