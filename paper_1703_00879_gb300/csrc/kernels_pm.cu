@@ -44,21 +44,18 @@ __device__ __forceinline__ Cic cic_setup(const PartParams& pp, int ix, int iy, i
   return c;
 }
 
-// Adds a0 at row[i0] and a1 at row[i1] (i1 = i0 + 1 unless the row wraps).
-// Adjacent cells inside one 16-byte group go out as a single vector atomic
-// (red.global.add.v4.f32, zeros in the other lanes).
+// Adds a0 at row[i0] and a1 at row[i1] (i1 = i0 + 1, or 0 when i0 ends the
+// row).  One vector atomic (red.global.add.v4.f32, zeros in the other lanes)
+// covers the 16-byte group of i0 and, unless i0 is the group's last cell, i1;
+// otherwise (q = 3, which includes the wrap: Nm is a multiple of 4) a scalar
+// atomic adds a1.  Every lane issues the vector atomic, so a warp runs two
+// atomic instructions per call rather than three on divergent paths.
 __device__ __forceinline__ void row_add(float* __restrict__ row, int i0, int i1, float a0, float a1) {
   const int q = i0 & 3;
-  if (i1 == i0 + 1 && q < 3) {
-    float4* p4 = reinterpret_cast<float4*>(row + (i0 - q));
-    const float4 v = q == 0 ? make_float4(a0, a1, 0.f, 0.f)
-                   : q == 1 ? make_float4(0.f, a0, a1, 0.f)
-                            : make_float4(0.f, 0.f, a0, a1);
-    atomicAdd(p4, v);
-  } else {
-    atomicAdd(row + i0, a0);
-    atomicAdd(row + i1, a1);
-  }
+  const float4 v = make_float4(q == 0 ? a0 : 0.f, q == 1 ? a0 : (q == 0 ? a1 : 0.f),
+                               q == 2 ? a0 : (q == 1 ? a1 : 0.f), q == 3 ? a0 : (q == 2 ? a1 : 0.f));
+  atomicAdd(reinterpret_cast<float4*>(row + (i0 - q)), v);
+  if (q == 3) atomicAdd(row + i1, a1);
 }
 
 __device__ __forceinline__ void cic_deposit(float* __restrict__ rho, int Nm, const Cic& c) {
