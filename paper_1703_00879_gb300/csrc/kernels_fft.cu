@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "cola_internal.h"
@@ -902,15 +903,41 @@ template <int N, int TWX>
 __device__ __forceinline__ void row_c2r_combine(float2* buf, const float2* tw, float kfs) {
   using C = RowCfg<N, TWX>;
   constexpr int M = N / 2;
-  for (int e = threadIdx.x; e < TWX * (M / 2 + 1); e += NT) {
-    const int r = e / (M / 2 + 1), k = e - r * (M / 2 + 1);
-    float2* z = buf + r * C::CW;
-    const float2 a = c2r_in<M>(z[k], k, kfs);
-    const float2 b = cconj(c2r_in<M>(z[M - k], M - k, kfs));
-    const float2 E = cadd(a, b);
-    const float2 O = cmul(cconj(tw[k]), csub(a, b));
-    z[k] = cadd(E, cmul_i(O));
-    if (k != 0 && k != M - k) z[M - k] = cadd(cconj(E), cmul_i(cconj(O)));
+  if constexpr (M >= 256) {
+    // long rows: warps take rows, lanes take k = lane, lane + 32, ... <= M/2
+    // (no division, and the derivative test hoisted out of the loop)
+    auto pairs = [&](auto deriv) {
+      constexpr bool D = decltype(deriv)::value;
+      for (int r = threadIdx.x >> 5; r < TWX; r += NT / 32) {
+        float2* z = buf + r * C::CW;
+        for (int k = threadIdx.x & 31; k <= M / 2; k += 32) {
+          float2 a = z[k], b = z[M - k];
+          if (D) {
+            a = cscale(cmul_i(a), kfs * (float)k);
+            b = k == 0 ? make_float2(0.f, 0.f) : cscale(cmul_i(b), kfs * (float)(M - k));
+          }
+          if (k == 0) a.y = b.y = 0.f;  // X[0], X[M] real
+          b = cconj(b);
+          const float2 E = cadd(a, b);
+          const float2 O = cmul(cconj(tw[k]), csub(a, b));
+          z[k] = cadd(E, cmul_i(O));
+          if (k != 0 && k != M - k) z[M - k] = cadd(cconj(E), cmul_i(cconj(O)));
+        }
+      }
+    };
+    if (kfs != 0.f) pairs(std::true_type{});
+    else pairs(std::false_type{});
+  } else {
+    for (int e = threadIdx.x; e < TWX * (M / 2 + 1); e += NT) {
+      const int r = e / (M / 2 + 1), k = e - r * (M / 2 + 1);
+      float2* z = buf + r * C::CW;
+      const float2 a = c2r_in<M>(z[k], k, kfs);
+      const float2 b = cconj(c2r_in<M>(z[M - k], M - k, kfs));
+      const float2 E = cadd(a, b);
+      const float2 O = cmul(cconj(tw[k]), csub(a, b));
+      z[k] = cadd(E, cmul_i(O));
+      if (k != 0 && k != M - k) z[M - k] = cadd(cconj(E), cmul_i(cconj(O)));
+    }
   }
   __syncthreads();
 }
