@@ -192,13 +192,15 @@ def ncu_traffic(stage: str, workload: str):
     return e.get("dram_bytes_per_launch")
 
 
-def workload_config(run, world: int):
+def workload_config(run, world: int, lpt_fast: bool = False):
     m = run.model
     grav = {0: "LCDM", 1: f"f(R) Hu-Sawicky n=1 |fR0|={m.fR0:g}", 2: f"nDGP rcH0={m.rcH0:g}"}[m.kind]
     if m.screening:
         grav += " + " + ("chameleon" if m.kind == 1 else "Vainshtein R=%g Mpc/h Gaussian" % m.R_smooth) + " screening"
     return {"workload": run.name, "particles": f"{run.Np}^3", "mesh": f"{run.Nmesh}^3",
-            "box_mpc_h": run.Lbox, "gravity": grav, "growth": "scale-dependent per-k tables (1024 log-k bins)",
+            "box_mpc_h": run.Lbox, "gravity": grav,
+            "growth": ("k-independent growth, LPT fields from stored Psi1, Psi2 (cola_set_lpt_fast)" if lpt_fast
+                       else "scale-dependent per-k tables (1024 log-k bins)"),
             "z_ini": run.z_ini, "steps_in_run": run.nsteps, "seed": run.seed,
             "l2": f"inputs larger than L2: each mesh array {run.Nmesh**3 * 4 / 1e9:.1f} GB",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
@@ -215,7 +217,7 @@ def bench_ours(args):
     base = WORKLOADS[args.workload]
     run = replica_run(base, rank, args.warmup + args.steps)
     stream = torch.cuda.current_stream()
-    sim = pkg.Simulation(run)
+    sim = pkg.Simulation(run, lpt_fast=args.lpt_fast)
     sim.step(args.warmup)
     torch.cuda.synchronize()
     barrier(dist)
@@ -267,11 +269,11 @@ def bench_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(run, world),
+            "config": workload_config(run, world, args.lpt_fast),
             "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback", "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": ncu_traffic(name, args.workload)},
+                         "traffic": None if args.lpt_fast else ncu_traffic(name, args.workload)},
             "step_ledger": {"algorithmic_GB_per_step": step_bytes / 1e9,
                             "achieved_GBps": step_bytes / (max_ms / args.steps / 1e3) / 1e9,
                             "frac_of_peak": step_bytes / (max_ms / args.steps / 1e3) / 1e9 / peak},
@@ -297,7 +299,7 @@ def bench_e2e(args, run, pkg, dist, world):
     barrier(dist)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim = pkg.Simulation(e2e_run)
+    sim = pkg.Simulation(e2e_run, lpt_fast=args.lpt_fast)
     sim.step(args.steps)
     pos, vel = sim.snapshot()
     k, pk, nm = sim.pk()
@@ -307,9 +309,9 @@ def bench_e2e(args, run, pkg, dist, world):
     torch.cuda.empty_cache()
     dt = reduce_max(t1 - t0, dist)
     P = run.Np ** 3
-    # tables [nsteps+1][nk] float4 x2, force parameters (56 B) and time integrals (12 B) per step
+    # tables [nsteps+2][nk] float4 x2, force parameters (56 B) and time integrals (12 B) per step
     # (twiddles are already resident from the timed run)
-    h2d = (2 * (e2e_run.nsteps + 1) * e2e_run.nk_table * 16 + e2e_run.nsteps * (56 + 12)) / args.steps
+    h2d = (2 * (e2e_run.nsteps + 2) * e2e_run.nk_table * 16 + e2e_run.nsteps * (56 + 12)) / args.steps
     d2h = (pos.nbytes + vel.nbytes + k.nbytes + pk.nbytes + nm.nbytes) / args.steps
     return {"value": whole_job_throughput(P * args.steps, world, dt), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -474,6 +476,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="big")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lpt-fast", action="store_true",
+                    help="scale-independent LPT fast path (models whose growth does not depend on k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble", action="store_true", help="batched ensemble benchmark instead")
     ap.add_argument("--ensemble-size", type=int, default=256)

@@ -115,6 +115,19 @@ int cola_init(const cola_config* cfg, cola_alloc_fn alloc, cola_free_fn free_fn,
  * non-positive fR0/rcH0/R_smooth where needed), COLA_ESTATE (after cola_ic). */
 int cola_set_model(cola_ctx* ctx, const cola_model* model);
 
+/* Scale-independent LPT fast path (on = 1; 0 restores the default).  When the
+ * growth of the model does not depend on k (LCDM; nDGP; any model with
+ * scale_dependent = 0) the LPT fields of every step are c1 Psi1 + c2 Psi2 of
+ * the real-space 2LPT displacements Psi_i = grad phi_i (Sec. 4.1 with
+ * D(k, a) = D(a)): Psi1 and Psi2 are transformed once, at cola_ic, and kept
+ * per particle, and each step forms its drift and kick fields in the particle
+ * kernels instead of running the six LPT inverse transforms.  The results
+ * equal those of the default path up to FP32 rounding.  COLA_F_LPT_DISP /
+ * COLA_F_LPT_ACC export the last step's fields formed the same way.  Must
+ * follow cola_set_model and precede cola_ic.  Errors: COLA_EINVAL (the growth
+ * depends on k), COLA_ESTATE (no model yet, or after cola_ic). */
+int cola_set_lpt_fast(cola_ctx* ctx, int32_t on);
+
 /* Initial conditions (Sec. 3, Sec. 4.1, App. A): Philox white noise on the Np^3
  * lattice, delta(k) with P_ini(k), phi1 = delta/k^2, phi2 from the 2LPT
  * source (Eq. lcdm2lpt); stores phi1(k), phi2(k) (the k-space seed fields),

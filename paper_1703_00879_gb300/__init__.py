@@ -81,6 +81,7 @@ _SIGS = {
     "cola_batch_pk": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     "cola_step_many": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "cola_ic_many": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "cola_set_lpt_fast": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cola_pk_async": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cola_pk_ready": (ctypes.c_int, [_P]),
     "cola_pk_result": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -199,10 +200,11 @@ def _torch_allocator(dev: int):
 
 
 class Simulation:
-    """One libcola context: cola_init + cola_set_model (+ cola_ic) on the current torch stream."""
+    """One libcola context: cola_init + cola_set_model (+ cola_set_lpt_fast) (+ cola_ic) on the
+    current torch stream."""
 
     def __init__(self, run, seed_precision: int = 0, ic: bool = True, phi=None, stream=None,
-                 torch_alloc: bool = True):
+                 torch_alloc: bool = True, lpt_fast: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libcola needs a CUDA GPU; none is visible")
@@ -224,6 +226,8 @@ class Simulation:
         self.P = run.Np ** 3
         self.M = run.Nmesh ** 3
         _check(L.cola_set_model(self.ctx, ctypes.byref(make_model(run.model))), self.ctx)
+        if lpt_fast:
+            _check(L.cola_set_lpt_fast(self.ctx, 1), self.ctx)
         if phi is not None:
             self.ic_from_potentials(*phi)
         elif ic:

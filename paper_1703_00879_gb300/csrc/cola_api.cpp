@@ -28,6 +28,9 @@ struct cola_ctx {
   cola_config cfg{};
   cola_model model{};
   bool model_set = false, ic_done = false, have_force = false, have_lpt = false;
+  // scale-independent LPT fast path: lr[0..2] hold Psi1 and lr[3..5] Psi2 from
+  // the ICs on, and the per-step LPT transforms are skipped
+  bool lpt_fast = false;
   cudaStream_t st = nullptr;
   cola_alloc_fn alloc = nullptr;
   cola_free_fn freef = nullptr;
@@ -651,6 +654,20 @@ EHDev eh_dev(const cola_ctx* ctx) {
   return eh;
 }
 
+// LPT mixing parameters of the fast path: coefficients from row row0 (+ the
+// device step when add_step) of the table (vtab when vel); Psi2 in lr[3..5].
+LptMix lpt_mix_of(const cola_ctx* ctx, int row0, int add_step, bool vel) {
+  LptMix x{};
+  x.hdr = ctx->hdr;
+  for (int d = 0; d < 3; ++d) x.q2[d] = ctx->lr[3 + d];
+  x.on = 1;
+  x.vel = vel ? 1 : 0;
+  x.row0 = row0;
+  x.add_step = add_step;
+  x.nk = ctx->nk;
+  return x;
+}
+
 // Initial conditions (Sec. 3, Sec. 4.1, App. A) of every simulation of g on
 // g.lead->st: white noise from each one's seed, phi1 = delta/k^2, the 2LPT phi2
 // (skipped when `potentials`: phi1 and phi2 are already in place), the
@@ -686,10 +703,25 @@ int ic_group(const Group& g, bool potentials) {
       CK(seed_quantise(N, ctx->phi[f], ctx->seedq[f], ctx->cfg.seed_precision, ctx->hdr, f, st, m));
     }
   }
+  const PartParams pp = part_params(ctx);
+  if (ctx->lpt_fast) {
+    // Psi1, Psi2 once (table row nsteps+1), then the particles and A_LPT at a_ini
+    // as combinations with row 0's coefficients
+    CHECK_RC(run_lpt(ctx, 0, ctx->cfg.nsteps + 1, false, m));
+    const LptMix mix = lpt_mix_of(ctx, 0, 0, false);
+    CK(ic_particles(ctx->P, ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->s[0], ctx->s[1], ctx->s[2],
+                    ctx->v[0], ctx->v[1], ctx->v[2], st, m, mix));
+    CK(zero_f32(ctx->rho, ctx->M, st, m));
+    CK(part_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->rho, ctx->P, st, m));
+    CHECK_RC(force_group(g, ctx->a[0], true, true));
+    CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
+                        ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[0], ctx->lr[1], ctx->lr[2],
+                        ctx->F[0], ctx->F[1], ctx->F[2], StepDt{nullptr, 0.f, 0.f}, ctx->P, st, m, mix));
+    return COLA_OK;
+  }
   CHECK_RC(run_lpt(ctx, 0, 0, false, m));
   CK(ic_particles(ctx->P, ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->s[0], ctx->s[1], ctx->s[2],
                   ctx->v[0], ctx->v[1], ctx->v[2], st, m));
-  const PartParams pp = part_params(ctx);
   CK(zero_f32(ctx->rho, ctx->M, st, m));
   CK(part_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->rho, ctx->P, st, m));
   CHECK_RC(force_group(g, ctx->a[0], true, true));
@@ -744,21 +776,26 @@ int enqueue_group_step(const Group& g, int n) {
   const PartParams pp = part_params(ctx);
   const double Pb = (double)ctx->P, Mb = (double)ctx->M;
   const StepDt dt{ctx->hdr, 0.f, 0.f};
-  CHECK_RC(run_lpt(ctx, 0, 1, true, m));
+  // fast path: the step's LPT fields are combinations of Psi1, Psi2 formed in
+  // the particle kernels (row 1 + step), no LPT transforms
+  const bool fast = ctx->lpt_fast;
+  const LptMix mix = fast ? lpt_mix_of(ctx, 1, 1, false) : LptMix{};
+  if (!fast) CHECK_RC(run_lpt(ctx, 0, 1, true, m));
   cudaEvent_t e = prof_begin(ctx);
   CK(zero_f32(ctx->rho, ctx->M, ctx->st, m));
   prof_end(ctx, ST_RHO_ZERO, e, 1, m.nb * 4.0 * Mb);
   e = prof_begin(ctx);
   CK(part_drift_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                         ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[0], ctx->lr[1],
-                        ctx->lr[2], ctx->rho, dt, ctx->P, ctx->st, m));
-  prof_end(ctx, ST_DRIFT_DEPOSIT, e, 1, m.nb * (72.0 * Pb + 8.0 * Mb));
+                        ctx->lr[2], ctx->rho, dt, ctx->P, ctx->st, m, mix));
+  prof_end(ctx, ST_DRIFT_DEPOSIT, e, 1, m.nb * ((fast ? 84.0 : 72.0) * Pb + 8.0 * Mb));
   CHECK_RC(force_group(g, ctx->a[n + 1], true));
   e = prof_begin(ctx);
+  const int ka = fast ? 0 : 3;  // A_LPT, or Psi1 mixed with Psi2
   CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
-                      ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[3], ctx->lr[4],
-                      ctx->lr[5], ctx->F[0], ctx->F[1], ctx->F[2], dt, ctx->P, ctx->st, m));
-  prof_end(ctx, ST_GATHER_KICK, e, 1, m.nb * (60.0 * Pb + 12.0 * Mb));
+                      ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[ka], ctx->lr[ka + 1],
+                      ctx->lr[ka + 2], ctx->F[0], ctx->F[1], ctx->F[2], dt, ctx->P, ctx->st, m, mix));
+  prof_end(ctx, ST_GATHER_KICK, e, 1, m.nb * ((fast ? 72.0 : 60.0) * Pb + 12.0 * Mb));
   CK(step_advance(ctx->hdr, ctx->st, m));
   return COLA_OK;
 }
@@ -892,7 +929,9 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
   }
   const cola_config& cfg = ctx->cfg;
   const int nk = ctx->nk, ns = cfg.nsteps;
-  const size_t tab_b = (size_t)(ns + 1) * nk * sizeof(float4);
+  // rows 0..ns as documented on SimHeader, plus row ns+1 = (1, 0, 0, 1): the
+  // Psi1 / Psi2 pass of the scale-independent fast path
+  const size_t tab_b = (size_t)(ns + 2) * nk * sizeof(float4);
   const size_t fp_off = 2 * tab_b, fp_b = ((size_t)ns * sizeof(ForceParams) + 255) / 256 * 256;
   const size_t dt_off = fp_off + fp_b, bytes = dt_off + 3 * (size_t)ns * sizeof(float);
   // kind 1: (every configuration field but the seed and the seed precision, the model)
@@ -920,6 +959,10 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
         vtab[i] = make_float4((float)g.dD1[i], (float)g.dD2[i], 0.f, 0.f);
       }
     }
+    for (int j = 0; j < nk; ++j) {
+      tab[(size_t)(ns + 1) * nk + j] = make_float4(1.f, 0.f, 0.f, 1.f);
+      vtab[(size_t)(ns + 1) * nk + j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     ForceParams* fp = reinterpret_cast<ForceParams*>(h + fp_off);
     float* dt = reinterpret_cast<float*>(h + dt_off);
     for (int n = 0; n < ns; ++n) {
@@ -944,6 +987,27 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
   ctx->hh.seed_target = ctx->cfg.seed_precision == COLA_SEED_FP16 ? 32768.f : 1.f;
   ctx->hh.eh = eh_dev(ctx);
   CK(set_header(ctx->hdr, ctx->hh, ctx->st));
+  return COLA_OK;
+}
+
+int cola_set_lpt_fast(cola_ctx* ctx, int32_t on) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!ctx->model_set) return fail(ctx, COLA_ESTATE, "cola_set_lpt_fast before cola_set_model");
+  if (ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_set_lpt_fast after cola_ic");
+  if (on) {
+    // only for growth that does not depend on k: every table column equal
+    Growth g;
+    growth_for(ctx->cfg, ctx->model, g, nullptr, nullptr, nullptr);
+    const std::vector<double>* cols[6] = {&g.D1, &g.dD1, &g.ddD1, &g.D2, &g.dD2, &g.ddD2};
+    for (const auto* c : cols)
+      for (int n = 0; n < g.na; ++n) {
+        const double ref = (*c)[(size_t)n * g.nk];
+        for (int j = 1; j < g.nk; ++j)
+          if (std::abs((*c)[(size_t)n * g.nk + j] - ref) > 1e-12 * std::max(1.0, std::abs(ref)))
+            return fail(ctx, COLA_EINVAL, "cola_set_lpt_fast: the growth of this model depends on k");
+      }
+  }
+  ctx->lpt_fast = on != 0;
   return COLA_OK;
 }
 
@@ -991,12 +1055,15 @@ int cola_snapshot(cola_ctx* ctx, float* pos, float* vel, int32_t where) {
   if (where != COLA_HOST && where != COLA_DEVICE) return fail(ctx, COLA_EINVAL, "bad where");
   if (!pos && !vel) return COLA_OK;
   const size_t bytes = (size_t)ctx->P * 3 * sizeof(float);
-  if (vel) CHECK_RC(run_lpt(ctx, 1, ctx->step, false));
+  // LPT velocity dPsi/dtau at a_step: the velocity-table transform, or on the
+  // fast path dD1 Psi1 + dD2 Psi2 formed in the snapshot kernel
+  const LptMix mix = ctx->lpt_fast ? lpt_mix_of(ctx, ctx->step, 0, true) : LptMix{};
+  if (vel && !ctx->lpt_fast) CHECK_RC(run_lpt(ctx, 1, ctx->step, false));
   const PartParams pp = part_params(ctx);
   const float vscale = (float)(100.0 / ctx->a[ctx->step]);
   if (where == COLA_DEVICE) {
     CK(part_snapshot(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
-                     ctx->lr[0], ctx->lr[1], ctx->lr[2], vscale, pos, vel, ctx->P, ctx->st));
+                     ctx->lr[0], ctx->lr[1], ctx->lr[2], vscale, pos, vel, ctx->P, ctx->st, mix));
     return COLA_OK;
   }
   // host: stage through the (step-scratch) mesh force buffers when they are big enough
@@ -1004,7 +1071,7 @@ int cola_snapshot(cola_ctx* ctx, float* pos, float* vel, int32_t where) {
   if ((pos && !tp.p) || (vel && !tv.p)) return fail(ctx, COLA_ENOMEM, "snapshot staging allocation failed");
   CK(part_snapshot(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                    ctx->lr[0], ctx->lr[1], ctx->lr[2], vscale, static_cast<float*>(tp.p),
-                   static_cast<float*>(tv.p), ctx->P, ctx->st));
+                   static_cast<float*>(tv.p), ctx->P, ctx->st, mix));
   if (pos) CK(cudaMemcpyAsync(pos, tp.p, bytes, cudaMemcpyDeviceToHost, ctx->st));
   if (vel) CK(cudaMemcpyAsync(vel, tv.p, bytes, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
@@ -1156,6 +1223,16 @@ int cola_export(cola_ctx* ctx, int32_t which, void* dst, int32_t where) {
     case COLA_F_LPT_ACC: {
       if (!ctx->have_lpt) return fail(ctx, COLA_ESTATE, "no LPT fields yet");
       const int o = which == COLA_F_LPT_DISP ? 0 : 3;
+      if (ctx->lpt_fast) {
+        // the fields of the last step (row `step`; row 0 before the first step),
+        // formed from Psi1, Psi2 into the idle LPT spectrum buffers
+        float* tmp[3] = {reinterpret_cast<float*>(ctx->lc[0]), reinterpret_cast<float*>(ctx->lc[1]),
+                         reinterpret_cast<float*>(ctx->lc[2])};
+        const float* psi1[3] = {ctx->lr[0], ctx->lr[1], ctx->lr[2]};
+        CK(lpt_mix(ctx->P, psi1, lpt_mix_of(ctx, ctx->step, 0, false), o == 3 ? 1 : 0, tmp, ctx->st));
+        for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * pb, tmp[c], pb, where));
+        return COLA_OK;
+      }
       for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * pb, ctx->lr[o + c], pb, where));
       return COLA_OK;
     }
@@ -1263,7 +1340,8 @@ static int bfail(cola_batch* b, int code, const std::string& m) {
 // counts may differ: those are read through each simulation's header).
 static bool same_shape(const cola_ctx* a, const cola_ctx* c) {
   return a->cfg.Np == c->cfg.Np && a->cfg.Nmesh == c->cfg.Nmesh && a->cfg.Lbox == c->cfg.Lbox &&
-         a->cfg.nk_table == c->cfg.nk_table && a->cfg.seed_precision == c->cfg.seed_precision;
+         a->cfg.nk_table == c->cfg.nk_table && a->cfg.seed_precision == c->cfg.seed_precision &&
+         a->lpt_fast == c->lpt_fast;
 }
 
 static cola_batch_plan normal_plan(const cola_batch* b, cola_batch_plan p) {

@@ -71,8 +71,9 @@ struct EHDev {
 struct SimHeader {
   const ForceParams* dfp;  // [nsteps]: force parameters at a_{n+1}
   const float* ddt;        // [nsteps][3]: half kick, drift, half kick time integrals
-  const float4* tab;       // [nsteps+1][nk] LPT reweight table (row 0: a_ini, row n+1: step n)
-  const float4* vtab;      // [nsteps+1][nk] velocity table
+  const float4* tab;       // [nsteps+2][nk] LPT reweight table (row 0: a_ini, row n+1: step n,
+                           // row nsteps+1: (1, 0, 0, 1), the Psi1 / Psi2 pass)
+  const float4* vtab;      // [nsteps+2][nk] velocity table (last row unused)
   int step;                // steps done
   float seed_scale[2];     // dequantisation scales of the 16-bit seeds (written on the device)
   float seed_target;       // 16-bit seeds: the largest |component| maps to this
@@ -185,16 +186,35 @@ struct StepDt {
   const SimHeader* hdr;
   float dtk, dtd;
 };
+// Scale-independent LPT fields (the fast path for k-independent growth): the
+// LPT fields of a step are c1 Psi1 + c2 Psi2 of the real-space fields
+// Psi_i = grad phi_i kept per particle (Sec. 4.1 with D(k, a) = D(a)).  When
+// `on`, a kernel reads the coefficients from row row0 (+ the simulation's step
+// when add_step) of its growth table (tab, or vtab when vel) at k index 0:
+// (c1, c2) = .xy for the drift, (e1, e2) = .zw for the kick, (dD1, dD2) = .xy
+// of vtab for the snapshot velocity.  The kernel's own LPT field pointers then
+// hold Psi1 and q2 holds Psi2; hdr and q2 move with each simulation's shift.
+struct LptMix {
+  const SimHeader* hdr;
+  const float* q2[3];
+  int on, vel, row0, add_step, nk;
+};
+// Growth-table coefficients of an LptMix for the simulation moved by `by`.
+__device__ __forceinline__ float4 mix_coeffs(const LptMix& x, int64_t by) {
+  const SimHeader* h = moved(x.hdr, by);
+  const int row = x.row0 + (x.add_step ? h->step : 0);
+  return (x.vel ? h->vtab : h->tab)[(size_t)row * x.nk];
+}
 cudaError_t part_drift_deposit(const PartParams& pp, float* sx, float* sy, float* sz, float* vx,
                                float* vy, float* vz, const float* ax, const float* ay,
                                const float* az, const float* dpx, const float* dpy,
                                const float* dpz, float* rho, StepDt dt, int64_t P,
-                               cudaStream_t s, Multi m = {});
+                               cudaStream_t s, Multi m = {}, LptMix mix = {});
 cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float* sy,
                              const float* sz, float* vx, float* vy, float* vz, float* ax,
                              float* ay, float* az, const float* Ax, const float* Ay,
                              const float* Az, const float* Fx, const float* Fy, const float* Fz,
-                             StepDt dt, int64_t P, cudaStream_t s, Multi m = {});
+                             StepDt dt, int64_t P, cudaStream_t s, Multi m = {}, LptMix mix = {});
 // hdr->step += 1 (end of a step)
 cudaError_t step_advance(SimHeader* hdr, cudaStream_t s, Multi m = {});
 // hdr = v (one simulation), except the seed scales, which keep their device values
@@ -207,7 +227,11 @@ cudaError_t zero_f32(float* p, int64_t n, cudaStream_t s, Multi m = {});
 cudaError_t part_snapshot(const PartParams& pp, const float* sx, const float* sy, const float* sz,
                           const float* vx, const float* vy, const float* vz, const float* lx,
                           const float* ly, const float* lz, float vscale, float* pos, float* vel,
-                          int64_t P, cudaStream_t s);
+                          int64_t P, cudaStream_t s, LptMix mix = {});
+// out_d = c1 Psi1_d + c2 Psi2_d (acc = 0) or e1 Psi1_d + e2 Psi2_d (acc = 1) for
+// one simulation, coefficients as LptMix (psi1: the Psi1 fields)
+cudaError_t lpt_mix(int64_t P, const float* const* psi1, const LptMix& mix, int acc, float* const* out,
+                    cudaStream_t s);
 cudaError_t pos_deposit(int Nm, float cellscale, const float* pos, int64_t n, float* rho,
                         cudaStream_t s);
 // acc_stride > 0: simulation b accumulates into acc + b acc_stride (acc not
@@ -234,7 +258,7 @@ cudaError_t ic_source(int64_t n, const float* hxx, const float* hyy, const float
 cudaError_t ic_phi2(int N, float2* c, float kf, cudaStream_t s, Multi m = {});
 cudaError_t ic_particles(int64_t P, const float* px, const float* py, const float* pz, float* sx,
                          float* sy, float* sz, float* vx, float* vy, float* vz,
-                         cudaStream_t s, Multi m = {});
+                         cudaStream_t s, Multi m = {}, LptMix mix = {});
 // pack a dense [N][N][N/2+1] half spectrum into / out of the padded layout
 cudaError_t half_pack(int N, const float2* dense, float2* padded, cudaStream_t s);
 cudaError_t half_unpack(int N, const float2* padded, float2* dense, cudaStream_t s);

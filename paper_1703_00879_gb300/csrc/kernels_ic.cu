@@ -165,7 +165,8 @@ __global__ void k_ic_particles(int64_t P, const float* __restrict__ px,
                                const float* __restrict__ py, const float* __restrict__ pz,
                                float* __restrict__ sx, float* __restrict__ sy,
                                float* __restrict__ sz, float* __restrict__ vx,
-                               float* __restrict__ vy, float* __restrict__ vz, Multi mm) {
+                               float* __restrict__ vy, float* __restrict__ vz, Multi mm,
+                               LptMix mix) {
   const int64_t i = (int64_t)blockIdx.x * NTI + threadIdx.x;
   if (i >= P) return;
   const int64_t by = shift_of(mm, blockIdx.y);
@@ -178,9 +179,16 @@ __global__ void k_ic_particles(int64_t P, const float* __restrict__ px,
   vx = moved(vx, by);
   vy = moved(vy, by);
   vz = moved(vz, by);
-  sx[i] = px[i];
-  sy[i] = py[i];
-  sz[i] = pz[i];
+  if (mix.on) {  // s = D1 Psi1 + D2 Psi2 at a_ini
+    const float4 cf = mix_coeffs(mix, by);
+    sx[i] = cf.x * px[i] + cf.y * moved(mix.q2[0], by)[i];
+    sy[i] = cf.x * py[i] + cf.y * moved(mix.q2[1], by)[i];
+    sz[i] = cf.x * pz[i] + cf.y * moved(mix.q2[2], by)[i];
+  } else {
+    sx[i] = px[i];
+    sy[i] = py[i];
+    sz[i] = pz[i];
+  }
   vx[i] = 0.f;
   vy[i] = 0.f;
   vz[i] = 0.f;
@@ -281,8 +289,29 @@ cudaError_t ic_phi2(int N, float2* c, float kf, cudaStream_t s, Multi m) {
 
 cudaError_t ic_particles(int64_t P, const float* px, const float* py, const float* pz, float* sx,
                          float* sy, float* sz, float* vx, float* vy, float* vz,
-                         cudaStream_t s, Multi m) {
-  k_ic_particles<<<dim3(blocks_for(P), m.nb), NTI, 0, s>>>(P, px, py, pz, sx, sy, sz, vx, vy, vz, m);
+                         cudaStream_t s, Multi m, LptMix mix) {
+  k_ic_particles<<<dim3(blocks_for(P), m.nb), NTI, 0, s>>>(P, px, py, pz, sx, sy, sz, vx, vy, vz, m,
+                                                           mix);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_lpt_mix(int64_t P, const float* __restrict__ p0, const float* __restrict__ p1,
+                          const float* __restrict__ p2, LptMix mix, int acc, float* __restrict__ o0,
+                          float* __restrict__ o1, float* __restrict__ o2) {
+  const int64_t i = (int64_t)blockIdx.x * NTI + threadIdx.x;
+  if (i >= P) return;
+  const float4 cf = mix_coeffs(mix, 0);
+  const float a = acc ? cf.z : cf.x, b = acc ? cf.w : cf.y;
+  o0[i] = a * p0[i] + b * mix.q2[0][i];
+  o1[i] = a * p1[i] + b * mix.q2[1][i];
+  o2[i] = a * p2[i] + b * mix.q2[2][i];
+}
+}  // namespace
+
+cudaError_t lpt_mix(int64_t P, const float* const* psi1, const LptMix& mix, int acc, float* const* out,
+                    cudaStream_t s) {
+  k_lpt_mix<<<blocks_for(P), NTI, 0, s>>>(P, psi1[0], psi1[1], psi1[2], mix, acc, out[0], out[1], out[2]);
   return cudaGetLastError();
 }
 

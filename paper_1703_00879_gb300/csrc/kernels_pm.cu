@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(NTP) k_drift_deposit(
     float* __restrict__ vx, float* __restrict__ vy, float* __restrict__ vz,
     const float* __restrict__ ax, const float* __restrict__ ay, const float* __restrict__ az,
     const float* __restrict__ dpx, const float* __restrict__ dpy,
-    const float* __restrict__ dpz, float* __restrict__ rho, StepDt dt, int64_t P, Multi m) {
+    const float* __restrict__ dpz, float* __restrict__ rho, StepDt dt, int64_t P, Multi m,
+    LptMix mix) {
   const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
   if (p >= P) return;
   const int64_t by = shift_of(m, blockIdx.y);
@@ -141,12 +142,19 @@ __global__ void __launch_bounds__(NTP) k_drift_deposit(
     dtk = h->ddt[3 * h->step];
     dtd = h->ddt[3 * h->step + 1];
   }
+  float lx = dpx[p], ly = dpy[p], lz = dpz[p];
+  if (mix.on) {  // Delta Psi = c1 Psi1 + c2 Psi2
+    const float4 cf = mix_coeffs(mix, by);
+    lx = cf.x * lx + cf.y * moved(mix.q2[0], by)[p];
+    ly = cf.x * ly + cf.y * moved(mix.q2[1], by)[p];
+    lz = cf.x * lz + cf.y * moved(mix.q2[2], by)[p];
+  }
   const float ux = vx[p] + ax[p] * dtk;
   const float uy = vy[p] + ay[p] * dtk;
   const float uz = vz[p] + az[p] * dtk;
-  const float nx = sx[p] + ux * dtd + dpx[p];
-  const float ny = sy[p] + uy * dtd + dpy[p];
-  const float nz = sz[p] + uz * dtd + dpz[p];
+  const float nx = sx[p] + ux * dtd + lx;
+  const float ny = sy[p] + uy * dtd + ly;
+  const float nz = sz[p] + uz * dtd + lz;
   vx[p] = ux;
   vy[p] = uy;
   vz[p] = uz;
@@ -169,7 +177,7 @@ __global__ void __launch_bounds__(NTP) k_gather_kick(
     float* __restrict__ vz, float* __restrict__ ax, float* __restrict__ ay,
     float* __restrict__ az, const float* __restrict__ Ax, const float* __restrict__ Ay,
     const float* __restrict__ Az, const float* __restrict__ Fx, const float* __restrict__ Fy,
-    const float* __restrict__ Fz, StepDt dt, int64_t P, Multi m) {
+    const float* __restrict__ Fz, StepDt dt, int64_t P, Multi m, LptMix mix) {
   const int64_t p0 = (int64_t)blockIdx.x * NTP * PPT + threadIdx.x;
   const int64_t by = shift_of(m, blockIdx.y);
   sx = moved(sx, by);
@@ -215,11 +223,19 @@ __global__ void __launch_bounds__(NTP) k_gather_kick(
       gz[u] = cic_interp(Fz, pp.Nm, c);
     }
   }
+  float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (mix.on) cf = mix_coeffs(mix, by);
 #pragma unroll
   for (int u = 0; u < PPT; ++u) {
     const int64_t p = p0 + u * NTP;
     if (p < P) {
-      const float ex = gx[u] - Ax[p], ey = gy[u] - Ay[p], ez = gz[u] - Az[p];
+      float lx = Ax[p], ly = Ay[p], lz = Az[p];
+      if (mix.on) {  // A_LPT = e1 Psi1 + e2 Psi2
+        lx = cf.z * lx + cf.w * moved(mix.q2[0], by)[p];
+        ly = cf.z * ly + cf.w * moved(mix.q2[1], by)[p];
+        lz = cf.z * lz + cf.w * moved(mix.q2[2], by)[p];
+      }
+      const float ex = gx[u] - lx, ey = gy[u] - ly, ez = gz[u] - lz;
       ax[p] = ex;
       ay[p] = ey;
       az[p] = ez;
@@ -235,7 +251,7 @@ __global__ void __launch_bounds__(NTP) k_snapshot(
     const float* __restrict__ sz, const float* __restrict__ vx, const float* __restrict__ vy,
     const float* __restrict__ vz, const float* __restrict__ lx, const float* __restrict__ ly,
     const float* __restrict__ lz, float vscale, float* __restrict__ pos,
-    float* __restrict__ vel, int64_t P) {
+    float* __restrict__ vel, int64_t P, LptMix mix) {
   const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
   if (p >= P) return;
   int li[3];
@@ -252,9 +268,15 @@ __global__ void __launch_bounds__(NTP) k_snapshot(
     }
   }
   if (vel) {
-    vel[p * 3 + 0] = (vx[p] + lx[p]) * vscale;
-    vel[p * 3 + 1] = (vy[p] + ly[p]) * vscale;
-    vel[p * 3 + 2] = (vz[p] + lz[p]) * vscale;
+    float l[3] = {lx[p], ly[p], lz[p]};
+    if (mix.on) {  // dPsi/dtau = dD1 Psi1 + dD2 Psi2
+      const float4 cf = mix_coeffs(mix, 0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) l[d] = cf.x * l[d] + cf.y * mix.q2[d][p];
+    }
+    vel[p * 3 + 0] = (vx[p] + l[0]) * vscale;
+    vel[p * 3 + 1] = (vy[p] + l[1]) * vscale;
+    vel[p * 3 + 2] = (vz[p] + l[2]) * vscale;
   }
 }
 
@@ -370,9 +392,9 @@ cudaError_t part_drift_deposit(const PartParams& pp, float* sx, float* sy, float
                                float* vy, float* vz, const float* ax, const float* ay,
                                const float* az, const float* dpx, const float* dpy,
                                const float* dpz, float* rho, StepDt dt, int64_t P,
-                               cudaStream_t s, Multi m) {
+                               cudaStream_t s, Multi m, LptMix mix) {
   k_drift_deposit<<<dim3(blocks_for(P), m.nb), NTP, 0, s>>>(pp, sx, sy, sz, vx, vy, vz, ax, ay, az,
-                                                            dpx, dpy, dpz, rho, dt, P, m);
+                                                            dpx, dpy, dpz, rho, dt, P, m, mix);
   return cudaGetLastError();
 }
 
@@ -380,18 +402,18 @@ cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float*
                              const float* sz, float* vx, float* vy, float* vz, float* ax,
                              float* ay, float* az, const float* Ax, const float* Ay,
                              const float* Az, const float* Fx, const float* Fy, const float* Fz,
-                             StepDt dt, int64_t P, cudaStream_t s, Multi m) {
+                             StepDt dt, int64_t P, cudaStream_t s, Multi m, LptMix mix) {
   k_gather_kick<<<dim3((unsigned)((P + NTP * PPT - 1) / (NTP * PPT)), m.nb), NTP, 0, s>>>(
-      pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, Fx, Fy, Fz, dt, P, m);
+      pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, Fx, Fy, Fz, dt, P, m, mix);
   return cudaGetLastError();
 }
 
 cudaError_t part_snapshot(const PartParams& pp, const float* sx, const float* sy, const float* sz,
                           const float* vx, const float* vy, const float* vz, const float* lx,
                           const float* ly, const float* lz, float vscale, float* pos, float* vel,
-                          int64_t P, cudaStream_t s) {
+                          int64_t P, cudaStream_t s, LptMix mix) {
   k_snapshot<<<blocks_for(P), NTP, 0, s>>>(pp, sx, sy, sz, vx, vy, vz, lx, ly, lz, vscale, pos,
-                                           vel, P);
+                                           vel, P, mix);
   return cudaGetLastError();
 }
 
