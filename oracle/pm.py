@@ -8,8 +8,9 @@ Test infrastructure only.  Follows:
   and the total force is -grad(Phi_N + phi).  In Fourier space
   Phi_tot(k) = -kappa [delta(k) + C S(k) k^2/(k^2 + a^2 m^2)] / k^2 with
   S = FFT[delta eps].  f(R) (Sec. 6.1): C = 1/3, m = m(a), eps from Phi_N.
-  nDGP (Sec. 6.2 and App. B): C = 1/(3 beta), m = 0, eps from the Gaussian-smoothed
-  density, W(k) = exp(-k^2 R^2/2).  Screening off: S = delta (so G_eff = mu).
+  nDGP (Sec. 6.2 and App. B): C = 1/(3 beta), m = 0, eps from the smoothed density,
+  with App. B's three windows of x = kR: Gaussian exp(-x^2/2), top-hat
+  3 (sin x - x cos x)/x^3, sharp-k Theta(1 - x).  Screening off: S = delta (so G_eff = mu).
 * Readings (silent in the paper): cloud-in-cell assignment with mesh points at
   integer multiples of the cell size; continuous Green's function -1/k^2;
   spectral gradient i k with the Nyquist plane of that axis zeroed; no CIC
@@ -20,8 +21,16 @@ prod_i sinc^4(pi n_i/N), linear bins [ (b+1/2) k_F, (b+3/2) k_F ), modes weighte
 once on the kx = 0 and kx = N/2 planes and twice elsewhere, no shot-noise
 subtraction.
 
+Readings: the top-hat window below x = 1/2 uses its Taylor series (the closed
+form cancels there); the sharp-k cut compares (kR)^2 with 1 in single
+precision with the operation order of the GPU kernel (k^2 = fl(kf^2) |n|^2,
+x^2 = 2 k^2 fl(R^2/2)), so that both sides keep the same modes.
+
 Pins (tests/test_oracle_pm.py): CIC mass conservation and hand-computed
 weights; a single Fourier mode of density gives F = -kappa A k sin(k.x)/|k|^2;
+the top-hat window equals the Fourier transform of a uniform sphere by radial
+quadrature, its series meets the closed form at x = 1/2, and W(pi) = 3/pi^2;
+the sharp-k window keeps exactly the modes with kR <= 1;
 screening off multiplies the single-mode force by mu(k, a); zero net force;
 the P(k) of a single mode lands in its bin with amplitude A^2 L^3/4 after deconvolution.
 """
@@ -88,6 +97,36 @@ def fifth_force_coupling(model, a: float, Om: float):
     return 0.0, 0.0
 
 
+def tophat_window(x):
+    """Fourier transform of a normalised uniform sphere, W(x) = 3 (sin x - x cos x)/x^3, x = kR;
+    the Taylor series 1 - x^2/10 + x^4/280 - x^6/15120 + x^8/1330560 below x = 1/2."""
+    x = np.asarray(x, dtype=np.float64)
+    xs = np.where(x < 0.5, 1.0, x)
+    closed = 3.0 * (np.sin(xs) - xs * np.cos(xs)) / xs**3
+    x2 = x * x
+    series = 1.0 - x2 / 10.0 + x2**2 / 280.0 - x2**3 / 15120.0 + x2**4 / 1330560.0
+    return np.where(x < 0.5, series, closed)
+
+
+def smoothing_window(N: int, L: float, R: float, kind: int):
+    """W(k) on the [z][y][x/2+1] half spectrum for the Vainshtein density (App. B):
+    0 Gaussian exp(-k^2 R^2/2), 1 top-hat, 2 sharp-k (1 for kR <= 1, else 0)."""
+    k2 = k2_grid(N, L)
+    if kind == 0:
+        return np.exp(-0.5 * k2 * R * R)
+    if kind == 1:
+        return tophat_window(np.sqrt(k2) * R)
+    if kind == 2:
+        # the cut decided in float32 with the kernel's operation order (see Readings)
+        kf = 2.0 * np.pi / L
+        n2 = np.rint(k2 / (kf * kf)).astype(np.int64)
+        kf32 = np.float32(kf)
+        k2_32 = (kf32 * kf32) * n2.astype(np.float32)
+        x2 = (np.float32(2.0) * k2_32) * np.float32(0.5 * R * R)
+        return (x2 <= np.float32(1.0)).astype(np.float64)
+    raise ValueError("smoothing window: 0 Gaussian, 1 top-hat, 2 sharp-k")
+
+
 def screening_factor(model, delta_k: np.ndarray, N: int, L: float, a: float, Om: float):
     """eps(x) on the mesh: chameleon from Phi_N (Sec. 6.1) or Vainshtein from delta_R (Sec. 6.2)."""
     k2 = k2_grid(N, L)
@@ -98,7 +137,7 @@ def screening_factor(model, delta_k: np.ndarray, N: int, L: float, a: float, Om:
         PhiN_metric = PhiN / (a * a * C_LIGHT**2)
         return models.eps_chameleon(PhiN_metric, float(models.phi_crit_fr(a, Om, model.fR0)))
     if model.kind == models.NDGP:
-        W = np.exp(-0.5 * k2 * model.R_smooth**2)
+        W = smoothing_window(N, L, model.R_smooth, getattr(model, "filter", 0))
         deltaR = irfft3(W * delta_k, N)
         return models.eps_vainshtein(models.vainshtein_x(1.0 + deltaR, a, Om, model.rcH0))
     raise ValueError("no screening for this model")

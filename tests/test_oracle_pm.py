@@ -168,6 +168,60 @@ def test_screening_limits_single_mode():
     assert eps0 < 1.0
 
 
+# ------------------------------------------------------------------ App. B smoothing windows
+def test_tophat_window_is_the_sphere_transform():
+    """W(k) = (1/V) int_sphere e^{ik.r} d^3r = (3/R^3) int_0^R r^2 sin(kr)/(kr) dr, by quadrature,
+    on both sides of the series/closed-form switch at kR = 1/2."""
+    from scipy.integrate import quad
+    R = 2.5
+    for k in [1e-4, 0.03, 0.15, 0.199, 0.2, 0.201, 0.6, 1.7, 4.0, 11.0]:
+        ref = 3.0 / R**3 * quad(lambda r: r * np.sin(k * r) / k, 0.0, R, limit=200, epsabs=1e-15)[0]
+        assert float(pm.tophat_window(k * R)) == pytest.approx(ref, rel=1e-11, abs=1e-14)
+    assert float(pm.tophat_window(np.pi)) == pytest.approx(3.0 / np.pi**2, rel=1e-14)
+    assert float(pm.tophat_window(0.0)) == 1.0
+
+
+def test_smoothing_windows_on_the_mesh():
+    N, L, R = 16, 100.0, 9.0
+    kf = 2 * np.pi / L
+    n = np.fft.fftfreq(N, d=1.0 / N)
+    nz, ny, nx = np.meshgrid(n, n, np.arange(N // 2 + 1), indexing="ij")
+    kk = kf * np.sqrt(nx**2 + ny**2 + nz**2)
+    W0 = pm.smoothing_window(N, L, R, 0)
+    assert np.allclose(W0, np.exp(-0.5 * (kk * R) ** 2), rtol=1e-12, atol=0)
+    W1 = pm.smoothing_window(N, L, R, 1)
+    i = (1, 2, 3)
+    x = kk[i] * R
+    assert W1[i] == pytest.approx(3 * (np.sin(x) - x * np.cos(x)) / x**3, rel=1e-13)
+    assert W1[0, 0, 0] == 1.0
+    # sharp-k keeps exactly the lattice vectors with |n|^2 <= (L/(2 pi R))^2 = 3.13 (no mode near the cut)
+    W2 = pm.smoothing_window(N, L, R, 2)
+    assert set(np.unique(W2)) == {0.0, 1.0}
+    kept = sorted(tuple(int(v) for v in t) for t in np.argwhere(W2 == 1.0))
+    brute = sorted((iz, iy, ix) for iz in range(N) for iy in range(N) for ix in range(N // 2 + 1)
+                   if n[iz] ** 2 + n[iy] ** 2 + ix**2 <= 3)
+    assert kept == brute and len(brute) == 1 + 5 + 8 + 4  # |n|^2 = 0, 1, 2, 3 with n_x >= 0
+    with pytest.raises(ValueError):
+        pm.smoothing_window(N, L, R, 3)
+
+
+def test_sharp_k_screening_of_a_short_mode_is_uniform():
+    """A mode with kR > 1 is cut from delta_R, so eps = eps(x(1)) everywhere at any amplitude and the
+    force is (1 + eps0/(3 beta)) Newton; the Gaussian window leaves it partly in delta_R."""
+    N, L, a, Om = 16, 64.0, 0.5, 0.3
+    A = 0.5
+    rho, s, kv = _mode_density(N, L, (0, 3, 0), A)
+    k2 = kv @ kv
+    R = 2.0 / np.sqrt(k2)
+    b = float(M.dgp_beta(a, Om, 1.0))
+    eps0 = float(M.eps_vainshtein(M.vainshtein_x(1.0, a, Om, 1.0)))
+    newton = -kappa(a, Om) * A * kv[1] * s / k2
+    F = pm.force_mesh(rho, 1.0, N, L, a, Om, Model(kind=NDGP, rcH0=1.0, screening=1, R_smooth=R, filter=2))
+    assert np.allclose(F[1], (1 + eps0 / (3 * b)) * newton, rtol=1e-12, atol=1e-14)
+    G = pm.force_mesh(rho, 1.0, N, L, a, Om, Model(kind=NDGP, rcH0=1.0, screening=1, R_smooth=R, filter=0))
+    assert np.abs(G[1] - F[1]).max() > 1e-6 * np.abs(F[1]).max()
+
+
 def test_zero_net_force_newtonian():
     N, L = 16, 32.0
     pos = random_positions(3000, L, 5)

@@ -36,8 +36,9 @@ class Model:
     fR0: float = 0.0          # |f_R0| of the Hu-Sawicky n=1 model
     rcH0: float = 0.0         # r_c H_0 of nDGP
     screening: int = 0        # 1 = approximate screening on
-    R_smooth: float = 1.0     # Gaussian smoothing radius for Vainshtein screening [Mpc/h]
+    R_smooth: float = 1.0     # smoothing radius for Vainshtein screening [Mpc/h]
     scale_dependent: int = 1  # 1 = per-k growth tables, 0 = LCDM growth factors
+    filter: int = 0           # Vainshtein smoothing window: 0 Gaussian, 1 top-hat, 2 sharp-k
 
 
 @dataclass(frozen=True)
