@@ -10,7 +10,8 @@ Follows the paper:
   evaluated at the orthogonal configuration k1 = k2 = k/sqrt(2) used by the
   approximate second-order growth (Eq. fofrapprox); the second term vanishes there.
 * General {m(a), beta(a)} chameleon (App. C): mu, gamma_2^E and Phi_crit, used
-  here to pin the f(R) special case.
+  here to pin the f(R) special case, and the symmetron model of App. C:
+  beta = beta_* sqrt(u), m^2 = m_*^2 u, u = 1 - (a_*/a)^3, both 0 before a_*.
 * Screening factors (Sec. 6): chameleon eps = min(1, |3 f_R(a) / (2 Phi_N)|);
   Vainshtein eps = 2 (sqrt(1+x) - 1)/x with x = 8 (r_c H0)^2 Omega_m (rho/rho_bar) / (9 beta^2).
 
@@ -23,12 +24,16 @@ Readings of the paper taken here (each listed in the design notes):
 * Phi_N in the chameleon factor is the metric potential: the code potential
   (a^2 times it, in (Mpc/h)^2 H0^2) divided by a^2 c^2.
 * (k/(aH))^2 in the f(R) gamma_2^E uses H = H(a).
+* Symmetron Phi_crit is the App. C integral from a_* with Phi_crit(a_*) = 0; it
+  equals 3 Omega_m H0^2/(a_*^3 m_*^2), twice the printed closed form (the same
+  integral gives Sec. 6.1's 3 |f_R(a)|/2 for f(R), so the integral is taken).
 
 Units: k in h/Mpc; m^2 in (h/Mpc)^2, using H0/c = 1/C_LIGHT h/Mpc.
 
 Pins (tests/test_oracle_models.py): mu limits k->0, k->inf and k = a m;
 f(R) mu and gamma_2^E against the App. C {m, beta} forms with beta = 1/sqrt(6);
-Phi_crit quadrature against the closed form; nDGP beta(1) closed form; the
+Phi_crit quadrature against the closed form, for f(R) and the symmetron; symmetron
+mu limits and gamma_2^E with the analytic dm^2/da; nDGP beta(1) closed form; the
 Vainshtein factor against a numerical solution of the spherical field equation;
 nDGP gamma_2 coefficient against the Vainshtein coefficient through the same
 spherical reduction.
@@ -40,7 +45,7 @@ from scipy import integrate
 
 from .background import C_LIGHT, E, dlnE_da
 
-LCDM, FOFR, NDGP = 0, 1, 2
+LCDM, FOFR, NDGP, SYMM = 0, 1, 2, 3
 H0_OVER_C = 1.0 / C_LIGHT   # h/Mpc
 
 
@@ -103,12 +108,15 @@ def dgp_gamma2E(a, Om, rcH0, cos2=0.0):
 
 # ---------------------------------------------------------------- model dispatch
 def mu(model, k, a, Om):
-    """mu(k,a) for a workloads.Model-like record (kind, fR0, rcH0)."""
+    """mu(k,a) for a workloads.Model-like record (kind, fR0, rcH0, beta_star, m_star, a_star)."""
     k = np.asarray(k, dtype=np.float64)
     if model.kind == FOFR:
         return fr_mu(k, a, Om, model.fR0)
     if model.kind == NDGP:
         return np.full_like(k, dgp_mu(a, Om, model.rcH0))
+    if model.kind == SYMM:
+        m2_fn, beta_fn = symm_fns(model)
+        return mb_mu(k, a, m2_fn(a), beta_fn(a))
     return np.ones_like(k)
 
 
@@ -124,6 +132,10 @@ def gamma2_orth(model, k, a, Om):
         return fr_gamma2E(k, q, q, a, Om, model.fR0)
     if model.kind == NDGP:
         return np.full_like(k, dgp_gamma2E(a, Om, model.rcH0, 0.0))
+    if model.kind == SYMM:
+        q = k / np.sqrt(2.0)
+        m2_fn, beta_fn = symm_fns(model)
+        return mb_gamma2E(k, q, q, a, Om, m2_fn, beta_fn)
     return np.zeros_like(k)
 
 
@@ -188,3 +200,50 @@ def mb_phi_crit(a, a_ini, phicrit_ini, Om, m2_fn, beta_fn):
                             epsabs=0.0, epsrel=1e-13, limit=400)
     return phicrit_ini + 9.0 * Om / (2.0 * beta_fn(a)) * val
 
+
+# ---------------------------------------------------------------- symmetron (App. C)
+def symm_u(a, a_star):
+    """1 - (a_*/a)^3, and 0 before a_* (no fifth force there)."""
+    a = np.asarray(a, dtype=np.float64)
+    return np.where(a > a_star, 1.0 - (a_star / a) ** 3, 0.0)
+
+
+def symm_beta(a, beta_star, a_star):
+    """beta(a) = beta_* sqrt(1 - (a_*/a)^3)."""
+    return beta_star * np.sqrt(symm_u(a, a_star))
+
+
+def symm_m2(a, m_star, a_star):
+    """m^2(a) = m_*^2 (1 - (a_*/a)^3) in (h/Mpc)^2; m_star is m_*/H0."""
+    return (m_star * H0_OVER_C) ** 2 * symm_u(a, a_star)
+
+
+def symm_fns(model):
+    """(m^2(a), beta(a)) of a symmetron record (beta_star, m_star = m_*/H0, a_star)."""
+    return (lambda a: symm_m2(a, model.m_star, model.a_star),
+            lambda a: symm_beta(a, model.beta_star, model.a_star))
+
+
+def phi_crit(model, a, Om):
+    """Critical metric potential of the chameleon-type factor at a.
+
+    f(R): 3 |f_R(a)| / 2 (Sec. 6.1).  Symmetron: the App. C integral from a_* (where
+    Phi_crit starts at 0), by quadrature after a' = a_* + t^2; 0 before a_*.
+    """
+    if model.kind == FOFR:
+        return float(phi_crit_fr(a, Om, model.fR0))
+    if model.kind == SYMM:
+        if a <= model.a_star:
+            return 0.0
+        # integrand beta/(m^2/H0^2 a'^4) = beta_* /(m_*^2/H0^2 sqrt(u) a'^4), u = 1 - (a_*/a')^3, which
+        # goes as (a' - a_*)^(-1/2); with a' = a_* + t^2, u = t^2 (a'^2 + a' a_* + a_*^2)/a'^3 and
+        # 2 t dt / sqrt(u) is smooth
+        s = model.a_star
+
+        def f(t):
+            x = s + t * t
+            return 2.0 * model.beta_star / (model.m_star**2 * x**4 * np.sqrt((x * x + x * s + s * s) / x**3))
+
+        val, _ = integrate.quad(f, 0.0, np.sqrt(a - s), epsabs=0.0, epsrel=1e-13, limit=400)
+        return float(9.0 * Om / (2.0 * symm_beta(a, model.beta_star, s)) * val)
+    raise ValueError("no chameleon-type screening for this model")

@@ -8,6 +8,7 @@ Test infrastructure only.  Follows:
   and the total force is -grad(Phi_N + phi).  In Fourier space
   Phi_tot(k) = -kappa [delta(k) + C S(k) k^2/(k^2 + a^2 m^2)] / k^2 with
   S = FFT[delta eps].  f(R) (Sec. 6.1): C = 1/3, m = m(a), eps from Phi_N.
+  Symmetron (App. C): C = 2 beta(a)^2, m = m(a), eps from Phi_N with the App. C Phi_crit.
   nDGP (Sec. 6.2 and App. B): C = 1/(3 beta), m = 0, eps from the smoothed density,
   with App. B's three windows of x = kR: Gaussian exp(-x^2/2), top-hat
   3 (sin x - x cos x)/x^3, sharp-k Theta(1 - x).  Screening off: S = delta (so G_eff = mu).
@@ -94,6 +95,9 @@ def fifth_force_coupling(model, a: float, Om: float):
         return 1.0 / 3.0, a * a * float(models.fr_m2(a, Om, model.fR0))
     if model.kind == models.NDGP:
         return 1.0 / (3.0 * float(models.dgp_beta(a, Om, model.rcH0))), 0.0
+    if model.kind == models.SYMM:
+        m2_fn, beta_fn = models.symm_fns(model)
+        return 2.0 * float(beta_fn(a)) ** 2, a * a * float(m2_fn(a))
     return 0.0, 0.0
 
 
@@ -130,12 +134,12 @@ def smoothing_window(N: int, L: float, R: float, kind: int):
 def screening_factor(model, delta_k: np.ndarray, N: int, L: float, a: float, Om: float):
     """eps(x) on the mesh: chameleon from Phi_N (Sec. 6.1) or Vainshtein from delta_R (Sec. 6.2)."""
     k2 = k2_grid(N, L)
-    if model.kind == models.FOFR:
+    if model.kind in (models.FOFR, models.SYMM):
         inv_k2 = np.zeros_like(k2)
         inv_k2[k2 > 0] = 1.0 / k2[k2 > 0]
         PhiN = irfft3(-kappa(a, Om) * delta_k * inv_k2, N)          # code potential
         PhiN_metric = PhiN / (a * a * C_LIGHT**2)
-        return models.eps_chameleon(PhiN_metric, float(models.phi_crit_fr(a, Om, model.fR0)))
+        return models.eps_chameleon(PhiN_metric, models.phi_crit(model, a, Om))
     if model.kind == models.NDGP:
         W = smoothing_window(N, L, model.R_smooth, getattr(model, "filter", 0))
         deltaR = irfft3(W * delta_k, N)

@@ -73,6 +73,49 @@ def test_phi_crit_integral_matches_closed_form():
     assert M.phi_crit_fr(1.0, Om, fR0) == pytest.approx(1.5e-5, rel=1e-14)
 
 
+def test_symmetron_phi_crit_integral_closed_form():
+    """App. C symmetron: with u = 1 - (a_*/a)^3 the integrand is beta_* H0^2/(m_*^2 a^4 sqrt(u)), so the
+    integral is 2 sqrt(u)/(3 a_*^3) beta_* H0^2/m_*^2 and Phi_crit = 3 Omega_m H0^2/(a_*^3 m_*^2) for
+    every a > a_*: twice the value printed for the symmetron (the reading taken here, since the same
+    integral reproduces Sec. 6.1's 3 |f_R(a)|/2 for f(R))."""
+    from workloads import SYMM_A
+    Om = 0.3
+    want = 3.0 * Om / (SYMM_A.a_star**3 * SYMM_A.m_star**2)
+    for a in (0.5001, 0.55, 0.8, 1.0):
+        assert M.phi_crit(SYMM_A, a, Om) == pytest.approx(want, rel=1e-9)
+    assert M.phi_crit(SYMM_A, 0.4, Om) == 0.0
+    printed = 3.0 * Om / (2.0 * SYMM_A.a_star**3) / SYMM_A.m_star**2
+    assert want == pytest.approx(2.0 * printed, rel=1e-15)
+
+
+def test_symmetron_mu_and_gamma2():
+    """mu = 1 + 2 beta^2 k^2/(k^2 + a^2 m^2): 1 at k -> 0 and before a_*, 1 + 2 beta(a)^2 at k -> inf,
+    1 + beta^2 at k = a m; gamma_2^E with dm^2/da = 3 m_*^2 a_*^3 / a^4 > 0 is positive and
+    vanishes before a_*."""
+    from workloads import SYMM_A
+    Om = 0.3
+    a = 0.8
+    b2 = SYMM_A.beta_star**2 * (1 - (SYMM_A.a_star / a) ** 3)
+    m = SYMM_A.m_star * M.H0_OVER_C * np.sqrt(1 - (SYMM_A.a_star / a) ** 3)
+    mu = M.mu(SYMM_A, np.array([1e-9, a * m, 1e9]), a, Om)
+    assert mu[0] == pytest.approx(1.0, abs=1e-12)
+    assert mu[1] == pytest.approx(1.0 + b2, rel=1e-14)
+    assert mu[2] == pytest.approx(1.0 + 2 * b2, rel=1e-12)
+    assert np.all(M.mu(SYMM_A, np.logspace(-3, 2, 7), 0.45, Om) == 1.0)
+    k = np.logspace(-2, 1, 5)
+    g = M.gamma2_orth(SYMM_A, k, a, Om)
+    assert np.all(g > 0)
+    # the same expression with the analytic derivative of m^2
+    h0 = M.H0_OVER_C
+    m2 = m * m
+    dm2 = 3 * (SYMM_A.m_star * h0) ** 2 * SYMM_A.a_star**3 / a**4
+    H = h0 * bg.E(a, Om)
+    Pi = lambda q: (q / (a * h0)) ** 2 + m2 / h0**2  # noqa: E731
+    ref = m2 * dm2 * b2 * Om * k**2 / (2 * h0**4 * Pi(k) * Pi(k / np.sqrt(2)) ** 2 * a**4 * H**2)
+    assert np.allclose(g, ref, rtol=1e-7)
+    assert np.all(M.gamma2_orth(SYMM_A, k, 0.45, Om) == 0.0)
+
+
 def test_ndgp_beta_today():
     # beta(1) = 1 + 2 rcH0 (1 - Omega_m/2)  (E(1) = 1, dlnE/da(1) = -3 Om/2)
     assert M.dgp_beta(1.0, 0.3, 1.0) == pytest.approx(2.7, rel=1e-14)

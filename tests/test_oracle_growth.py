@@ -39,6 +39,21 @@ def test_eds_fR_limits_are_powerlaws():
     assert np.allclose(D1[:, 1], _eds_powerlaw(4.0 / 3.0, a / a[0]), rtol=1e-7)
 
 
+def test_eds_symmetron_limits_are_powerlaws():
+    """Symmetron (App. C) in EdS with a_* far before a_i: k -> 0 gives D = a/a_i; k -> inf gives
+    the mu = 1 + 2 beta_*^2 power law; with a_* after today the model never switches on."""
+    from workloads import SYMM
+    a = np.linspace(0.05, 1.0, 9)
+    k = np.array([1e-9, 1e6])
+    m = Model(kind=SYMM, beta_star=0.5, m_star=3000.0, a_star=1e-4)
+    g = growth.solve_growth(m, 1.0, a, k)
+    assert np.allclose(g["D1"][:, 0], a / a[0], rtol=1e-9)
+    assert np.allclose(g["D1"][:, 1], _eds_powerlaw(1.5, a / a[0]), rtol=1e-7)
+    late = growth.solve_growth(Model(kind=SYMM, beta_star=1.0, m_star=3000.0, a_star=2.0), 1.0, a, k)
+    assert np.allclose(late["D1"], (a / a[0])[:, None], rtol=1e-10)
+    assert np.allclose(late["D2"], -3.0 / 7.0 * ((a / a[0]) ** 2)[:, None], rtol=1e-10)
+
+
 def test_lcdm_growing_mode_integral():
     """LCDM: D(a)/D(1) equals E(a) int_0^a da/(a E)^3 normalised at a = 1."""
     Om = 0.3

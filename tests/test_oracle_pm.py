@@ -1,4 +1,6 @@
 """Pins of the oracle's ICs (Sec. 3.2), PM force (Sec. 2, App. B) and P(k) estimator."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -166,6 +168,34 @@ def test_screening_limits_single_mode():
     assert np.allclose(F[1], (1 + eps0 / (3 * b)) * newton, rtol=1e-5, atol=1e-6 * np.abs(newton).max())
     # screening with eps == 1 everywhere is the unscreened model (App. B vs Sec. 5)
     assert eps0 < 1.0
+
+
+def test_symmetron_single_mode_force_and_screening():
+    """App. C symmetron through the App. B field equation: C = 2 beta^2, a^2 m^2 from m(a); a small
+    mode feels mu(k, a) Newton, a large one is screened towards Newton, and before a_* there is
+    no fifth force at all."""
+    from workloads import SYMM_A
+    N, L, Om = 16, 64.0, 0.3
+    m_off = dataclasses.replace(SYMM_A, screening=0)
+    for a in (0.45, 0.8):
+        rho, s, kv = _mode_density(N, L, (1, 2, 0), 1e-2)
+        k2 = kv @ kv
+        mu = float(M.mu(SYMM_A, np.sqrt(k2), a, Om))
+        assert (mu == 1.0) == (a < SYMM_A.a_star)
+        F = pm.force_mesh(rho, 1.0, N, L, a, Om, m_off)
+        assert np.allclose(F[0], -mu * kappa(a, Om) * 1e-2 * kv[0] * s / k2, atol=1e-14, rtol=1e-12)
+    a = 0.8
+    for A, screened in [(1e-4, False), (1e2, True)]:
+        rho, s, kv = _mode_density(N, L, (1, 0, 0), A)
+        k2 = kv @ kv
+        F = pm.force_mesh(rho, 1.0, N, L, a, Om, SYMM_A)
+        newton = -kappa(a, Om) * A * kv[0] * s / k2
+        mu = float(M.mu(SYMM_A, np.sqrt(k2), a, Om))
+        ratio = np.max(np.abs(F[0])) / np.max(np.abs(newton))
+        if screened:
+            assert 1.0 < ratio < 1.0 + 0.05 * (mu - 1.0)
+        else:
+            assert ratio == pytest.approx(mu, rel=1e-8)
 
 
 # ------------------------------------------------------------------ App. B smoothing windows

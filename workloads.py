@@ -18,7 +18,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # Model kinds (same integer codes as the C ABI).
-LCDM, FOFR, NDGP = 0, 1, 2
+LCDM, FOFR, NDGP, SYMM = 0, 1, 2, 3
 
 
 @dataclass(frozen=True)
@@ -39,6 +39,9 @@ class Model:
     R_smooth: float = 1.0     # smoothing radius for Vainshtein screening [Mpc/h]
     scale_dependent: int = 1  # 1 = per-k growth tables, 0 = LCDM growth factors
     filter: int = 0           # Vainshtein smoothing window: 0 Gaussian, 1 top-hat, 2 sharp-k
+    beta_star: float = 0.0    # symmetron coupling beta_* (App. C)
+    m_star: float = 0.0       # symmetron mass m_*/H0 (range c/m_* = 2997.92458/m_star Mpc/h)
+    a_star: float = 0.0       # symmetron symmetry-breaking scale factor a_*
 
 
 @dataclass(frozen=True)
@@ -73,6 +76,8 @@ class Run:
 F5 = Model(kind=FOFR, fR0=1e-5, screening=1)
 F5_NOSCREEN = Model(kind=FOFR, fR0=1e-5, screening=0)
 NDGP1 = Model(kind=NDGP, rcH0=1.0, screening=1, R_smooth=1.0)
+# symmetron with beta_* = 1, a_* = 0.5 and a range c/m_* of 1 Mpc/h
+SYMM_A = Model(kind=SYMM, beta_star=1.0, m_star=2997.92458, a_star=0.5, screening=1)
 LCDM_MODEL = Model()
 
 # The five workloads of the hot-path scope.
