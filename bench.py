@@ -194,9 +194,11 @@ def ncu_traffic(stage: str, workload: str):
 
 def workload_config(run, world: int, lpt_fast: bool = False):
     m = run.model
-    grav = {0: "LCDM", 1: f"f(R) Hu-Sawicky n=1 |fR0|={m.fR0:g}", 2: f"nDGP rcH0={m.rcH0:g}"}[m.kind]
+    grav = {0: "LCDM", 1: f"f(R) Hu-Sawicky n=1 |fR0|={m.fR0:g}", 2: f"nDGP rcH0={m.rcH0:g}",
+            3: f"symmetron beta*={m.beta_star:g} m*/H0={m.m_star:g} a*={m.a_star:g}"}[m.kind]
     if m.screening:
-        grav += " + " + ("chameleon" if m.kind == 1 else "Vainshtein R=%g Mpc/h Gaussian" % m.R_smooth) + " screening"
+        win = ("Gaussian", "top-hat", "sharp-k")[getattr(m, "filter", 0)]
+        grav += " + " + ("chameleon" if m.kind in (1, 3) else "Vainshtein R=%g Mpc/h %s" % (m.R_smooth, win)) + " screening"
     return {"workload": run.name, "particles": f"{run.Np}^3", "mesh": f"{run.Nmesh}^3",
             "box_mpc_h": run.Lbox, "gravity": grav,
             "growth": ("k-independent growth, LPT fields from stored Psi1, Psi2 (cola_set_lpt_fast)" if lpt_fast

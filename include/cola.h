@@ -55,7 +55,7 @@ enum {
 };
 
 /* Model kinds. */
-enum { COLA_LCDM = 0, COLA_FOFR = 1, COLA_NDGP = 2 };
+enum { COLA_LCDM = 0, COLA_FOFR = 1, COLA_NDGP = 2, COLA_SYMM = 3 };
 
 /* Where a caller-owned buffer lives. */
 enum { COLA_HOST = 0, COLA_DEVICE = 1 };
@@ -87,13 +87,24 @@ typedef struct {
 
 /* Gravity model (Sec. 5, Sec. 6, App. B). */
 typedef struct {
-  int32_t kind;            /* COLA_LCDM, COLA_FOFR (Hu-Sawicky n = 1), COLA_NDGP */
+  int32_t kind;            /* COLA_LCDM, COLA_FOFR (Hu-Sawicky n = 1), COLA_NDGP, COLA_SYMM */
   double fR0;              /* |f_R0| (f(R) only, > 0) */
   double rcH0;             /* r_c H0 (nDGP only, > 0) */
   int32_t screening;       /* 1: approximate screening of the fifth force (Sec. 6) */
-  int32_t filter;          /* smoothing window of the Vainshtein density: 0 = Gaussian */
+  int32_t filter;          /* smoothing window of the Vainshtein density (App. B), x = kR:
+                              0 Gaussian exp(-x^2/2), 1 top-hat 3 (sin x - x cos x)/x^3,
+                              2 sharp-k (1 for x <= 1, else 0; the cut decided in single
+                              precision); any other value fails with COLA_EINVAL */
   double R_smooth;         /* smoothing radius [Mpc/h] (nDGP screening) */
   int32_t scale_dependent; /* 1: per-k growth D(k,a) (Sec. 4); 0: LCDM growth factors */
+  /* Symmetron, the App. C {m(a), beta(a)} model with chameleon-type screening:
+     beta(a) = beta_star sqrt(u), m^2(a) = (m_star H0)^2 u, u = 1 - (a_star / a)^3,
+     both 0 for a <= a_star.  Fifth force C = 2 beta^2 with range 1/m;
+     eps = min(1, Phi_crit / |Phi_N|) with Phi_crit = 3 Omega_m / (a_star^3 m_star^2),
+     the App. C integral from a_star. */
+  double beta_star;        /* coupling beta at late times, > 0 (symmetron only) */
+  double m_star;           /* mass at late times over H0, > 0 (symmetron only); range 2997.92458 / m_star Mpc/h */
+  double a_star;           /* symmetry-breaking scale factor in (0, 1] (symmetron only) */
 } cola_model;
 
 /* Creates a context: validates the configuration, allocates every device

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libcola.so")
 
 COLA_OK, COLA_EINVAL, COLA_ENOMEM, COLA_ECUDA, COLA_ESTATE, COLA_ETIMEOUT = 0, -1, -2, -3, -4, -5
-COLA_LCDM, COLA_FOFR, COLA_NDGP = 0, 1, 2
+COLA_LCDM, COLA_FOFR, COLA_NDGP, COLA_SYMM = 0, 1, 2, 3
 COLA_HOST, COLA_DEVICE = 0, 1
 COLA_F_DISP, COLA_F_DV, COLA_F_ACC, COLA_F_RHO, COLA_F_DELTAK = 0, 1, 2, 3, 4
 COLA_F_FORCE, COLA_F_PHI1, COLA_F_PHI2, COLA_F_LPT_DISP, COLA_F_LPT_ACC = 5, 6, 7, 8, 9
@@ -42,7 +42,8 @@ class cola_config(ctypes.Structure):
 class cola_model(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("fR0", ctypes.c_double), ("rcH0", ctypes.c_double),
                 ("screening", ctypes.c_int32), ("filter", ctypes.c_int32), ("R_smooth", ctypes.c_double),
-                ("scale_dependent", ctypes.c_int32)]
+                ("scale_dependent", ctypes.c_int32), ("beta_star", ctypes.c_double),
+                ("m_star", ctypes.c_double), ("a_star", ctypes.c_double)]
 
 
 class cola_batch_plan(ctypes.Structure):
@@ -135,8 +136,9 @@ def make_config(run) -> cola_config:
 
 
 def make_model(m) -> cola_model:
-    return cola_model(int(m.kind), float(m.fR0), float(m.rcH0), int(m.screening), 0,
-                      float(m.R_smooth), int(m.scale_dependent))
+    return cola_model(int(m.kind), float(m.fR0), float(m.rcH0), int(m.screening), int(getattr(m, "filter", 0)),
+                      float(m.R_smooth), int(m.scale_dependent), float(getattr(m, "beta_star", 0.0)),
+                      float(getattr(m, "m_star", 0.0)), float(getattr(m, "a_star", 0.0)))
 
 
 def cola_host_growth(run):

@@ -241,12 +241,15 @@ int validate_cfg(const cola_config* cfg, cola_ctx* c) {
 
 int validate_model(const cola_model* m, cola_ctx* c) {
   if (!m) return fail(c, COLA_EINVAL, "model is NULL");
-  if (m->kind < 0 || m->kind > 2) return fail(c, COLA_EINVAL, "unknown model kind");
+  if (m->kind < 0 || m->kind > 3) return fail(c, COLA_EINVAL, "unknown model kind");
+  if (m->kind == COLA_SYMM && !(m->beta_star > 0 && m->m_star > 0 && m->a_star > 0 && m->a_star <= 1))
+    return fail(c, COLA_EINVAL, "symmetron needs beta_star > 0, m_star > 0 and 0 < a_star <= 1");
   if (m->kind == COLA_FOFR && !(m->fR0 > 0)) return fail(c, COLA_EINVAL, "f(R) needs fR0 > 0");
   if (m->kind == COLA_NDGP && !(m->rcH0 > 0)) return fail(c, COLA_EINVAL, "nDGP needs rcH0 > 0");
   if (m->kind == COLA_NDGP && m->screening && !(m->R_smooth > 0))
     return fail(c, COLA_EINVAL, "Vainshtein screening needs R_smooth > 0");
-  if (m->filter != 0) return fail(c, COLA_EINVAL, "only the Gaussian filter (0) is available");
+  if (m->filter < 0 || m->filter > 2)
+    return fail(c, COLA_EINVAL, "filter: 0 Gaussian, 1 top-hat, 2 sharp-k");
   return COLA_OK;
 }
 
@@ -270,6 +273,9 @@ void k_nodes(const cola_config& cfg, double& lnk0, double& dlnk, std::vector<dou
 HModel hmodel(const cola_model& m) {
   HModel h;
   h.kind = m.kind;
+  h.beta_star = m.beta_star;
+  h.m_star = m.m_star;
+  h.a_star = m.a_star;
   h.fR0 = m.fR0;
   h.rcH0 = m.rcH0;
   h.R_smooth = m.R_smooth;
@@ -291,7 +297,8 @@ void growth_for(const cola_config& cfg, const cola_model& m, Growth& g, std::vec
   const bool lcdm = (m.kind == COLA_LCDM) || !m.scale_dependent;
   const std::vector<double> key = {cfg.Omega_m, cfg.Lbox, (double)cfg.Np, cfg.z_ini, cfg.z_final,
                                    (double)cfg.nsteps, (double)cfg.nk_table, (double)m.kind,
-                                   lcdm ? 0.0 : m.fR0, lcdm ? 0.0 : m.rcH0, lcdm ? 1.0 : 0.0};
+                                   lcdm ? 0.0 : m.fR0, lcdm ? 0.0 : m.rcH0, lcdm ? 1.0 : 0.0,
+                                   lcdm ? 0.0 : m.beta_star, lcdm ? 0.0 : m.m_star, lcdm ? 0.0 : m.a_star};
   {
     std::lock_guard<std::mutex> lk(g_growth_mu);
     auto it = g_growth_cache.find(key);
@@ -448,12 +455,19 @@ ForceParams force_params(const cola_ctx* c, double a) {
   fp.kappa_norm = (float)(1.5 * Om * a / N3);
   fp.norm = (float)(1.0 / N3);
   fp.inv_rhobar = (float)(N3 / ((double)c->Np * c->Np * c->Np));
-  fp.model = c->model.kind;
+  fp.model = c->model.kind == COLA_SYMM ? COLA_FOFR : c->model.kind;  // screening family
   fp.screened = 0;
   if (c->model.kind == COLA_FOFR) {
     fp.C = (float)(1.0 / 3.0);
     fp.a2m2 = (float)(a * a * fr_m2(a, Om, c->model.fR0));
     fp.fr_thr = (float)(1.5 * fr_fR(a, Om, c->model.fR0) * a * a * kCLight * kCLight);
+    fp.screened = c->model.screening ? 1 : 0;
+  } else if (c->model.kind == COLA_SYMM) {
+    // App. C: C = 2 beta^2(a), range 1/m(a), Phi_crit from the App. C integral (0 before a_*)
+    const double u = symm_u(a, c->model.a_star);
+    fp.C = (float)(2.0 * c->model.beta_star * c->model.beta_star * u);
+    fp.a2m2 = (float)(a * a * c->model.m_star * c->model.m_star * u * kH0OverC * kH0OverC);
+    fp.fr_thr = (float)(symm_phi_crit(a, Om, c->model.m_star, c->model.a_star) * a * a * kCLight * kCLight);
     fp.screened = c->model.screening ? 1 : 0;
   } else if (c->model.kind == COLA_NDGP) {
     const double b = dgp_beta(a, Om, c->model.rcH0);
@@ -461,6 +475,7 @@ ForceParams force_params(const cola_ctx* c, double a) {
     fp.a2m2 = 0.f;
     fp.dgp_coef = (float)(8.0 * c->model.rcH0 * c->model.rcH0 * Om / (9.0 * b * b));
     fp.R2half = (float)(0.5 * c->model.R_smooth * c->model.R_smooth);
+    fp.filter = c->model.filter;
     fp.screened = c->model.screening ? 1 : 0;
   }
   return fp;
@@ -545,7 +560,7 @@ Group single_group(cola_ctx* ctx) {
   const Group::Sub me{ctx, Multi{}};
   const bool scr = ctx->model.kind != COLA_LCDM && ctx->model.screening;
   if (!scr) g.unscreened = me;
-  else if (ctx->model.kind == COLA_FOFR) g.fr_screened = g.screened = me;
+  else if (ctx->model.kind == COLA_FOFR || ctx->model.kind == COLA_SYMM) g.fr_screened = g.screened = me;
   else g.dgp_screened = g.screened = me;
   return g;
 }
@@ -939,7 +954,8 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
                                    cfg.z_ini, cfg.z_final, cfg.Omega_m, cfg.Omega_b, cfg.h, cfg.n_s,
                                    cfg.sigma8, (double)nk, (double)model->kind, model->fR0, model->rcH0,
                                    model->R_smooth, (double)model->screening,
-                                   (double)model->scale_dependent, (double)model->filter};
+                                   (double)model->scale_dependent, (double)model->filter,
+                                   model->beta_star, model->m_star, model->a_star};
   void* mem = nullptr;
   CHECK_RC(acquire_consts(ctx, key, bytes, [&](char* h) {
     Growth g;
@@ -1341,7 +1357,7 @@ static int bfail(cola_batch* b, int code, const std::string& m) {
 static bool same_shape(const cola_ctx* a, const cola_ctx* c) {
   return a->cfg.Np == c->cfg.Np && a->cfg.Nmesh == c->cfg.Nmesh && a->cfg.Lbox == c->cfg.Lbox &&
          a->cfg.nk_table == c->cfg.nk_table && a->cfg.seed_precision == c->cfg.seed_precision &&
-         a->lpt_fast == c->lpt_fast;
+         a->lpt_fast == c->lpt_fast && a->model.filter == c->model.filter;  // one smoothing window per launch
 }
 
 static cola_batch_plan normal_plan(const cola_batch* b, cola_batch_plan p) {
@@ -1387,7 +1403,7 @@ static void plan_groups(const std::vector<cola_ctx*>& ctxs, int group, std::vect
       const bool scr = c->model.kind != COLA_LCDM && c->model.screening;
       lists[0].push_back(c);
       if (!scr) lists[1].push_back(c);
-      else if (c->model.kind == COLA_FOFR) lists[2].push_back(c);
+      else if (c->model.kind == COLA_FOFR || c->model.kind == COLA_SYMM) lists[2].push_back(c);
       else lists[3].push_back(c);
       if (scr) lists[4].push_back(c);
     }

@@ -44,12 +44,13 @@ struct ForceParams {
   float C;           // fifth-force coupling C(a) (0 for LCDM)
   float a2m2;        // a^2 m^2(a)  [(h/Mpc)^2]
   float inv_rhobar;  // Nmesh^3 / Np^3
-  float fr_thr;      // f(R): Phi_crit(a) a^2 c^2, threshold on |Phi_N| in code units
+  float fr_thr;      // f(R), symmetron: Phi_crit(a) a^2 c^2, threshold on |Phi_N| in code units
   float dgp_coef;    // nDGP: 8 (r_c H0)^2 Omega_m / (9 beta^2)
   float R2half;      // nDGP: R_smooth^2 / 2
   float norm;        // 1 / N^3
-  int model;         // 0 LCDM, 1 f(R), 2 nDGP
+  int model;         // screening family: 0 none (LCDM), 1 chameleon-type (f(R), symmetron), 2 Vainshtein (nDGP)
   int screened;      // 1: screened fifth force
+  int filter;        // nDGP: smoothing window of the density, 0 Gaussian, 1 top-hat, 2 sharp-k
   // When hdr is set, kernels replace every value above by the simulation's
   // own: the current step's entry hdr->dfp[hdr->step], or hdr->fp_ini when ini
   // is set (hdr moved by the simulation's shift).

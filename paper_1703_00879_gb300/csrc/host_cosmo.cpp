@@ -84,6 +84,20 @@ double dgp_beta(double a, double Om, double rcH0) {
   return 1.0 + 2.0 * rcH0 * hE(a, Om) * (1.0 + a * hdlnE_da(a, Om) / 3.0);
 }
 
+double symm_u(double a, double a_star) {
+  if (!(a > a_star)) return 0.0;
+  const double r = a_star / a;
+  return 1.0 - r * r * r;
+}
+
+// The App. C integral 9 Omega_m/(2 beta(a)) int_{a_*}^a beta/(m^2/H0^2 a'^4) da' with
+// beta/m^2 = beta_*/(m_*^2 sqrt(u)) and d u = 3 a_*^3 a'^-4 da': 2 sqrt(u)/(3 a_*^3) times
+// beta_*/m_*^2, so Phi_crit = 3 Omega_m/(a_*^3 m_*^2) once the field has switched on.
+double symm_phi_crit(double a, double Om, double m_star, double a_star) {
+  if (!(a > a_star)) return 0.0;
+  return 3.0 * Om / (a_star * a_star * a_star * m_star * m_star);
+}
+
 namespace {
 
 // mu(k, a) and gamma_2(k, k/sqrt2, k/sqrt2, a) for every k (Sec. 5).
@@ -104,6 +118,23 @@ void model_terms(const HModel& m, double Om, double a, const std::vector<double>
     for (size_t i = 0; i < nk; ++i) {
       mu[i] = mu0;
       g2[i] = g0;
+    }
+    return;
+  }
+  if (m.kind == 3) {
+    // App. C: mu = 1 + 2 beta^2 k^2/(k^2 + a^2 m^2); gamma_2^E = m^2 (dm^2/da) beta^2 Omega_m
+    // k^2 / (2 H0^4 Pi(k) Pi(k1) Pi(k2) a^4 H^2), Pi(q) = (q/(a H0))^2 + m^2/H0^2, at k1 = k2 = k/sqrt2
+    const double u = symm_u(a, m.a_star);
+    const double b2 = m.beta_star * m.beta_star * u;
+    const double M2 = m.m_star * m.m_star * u;  // m^2 / H0^2
+    const double a2m2 = a * a * M2 * kH0OverC * kH0OverC;
+    const double dM2 = 3.0 * m.m_star * m.m_star * m.a_star * m.a_star * m.a_star / (a * a * a * a);
+    const double E = hE(a, Om), a4 = a * a * a * a;
+    for (size_t i = 0; i < nk; ++i) {
+      const double kk = k[i], kh = kk / kH0OverC;
+      mu[i] = 1.0 + 2.0 * b2 * kk * kk / (kk * kk + a2m2);
+      const double Pk = kh * kh / (a * a) + M2, Pq = 0.5 * kh * kh / (a * a) + M2;
+      g2[i] = M2 * dM2 * b2 * Om * kh * kh / (a4 * E * E) / (2.0 * Pk * Pq * Pq);
     }
     return;
   }
@@ -130,7 +161,7 @@ void model_terms(const HModel& m, double Om, double a, const std::vector<double>
 
 void solve_growth(const HModel& m, double Om, const std::vector<double>& a_nodes,
                   const std::vector<double>& kin, bool lcdm_growth, Growth& out) {
-  const bool kind_indep = lcdm_growth || m.kind != 1;
+  const bool kind_indep = lcdm_growth || (m.kind != 1 && m.kind != 3);
   // k-independent models: solve one column, replicate.
   std::vector<double> k = kind_indep ? std::vector<double>{kin.empty() ? 1.0 : kin[0]} : kin;
   const size_t nk = k.size(), na = a_nodes.size();
@@ -178,21 +209,40 @@ void solve_growth(const HModel& m, double Om, const std::vector<double>& a_nodes
   };
   record(0, a0);
   const double hmax = 2e-3;  // RK4 in ln a: global error ~1e-11, far below float tables
+  auto rk4 = [&](double t, double h) {
+    rhs(t, y, k1);
+    for (size_t i = 0; i < y.size(); ++i) tmp[i] = y[i] + 0.5 * h * k1[i];
+    rhs(t + 0.5 * h, tmp, k2);
+    for (size_t i = 0; i < y.size(); ++i) tmp[i] = y[i] + 0.5 * h * k2[i];
+    rhs(t + 0.5 * h, tmp, k3);
+    for (size_t i = 0; i < y.size(); ++i) tmp[i] = y[i] + h * k3[i];
+    rhs(t + h, tmp, k4);
+    for (size_t i = 0; i < y.size(); ++i) y[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+  };
   for (size_t n = 1; n < na; ++n) {
-    const double t0 = std::log(a_nodes[n - 1]), t1 = std::log(a_nodes[n]);
-    const int nsub = std::max(2, (int)std::ceil((t1 - t0) / hmax));
-    const double h = (t1 - t0) / nsub;
-    for (int s = 0; s < nsub; ++s) {
-      const double t = t0 + s * h;
-      rhs(t, y, k1);
-      for (size_t i = 0; i < y.size(); ++i) tmp[i] = y[i] + 0.5 * h * k1[i];
-      rhs(t + 0.5 * h, tmp, k2);
-      for (size_t i = 0; i < y.size(); ++i) tmp[i] = y[i] + 0.5 * h * k2[i];
-      rhs(t + 0.5 * h, tmp, k3);
-      for (size_t i = 0; i < y.size(); ++i) tmp[i] = y[i] + h * k3[i];
-      rhs(t + h, tmp, k4);
-      for (size_t i = 0; i < y.size(); ++i)
-        y[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    const double ta = std::log(a_nodes[n - 1]), tb = std::log(a_nodes[n]);
+    // The symmetron switches on at a_*: mu(k, a) has a kink there, and at low k it rises
+    // to its plateau within Delta u ~ (k / (a m_*))^2 of it.  No RK4 step straddles a_*,
+    // and the steps after it grow geometrically from 1e-10 in ln a.
+    double cuts[3] = {ta, tb, tb};
+    int nseg = 1;
+    const bool sw = m.kind == 3 && !lcdm_growth && m.a_star >= a_nodes[n - 1] && m.a_star < a_nodes[n];
+    if (sw && m.a_star > a_nodes[n - 1]) {
+      cuts[1] = std::log(m.a_star);
+      nseg = 2;
+    }
+    for (int seg = 0; seg < nseg; ++seg) {
+      const double t0 = cuts[seg], t1 = cuts[seg + 1];
+      if (sw && seg == nseg - 1) {
+        for (double t = t0, h = 1e-10; t < t1; t += h, h = std::min(h * 1.05, hmax)) {
+          h = std::min(h, t1 - t);
+          rk4(t, h);
+        }
+      } else {
+        const int nsub = std::max(2, (int)std::ceil((t1 - t0) / hmax));
+        const double h = (t1 - t0) / nsub;
+        for (int s = 0; s < nsub; ++s) rk4(t0 + s * h, h);
+      }
     }
     record(n, a_nodes[n]);
   }

@@ -9,8 +9,9 @@ constexpr double kH0OverC = 1.0 / kCLight;
 constexpr double kPi = 3.14159265358979323846;
 
 struct HModel {
-  int kind = 0;  // 0 LCDM, 1 f(R), 2 nDGP
+  int kind = 0;  // 0 LCDM, 1 f(R), 2 nDGP, 3 symmetron
   double fR0 = 0, rcH0 = 0, R_smooth = 1;
+  double beta_star = 0, m_star = 0, a_star = 0;  // symmetron (App. C), m_star = m_* / H0
   int screening = 0, scale_dependent = 1;
 };
 
@@ -22,6 +23,10 @@ double hdtau(double a1, double a2, double Om);
 double fr_m2(double a, double Om, double fR0);       // (h/Mpc)^2
 double fr_fR(double a, double Om, double fR0);       // |f_R(a)|
 double dgp_beta(double a, double Om, double rcH0);
+// Symmetron (App. C): u = 1 - (a_*/a)^3 (0 for a <= a_*), beta^2(a) = beta_*^2 u,
+// m^2(a)/H0^2 = m_*^2 u, and Phi_crit = 3 Omega_m / (a_*^3 (m_*/H0)^2) for a > a_*, else 0.
+double symm_u(double a, double a_star);
+double symm_phi_crit(double a, double Om, double m_star, double a_star);
 
 // Growth tables at a-nodes (Sec. 4.1, Eq. fofrapprox), row-major [na][nk].
 struct Growth {

@@ -492,16 +492,37 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(yinv2r_smem<N, TW>(), N)) 
 }
 
 // ---------------------------------------------------------------- screening field (z pass)
+// Smoothing window of the Vainshtein density (App. B) at h = k^2 R^2 / 2:
+// 0 Gaussian exp(-h); 1 top-hat 3 (sin x - x cos x) / x^3 with x^2 = 2h, by its
+// Taylor series below x = 1/2 where the closed form cancels; 2 sharp-k, 1 for
+// kR <= 1 (h <= 1/2) and 0 beyond.
+__device__ __forceinline__ float smoothing_window(float h, int filter) {
+  if (filter == 0) return __expf(-h);
+  if (filter == 2) return h <= 0.5f ? 1.f : 0.f;
+  const float x2 = 2.f * h;
+  if (x2 < 0.25f)
+    return fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 1330560.f, -1.f / 15120.f), 1.f / 280.f), -0.1f), 1.f);
+  const float x = sqrtf(x2);
+  float s, c;
+  sincospif(x * 0.318309886f, &s, &c);  // argument reduction exact in units of pi
+  return 3.f * (s - x * c) / (x * x2);
+}
+
+// MODEL: 1 the Newtonian potential (chameleon-type screening); 2 the density
+// smoothed by the Gaussian window; 3 the density smoothed by the top-hat or
+// sharp-k window (fp.filter).  The Gaussian keeps a kernel of its own: a
+// per-element switch over the windows slows the pass by a third.
 template <int N, int TW, int MODEL>
 struct OpZScreenField {
   // Store hook of the forward transform: delta(k) out to HBM, the field's
-  // multiplier (f(R): -kappa/k^2; nDGP: the Gaussian filter) applied in place.
+  // multiplier (-kappa/k^2, or the smoothing window) applied in place.
   struct Field {
     static constexpr bool kSmem = true;
     float2* dk;  // delta(k) of the tile: element (n, c) at dk[(n >> 1) ra + (n & 1) rb + hcol(c)]
     int64_t ra, rb;
     int c0, fy2;
     float kf2, kappa_norm, R2half, norm;
+    int filter;
     __device__ __forceinline__ float2 operator()(float2 v, int n, int c, int) const {
       if (c0 + c < N / 2 + 1) dk[(n >> 1) * ra + (n & 1) * rb + hcol(c)] = v;
       const int fx = c0 + c, fz = freq_index(n, N);
@@ -509,7 +530,8 @@ struct OpZScreenField {
       float m = 0.f;
       if (k2 > 0.f) {
         if (MODEL == 1) m = __fdividef(-kappa_norm, k2);
-        else m = __expf(-k2 * R2half) * norm;
+        else if (MODEL == 2) m = __expf(-k2 * R2half) * norm;
+        else m = smoothing_window(k2 * R2half, filter) * norm;
       }
       return cscale(v, m);
     }
@@ -535,7 +557,7 @@ struct OpZScreenField {
     resolve(fp, by);
     const int fy = freq_index(iy, N);
     const Field f{moved(dk_out, by) + base, geo.ra, geo.rb, c0, fy * fy, fp.kf * fp.kf, fp.kappa_norm,
-                  fp.R2half, fp.norm};
+                  fp.R2half, fp.norm, fp.filter};
     fft_tile_call<N, TW, TW, NT, false, 1, TileLoad, Field>(buf, tw, TileLoad{}, f);
     fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(
         buf, tw, TileLoad{}, ColOut{moved(w_out, by) + base, geo.ra, geo.rb, N / 2 + 1 - c0});
@@ -1357,18 +1379,17 @@ static cudaError_t launch_zsf(const float2* in, float2* dk_out, float2* w_out,
   constexpr size_t sm = col_smem_tw(N, TW);
   const int64_t ntiles = col_tiles<N, TW>() * m.nb;
   unsigned grid;
-  if (fp.model == 1) {
-    auto k = k_z_screen_field<N, TW, 1>;
+  auto go = [&](auto model) {
+    constexpr int MODEL = decltype(model)::value;
+    auto k = k_z_screen_field<N, TW, MODEL>;
     cudaError_t e = prep(k, sm, ntiles, grid);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(OpZScreenField<N, TW, 1>{geo_z<N, TW>(m), in, dk_out, w_out, fp}, tw, ntiles);
-  } else {
-    auto k = k_z_screen_field<N, TW, 2>;
-    cudaError_t e = prep(k, sm, ntiles, grid);
-    if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(OpZScreenField<N, TW, 2>{geo_z<N, TW>(m), in, dk_out, w_out, fp}, tw, ntiles);
-  }
-  return cudaGetLastError();
+    k<<<grid, NT, sm, s>>>(OpZScreenField<N, TW, MODEL>{geo_z<N, TW>(m), in, dk_out, w_out, fp}, tw, ntiles);
+    return cudaGetLastError();
+  };
+  if (fp.model == 1) return go(std::integral_constant<int, 1>{});
+  if (fp.filter == 0) return go(std::integral_constant<int, 2>{});
+  return go(std::integral_constant<int, 3>{});
 }
 
 cudaError_t mesh_z_screen_field(int Nv, const float2* in, float2* dk_out, float2* w_out,

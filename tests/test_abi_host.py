@@ -2,6 +2,7 @@
 declared in include/cola.h, validates its inputs, and its host-side double
 precision tables (growth factors, time integrals) match the oracle."""
 import ctypes
+import dataclasses
 import os
 import re
 
@@ -11,7 +12,7 @@ import pytest
 import paper_1703_00879_gb300 as pkg
 from oracle import background as bg
 from oracle import growth as og
-from workloads import F5, MAIN_F5, NDGP1, SMALL_F5, Model
+from workloads import F5, MAIN_F5, NDGP1, SMALL_F5, SYMM_A, Model
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -56,10 +57,19 @@ def test_host_growth_rejects_bad_model(lib):
     bad = pkg.make_model(Model(kind=1, fR0=0.0))
     out = np.zeros((SMALL_F5.nsteps + 1, 6, SMALL_F5.nk_table))
     assert lib.cola_host_growth(ctypes.byref(cfg), ctypes.byref(bad), out.ctypes.data, None) == pkg.COLA_EINVAL
+    # App. B smoothing windows: 0 Gaussian, 1 top-hat, 2 sharp-k; nothing else
+    for f, want in [(1, pkg.COLA_OK), (2, pkg.COLA_OK), (3, pkg.COLA_EINVAL), (-1, pkg.COLA_EINVAL)]:
+        m = pkg.make_model(Model(kind=2, rcH0=1.0, screening=1, R_smooth=2.0, filter=f))
+        assert lib.cola_host_growth(ctypes.byref(cfg), ctypes.byref(m), out.ctypes.data, None) == want, f
+    # symmetron (App. C): beta_*, m_*/H0 > 0 and 0 < a_* <= 1
+    for kw, want in [({}, pkg.COLA_OK), ({"beta_star": 0.0}, pkg.COLA_EINVAL), ({"m_star": -1.0}, pkg.COLA_EINVAL),
+                     ({"a_star": 0.0}, pkg.COLA_EINVAL), ({"a_star": 1.5}, pkg.COLA_EINVAL)]:
+        m = pkg.make_model(dataclasses.replace(SYMM_A, **kw))
+        assert lib.cola_host_growth(ctypes.byref(cfg), ctypes.byref(m), out.ctypes.data, None) == want, kw
 
 
 @pytest.mark.parametrize("run", [SMALL_F5, SMALL_F5.with_model(NDGP1), SMALL_F5.with_model(Model()),
-                                 MAIN_F5.with_(nk_table=256)])
+                                 MAIN_F5.with_(nk_table=256), SMALL_F5.with_model(SYMM_A)])
 def test_host_growth_tables_match_oracle(lib, run):
     out, k = pkg.cola_host_growth(run)
     a = bg.a_nodes(run.a_ini, run.a_final, run.nsteps)

@@ -6,12 +6,14 @@ particles); particle displacements after all steps within 1e-4 of a mesh
 cell; P(k) within 1e-4 relative per bin; the boost P_MG/P_LCDM within 1e-4
 absolute.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
 from oracle import ics, pm
 from oracle.cola import Simulation as OracleSim
-from workloads import (F5, F5_NOSCREEN, LCDM_MODEL, NDGP1, SMALL_F5, Cosmo, Model, Run,
+from workloads import (F5, F5_NOSCREEN, LCDM_MODEL, NDGP1, SMALL_F5, SYMM_A, Cosmo, Model, Run,
                        random_field, random_positions)
 
 pytestmark = pytest.mark.gpu
@@ -84,8 +86,12 @@ def _density(N, seed):
     return np.exp(0.8 * g - 0.32)
 
 
-@pytest.mark.parametrize("model", [LCDM_MODEL, F5, F5_NOSCREEN, NDGP1, Model(kind=2, rcH0=1.0)],
-                         ids=["lcdm", "F5", "F5_noscreen", "nDGP_screen", "nDGP_noscreen"])
+@pytest.mark.parametrize("model", [LCDM_MODEL, F5, F5_NOSCREEN, NDGP1, Model(kind=2, rcH0=1.0),
+                                   Model(kind=2, rcH0=1.0, screening=1, R_smooth=20.0, filter=1),
+                                   Model(kind=2, rcH0=1.0, screening=1, R_smooth=20.0, filter=2),
+                                   SYMM_A, dataclasses.replace(SYMM_A, screening=0)],
+                         ids=["lcdm", "F5", "F5_noscreen", "nDGP_screen", "nDGP_noscreen",
+                              "nDGP_tophat", "nDGP_sharpk", "symm", "symm_noscreen"])
 @pytest.mark.parametrize("N", [32, 64])
 def test_force_from_density_vs_oracle(pkg, model, N):
     # a box of 16 cells/Mpc^-1 per cell makes |Phi_N| cross the F5 threshold in ~40-85% of cells
@@ -181,7 +187,11 @@ def test_small_config_boost_vs_oracle(pkg, oracle_small):
     SMALL_F5.with_(model=Model(kind=1, fR0=1e-5, screening=1, scale_dependent=0), nsteps=5),
     SMALL_F5.with_(Np=64, Nmesh=32, Lbox=64.0, nsteps=3),      # mesh coarser than particles
     SMALL_F5.with_(nsteps=1, seed=12345678901),                # single step, 64-bit seed
-], ids=["mesh64", "ndgp", "fR_lcdm_growth", "np64_nm32", "one_step"])
+    SMALL_F5.with_(model=Model(kind=2, rcH0=1.0, screening=1, R_smooth=4.0, filter=1), nsteps=5),
+    SMALL_F5.with_(model=Model(kind=2, rcH0=1.0, screening=1, R_smooth=4.0, filter=2), nsteps=5),
+    SMALL_F5.with_(model=SYMM_A, nsteps=5),                    # symmetron, switching on at a_* = 0.5
+], ids=["mesh64", "ndgp", "fR_lcdm_growth", "np64_nm32", "one_step", "ndgp_tophat", "ndgp_sharpk",
+        "symmetron"])
 def test_variants_vs_oracle(pkg, run):
     o = OracleSim(run).run_to_end()
     with pkg.Simulation(run) as s:
