@@ -24,6 +24,10 @@ Readings of the paper taken here (each listed in the design notes):
 * Phi_N in the chameleon factor is the metric potential: the code potential
   (a^2 times it, in (Mpc/h)^2 H0^2) divided by a^2 c^2.
 * (k/(aH))^2 in the f(R) gamma_2^E uses H = H(a).
+* A general {m(a), beta(a)} model is given by tables of beta and m/H0 at ascending
+  scale factors; beta and m^2 are linear in a between nodes, dm^2/da is the
+  slope of the segment, and Phi_crit(a) is the App. C integral from the first
+  node plus the given Phi_crit there.
 * Symmetron Phi_crit is the App. C integral from a_* with Phi_crit(a_*) = 0; it
   equals 3 Omega_m H0^2/(a_*^3 m_*^2), twice the printed closed form (the same
   integral gives Sec. 6.1's 3 |f_R(a)|/2 for f(R), so the integral is taken).
@@ -33,7 +37,9 @@ Units: k in h/Mpc; m^2 in (h/Mpc)^2, using H0/c = 1/C_LIGHT h/Mpc.
 Pins (tests/test_oracle_models.py): mu limits k->0, k->inf and k = a m;
 f(R) mu and gamma_2^E against the App. C {m, beta} forms with beta = 1/sqrt(6);
 Phi_crit quadrature against the closed form, for f(R) and the symmetron; symmetron
-mu limits and gamma_2^E with the analytic dm^2/da; nDGP beta(1) closed form; the
+mu limits and gamma_2^E with the analytic dm^2/da; a tabulated model with constant
+beta and m against the closed-form integral, and one sampled from f(R) against
+Sec. 5.1 and Sec. 6.1; nDGP beta(1) closed form; the
 Vainshtein factor against a numerical solution of the spherical field equation;
 nDGP gamma_2 coefficient against the Vainshtein coefficient through the same
 spherical reduction.
@@ -45,7 +51,7 @@ from scipy import integrate
 
 from .background import C_LIGHT, E, dlnE_da
 
-LCDM, FOFR, NDGP, SYMM = 0, 1, 2, 3
+LCDM, FOFR, NDGP, SYMM, MB = 0, 1, 2, 3, 4
 H0_OVER_C = 1.0 / C_LIGHT   # h/Mpc
 
 
@@ -117,6 +123,9 @@ def mu(model, k, a, Om):
     if model.kind == SYMM:
         m2_fn, beta_fn = symm_fns(model)
         return mb_mu(k, a, m2_fn(a), beta_fn(a))
+    if model.kind == MB:
+        b, m2, _ = table_mb(model, a)
+        return mb_mu(k, a, m2, b)
     return np.ones_like(k)
 
 
@@ -136,6 +145,13 @@ def gamma2_orth(model, k, a, Om):
         q = k / np.sqrt(2.0)
         m2_fn, beta_fn = symm_fns(model)
         return mb_gamma2E(k, q, q, a, Om, m2_fn, beta_fn)
+    if model.kind == MB:
+        b, m2, dm2 = table_mb(model, a)
+        h0 = H0_OVER_C
+        H = h0 * E(a, Om)
+        Pk = (k / (a * h0)) ** 2 + m2 / h0**2
+        Pq = 0.5 * (k / (a * h0)) ** 2 + m2 / h0**2
+        return m2 * dm2 * b**2 * Om * k**2 / (2.0 * h0**4 * Pk * Pq * Pq * a**4 * H**2)
     return np.zeros_like(k)
 
 
@@ -246,4 +262,36 @@ def phi_crit(model, a, Om):
 
         val, _ = integrate.quad(f, 0.0, np.sqrt(a - s), epsabs=0.0, epsrel=1e-13, limit=400)
         return float(9.0 * Om / (2.0 * symm_beta(a, model.beta_star, s)) * val)
+    if model.kind == MB:
+        # adaptive quadrature segment by segment (beta and m^2 are linear on each)
+        ta = np.asarray(model.mb_a, dtype=np.float64)
+        tb = np.asarray(model.mb_beta, dtype=np.float64)
+        tM2 = np.asarray(model.mb_m, dtype=np.float64) ** 2          # m^2 / H0^2
+        val = 0.0
+        for i in range(len(ta) - 1):
+            lo, hi = ta[i], min(ta[i + 1], a) if i < len(ta) - 2 else a
+            if hi <= lo:
+                break
+            w = ta[i + 1] - ta[i]
+
+            def f(x, i=i, w=w):
+                t = (x - ta[i]) / w
+                return (tb[i] + t * (tb[i + 1] - tb[i])) / ((tM2[i] + t * (tM2[i + 1] - tM2[i])) * x**4)
+
+            val += integrate.quad(f, lo, hi, epsabs=0.0, epsrel=1e-13)[0]
+        return float(model.mb_phicrit0 + 9.0 * Om / (2.0 * table_mb(model, a)[0]) * val)
     raise ValueError("no chameleon-type screening for this model")
+
+
+# ---------------------------------------------------------------- tabulated {m(a), beta(a)} (App. C)
+def table_mb(model, a):
+    """(beta, m^2 [(h/Mpc)^2], dm^2/da) of a tabulated {m, beta} record at a: beta and m^2 linear
+    in a between the nodes mb_a (m^2 from the node values of m/H0), dm^2/da the slope of the
+    segment [a_i, a_i+1) holding a (the last segment at and beyond the last node)."""
+    ta = np.asarray(model.mb_a, dtype=np.float64)
+    tb = np.asarray(model.mb_beta, dtype=np.float64)
+    tm2 = (np.asarray(model.mb_m, dtype=np.float64) * H0_OVER_C) ** 2
+    i = int(np.clip(np.searchsorted(ta, a, side="right") - 1, 0, len(ta) - 2))
+    t = (a - ta[i]) / (ta[i + 1] - ta[i])
+    slope = (tm2[i + 1] - tm2[i]) / (ta[i + 1] - ta[i])
+    return (float(tb[i] + t * (tb[i + 1] - tb[i])), float(tm2[i] + t * (tm2[i + 1] - tm2[i])), float(slope))

@@ -98,6 +98,9 @@ def fifth_force_coupling(model, a: float, Om: float):
     if model.kind == models.SYMM:
         m2_fn, beta_fn = models.symm_fns(model)
         return 2.0 * float(beta_fn(a)) ** 2, a * a * float(m2_fn(a))
+    if model.kind == models.MB:
+        b, m2, _ = models.table_mb(model, a)
+        return 2.0 * b * b, a * a * m2
     return 0.0, 0.0
 
 
@@ -134,7 +137,7 @@ def smoothing_window(N: int, L: float, R: float, kind: int):
 def screening_factor(model, delta_k: np.ndarray, N: int, L: float, a: float, Om: float):
     """eps(x) on the mesh: chameleon from Phi_N (Sec. 6.1) or Vainshtein from delta_R (Sec. 6.2)."""
     k2 = k2_grid(N, L)
-    if model.kind in (models.FOFR, models.SYMM):
+    if model.kind in (models.FOFR, models.SYMM, models.MB):
         inv_k2 = np.zeros_like(k2)
         inv_k2[k2 > 0] = 1.0 / k2[k2 > 0]
         PhiN = irfft3(-kappa(a, Om) * delta_k * inv_k2, N)          # code potential

@@ -116,6 +116,39 @@ def test_symmetron_mu_and_gamma2():
     assert np.all(M.gamma2_orth(SYMM_A, k, 0.45, Om) == 0.0)
 
 
+def test_tabulated_mb_constant_model_closed_form():
+    """App. C with constant beta and m: Phi_crit = Phi_0 + 3 Omega_m (a_0^-3 - a^-3) / (2 (m/H0)^2),
+    mu = 1 + 2 beta^2 k^2/(k^2 + a^2 m^2), and gamma_2^E = 0 (dm^2/da = 0)."""
+    from workloads import MB, Model
+    Om, b, mh = 0.3, 0.5, 1000.0
+    m = Model(kind=MB, mb_a=(0.01, 0.5, 1.2), mb_beta=(b, b, b), mb_m=(mh, mh, mh), mb_phicrit0=2e-7)
+    for a in (0.02, 0.5, 0.77, 1.0):
+        want = 2e-7 + 3.0 * Om * (0.01**-3 - a**-3) / (2.0 * mh**2)
+        assert M.phi_crit(m, a, Om) == pytest.approx(want, rel=1e-10)
+        k = np.array([1e-3, 0.3, 30.0])
+        am = a * mh * M.H0_OVER_C
+        assert np.allclose(M.mu(m, k, a, Om), 1 + 2 * b * b * k**2 / (k**2 + am**2), rtol=1e-14)
+        assert np.all(M.gamma2_orth(m, k, a, Om) == 0.0)
+
+
+def test_tabulated_mb_reproduces_fR():
+    """f(R) F5 sampled at 2000 geometric nodes in a as {beta = 1/sqrt6, m(a)}: mu, gamma_2 and Phi_crit
+    agree with the Sec. 5.1 / Sec. 6.1 closed forms to the accuracy of linear interpolation (m^2
+    goes as a^-9 early on; gamma_2 takes the secant slope of m^2)."""
+    from workloads import MB, Model
+    Om, fR0 = 0.3, 1e-5
+    ta = np.geomspace(0.02, 1.0, 2000)
+    m = Model(kind=MB, mb_a=tuple(ta), mb_beta=tuple(np.full_like(ta, 1 / np.sqrt(6.0))),
+              mb_m=tuple(np.sqrt(M.fr_m2(ta, Om, fR0)) / M.H0_OVER_C),
+              mb_phicrit0=float(M.phi_crit_fr(0.02, Om, fR0)))
+    k = np.logspace(-2, 1, 7)
+    for a in (0.1031, 0.4, 0.9):
+        assert np.allclose(M.mu(m, k, a, Om), M.fr_mu(k, a, Om, fR0), rtol=1e-5)
+        q = k / np.sqrt(2)
+        assert np.allclose(M.gamma2_orth(m, k, a, Om), M.fr_gamma2E(k, q, q, a, Om, fR0), rtol=1e-2)
+        assert M.phi_crit(m, a, Om) == pytest.approx(float(M.phi_crit_fr(a, Om, fR0)), rel=2e-4)
+
+
 def test_ndgp_beta_today():
     # beta(1) = 1 + 2 rcH0 (1 - Omega_m/2)  (E(1) = 1, dlnE/da(1) = -3 Om/2)
     assert M.dgp_beta(1.0, 0.3, 1.0) == pytest.approx(2.7, rel=1e-14)

@@ -18,7 +18,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # Model kinds (same integer codes as the C ABI).
-LCDM, FOFR, NDGP, SYMM = 0, 1, 2, 3
+LCDM, FOFR, NDGP, SYMM, MB = 0, 1, 2, 3, 4
 
 
 @dataclass(frozen=True)
@@ -42,6 +42,11 @@ class Model:
     beta_star: float = 0.0    # symmetron coupling beta_* (App. C)
     m_star: float = 0.0       # symmetron mass m_*/H0 (range c/m_* = 2997.92458/m_star Mpc/h)
     a_star: float = 0.0       # symmetron symmetry-breaking scale factor a_*
+    # general {m(a), beta(a)} model (App. C): beta and m/H0 at ascending scale factors
+    mb_a: tuple = ()
+    mb_beta: tuple = ()
+    mb_m: tuple = ()
+    mb_phicrit0: float = 0.0  # Phi_crit at mb_a[0]
 
 
 @dataclass(frozen=True)
