@@ -55,7 +55,7 @@ enum {
 };
 
 /* Model kinds. */
-enum { COLA_LCDM = 0, COLA_FOFR = 1, COLA_NDGP = 2, COLA_SYMM = 3 };
+enum { COLA_LCDM = 0, COLA_FOFR = 1, COLA_NDGP = 2, COLA_SYMM = 3, COLA_MB = 4 };
 
 /* Where a caller-owned buffer lives. */
 enum { COLA_HOST = 0, COLA_DEVICE = 1 };
@@ -87,7 +87,7 @@ typedef struct {
 
 /* Gravity model (Sec. 5, Sec. 6, App. B). */
 typedef struct {
-  int32_t kind;            /* COLA_LCDM, COLA_FOFR (Hu-Sawicky n = 1), COLA_NDGP, COLA_SYMM */
+  int32_t kind;            /* COLA_LCDM, COLA_FOFR (Hu-Sawicky n = 1), COLA_NDGP, COLA_SYMM, COLA_MB */
   double fR0;              /* |f_R0| (f(R) only, > 0) */
   double rcH0;             /* r_c H0 (nDGP only, > 0) */
   int32_t screening;       /* 1: approximate screening of the fifth force (Sec. 6) */
@@ -105,6 +105,19 @@ typedef struct {
   double beta_star;        /* coupling beta at late times, > 0 (symmetron only) */
   double m_star;           /* mass at late times over H0, > 0 (symmetron only); range 2997.92458 / m_star Mpc/h */
   double a_star;           /* symmetry-breaking scale factor in (0, 1] (symmetron only) */
+  /* General {m(a), beta(a)} model (App. C), COLA_MB, with chameleon-type screening:
+     beta(a) and m(a) / H0 at mb_n scale factors mb_a[0] < ... < mb_a[mb_n - 1],
+     2 <= mb_n <= 4096, covering the run's [a_ini, a_final]; beta >= 0, m > 0.
+     beta and m^2 are linear in a between nodes (dm^2/da the slope of the node
+     interval).  mu = 1 + 2 beta^2 k^2 / (k^2 + a^2 m^2), C = 2 beta^2, range 1/m;
+     Phi_crit(a) = mb_phicrit0 + 9 Omega_m / (2 beta(a)) int_{mb_a[0]}^a beta /
+     (m^2 / H0^2 a'^4) da'.  The three arrays are caller-owned host memory, read
+     during cola_set_model / cola_host_growth only; a violation fails with COLA_EINVAL. */
+  const double* mb_a;
+  const double* mb_beta;
+  const double* mb_m;
+  int32_t mb_n;
+  double mb_phicrit0;      /* Phi_crit(mb_a[0]) >= 0 */
 } cola_model;
 
 /* Creates a context: validates the configuration, allocates every device

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libcola.so")
 
 COLA_OK, COLA_EINVAL, COLA_ENOMEM, COLA_ECUDA, COLA_ESTATE, COLA_ETIMEOUT = 0, -1, -2, -3, -4, -5
-COLA_LCDM, COLA_FOFR, COLA_NDGP, COLA_SYMM = 0, 1, 2, 3
+COLA_LCDM, COLA_FOFR, COLA_NDGP, COLA_SYMM, COLA_MB = 0, 1, 2, 3, 4
 COLA_HOST, COLA_DEVICE = 0, 1
 COLA_F_DISP, COLA_F_DV, COLA_F_ACC, COLA_F_RHO, COLA_F_DELTAK = 0, 1, 2, 3, 4
 COLA_F_FORCE, COLA_F_PHI1, COLA_F_PHI2, COLA_F_LPT_DISP, COLA_F_LPT_ACC = 5, 6, 7, 8, 9
@@ -43,7 +43,9 @@ class cola_model(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("fR0", ctypes.c_double), ("rcH0", ctypes.c_double),
                 ("screening", ctypes.c_int32), ("filter", ctypes.c_int32), ("R_smooth", ctypes.c_double),
                 ("scale_dependent", ctypes.c_int32), ("beta_star", ctypes.c_double),
-                ("m_star", ctypes.c_double), ("a_star", ctypes.c_double)]
+                ("m_star", ctypes.c_double), ("a_star", ctypes.c_double),
+                ("mb_a", ctypes.c_void_p), ("mb_beta", ctypes.c_void_p), ("mb_m", ctypes.c_void_p),
+                ("mb_n", ctypes.c_int32), ("mb_phicrit0", ctypes.c_double)]
 
 
 class cola_batch_plan(ctypes.Structure):
@@ -136,9 +138,16 @@ def make_config(run) -> cola_config:
 
 
 def make_model(m) -> cola_model:
-    return cola_model(int(m.kind), float(m.fR0), float(m.rcH0), int(m.screening), int(getattr(m, "filter", 0)),
-                      float(m.R_smooth), int(m.scale_dependent), float(getattr(m, "beta_star", 0.0)),
-                      float(getattr(m, "m_star", 0.0)), float(getattr(m, "a_star", 0.0)))
+    tabs = [np.ascontiguousarray(getattr(m, f, ()), dtype=np.float64) for f in ("mb_a", "mb_beta", "mb_m")]
+    if not tabs[0].size == tabs[1].size == tabs[2].size:
+        raise ValueError("mb_a, mb_beta and mb_m must have the same length")
+    cm = cola_model(int(m.kind), float(m.fR0), float(m.rcH0), int(m.screening), int(getattr(m, "filter", 0)),
+                    float(m.R_smooth), int(m.scale_dependent), float(getattr(m, "beta_star", 0.0)),
+                    float(getattr(m, "m_star", 0.0)), float(getattr(m, "a_star", 0.0)),
+                    *[t.ctypes.data if t.size else None for t in tabs], int(tabs[0].size),
+                    float(getattr(m, "mb_phicrit0", 0.0)))
+    cm._tables = tabs  # the C side reads them during the call that takes the struct
+    return cm
 
 
 def cola_host_growth(run):

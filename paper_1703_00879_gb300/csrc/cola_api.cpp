@@ -26,7 +26,8 @@ void cola::set_context_free_error(const std::string& msg) { g_err = msg; }
 
 struct cola_ctx {
   cola_config cfg{};
-  cola_model model{};
+  cola_model model{};  // its table pointers are cleared: the tables live in hm
+  HModel hm;            // the model as the host solvers take it
   bool model_set = false, ic_done = false, have_force = false, have_lpt = false;
   // scale-independent LPT fast path: lr[0..2] hold Psi1 and lr[3..5] Psi2 from
   // the ICs on, and the per-step LPT transforms are skipped
@@ -241,7 +242,19 @@ int validate_cfg(const cola_config* cfg, cola_ctx* c) {
 
 int validate_model(const cola_model* m, cola_ctx* c) {
   if (!m) return fail(c, COLA_EINVAL, "model is NULL");
-  if (m->kind < 0 || m->kind > 3) return fail(c, COLA_EINVAL, "unknown model kind");
+  if (m->kind < 0 || m->kind > 4) return fail(c, COLA_EINVAL, "unknown model kind");
+  if (m->kind == COLA_MB) {
+    if (m->mb_n < 2 || m->mb_n > 4096) return fail(c, COLA_EINVAL, "mb_n must be in [2, 4096]");
+    if (!m->mb_a || !m->mb_beta || !m->mb_m) return fail(c, COLA_EINVAL, "mb tables are NULL");
+    for (int i = 0; i < m->mb_n; ++i) {
+      if (!(m->mb_a[i] > 0) || (i > 0 && !(m->mb_a[i] > m->mb_a[i - 1])) || !std::isfinite(m->mb_a[i]))
+        return fail(c, COLA_EINVAL, "mb_a must be positive and strictly ascending");
+      if (!(m->mb_beta[i] >= 0) || !std::isfinite(m->mb_beta[i]))
+        return fail(c, COLA_EINVAL, "mb_beta must be finite and >= 0");
+      if (!(m->mb_m[i] > 0) || !std::isfinite(m->mb_m[i])) return fail(c, COLA_EINVAL, "mb_m must be finite and > 0");
+    }
+    if (!(m->mb_phicrit0 >= 0)) return fail(c, COLA_EINVAL, "mb_phicrit0 must be >= 0");
+  }
   if (m->kind == COLA_SYMM && !(m->beta_star > 0 && m->m_star > 0 && m->a_star > 0 && m->a_star <= 1))
     return fail(c, COLA_EINVAL, "symmetron needs beta_star > 0, m_star > 0 and 0 < a_star <= 1");
   if (m->kind == COLA_FOFR && !(m->fR0 > 0)) return fail(c, COLA_EINVAL, "f(R) needs fR0 > 0");
@@ -252,6 +265,17 @@ int validate_model(const cola_model* m, cola_ctx* c) {
     return fail(c, COLA_EINVAL, "filter: 0 Gaussian, 1 top-hat, 2 sharp-k");
   return COLA_OK;
 }
+
+// A tabulated {m, beta} model must cover the run's scale factors.
+int validate_model_range(const cola_config& cfg, const cola_model& m, cola_ctx* c) {
+  if (m.kind != COLA_MB) return COLA_OK;
+  const double ai = 1.0 / (1.0 + cfg.z_ini), af = 1.0 / (1.0 + cfg.z_final);
+  if (m.mb_a[0] > ai || m.mb_a[m.mb_n - 1] < af)
+    return fail(c, COLA_EINVAL, "mb_a must cover [a_ini, a_final] of the run");
+  return COLA_OK;
+}
+
+bool chameleon_kind(int kind) { return kind == COLA_FOFR || kind == COLA_SYMM || kind == COLA_MB; }
 
 std::vector<double> a_nodes(const cola_config& cfg) {
   const double ai = 1.0 / (1.0 + cfg.z_ini), af = 1.0 / (1.0 + cfg.z_final);
@@ -281,6 +305,14 @@ HModel hmodel(const cola_model& m) {
   h.R_smooth = m.R_smooth;
   h.screening = m.screening;
   h.scale_dependent = m.scale_dependent;
+  if (m.kind == COLA_MB) {
+    h.ta.assign(m.mb_a, m.mb_a + m.mb_n);
+    h.tbeta.assign(m.mb_beta, m.mb_beta + m.mb_n);
+    h.tM2.resize(m.mb_n);
+    for (int i = 0; i < m.mb_n; ++i) h.tM2[i] = m.mb_m[i] * m.mb_m[i];
+    h.phicrit0 = m.mb_phicrit0;
+    mb_prepare(h);
+  }
   return h;
 }
 
@@ -289,16 +321,18 @@ HModel hmodel(const cola_model& m) {
 std::mutex g_growth_mu;
 std::map<std::vector<double>, Growth> g_growth_cache;
 
-void growth_for(const cola_config& cfg, const cola_model& m, Growth& g, std::vector<double>* kout,
+void growth_for(const cola_config& cfg, const HModel& m, Growth& g, std::vector<double>* kout,
                 double* lnk0_out, double* dlnk_out) {
   double lnk0, dlnk;
   std::vector<double> k;
   k_nodes(cfg, lnk0, dlnk, k);
   const bool lcdm = (m.kind == COLA_LCDM) || !m.scale_dependent;
-  const std::vector<double> key = {cfg.Omega_m, cfg.Lbox, (double)cfg.Np, cfg.z_ini, cfg.z_final,
-                                   (double)cfg.nsteps, (double)cfg.nk_table, (double)m.kind,
-                                   lcdm ? 0.0 : m.fR0, lcdm ? 0.0 : m.rcH0, lcdm ? 1.0 : 0.0,
-                                   lcdm ? 0.0 : m.beta_star, lcdm ? 0.0 : m.m_star, lcdm ? 0.0 : m.a_star};
+  std::vector<double> key = {cfg.Omega_m, cfg.Lbox, (double)cfg.Np, cfg.z_ini, cfg.z_final,
+                             (double)cfg.nsteps, (double)cfg.nk_table, (double)m.kind,
+                             lcdm ? 0.0 : m.fR0, lcdm ? 0.0 : m.rcH0, lcdm ? 1.0 : 0.0,
+                             lcdm ? 0.0 : m.beta_star, lcdm ? 0.0 : m.m_star, lcdm ? 0.0 : m.a_star};
+  if (!lcdm)
+    for (const auto* v : {&m.ta, &m.tbeta, &m.tM2}) key.insert(key.end(), v->begin(), v->end());
   {
     std::lock_guard<std::mutex> lk(g_growth_mu);
     auto it = g_growth_cache.find(key);
@@ -310,7 +344,7 @@ void growth_for(const cola_config& cfg, const cola_model& m, Growth& g, std::vec
       return;
     }
   }
-  solve_growth(hmodel(m), cfg.Omega_m, a_nodes(cfg), k, lcdm, g);
+  solve_growth(m, cfg.Omega_m, a_nodes(cfg), k, lcdm, g);
   {
     std::lock_guard<std::mutex> lk(g_growth_mu);
     if (g_growth_cache.size() > 4096) g_growth_cache.clear();
@@ -455,7 +489,7 @@ ForceParams force_params(const cola_ctx* c, double a) {
   fp.kappa_norm = (float)(1.5 * Om * a / N3);
   fp.norm = (float)(1.0 / N3);
   fp.inv_rhobar = (float)(N3 / ((double)c->Np * c->Np * c->Np));
-  fp.model = c->model.kind == COLA_SYMM ? COLA_FOFR : c->model.kind;  // screening family
+  fp.model = chameleon_kind(c->model.kind) ? COLA_FOFR : c->model.kind;  // screening family
   fp.screened = 0;
   if (c->model.kind == COLA_FOFR) {
     fp.C = (float)(1.0 / 3.0);
@@ -468,6 +502,14 @@ ForceParams force_params(const cola_ctx* c, double a) {
     fp.C = (float)(2.0 * c->model.beta_star * c->model.beta_star * u);
     fp.a2m2 = (float)(a * a * c->model.m_star * c->model.m_star * u * kH0OverC * kH0OverC);
     fp.fr_thr = (float)(symm_phi_crit(a, Om, c->model.m_star, c->model.a_star) * a * a * kCLight * kCLight);
+    fp.screened = c->model.screening ? 1 : 0;
+  } else if (c->model.kind == COLA_MB) {
+    // App. C with tabulated beta(a), m(a): C = 2 beta^2, range 1/m, Phi_crit from the integral
+    double beta, M2, dM2;
+    mb_eval(c->hm, a, beta, M2, dM2);
+    fp.C = (float)(2.0 * beta * beta);
+    fp.a2m2 = (float)(a * a * M2 * kH0OverC * kH0OverC);
+    fp.fr_thr = (float)(mb_phi_crit(c->hm, a, Om) * a * a * kCLight * kCLight);
     fp.screened = c->model.screening ? 1 : 0;
   } else if (c->model.kind == COLA_NDGP) {
     const double b = dgp_beta(a, Om, c->model.rcH0);
@@ -560,7 +602,7 @@ Group single_group(cola_ctx* ctx) {
   const Group::Sub me{ctx, Multi{}};
   const bool scr = ctx->model.kind != COLA_LCDM && ctx->model.screening;
   if (!scr) g.unscreened = me;
-  else if (ctx->model.kind == COLA_FOFR || ctx->model.kind == COLA_SYMM) g.fr_screened = g.screened = me;
+  else if (chameleon_kind(ctx->model.kind)) g.fr_screened = g.screened = me;
   else g.dgp_screened = g.screened = me;
   return g;
 }
@@ -928,7 +970,10 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
   if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
   CHECK_RC(validate_model(model, ctx));
   if (ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_set_model after cola_ic");
+  CHECK_RC(validate_model_range(ctx->cfg, *model, ctx));
+  ctx->hm = hmodel(*model);
   ctx->model = *model;
+  ctx->model.mb_a = ctx->model.mb_beta = ctx->model.mb_m = nullptr;
   ctx->model_set = true;  // force_params reads the model
   // a second cola_set_model before cola_ic drops the first model's tables
   if (ctx->tab) {
@@ -950,16 +995,17 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
   const size_t fp_off = 2 * tab_b, fp_b = ((size_t)ns * sizeof(ForceParams) + 255) / 256 * 256;
   const size_t dt_off = fp_off + fp_b, bytes = dt_off + 3 * (size_t)ns * sizeof(float);
   // kind 1: (every configuration field but the seed and the seed precision, the model)
-  const std::vector<double> key = {1.0, (double)cfg.Np, (double)cfg.Nmesh, cfg.Lbox, (double)ns,
-                                   cfg.z_ini, cfg.z_final, cfg.Omega_m, cfg.Omega_b, cfg.h, cfg.n_s,
-                                   cfg.sigma8, (double)nk, (double)model->kind, model->fR0, model->rcH0,
-                                   model->R_smooth, (double)model->screening,
-                                   (double)model->scale_dependent, (double)model->filter,
-                                   model->beta_star, model->m_star, model->a_star};
+  std::vector<double> key = {1.0, (double)cfg.Np, (double)cfg.Nmesh, cfg.Lbox, (double)ns,
+                             cfg.z_ini, cfg.z_final, cfg.Omega_m, cfg.Omega_b, cfg.h, cfg.n_s,
+                             cfg.sigma8, (double)nk, (double)model->kind, model->fR0, model->rcH0,
+                             model->R_smooth, (double)model->screening,
+                             (double)model->scale_dependent, (double)model->filter,
+                             model->beta_star, model->m_star, model->a_star, ctx->hm.phicrit0};
+  for (const auto* v : {&ctx->hm.ta, &ctx->hm.tbeta, &ctx->hm.tM2}) key.insert(key.end(), v->begin(), v->end());
   void* mem = nullptr;
   CHECK_RC(acquire_consts(ctx, key, bytes, [&](char* h) {
     Growth g;
-    growth_for(cfg, *model, g, nullptr, nullptr, nullptr);
+    growth_for(cfg, ctx->hm, g, nullptr, nullptr, nullptr);
     float4* tab = reinterpret_cast<float4*>(h);
     float4* vtab = reinterpret_cast<float4*>(h + tab_b);
     for (int n = 0; n <= ns; ++n) {
@@ -1013,7 +1059,7 @@ int cola_set_lpt_fast(cola_ctx* ctx, int32_t on) {
   if (on) {
     // only for growth that does not depend on k: every table column equal
     Growth g;
-    growth_for(ctx->cfg, ctx->model, g, nullptr, nullptr, nullptr);
+    growth_for(ctx->cfg, ctx->hm, g, nullptr, nullptr, nullptr);
     const std::vector<double>* cols[6] = {&g.D1, &g.dD1, &g.ddD1, &g.D2, &g.dD2, &g.ddD2};
     for (const auto* c : cols)
       for (int n = 0; n < g.na; ++n) {
@@ -1403,7 +1449,7 @@ static void plan_groups(const std::vector<cola_ctx*>& ctxs, int group, std::vect
       const bool scr = c->model.kind != COLA_LCDM && c->model.screening;
       lists[0].push_back(c);
       if (!scr) lists[1].push_back(c);
-      else if (c->model.kind == COLA_FOFR || c->model.kind == COLA_SYMM) lists[2].push_back(c);
+      else if (chameleon_kind(c->model.kind)) lists[2].push_back(c);
       else lists[3].push_back(c);
       if (scr) lists[4].push_back(c);
     }
@@ -1919,7 +1965,9 @@ int cola_host_growth(const cola_config* cfg, const cola_model* model, double* ou
   if (!out) return fail(nullptr, COLA_EINVAL, "out is NULL");
   Growth g;
   std::vector<double> k;
-  growth_for(*cfg, *model, g, &k, nullptr, nullptr);
+  rc = validate_model_range(*cfg, *model, nullptr);
+  if (rc) return rc;
+  growth_for(*cfg, hmodel(*model), g, &k, nullptr, nullptr);
   const int nk = cfg->nk_table;
   for (int n = 0; n <= cfg->nsteps; ++n) {
     const std::vector<double>* cols[6] = {&g.D1, &g.dD1, &g.ddD1, &g.D2, &g.dD2, &g.ddD2};

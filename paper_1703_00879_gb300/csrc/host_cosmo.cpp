@@ -98,11 +98,56 @@ double symm_phi_crit(double a, double Om, double m_star, double a_star) {
   return 3.0 * Om / (a_star * a_star * a_star * m_star * m_star);
 }
 
+long mb_interval(const HModel& m, double a) {
+  const long n = (long)m.ta.size();
+  long i = (long)(std::upper_bound(m.ta.begin(), m.ta.end(), a) - m.ta.begin());
+  i = i == 0 ? 0 : i - 1;
+  return std::min(i, n - 2);
+}
+
+void mb_eval(const HModel& m, double a, double& beta, double& M2, double& dM2, long in) {
+  const size_t i = (size_t)(in >= 0 ? in : mb_interval(m, a));
+  const double w = m.ta[i + 1] - m.ta[i], t = (a - m.ta[i]) / w;
+  beta = m.tbeta[i] + t * (m.tbeta[i + 1] - m.tbeta[i]);
+  M2 = m.tM2[i] + t * (m.tM2[i + 1] - m.tM2[i]);
+  dM2 = (m.tM2[i + 1] - m.tM2[i]) / w;
+}
+
+// int_{ta[i]}^{x} beta / (M2 a^4) da on node interval i, where beta and M2 are
+// linear: 16-point Gauss-Legendre, ample for a rational function on an interval
+// where M2 > 0.
+static double mb_segment(const HModel& m, size_t i, double x) {
+  const GL& g = gl16();
+  const double lo = m.ta[i], h = x - lo, w = m.ta[i + 1] - m.ta[i];
+  double sum = 0;
+  for (size_t q = 0; q < g.x.size(); ++q) {
+    const double a = lo + 0.5 * h * (g.x[q] + 1.0), t = (a - lo) / w;
+    const double b = m.tbeta[i] + t * (m.tbeta[i + 1] - m.tbeta[i]);
+    const double M2 = m.tM2[i] + t * (m.tM2[i + 1] - m.tM2[i]);
+    sum += 0.5 * h * g.w[q] * b / (M2 * a * a * a * a);
+  }
+  return sum;
+}
+
+void mb_prepare(HModel& m) {
+  m.tcum.assign(m.ta.size(), 0.0);
+  for (size_t i = 0; i + 1 < m.ta.size(); ++i) m.tcum[i + 1] = m.tcum[i] + mb_segment(m, i, m.ta[i + 1]);
+}
+
+double mb_phi_crit(const HModel& m, double a, double Om) {
+  const size_t i = (size_t)mb_interval(m, a);
+  double beta, M2, dM2;
+  mb_eval(m, a, beta, M2, dM2);
+  if (!(beta > 0)) return m.phicrit0;  // no coupling: the factor multiplies a zero fifth force
+  return m.phicrit0 + 9.0 * Om / (2.0 * beta) * (m.tcum[i] + mb_segment(m, i, a));
+}
+
 namespace {
 
 // mu(k, a) and gamma_2(k, k/sqrt2, k/sqrt2, a) for every k (Sec. 5).
+// mb_in: the node interval of a tabulated model to use (-1: the one holding a).
 void model_terms(const HModel& m, double Om, double a, const std::vector<double>& k,
-                 bool lcdm, std::vector<double>& mu, std::vector<double>& g2) {
+                 bool lcdm, std::vector<double>& mu, std::vector<double>& g2, long mb_in = -1) {
   const size_t nk = k.size();
   if (lcdm || m.kind == 0) {
     for (size_t i = 0; i < nk; ++i) {
@@ -121,14 +166,21 @@ void model_terms(const HModel& m, double Om, double a, const std::vector<double>
     }
     return;
   }
-  if (m.kind == 3) {
+  if (m.kind == 3 || m.kind == 4) {
     // App. C: mu = 1 + 2 beta^2 k^2/(k^2 + a^2 m^2); gamma_2^E = m^2 (dm^2/da) beta^2 Omega_m
     // k^2 / (2 H0^4 Pi(k) Pi(k1) Pi(k2) a^4 H^2), Pi(q) = (q/(a H0))^2 + m^2/H0^2, at k1 = k2 = k/sqrt2
-    const double u = symm_u(a, m.a_star);
-    const double b2 = m.beta_star * m.beta_star * u;
-    const double M2 = m.m_star * m.m_star * u;  // m^2 / H0^2
+    double b2, M2, dM2;  // beta^2, m^2 / H0^2, d(m^2 / H0^2)/da
+    if (m.kind == 3) {
+      const double u = symm_u(a, m.a_star);
+      b2 = m.beta_star * m.beta_star * u;
+      M2 = m.m_star * m.m_star * u;
+      dM2 = 3.0 * m.m_star * m.m_star * m.a_star * m.a_star * m.a_star / (a * a * a * a);
+    } else {
+      double beta;
+      mb_eval(m, a, beta, M2, dM2, mb_in);
+      b2 = beta * beta;
+    }
     const double a2m2 = a * a * M2 * kH0OverC * kH0OverC;
-    const double dM2 = 3.0 * m.m_star * m.m_star * m.a_star * m.a_star * m.a_star / (a * a * a * a);
     const double E = hE(a, Om), a4 = a * a * a * a;
     for (size_t i = 0; i < nk; ++i) {
       const double kk = k[i], kh = kk / kH0OverC;
@@ -161,7 +213,7 @@ void model_terms(const HModel& m, double Om, double a, const std::vector<double>
 
 void solve_growth(const HModel& m, double Om, const std::vector<double>& a_nodes,
                   const std::vector<double>& kin, bool lcdm_growth, Growth& out) {
-  const bool kind_indep = lcdm_growth || (m.kind != 1 && m.kind != 3);
+  const bool kind_indep = lcdm_growth || (m.kind != 1 && m.kind != 3 && m.kind != 4);
   // k-independent models: solve one column, replicate.
   std::vector<double> k = kind_indep ? std::vector<double>{kin.empty() ? 1.0 : kin[0]} : kin;
   const size_t nk = k.size(), na = a_nodes.size();
@@ -174,11 +226,12 @@ void solve_growth(const HModel& m, double Om, const std::vector<double>& a_nodes
     y[2 * nk + i] = -3.0 / 7.0;
     y[3 * nk + i] = -6.0 / 7.0 * a0 * a0 * E0;
   }
+  long seg_in = -1;  // node interval of the RK4 segment (tabulated models: dm^2/da jumps at nodes)
   auto rhs = [&](double lna, const std::vector<double>& s, std::vector<double>& d) {
     const double a = std::exp(lna), E = hE(a, Om);
     const double kap = 1.5 * Om * a;
     const double dt = 1.0 / (a * a * E);
-    model_terms(m, Om, a, k, lcdm_growth, mu, g2);
+    model_terms(m, Om, a, k, lcdm_growth, mu, g2, seg_in);
     const double a4E2 = a * a * a * a * E * E;
     for (size_t i = 0; i < nk; ++i) {
       const double D1 = s[i], dD1 = s[nk + i], D2 = s[2 * nk + i], dD2 = s[3 * nk + i];
@@ -224,15 +277,18 @@ void solve_growth(const HModel& m, double Om, const std::vector<double>& a_nodes
     // The symmetron switches on at a_*: mu(k, a) has a kink there, and at low k it rises
     // to its plateau within Delta u ~ (k / (a m_*))^2 of it.  No RK4 step straddles a_*,
     // and the steps after it grow geometrically from 1e-10 in ln a.
-    double cuts[3] = {ta, tb, tb};
-    int nseg = 1;
+    std::vector<double> cuts = {ta};
     const bool sw = m.kind == 3 && !lcdm_growth && m.a_star >= a_nodes[n - 1] && m.a_star < a_nodes[n];
-    if (sw && m.a_star > a_nodes[n - 1]) {
-      cuts[1] = std::log(m.a_star);
-      nseg = 2;
-    }
+    if (sw && m.a_star > a_nodes[n - 1]) cuts.push_back(std::log(m.a_star));
+    // a tabulated model's mu has kinks at its nodes: RK4 steps end on them too
+    if (m.kind == 4 && !lcdm_growth)
+      for (double x : m.ta)
+        if (x > a_nodes[n - 1] && x < a_nodes[n]) cuts.push_back(std::log(x));
+    cuts.push_back(tb);
+    const int nseg = (int)cuts.size() - 1;
     for (int seg = 0; seg < nseg; ++seg) {
       const double t0 = cuts[seg], t1 = cuts[seg + 1];
+      seg_in = m.kind == 4 ? mb_interval(m, std::exp(0.5 * (t0 + t1))) : -1;
       if (sw && seg == nseg - 1) {
         for (double t = t0, h = 1e-10; t < t1; t += h, h = std::min(h * 1.05, hmax)) {
           h = std::min(h, t1 - t);

@@ -12,6 +12,10 @@ struct HModel {
   int kind = 0;  // 0 LCDM, 1 f(R), 2 nDGP, 3 symmetron
   double fR0 = 0, rcH0 = 0, R_smooth = 1;
   double beta_star = 0, m_star = 0, a_star = 0;  // symmetron (App. C), m_star = m_* / H0
+  // general {m(a), beta(a)} (App. C): nodes, beta, m^2 / H0^2 at the nodes, and the
+  // integral int beta / (m^2/H0^2 a^4) da from the first node to each node
+  std::vector<double> ta, tbeta, tM2, tcum;
+  double phicrit0 = 0;
   int screening = 0, scale_dependent = 1;
 };
 
@@ -27,6 +31,13 @@ double dgp_beta(double a, double Om, double rcH0);
 // m^2(a)/H0^2 = m_*^2 u, and Phi_crit = 3 Omega_m / (a_*^3 (m_*/H0)^2) for a > a_*, else 0.
 double symm_u(double a, double a_star);
 double symm_phi_crit(double a, double Om, double m_star, double a_star);
+// Tabulated {m, beta}: beta(a), m^2(a)/H0^2 (linear in a between nodes) and d(m^2/H0^2)/da
+// (the slope of the node interval [a_i, a_i+1) holding a, or of interval `in` when in >= 0);
+// mb_prepare fills tcum.
+void mb_eval(const HModel& m, double a, double& beta, double& M2, double& dM2, long in = -1);
+long mb_interval(const HModel& m, double a);
+void mb_prepare(HModel& m);
+double mb_phi_crit(const HModel& m, double a, double Om);
 
 // Growth tables at a-nodes (Sec. 4.1, Eq. fofrapprox), row-major [na][nk].
 struct Growth {

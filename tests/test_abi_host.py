@@ -52,6 +52,15 @@ def test_init_rejects_bad_config_without_touching_the_gpu(lib):
                          ctypes.byref(h)) == pkg.COLA_EINVAL
 
 
+def _mb_f5(n):
+    """f(R) F5 as a tabulated {m, beta} model on n geometric nodes from a = 0.04 to 1.01."""
+    from oracle import models as OM
+    ta = np.geomspace(0.04, 1.01, n)
+    return Model(kind=4, screening=1, mb_a=tuple(ta), mb_beta=tuple(np.full(n, 1 / np.sqrt(6.0))),
+                 mb_m=tuple(np.sqrt(OM.fr_m2(ta, 0.3, 1e-5)) / OM.H0_OVER_C),
+                 mb_phicrit0=float(OM.phi_crit_fr(0.04, 0.3, 1e-5)))
+
+
 def test_host_growth_rejects_bad_model(lib):
     cfg = pkg.make_config(SMALL_F5)
     bad = pkg.make_model(Model(kind=1, fR0=0.0))
@@ -61,6 +70,15 @@ def test_host_growth_rejects_bad_model(lib):
     for f, want in [(1, pkg.COLA_OK), (2, pkg.COLA_OK), (3, pkg.COLA_EINVAL), (-1, pkg.COLA_EINVAL)]:
         m = pkg.make_model(Model(kind=2, rcH0=1.0, screening=1, R_smooth=2.0, filter=f))
         assert lib.cola_host_growth(ctypes.byref(cfg), ctypes.byref(m), out.ctypes.data, None) == want, f
+    # tabulated {m, beta} (App. C): ascending a covering the run, beta >= 0, m > 0, 2 <= n <= 4096
+    good = _mb_f5(40)
+    for kw, want in [({}, pkg.COLA_OK), ({"mb_a": good.mb_a[::-1]}, pkg.COLA_EINVAL),
+                     ({"mb_a": tuple(x + 0.05 for x in good.mb_a)}, pkg.COLA_EINVAL),
+                     ({"mb_m": (0.0,) + good.mb_m[1:]}, pkg.COLA_EINVAL),
+                     ({"mb_beta": (-1.0,) + good.mb_beta[1:]}, pkg.COLA_EINVAL),
+                     ({"mb_a": good.mb_a[:1], "mb_beta": good.mb_beta[:1], "mb_m": good.mb_m[:1]}, pkg.COLA_EINVAL)]:
+        m = pkg.make_model(dataclasses.replace(good, **kw))
+        assert lib.cola_host_growth(ctypes.byref(cfg), ctypes.byref(m), out.ctypes.data, None) == want, kw
     # symmetron (App. C): beta_*, m_*/H0 > 0 and 0 < a_* <= 1
     for kw, want in [({}, pkg.COLA_OK), ({"beta_star": 0.0}, pkg.COLA_EINVAL), ({"m_star": -1.0}, pkg.COLA_EINVAL),
                      ({"a_star": 0.0}, pkg.COLA_EINVAL), ({"a_star": 1.5}, pkg.COLA_EINVAL)]:
@@ -69,7 +87,8 @@ def test_host_growth_rejects_bad_model(lib):
 
 
 @pytest.mark.parametrize("run", [SMALL_F5, SMALL_F5.with_model(NDGP1), SMALL_F5.with_model(Model()),
-                                 MAIN_F5.with_(nk_table=256), SMALL_F5.with_model(SYMM_A)])
+                                 MAIN_F5.with_(nk_table=256), SMALL_F5.with_model(SYMM_A),
+                                 SMALL_F5.with_model(_mb_f5(60))])
 def test_host_growth_tables_match_oracle(lib, run):
     out, k = pkg.cola_host_growth(run)
     a = bg.a_nodes(run.a_ini, run.a_final, run.nsteps)

@@ -80,6 +80,15 @@ def test_cic_deposit_empty(pkg):
 
 
 # ------------------------------------------------------------------ force from density
+def _mb_f5(n):
+    """f(R) F5 as a tabulated {m, beta} model (App. C) on n geometric nodes, a = 0.04 to 1.01."""
+    from oracle import models as OM
+    ta = np.geomspace(0.04, 1.01, n)
+    return Model(kind=4, screening=1, mb_a=tuple(ta), mb_beta=tuple(np.full(n, 1 / np.sqrt(6.0))),
+                 mb_m=tuple(np.sqrt(OM.fr_m2(ta, 0.3, 1e-5)) / OM.H0_OVER_C),
+                 mb_phicrit0=float(OM.phi_crit_fr(0.04, 0.3, 1e-5)))
+
+
 def _density(N, seed):
     # lognormal-like positive density with mean ~ rho_bar = 1 (Np = Nm)
     g = random_field(N, seed)
@@ -89,9 +98,9 @@ def _density(N, seed):
 @pytest.mark.parametrize("model", [LCDM_MODEL, F5, F5_NOSCREEN, NDGP1, Model(kind=2, rcH0=1.0),
                                    Model(kind=2, rcH0=1.0, screening=1, R_smooth=20.0, filter=1),
                                    Model(kind=2, rcH0=1.0, screening=1, R_smooth=20.0, filter=2),
-                                   SYMM_A, dataclasses.replace(SYMM_A, screening=0)],
+                                   SYMM_A, dataclasses.replace(SYMM_A, screening=0), _mb_f5(60)],
                          ids=["lcdm", "F5", "F5_noscreen", "nDGP_screen", "nDGP_noscreen",
-                              "nDGP_tophat", "nDGP_sharpk", "symm", "symm_noscreen"])
+                              "nDGP_tophat", "nDGP_sharpk", "symm", "symm_noscreen", "mb_table"])
 @pytest.mark.parametrize("N", [32, 64])
 def test_force_from_density_vs_oracle(pkg, model, N):
     # a box of 16 cells/Mpc^-1 per cell makes |Phi_N| cross the F5 threshold in ~40-85% of cells
@@ -190,8 +199,9 @@ def test_small_config_boost_vs_oracle(pkg, oracle_small):
     SMALL_F5.with_(model=Model(kind=2, rcH0=1.0, screening=1, R_smooth=4.0, filter=1), nsteps=5),
     SMALL_F5.with_(model=Model(kind=2, rcH0=1.0, screening=1, R_smooth=4.0, filter=2), nsteps=5),
     SMALL_F5.with_(model=SYMM_A, nsteps=5),                    # symmetron, switching on at a_* = 0.5
+    SMALL_F5.with_(model=_mb_f5(60), nsteps=5),                # tabulated {m, beta}
 ], ids=["mesh64", "ndgp", "fR_lcdm_growth", "np64_nm32", "one_step", "ndgp_tophat", "ndgp_sharpk",
-        "symmetron"])
+        "symmetron", "mb_table"])
 def test_variants_vs_oracle(pkg, run):
     o = OracleSim(run).run_to_end()
     with pkg.Simulation(run) as s:
