@@ -137,3 +137,48 @@ def lcdm_D1(Om: float, a_ini: float, a_eval) -> np.ndarray:
     nodes = np.concatenate([[a_ini], a_eval])
     g = solve_growth(None, Om, nodes, np.array([1.0]), lcdm_growth=True)
     return g["D1"][1:, 0]
+
+
+def d2_exact(model, Om: float, a_ini: float, a_end: float, k: float, k1: float, k2: float,
+             rtol: float = 1e-11) -> float:
+    """D2(k, k1, k2) at a_end from the exact second-order equation of Sec. 4 (Eq. fofrexact).
+
+    With cos(theta) = k1.k2/(k1 k2) fixed by the triangle k^2 = k1^2 + k2^2 + 2 k1 k2 cos(theta):
+      D2'' - kappa mu(k) D2 = -kappa mu(k) D1(k1) D1(k2) [1 - (2 mu(k1) - mu(k))/mu(k) cos^2
+                              + 2 a^4 H^2 gamma_2(k, k1, k2) / (kappa mu(k))],
+      gamma_2 = gamma_2^E(k, k1, k2) + (3/2) Omega_m(a) [mu(k) - mu(k1)] k1.k2 / k2^2,
+    D2 = -(3/7)(1 - cos^2), D2' = -(6/7)(1 - cos^2) a^2 E at a_ini (' = d/dtau, H in units of
+    H0).  gamma_2^E: Sec. 5.1 for f(R), Sec. 5.2 (prop. to 1 - cos^2) for nDGP.  Used only to check
+    the orthogonal-configuration approximation of Eq. fofrapprox (Fig. 1).
+    """
+    c = (k * k - k1 * k1 - k2 * k2) / (2.0 * k1 * k2)
+    if not -1.0 - 1e-12 <= c <= 1.0 + 1e-12:
+        raise ValueError("(k, k1, k2) is not a triangle")
+    c2 = min(c * c, 1.0)
+    kk = np.array([k, k1, k2], dtype=np.float64)
+
+    def rhs(t, y):
+        a = np.exp(t)
+        Ea = float(E(a, Om))
+        dt = 1.0 / (a * a * Ea)
+        kap = kappa(a, Om)
+        mu_k, mu_1, mu_2 = models.mu(model, kk, a, Om)
+        Om_a = Om / (a**3 * Ea * Ea)
+        if model.kind == models.FOFR:
+            g2E = float(models.fr_gamma2E(k, k1, k2, a, Om, model.fR0))
+        elif model.kind == models.NDGP:
+            g2E = float(models.dgp_gamma2E(a, Om, model.rcH0, c2))
+        else:
+            raise ValueError("exact D2: f(R) or nDGP")
+        g2 = g2E + 1.5 * Om_a * (mu_k - mu_1) * k1 * k2 * c / (k2 * k2)
+        D1a, dD1a, D1b, dD1b, D2, dD2 = y
+        src = 1.0 - (2.0 * mu_1 - mu_k) / mu_k * c2 + 2.0 * a**4 * Ea * Ea * g2 / (kap * mu_k)
+        return [dD1a * dt, kap * mu_1 * D1a * dt, dD1b * dt, kap * mu_2 * D1b * dt,
+                dD2 * dt, (kap * mu_k * D2 - kap * mu_k * D1a * D1b * src) * dt]
+
+    E0 = float(E(a_ini, Om))
+    y0 = [1.0, a_ini**2 * E0, 1.0, a_ini**2 * E0, -3.0 / 7.0 * (1 - c2), -6.0 / 7.0 * (1 - c2) * a_ini**2 * E0]
+    sol = integrate.solve_ivp(rhs, (np.log(a_ini), np.log(a_end)), y0, method="DOP853", rtol=rtol, atol=1e-14)
+    if not sol.success:
+        raise RuntimeError(sol.message)
+    return float(sol.y[4, -1])
