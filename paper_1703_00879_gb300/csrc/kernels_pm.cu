@@ -72,6 +72,39 @@ __device__ __forceinline__ void cic_deposit(float* __restrict__ rho, int Nm, con
   row_add(rho + r11, c.i0[0], c.i1[0], w11 * wx0, w11 * wx1);
 }
 
+// CIC deposit from a whole warp (every lane calls it; `valid` marks real
+// particles).  Particles of the warp with the same base cell reach the same
+// eight cells: their weights are summed on the lowest such lane, which alone
+// issues the atomics.  Clustered particles then cost shuffles instead of
+// atomics on the same addresses.
+__device__ __forceinline__ void cic_deposit_merged(float* __restrict__ rho, int Nm, const Cic& c, bool valid) {
+  const unsigned act = __ballot_sync(0xffffffffu, valid);
+  if (!valid) return;
+  const float wx0 = 1.f - c.f[0], wx1 = c.f[0];
+  const float wy0 = 1.f - c.f[1], wy1 = c.f[1];
+  const float wz0 = 1.f - c.f[2], wz1 = c.f[2];
+  float w[8] = {wz0 * wy0 * wx0, wz0 * wy0 * wx1, wz0 * wy1 * wx0, wz0 * wy1 * wx1,
+                wz1 * wy0 * wx0, wz1 * wy0 * wx1, wz1 * wy1 * wx0, wz1 * wy1 * wx1};
+  const uint32_t key = ((uint32_t)c.i0[2] * (uint32_t)Nm + (uint32_t)c.i0[1]) * (uint32_t)Nm + (uint32_t)c.i0[0];
+  const unsigned peers = __match_any_sync(act, key);
+  const int lane = (int)(threadIdx.x & 31), leader = __ffs(peers) - 1;
+  for (unsigned todo = __ballot_sync(act, lane != leader); todo; todo &= todo - 1) {  // warp-uniform
+    const int j = __ffs(todo) - 1;
+    const bool take = lane == leader && ((peers >> j) & 1u);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float v = __shfl_sync(act, w[q], j);
+      if (take) w[q] += v;
+    }
+  }
+  if (lane != leader) return;
+  const int64_t z0 = (int64_t)c.i0[2] * Nm, z1 = (int64_t)c.i1[2] * Nm;
+  row_add(rho + (z0 + c.i0[1]) * Nm, c.i0[0], c.i1[0], w[0], w[1]);
+  row_add(rho + (z0 + c.i1[1]) * Nm, c.i0[0], c.i1[0], w[2], w[3]);
+  row_add(rho + (z1 + c.i0[1]) * Nm, c.i0[0], c.i1[0], w[4], w[5]);
+  row_add(rho + (z1 + c.i1[1]) * Nm, c.i0[0], c.i1[0], w[6], w[7]);
+}
+
 __device__ __forceinline__ float cic_interp(const float* __restrict__ F, int Nm, const Cic& c) {
   const float wx0 = 1.f - c.f[0], wx1 = c.f[0];
   const float wy0 = 1.f - c.f[1], wy1 = c.f[1];
@@ -137,7 +170,7 @@ __global__ void __launch_bounds__(NTP) k_drift_deposit(
     const float* __restrict__ dpz, float* __restrict__ rho, StepDt dt, int64_t P, Multi m,
     LptMix mix) {
   const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
-  if (p >= P) return;
+  const bool valid = p < P;
   const int64_t by = shift_of(m, blockIdx.y);
   sx = moved(sx, by);
   sy = moved(sy, by);
@@ -158,28 +191,32 @@ __global__ void __launch_bounds__(NTP) k_drift_deposit(
     dtk = h->ddt[3 * h->step];
     dtd = h->ddt[3 * h->step + 1];
   }
-  float lx = dpx[p], ly = dpy[p], lz = dpz[p];
-  if (mix.on) {  // Delta Psi = c1 Psi1 + c2 Psi2
-    const float4 cf = mix_coeffs(mix, by);
-    lx = cf.x * lx + cf.y * moved(mix.q2[0], by)[p];
-    ly = cf.x * ly + cf.y * moved(mix.q2[1], by)[p];
-    lz = cf.x * lz + cf.y * moved(mix.q2[2], by)[p];
+  Cic c{};
+  if (valid) {
+    float lx = dpx[p], ly = dpy[p], lz = dpz[p];
+    if (mix.on) {  // Delta Psi = c1 Psi1 + c2 Psi2
+      const float4 cf = mix_coeffs(mix, by);
+      lx = cf.x * lx + cf.y * moved(mix.q2[0], by)[p];
+      ly = cf.x * ly + cf.y * moved(mix.q2[1], by)[p];
+      lz = cf.x * lz + cf.y * moved(mix.q2[2], by)[p];
+    }
+    const float ux = vx[p] + ax[p] * dtk;
+    const float uy = vy[p] + ay[p] * dtk;
+    const float uz = vz[p] + az[p] * dtk;
+    const float nx = sx[p] + ux * dtd + lx;
+    const float ny = sy[p] + uy * dtd + ly;
+    const float nz = sz[p] + uz * dtd + lz;
+    vx[p] = ux;
+    vy[p] = uy;
+    vz[p] = uz;
+    sx[p] = nx;
+    sy[p] = ny;
+    sz[p] = nz;
+    int ix, iy, iz;
+    lattice(pp, p, ix, iy, iz);
+    c = cic_setup(pp, ix, iy, iz, nx, ny, nz);
   }
-  const float ux = vx[p] + ax[p] * dtk;
-  const float uy = vy[p] + ay[p] * dtk;
-  const float uz = vz[p] + az[p] * dtk;
-  const float nx = sx[p] + ux * dtd + lx;
-  const float ny = sy[p] + uy * dtd + ly;
-  const float nz = sz[p] + uz * dtd + lz;
-  vx[p] = ux;
-  vy[p] = uy;
-  vz[p] = uz;
-  sx[p] = nx;
-  sy[p] = ny;
-  sz[p] = nz;
-  int ix, iy, iz;
-  lattice(pp, p, ix, iy, iz);
-  cic_deposit(rho, pp.Nm, cic_setup(pp, ix, iy, iz, nx, ny, nz));
+  cic_deposit_merged(rho, pp.Nm, c, valid);
 }
 
 // Sec. 2 kick: acc = g(x) - A_LPT(q), delta_v += acc dtk.  Each thread handles
