@@ -61,6 +61,11 @@ def _mb_f5(n):
                  mb_phicrit0=float(OM.phi_crit_fr(0.04, 0.3, 1e-5)))
 
 
+def test_make_model_checks_table_lengths():
+    with pytest.raises(ValueError):
+        pkg.make_model(Model(kind=4, mb_a=(0.1, 1.0), mb_beta=(0.5,), mb_m=(1.0, 1.0)))
+
+
 def test_host_growth_rejects_bad_model(lib):
     cfg = pkg.make_config(SMALL_F5)
     bad = pkg.make_model(Model(kind=1, fR0=0.0))
