@@ -121,3 +121,30 @@ def test_binding_fails_loudly_without_gpu(lib):
         pytest.skip("a GPU is visible")
     with pytest.raises(RuntimeError):
         pkg.Simulation(SMALL_F5)
+
+
+def test_header_is_c99_and_matches_the_binding(tmp_path):
+    """include/cola.h compiles as plain C99, and the binding's structs have the C layout."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"cola_config": pkg.cola_config, "cola_model": pkg.cola_model, "cola_batch_plan": pkg.cola_batch_plan}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "cola.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
