@@ -8,7 +8,7 @@ Units: lengths in Mpc/h, time in 1/H0 (so H0 = 1 and H(a) = E(a)).
 * Flat LCDM expansion E(a)^2 = Omega_m a^-3 + 1 - Omega_m (App. B: the fiducial background).
 
 Pins: Delta tau against the Einstein-de Sitter closed form; E and its
-logarithmic derivative against finite differences (tests/test_oracle_background.py).
+logarithmic derivative against finite differences (tests/test_oracle_basics.py).
 """
 from __future__ import annotations
 

@@ -14,7 +14,9 @@ per mode by linear interpolation in ln k; the table is the discretisation
 of the growth factors used by both the oracle and the CUDA path.
 
 Pins (tests/test_oracle_growth.py): Einstein-de Sitter D1 = a/a_ini and
-D2 = -3/7 D1^2; EdS with constant mu against the power-law solution; LCDM
+D2 = -3/7 D1^2; EdS with constant mu against the power-law solution; EdS with
+constant mu and a constant gamma_2 against the closed-form D2 (power-law
+particular solutions of the gamma_2 source term); LCDM
 against the growing-mode integral E(a) int da/(a E)^3; f(R) columns reduce to
 LCDM at k -> 0 and to mu = 4/3 at k -> infinity.
 """

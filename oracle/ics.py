@@ -15,7 +15,7 @@ Conventions (unnormalised forward DFT, e^{+ikx} synthesis with 1/N^3):
 
 Arrays are indexed [z][y][x] and the half spectrum keeps kx = 0..N/2 (numpy rfftn).
 
-Pins (tests/test_oracle_ics.py): one cosine mode gives phi2 = 0; two
+Pins (tests/test_oracle_pm.py): one cosine mode gives phi2 = 0; two
 perpendicular modes give phi2 = -A B k1^2 k2^2 cos(k1 x) cos(k2 y)/(k1^2 + k2^2);
 the IC power spectrum matches P_ini within cosmic variance; the DFT
 conventions against a direct sum on an 8^3 grid.

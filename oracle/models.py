@@ -15,7 +15,7 @@ Follows the paper:
 * Screening factors (Sec. 6): chameleon eps = min(1, |3 f_R(a) / (2 Phi_N)|);
   Vainshtein eps = 2 (sqrt(1+x) - 1)/x with x = 8 (r_c H0)^2 Omega_m (rho/rho_bar) / (9 beta^2).
 
-Readings of the paper taken here (each listed in the design notes):
+Readings of the paper taken here, where it is silent, garbled or inconsistent:
 * The printed Vainshtein factor 2 sqrt(1+x)/x diverges as x -> 0; the factor
   used is 2 (sqrt(1+x) - 1)/x, the positive root of the spherical solution of
   the nDGP field equation (eps -> 1 as x -> 0).
@@ -34,7 +34,7 @@ Readings of the paper taken here (each listed in the design notes):
 
 Units: k in h/Mpc; m^2 in (h/Mpc)^2, using H0/c = 1/C_LIGHT h/Mpc.
 
-Pins (tests/test_oracle_models.py): mu limits k->0, k->inf and k = a m;
+Pins (tests/test_oracle_basics.py): mu limits k->0, k->inf and k = a m;
 f(R) mu and gamma_2^E against the App. C {m, beta} forms with beta = 1/sqrt(6);
 Phi_crit quadrature against the closed form, for f(R) and the symmetron; symmetron
 mu limits and gamma_2^E with the analytic dm^2/da; a tabulated model with constant

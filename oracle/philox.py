@@ -15,7 +15,7 @@ the lattice point with linear index idx = (z N + y) N + x uses counter
 first two output words give u_i = (w_i + 1/2)/2^32 and
 g = sqrt(-2 ln u1) cos(2 pi u2) in double precision (Box-Muller).
 
-Pins (tests/test_oracle_philox.py): the published known-answer vectors of
+Pins (tests/test_oracle_basics.py): the published known-answer vectors of
 Philox-4x32-10; moments of the normal deviates.
 """
 from __future__ import annotations

@@ -23,9 +23,10 @@ once on the kx = 0 and kx = N/2 planes and twice elsewhere, no shot-noise
 subtraction.
 
 Readings: the top-hat window below x = 1/2 uses its Taylor series (the closed
-form cancels there); the sharp-k cut compares (kR)^2 with 1 in single
-precision with the operation order of the GPU kernel (k^2 = fl(kf^2) |n|^2,
-x^2 = 2 k^2 fl(R^2/2)), so that both sides keep the same modes.
+form cancels there); the sharp-k cut keeps the modes with (kR)^2 <= 1, decided
+in double precision.  A single-precision kernel can decide a mode whose (kR)^2
+lies within float rounding of 1 either way; the parity tests list such modes
+for their radius and box (there are none at the radii they use).
 
 Pins (tests/test_oracle_pm.py): CIC mass conservation and hand-computed
 weights; a single Fourier mode of density gives F = -kappa A k sin(k.x)/|k|^2;
@@ -124,13 +125,7 @@ def smoothing_window(N: int, L: float, R: float, kind: int):
     if kind == 1:
         return tophat_window(np.sqrt(k2) * R)
     if kind == 2:
-        # the cut decided in float32 with the kernel's operation order (see Readings)
-        kf = 2.0 * np.pi / L
-        n2 = np.rint(k2 / (kf * kf)).astype(np.int64)
-        kf32 = np.float32(kf)
-        k2_32 = (kf32 * kf32) * n2.astype(np.float32)
-        x2 = (np.float32(2.0) * k2_32) * np.float32(0.5 * R * R)
-        return (x2 <= np.float32(1.0)).astype(np.float64)
+        return (k2 * R * R <= 1.0).astype(np.float64)
     raise ValueError("smoothing window: 0 Gaussian, 1 top-hat, 2 sharp-k")
 
 

@@ -14,7 +14,7 @@ with w_m = Omega_m h^2, w_b = Omega_b h^2, f_b = Omega_b/Omega_m and
 T_CMB = 2.7255 K.  P(k, z=0) = A k^n_s T0(k)^2 with A fixed by sigma_8 in a
 real-space top-hat of radius 8 Mpc/h.
 
-Pins (tests/test_oracle_power.py): T0 -> 1 as k -> 0; the sigma_8
+Pins (tests/test_oracle_basics.py): T0 -> 1 as k -> 0; the sigma_8
 normalisation reproduces sigma_8 by an independent quadrature; the
 small-scale slope T0 ~ ln(q)/q^2.
 """

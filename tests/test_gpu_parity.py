@@ -114,6 +114,23 @@ def test_force_from_density_vs_oracle(pkg, model, N):
         assert _relmax(F[i], ref[i]) < 3e-5, i
 
 
+def _sharp_k_modes_at_the_cut(N, L, R, rel=1e-5):
+    """Lattice modes whose (kR)^2 lies within `rel` of 1: the FP64 oracle and the FP32 kernel may
+    decide these either way (the sharp-k window of App. B).  Every other mode is decided alike."""
+    n = np.fft.fftfreq(N, d=1.0 / N)
+    n2 = n[:, None, None] ** 2 + n[None, :, None] ** 2 + np.arange(N // 2 + 1)[None, None, :] ** 2
+    x2 = n2 * (2 * np.pi / L * R) ** 2
+    return np.argwhere(np.abs(x2 - 1.0) <= rel)
+
+
+def test_sharp_k_cases_have_no_mode_at_the_cut():
+    """The sharp-k cases below (force: N = 32, 64, L = 16 N, R = 20; run: N = 32, L = 64, R = 4)
+    have no mode within float rounding of kR = 1, so both sides keep the same modes."""
+    for N in (32, 64):
+        assert _sharp_k_modes_at_the_cut(N, 16.0 * N, 20.0).size == 0
+    assert _sharp_k_modes_at_the_cut(32, 64.0, 4.0).size == 0
+
+
 def test_force_screening_active():
     """The f(R) screening threshold is actually crossed in this test density."""
     N = 32

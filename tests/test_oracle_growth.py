@@ -54,6 +54,61 @@ def test_eds_symmetron_limits_are_powerlaws():
     assert np.allclose(late["D2"], -3.0 / 7.0 * ((a / a[0]) ** 2)[:, None], rtol=1e-10)
 
 
+def _eds_d2_with_gamma2(mu, g2, x):
+    """Closed form of the second-order ODE of Eq. fofrapprox in EdS with constant mu and gamma_2.
+
+    EdS: kappa = 3a/2 and a^4 E^2 = a, so in x = a/a_i the ODE reads
+    x^2 D2'' + (3/2) x D2' - (3/2) mu D2 = -(3 mu/2 + 2 gamma_2) D1^2 with
+    D1 = c+ x^p+ + c- x^p-.  Each power x^q of D1^2 has the particular solution
+    x^q / (q^2 + q/2 - 3 mu/2) times the source factor; the homogeneous part
+    d+ x^p+ + d- x^p- takes the Sec. 3.2 initial values D2 = -3/7 and
+    dD2/dtau = -(6/7) a^2 E, i.e. x dD2/dx = -6/7 at x = 1.
+    Returns (D1, D2, x dD2/dx)."""
+    s = np.sqrt(0.25 + 6.0 * mu)
+    pp, pm = (-0.5 + s) / 2, (-0.5 - s) / 2
+    cp = (1 - pm) / (pp - pm)
+    cm = 1 - cp
+    src = -(1.5 * mu + 2.0 * g2)
+    terms = [(2 * pp, cp * cp), (pp + pm, 2 * cp * cm), (2 * pm, cm * cm)]
+    amp = [(q, src * c / (q * q + 0.5 * q - 1.5 * mu)) for q, c in terms]
+    part0 = sum(A for _, A in amp)
+    dpart0 = sum(q * A for q, A in amp)
+    # d+ + d- = -3/7 - part(1);  p+ d+ + p- d- = -6/7 - x part'(1)
+    r1, r2 = -3.0 / 7.0 - part0, -6.0 / 7.0 - dpart0
+    dp = (r2 - pm * r1) / (pp - pm)
+    dm = r1 - dp
+    D1 = cp * x**pp + cm * x**pm
+    D2 = sum(A * x**q for q, A in amp) + dp * x**pp + dm * x**pm
+    xdD2 = sum(q * A * x**q for q, A in amp) + pp * dp * x**pp + pm * dm * x**pm
+    return D1, D2, xdD2
+
+
+@pytest.mark.parametrize("mu,g2", [(1.2, 0.3), (4.0 / 3.0, -0.25), (1.0, 0.5)])
+def test_eds_gamma2_source_closed_form(monkeypatch, mu, g2):
+    """Pins the gamma_2 source term -2 a^4 E^2 gamma_2 D1^2 of Eq. fofrapprox (Sec. 4.2): EdS with a
+    constant mu and a constant gamma_2 (a test-local model: the oracle's mu and gamma_2 replaced by
+    constants) against the power-law solution above.  A sign or factor error in the gamma_2 term,
+    or in how it is scaled by a^4 E^2, moves D2 by tens of per cent."""
+    from oracle import models as om
+    monkeypatch.setattr(om, "mu", lambda model, k, a, Om: np.full_like(np.asarray(k, float), mu))
+    monkeypatch.setattr(om, "gamma2_orth", lambda model, k, a, Om: np.full_like(np.asarray(k, float), g2))
+    a = np.linspace(0.05, 1.0, 12)
+    g = growth.solve_growth(None, 1.0, a, np.array([0.3, 2.0]))
+    D1, D2, xdD2 = _eds_d2_with_gamma2(mu, g2, a / a[0])
+    for j in range(2):
+        assert np.allclose(g["D1"][:, j], D1, rtol=1e-9, atol=0)
+        assert np.allclose(g["D2"][:, j], D2, rtol=1e-9, atol=1e-12)
+        # dD2/dtau = a^3 E dD2/da = a^(1/2) x dD2/dx in EdS
+        assert np.allclose(g["dD2"][:, j], np.sqrt(a) * xdD2, rtol=1e-9, atol=1e-12)
+        # the stored second derivative is the ODE's right-hand side: kappa mu (D2 - D1^2) - 2 a gamma_2 D1^2
+        assert np.allclose(g["ddD2"][:, j], 1.5 * a * mu * (D2 - D1**2) - 2.0 * a * g2 * D1**2,
+                           rtol=1e-9, atol=1e-12)
+    # gamma_2 = 0 with the same mu differs: the term is not silently dropped
+    _, D2_0, _ = _eds_d2_with_gamma2(mu, 0.0, a / a[0])
+    if g2 != 0:
+        assert np.max(np.abs(D2 / D2_0 - 1)) > 0.05
+
+
 def test_lcdm_growing_mode_integral():
     """LCDM: D(a)/D(1) equals E(a) int_0^a da/(a E)^3 normalised at a = 1."""
     Om = 0.3

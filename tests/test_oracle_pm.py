@@ -235,6 +235,28 @@ def test_smoothing_windows_on_the_mesh():
         pm.smoothing_window(N, L, R, 3)
 
 
+def test_sharp_k_cut_is_decided_in_double_precision():
+    """App. B sharp-k window: exactly the modes with (kR)^2 <= 1 in FP64, including a mode that
+    sits on the cut (kept) and one a few ulp above it (cut).  The GPU parity cases use radii
+    whose modes lie far from the cut (tests/test_gpu_parity.py lists them as empty)."""
+    N, L = 16, 64.0
+    kf = 2 * np.pi / L
+    R_on = 1.0 / (kf * np.sqrt(5.0))                 # |n|^2 = 5 exactly on the cut
+    W = pm.smoothing_window(N, L, R_on, 2)
+    n = np.fft.fftfreq(N, d=1.0 / N)
+    n2 = n[:, None, None] ** 2 + n[None, :, None] ** 2 + np.arange(N // 2 + 1)[None, None, :] ** 2
+    x2 = n2 * (kf * R_on) ** 2
+    assert np.array_equal(W == 1.0, x2 <= 1.0)
+    on = np.abs(x2 - 1.0) < 1e-12
+    assert on.any() and np.all(W[on & (x2 <= 1.0)] == 1.0)
+    R_up = R_on * (1.0 + 1e-12)
+    assert np.all(pm.smoothing_window(N, L, R_up, 2)[n2 == 5] == 0.0)
+    for N2, L2, R2 in ((32, 512.0, 20.0), (64, 1024.0, 20.0), (32, 64.0, 4.0)):
+        nn = np.fft.fftfreq(N2, d=1.0 / N2)
+        m2 = nn[:, None, None] ** 2 + nn[None, :, None] ** 2 + np.arange(N2 // 2 + 1)[None, None, :] ** 2
+        assert not np.any(np.abs(m2 * (2 * np.pi / L2 * R2) ** 2 - 1.0) <= 1e-5)
+
+
 def test_sharp_k_screening_of_a_short_mode_is_uniform():
     """A mode with kR > 1 is cut from delta_R, so eps = eps(x(1)) everywhere at any amplitude and the
     force is (1 + eps0/(3 beta)) Newton; the Gaussian window leaves it partly in delta_R."""
