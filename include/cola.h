@@ -20,18 +20,25 @@
  *     failure; no call aborts or prints.  The message of the last failure is
  *     returned by cola_last_error (a context-free failure, e.g. in cola_init
  *     before the context exists, is reported by cola_last_error(NULL)).
- *   - Memory: the per-context buffers are one allocation made through the
- *     alloc/free callbacks given to cola_init (NULL callbacks:
- *     cudaMallocAsync/cudaFreeAsync on the stream); the context owns it and
- *     releases it in cola_free.  Read-only tables that depend only on the
- *     configuration and model (twiddles, growth tables, per-step parameters)
- *     are library-owned (cudaMalloc), uploaded once per distinct key and
- *     shared by every context with that key.  Buffers passed in by the
- *     caller stay owned by the caller.
+ *   - Memory: every device byte a context uses comes through the alloc/free
+ *     callbacks given to cola_init (NULL callbacks: cudaMallocAsync /
+ *     cudaFreeAsync on the stream).  The per-context buffers, including the
+ *     context's copy of its twiddle, growth and per-step tables, are ONE
+ *     allocation, released in cola_free.  Batches and multi-context calls
+ *     allocate their small shift and P(k) arrays through the first context's
+ *     callbacks.  The library itself never calls cudaMalloc or cudaFree; the
+ *     host keeps computed growth tables in a bounded host cache and stages
+ *     uploads through one pinned host ring allocated at the first cola_init,
+ *     so creating, stepping and freeing contexts never synchronises the
+ *     device.  Buffers passed in by the caller stay owned by the caller.
+ *   - Allocator contract: alloc(bytes, stream, user) returns memory usable on
+ *     `stream`; free(ptr, stream, user) releases it in stream order (later
+ *     work on `stream` may reuse it, earlier work still sees it), as PyTorch's
+ *     caching allocator and cudaFreeAsync do.
  *   - Streams: all device work is enqueued on the stream given to cola_init
  *     (borrowed, never destroyed).  Calls that take or return HOST buffers
- *     synchronise that stream before returning; calls with DEVICE buffers do
- *     not.
+ *     wait on the host for that stream before returning (bounded by
+ *     cola_set_wait_limit); calls with DEVICE buffers do not.
  *   - No CPU fallback: every step of the method runs in the library's CUDA
  *     kernels; without a usable GPU cola_init fails with COLA_ECUDA.
  */
@@ -51,7 +58,8 @@ enum {
   COLA_ENOMEM = -2,   /* the allocator returned NULL */
   COLA_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
   COLA_ESTATE = -4,   /* calls made in the wrong order */
-  COLA_ETIMEOUT = -5  /* a bounded device-side wait expired */
+  COLA_ETIMEOUT = -5  /* a host wait for device work ran past the context's wait limit
+                         (cola_set_wait_limit); the work stays queued */
 };
 
 /* Model kinds. */
@@ -132,10 +140,10 @@ int cola_init(const cola_config* cfg, cola_alloc_fn alloc, cola_free_fn free_fn,
 /* Sets the gravity model and solves, in double precision on the host, the
  * growth ODEs of Sec. 4.1 (D1'' = kappa mu(k,a) D1) and Eq. fofrapprox
  * (approximate second-order D2 with gamma_2(k, k/sqrt2, k/sqrt2, a)) on
- * nk_table log-spaced k nodes at every step boundary; uploads the float
- * tables (once per distinct configuration and model: later contexts with
- * the same key share that copy and this call then copies nothing and does
- * not synchronise).  Must precede cola_ic.  Errors: COLA_EINVAL (unknown kind,
+ * nk_table log-spaced k nodes at every step boundary (once per distinct
+ * configuration and model: the host keeps the result in a bounded cache), and
+ * copies the float tables into the context's own allocation, asynchronously
+ * on its stream.  Never synchronises the device.  Must precede cola_ic.  Errors: COLA_EINVAL (unknown kind,
  * non-positive fR0/rcH0/R_smooth where needed), COLA_ESTATE (after cola_ic). */
 int cola_set_model(cola_ctx* ctx, const cola_model* model);
 
@@ -175,22 +183,27 @@ int cola_step(cola_ctx* ctx, int32_t nsteps);
 /* Particle positions (wrapped into [0, Lbox), [Np^3][3] floats, Mpc/h) and
  * peculiar velocities ([Np^3][3] floats, km/s) at the current scale factor,
  * written to caller-owned buffers on the host or device; either pointer may
- * be NULL.  Host buffers synchronise the stream. */
+ * be NULL.  Host buffers wait for the stream (bounded by cola_set_wait_limit). */
 int cola_snapshot(cola_ctx* ctx, float* pos, float* vel, int32_t where);
 
 /* Matter power spectrum of the current particles: CIC on the Nmesh mesh,
  * deconvolved by the CIC window, linear bins b = 0..nbins-1 covering
  * |k| in [(b+1/2) k_F, (b+3/2) k_F), k_F = 2 pi/Lbox, no shot-noise
  * subtraction.  Host arrays of nbins entries (k = mean |k| of the bin's modes,
- * pk in (Mpc/h)^3, nmodes = number of modes); any may be NULL.  Synchronises. */
+ * pk in (Mpc/h)^3, nmodes = number of modes); any may be NULL.  Waits for the
+ * stream (bounded by cola_set_wait_limit: on COLA_ETIMEOUT the outputs are not
+ * written).  Errors: COLA_EINVAL, COLA_ESTATE (no ICs, or a cola_pk_async result
+ * still pending), COLA_ECUDA, COLA_ETIMEOUT. */
 int cola_pk(cola_ctx* ctx, int32_t nbins, double* k, double* pk, int64_t* nmodes);
 
 /* Non-blocking P(k): cola_pk_async enqueues the same computation and a copy
  * of the bin sums into a pinned host buffer owned by the context, and returns
  * at once; cola_pk_ready returns 1 when that copy has landed (0 while pending);
- * cola_pk_result waits for it if needed and fills k, pk, nmodes like cola_pk.
- * One request per context may be pending.  Errors: COLA_EINVAL, COLA_ESTATE
- * (no ICs; a request already pending / none pending), COLA_ECUDA. */
+ * cola_pk_result waits for it if needed (bounded by cola_set_wait_limit; on
+ * COLA_ETIMEOUT the request stays pending and may be collected later) and fills
+ * k, pk, nmodes like cola_pk.  One request per context may be pending.  Errors:
+ * COLA_EINVAL, COLA_ESTATE (no ICs; a request already pending / none pending),
+ * COLA_ECUDA, COLA_ETIMEOUT. */
 int cola_pk_async(cola_ctx* ctx, int32_t nbins);
 int cola_pk_ready(cola_ctx* ctx);
 int cola_pk_result(cola_ctx* ctx, double* k, double* pk, int64_t* nmodes);
@@ -199,6 +212,19 @@ int cola_pk_result(cola_ctx* ctx, double* k, double* pk, int64_t* nmodes);
  * runs before anything later enqueued on the new one (an event wait, no host
  * synchronisation).  Errors: COLA_EINVAL, COLA_ECUDA. */
 int cola_set_stream(cola_ctx* ctx, void* stream);
+
+/* Bounded host waits.  Every call that waits on the host for the context's
+ * stream (host-buffer snapshots, exports and imports, cola_pk, cola_pk_result,
+ * cola_wait) gives up after `seconds` with COLA_ETIMEOUT when seconds > 0
+ * (0, the default: wait without limit).  The device work stays queued and
+ * completes later; the context stays usable.  After a timed-out call with a
+ * caller-owned HOST destination, that buffer is written when the queued copy
+ * completes: keep it alive and call cola_wait (returns COLA_OK once the stream
+ * has drained) before reading or releasing it.  The paper has no counterpart:
+ * this serves callers with a latency budget, such as a request loop.  Errors:
+ * COLA_EINVAL (negative or non-finite limit). */
+int cola_set_wait_limit(cola_ctx* ctx, double seconds);
+int cola_wait(cola_ctx* ctx);
 
 /* Current scale factor (NaN for a NULL context) and completed steps. */
 double cola_scale_factor(const cola_ctx* ctx);

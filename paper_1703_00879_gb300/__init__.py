@@ -89,6 +89,8 @@ _SIGS = {
     "cola_pk_ready": (ctypes.c_int, [_P]),
     "cola_pk_result": (ctypes.c_int, [_P, _P, _P, _P]),
     "cola_set_stream": (ctypes.c_int, [_P, _P]),
+    "cola_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_double]),
+    "cola_wait": (ctypes.c_int, [_P]),
     "cola_batch_steps_done": (ctypes.c_int32, [_P]),
     "cola_batch_free": (None, [_P]),
     "cola_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
@@ -316,6 +318,14 @@ class Simulation:
         k, pk, nm = np.empty(nb), np.empty(nb), np.empty(nb, np.int64)
         _check(lib().cola_pk_result(self.ctx, k.ctypes.data, pk.ctypes.data, nm.ctypes.data), self.ctx)
         return k, pk, nm
+
+    def set_wait_limit(self, seconds: float):
+        """Host waits of this context give up after `seconds` with COLA_ETIMEOUT (0: no limit)."""
+        _check(lib().cola_set_wait_limit(self.ctx, float(seconds)), self.ctx)
+
+    def wait(self):
+        """Waits (within the wait limit) until the context's queued work has completed."""
+        _check(lib().cola_wait(self.ctx), self.ctx)
 
     def set_stream(self, stream):
         """Moves the context to another torch stream (ordered after its queued work)."""

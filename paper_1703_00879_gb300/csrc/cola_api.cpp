@@ -3,12 +3,16 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <deque>
 #include <functional>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -38,8 +42,9 @@ struct cola_ctx {
   void* user = nullptr;
   std::string err;
   std::vector<void*> allocs;
-  std::vector<std::vector<double>> const_keys;  // shared device constants this context holds
   cudaEvent_t ev_order = nullptr;  // orders the context's stream with cola_step_many's stream
+  double wait_limit_s = 0;         // > 0: host waits give up after this long (COLA_ETIMEOUT)
+  cudaEvent_t ev_wait = nullptr;   // recorded by bounded host waits
   double* pk_host = nullptr;       // pinned [3 * kMaxBins] (cola_pk_async)
   cudaEvent_t pk_event = nullptr;
   int pk_nbins = 0;                // bins of the pending cola_pk_async, 0: none
@@ -64,6 +69,8 @@ struct cola_ctx {
   float2 *Cd = nullptr, *Ck = nullptr, *Cw = nullptr, *Cphi = nullptr, *Cphz = nullptr;
   float* F[3] = {};
   float2 *tw_np = nullptr, *tw_nm = nullptr;
+  char* tables = nullptr;      // tab, vtab, dfp, ddt: this context's copy of its key's tables
+  size_t tables_bytes = 0;
   float4 *tab = nullptr, *vtab = nullptr;
   double* pk_acc = nullptr;
   float* scratch = nullptr;
@@ -73,8 +80,8 @@ struct cola_ctx {
   // launch sequence of a step does not depend on which step it is
   SimHeader* hdr = nullptr;    // device header (in the context's allocation)
   SimHeader hh{};              // host copy of what was last written to it
-  ForceParams* dfp = nullptr;  // [nsteps]: force parameters at a_{n+1} (shared)
-  float* ddt = nullptr;        // [nsteps][3]: half kick, drift, half kick (shared)
+  ForceParams* dfp = nullptr;  // [nsteps]: force parameters at a_{n+1}
+  float* ddt = nullptr;        // [nsteps][3]: half kick, drift, half kick
   // per-stage event timing
   bool prof = false;
   struct Stage {
@@ -102,9 +109,11 @@ struct cola_batch {
   struct Graph {
     cudaGraphExec_t exec = nullptr;
     void* shifts = nullptr;                // device shift arrays the graph's launches read
+                                           // (through the first context's allocator, on cap_st)
   };
   std::map<std::tuple<int, int, int>, Graph> graphs;  // plan -> graph serving every step
-  double* pk_acc = nullptr;                // [n][3 * kMaxBins] (batch P(k))
+  double* pk_acc = nullptr;                // [n][3 * kMaxBins] + n shifts (batch P(k)), through
+                                           // the first context's allocator, on st
   std::string err;
 };
 
@@ -183,22 +192,27 @@ int ilog2i(int n) {
   return l;
 }
 
-void* dev_alloc(cola_ctx* c, size_t bytes) {
+// Device memory through the context's callbacks, for use on stream st (NULL
+// callbacks: the stream-ordered cudaMallocAsync / cudaFreeAsync).
+void* dev_alloc_on(cola_ctx* c, size_t bytes, cudaStream_t st) {
   void* p = nullptr;
   if (c->alloc) {
-    p = c->alloc(bytes, (void*)c->st, c->user);
-  } else if (cudaMallocAsync(&p, bytes, c->st) != cudaSuccess) {
+    p = c->alloc(bytes, (void*)st, c->user);
+  } else if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
   }
   return p;
 }
 
-void dev_free(cola_ctx* c, void* p) {
+void dev_free_on(cola_ctx* c, void* p, cudaStream_t st) {
   if (!p) return;
-  if (c->freef) c->freef(p, (void*)c->st, c->user);
-  else if (!c->alloc) cudaFreeAsync(p, c->st);
+  if (c->freef) c->freef(p, (void*)st, c->user);
+  else if (!c->alloc) cudaFreeAsync(p, st);
 }
+
+void* dev_alloc(cola_ctx* c, size_t bytes) { return dev_alloc_on(c, bytes, c->st); }
+void dev_free(cola_ctx* c, void* p) { dev_free_on(c, p, c->st); }
 
 template <class T>
 int alloc_buf(cola_ctx* c, T** out, size_t count) {
@@ -209,20 +223,37 @@ int alloc_buf(cola_ctx* c, T** out, size_t count) {
   return COLA_OK;
 }
 
-// Temporary device buffer released by the destructor (after a stream sync).
+// Temporary device buffer, released by the destructor in stream order (the
+// free callback, like cudaFreeAsync, lets only later work on the stream reuse it).
 struct Temp {
   cola_ctx* c;
   void* p = nullptr;
   Temp(cola_ctx* cc, size_t bytes) : c(cc) {
     if (bytes) p = dev_alloc(c, bytes);
   }
-  ~Temp() {
-    if (p) {
-      cudaStreamSynchronize(c->st);
-      dev_free(c, p);
-    }
-  }
+  ~Temp() { dev_free(c, p); }
 };
+
+// Waits on the host for the work queued so far on the context's stream; with a
+// wait limit set, gives up after that long with COLA_ETIMEOUT (the work stays
+// queued and completes later; the context stays usable).
+int host_wait(cola_ctx* ctx) {
+  if (!(ctx->wait_limit_s > 0)) {
+    CK(cudaStreamSynchronize(ctx->st));
+    return COLA_OK;
+  }
+  if (!ctx->ev_wait) CK(cudaEventCreateWithFlags(&ctx->ev_wait, cudaEventDisableTiming));
+  CK(cudaEventRecord(ctx->ev_wait, ctx->st));
+  const auto t_end = std::chrono::steady_clock::now() + std::chrono::duration<double>(ctx->wait_limit_s);
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ctx->ev_wait);
+    if (e == cudaSuccess) return COLA_OK;
+    if (e != cudaErrorNotReady) return fail(ctx, COLA_ECUDA, std::string("cudaEventQuery: ") + cudaGetErrorString(e));
+    if (std::chrono::steady_clock::now() >= t_end)
+      return fail(ctx, COLA_ETIMEOUT, "the device work did not complete within the wait limit");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
 
 int validate_cfg(const cola_config* cfg, cola_ctx* c) {
   if (!cfg) return fail(c, COLA_EINVAL, "cfg is NULL");
@@ -355,82 +386,164 @@ void growth_for(const cola_config& cfg, const HModel& m, Growth& g, std::vector<
   if (dlnk_out) *dlnk_out = dlnk;
 }
 
-// ---------------------------------------------------------------- shared device constants
-// Read-only device data that depends only on a key: the twiddle table of a
-// transform length, and per (configuration without the seed, model) the LPT
-// growth tables, the per-step force parameters and the time integrals.  Every
-// context with the same key on the same device points at one copy, so once a
-// key has been seen cola_init and cola_set_model copy nothing to the device.
-// The copies are library-owned (cudaMalloc), uploaded on a library stream and
-// published only after that upload has completed; entries that no context
-// holds are released once the cache grows past kMaxConstEntries.
-constexpr size_t kMaxConstEntries = 512;
-struct ConstEntry {
-  void* mem = nullptr;
-  int refs = 0;
-};
-std::mutex g_const_mu;
-std::map<std::vector<double>, ConstEntry> g_consts;
-std::map<int, cudaStream_t> g_const_stream;
+// ---------------------------------------------------------------- host tables and uploads
+// Read-only data that depends only on a key (the growth tables, per-step force
+// parameters and time integrals of a (configuration without the seed, model)
+// pair) is computed on the host once per key and kept in a bounded host cache;
+// every context holds its own device copy inside its single allocation, so all
+// device memory comes through the caller's allocator and goes in cola_free.
+constexpr size_t kMaxHostTables = 1024;
+std::mutex g_host_mu;
+std::map<std::vector<double>, std::shared_ptr<const std::vector<char>>> g_host_tables;
+std::vector<std::vector<double>> g_host_order;  // insertion order, for eviction
 
-int acquire_consts(cola_ctx* ctx, std::vector<double> key, size_t bytes,
-                   const std::function<void(char*)>& fill, void** out) {
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  key.insert(key.begin(), (double)dev);
-  std::lock_guard<std::mutex> lk(g_const_mu);
-  auto it = g_consts.find(key);
-  if (it == g_consts.end()) {
-    if (g_consts.size() >= kMaxConstEntries) {
-      for (auto e = g_consts.begin(); e != g_consts.end();) {
-        if (e->second.refs == 0) {
-          cudaFree(e->second.mem);
-          e = g_consts.erase(e);
-        } else {
-          ++e;
-        }
+std::shared_ptr<const std::vector<char>> host_table(const std::vector<double>& key, size_t bytes,
+                                                    const std::function<void(char*)>& fill) {
+  {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    auto it = g_host_tables.find(key);
+    if (it != g_host_tables.end()) return it->second;
+  }
+  auto v = std::make_shared<std::vector<char>>(bytes);
+  fill(v->data());
+  std::lock_guard<std::mutex> lk(g_host_mu);
+  if (g_host_tables.size() >= kMaxHostTables) {
+    g_host_tables.erase(g_host_order.front());
+    g_host_order.erase(g_host_order.begin());
+  }
+  if (g_host_tables.emplace(key, v).second) g_host_order.push_back(key);
+  return v;
+}
+
+// Host-to-device uploads are staged through one pinned ring (allocated once per
+// process) and copied asynchronously on the caller's stream, so an upload never
+// waits for other work on that stream and never synchronises the device.  A
+// ring region is reused once the copy that last read it has completed; that
+// copy was issued a whole ring earlier.
+#define CHECK_CUDA_RET(x)                   \
+  do {                                      \
+    cudaError_t e_ = (x);                   \
+    if (e_ != cudaSuccess) return e_;       \
+  } while (0)
+class UploadRing {
+ public:
+  cudaError_t copy(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(mu_);
+    if (!buf_) {
+      cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&buf_), kCap, cudaHostAllocPortable);
+      if (e != cudaSuccess) {
+        buf_ = nullptr;
+        return e;
       }
     }
-    cudaStream_t& cs = g_const_stream[dev];
-    if (!cs) CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    std::vector<char> h(bytes);
-    fill(h.data());
-    void* mem = nullptr;
-    CK(cudaMalloc(&mem, bytes));
-    cudaError_t e = cudaMemcpyAsync(mem, h.data(), bytes, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
-    if (e != cudaSuccess) {
-      cudaFree(mem);
-      return fail(ctx, COLA_ECUDA, std::string("constant upload: ") + cudaGetErrorString(e));
+    const char* in = static_cast<const char*>(src);
+    char* out = static_cast<char*>(dst);
+    for (size_t done = 0; done < bytes;) {
+      const size_t len = std::min(bytes - done, kCap / 4);
+      if (head_ + len > kCap) {
+        // the tail past head_ is skipped: its copies, a lap old, must be done
+        while (!live_.empty() && live_.front().off >= head_) CHECK_CUDA_RET(retire());
+        head_ = 0;
+      }
+      while (!live_.empty() && live_.front().off < head_ + len && head_ < live_.front().off + live_.front().len)
+        CHECK_CUDA_RET(retire());
+      std::memcpy(buf_ + head_, in + done, len);
+      cudaError_t e = cudaMemcpyAsync(out + done, buf_ + head_, len, cudaMemcpyHostToDevice, st);
+      cudaEvent_t ev = nullptr;
+      if (e == cudaSuccess) e = take(&ev);
+      if (e == cudaSuccess) e = cudaEventRecord(ev, st);
+      if (e != cudaSuccess) {
+        // the copy may be in flight: wait for it before the region can be reused
+        cudaStreamSynchronize(st);
+        if (ev) spare_.push_back(ev);
+        return e;
+      }
+      live_.push_back({head_, len, ev});
+      head_ += len;
+      done += len;
     }
-    it = g_consts.emplace(key, ConstEntry{mem, 0}).first;
+    return cudaSuccess;
   }
-  it->second.refs += 1;
-  ctx->const_keys.push_back(key);
-  *out = it->second.mem;
+
+ private:
+  static constexpr size_t kCap = 64u << 20;
+  struct Span {
+    size_t off, len;
+    cudaEvent_t ev;
+  };
+  cudaError_t retire() {
+    Span s = live_.front();
+    live_.pop_front();
+    cudaError_t e = cudaEventSynchronize(s.ev);
+    spare_.push_back(s.ev);
+    return e;
+  }
+  cudaError_t take(cudaEvent_t* ev) {
+    if (!spare_.empty()) {
+      *ev = spare_.back();
+      spare_.pop_back();
+      return cudaSuccess;
+    }
+    return cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  }
+  std::mutex mu_;
+  char* buf_ = nullptr;
+  size_t head_ = 0;
+  std::deque<Span> live_;
+  std::vector<cudaEvent_t> spare_;
+};
+#undef CHECK_CUDA_RET
+
+UploadRing g_ring;
+
+// Pinned host buffers of cola_pk_async results ([3 * kMaxBins] doubles each),
+// recycled across contexts and never released: page-locked allocations and
+// releases can synchronise the device, which a serving loop must not see.
+class PinnedSlots {
+ public:
+  double* get() {
+    std::lock_guard<std::mutex> lk(mu_);
+    if (free_.empty()) {
+      constexpr int kChunk = 32;
+      const size_t each = 3 * (size_t)kMaxBins;
+      double* p = nullptr;
+      if (cudaHostAlloc(reinterpret_cast<void**>(&p), kChunk * each * sizeof(double), cudaHostAllocPortable) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      for (int i = 0; i < kChunk; ++i) free_.push_back(p + i * each);
+    }
+    double* p = free_.back();
+    free_.pop_back();
+    return p;
+  }
+  void put(double* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(mu_);
+    free_.push_back(p);
+  }
+
+ private:
+  std::mutex mu_;
+  std::vector<double*> free_;
+};
+
+PinnedSlots g_pk_slots;
+
+int upload(cola_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  CK(g_ring.copy(dst, src, bytes, ctx->st));
   return COLA_OK;
 }
 
-void release_consts(cola_ctx* ctx) {
-  std::lock_guard<std::mutex> lk(g_const_mu);
-  for (const auto& k : ctx->const_keys) {
-    auto it = g_consts.find(k);
-    if (it != g_consts.end() && it->second.refs > 0) it->second.refs -= 1;
+// Twiddle table e^{-2 pi i m/N}, m = 0..N-1, computed in FP64.
+int upload_twiddles(cola_ctx* ctx, int N, float2* dst) {
+  std::vector<float2> t(N);
+  for (int m = 0; m < N; ++m) {
+    const double ang = -2.0 * kPi * m / N;
+    t[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
   }
-  ctx->const_keys.clear();
-}
-
-int shared_twiddles(cola_ctx* ctx, int N, float2** dst) {
-  void* p = nullptr;
-  CHECK_RC(acquire_consts(ctx, {0.0, (double)N}, (size_t)N * sizeof(float2), [N](char* h) {
-    float2* t = reinterpret_cast<float2*>(h);
-    for (int m = 0; m < N; ++m) {
-      const double ang = -2.0 * kPi * m / N;
-      t[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-    }
-  }, &p));
-  *dst = static_cast<float2*>(p);
-  return COLA_OK;
+  return upload(ctx, dst, t.data(), t.size() * sizeof(float2));
 }
 
 // ---------------------------------------------------------------- context memory
@@ -450,6 +563,21 @@ struct Layout {
   }
   void place(char* base) const {
     for (const auto& it : items) *it.dst = base + it.off;
+  }
+};
+
+// Byte layout of a context's tables: [tab | vtab] float4 rows 0..nsteps+1 (rows
+// as documented on SimHeader, plus row nsteps+1 = (1, 0, 0, 1), the Psi1 / Psi2
+// pass of the scale-independent fast path), the per-step force parameters and
+// the per-step time integrals.
+struct TableLayout {
+  size_t tab_b, fp_off, dt_off, bytes;
+  explicit TableLayout(const cola_config& cfg) {
+    const size_t ns = (size_t)cfg.nsteps, nk = (size_t)cfg.nk_table;
+    tab_b = (ns + 2) * nk * sizeof(float4);
+    fp_off = 2 * tab_b;
+    dt_off = fp_off + (ns * sizeof(ForceParams) + 255) / 256 * 256;
+    bytes = dt_off + 3 * ns * sizeof(float);
   }
 };
 
@@ -479,6 +607,10 @@ void context_layout(cola_ctx* c, const cola_config& cfg, Layout& L) {
   L.add(&c->pk_acc, 3 * kMaxBins);
   L.add(&c->hdr, 1);
   L.add(&c->scratch, 64);
+  L.add(&c->tw_np, cfg.Np);
+  L.add(&c->tw_nm, cfg.Nmesh);
+  c->tables_bytes = TableLayout(cfg).bytes;
+  L.add(&c->tables, c->tables_bytes);
 }
 
 ForceParams force_params(const cola_ctx* c, double a) {
@@ -801,14 +933,14 @@ int finish_ic(cola_ctx* ctx, bool potentials) {
 int copy_out(cola_ctx* ctx, void* dst, const void* src, size_t bytes, int where) {
   CK(cudaMemcpyAsync(dst, src, bytes, where == COLA_HOST ? cudaMemcpyDeviceToHost
                                                          : cudaMemcpyDeviceToDevice, ctx->st));
-  if (where == COLA_HOST) CK(cudaStreamSynchronize(ctx->st));
+  if (where == COLA_HOST) return host_wait(ctx);
   return COLA_OK;
 }
 
 int copy_in(cola_ctx* ctx, void* dst, const void* src, size_t bytes, int where) {
   CK(cudaMemcpyAsync(dst, src, bytes, where == COLA_HOST ? cudaMemcpyHostToDevice
                                                          : cudaMemcpyDeviceToDevice, ctx->st));
-  if (where == COLA_HOST) CK(cudaStreamSynchronize(ctx->st));
+  if (where == COLA_HOST) return host_wait(ctx);
   return COLA_OK;
 }
 
@@ -935,8 +1067,8 @@ int cola_init(const cola_config* cfg, cola_alloc_fn alloc, cola_free_fn free_fn,
       lay.place(static_cast<char*>(slab));
     }
   }
-  if (!rc) rc = shared_twiddles(ctx, ctx->Np, &ctx->tw_np);
-  if (!rc) rc = shared_twiddles(ctx, ctx->Nm, &ctx->tw_nm);
+  if (!rc) rc = upload_twiddles(ctx, ctx->Np, ctx->tw_np);
+  if (!rc) rc = upload_twiddles(ctx, ctx->Nm, ctx->tw_nm);
   if (rc) {
     g_err = ctx->err;
     cola_free(ctx);
@@ -975,25 +1107,10 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
   ctx->model = *model;
   ctx->model.mb_a = ctx->model.mb_beta = ctx->model.mb_m = nullptr;
   ctx->model_set = true;  // force_params reads the model
-  // a second cola_set_model before cola_ic drops the first model's tables
-  if (ctx->tab) {
-    std::vector<std::vector<double>> keep;
-    for (auto& k : ctx->const_keys)
-      if (k.size() > 2 && k[1] != 1.0) keep.push_back(k);
-    std::lock_guard<std::mutex> lk(g_const_mu);
-    for (auto& k : ctx->const_keys) {
-      auto it = g_consts.find(k);
-      if (k.size() > 2 && k[1] == 1.0 && it != g_consts.end() && it->second.refs > 0) it->second.refs -= 1;
-    }
-    ctx->const_keys = keep;
-  }
   const cola_config& cfg = ctx->cfg;
   const int nk = ctx->nk, ns = cfg.nsteps;
-  // rows 0..ns as documented on SimHeader, plus row ns+1 = (1, 0, 0, 1): the
-  // Psi1 / Psi2 pass of the scale-independent fast path
-  const size_t tab_b = (size_t)(ns + 2) * nk * sizeof(float4);
-  const size_t fp_off = 2 * tab_b, fp_b = ((size_t)ns * sizeof(ForceParams) + 255) / 256 * 256;
-  const size_t dt_off = fp_off + fp_b, bytes = dt_off + 3 * (size_t)ns * sizeof(float);
+  const TableLayout tl(cfg);
+  const size_t tab_b = tl.tab_b, fp_off = tl.fp_off, dt_off = tl.dt_off, bytes = tl.bytes;
   // kind 1: (every configuration field but the seed and the seed precision, the model)
   std::vector<double> key = {1.0, (double)cfg.Np, (double)cfg.Nmesh, cfg.Lbox, (double)ns,
                              cfg.z_ini, cfg.z_final, cfg.Omega_m, cfg.Omega_b, cfg.h, cfg.n_s,
@@ -1002,8 +1119,7 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
                              (double)model->scale_dependent, (double)model->filter,
                              model->beta_star, model->m_star, model->a_star, ctx->hm.phicrit0};
   for (const auto* v : {&ctx->hm.ta, &ctx->hm.tbeta, &ctx->hm.tM2}) key.insert(key.end(), v->begin(), v->end());
-  void* mem = nullptr;
-  CHECK_RC(acquire_consts(ctx, key, bytes, [&](char* h) {
+  const auto host = host_table(key, bytes, [&](char* h) {
     Growth g;
     growth_for(cfg, ctx->hm, g, nullptr, nullptr, nullptr);
     float4* tab = reinterpret_cast<float4*>(h);
@@ -1033,8 +1149,9 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
       dt[3 * n + 1] = (float)ctx->dtd[n];
       dt[3 * n + 2] = (float)ctx->dtk2[n];
     }
-  }, &mem));
-  char* base = static_cast<char*>(mem);
+  });
+  CHECK_RC(upload(ctx, ctx->tables, host->data(), bytes));
+  char* base = ctx->tables;
   ctx->tab = reinterpret_cast<float4*>(base);
   ctx->vtab = reinterpret_cast<float4*>(base + tab_b);
   ctx->dfp = reinterpret_cast<ForceParams*>(base + fp_off);
@@ -1094,7 +1211,7 @@ int cola_ic_from_potentials(cola_ctx* ctx, const float* phi1, const float* phi2,
       dense = ctx->lc[0];
     }
     CK(half_pack(N, dense, ctx->phi[f], ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
+    CHECK_RC(host_wait(ctx));
   }
   return finish_ic(ctx, true);
 }
@@ -1136,8 +1253,7 @@ int cola_snapshot(cola_ctx* ctx, float* pos, float* vel, int32_t where) {
                    static_cast<float*>(tv.p), ctx->P, ctx->st, mix));
   if (pos) CK(cudaMemcpyAsync(pos, tp.p, bytes, cudaMemcpyDeviceToHost, ctx->st));
   if (vel) CK(cudaMemcpyAsync(vel, tv.p, bytes, cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
-  return COLA_OK;
+  return host_wait(ctx);
 }
 
 // Deposit, forward transform and binning of the current particles into
@@ -1171,11 +1287,15 @@ int cola_pk(cola_ctx* ctx, int32_t nbins, double* k, double* pk, int64_t* nmodes
   if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
   if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_pk before cola_ic");
   if (nbins < 1 || nbins > kMaxBins) return fail(ctx, COLA_EINVAL, "nbins out of range 1..2000");
+  if (ctx->pk_nbins) return fail(ctx, COLA_ESTATE, "a cola_pk_async result is still pending");
   CHECK_RC(enqueue_pk(ctx, nbins));
-  std::vector<double> h(3 * nbins);
-  CK(cudaMemcpyAsync(h.data(), ctx->pk_acc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
-  finish_pk(ctx, h.data(), nbins, k, pk, nmodes);
+  // the sums land in a pinned slot, so a wait that times out leaves no copy into freed memory
+  if (!ctx->pk_host && !(ctx->pk_host = g_pk_slots.get()))
+    return fail(ctx, COLA_ENOMEM, "cola_pk: pinned host buffer allocation failed");
+  CK(cudaMemcpyAsync(ctx->pk_host, ctx->pk_acc, 3 * (size_t)nbins * sizeof(double), cudaMemcpyDeviceToHost,
+                     ctx->st));
+  CHECK_RC(host_wait(ctx));
+  finish_pk(ctx, ctx->pk_host, nbins, k, pk, nmodes);
   return COLA_OK;
 }
 
@@ -1184,7 +1304,8 @@ int cola_pk_async(cola_ctx* ctx, int32_t nbins) {
   if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_pk_async before cola_ic");
   if (nbins < 1 || nbins > kMaxBins) return fail(ctx, COLA_EINVAL, "nbins out of range 1..2000");
   if (ctx->pk_nbins) return fail(ctx, COLA_ESTATE, "a cola_pk_async result is still pending");
-  if (!ctx->pk_host) CK(cudaMallocHost(&ctx->pk_host, 3 * (size_t)kMaxBins * sizeof(double)));
+  if (!ctx->pk_host && !(ctx->pk_host = g_pk_slots.get()))
+    return fail(ctx, COLA_ENOMEM, "cola_pk_async: pinned host buffer allocation failed");
   if (!ctx->pk_event) CK(cudaEventCreateWithFlags(&ctx->pk_event, cudaEventDisableTiming));
   CHECK_RC(enqueue_pk(ctx, nbins));
   CK(cudaMemcpyAsync(ctx->pk_host, ctx->pk_acc, 3 * (size_t)nbins * sizeof(double), cudaMemcpyDeviceToHost,
@@ -1206,10 +1327,34 @@ int cola_pk_ready(cola_ctx* ctx) {
 int cola_pk_result(cola_ctx* ctx, double* k, double* pk, int64_t* nmodes) {
   if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
   if (!ctx->pk_nbins) return fail(ctx, COLA_ESTATE, "no cola_pk_async pending");
-  CK(cudaEventSynchronize(ctx->pk_event));
+  if (ctx->wait_limit_s > 0) {
+    const auto t_end = std::chrono::steady_clock::now() + std::chrono::duration<double>(ctx->wait_limit_s);
+    for (;;) {
+      const cudaError_t e = cudaEventQuery(ctx->pk_event);
+      if (e == cudaSuccess) break;
+      if (e != cudaErrorNotReady) return fail(ctx, COLA_ECUDA, std::string("cudaEventQuery: ") + cudaGetErrorString(e));
+      if (std::chrono::steady_clock::now() >= t_end)
+        return fail(ctx, COLA_ETIMEOUT, "the P(k) did not complete within the wait limit");
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+  } else {
+    CK(cudaEventSynchronize(ctx->pk_event));
+  }
   finish_pk(ctx, ctx->pk_host, ctx->pk_nbins, k, pk, nmodes);
   ctx->pk_nbins = 0;
   return COLA_OK;
+}
+
+int cola_set_wait_limit(cola_ctx* ctx, double seconds) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!(seconds >= 0) || !std::isfinite(seconds)) return fail(ctx, COLA_EINVAL, "wait limit must be finite and >= 0");
+  ctx->wait_limit_s = seconds;
+  return COLA_OK;
+}
+
+int cola_wait(cola_ctx* ctx) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  return host_wait(ctx);
 }
 
 int cola_set_stream(cola_ctx* ctx, void* stream) {
@@ -1241,10 +1386,10 @@ void cola_free(cola_ctx* ctx) {
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->ev_order) cudaEventDestroy(ctx->ev_order);
   if (ctx->pk_event) cudaEventDestroy(ctx->pk_event);
-  if (ctx->pk_host) cudaFreeHost(ctx->pk_host);
+  if (ctx->ev_wait) cudaEventDestroy(ctx->ev_wait);
+  g_pk_slots.put(ctx->pk_host);
   for (void* p : ctx->allocs) dev_free(ctx, p);
   if (!ctx->alloc) cudaStreamSynchronize(ctx->st);
-  release_consts(ctx);
   cudaGetLastError();
   delete ctx;
 }
@@ -1482,9 +1627,11 @@ static int batch_capture(cola_batch* b, int n, const cola_batch_plan& p, cola_ba
   CHECK_RC(chain_streams(b, p.chains));
   int64_t* dsh = nullptr;
   if (!hsh.empty()) {
-    BCK(cudaMalloc(&dsh, hsh.size() * sizeof(int64_t)));
+    dsh = static_cast<int64_t*>(dev_alloc_on(b->ctx[0], hsh.size() * sizeof(int64_t), b->cap_st));
+    if (!dsh) return bfail(b, COLA_ENOMEM, "batch capture: shift array allocation failed");
     out->shifts = dsh;
-    BCK(cudaMemcpy(dsh, hsh.data(), hsh.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpyAsync(dsh, hsh.data(), hsh.size() * sizeof(int64_t), cudaMemcpyHostToDevice, b->cap_st));
+    BCK(cudaStreamSynchronize(b->cap_st));
   }
   for (GroupPlan& gp : groups) {
     Multi* ms[5] = {&gp.g.all, &gp.g.unscreened.m, &gp.g.fr_screened.m, &gp.g.dgp_screened.m,
@@ -1536,7 +1683,7 @@ static int batch_graph(cola_batch* b, const cola_batch_plan& p, cudaGraphExec_t*
     cola_batch::Graph g;
     int rc = batch_capture(b, b->step, p, &g);
     if (rc != COLA_OK) {
-      if (g.shifts) cudaFree(g.shifts);
+      if (g.shifts) dev_free_on(b->ctx[0], g.shifts, b->cap_st);
       return rc;
     }
     it = b->graphs.emplace(key, g).first;
@@ -1554,8 +1701,9 @@ static int batch_eager(cola_batch* b, const cola_batch_plan& p, int n) {
   plan_groups(b->ctx, p.group, groups, hsh);
   int64_t* dsh = nullptr;
   if (!hsh.empty()) {
-    BCK(cudaMallocAsync(&dsh, hsh.size() * sizeof(int64_t), b->cap_st));
-    BCK(cudaMemcpyAsync(dsh, hsh.data(), hsh.size() * sizeof(int64_t), cudaMemcpyHostToDevice, b->cap_st));
+    dsh = static_cast<int64_t*>(dev_alloc_on(b->ctx[0], hsh.size() * sizeof(int64_t), b->cap_st));
+    if (!dsh) return bfail(b, COLA_ENOMEM, "batch step: shift array allocation failed");
+    BCK(write_words(dsh, hsh.data(), (int64_t)hsh.size(), b->cap_st));
   }
   int rc = COLA_OK;
   for (GroupPlan& gp : groups) {
@@ -1574,7 +1722,7 @@ static int batch_eager(cola_batch* b, const cola_batch_plan& p, int n) {
       break;
     }
   }
-  if (dsh) BCK(cudaFreeAsync(dsh, b->cap_st));
+  dev_free_on(b->ctx[0], dsh, b->cap_st);
   return rc == COLA_OK ? COLA_OK : bfail(b, rc, "batch step: " + b->err);
 }
 
@@ -1744,7 +1892,10 @@ int cola_batch_pk(cola_batch* b, int32_t nbins, double* k, double* pk, int64_t* 
   const int N = lead->Nm;
   const int64_t stride = 3 * (int64_t)kMaxBins;
   // [n][stride] accumulators, then the n shifts
-  if (!b->pk_acc) BCK(cudaMalloc(&b->pk_acc, ((size_t)n * stride + n) * sizeof(double)));
+  if (!b->pk_acc) {
+    b->pk_acc = static_cast<double*>(dev_alloc_on(lead, ((size_t)n * stride + n) * sizeof(double), b->st));
+    if (!b->pk_acc) return bfail(b, COLA_ENOMEM, "batch P(k): accumulator allocation failed");
+  }
   std::vector<int64_t> hsh(n);
   const char* base = static_cast<const char*>(lead->allocs[0]);
   for (int i = 0; i < n; ++i) hsh[i] = static_cast<const char*>(b->ctx[i]->allocs[0]) - base;
@@ -1818,8 +1969,16 @@ static int run_on_groups(cola_ctx* const* ctxs, int32_t n, void* stream, const c
   for (const auto& bk : buckets) plan_groups(bk, (int)bk.size(), groups, hsh);
   int64_t* dsh = nullptr;
   if (!hsh.empty()) {
-    CHECK_RC(ck(cudaMallocAsync(&dsh, hsh.size() * sizeof(int64_t), st), "shift buffer"));
-    CHECK_RC(ck(write_words(dsh, hsh.data(), (int64_t)hsh.size(), st), "shift upload"));
+    dsh = static_cast<int64_t*>(dev_alloc_on(ctxs[0], hsh.size() * sizeof(int64_t), st));
+    if (!dsh) {
+      g_err = std::string(who) + ": shift buffer allocation failed";
+      return COLA_ENOMEM;
+    }
+    int rc0 = ck(write_words(dsh, hsh.data(), (int64_t)hsh.size(), st), "shift upload");
+    if (rc0 != COLA_OK) {
+      dev_free_on(ctxs[0], dsh, st);
+      return rc0;
+    }
   }
   int rc = COLA_OK;
   for (GroupPlan& gp : groups) {
@@ -1836,7 +1995,7 @@ static int run_on_groups(cola_ctx* const* ctxs, int32_t n, void* stream, const c
       break;
     }
   }
-  if (dsh) cudaFreeAsync(dsh, st);
+  dev_free_on(ctxs[0], dsh, st);
   if (rc != COLA_OK) return rc;
   for (int i = 0; i < n; ++i) {
     cola_ctx* c = ctxs[i];
@@ -1900,9 +2059,9 @@ void cola_batch_free(cola_batch* b) {
   cudaStreamSynchronize(b->st);
   for (auto& kv : b->graphs) {
     cudaGraphExecDestroy(kv.second.exec);
-    if (kv.second.shifts) cudaFree(kv.second.shifts);
+    dev_free_on(b->ctx[0], kv.second.shifts, b->cap_st);
   }
-  if (b->pk_acc) cudaFree(b->pk_acc);
+  dev_free_on(b->ctx[0], b->pk_acc, b->st);
   if (b->cap_st) cudaStreamDestroy(b->cap_st);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);

@@ -3,9 +3,12 @@
 256^3 particles / 512^3 mesh, f(R) F5 + chameleon, 30 steps: sampled
 displacements against stored FP64 oracle values (tests/golden/oracle_main_f5.npz,
 written by make_full_size_oracle.py), P(k) per bin and the boost against the
-LCDM twin.  512^3 / 1024^3 nDGP: the 2LPT ICs at sampled particles against the
-oracle (oracle_big_ic.npz), and properties that hold at any size (mass
-conservation of the deposit, zero net PM force of an LCDM step).
+LCDM twin.  The screened nDGP workload: its whole 30-step run on a 128^3 / 256^3
+sub-box with the same spacing, cell and steps (oracle_ndgp_reduced.npz), and at
+512^3 / 1024^3 the 2LPT ICs (oracle_big_ic.npz) and one full step
+(oracle_big_ndgp_step1.npz) at sampled particles against the oracle, plus
+properties that hold at any size (mass conservation of the deposit, zero net PM
+force of an LCDM step).
 Tolerances as in test_gpu_parity: 1e-4 cell, 1e-4 in P(k) and the boost.
 """
 import os
@@ -55,6 +58,67 @@ def test_big_ndgp_ics_vs_stored_oracle():
     with pkg.Simulation(BIG_NDGP) as s:
         d0 = s.export(pkg.COLA_F_DISP).T[ref["idx"]]
     assert np.max(np.abs(d0 - ref["s0"])) / cell <= 1e-4
+
+
+def test_ndgp_reduced_box_full_run_vs_stored_oracle():
+    """The bench workload's model, particle spacing, cell size and time steps on a 128^3 / 256^3
+    sub-box (L = 256 Mpc/h), whole 30-step run with Vainshtein screening (Sec. 6.2, App. B)
+    against the FP64 oracle run stored by make_ndgp_reduced_oracle.py: sampled displacements at
+    a_ini and z = 0 (1e-4 cell), P(k) per bin (1e-4) and the boost against the LCDM twin (1e-4)."""
+    import paper_1703_00879_gb300 as pkg
+    from workloads import NDGP_REDUCED as run
+    ref = _load("oracle_ndgp_reduced.npz")
+    idx = ref["idx"]
+    cell = run.Lbox / run.Nmesh
+    with pkg.Simulation(run) as s:
+        d0 = s.export(pkg.COLA_F_DISP).T[idx]
+        assert np.max(np.abs(d0 - ref["s0"])) / cell <= 1e-4
+        s.run_to_end()
+        d = s.export(pkg.COLA_F_DISP).T[idx].astype(np.float64)
+        _, P, nm = s.pk()
+    err = np.abs(d - ref["s_final"]) / cell
+    print(f"\nreduced nDGP: max {err.max():.2e} cell, 99.9% {np.percentile(err, 99.9):.2e}, "
+          f"rms {np.sqrt((err ** 2).mean()):.2e}")
+    assert err.max() <= 1e-4
+    ok = ref["nm"] > 0
+    assert np.array_equal(nm[ok], ref["nm"][ok].astype(np.int64))
+    assert np.max(np.abs(P[ok] / ref["P"][ok] - 1)) <= 1e-4
+    with pkg.Simulation(run.with_model(LCDM_MODEL)) as s:
+        s.run_to_end()
+        _, P0, _ = s.pk()
+    assert np.max(np.abs(P[ok] / P0[ok] - ref["P"][ok] / ref["P_lcdm"][ok])) <= 1e-4
+
+
+def test_big_ndgp_one_step_vs_stored_oracle():
+    """The bench workload itself, 512^3 particles on the 1024^3 mesh with Vainshtein screening, in
+    the launch configuration the bench times: one full step (initial half kick with the force at
+    a_ini, drift, the screened force at a_1, second half kick) against the FP64 oracle step stored
+    by make_big_ndgp_step_oracle.py.  At the 4096 sampled particles: displacement within 1e-4
+    cell; the gathered PM force g = acc + A_LPT and the residual velocity within 1e-4 of their
+    largest sampled magnitude; every P(k) bin within 1e-4."""
+    import paper_1703_00879_gb300 as pkg
+    ref = _load("oracle_big_ndgp_step1.npz")
+    idx = ref["idx"]
+    cell = BIG_NDGP.Lbox / BIG_NDGP.Nmesh
+    with pkg.Simulation(BIG_NDGP) as s:
+        s.step(1)
+        d = s.export(pkg.COLA_F_DISP).T[idx].astype(np.float64)
+        dv = s.export(pkg.COLA_F_DV).T[idx].astype(np.float64)
+        acc = s.export(pkg.COLA_F_ACC).T[idx].astype(np.float64)
+        A = s.export(pkg.COLA_F_LPT_ACC).T[idx].astype(np.float64)
+        _, P, nm = s.pk()
+    err = np.abs(d - ref["s1"]) / cell
+    g = acc + A
+    eg = np.max(np.abs(g - ref["g1"])) / np.max(np.abs(ref["g1"]))
+    ev = np.max(np.abs(dv - ref["dv1"])) / np.max(np.abs(ref["dv1"]))
+    ok = ref["nm"] > 0
+    ep = float(np.max(np.abs(P[ok] / ref["P"][ok] - 1)))
+    print(f"\nbig nDGP step 1: disp max {err.max():.2e} cell, force {eg:.2e}, dv {ev:.2e}, P(k) {ep:.2e}")
+    assert err.max() <= 1e-4
+    assert eg <= 1e-4
+    assert ev <= 1e-4
+    assert np.array_equal(nm[ok], ref["nm"][ok].astype(np.int64))
+    assert ep <= 1e-4
 
 
 def test_big_mesh_mass_conservation_and_zero_net_force():

@@ -185,7 +185,7 @@ def test_small_config_run_vs_oracle(pkg, oracle_small):
     assert np.max(np.abs(P[ok] / Po[ok] - 1)) <= 1e-4
     L = SMALL_F5.Lbox
     dpos = (pos.astype(np.float64) - osim.positions() + L / 2) % L - L / 2   # periodic difference
-    assert np.max(np.abs(dpos)) / (L / SMALL_F5.Nmesh) <= 1e-4 + 1e-5
+    assert np.max(np.abs(dpos)) / (L / SMALL_F5.Nmesh) <= 1e-4
     v_ref = osim.velocities_kms()
     assert _relmax(vel, v_ref) < 1e-4
 

@@ -92,6 +92,10 @@ MAIN_F5 = Run(Np=256, Nmesh=512, Lbox=512.0, nsteps=30, model=F5,
               name="fR_F5_screened_256p_512m_L512_30steps")
 BIG_NDGP = Run(Np=512, Nmesh=1024, Lbox=1024.0, nsteps=30, model=NDGP1,
                name="nDGP_rc1_vainshtein_R1_512p_1024m_L1024_30steps")
+# The 512^3 / 1024^3 nDGP workload on a 128^3 / 256^3 sub-box: the same particle spacing,
+# cell size, model and time steps (the box the oracle runs in full).
+NDGP_REDUCED = Run(Np=128, Nmesh=256, Lbox=256.0, nsteps=30, model=NDGP1,
+                   name="nDGP_rc1_vainshtein_R1_128p_256m_L256_30steps")
 
 # Model cycle of the batched ensemble: seed mod 6 picks the model.
 ENSEMBLE_MODELS = (
