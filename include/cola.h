@@ -402,12 +402,19 @@ int cola_profile_read(cola_ctx* ctx, double* ms, int64_t* launches, double* byte
  *            rejected with COLA_EINVAL
  *   Lbox   : box side [Mpc/h];  nbins: 1..2000
  *   k, pk, nmodes : HOST arrays of nbins entries (any may be NULL), as cola_pk
- *   stream : cudaStream_t for the work; the call synchronises it.
+ *   stream : cudaStream_t for the work.  The call copies its bin sums to the
+ *            host and synchronises this stream before returning, so it must
+ *            not be called while the stream is being captured into a graph.
  * No cudaMalloc, cudaFree or allocating library routine is called.  The
- * first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the scratch and
- * it keeps the last call's contents (each call clears what must start at
+ * scratch is reserved when its module loads; with CUDA's lazy module loading
+ * that would be the first use, so cola_init loads it, once per device, with
+ * that device current (a failure there makes cola_init return COLA_ECUDA).
+ * A caller that never creates a context reserves it with its first
+ * cola_pk_noalloc call on the device, which may then fail with COLA_ECUDA if
+ * the device is out of memory.  Every call asks for the scratch's device
+ * address (cudaGetSymbolAddress) with the device current, so no cached
+ * address outlives a device reset.  All calls on a device share the scratch
+ * and it keeps the last call's contents (each call clears what must start at
  * zero), so calls whose device work could overlap race and must not be
  * issued.  Errors: COLA_EINVAL, COLA_ECUDA; message in cola_last_error(NULL).
  * --------------------------------------------------------------------- */

@@ -1010,6 +1010,11 @@ int cola_init(const cola_config* cfg, cola_alloc_fn alloc, cola_free_fn free_fn,
     cudaGetLastError();
     return fail(nullptr, COLA_ECUDA, "no CUDA device available");
   }
+  {
+    // the allocation-free P(k) scratch is reserved on this device now (see cola_pk_noalloc)
+    int rc = pk_noalloc_reserve();
+    if (rc) return rc;
+  }
   cola_ctx* ctx = new cola_ctx();
   ctx->cfg = *cfg;
   ctx->st = static_cast<cudaStream_t>(stream);

@@ -86,8 +86,9 @@ struct SimHeader {
 // One launch over several simulations of one shape.  Each simulation's
 // buffers sit at the same offsets of its own allocation, so simulation b's
 // pointers are simulation 0's moved by shift[b] bytes.  shift == nullptr: a
-// single simulation.  Shared read-only tables (twiddles) are never moved;
-// per-simulation parameters are reached through the moved SimHeader.
+// single simulation.  Read-only tables equal in every simulation of a launch
+// (twiddles) are read from the first simulation's copy, unmoved; per-simulation
+// parameters are reached through the moved SimHeader.
 struct Multi {
   const int64_t* shift = nullptr;
   int nb = 1;
@@ -274,6 +275,10 @@ cudaError_t seed_quantise(int N, const float2* src, void* dst, int prec, const S
 // Caps the persistent grid of the FFT-pass kernels launched by the calling
 // thread (0 = no cap: resident CTAs x SMs).
 void set_grid_cap(int max_ctas);
+
+// Loads the allocation-free P(k) scratch on the current device (once per
+// device; later calls return at once).  COLA_OK or COLA_ECUDA.
+int pk_noalloc_reserve();
 
 // Sets the message cola_last_error(NULL) returns (calling thread).
 void set_context_free_error(const std::string& msg);

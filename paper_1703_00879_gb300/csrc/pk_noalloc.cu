@@ -44,32 +44,42 @@ constexpr size_t kScratchBytes = kTwBytes + kAccBytes + kRhoBytes + kHalfBytes;
 static __device__ __align__(256) unsigned char g_pk_scratch[kScratchBytes];
 
 std::mutex g_mu;
-std::vector<void*> g_addr;  // per device: device address of g_pk_scratch
+std::vector<char> g_reserved;  // per device: the scratch's module has been loaded
 
 int na_fail(int code, const std::string& m) {
   cola::set_context_free_error(m);  // reported by cola_last_error(NULL)
   return code;
 }
 
-// Once per device, with that device current: the device address of the scratch.
+// The device address of the scratch on the current device.  Asked for on every
+// call (cheap once the module is loaded), so no address outlives a device reset.
 int scratch_address(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return na_fail(COLA_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  std::lock_guard<std::mutex> lk(g_mu);
-  if ((int)g_addr.size() <= dev) g_addr.resize(dev + 1, nullptr);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_pk_scratch);
-    if (e != cudaSuccess || !p)
-      return na_fail(COLA_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_addr[dev] = p;
-  }
-  *out = static_cast<unsigned char*>(g_addr[dev]);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_pk_scratch);
+  if (e != cudaSuccess || !p)
+    return na_fail(COLA_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = static_cast<unsigned char*>(p);
   return COLA_OK;
 }
 
 }  // namespace
+
+// Set-up, once per device with that device current (cola_init calls it): with
+// lazy module loading the scratch is reserved only when its module loads, so
+// this loads it now, at a known time, rather than at the first cola_pk_noalloc.
+int cola::pk_noalloc_reserve() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return na_fail(COLA_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  std::lock_guard<std::mutex> lk(g_mu);
+  if ((int)g_reserved.size() <= dev) g_reserved.resize(dev + 1, 0);
+  if (g_reserved[dev]) return COLA_OK;
+  unsigned char* p = nullptr;
+  const int rc = scratch_address(&p);
+  if (rc != COLA_OK) return rc;
+  g_reserved[dev] = 1;
+  return COLA_OK;
+}
 
 extern "C" int cola_pk_noalloc(const float* pos, int64_t n, int32_t nmesh, double Lbox,
                                int32_t nbins, double* k, double* pk, int64_t* nmodes,

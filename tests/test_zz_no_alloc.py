@@ -25,7 +25,7 @@ def _device_positions(pkg, sim, run):
     return pos
 
 
-@pytest.mark.parametrize("nmesh", [32, 64])
+@pytest.mark.parametrize("nmesh", [32, 64, 128])
 def test_pk_noalloc_matches_cola_pk_on_two_calls(nmesh):
     import torch
 
@@ -37,8 +37,15 @@ def test_pk_noalloc_matches_cola_pk_on_two_calls(nmesh):
         pos = _device_positions(pkg, sim, run)
         stream = torch.cuda.current_stream().cuda_stream
         ok = n0 > 0
-        for _ in range(2):
+        free_before = None
+        for call in range(2):
             k, p, n = pkg.cola_pk_noalloc(pos.data_ptr(), pos.shape[0], nmesh, run.Lbox, nmesh // 2, stream)
+            torch.cuda.synchronize()
+            if call == 0:
+                free_before = torch.cuda.mem_get_info()[0]
+            else:
+                # the second call allocated nothing: the device's free memory is unchanged
+                assert torch.cuda.mem_get_info()[0] == free_before
             assert np.array_equal(n, n0)
             assert np.allclose(k[ok], k0[ok], rtol=1e-12)
             assert np.max(np.abs(p[ok] / p0[ok] - 1.0)) <= 1e-4
