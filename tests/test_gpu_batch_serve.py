@@ -47,6 +47,31 @@ def test_batch_equals_solo(plan):
         s.close()
 
 
+def test_batch_members_vs_oracle():
+    """One member of every model class of the ensemble (LCDM, f(R) 1e-6/1e-5/1e-4, nDGP r_c H0 = 1
+    and 5, each screened) advanced together in one batch, against the FP64 oracle run of the same
+    record: displacements within 1e-4 cell, every P(k) bin within 1e-4 (Sec. 2, Sec. 6, App. B)."""
+    import paper_1703_00879_gb300 as pkg
+    from oracle.cola import Simulation as OracleSim
+    runs = _runs(len(ENSEMBLE_MODELS))
+    sims = [pkg.Simulation(r) for r in runs]
+    with pkg.Batch(sims) as b:
+        b.step(-1)
+        k, P, nm = b.pk()
+    for i, (r, s) in enumerate(zip(runs, sims)):
+        o = OracleSim(r).run_to_end()
+        d = s.export(pkg.COLA_F_DISP).T.astype(np.float64)
+        err = np.max(np.abs(d - o.s)) / (r.Lbox / r.Nmesh)
+        ko, Po, nmo = o.power_spectrum(r.Nmesh // 2)
+        ok = nmo > 0
+        print(f"\nbatch member {i} (model kind {r.model.kind}): {err:.2e} cell, "
+              f"P(k) {np.max(np.abs(P[i][ok] / Po[ok] - 1)):.2e}")
+        assert err <= 1e-4
+        assert np.array_equal(nm[i][ok], nmo[ok].astype(np.int64))
+        assert np.max(np.abs(P[i][ok] / Po[ok] - 1)) <= 1e-4
+        s.close()
+
+
 def test_batch_of_mixed_shapes_runs_one_context_per_group():
     import paper_1703_00879_gb300 as pkg
     runs = [ensemble_run(0, Np=32, Nmesh=64, Lbox=64.0, nsteps=3),
@@ -184,3 +209,13 @@ def test_serving_results_equal_solo_runs():
         assert np.max(np.abs(res.pk[ok] / P[ok] - 1)) <= 1e-4
     s = st.summary()
     assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
+    # two served requests (one of each size) against the FP64 oracle run of the same record
+    from oracle.cola import Simulation as OracleSim
+    picked = {}
+    for res in st.results:
+        picked.setdefault(res.run.Np, res)
+    for res in picked.values():
+        ko, Po, nmo = OracleSim(res.run).run_to_end().power_spectrum(len(res.pk))
+        ok = nmo > 0
+        assert np.array_equal(res.nmodes[ok], nmo[ok].astype(np.int64))
+        assert np.max(np.abs(res.pk[ok] / Po[ok] - 1)) <= 1e-4, res.run

@@ -20,3 +20,39 @@ def test_e4_e7_small():
     for r in r7.values():
         for n in ("10", "20"):
             assert np.isfinite(r["max_dev_vs_n30"][n]["k<1"])
+
+
+def _oracle_boost(run, model, nbins):
+    from oracle.cola import Simulation as OracleSim
+    from workloads import Model
+    _, p0, n0 = OracleSim(run.with_model(Model())).run_to_end().power_spectrum(nbins)
+    _, p1, _ = OracleSim(run.with_model(model)).run_to_end().power_spectrum(nbins)
+    ok = (n0 > 0) & (p0 > 0)
+    return p1[ok] / p0[ok]
+
+
+def test_e4_e7_boosts_vs_oracle():
+    """The Sec. 7.1 and Sec. 7.3 boosts B(k) = P_MG/P_LCDM at 32^3 particles on a 64^3 mesh against
+    the same boosts from FP64 oracle runs of the same records, within 1e-4 absolute per bin: e4's
+    three F5 variants (true growth, LCDM growth, no screening) at n = 10, and e7's F5, F6 and
+    nDGP boosts at n = 10 and 20."""
+    pytest.importorskip("torch")
+    from paper_1703_00879_gb300 import experiments as ex
+    from workloads import FOFR, Cosmo, Model, Run
+    Np, Nm, nb = 32, 64, 16
+    r4 = ex.e4(Np, Nm, nb)
+    run4 = Run(Np=Np, Nmesh=Nm, Lbox=250.0 * Np / 512, nsteps=10, cosmo=ex.PAPER_FR_COSMO, seed=7, name="e4")
+    for key, model in (("B_true", ex.F5), ("B_lcdm_growth", Model(kind=FOFR, fR0=1e-5, screening=1,
+                                                                   scale_dependent=0)),
+                       ("B_noscreen", Model(kind=FOFR, fR0=1e-5, screening=0))):
+        Bo = _oracle_boost(run4, model, nb)
+        assert np.max(np.abs(np.asarray(r4[key]) - Bo)) <= 1e-4, key
+    r7 = {r["model"]: r for r in ex.e7(Np, Nm, nb)}
+    for name, model, L, cosmo in (("F5", ex.F5, 250.0, ex.PAPER_FR_COSMO), ("F6", ex.F6, 250.0, ex.PAPER_FR_COSMO),
+                                  ("nDGP_rc1", ex.N1, 512.0, Cosmo())):
+        base = Run(Np=Np, Nmesh=Nm, Lbox=L * Np / 512, nsteps=30, cosmo=cosmo, seed=11, name="e7")
+        for n in (10, 20):
+            Bo = _oracle_boost(base.with_(nsteps=n), model, nb)
+            err = np.max(np.abs(np.asarray(r7[name][f"B_n{n}"]) - Bo))
+            print(f"\ne7 {name} n={n}: max |B - B_oracle| = {err:.2e}")
+            assert err <= 1e-4, (name, n)
