@@ -39,6 +39,9 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 FALLBACK_HBM_GBS = 6800.0
 
 WORKLOADS = {"big": W.BIG_NDGP, "main": W.MAIN_F5, "small": W.SMALL_F5}
+PRECISION = {0: "FP32 seeds and LPT fields",
+             1: "BF16 seeds and per-step LPT fields, one FP32 scale per field, FP32 arithmetic",
+             2: "FP16 seeds and per-step LPT fields, one FP32 scale per field, FP32 arithmetic"}
 
 
 # ---------------------------------------------------------------- distributed helpers
@@ -219,7 +222,7 @@ def bench_ours(args):
     base = WORKLOADS[args.workload]
     run = replica_run(base, rank, args.warmup + args.steps)
     stream = torch.cuda.current_stream()
-    sim = pkg.Simulation(run, lpt_fast=args.lpt_fast)
+    sim = pkg.Simulation(run, lpt_fast=args.lpt_fast, seed_precision=args.seed_precision)
     sim.step(args.warmup)
     torch.cuda.synchronize()
     barrier(dist)
@@ -271,7 +274,8 @@ def bench_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(run, world, args.lpt_fast),
+            "config": dict(workload_config(run, world, args.lpt_fast),
+                           precision=PRECISION[args.seed_precision]),
             "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback", "unit": "GB/s", "frac": achieved / peak,
@@ -301,7 +305,7 @@ def bench_e2e(args, run, pkg, dist, world):
     barrier(dist)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim = pkg.Simulation(e2e_run, lpt_fast=args.lpt_fast)
+    sim = pkg.Simulation(e2e_run, lpt_fast=args.lpt_fast, seed_precision=args.seed_precision)
     sim.step(args.steps)
     pos, vel = sim.snapshot()
     k, pk, nm = sim.pk()
@@ -481,6 +485,8 @@ def main(argv=None):
     ap.add_argument("--lpt-fast", action="store_true",
                     help="scale-independent LPT fast path (models whose growth does not depend on k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed-precision", type=int, choices=[0, 1, 2], default=0,
+                    help="variant a.S1: 0 FP32, 1 BF16, 2 FP16 seeds and per-step LPT fields")
     ap.add_argument("--ensemble", action="store_true", help="batched ensemble benchmark instead")
     ap.add_argument("--ensemble-size", type=int, default=256)
     ap.add_argument("--ensemble-solo", type=int, default=48)

@@ -64,6 +64,9 @@ struct cola_ctx {
   // LPT work
   float2* lc[6] = {};
   float* lr[6] = {};
+  // reduced-precision variant: the per-step drift (0..2) and kick (3..5) LPT
+  // fields as 16-bit values with one FP32 scale per field (SimHeader lq_*)
+  uint16_t* lq[6] = {};
   // mesh
   float* rho = nullptr;
   float2 *Cd = nullptr, *Ck = nullptr, *Cw = nullptr, *Cphi = nullptr, *Cphz = nullptr;
@@ -596,6 +599,7 @@ void context_layout(cola_ctx* c, const cola_config& cfg, Layout& L) {
   for (int i = 0; i < 6; ++i) {
     L.add(&c->lc[i], hp);
     L.add(&c->lr[i], P);
+    if (cfg.seed_precision) L.add(&c->lq[i], P);
   }
   L.add(&c->rho, M);
   L.add(&c->Cd, hm);
@@ -704,13 +708,22 @@ int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}) {
   CK(fft_col(N, ctx->lc[3], 1, true, ctx->tw_np, st, m));
   prof_end(ctx, ST_LPT_Y, e, 4, m.nb * 10.0 * H);
   e = prof_begin(ctx);
+  // variant a.S1: the per-step drift and kick fields leave the x pass as 16-bit
+  // values (one FP32 scale per field, delayed scaling)
+  const bool q16 = lp.seed_prec != 0 && vel == 0 && add_step;
   {
     const float2* in6[6] = {ctx->lc[0], ctx->lc[4], ctx->lc[1], ctx->lc[2], ctx->lc[5], ctx->lc[3]};
-    float* out6[6] = {ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->lr[3], ctx->lr[4], ctx->lr[5]};
     const float kfs6[6] = {kf, 0.f, 0.f, kf, 0.f, 0.f};
-    CK(fft_xc2r_multi(N, 6, in6, out6, kfs6, ctx->tw_np, st, m));
+    if (q16) {
+      void* out6[6] = {ctx->lq[0], ctx->lq[1], ctx->lq[2], ctx->lq[3], ctx->lq[4], ctx->lq[5]};
+      CK(fft_xc2r_multi16(N, 6, in6, out6, kfs6, lp.seed_prec, ctx->hdr, ctx->tw_np, st, m));
+      CK(lq_update(ctx->hdr, lp.seed_prec, st, m));
+    } else {
+      float* out6[6] = {ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->lr[3], ctx->lr[4], ctx->lr[5]};
+      CK(fft_xc2r_multi(N, 6, in6, out6, kfs6, ctx->tw_np, st, m));
+    }
   }
-  prof_end(ctx, ST_LPT_X, e, 1, m.nb * 6 * (H + R));
+  prof_end(ctx, ST_LPT_X, e, q16 ? 2 : 1, m.nb * 6 * (H + (q16 ? 0.5 : 1.0) * R));
   ctx->have_lpt = true;
   return COLA_OK;
 }
@@ -909,6 +922,11 @@ int ic_group(const Group& g, bool potentials) {
     return COLA_OK;
   }
   CHECK_RC(run_lpt(ctx, 0, 0, false, m));
+  if (ctx->cfg.seed_precision) {
+    // first scales of the 16-bit per-step fields: the drift and kick fields at a_ini
+    const float* f6[6] = {ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->lr[3], ctx->lr[4], ctx->lr[5]};
+    CK(lq_init(ctx->hdr, f6, ctx->P, ctx->cfg.seed_precision, st, m));
+  }
   CK(ic_particles(ctx->P, ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->s[0], ctx->s[1], ctx->s[2],
                   ctx->v[0], ctx->v[1], ctx->v[2], st, m));
   CK(zero_f32(ctx->rho, ctx->M, st, m));
@@ -964,27 +982,39 @@ int enqueue_group_step(const Group& g, int n) {
   const Multi m = g.all;
   const PartParams pp = part_params(ctx);
   const double Pb = (double)ctx->P, Mb = (double)ctx->M;
-  const StepDt dt{ctx->hdr, 0.f, 0.f};
+  const StepDt dt0{ctx->hdr, 0.f, 0.f};
   // fast path: the step's LPT fields are combinations of Psi1, Psi2 formed in
   // the particle kernels (row 1 + step), no LPT transforms
   const bool fast = ctx->lpt_fast;
   const LptMix mix = fast ? lpt_mix_of(ctx, 1, 1, false) : LptMix{};
   if (!fast) CHECK_RC(run_lpt(ctx, 0, 1, true, m));
+  // variant a.S1: the drift and kick read the 16-bit fields
+  const int lq = (!fast && ctx->cfg.seed_precision) ? ctx->cfg.seed_precision : 0;
+  StepDt dt = dt0;
+  dt.lq = lq;
+  const float* ld[3] = {ctx->lr[0], ctx->lr[1], ctx->lr[2]};
+  const float* lk[3] = {ctx->lr[3], ctx->lr[4], ctx->lr[5]};
+  if (lq)
+    for (int d = 0; d < 3; ++d) {
+      ld[d] = reinterpret_cast<const float*>(ctx->lq[d]);
+      lk[d] = reinterpret_cast<const float*>(ctx->lq[3 + d]);
+    }
   cudaEvent_t e = prof_begin(ctx);
   CK(zero_f32(ctx->rho, ctx->M, ctx->st, m));
   prof_end(ctx, ST_RHO_ZERO, e, 1, m.nb * 4.0 * Mb);
   e = prof_begin(ctx);
   CK(part_drift_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
-                        ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[0], ctx->lr[1],
-                        ctx->lr[2], ctx->rho, dt, ctx->P, ctx->st, m, mix));
-  prof_end(ctx, ST_DRIFT_DEPOSIT, e, 1, m.nb * ((fast ? 84.0 : 72.0) * Pb + 8.0 * Mb));
+                        ctx->acc[0], ctx->acc[1], ctx->acc[2], ld[0], ld[1], ld[2], ctx->rho, dt,
+                        ctx->P, ctx->st, m, mix));
+  prof_end(ctx, ST_DRIFT_DEPOSIT, e, 1, m.nb * ((fast ? 84.0 : lq ? 66.0 : 72.0) * Pb + 8.0 * Mb));
   CHECK_RC(force_group(g, ctx->a[n + 1], true));
   e = prof_begin(ctx);
-  const int ka = fast ? 0 : 3;  // A_LPT, or Psi1 mixed with Psi2
+  if (fast)  // A_LPT: Psi1 (lr[0..2]) mixed with Psi2
+    for (int d = 0; d < 3; ++d) lk[d] = ctx->lr[d];
   CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
-                      ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[ka], ctx->lr[ka + 1],
-                      ctx->lr[ka + 2], ctx->F[0], ctx->F[1], ctx->F[2], dt, ctx->P, ctx->st, m, mix));
-  prof_end(ctx, ST_GATHER_KICK, e, 1, m.nb * ((fast ? 72.0 : 60.0) * Pb + 12.0 * Mb));
+                      ctx->acc[0], ctx->acc[1], ctx->acc[2], lk[0], lk[1], lk[2], ctx->F[0], ctx->F[1],
+                      ctx->F[2], dt, ctx->P, ctx->st, m, mix));
+  prof_end(ctx, ST_GATHER_KICK, e, 1, m.nb * ((fast ? 72.0 : lq ? 54.0 : 60.0) * Pb + 12.0 * Mb));
   CK(step_advance(ctx->hdr, ctx->st, m));
   return COLA_OK;
 }
@@ -1443,6 +1473,15 @@ int cola_export(cola_ctx* ctx, int32_t which, void* dst, int32_t where) {
         const float* psi1[3] = {ctx->lr[0], ctx->lr[1], ctx->lr[2]};
         CK(lpt_mix(ctx->P, psi1, lpt_mix_of(ctx, ctx->step, 0, false), o == 3 ? 1 : 0, tmp, ctx->st));
         for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * pb, tmp[c], pb, where));
+        return COLA_OK;
+      }
+      if (ctx->cfg.seed_precision && ctx->step > 0) {
+        // variant a.S1: the last step's fields are the 16-bit ones, dequantised
+        float* tmp = reinterpret_cast<float*>(ctx->lc[0]);
+        for (int c = 0; c < 3; ++c) {
+          CK(lq_dequant(ctx->lq[o + c], tmp, ctx->P, ctx->cfg.seed_precision, ctx->hdr, o + c, ctx->st));
+          CHECK_RC(copy_out(ctx, d + c * pb, tmp, pb, where));
+        }
         return COLA_OK;
       }
       for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * pb, ctx->lr[o + c], pb, where));

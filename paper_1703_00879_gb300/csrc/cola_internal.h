@@ -81,6 +81,13 @@ struct SimHeader {
   unsigned long long seed; // white-noise seed
   EHDev eh;                // spectrum of the initial conditions
   ForceParams fp_ini;      // force parameters at a_ini
+  // Reduced-precision LPT fields (16-bit per-step drift and kick fields, one
+  // FP32 scale per field; written on the device only): lq_scale quantises the
+  // next pass, lq_used dequantises the fields of the current step, lq_amax
+  // collects the largest |value| a pass writes (delayed scaling).
+  float lq_scale[6];
+  float lq_used[6];
+  float lq_amax[6];
 };
 
 // One launch over several simulations of one shape.  Each simulation's
@@ -150,6 +157,11 @@ cudaError_t fft_xc2r(int N, const float2* in, float* out, float kfs, const float
 // up to six independent c2r row passes in one launch
 cudaError_t fft_xc2r_multi(int N, int njobs, const float2* const* in, float* const* out,
                            const float* kfs, const float2* tw, cudaStream_t s, Multi m = {});
+// the same with 16-bit outputs (prec 1 bf16, 2 fp16): job j writes value / hdr->lq_scale[j]
+// and adds its largest |value| into hdr->lq_amax[j] (hdr moved per simulation)
+cudaError_t fft_xc2r_multi16(int N, int njobs, const float2* const* in, void* const* out,
+                             const float* kfs, int prec, const SimHeader* hdr, const float2* tw,
+                             cudaStream_t s, Multi m = {});
 // axis 1 = y, 2 = z; in place
 cudaError_t fft_col(int N, float2* data, int axis, bool inv, const float2* tw, cudaStream_t s,
                     Multi m = {});
@@ -187,6 +199,10 @@ cudaError_t part_deposit(const PartParams& pp, const float* sx, const float* sy,
 struct StepDt {
   const SimHeader* hdr;
   float dtk, dtd;
+  // 0: the LPT field arguments of the drift / kick are FP32 arrays; 1 bf16, 2
+  // fp16: 16-bit arrays dequantised with hdr->lq_used (fields 0..2 drift,
+  // 3..5 kick; needs hdr)
+  int lq = 0;
 };
 // Scale-independent LPT fields (the fast path for k-independent growth): the
 // LPT fields of a step are c1 Psi1 + c2 Psi2 of the real-space fields
@@ -217,6 +233,19 @@ cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float*
                              float* ay, float* az, const float* Ax, const float* Ay,
                              const float* Az, const float* Fx, const float* Fy, const float* Fz,
                              StepDt dt, int64_t P, cudaStream_t s, Multi m = {}, LptMix mix = {});
+// Per simulation: lq_used = lq_scale (the scale the fields just written carry),
+// lq_scale = lq_amax / target (for the next pass; unchanged if nothing was
+// written), lq_amax = 0.  target: the largest 16-bit value maps to it (fp16
+// 2^14, four times below the format's largest finite value; bf16 1).
+cudaError_t lq_update(SimHeader* hdr, int prec, cudaStream_t s, Multi m = {});
+// Initial scales from six FP32 fields of P values (the LPT fields at a_ini):
+// lq_scale = lq_used = max |field| / target, lq_amax = 0.
+cudaError_t lq_init(SimHeader* hdr, const float* const* fields, int64_t P, int prec, cudaStream_t s,
+                    Multi m = {});
+// FP32 copy of the 16-bit field f (dequantised with lq_used[f]), one simulation.
+cudaError_t lq_dequant(const void* src, float* dst, int64_t P, int prec, const SimHeader* hdr, int f,
+                       cudaStream_t s);
+
 // hdr->step += 1 (end of a step)
 cudaError_t step_advance(SimHeader* hdr, cudaStream_t s, Multi m = {});
 // hdr = v (one simulation), except the seed scales, which keep their device values

@@ -1036,6 +1036,7 @@ struct RowJobs {
   float kfs[6];
   int njobs;
   uint32_t jmul, jshift;  // q / njobs = (umulhi(q, jmul) + q) >> jshift for q < 2^31
+  const SimHeader* hdr;   // 16-bit outputs: scales and absmax of each job (moved per simulation)
 };
 
 // Division by an invariant integer d >= 1 through a multiply-high (Granlund and
@@ -1056,13 +1057,14 @@ __device__ __forceinline__ uint32_t fast_div(uint32_t n, uint32_t mul, uint32_t 
 struct JobTile {
   int job;
   int64_t row0, by;
+  uint32_t q;  // simulation * njobs + job
 };
 template <int N, int TWX>
 __device__ __forceinline__ JobTile job_tile(int64_t t64, const RowJobs& jobs, const Multi& m) {
   constexpr uint32_t TPJ = (uint32_t)N * N / TWX;  // tiles per job
   const uint32_t t = (uint32_t)t64, q = t / TPJ;     // q = simulation * njobs + job
   const uint32_t b = fast_div(q, jobs.jmul, jobs.jshift);
-  return JobTile{(int)(q - b * (uint32_t)jobs.njobs), (int64_t)(t - q * TPJ) * TWX, shift_of(m, (int)b)};
+  return JobTile{(int)(q - b * (uint32_t)jobs.njobs), (int64_t)(t - q * TPJ) * TWX, shift_of(m, (int)b), q};
 }
 
 // Store hook of the c2r row transform: tile row r's M complex outputs (2M
@@ -1077,7 +1079,41 @@ struct RealRowOut {
   }
 };
 
-template <int N, int TWX>
+// The same with 16-bit outputs (variant a.S1, the six per-step LPT fields):
+// value / scale as bf16 (OUT 1) or fp16 (OUT 2, saturated at the largest
+// finite value), two reals per 32-bit word; the largest |value| is kept in *amax.
+template <int M, int OUT>
+struct RealRowOut16 {
+  static constexpr bool kSmem = false;
+  uint32_t *o0, *o1;
+  float inv;
+  float* amax;
+  __device__ __forceinline__ float2 operator()(float2 v, int r, int k) const {
+    *amax = fmaxf(*amax, fmaxf(fabsf(v.x), fabsf(v.y)));
+    float a = v.x * inv, b = v.y * inv;
+    uint32_t w;
+    if constexpr (OUT == 1) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+      w = *reinterpret_cast<const uint32_t*>(&h);
+    } else {
+      a = fminf(fmaxf(a, -65504.f), 65504.f);
+      b = fminf(fmaxf(b, -65504.f), 65504.f);
+      const __half2 h = __floats2half2_rn(a, b);
+      w = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    ((r & 1) ? o1 : o0)[(r >> 1) * M + k] = w;
+    return v;
+  }
+};
+
+// Largest |value| of a job's tiles into hdr->lq_amax[job] (one atomic per warp).
+__device__ __forceinline__ void amax_flush(const SimHeader* h, int job, float a) {
+  const unsigned ua = __reduce_max_sync(0xffffffffu, __float_as_uint(a));
+  if ((threadIdx.x & 31) == 0 && ua != 0u && h)
+    atomicMax(reinterpret_cast<unsigned*>(const_cast<float*>(&h->lq_amax[job])), ua);
+}
+
+template <int N, int TWX, int OUT = 0>
 __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_constant__ RowJobs jobs,
                                                 const float2* __restrict__ twg, int64_t tiles_per_job,
                                                 Multi m) {
@@ -1096,6 +1132,11 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
   }
   cp_async_commit();
   int cur = 0;
+  // 16-bit outputs: running |value| maximum of the current (simulation, job)
+  float run_max = 0.f;
+  uint32_t run_q = 0xffffffffu;
+  const SimHeader* run_h = nullptr;
+  int run_job = 0;
   for (; t < ntiles; t += gridDim.x) {
     const JobTile j = job_tile<N, TWX>(t, jobs, m);
     const int64_t tn = t + gridDim.x;
@@ -1111,13 +1152,31 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
     row_c2r_combine<N, TWX>(buf, tw, jobs.kfs[j.job]);
     // even tile rows go to one block of consecutive real rows, odd ones to
     // another, straight from the transform's last step
-    float* out = moved(static_cast<float*>(jobs.out[j.job]), j.by);
-    const RealRowOut<M> o{reinterpret_cast<float2*>(out + real_row_q(j.row0, N) * N),
-                          reinterpret_cast<float2*>(out + real_row_q(j.row0 + 1, N) * N)};
-    fft_rowtile<M, TWX, C::CW, NT, true, 2, NoPre, false, RealRowOut<M>>(buf, tw, NoPre{}, o);
+    if constexpr (OUT == 0) {
+      float* out = moved(static_cast<float*>(jobs.out[j.job]), j.by);
+      const RealRowOut<M> o{reinterpret_cast<float2*>(out + real_row_q(j.row0, N) * N),
+                            reinterpret_cast<float2*>(out + real_row_q(j.row0 + 1, N) * N)};
+      fft_rowtile<M, TWX, C::CW, NT, true, 2, NoPre, false, RealRowOut<M>>(buf, tw, NoPre{}, o);
+    } else {
+      const SimHeader* h = moved(jobs.hdr, j.by);
+      if (j.q != run_q) {  // the same for every thread of the CTA
+        amax_flush(run_h, run_job, run_max);
+        run_max = 0.f;
+        run_q = j.q;
+        run_h = h;
+        run_job = j.job;
+      }
+      uint32_t* out = moved(static_cast<uint32_t*>(jobs.out[j.job]), j.by);
+      float tile_max = 0.f;
+      const RealRowOut16<M, OUT> o{out + real_row_q(j.row0, N) * M, out + real_row_q(j.row0 + 1, N) * M,
+                                   1.f / h->lq_scale[j.job], &tile_max};
+      fft_rowtile<M, TWX, C::CW, NT, true, 2, NoPre, false, RealRowOut16<M, OUT>>(buf, tw, NoPre{}, o);
+      run_max = fmaxf(run_max, tile_max);
+    }
     __syncthreads();
     cur ^= 1;
   }
+  if constexpr (OUT != 0) amax_flush(run_h, run_job, run_max);
   cp_async_wait<0>();
 }
 
@@ -1304,6 +1363,48 @@ cudaError_t fft_xc2r_multi(int Nv, int njobs, const float2* const* in, float* co
   if (njobs < 1 || njobs > 6) return cudaErrorInvalidValue;
   COLA_SWITCH_N(Nv, return launch_xc2r_multi<N>(njobs, in, out, kfs, tw, s, m));
   return cudaSuccess;
+}
+
+template <int N, int OUT>
+static cudaError_t launch_xc2r_multi16(int njobs, const float2* const* in, void* const* out, const float* kfs,
+                                       const SimHeader* hdr, const float2* tw, cudaStream_t s, Multi m) {
+  constexpr int TWX = row_tw(N);
+  const size_t sm = row_smem<N>();
+  RowJobs jobs{};
+  jobs.njobs = njobs;
+  jobs.hdr = hdr;
+  fast_div_magic((uint32_t)njobs, jobs.jmul, jobs.jshift);
+  for (int i = 0; i < njobs; ++i) {
+    jobs.in[i] = in[i];
+    jobs.out[i] = out[i];
+    jobs.kfs[i] = kfs[i];
+  }
+  const int64_t tpj = (int64_t)N * N / TWX;
+  auto k = k_xc2r<N, TWX, OUT>;
+  unsigned grid;
+  cudaError_t e = prep(k, sm, tpj * njobs * m.nb, grid);
+  if (e != cudaSuccess) return e;
+  k<<<grid, NT, sm, s>>>(jobs, tw, tpj, m);
+  return cudaGetLastError();
+}
+
+cudaError_t fft_xc2r_multi16(int Nv, int njobs, const float2* const* in, void* const* out, const float* kfs,
+                             int prec, const SimHeader* hdr, const float2* tw, cudaStream_t s, Multi m) {
+  if (njobs < 1 || njobs > 6 || !hdr || (prec != 1 && prec != 2)) return cudaErrorInvalidValue;
+#define COLA_C2R16(NN)                                                                                    \
+  case NN:                                                                                               \
+    return prec == 1 ? launch_xc2r_multi16<NN, 1>(njobs, in, out, kfs, hdr, tw, s, m)                    \
+                     : launch_xc2r_multi16<NN, 2>(njobs, in, out, kfs, hdr, tw, s, m);
+  switch (Nv) {
+    COLA_C2R16(32)
+    COLA_C2R16(64)
+    COLA_C2R16(128)
+    COLA_C2R16(256)
+    COLA_C2R16(512)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef COLA_C2R16
 }
 
 cudaError_t fft_xc2r(int Nv, const float2* in, float* out, float kfs, const float2* tw,

@@ -141,8 +141,8 @@ def test_big_mesh_mass_conservation_and_zero_net_force():
 
 @pytest.mark.parametrize("prec,u", [(1, 2.0 ** -8), (2, 2.0 ** -11)], ids=["bf16", "fp16"])
 def test_big_ndgp_reduced_seeds(prec, u):
-    """Precision variant at 512^3 / 1024^3: BF16 / FP16 seeds with a per-field
-    scale.  At a_ini the sampled displacements sit within the Parseval bound
+    """Precision variant at 512^3 / 1024^3: BF16 / FP16 seeds and per-step LPT fields
+    with a per-field scale.  At a_ini the sampled displacements sit within the Parseval bound
     u (RMS|grad phi1| + 3/7 RMS|grad phi2|) of the FP64 oracle (RMS over the
     4096 samples, with a factor 1.5 for sampling); after 30 steps the RMS
     position difference to the FP32 run and the P(k) difference per bin are
@@ -164,15 +164,16 @@ def test_big_ndgp_reduced_seeds(prec, u):
     e0 = rms(d0 - ref["s0"])
     bound0 = u * (ref["rms_psi"][0] + 3.0 / 7.0 * ref["rms_psi"][1]) + 2e-5 * np.max(np.abs(ref["s0"]))
     e1 = rms(d - d32)
-    bound1 = 2.0 * 1.5 * bound0 * rms(d32) / rms(ref["s0"])
+    # seeds (scaled by the displacement growth, factor 2 nonlinear) and the 16-bit LPT fields (2u)
+    bound1 = 1.5 * (2.0 * bound0 * rms(d32) / rms(ref["s0"]) + 2.0 * u * rms(d32))
     ok = nm > 0
     perr = float(np.max(np.abs(P[ok] / P32[ok] - 1)))
     print(f"\nprec {prec}: a_ini RMS err vs FP64 oracle {e0 / cell:.3e} cell (bound {1.5 * bound0 / cell:.3e}); "
           f"z=0 RMS diff vs FP32 {e1 / cell:.3e} cell (bound {bound1 / cell:.3e}); "
-          f"P(k) max rel diff vs FP32 {perr:.3e} (bound {4 * u:.3e})")
+          f"P(k) max rel diff vs FP32 {perr:.3e} (bound {6 * u:.3e})")
     assert e0 <= 1.5 * bound0
     assert e1 <= bound1
-    assert perr <= 4 * u
+    assert perr <= 6 * u
 
 
 # ------------------------------------------------------------------ 1024^3 mesh force against closed forms
