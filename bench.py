@@ -259,15 +259,33 @@ def bench_ours(args):
                     for k, v in stages.items() if v[1] > 0 or v[0] > 0}
     # whole-step ledger: algorithmic bytes of every stage per step / step time
     step_bytes = sum(v[2] * v[1] for v in stages.values()) / args.steps
+    # the one-pass-per-transform byte count of the hot-path scope: each distinct array read
+    # once and written once per step (screened MG 128 B/particle + 64 B/cell, 100 B/particle
+    # with 16-bit seeds and LPT fields; LCDM 40 B/cell)
+    m = run.model
+    screened = m.kind != 0 and m.screening
+    per_particle = 100.0 if args.seed_precision else 128.0
+    per_cell = 64.0 if screened else 40.0
+    scope_bytes = P * per_particle + run.Nmesh ** 3 * per_cell
     torch.cuda.empty_cache()
 
     e2e = None
     if not args.no_e2e:
         e2e = bench_e2e(args, run, pkg, dist, world)
 
+    fftref = None
+    if rank == 0 and world == 1 and not args.no_fft_reference:
+        fftref = fft_reference(run, pkg, stages, args.steps)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(run, args)
+
+    ens = srv = None
+    if rank == 0 and world == 1 and not args.no_ensemble:
+        ens = bench_ensemble(args, quiet=True)
+    if rank == 0 and world == 1 and not args.no_serve:
+        srv = bench_serve(args, quiet=True)
 
     if rank == 0:
         out = {
@@ -282,12 +300,23 @@ def bench_ours(args):
                          "traffic": None if args.lpt_fast else ncu_traffic(name, args.workload)},
             "step_ledger": {"algorithmic_GB_per_step": step_bytes / 1e9,
                             "achieved_GBps": step_bytes / (max_ms / args.steps / 1e3) / 1e9,
-                            "frac_of_peak": step_bytes / (max_ms / args.steps / 1e3) / 1e9 / peak},
+                            "frac_of_peak": step_bytes / (max_ms / args.steps / 1e3) / 1e9 / peak,
+                            "what": "bytes of this build's passes (three HBM passes per 3-D transform)"},
+            "step_roofline": {"bound": "hbm", "algorithmic_GB_per_step": scope_bytes / 1e9,
+                              "achieved": scope_bytes / (max_ms / args.steps / 1e3) / 1e9, "peak": peak,
+                              "unit": "GB/s", "frac": scope_bytes / (max_ms / args.steps / 1e3) / 1e9 / peak,
+                              "frac_of_nominal_8TBps": scope_bytes / (max_ms / args.steps / 1e3) / 8e12,
+                              "what": f"{per_particle:g} B/particle + {per_cell:g} B/cell: every distinct "
+                                      "array of the step read once and written once (one HBM pass per "
+                                      "3-D transform)"},
             "stages": stage_report,
             "clocks": clk,
             "gpu_launches": int(launches),
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "fft_reference": fftref,
+            "ensemble": ens,
+            "serve": srv,
         }
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -322,6 +351,57 @@ def bench_e2e(args, run, pkg, dist, world):
     return {"value": whole_job_throughput(P * args.steps, world, dt), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "what": "cola_init + cola_set_model + cola_ic + cola_step(K) + cola_snapshot(host) + cola_pk(host)"}
+
+
+# ---------------------------------------------------------------- cuFFT yardstick
+def fft_reference(run, pkg, stages, steps):
+    """cuFFT (torch.fft) 3-D r2c and c2r of one mesh-sized FP32 field, timed with CUDA events, beside
+    the library's own transforms.  A yardstick only: cuFFT is not on the library's path.  The
+    library's cola_fft with device buffers also converts between the dense layout of the public
+    API and the internal interleaved one (one more read and write of the half spectrum)."""
+    import torch
+    N = run.Nmesh
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev).manual_seed(5)
+    x = torch.randn((N, N, N), device=dev, dtype=torch.float32, generator=g)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(reps):
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(min(ts))
+
+    X = torch.fft.rfftn(x)
+    t_r2c = timed(lambda: torch.fft.rfftn(x))
+    t_c2r = timed(lambda: torch.fft.irfftn(X, s=(N, N, N)))
+    del X
+    torch.cuda.empty_cache()
+    out = {"what": f"one {N}^3 FP32 field; min of 3 after a warm-up; CUDA events",
+           "cufft_r2c_ms": t_r2c, "cufft_c2r_ms": t_c2r}
+    with pkg.Simulation(run.with_(Np=min(run.Np, 64)), ic=False) as s:
+        Xd = torch.empty((N, N, N // 2 + 1), device=dev, dtype=torch.complex64)
+        y = torch.empty_like(x)
+        out["lib_r2c_ms_with_layout_conversion"] = timed(lambda: s.fft_device(x, Xd, 1))
+        out["lib_c2r_ms_with_layout_conversion"] = timed(lambda: s.fft_device(Xd, y, -1))
+        del Xd, y
+    per = {k: (v[0] / steps) for k, v in stages.items()}
+    out["step_forward_density_ms"] = per.get("mesh_x_r2c", 0.0) + per.get("mesh_y_forward", 0.0) / 2
+    out["step_forward_density_note"] = ("x r2c + y forward of delta in the step; its z forward is fused "
+                                        "into the screening-field z pass")
+    out["step_force_side_ms"] = per.get("z_force", 0.0) + per.get("mesh_x_c2r", 0.0) + per.get("mesh_y_inverse", 0.0)
+    out["step_force_side_note"] = ("forward z of S, Green's function and gradients, and the three force "
+                                   "inverse transforms (a cuFFT path would need one r2c z pass plus three "
+                                   "c2r: about cufft_c2r_ms x 3 + cufft_r2c_ms / 3)")
+    del x
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------- oracle (CPU) timing
@@ -382,7 +462,7 @@ def _run_one(pkg, run):
         return sim.pk()
 
 
-def bench_ensemble(args):
+def bench_ensemble(args, quiet: bool = False):
     """256 sims of 64^3 / 128^3, models cycled: batched graph launches vs one at a time."""
     import torch
     import paper_1703_00879_gb300 as pkg
@@ -435,10 +515,12 @@ def bench_ensemble(args):
                         "steps_used": args.autotune_steps, "on": "an untimed batch of the same shape and size"},
            "seconds": {"init_and_ic": t_init, "steps": t_steps, "total": t_batch, "one_at_a_time_prefix": t_solo,
                        "one_at_a_time_sims": n1}}
-    print(json.dumps(out), flush=True)
+    if not quiet:
+        print(json.dumps(out), flush=True)
+    return out
 
 
-def bench_serve(args):
+def bench_serve(args, quiet: bool = False):
     """Poisson arrivals (mean 20/s) of mixed sims under an 80 GB HBM budget: p50/p99 latency and
     sims/hour; the same requests all at once (throughput when the GPU, not the arrivals, limits it);
     and a one-at-a-time prefix of them."""
@@ -471,7 +553,9 @@ def bench_serve(args):
            "config": {"workload": "Poisson arrivals mean 20/s, particles^(1/3) in {32,64,128,256}, mesh 2x, "
                       "L = 2 Np Mpc/h, 10-30 steps, models from the ensemble set, 80 GB HBM budget; "
                       "saturated: the same requests all at t=0"}}
-    print(json.dumps(out), flush=True)
+    if not quiet:
+        print(json.dumps(out), flush=True)
+    return out
 
 
 def main(argv=None):
@@ -485,6 +569,9 @@ def main(argv=None):
     ap.add_argument("--lpt-fast", action="store_true",
                     help="scale-independent LPT fast path (models whose growth does not depend on k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fft-reference", action="store_true", help="skip the cuFFT yardstick")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble sub-object")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving sub-object")
     ap.add_argument("--seed-precision", type=int, choices=[0, 1, 2], default=0,
                     help="variant a.S1: 0 FP32, 1 BF16, 2 FP16 seeds and per-step LPT fields")
     ap.add_argument("--ensemble", action="store_true", help="batched ensemble benchmark instead")

@@ -383,6 +383,12 @@ class Simulation:
         _check(lib().cola_fft(self.ctx, int(direction), src.ctypes.data, out.ctypes.data, COLA_HOST), self.ctx)
         return out
 
+    def fft_device(self, src_t, dst_t, direction: int):
+        """cola_fft on device tensors: direction 1 real [N,N,N] float32 -> [N,N,N/2+1] complex64,
+        -1 the reverse (unnormalised); enqueued on the context's stream."""
+        _check(lib().cola_fft(self.ctx, int(direction), _P(src_t.data_ptr()), _P(dst_t.data_ptr()), COLA_DEVICE),
+               self.ctx)
+
     def cic_deposit(self, pos: np.ndarray) -> np.ndarray:
         N = self.run.Nmesh
         p = np.ascontiguousarray(pos, dtype=np.float32)

@@ -574,13 +574,14 @@ struct Layout {
 // pass of the scale-independent fast path), the per-step force parameters and
 // the per-step time integrals.
 struct TableLayout {
-  size_t tab_b, fp_off, dt_off, bytes;
+  size_t tab_b, fp_off, dt_off, g_off, bytes;
   explicit TableLayout(const cola_config& cfg) {
     const size_t ns = (size_t)cfg.nsteps, nk = (size_t)cfg.nk_table;
     tab_b = (ns + 2) * nk * sizeof(float4);
     fp_off = 2 * tab_b;
     dt_off = fp_off + (ns * sizeof(ForceParams) + 255) / 256 * 256;
-    bytes = dt_off + 3 * ns * sizeof(float);
+    g_off = dt_off + (3 * ns * sizeof(float) + 255) / 256 * 256;  // [ns + 2] float2 row growth
+    bytes = g_off + (ns + 2) * sizeof(float2);
   }
 };
 
@@ -717,7 +718,7 @@ int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}) {
     if (q16) {
       void* out6[6] = {ctx->lq[0], ctx->lq[1], ctx->lq[2], ctx->lq[3], ctx->lq[4], ctx->lq[5]};
       CK(fft_xc2r_multi16(N, 6, in6, out6, kfs6, lp.seed_prec, ctx->hdr, ctx->tw_np, st, m));
-      CK(lq_update(ctx->hdr, lp.seed_prec, st, m));
+      CK(lq_update(ctx->hdr, lp.seed_prec, ctx->cfg.nsteps, st, m));
     } else {
       float* out6[6] = {ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->lr[3], ctx->lr[4], ctx->lr[5]};
       CK(fft_xc2r_multi(N, 6, in6, out6, kfs6, ctx->tw_np, st, m));
@@ -1145,7 +1146,7 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
   const cola_config& cfg = ctx->cfg;
   const int nk = ctx->nk, ns = cfg.nsteps;
   const TableLayout tl(cfg);
-  const size_t tab_b = tl.tab_b, fp_off = tl.fp_off, dt_off = tl.dt_off, bytes = tl.bytes;
+  const size_t tab_b = tl.tab_b, fp_off = tl.fp_off, dt_off = tl.dt_off, g_off = tl.g_off, bytes = tl.bytes;
   // kind 1: (every configuration field but the seed and the seed precision, the model)
   std::vector<double> key = {1.0, (double)cfg.Np, (double)cfg.Nmesh, cfg.Lbox, (double)ns,
                              cfg.z_ini, cfg.z_final, cfg.Omega_m, cfg.Omega_b, cfg.h, cfg.n_s,
@@ -1184,6 +1185,16 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
       dt[3 * n + 1] = (float)ctx->dtd[n];
       dt[3 * n + 2] = (float)ctx->dtk2[n];
     }
+    // per row: the largest Psi1 coefficient of the drift (c1) and kick (e1) fields
+    float2* rg = reinterpret_cast<float2*>(h + g_off);
+    for (int n = 0; n < ns + 2; ++n) {
+      float c = 0.f, e = 0.f;
+      for (int j = 0; j < nk; ++j) {
+        c = std::max(c, std::abs(tab[(size_t)n * nk + j].x));
+        e = std::max(e, std::abs(tab[(size_t)n * nk + j].z));
+      }
+      rg[n] = make_float2(c, e);
+    }
   });
   CHECK_RC(upload(ctx, ctx->tables, host->data(), bytes));
   char* base = ctx->tables;
@@ -1195,6 +1206,7 @@ int cola_set_model(cola_ctx* ctx, const cola_model* model) {
   ctx->hh.ddt = ctx->ddt;
   ctx->hh.tab = ctx->tab;
   ctx->hh.vtab = ctx->vtab;
+  ctx->hh.lqg = reinterpret_cast<const float2*>(base + g_off);
   ctx->hh.fp_ini = force_params(ctx, ctx->a[0]);
   ctx->hh.seed = ctx->cfg.seed;
   // bf16: unit scale of the largest value; fp16: the largest value at 2^15

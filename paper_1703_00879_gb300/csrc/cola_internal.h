@@ -88,6 +88,10 @@ struct SimHeader {
   float lq_scale[6];
   float lq_used[6];
   float lq_amax[6];
+  // per table row n: (max_k |c1|, max_k |e1|), the growth coefficient of Psi1 in
+  // the drift and in the kick fields; their ratio between consecutive rows
+  // predicts how the fields grow from one pass to the next
+  const float2* lqg;
 };
 
 // One launch over several simulations of one shape.  Each simulation's
@@ -233,13 +237,15 @@ cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float*
                              float* ay, float* az, const float* Ax, const float* Ay,
                              const float* Az, const float* Fx, const float* Fy, const float* Fz,
                              StepDt dt, int64_t P, cudaStream_t s, Multi m = {}, LptMix mix = {});
-// Per simulation: lq_used = lq_scale (the scale the fields just written carry),
-// lq_scale = lq_amax / target (for the next pass; unchanged if nothing was
-// written), lq_amax = 0.  target: the largest 16-bit value maps to it (fp16
-// 2^14, four times below the format's largest finite value; bf16 1).
-cudaError_t lq_update(SimHeader* hdr, int prec, cudaStream_t s, Multi m = {});
-// Initial scales from six FP32 fields of P values (the LPT fields at a_ini):
-// lq_scale = lq_used = max |field| / target, lq_amax = 0.
+// Per simulation: lq_used = lq_scale (the scale the fields just written, table
+// row step + 1, carry), lq_scale = lq_amax x (growth of the next row over this
+// one, lqg) / target for the next pass (unchanged if nothing was written),
+// lq_amax = 0.  target: the predicted largest value maps to it (fp16 2^10, a
+// factor 64 below the format's largest finite value; bf16 1).
+cudaError_t lq_update(SimHeader* hdr, int prec, int nsteps, cudaStream_t s, Multi m = {});
+// Initial scales from six FP32 fields of P values (the LPT fields at a_ini, row
+// 0): lq_scale = lq_used = max |field| x (growth of row 1 over row 0) / target,
+// lq_amax = 0.
 cudaError_t lq_init(SimHeader* hdr, const float* const* fields, int64_t P, int prec, cudaStream_t s,
                     Multi m = {});
 // FP32 copy of the 16-bit field f (dequantised with lq_used[f]), one simulation.

@@ -19,6 +19,11 @@ namespace {
 
 constexpr int NTP = 256;
 
+// Value of a 16-bit field entry (prec 1 bf16, 2 fp16), before its field scale.
+__device__ __forceinline__ float lq_value(unsigned short u, int prec) {
+  return prec == 1 ? __bfloat162float(__ushort_as_bfloat16(u)) : __half2float(__ushort_as_half(u));
+}
+
 struct Cic {
   int i0[3], i1[3];
   float f[3];
@@ -129,227 +134,51 @@ __device__ __forceinline__ void lattice(const PartParams& pp, int64_t p, int& ix
   iz = (int)(p >> (2 * pp.lgNp));
 }
 
-// Value of a 16-bit field entry (prec 1 bf16, 2 fp16), before its field scale.
-__device__ __forceinline__ float lq_value(unsigned short u, int prec) {
-  return prec == 1 ? __bfloat162float(__ushort_as_bfloat16(u)) : __half2float(__ushort_as_half(u));
-}
-
-// ---------------------------------------------------------------- Lagrangian blocks
-// The step's particle kernels give each CTA an 8 x 8 x 8 block of the Lagrangian
-// lattice (two particles per thread).  Particles that start together stay close
-// for most of a run, so the block's particles cover a compact box of mesh
-// cells: the CTA finds that box (the bounding box of the particles' CIC base
-// cells, plus one cell for the upper CIC neighbours) and works on a copy of it
-// in shared memory.
-//   * deposit: the CIC weights are summed into the shared box with shared-memory
-//     atomics; the box then leaves with one 16-byte vector atomic per four cells
-//     (zero groups skipped), rows along x, instead of eight scattered global
-//     atomics per particle;
-//   * gather: the three force components of the box are read once with loads
-//     along x rows and every particle interpolates from shared memory, instead
-//     of 24 scattered global loads per particle.
-// A block whose box is larger than the shared copy (particles spread far apart,
-// e.g. in late-time voids) falls back to global atomics / global loads.  Both
-// paths give the same values (the same weights and field values; only the order
-// of float additions in the deposit differs).
-constexpr int LB = 8;                    // lattice block side
-constexpr int LBP = LB * LB * LB;        // particles per CTA (2 per thread)
-constexpr int GATHER_BOX = 8192;         // cells staged by the gather (3 floats each: 96 KB)
-constexpr int DEPOSIT_BOX = 16384;       // cells binned by the deposit (64 KB)
-static_assert(LBP == 2 * NTP, "two particles per thread");
-
-// CIC base cell without the periodic wrap (so that a block's cells form one
-// box) and the fractions; the arithmetic of cic_setup.
-struct CicU {
-  int i0[3];
-  float f[3];
-};
-
-__device__ __forceinline__ CicU cic_unwrapped(const PartParams& pp, int ix, int iy, int iz, float sx, float sy,
-                                             float sz) {
-  CicU c;
-  const int li[3] = {ix, iy, iz};
-  const float sv[3] = {sx, sy, sz};
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int num = li[d] * pp.Nm;
-    const int base = num >> pp.lgNp;
-    const float qf = (float)(num - (base << pp.lgNp)) * __int_as_float((127 - pp.lgNp) << 23);
-    const float u = qf + sv[d] * pp.cellscale;
-    const float fl = floorf(u);
-    c.f[d] = u - fl;
-    c.i0[d] = base + (int)fl;
-  }
-  return c;
-}
-
-__device__ __forceinline__ Cic wrap(const CicU& u, int Nm) {
-  Cic c;
-  const int mask = Nm - 1;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    c.i0[d] = u.i0[d] & mask;
-    c.i1[d] = (c.i0[d] + 1) & mask;
-    c.f[d] = u.f[d];
-  }
-  return c;
-}
-
-// Lattice point of particle k (0, 1) of this thread in the CTA's block, and its index.
-struct BlockLattice {
-  int ox, oy, oz;
-  __device__ __forceinline__ explicit BlockLattice(const PartParams& pp) {
-    const int lg = pp.lgNp - 3, m = (1 << lg) - 1;
-    const uint32_t b = blockIdx.x;
-    ox = (int)(b & m) << 3;
-    oy = (int)((b >> lg) & m) << 3;
-    oz = (int)(b >> (2 * lg)) << 3;
-  }
-  __device__ __forceinline__ int64_t at(const PartParams& pp, int k, int& ix, int& iy, int& iz) const {
-    const int l = threadIdx.x + k * NTP;
-    ix = ox + (l & 7);
-    iy = oy + ((l >> 3) & 7);
-    iz = oz + (l >> 6);
-    return ((((int64_t)iz << pp.lgNp) + iy) << pp.lgNp) + ix;
-  }
-};
-
-// The block's box: lo = smallest base cell per axis, ex = cells per axis (the
-// largest base cell + 2 - lo).  Every thread gets the result.
-struct Box {
-  int lo[3], ex[3];
-};
-
-__device__ __forceinline__ Box block_box(const CicU (&c)[2], int (*red)[6]) {
-  int v[6];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    v[d] = min(c[0].i0[d], c[1].i0[d]);
-    v[3 + d] = -max(c[0].i0[d], c[1].i0[d]);
-  }
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) v[q] = __reduce_min_sync(0xffffffffu, v[q]);
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < 6; ++q) red[w][q] = v[q];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    int r = red[0][q];
-#pragma unroll
-    for (int j = 1; j < NTP / 32; ++j) r = min(r, red[j][q]);
-    v[q] = r;
-  }
-  Box b;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    b.lo[d] = v[d];
-    b.ex[d] = -v[3 + d] + 2 - v[d];
-  }
-  return b;
-}
-
-// Rows (y, z) of a box with `len` entries along x, walked by the CTA: each warp
-// takes 32 / len rows at a time when a row fits in a warp, else one row whose
-// entries its lanes stride through.  f(e, r, yy, zz) for entry e of row r.
-template <class F>
-__device__ __forceinline__ void for_box_rows(int len, int ey, int ez, F f) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nrow = ey * ez;
-  if (len <= 32) {
-    const int rpw = 32 / len, sub = lane / len, e = lane - sub * len;
-    if (sub >= rpw) return;
-    for (int r = w * rpw + sub; r < nrow; r += (NTP / 32) * rpw) {
-      const int zz = r / ey, yy = r - zz * ey;
-      f(e, r, yy, zz);
-    }
-  } else {
-    for (int r = w; r < nrow; r += NTP / 32) {
-      const int zz = r / ey, yy = r - zz * ey;
-      for (int e = lane; e < len; e += 32) f(e, r, yy, zz);
-    }
-  }
-}
-
-// CIC deposit of the CTA's 512 particles (c: this thread's two, valid) into rho.
-__device__ __forceinline__ void deposit_block(float* __restrict__ rho, int Nm, const CicU (&c)[2],
-                                              float* __restrict__ sbox, int (*red)[6]) {
-  const Box b = block_box(c, red);
-  const int x0 = b.lo[0] & ~3;                                  // 16-byte aligned rows
-  const int ex = ((b.lo[0] + b.ex[0] - x0) + 3) & ~3;
-  const int64_t ncell = (int64_t)ex * b.ex[1] * b.ex[2];
-  if (ncell > DEPOSIT_BOX) {
-#pragma unroll
-    for (int k = 0; k < 2; ++k) cic_deposit_merged(rho, Nm, wrap(c[k], Nm), true);
-    return;
-  }
-  float4* s4 = reinterpret_cast<float4*>(sbox);
-  const int n4 = (int)ncell >> 2;
-  for (int i = threadIdx.x; i < n4; i += NTP) s4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncthreads();
-  const int sy = ex, sz = ex * b.ex[1];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const float wx0 = 1.f - c[k].f[0], wx1 = c[k].f[0];
-    const float wy0 = 1.f - c[k].f[1], wy1 = c[k].f[1];
-    const float wz0 = 1.f - c[k].f[2], wz1 = c[k].f[2];
-    float* q = sbox + (c[k].i0[2] - b.lo[2]) * sz + (c[k].i0[1] - b.lo[1]) * sy + (c[k].i0[0] - x0);
-    atomicAdd(q, wz0 * wy0 * wx0);
-    atomicAdd(q + 1, wz0 * wy0 * wx1);
-    atomicAdd(q + sy, wz0 * wy1 * wx0);
-    atomicAdd(q + sy + 1, wz0 * wy1 * wx1);
-    atomicAdd(q + sz, wz1 * wy0 * wx0);
-    atomicAdd(q + sz + 1, wz1 * wy0 * wx1);
-    atomicAdd(q + sz + sy, wz1 * wy1 * wx0);
-    atomicAdd(q + sz + sy + 1, wz1 * wy1 * wx1);
-  }
-  __syncthreads();
-  const int mask = Nm - 1;
-  for_box_rows(ex >> 2, b.ex[1], b.ex[2], [&](int g, int r, int yy, int zz) {
-    const float4 v = s4[r * (ex >> 2) + g];
-    if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
-      const int64_t row = ((int64_t)((b.lo[2] + zz) & mask) * Nm + ((b.lo[1] + yy) & mask)) * Nm;
-      atomicAdd(reinterpret_cast<float4*>(rho + row + ((x0 + 4 * g) & mask)), v);
-    }
-  });
-}
-
 // Multi-simulation kernels take the simulation from blockIdx.y and move every
 // buffer pointer by its shift.
-__global__ void __launch_bounds__(NTP, 3) k_deposit(PartParams pp, const float* __restrict__ sx,
-                                                    const float* __restrict__ sy,
-                                                    const float* __restrict__ sz,
-                                                    float* __restrict__ rho, Multi m) {
-  extern __shared__ __align__(16) float sbox[];
-  __shared__ int red[NTP / 32][6];
+__global__ void __launch_bounds__(NTP) k_deposit(PartParams pp, const float* __restrict__ sx,
+                                                 const float* __restrict__ sy,
+                                                 const float* __restrict__ sz,
+                                                 float* __restrict__ rho, int64_t P, Multi m) {
+  const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
+  if (p >= P) return;
   const int64_t by = shift_of(m, blockIdx.y);
   sx = moved(sx, by);
   sy = moved(sy, by);
   sz = moved(sz, by);
   rho = moved(rho, by);
-  const BlockLattice bl(pp);
-  CicU c[2];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    int ix, iy, iz;
-    const int64_t p = bl.at(pp, k, ix, iy, iz);
-    c[k] = cic_unwrapped(pp, ix, iy, iz, sx[p], sy[p], sz[p]);
-  }
-  deposit_block(rho, pp.Nm, c, sbox, red);
+  int ix, iy, iz;
+  lattice(pp, p, ix, iy, iz);
+  cic_deposit(rho, pp.Nm, cic_setup(pp, ix, iy, iz, sx[p], sy[p], sz[p]));
+}
+
+// Particle of work item i of the gather: a warp takes an 8 x 4 patch of the
+// Lagrangian lattice (8 along x, 4 along y) instead of 32 along x.  Loads of
+// per-particle arrays still fill whole 32-byte sectors, and once the particles
+// have clustered a compact patch touches fewer mesh sectors than a line (the
+// last step's gather 9.95 -> 6.9 ms at 512^3 / 1024^3).  The deposit keeps
+// lines: its atomics from a patch collide more (4.0 -> 4.5 ms at the first step).
+__device__ __forceinline__ int64_t patch84(const PartParams& pp, int64_t i) {
+  const int lane = (int)(i & 31);
+  const int64_t w = i >> 5;
+  const int xw = pp.lgNp - 3;                      // warps along x per 4-row band
+  const int64_t xh = w & ((1 << xw) - 1), band = w >> xw;  // band = z Np/4 + y/4
+  const int64_t x = (xh << 3) | (lane & 7);
+  const int64_t yz = (band << 2) | (lane >> 3);    // y + z Np (4 | Np)
+  return (yz << pp.lgNp) | x;
 }
 
 // Sec. 2 drift in the LPT frame: delta_v += acc dtk (closing the previous
 // half kick), s += delta_v dtd + dPsi_LPT(q); then CIC deposit of x = q + s.
-__global__ void __launch_bounds__(NTP, 3) k_drift_deposit(
+__global__ void __launch_bounds__(NTP) k_drift_deposit(
     PartParams pp, float* __restrict__ sx, float* __restrict__ sy, float* __restrict__ sz,
     float* __restrict__ vx, float* __restrict__ vy, float* __restrict__ vz,
     const float* __restrict__ ax, const float* __restrict__ ay, const float* __restrict__ az,
     const float* __restrict__ dpx, const float* __restrict__ dpy,
-    const float* __restrict__ dpz, float* __restrict__ rho, StepDt dt, Multi m, LptMix mix) {
-  extern __shared__ __align__(16) float sbox[];
-  __shared__ int red[NTP / 32][6];
+    const float* __restrict__ dpz, float* __restrict__ rho, StepDt dt, int64_t P, Multi m,
+    LptMix mix) {
+  const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
+  const bool valid = p < P;
   const int64_t by = shift_of(m, blockIdx.y);
   sx = moved(sx, by);
   sy = moved(sy, by);
@@ -370,30 +199,21 @@ __global__ void __launch_bounds__(NTP, 3) k_drift_deposit(
     dtk = h->ddt[3 * h->step];
     dtd = h->ddt[3 * h->step + 1];
   }
-  float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (mix.on) cf = mix_coeffs(mix, by);
-  float qs[3] = {1.f, 1.f, 1.f};
-  if (dt.lq) {
-    const SimHeader* h = moved(dt.hdr, by);
-    for (int d = 0; d < 3; ++d) qs[d] = h->lq_used[d];
-  }
-  const BlockLattice bl(pp);
-  CicU c[2];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    int ix, iy, iz;
-    const int64_t p = bl.at(pp, k, ix, iy, iz);
+  Cic c{};
+  if (valid) {
     float lx, ly, lz;
     if (dt.lq) {  // 16-bit drift fields, one scale per field
-      lx = lq_value(reinterpret_cast<const unsigned short*>(dpx)[p], dt.lq) * qs[0];
-      ly = lq_value(reinterpret_cast<const unsigned short*>(dpy)[p], dt.lq) * qs[1];
-      lz = lq_value(reinterpret_cast<const unsigned short*>(dpz)[p], dt.lq) * qs[2];
+      const SimHeader* h = moved(dt.hdr, by);
+      lx = lq_value(reinterpret_cast<const unsigned short*>(dpx)[p], dt.lq) * h->lq_used[0];
+      ly = lq_value(reinterpret_cast<const unsigned short*>(dpy)[p], dt.lq) * h->lq_used[1];
+      lz = lq_value(reinterpret_cast<const unsigned short*>(dpz)[p], dt.lq) * h->lq_used[2];
     } else {
       lx = dpx[p];
       ly = dpy[p];
       lz = dpz[p];
     }
     if (mix.on) {  // Delta Psi = c1 Psi1 + c2 Psi2
+      const float4 cf = mix_coeffs(mix, by);
       lx = cf.x * lx + cf.y * moved(mix.q2[0], by)[p];
       ly = cf.x * ly + cf.y * moved(mix.q2[1], by)[p];
       lz = cf.x * lz + cf.y * moved(mix.q2[2], by)[p];
@@ -410,34 +230,26 @@ __global__ void __launch_bounds__(NTP, 3) k_drift_deposit(
     sx[p] = nx;
     sy[p] = ny;
     sz[p] = nz;
-    c[k] = cic_unwrapped(pp, ix, iy, iz, nx, ny, nz);
+    int ix, iy, iz;
+    lattice(pp, p, ix, iy, iz);
+    c = cic_setup(pp, ix, iy, iz, nx, ny, nz);
   }
-  deposit_block(rho, pp.Nm, c, sbox, red);
+  cic_deposit_merged(rho, pp.Nm, c, valid);
 }
 
-// CIC interpolation from a shared box (strides 1, sy, sz; q = the base cell), in
-// the operation order of cic_interp.
-__device__ __forceinline__ float box_interp(const float* __restrict__ q, int sy, int sz, const CicU& c) {
-  const float wx0 = 1.f - c.f[0], wx1 = c.f[0];
-  const float wy0 = 1.f - c.f[1], wy1 = c.f[1];
-  const float wz0 = 1.f - c.f[2], wz1 = c.f[2];
-  const float a00 = wx0 * q[0] + wx1 * q[1];
-  const float a01 = wx0 * q[sy] + wx1 * q[sy + 1];
-  const float a10 = wx0 * q[sz] + wx1 * q[sz + 1];
-  const float a11 = wx0 * q[sz + sy] + wx1 * q[sz + sy + 1];
-  return wz0 * (wy0 * a00 + wy1 * a01) + wz1 * (wy0 * a10 + wy1 * a11);
-}
+// Sec. 2 kick: acc = g(x) - A_LPT(q), delta_v += acc dtk.  Each thread handles
+// PPT particles (p, p + NTP, ...) of its block so that the dependent chains
+// (displacement load -> cell index -> 24 mesh loads) of different particles overlap.
+constexpr int PPT = 2;
 
-// Sec. 2 kick: acc = g(x) - A_LPT(q), delta_v += acc dtk.
-__global__ void __launch_bounds__(NTP, 2) k_gather_kick(
+__global__ void __launch_bounds__(NTP) k_gather_kick(
     PartParams pp, const float* __restrict__ sx, const float* __restrict__ sy,
     const float* __restrict__ sz, float* __restrict__ vx, float* __restrict__ vy,
     float* __restrict__ vz, float* __restrict__ ax, float* __restrict__ ay,
     float* __restrict__ az, const float* __restrict__ Ax, const float* __restrict__ Ay,
     const float* __restrict__ Az, const float* __restrict__ Fx, const float* __restrict__ Fy,
-    const float* __restrict__ Fz, StepDt dt, Multi m, LptMix mix) {
-  extern __shared__ __align__(16) float sbox[];
-  __shared__ int red[NTP / 32][6];
+    const float* __restrict__ Fz, StepDt dt, int64_t P, Multi m, LptMix mix) {
+  const int64_t p0 = (int64_t)blockIdx.x * NTP * PPT + threadIdx.x;
   const int64_t by = shift_of(m, blockIdx.y);
   sx = moved(sx, by);
   sy = moved(sy, by);
@@ -459,43 +271,27 @@ __global__ void __launch_bounds__(NTP, 2) k_gather_kick(
     const SimHeader* h = moved(dt.hdr, by);
     dtk = h->ddt[3 * h->step + 2];
   }
-  const BlockLattice bl(pp);
-  int64_t p[2];
-  CicU c[2];
+  float px[PPT], py[PPT], pz[PPT];
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    int ix, iy, iz;
-    p[k] = bl.at(pp, k, ix, iy, iz);
-    c[k] = cic_unwrapped(pp, ix, iy, iz, sx[p[k]], sy[p[k]], sz[p[k]]);
-  }
-  const Box b = block_box(c, red);
-  const int64_t ncell = (int64_t)b.ex[0] * b.ex[1] * b.ex[2];
-  float g[2][3];
-  if (ncell <= GATHER_BOX) {
-    const int Nm = pp.Nm, mask = Nm - 1, ex = b.ex[0];
-    for_box_rows(ex, b.ex[1], b.ex[2], [&](int e, int r, int yy, int zz) {
-      const int64_t gi = ((int64_t)((b.lo[2] + zz) & mask) * Nm + ((b.lo[1] + yy) & mask)) * Nm +
-                         ((b.lo[0] + e) & mask);
-      const int cell = r * ex + e;
-      sbox[cell] = __ldg(Fx + gi);
-      sbox[GATHER_BOX + cell] = __ldg(Fy + gi);
-      sbox[2 * GATHER_BOX + cell] = __ldg(Fz + gi);
-    });
-    __syncthreads();
-    const int sy_ = ex, sz_ = ex * b.ex[1];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int o = (c[k].i0[2] - b.lo[2]) * sz_ + (c[k].i0[1] - b.lo[1]) * sy_ + (c[k].i0[0] - b.lo[0]);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) g[k][d] = box_interp(sbox + d * GATHER_BOX + o, sy_, sz_, c[k]);
+  for (int u = 0; u < PPT; ++u) {
+    const int64_t p = patch84(pp, p0 + u * NTP);
+    if (p0 + u * NTP < P) {
+      px[u] = sx[p];
+      py[u] = sy[p];
+      pz[u] = sz[p];
     }
-  } else {
+  }
+  float gx[PPT], gy[PPT], gz[PPT];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const Cic cw = wrap(c[k], pp.Nm);
-      g[k][0] = cic_interp(Fx, pp.Nm, cw);
-      g[k][1] = cic_interp(Fy, pp.Nm, cw);
-      g[k][2] = cic_interp(Fz, pp.Nm, cw);
+  for (int u = 0; u < PPT; ++u) {
+    const int64_t p = patch84(pp, p0 + u * NTP);
+    if (p0 + u * NTP < P) {
+      int ix, iy, iz;
+      lattice(pp, p, ix, iy, iz);
+      const Cic c = cic_setup(pp, ix, iy, iz, px[u], py[u], pz[u]);
+      gx[u] = cic_interp(Fx, pp.Nm, c);
+      gy[u] = cic_interp(Fy, pp.Nm, c);
+      gz[u] = cic_interp(Fz, pp.Nm, c);
     }
   }
   float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -506,30 +302,32 @@ __global__ void __launch_bounds__(NTP, 2) k_gather_kick(
     for (int d = 0; d < 3; ++d) qs[d] = h->lq_used[3 + d];
   }
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int64_t q = p[k];
-    float lx, ly, lz;
-    if (dt.lq) {  // 16-bit kick fields, one scale per field
-      lx = lq_value(reinterpret_cast<const unsigned short*>(Ax)[q], dt.lq) * qs[0];
-      ly = lq_value(reinterpret_cast<const unsigned short*>(Ay)[q], dt.lq) * qs[1];
-      lz = lq_value(reinterpret_cast<const unsigned short*>(Az)[q], dt.lq) * qs[2];
-    } else {
-      lx = Ax[q];
-      ly = Ay[q];
-      lz = Az[q];
+  for (int u = 0; u < PPT; ++u) {
+    const int64_t p = patch84(pp, p0 + u * NTP);
+    if (p0 + u * NTP < P) {
+      float lx, ly, lz;
+      if (dt.lq) {  // 16-bit kick fields, one scale per field
+        lx = lq_value(reinterpret_cast<const unsigned short*>(Ax)[p], dt.lq) * qs[0];
+        ly = lq_value(reinterpret_cast<const unsigned short*>(Ay)[p], dt.lq) * qs[1];
+        lz = lq_value(reinterpret_cast<const unsigned short*>(Az)[p], dt.lq) * qs[2];
+      } else {
+        lx = Ax[p];
+        ly = Ay[p];
+        lz = Az[p];
+      }
+      if (mix.on) {  // A_LPT = e1 Psi1 + e2 Psi2
+        lx = cf.z * lx + cf.w * moved(mix.q2[0], by)[p];
+        ly = cf.z * ly + cf.w * moved(mix.q2[1], by)[p];
+        lz = cf.z * lz + cf.w * moved(mix.q2[2], by)[p];
+      }
+      const float ex = gx[u] - lx, ey = gy[u] - ly, ez = gz[u] - lz;
+      ax[p] = ex;
+      ay[p] = ey;
+      az[p] = ez;
+      vx[p] += ex * dtk;
+      vy[p] += ey * dtk;
+      vz[p] += ez * dtk;
     }
-    if (mix.on) {  // A_LPT = e1 Psi1 + e2 Psi2
-      lx = cf.z * lx + cf.w * moved(mix.q2[0], by)[q];
-      ly = cf.z * ly + cf.w * moved(mix.q2[1], by)[q];
-      lz = cf.z * lz + cf.w * moved(mix.q2[2], by)[q];
-    }
-    const float ex_ = g[k][0] - lx, ey = g[k][1] - ly, ez = g[k][2] - lz;
-    ax[q] = ex_;
-    ay[q] = ey;
-    az[q] = ez;
-    vx[q] += ex_ * dtk;
-    vy[q] += ey * dtk;
-    vz[q] += ez * dtk;
   }
 }
 
@@ -655,15 +453,24 @@ __global__ void k_set_header(SimHeader* hdr, SimHeader v) {
   *hdr = v;
 }
 
-__device__ __forceinline__ float lq_target(int prec) { return prec == 2 ? 16384.f : 1.f; }
+__device__ __forceinline__ float lq_target(int prec) { return prec == 2 ? 1024.f : 1.f; }
 
-__global__ void k_lq_update(SimHeader* hdr, int prec, Multi m) {
+// Growth of field f's coefficient from table row r0 to r1 (1 when unknown).
+__device__ __forceinline__ float lq_growth(const SimHeader* h, int f, int r0, int r1) {
+  if (!h->lqg) return 1.f;
+  const float2 g0 = h->lqg[r0], g1 = h->lqg[r1];
+  const float a = f < 3 ? g0.x : g0.y, b = f < 3 ? g1.x : g1.y;
+  return a > 0.f && b > 0.f ? b / a : 1.f;
+}
+
+__global__ void k_lq_update(SimHeader* hdr, int prec, int nsteps, Multi m) {
   const int b = blockIdx.x, f = threadIdx.x;
   if (f >= 6) return;
   SimHeader* h = moved(hdr, shift_of(m, b));
   h->lq_used[f] = h->lq_scale[f];
   const float a = h->lq_amax[f];
-  if (a > 0.f) h->lq_scale[f] = a / lq_target(prec);
+  const int r = h->step + 1;  // the row just written; the next pass writes r + 1
+  if (a > 0.f) h->lq_scale[f] = a * (r + 1 <= nsteps ? lq_growth(h, f, r, r + 1) : 1.f) / lq_target(prec);
   h->lq_amax[f] = 0.f;
 }
 
@@ -688,7 +495,7 @@ __global__ void k_lq_init(SimHeader* hdr, int prec, Multi m) {
   if (f >= 6) return;
   SimHeader* h = moved(hdr, shift_of(m, b));
   const float a = h->lq_amax[f];
-  h->lq_scale[f] = h->lq_used[f] = a > 0.f ? a / lq_target(prec) : 1.f;
+  h->lq_scale[f] = h->lq_used[f] = a > 0.f ? a * lq_growth(h, f, 0, 1) / lq_target(prec) : 1.f;
   h->lq_amax[f] = 0.f;
 }
 
@@ -721,26 +528,11 @@ __global__ void __launch_bounds__(NTP) k_zero(float4* __restrict__ p, int64_t n4
     p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Shared memory of the block kernels, set once per kernel.
-template <class K>
-cudaError_t smem_attr(K kernel, size_t bytes, bool& done) {
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) done = true;
-  return e;
-}
-constexpr size_t kDepositSmem = DEPOSIT_BOX * sizeof(float);
-constexpr size_t kGatherSmem = 3 * GATHER_BOX * sizeof(float);
-bool g_dep_attr = false, g_ddep_attr = false, g_gk_attr = false;
-
 }  // namespace
 
 cudaError_t part_deposit(const PartParams& pp, const float* sx, const float* sy, const float* sz,
                          float* rho, int64_t P, cudaStream_t s, Multi m) {
-  if (P != (int64_t)pp.Np * pp.Np * pp.Np || pp.Np < LB) return cudaErrorInvalidValue;
-  cudaError_t e = smem_attr(k_deposit, kDepositSmem, g_dep_attr);
-  if (e != cudaSuccess) return e;
-  k_deposit<<<dim3((unsigned)(P / LBP), m.nb), NTP, kDepositSmem, s>>>(pp, sx, sy, sz, rho, m);
+  k_deposit<<<dim3(blocks_for(P), m.nb), NTP, 0, s>>>(pp, sx, sy, sz, rho, P, m);
   return cudaGetLastError();
 }
 
@@ -749,11 +541,8 @@ cudaError_t part_drift_deposit(const PartParams& pp, float* sx, float* sy, float
                                const float* az, const float* dpx, const float* dpy,
                                const float* dpz, float* rho, StepDt dt, int64_t P,
                                cudaStream_t s, Multi m, LptMix mix) {
-  if (P != (int64_t)pp.Np * pp.Np * pp.Np || pp.Np < LB) return cudaErrorInvalidValue;
-  cudaError_t e = smem_attr(k_drift_deposit, kDepositSmem, g_ddep_attr);
-  if (e != cudaSuccess) return e;
-  k_drift_deposit<<<dim3((unsigned)(P / LBP), m.nb), NTP, kDepositSmem, s>>>(
-      pp, sx, sy, sz, vx, vy, vz, ax, ay, az, dpx, dpy, dpz, rho, dt, m, mix);
+  k_drift_deposit<<<dim3(blocks_for(P), m.nb), NTP, 0, s>>>(pp, sx, sy, sz, vx, vy, vz, ax, ay, az,
+                                                            dpx, dpy, dpz, rho, dt, P, m, mix);
   return cudaGetLastError();
 }
 
@@ -762,11 +551,8 @@ cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float*
                              float* ay, float* az, const float* Ax, const float* Ay,
                              const float* Az, const float* Fx, const float* Fy, const float* Fz,
                              StepDt dt, int64_t P, cudaStream_t s, Multi m, LptMix mix) {
-  if (P != (int64_t)pp.Np * pp.Np * pp.Np || pp.Np < LB) return cudaErrorInvalidValue;
-  cudaError_t e = smem_attr(k_gather_kick, kGatherSmem, g_gk_attr);
-  if (e != cudaSuccess) return e;
-  k_gather_kick<<<dim3((unsigned)(P / LBP), m.nb), NTP, kGatherSmem, s>>>(
-      pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, Fx, Fy, Fz, dt, m, mix);
+  k_gather_kick<<<dim3((unsigned)((P + NTP * PPT - 1) / (NTP * PPT)), m.nb), NTP, 0, s>>>(
+      pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, Fx, Fy, Fz, dt, P, m, mix);
   return cudaGetLastError();
 }
 
@@ -779,8 +565,8 @@ cudaError_t part_snapshot(const PartParams& pp, const float* sx, const float* sy
   return cudaGetLastError();
 }
 
-cudaError_t lq_update(SimHeader* hdr, int prec, cudaStream_t s, Multi m) {
-  k_lq_update<<<m.nb, 32, 0, s>>>(hdr, prec, m);
+cudaError_t lq_update(SimHeader* hdr, int prec, int nsteps, cudaStream_t s, Multi m) {
+  k_lq_update<<<m.nb, 32, 0, s>>>(hdr, prec, nsteps, m);
   return cudaGetLastError();
 }
 
