@@ -511,7 +511,8 @@ def bench_ensemble(args, quiet: bool = False):
            "one_at_a_time_sims_per_hour": solo_rate, "speedup_vs_one_at_a_time": (n / t_batch * 3600.0) / solo_rate,
            "n_sims": n, "steps": runs[0].nsteps, "config": {"workload": "ensemble 64^3 particles / 128^3 mesh, "
            "L=128 Mpc/h, 20 steps, models cycled over LCDM, F6, F5, F4, nDGP rcH0=1, nDGP rcH0=5, seeds 0..%d" % (n - 1)},
-           "autotune": {"group": plan[0], "chains": plan[1], "grid_cap": plan[2],
+           "autotune": {"group": plan[0], "chains": plan[1], "grid_cap": plan[2], "deposit_box": plan[3],
+                        "gather_box": plan[4],
                         "steps_used": args.autotune_steps, "on": "an untimed batch of the same shape and size"},
            "seconds": {"init_and_ic": t_init, "steps": t_steps, "total": t_batch, "one_at_a_time_prefix": t_solo,
                        "one_at_a_time_sims": n1}}
@@ -577,7 +578,7 @@ def main(argv=None):
     ap.add_argument("--ensemble", action="store_true", help="batched ensemble benchmark instead")
     ap.add_argument("--ensemble-size", type=int, default=256)
     ap.add_argument("--ensemble-solo", type=int, default=48)
-    ap.add_argument("--autotune-steps", type=int, default=6)
+    ap.add_argument("--autotune-steps", type=int, default=11)
     ap.add_argument("--serve", action="store_true", help="serving benchmark instead")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-solo", type=int, default=60)

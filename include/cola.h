@@ -302,11 +302,21 @@ typedef struct cola_batch cola_batch;
  * equal Np, Nmesh, Lbox, nk_table and seed_precision (seeds, models and
  * cosmologies may differ); otherwise groups have one context.  Groups are
  * spread round-robin over `chains` concurrent streams; `grid_cap` > 0 bounds
- * the persistent grid of every FFT pass so concurrent groups share the SMs. */
+ * the persistent grid of every FFT pass so concurrent groups share the SMs.
+ * deposit_box / gather_box choose the particle kernels of the step: 0 the
+ * direct ones (CIC deposit by global atomics merged within each warp; gather
+ * by direct loads of the mesh); > 0 the shared-memory box kernels, where each
+ * CTA takes an 8 x 8 x 8 block of the Lagrangian lattice and bins its deposit
+ * in, or stages its gather from, a box of at most that many mesh cells in
+ * shared memory (deposit <= 16384, gather <= 8192; larger values are clamped,
+ * values are rounded down to a multiple of 4; a block whose box does not fit
+ * uses the direct path).  The results agree to float rounding either way. */
 typedef struct {
-  int32_t group;    /* contexts per group; <= 0: all (one shape) or 1 */
-  int32_t chains;   /* concurrent streams, >= 1 */
-  int32_t grid_cap; /* CTAs per FFT pass, 0 = no cap */
+  int32_t group;       /* contexts per group; <= 0: all (one shape) or 1 */
+  int32_t chains;      /* concurrent streams, >= 1 */
+  int32_t grid_cap;    /* CTAs per FFT pass, 0 = no cap */
+  int32_t deposit_box; /* shared-memory deposit bins (cells), 0 = direct atomics */
+  int32_t gather_box;  /* shared-memory gather box (cells), 0 = direct loads */
 } cola_batch_plan;
 
 /* Groups 1..65535 distinct contexts that completed cola_ic, have equal nsteps
@@ -329,9 +339,12 @@ int cola_batch_get_plan(const cola_batch* b, cola_batch_plan* out);
  * first group's stage timings (covering all of its simulations) are recorded. */
 int cola_batch_step(cola_batch* b, int32_t nsteps);
 /* Autotuner: times up to max_steps real steps (they advance the batch), one
- * per candidate plan (one group over everything; halves and quarters on
- * concurrent chains; small groups on many chains with a capped grid), and
- * keeps the fastest for later steps; *best_out receives it (may be NULL). */
+ * per candidate plan, and keeps the fastest for later steps; *best_out
+ * receives it (may be NULL).  Candidates: first the launch grouping (one
+ * group over everything; halves and quarters on concurrent chains; small
+ * groups on many chains with a capped grid), then, with the best grouping,
+ * the particle kernels (deposit bins of 4096 and 16384 cells against direct
+ * atomics, gather boxes of 4096 and 8192 cells against direct loads). */
 int cola_batch_autotune(cola_batch* b, int32_t max_steps, cola_batch_plan* best_out);
 /* Matter power spectrum of every context (same estimator and bins as
  * cola_pk), computed by multi-simulation launches with one synchronisation:

@@ -49,7 +49,18 @@ class cola_model(ctypes.Structure):
 
 
 class cola_batch_plan(ctypes.Structure):
-    _fields_ = [("group", ctypes.c_int32), ("chains", ctypes.c_int32), ("grid_cap", ctypes.c_int32)]
+    _fields_ = [("group", ctypes.c_int32), ("chains", ctypes.c_int32), ("grid_cap", ctypes.c_int32),
+                ("deposit_box", ctypes.c_int32), ("gather_box", ctypes.c_int32)]
+
+
+def _plan5(plan):
+    """(group, chains, grid_cap[, deposit_box, gather_box]) -> cola_batch_plan."""
+    v = tuple(int(x) for x in plan) + (0,) * (5 - len(plan))
+    return cola_batch_plan(*v[:5])
+
+
+def _plan_tuple(p) -> tuple:
+    return int(p.group), int(p.chains), int(p.grid_cap), int(p.deposit_box), int(p.gather_box)
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -429,8 +440,9 @@ def ic_many(sims, stream=None):
 class Batch:
     """cola_batch over Simulations: one CUDA graph launch per step for all of them.
 
-    plan = (group, chains, grid_cap) as in cola_batch_plan; None: one group over
-    all simulations when they share a shape, else one per group on one chain.
+    plan = (group, chains, grid_cap[, deposit_box, gather_box]) as in cola_batch_plan;
+    None: one group over all simulations when they share a shape, else one per group
+    on one chain, direct particle kernels.
     """
 
     def __init__(self, sims, plan=None, stream=None):
@@ -439,7 +451,7 @@ class Batch:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         arr = (_P * len(self.sims))(*[s.ctx for s in self.sims])
         h = _P()
-        p = ctypes.byref(cola_batch_plan(*plan)) if plan is not None else None
+        p = ctypes.byref(_plan5(plan)) if plan is not None else None
         _check(lib().cola_batch_create(arr, len(self.sims), p, _P(self.stream.cuda_stream), ctypes.byref(h)))
         self.h = h
 
@@ -450,17 +462,17 @@ class Batch:
         """Times candidate plans on real steps; returns the kept (group, chains, grid_cap)."""
         p = cola_batch_plan()
         _check(lib().cola_batch_autotune(self.h, int(max_steps), ctypes.byref(p)))
-        return int(p.group), int(p.chains), int(p.grid_cap)
+        return _plan_tuple(p)
 
     @property
     def plan(self):
         p = cola_batch_plan()
         _check(lib().cola_batch_get_plan(self.h, ctypes.byref(p)))
-        return int(p.group), int(p.chains), int(p.grid_cap)
+        return _plan_tuple(p)
 
     @plan.setter
     def plan(self, value):
-        _check(lib().cola_batch_set_plan(self.h, ctypes.byref(cola_batch_plan(*value))))
+        _check(lib().cola_batch_set_plan(self.h, ctypes.byref(_plan5(value))))
 
     def pk(self, nbins: Optional[int] = None):
         """(k, P, nmodes), each [n_sims, nbins], for every simulation in batch order."""

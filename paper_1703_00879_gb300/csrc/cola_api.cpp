@@ -107,14 +107,14 @@ struct cola_batch {
   std::vector<cudaStream_t> chain_st;      // forked capture streams (owned, created on demand)
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;           // one per chain stream (owned)
-  cola_batch_plan plan{1, 1, 0};
+  cola_batch_plan plan{1, 1, 0, 0, 0};
   int step = 0;
   struct Graph {
     cudaGraphExec_t exec = nullptr;
     void* shifts = nullptr;                // device shift arrays the graph's launches read
                                            // (through the first context's allocator, on cap_st)
   };
-  std::map<std::tuple<int, int, int>, Graph> graphs;  // plan -> graph serving every step
+  std::map<std::tuple<int, int, int, int, int>, Graph> graphs;  // plan -> graph serving every step
   double* pk_acc = nullptr;                // [n][3 * kMaxBins] + n shifts (batch P(k)), through
                                            // the first context's allocator, on st
   std::string err;
@@ -1614,6 +1614,8 @@ static cola_batch_plan normal_plan(const cola_batch* b, cola_batch_plan p) {
   const int groups = (n + p.group - 1) / p.group;
   p.chains = std::max(1, std::min(p.chains < 1 ? 1 : p.chains, groups));
   p.grid_cap = std::max(0, p.grid_cap);
+  p.deposit_box = std::max(0, std::min(p.deposit_box, 16384)) & ~3;
+  p.gather_box = std::max(0, std::min(p.gather_box, 8192)) & ~3;
   return p;
 }
 
@@ -1701,6 +1703,7 @@ static int batch_capture(cola_batch* b, int n, const cola_batch_plan& p, cola_ba
   cudaError_t e = cudaEventRecord(b->fork, b->cap_st);
   for (int c = 0; c < C && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(b->chain_st[c], b->fork, 0);
   set_grid_cap(p.grid_cap);
+  set_particle_plan(p.deposit_box, p.gather_box);
   for (size_t j = 0; j < groups.size() && e == cudaSuccess && rc == COLA_OK; ++j) {
     cola_ctx* lead = groups[j].g.lead;
     cudaStream_t saved = lead->st;
@@ -1713,6 +1716,7 @@ static int batch_capture(cola_batch* b, int n, const cola_batch_plan& p, cola_ba
     if (rc != COLA_OK) b->err = lead->err;
   }
   set_grid_cap(0);
+  set_particle_plan(0, 0);
   for (int c = 0; c < C && e == cudaSuccess; ++c) {
     e = cudaEventRecord(b->join[c], b->chain_st[c]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap_st, b->join[c], 0);
@@ -1733,7 +1737,7 @@ static int batch_capture(cola_batch* b, int n, const cola_batch_plan& p, cola_ba
 }
 
 static int batch_graph(cola_batch* b, const cola_batch_plan& p, cudaGraphExec_t* ex) {
-  const auto key = std::make_tuple(p.group, p.chains, p.grid_cap);
+  const auto key = std::make_tuple(p.group, p.chains, p.grid_cap, p.deposit_box, p.gather_box);
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
     cola_batch::Graph g;
@@ -1770,8 +1774,10 @@ static int batch_eager(cola_batch* b, const cola_batch_plan& p, int n) {
     cudaStream_t saved = lead->st;
     lead->st = b->cap_st;
     set_grid_cap(p.grid_cap);
+    set_particle_plan(p.deposit_box, p.gather_box);
     rc = enqueue_group_step(gp.g, n);
     set_grid_cap(0);
+    set_particle_plan(0, 0);
     lead->st = saved;
     if (rc != COLA_OK) {
       b->err = lead->err;
@@ -1825,7 +1831,7 @@ int cola_batch_create(cola_ctx* const* ctxs, int32_t n, const cola_batch_plan* p
   b->step = ctxs[0]->step;
   b->uniform = true;
   for (int i = 1; i < n; ++i) b->uniform = b->uniform && same_shape(ctxs[0], ctxs[i]);
-  b->plan = normal_plan(b, plan ? *plan : cola_batch_plan{0, 1, 0});
+  b->plan = normal_plan(b, plan ? *plan : cola_batch_plan{0, 1, 0, 0, 0});
   auto bail = [&](cudaError_t e) {
     g_err = std::string("cola_batch_create: ") + cudaGetErrorString(e);
     cola_batch_free(b);
@@ -1880,16 +1886,21 @@ int cola_batch_autotune(cola_batch* b, int32_t max_steps, cola_batch_plan* best_
   if (b->uniform) {
     // one group over everything; halves and quarters on concurrent chains;
     // small groups on many chains with a capped grid (more on-chip reuse)
-    cand = {{n, 1, 0}, {(n + 1) / 2, 2, 0}, {(n + 3) / 4, 4, 0}, {(n + 7) / 8, 4, 0},
-            {std::max(1, n / 32), 8, sms}, {1, 32, sms}};
+    cand = {{n, 1, 0, 0, 0}, {(n + 1) / 2, 2, 0, 0, 0}, {(n + 3) / 4, 4, 0, 0, 0}, {(n + 7) / 8, 4, 0, 0, 0},
+            {std::max(1, n / 32), 8, sms, 0, 0}, {1, 32, sms, 0, 0}};
   } else {
-    cand = {{1, 32, sms}, {1, 64, sms / 2}, {1, 16, 2 * sms}, {1, 128, sms / 4}, {1, 8, 0}, {1, 32, 0}};
+    cand = {{1, 32, sms, 0, 0}, {1, 64, sms / 2, 0, 0}, {1, 16, 2 * sms, 0, 0}, {1, 128, sms / 4, 0, 0},
+            {1, 8, 0, 0, 0}, {1, 32, 0, 0, 0}};
   }
+  auto same = [](const cola_batch_plan& a, const cola_batch_plan& q) {
+    return a.group == q.group && a.chains == q.chains && a.grid_cap == q.grid_cap &&
+           a.deposit_box == q.deposit_box && a.gather_box == q.gather_box;
+  };
   std::vector<cola_batch_plan> plans;
   for (const auto& c : cand) {
     const cola_batch_plan p = normal_plan(b, c);
     bool dup = false;
-    for (const auto& q : plans) dup = dup || (q.group == p.group && q.chains == p.chains && q.grid_cap == p.grid_cap);
+    for (const auto& q : plans) dup = dup || same(q, p);
     if (!dup) plans.push_back(p);
   }
   const int budget = std::min<int>(max_steps > 0 ? max_steps : total, total - b->step);
@@ -1900,28 +1911,48 @@ int cola_batch_autotune(cola_batch* b, int32_t max_steps, cola_batch_plan* best_
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
   int rc = COLA_OK;
-  for (const auto& p : plans) {
-    if (used >= budget) break;
-    // capture outside the timed region, then time one launch (one real step)
+  // one real step under plan p, timed on the caller's stream (capture outside the timing)
+  auto time_plan = [&](const cola_batch_plan& p, float& ms) -> int {
     cudaGraphExec_t ex = nullptr;
-    rc = batch_graph(b, p, &ex);
-    if (rc != COLA_OK) break;
+    int r = batch_graph(b, p, &ex);
+    if (r != COLA_OK) return r;
     cudaError_t e = cudaEventRecord(e0, b->st);
-    if (e == cudaSuccess) rc = batch_launch(b, p);
-    if (rc != COLA_OK) break;
-    if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);  // the caller's stream waits for the graph
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      rc = bfail(b, COLA_ECUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
-      break;
+    if (e == cudaSuccess) {
+      r = batch_launch(b, p);
+      if (r != COLA_OK) return r;
+      e = cudaEventRecord(e1, b->st);  // the caller's stream waits for the graph
     }
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) return bfail(b, COLA_ECUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
     ++used;
+    return COLA_OK;
+  };
+  auto consider = [&](const cola_batch_plan& p) -> int {
+    if (used >= budget) return COLA_OK;
+    float ms = 0.f;
+    CHECK_RC(time_plan(p, ms));
     if (ms < best) {
       best = ms;
       bestp = p;
     }
+    return COLA_OK;
+  };
+  // 1. the launch grouping
+  for (const auto& p : plans)
+    if ((rc = consider(p)) != COLA_OK) break;
+  // 2. the particle kernels with the best grouping: that plan is timed again
+  //    first (later steps cost more once particles cluster), then deposit bins
+  //    and gather boxes against it
+  if (rc == COLA_OK && used + 1 < budget) {
+    float ms = 0.f;
+    rc = time_plan(bestp, ms);
+    if (rc == COLA_OK) best = ms;
+    for (int v : {4096, 16384})
+      if (rc == COLA_OK) rc = consider(normal_plan(b, {bestp.group, bestp.chains, bestp.grid_cap, v, 0}));
+    const int dep = bestp.deposit_box;
+    for (int v : {4096, 8192})
+      if (rc == COLA_OK) rc = consider(normal_plan(b, {bestp.group, bestp.chains, bestp.grid_cap, dep, v}));
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -310,6 +310,10 @@ cudaError_t seed_quantise(int N, const float2* src, void* dst, int prec, const S
 // Caps the persistent grid of the FFT-pass kernels launched by the calling
 // thread (0 = no cap: resident CTAs x SMs).
 void set_grid_cap(int max_ctas);
+// Particle kernels the calling thread's step launches use: deposit_box /
+// gather_box > 0 selects the shared-memory box kernels with that many cells
+// (rounded down to a multiple of 4; at most 16384 / 8192), 0 the direct ones.
+void set_particle_plan(int deposit_box, int gather_box);
 
 // Loads the allocation-free P(k) scratch on the current device (once per
 // device; later calls return at once).  COLA_OK or COLA_ECUDA.

@@ -23,8 +23,10 @@ def _solo(pkg, run):
         return s.export(pkg.COLA_F_DISP), s.pk()
 
 
-@pytest.mark.parametrize("plan", [None, (2, 1, 0), (4, 2, 0), (3, 2, 76), (1, 3, 0)],
-                         ids=["one_group", "pairs", "quads_2chains", "triples_capped", "singles_3chains"])
+@pytest.mark.parametrize("plan", [None, (2, 1, 0), (4, 2, 0), (3, 2, 76), (1, 3, 0), (6, 1, 0, 16384, 8192),
+                                  (6, 1, 0, 64, 64), (2, 2, 0, 4096, 0)],
+                         ids=["one_group", "pairs", "quads_2chains", "triples_capped", "singles_3chains",
+                              "shared_boxes", "tiny_boxes_fall_back", "pairs_deposit_bins"])
 def test_batch_equals_solo(plan):
     """Every model of the ensemble set (LCDM, f(R) x3, nDGP x2) in one batch:
     the model-dependent force stages run per model subset of each group."""
@@ -109,13 +111,14 @@ def test_batch_of_reduced_precision_seeds_equals_solo():
 
 def test_batch_autotune_keeps_results():
     import paper_1703_00879_gb300 as pkg
-    runs = _runs(8, steps=8)
+    runs = _runs(8, steps=10)
     solo = [_solo(pkg, r) for r in runs]
     sims = [pkg.Simulation(r) for r in runs]
     with pkg.Batch(sims) as b:
-        group, chains, cap = b.autotune(max_steps=6)
+        group, chains, cap, dep, gk = b.autotune(max_steps=8)
         assert 1 <= group <= 8 and 1 <= chains <= 8 and cap >= 0
-        assert b.plan == (group, chains, cap)
+        assert dep in (0, 4096, 16384) and gk in (0, 4096, 8192)
+        assert b.plan == (group, chains, cap, dep, gk)
         b.step(-1)
     for r, s, (d0, _) in zip(runs, sims, solo):
         assert np.max(np.abs(s.export(pkg.COLA_F_DISP) - d0)) / (r.Lbox / r.Nmesh) <= 1e-4
