@@ -52,18 +52,30 @@ __device__ __forceinline__ Cic cic_setup(const PartParams& pp, int ix, int iy, i
   return c;
 }
 
+// Non-returning global reductions.  atomicAdd on a float4 returns the old
+// value, and those returns cost as much crossbar traffic as the additions
+// themselves (ncu: as many xbar-to-L1 sectors as L1-to-xbar sectors); the
+// deposit never reads them.
+__device__ __forceinline__ void red_add4(float* p, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
 // Adds a0 at row[i0] and a1 at row[i1] (i1 = i0 + 1, or 0 when i0 ends the
-// row).  One vector atomic (red.global.add.v4.f32, zeros in the other lanes)
+// row).  One vector reduction (red.global.add.v4.f32, zeros in the other lanes)
 // covers the 16-byte group of i0 and, unless i0 is the group's last cell, i1;
 // otherwise (q = 3, which includes the wrap: Nm is a multiple of 4) a scalar
-// atomic adds a1.  Every lane issues the vector atomic, so a warp runs two
-// atomic instructions per call rather than three on divergent paths.
+// reduction adds a1.  Every lane issues the vector reduction, so a warp runs two
+// reduction instructions per call rather than three on divergent paths.
 __device__ __forceinline__ void row_add(float* __restrict__ row, int i0, int i1, float a0, float a1) {
   const int q = i0 & 3;
   const float4 v = make_float4(q == 0 ? a0 : 0.f, q == 1 ? a0 : (q == 0 ? a1 : 0.f),
                                q == 2 ? a0 : (q == 1 ? a1 : 0.f), q == 3 ? a0 : (q == 2 ? a1 : 0.f));
-  atomicAdd(reinterpret_cast<float4*>(row + (i0 - q)), v);
-  if (q == 3) atomicAdd(row + i1, a1);
+  red_add4(row + (i0 - q), v);
+  if (q == 3) red_add(row + i1, a1);
 }
 
 __device__ __forceinline__ void cic_deposit(float* __restrict__ rho, int Nm, const Cic& c) {
@@ -600,7 +612,7 @@ __global__ void __launch_bounds__(NTP, 3) k_drift_deposit_box(
     const float4 v = s4[r * (ex >> 2) + g];
     if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
       const int64_t row = ((int64_t)((b.lo[2] + zz) & mask) * Nm + ((b.lo[1] + yy) & mask)) * Nm;
-      atomicAdd(reinterpret_cast<float4*>(rho + row + ((x0 + 4 * g) & mask)), v);
+      red_add4(rho + row + ((x0 + 4 * g) & mask), v);
     }
   });
 }
