@@ -213,6 +213,15 @@ int cola_pk_result(cola_ctx* ctx, double* k, double* pk, int64_t* nmodes);
  * synchronisation).  Errors: COLA_EINVAL, COLA_ECUDA. */
 int cola_set_stream(cola_ctx* ctx, void* stream);
 
+/* Failure detection: the number of non-finite values (NaN, +-Inf) in the particle
+ * state (displacement, residual velocity and residual acceleration: 9 Np^3 floats),
+ * counted on the device, in *nonfinite (0: the state is finite).  A run that went
+ * unstable (too few steps for its model, a corrupted import) shows here before
+ * its P(k) does.  Waits for the stream (bounded by cola_set_wait_limit).  The paper
+ * has no counterpart.  Errors: COLA_EINVAL, COLA_ESTATE (no ICs yet, or a
+ * cola_pk_async result pending), COLA_ECUDA, COLA_ETIMEOUT. */
+int cola_check_state(cola_ctx* ctx, int64_t* nonfinite);
+
 /* Bounded host waits.  Every call that waits on the host for the context's
  * stream (host-buffer snapshots, exports and imports, cola_pk, cola_pk_result,
  * cola_wait) gives up after `seconds` with COLA_ETIMEOUT when seconds > 0

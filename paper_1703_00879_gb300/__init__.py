@@ -101,6 +101,7 @@ _SIGS = {
     "cola_pk_result": (ctypes.c_int, [_P, _P, _P, _P]),
     "cola_set_stream": (ctypes.c_int, [_P, _P]),
     "cola_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_double]),
+    "cola_check_state": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "cola_wait": (ctypes.c_int, [_P]),
     "cola_batch_steps_done": (ctypes.c_int32, [_P]),
     "cola_batch_free": (None, [_P]),
@@ -329,6 +330,12 @@ class Simulation:
         k, pk, nm = np.empty(nb), np.empty(nb), np.empty(nb, np.int64)
         _check(lib().cola_pk_result(self.ctx, k.ctypes.data, pk.ctypes.data, nm.ctypes.data), self.ctx)
         return k, pk, nm
+
+    def check_state(self) -> int:
+        """Number of non-finite values in the particle state (0 when it is finite)."""
+        v = ctypes.c_int64(-1)
+        _check(lib().cola_check_state(self.ctx, ctypes.byref(v)), self.ctx)
+        return int(v.value)
 
     def set_wait_limit(self, seconds: float):
         """Host waits of this context give up after `seconds` with COLA_ETIMEOUT (0: no limit)."""

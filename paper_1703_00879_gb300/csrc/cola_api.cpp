@@ -1,6 +1,7 @@
 // C ABI of libcola: context, buffers, and the orchestration of the COLA step
 // (Sec. 2, Sec. 4, Sec. 6, App. A, App. B) on one CUDA stream.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <chrono>
 #include <algorithm>
@@ -148,8 +149,11 @@ cudaEvent_t take_event(cola_ctx* c) {
   return e;
 }
 
-// Records the start of a launch group; returns the event (null when not profiling).
-cudaEvent_t prof_begin(cola_ctx* c) {
+// Records the start of a launch group; returns the event (null when not
+// profiling).  Every stage is also an NVTX range (a no-op without a tool
+// attached), so a timeline profiler shows the step's stages by name.
+cudaEvent_t prof_begin(cola_ctx* c, int stage) {
+  nvtxRangePushA(kStageNames[stage]);
   if (!c->prof) return nullptr;
   cudaEvent_t e = take_event(c);
   if (e) cudaEventRecord(e, c->st);
@@ -159,6 +163,7 @@ cudaEvent_t prof_begin(cola_ctx* c) {
 // Closes a launch group of `launches` kernels that moves `bytes` algorithmic
 // bytes in total.
 void prof_end(cola_ctx* c, int stage, cudaEvent_t start, int launches, double bytes) {
+  nvtxRangePop();
   if (!c->prof || !start) return;
   cudaEvent_t e = take_event(c);
   if (!e) return;
@@ -699,16 +704,16 @@ int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}) {
   auto st = ctx->st;
   const double H = (double)N * N * (N / 2 + 1) * 8.0, R = (double)N * N * N * 4.0;
   const double seedH = H * (lp.seed_prec ? 0.5 : 1.0);
-  cudaEvent_t e = prof_begin(ctx);
+  cudaEvent_t e = prof_begin(ctx, ST_LPT_Z);
   CK(lpt_z(N, p1, p2, ctx->lc[0], ctx->lc[1], ctx->lc[2], ctx->lc[3], lp, ctx->tw_np, st, m));
   prof_end(ctx, ST_LPT_Z, e, 1, m.nb * (2 * seedH + 4 * H));
-  e = prof_begin(ctx);
+  e = prof_begin(ctx, ST_LPT_Y);
   CK(fft_yinv2(N, ctx->lc[0], ctx->lc[0], ctx->lc[4], kf, ctx->tw_np, st, m));
   CK(fft_col(N, ctx->lc[1], 1, true, ctx->tw_np, st, m));
   CK(fft_yinv2(N, ctx->lc[2], ctx->lc[2], ctx->lc[5], kf, ctx->tw_np, st, m));
   CK(fft_col(N, ctx->lc[3], 1, true, ctx->tw_np, st, m));
   prof_end(ctx, ST_LPT_Y, e, 4, m.nb * 10.0 * H);
-  e = prof_begin(ctx);
+  e = prof_begin(ctx, ST_LPT_X);
   // variant a.S1: the per-step drift and kick fields leave the x pass as 16-bit
   // values (one FP32 scale per field, delayed scaling)
   const bool q16 = lp.seed_prec != 0 && vel == 0 && add_step;
@@ -774,49 +779,49 @@ int force_group(const Group& g, double a, bool device_params, bool ini = false) 
   auto st = ctx->st;
   const float2* tw = ctx->tw_nm;
   const double H = (double)N * N * (N / 2 + 1) * 8.0, R = (double)N * N * N * 4.0;
-  cudaEvent_t e = prof_begin(ctx);
+  cudaEvent_t e = prof_begin(ctx, ST_MESH_XR2C);
   CK(fft_xr2c(N, ctx->rho, ctx->Cd, fp.inv_rhobar, -1.f, tw, st, all));
   prof_end(ctx, ST_MESH_XR2C, e, 1, all.nb * (R + H));
-  e = prof_begin(ctx);
+  e = prof_begin(ctx, ST_MESH_Y);
   CK(fft_col(N, ctx->Cd, 1, false, tw, st, all));
   prof_end(ctx, ST_MESH_Y, e, 1, all.nb * 2 * H);
   if (const Group::Sub& sc = g.screened; sc.lead) {
-    e = prof_begin(ctx);
+    e = prof_begin(ctx, ST_Z_SCREEN_FIELD);
     for (const Group::Sub* sub : {&g.fr_screened, &g.dgp_screened})
       if (sub->lead)
         CK(mesh_z_screen_field(N, sub->lead->Cd, sub->lead->Ck, sub->lead->Cw, fp_of(sub->lead), tw, st,
                                sub->m));
     prof_end(ctx, ST_Z_SCREEN_FIELD, e, (g.fr_screened.lead ? 1 : 0) + (g.dgp_screened.lead ? 1 : 0),
              sc.m.nb * 3 * H);
-    e = prof_begin(ctx);
+    e = prof_begin(ctx, ST_MESH_YINV);
     CK(fft_col(N, sc.lead->Cw, 1, true, tw, st, sc.m));
     prof_end(ctx, ST_MESH_YINV, e, 1, sc.m.nb * 2 * H);
-    e = prof_begin(ctx);
+    e = prof_begin(ctx, ST_X_SCREEN_SOURCE);
     for (const Group::Sub* sub : {&g.fr_screened, &g.dgp_screened})
       if (sub->lead)
         CK(mesh_x_screen_source(N, sub->lead->Cw, sub->lead->rho, sub->lead->Cd, fp_of(sub->lead), tw,
                                 st, sub->m));
     prof_end(ctx, ST_X_SCREEN_SOURCE, e, (g.fr_screened.lead ? 1 : 0) + (g.dgp_screened.lead ? 1 : 0),
              sc.m.nb * (2 * H + R));
-    e = prof_begin(ctx);
+    e = prof_begin(ctx, ST_MESH_Y);
     CK(fft_col(N, sc.lead->Cd, 1, false, tw, st, sc.m));
     prof_end(ctx, ST_MESH_Y, e, 1, sc.m.nb * 2 * H);
-    e = prof_begin(ctx);
+    e = prof_begin(ctx, ST_Z_FORCE);
     CK(mesh_z_force(N, sc.lead->Cd, sc.lead->Ck, sc.lead->Cphi, sc.lead->Cphz, fp_of(sc.lead), tw, st,
                     sc.m));
     prof_end(ctx, ST_Z_FORCE, e, 1, sc.m.nb * 4 * H);
   }
   if (const Group::Sub& un = g.unscreened; un.lead) {
-    e = prof_begin(ctx);
+    e = prof_begin(ctx, ST_Z_FORCE);
     CK(mesh_z_force(N, un.lead->Cd, nullptr, un.lead->Cphi, un.lead->Cphz, fp_of(un.lead), tw, st,
                     un.m));
     prof_end(ctx, ST_Z_FORCE, e, 1, un.m.nb * 3 * H);
   }
-  e = prof_begin(ctx);
+  e = prof_begin(ctx, ST_MESH_YINV);
   CK(fft_yinv2(N, ctx->Cphi, ctx->Cphi, ctx->Cw, -fp.kf, tw, st, all));
   CK(fft_col(N, ctx->Cphz, 1, true, tw, st, all));
   prof_end(ctx, ST_MESH_YINV, e, 2, all.nb * 5.0 * H);
-  e = prof_begin(ctx);
+  e = prof_begin(ctx, ST_MESH_XC2R);
   {
     const float2* in3[3] = {ctx->Cphi, ctx->Cw, ctx->Cphz};
     float* out3[3] = {ctx->F[0], ctx->F[1], ctx->F[2]};
@@ -1000,16 +1005,16 @@ int enqueue_group_step(const Group& g, int n) {
       ld[d] = reinterpret_cast<const float*>(ctx->lq[d]);
       lk[d] = reinterpret_cast<const float*>(ctx->lq[3 + d]);
     }
-  cudaEvent_t e = prof_begin(ctx);
+  cudaEvent_t e = prof_begin(ctx, ST_RHO_ZERO);
   CK(zero_f32(ctx->rho, ctx->M, ctx->st, m));
   prof_end(ctx, ST_RHO_ZERO, e, 1, m.nb * 4.0 * Mb);
-  e = prof_begin(ctx);
+  e = prof_begin(ctx, ST_DRIFT_DEPOSIT);
   CK(part_drift_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                         ctx->acc[0], ctx->acc[1], ctx->acc[2], ld[0], ld[1], ld[2], ctx->rho, dt,
                         ctx->P, ctx->st, m, mix));
   prof_end(ctx, ST_DRIFT_DEPOSIT, e, 1, m.nb * ((fast ? 84.0 : lq ? 66.0 : 72.0) * Pb + 8.0 * Mb));
   CHECK_RC(force_group(g, ctx->a[n + 1], true));
-  e = prof_begin(ctx);
+  e = prof_begin(ctx, ST_GATHER_KICK);
   if (fast)  // A_LPT: Psi1 (lr[0..2]) mixed with Psi2
     for (int d = 0; d < 3; ++d) lk[d] = ctx->lr[d];
   CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
@@ -1389,6 +1394,26 @@ int cola_pk_result(cola_ctx* ctx, double* k, double* pk, int64_t* nmodes) {
   }
   finish_pk(ctx, ctx->pk_host, ctx->pk_nbins, k, pk, nmodes);
   ctx->pk_nbins = 0;
+  return COLA_OK;
+}
+
+int cola_check_state(cola_ctx* ctx, int64_t* nonfinite) {
+  if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
+  if (!nonfinite) return fail(ctx, COLA_EINVAL, "nonfinite is NULL");
+  if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_check_state before cola_ic");
+  const float* f[9] = {ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
+                       ctx->acc[0], ctx->acc[1], ctx->acc[2]};
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(ctx->scratch);
+  CK(count_nonfinite(f, 9, ctx->P, d, ctx->st));
+  // the count lands in a pinned slot, so a wait that times out leaves no copy into freed memory
+  if (!ctx->pk_host && !(ctx->pk_host = g_pk_slots.get()))
+    return fail(ctx, COLA_ENOMEM, "cola_check_state: pinned host buffer allocation failed");
+  if (ctx->pk_nbins) return fail(ctx, COLA_ESTATE, "a cola_pk_async result is still pending");
+  CK(cudaMemcpyAsync(ctx->pk_host, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->st));
+  CHECK_RC(host_wait(ctx));
+  unsigned long long v = 0;
+  std::memcpy(&v, ctx->pk_host, sizeof(v));
+  *nonfinite = (int64_t)v;
   return COLA_OK;
 }
 

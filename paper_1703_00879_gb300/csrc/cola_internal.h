@@ -252,6 +252,9 @@ cudaError_t lq_init(SimHeader* hdr, const float* const* fields, int64_t P, int p
 cudaError_t lq_dequant(const void* src, float* dst, int64_t P, int prec, const SimHeader* hdr, int f,
                        cudaStream_t s);
 
+// *out = the number of non-finite values among nf (<= 9) device arrays of n floats.
+cudaError_t count_nonfinite(const float* const* f, int nf, int64_t n, unsigned long long* out, cudaStream_t s);
+
 // hdr->step += 1 (end of a step)
 cudaError_t step_advance(SimHeader* hdr, cudaStream_t s, Multi m = {});
 // hdr = v (one simulation), except the seed scales, which keep their device values

@@ -1013,6 +1013,31 @@ cudaError_t lq_dequant(const void* src, float* dst, int64_t P, int prec, const S
   return cudaGetLastError();
 }
 
+// Non-finite values (NaN, +-Inf) among nf arrays of n floats each, added into *out.
+struct NineArrays {
+  const float* f[9];
+};
+__global__ void __launch_bounds__(NTP) k_count_nonfinite(const __grid_constant__ NineArrays a, int nf, int64_t n,
+                                                         unsigned long long* __restrict__ out) {
+  unsigned cnt = 0;
+  for (int j = 0; j < nf; ++j)
+    for (int64_t i = (int64_t)blockIdx.x * NTP + threadIdx.x; i < n; i += (int64_t)gridDim.x * NTP)
+      cnt += isfinite(a.f[j][i]) ? 0u : 1u;
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, (unsigned long long)cnt);
+}
+
+cudaError_t count_nonfinite(const float* const* f, int nf, int64_t n, unsigned long long* out, cudaStream_t s) {
+  if (nf < 1 || nf > 9) return cudaErrorInvalidValue;
+  NineArrays a{};
+  for (int j = 0; j < nf; ++j) a.f[j] = f[j];
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + NTP - 1) / NTP, 152 * 8));
+  k_count_nonfinite<<<gx, NTP, 0, s>>>(a, nf, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t step_advance(SimHeader* hdr, cudaStream_t s, Multi m) {
   k_step_advance<<<(m.nb + 127) / 128, 128, 0, s>>>(hdr, m);
   return cudaGetLastError();

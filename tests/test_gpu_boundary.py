@@ -164,3 +164,71 @@ def test_wait_limit_returns_etimeout_and_keeps_the_context_usable(pkg):
         k2, P2, _ = s.pk()
         assert np.all(np.isfinite(P2[nm > 0])) and not np.array_equal(P, P2)
     torch.cuda.synchronize()
+
+
+class _Failing(_Counting):
+    """Counting callbacks that return NULL once `budget` allocations have been handed out."""
+
+    def __init__(self, pkg, budget):
+        import torch
+        dev = torch.cuda.current_device()
+        self.live, self.calls, self.budget = {}, [], budget
+
+        def _alloc(nbytes, stream, user):
+            if len(self.calls) >= self.budget:
+                self.calls.append(-int(nbytes))
+                return None
+            p = torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+            self.live[int(p)] = int(nbytes)
+            self.calls.append(int(nbytes))
+            return p
+
+        def _free(ptr, stream, user):
+            assert int(ptr) in self.live
+            del self.live[int(ptr)]
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.cbs = (pkg.ALLOC_FN(_alloc), pkg.FREE_FN(_free))
+
+
+def test_failing_allocator_gives_enomem_and_leaks_nothing(pkg):
+    """Fault injection on the host: an allocator that refuses.  cola_init returns COLA_ENOMEM with
+    nothing allocated; a batch whose shift array cannot be allocated fails its step with
+    COLA_ENOMEM and the contexts stay usable."""
+    import torch
+    L = pkg.lib()
+    st = torch.cuda.current_stream()
+    run = SMALL_F5.with_(nsteps=3)
+    cb = _Failing(pkg, 0)
+    cfg = pkg.make_config(run)
+    h = ctypes.c_void_p()
+    rc = L.cola_init(ctypes.byref(cfg), cb.cbs[0], cb.cbs[1], None, ctypes.c_void_p(st.cuda_stream), ctypes.byref(h))
+    assert rc == pkg.COLA_ENOMEM and not h.value and cb.live == {}
+    cb = _Failing(pkg, 2)                                  # the two contexts, then nothing
+    ctxs = [_ctx(pkg, run.with_(seed=i), cb, st) for i in range(2)]
+    for c in ctxs:
+        pkg._check(L.cola_ic(c), c)
+    arr = (ctypes.c_void_p * 2)(*[c.value for c in ctxs])
+    b = ctypes.c_void_p()
+    pkg._check(L.cola_batch_create(arr, 2, None, ctypes.c_void_p(st.cuda_stream), ctypes.byref(b)))
+    assert L.cola_batch_step(b, 1) == pkg.COLA_ENOMEM     # the graph's shift array
+    L.cola_batch_free(b)
+    pkg._check(L.cola_step(ctxs[0], 1), ctxs[0])           # the contexts are still usable
+    for c in ctxs:
+        L.cola_free(c)
+    torch.cuda.synchronize()
+    assert cb.live == {}
+
+
+def test_check_state_counts_non_finite_values(pkg):
+    """cola_check_state: 0 for a healthy run; a NaN and an Inf planted in the imported state are
+    counted, and the next step's residual acceleration is checked as well."""
+    run = SMALL_F5.with_(nsteps=4)
+    with pkg.Simulation(run) as s:
+        s.step(2)
+        assert s.check_state() == 0
+        d, v, a = (s.export(w) for w in (pkg.COLA_F_DISP, pkg.COLA_F_DV, pkg.COLA_F_ACC))
+        d[0, 5] = np.nan
+        v[2, 7] = np.inf
+        s.import_state(d, v, a, steps_done=2)
+        assert s.check_state() == 2
