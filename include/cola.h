@@ -28,7 +28,8 @@
  *     allocate their small shift and P(k) arrays through the first context's
  *     callbacks.  The library itself never calls cudaMalloc or cudaFree; the
  *     host keeps computed growth tables in a bounded host cache and stages
- *     uploads through one pinned host ring allocated at the first cola_init,
+ *     uploads through a pinned host ring per device, allocated at the first
+ *     cola_init on that device,
  *     so creating, stepping and freeing contexts never synchronises the
  *     device.  Buffers passed in by the caller stay owned by the caller.
  *   - Allocator contract: alloc(bytes, stream, user) returns memory usable on

@@ -400,10 +400,11 @@ void growth_for(const cola_config& cfg, const HModel& m, Growth& g, std::vector<
 // pair) is computed on the host once per key and kept in a bounded host cache;
 // every context holds its own device copy inside its single allocation, so all
 // device memory comes through the caller's allocator and goes in cola_free.
-constexpr size_t kMaxHostTables = 1024;
+constexpr size_t kMaxHostTableBytes = (size_t)256 << 20;
 std::mutex g_host_mu;
 std::map<std::vector<double>, std::shared_ptr<const std::vector<char>>> g_host_tables;
-std::vector<std::vector<double>> g_host_order;  // insertion order, for eviction
+std::deque<std::vector<double>> g_host_order;  // insertion order, for eviction
+size_t g_host_bytes = 0;
 
 std::shared_ptr<const std::vector<char>> host_table(const std::vector<double>& key, size_t bytes,
                                                     const std::function<void(char*)>& fill) {
@@ -415,11 +416,20 @@ std::shared_ptr<const std::vector<char>> host_table(const std::vector<double>& k
   auto v = std::make_shared<std::vector<char>>(bytes);
   fill(v->data());
   std::lock_guard<std::mutex> lk(g_host_mu);
-  if (g_host_tables.size() >= kMaxHostTables) {
-    g_host_tables.erase(g_host_order.front());
-    g_host_order.erase(g_host_order.begin());
+  // oldest entries out until the new one fits (contexts hold no reference: their
+  // device copies were made at upload)
+  while (!g_host_order.empty() && g_host_bytes + bytes > kMaxHostTableBytes) {
+    auto it = g_host_tables.find(g_host_order.front());
+    if (it != g_host_tables.end()) {
+      g_host_bytes -= it->second->size();
+      g_host_tables.erase(it);
+    }
+    g_host_order.pop_front();
   }
-  if (g_host_tables.emplace(key, v).second) g_host_order.push_back(key);
+  if (g_host_tables.emplace(key, v).second) {
+    g_host_order.push_back(key);
+    g_host_bytes += bytes;
+  }
   return v;
 }
 
@@ -502,7 +512,19 @@ class UploadRing {
 };
 #undef CHECK_CUDA_RET
 
-UploadRing g_ring;
+// One ring per device: a ring's events belong to the device current when they
+// were created, and are recorded on that device's streams.
+std::mutex g_ring_mu;
+std::map<int, std::unique_ptr<UploadRing>> g_rings;
+
+UploadRing* ring_of_current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_ring_mu);
+  auto& r = g_rings[dev];
+  if (!r) r = std::make_unique<UploadRing>();
+  return r.get();
+}
 
 // Pinned host buffers of cola_pk_async results ([3 * kMaxBins] doubles each),
 // recycled across contexts and never released: page-locked allocations and
@@ -540,7 +562,9 @@ class PinnedSlots {
 PinnedSlots g_pk_slots;
 
 int upload(cola_ctx* ctx, void* dst, const void* src, size_t bytes) {
-  CK(g_ring.copy(dst, src, bytes, ctx->st));
+  UploadRing* ring = ring_of_current_device();
+  if (!ring) return fail(ctx, COLA_ECUDA, "upload: no current device");
+  CK(ring->copy(dst, src, bytes, ctx->st));
   return COLA_OK;
 }
 
