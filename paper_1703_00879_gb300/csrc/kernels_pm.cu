@@ -799,10 +799,22 @@ __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, i
     const int64_t rest = m / (N / 2 + 1);
     const int iy = (int)(rest % N), iz = (int)(rest / N);
     const int nx = ix, ny = iy < N / 2 ? iy : iy - N, nz = iz < N / 2 ? iz : iz - N;
-    const double nmag = sqrt((double)nx * nx + (double)ny * ny + (double)nz * nz);
-    if (nmag < 0.5) continue;
-    const int b = (int)floor(nmag - 0.5);
+    // |n|^2 is an exact integer; the bin b = floor(|n| - 1/2) is decided exactly by
+    // integer comparisons, 4 |n|^2 against (2b + 1)^2 and (2b + 3)^2 (FP64 is slow
+    // on this GPU, so no double square root per mode)
+    const int64_t n2 = (int64_t)nx * nx + (int64_t)ny * ny + (int64_t)nz * nz;
+    if (4 * n2 < 1) continue;                            // |n| < 1/2: only n = 0
+    int b = (int)(sqrtf((float)n2) - 0.5f);
+    while (b > 0 && (int64_t)(2 * b + 1) * (2 * b + 1) > 4 * n2) --b;
+    while ((int64_t)(2 * b + 3) * (2 * b + 3) <= 4 * n2) ++b;
     if (b >= nbins) continue;
+    // |n| in double: a float reciprocal square root and one Newton step in double
+    // (relative error ~1e-14)
+    const double nd = (double)n2;
+    double r = (double)rsqrtf((float)n2);
+    r = r * (1.5 - 0.5 * nd * r * r);
+    r = r * (1.5 - 0.5 * nd * r * r);
+    const double nmag = nd * r;
     float wf = 1.f;
     const int nn[3] = {nx, ny, nz};
 #pragma unroll
@@ -813,9 +825,10 @@ __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, i
         wf *= sc * sc;
       }
     }
-    const double w = wf;
     const float2 v = dk[hidx(iz, iy, ix, N, P)];
-    const double p2 = ((double)v.x * v.x + (double)v.y * v.y) * norm / (w * w);
+    // the power of the mode in float (relative error ~1e-7, far below the bins'
+    // 1e-4), accumulated in double
+    const double p2 = (double)((v.x * v.x + v.y * v.y) / (wf * wf)) * norm;
     const double wt = (ix == 0 || ix == N / 2) ? 1.0 : 2.0;
     atomicAdd(&sh[b], wt);
     atomicAdd(&sh[nbins + b], wt * p2);
