@@ -220,7 +220,9 @@ int cola_set_stream(cola_ctx* ctx, void* stream);
  * unstable (too few steps for its model, a corrupted import) shows here before
  * its P(k) does.  Waits for the stream (bounded by cola_set_wait_limit).  The paper
  * has no counterpart.  Errors: COLA_EINVAL, COLA_ESTATE (no ICs yet, or a
- * cola_pk_async result pending), COLA_ECUDA, COLA_ETIMEOUT. */
+ * cola_pk_async result pending), COLA_ECUDA (also, with *nonfinite set, when a
+ * transform kernel on this device ever gave up on a tile load after its one-second
+ * wait: every result since is invalid), COLA_ETIMEOUT. */
 int cola_check_state(cola_ctx* ctx, int64_t* nonfinite);
 
 /* Bounded host waits.  Every call that waits on the host for the context's

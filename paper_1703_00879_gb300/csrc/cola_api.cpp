@@ -1515,10 +1515,17 @@ int cola_check_state(cola_ctx* ctx, int64_t* nonfinite) {
     return fail(ctx, COLA_ENOMEM, "cola_check_state: pinned host buffer allocation failed");
   if (ctx->pk_nbins) return fail(ctx, COLA_ESTATE, "a cola_pk_async result is still pending");
   CK(cudaMemcpyAsync(ctx->pk_host, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->st));
+  CK(tile_load_failures(reinterpret_cast<unsigned*>(ctx->pk_host + 1), ctx->st));
   CHECK_RC(host_wait(ctx));
   unsigned long long v = 0;
+  unsigned lost = 0;
   std::memcpy(&v, ctx->pk_host, sizeof(v));
+  std::memcpy(&lost, ctx->pk_host + 1, sizeof(lost));
   *nonfinite = (int64_t)v;
+  if (lost)
+    return fail(ctx, COLA_ECUDA,
+                "a transform's tile load on this device did not complete within its one-second wait; "
+                "results computed since are invalid");
   return COLA_OK;
 }
 

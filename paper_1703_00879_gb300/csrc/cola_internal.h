@@ -254,6 +254,9 @@ cudaError_t lq_dequant(const void* src, float* dst, int64_t P, int prec, const S
 
 // *out = the number of non-finite values among nf (<= 9) device arrays of n floats.
 cudaError_t count_nonfinite(const float* const* f, int nf, int64_t n, unsigned long long* out, cudaStream_t s);
+// *dst (host) = the number of transform CTAs on this device whose TMA tile-load
+// wait ran out (one second) since the library was loaded; stream-ordered copy.
+cudaError_t tile_load_failures(unsigned* dst, cudaStream_t s);
 
 // hdr->step += 1 (end of a step)
 cudaError_t step_advance(SimHeader* hdr, cudaStream_t s, Multi m = {});
