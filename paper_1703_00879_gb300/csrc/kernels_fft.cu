@@ -610,66 +610,127 @@ struct Yinv2rCfg {
   static constexpr bool ONE_CTA = blocks_for_smem(yinv2r_smem<N, TW>(), N) < 2;
 };
 
+// Both transforms of tile t from input buffer bi (the derivative into bd).
 template <int N, int TW>
+__device__ __forceinline__ void yinv2r_tile(const ColGeo<N, TW>& geo, float2* bi, float2* bd,
+                                            const float2* tw, float2* __restrict__ outp,
+                                            float2* __restrict__ outd, float kfs, int64_t t) {
+  int o, c0;
+  int64_t base, by;
+  geo.tile(t, o, c0, base, by);
+  const ColOut out{nullptr, geo.ra, geo.rb, N / 2 + 1 - c0};
+  ColOut od = out, op = out;
+  od.g = moved(outd, by) + base;
+  op.g = moved(outp, by) + base;
+  if constexpr (Yinv2rCfg<N, TW>::ONE_CTA) {
+    // one CTA per SM: the derivative transform runs first, its first step
+    // reading the input (times i kfs f_n) from bi, which the plain transform
+    // then overwrites; both store straight to HBM
+    fft_tile_call<N, TW, TW, NT, true, 1, DerivLoad<N>, ColOut>(bd, tw, DerivLoad<N>{bi, kfs}, od);
+    fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(bi, tw, TileLoad{}, op);
+  } else {
+    // two CTAs per SM (128 registers, where the load hook spills): a pass over the tile
+    const DerivLoad<N> dl{bi, kfs};
+    for (int e = threadIdx.x; e < N * TW; e += NT) bd[e] = dl(bd, e / TW, 0, e);
+    __syncthreads();
+    fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(bd, tw, TileLoad{}, od);
+    fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(bi, tw, TileLoad{}, op);
+  }
+}
+
+// TMA: buffer i's copies complete on barrier i (after the three buffers; the
+// failure flag follows), as in col_pipeline_tma.
+template <int N, int TW, bool TMA>
 __global__ void __launch_bounds__(NT, blocks_for_smem(yinv2r_smem<N, TW>(), N)) k_yinv2r(
     ColGeo<N, TW> geo, const float2* __restrict__ in, float2* __restrict__ outp,
-    float2* __restrict__ outd, float kfs, const float2* __restrict__ twg, int64_t ntiles) {
+    float2* __restrict__ outd, float kfs, const float2* __restrict__ twg, int64_t ntiles,
+    const __grid_constant__ CUtensorMap map) {
   constexpr int B = fft_rows<N>() * TW;
   extern __shared__ __align__(128) float2 sm[];
   float2* tw = sm;
-  load_tw(tw, twg, N);
-  int64_t t = blockIdx.x;
-  if (t < ntiles) {
-    int o, c0;
-    int64_t base, by;
-    geo.tile(t, o, c0, base, by);
-    col_issue<N, TW, TW>(sm + N, 0, moved(in, by), base, geo.ra, geo.rb, c0);
-  }
-  cp_async_commit();
-  int I = 0;
-  for (; t < ntiles; t += gridDim.x) {
-    const int D = I == 2 ? 0 : I + 1, F = I == 0 ? 2 : I - 1;
-    const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) {
+  auto buf = [&](int i) { return sm + N + i * B; };
+  if constexpr (TMA) {
+    static_assert((N * sizeof(float2)) % 128 == 0 && (B * sizeof(float2)) % 128 == 0,
+                  "TMA destinations 128-byte aligned");
+    uint64_t* bars = reinterpret_cast<uint64_t*>(buf(3));
+    int& fail = *reinterpret_cast<int*>(bars + 3);
+    const bool lead = threadIdx.x == 0;
+    if (lead) {
+      bar_init(&bars[0]);
+      bar_init(&bars[1]);
+      bar_init(&bars[2]);
+      fence_bar_init();
+      fail = (smem_u32(sm) & 127) ? 1 : 0;
+    }
+    load_tw(tw, twg, N);
+    __syncthreads();
+    if (fail) {
+      if (lead) atomicAdd(&g_tile_load_failures, 1u);
+      return;
+    }
+    uint32_t par = 0, pend = 0;  // thread 0: next phase parity and pending copies, bit i = barrier i
+    int64_t t = blockIdx.x;
+    if (lead && t < ntiles) {
+      tma_tile(geo, &map, buf(0), t, &bars[0]);
+      pend |= 1u;
+    }
+    int I = 0;
+    for (; t < ntiles; t += gridDim.x) {
+      const int D = I == 2 ? 0 : I + 1, F = I == 0 ? 2 : I - 1;
+      if (lead) {
+        fence_async_smem();
+        const int64_t tn = t + gridDim.x;
+        if (tn < ntiles) {
+          tma_tile(geo, &map, buf(F), tn, &bars[F]);
+          pend |= 1u << F;
+        }
+        if (bar_wait(&bars[I], (par >> I) & 1u)) {
+          par ^= 1u << I;
+          pend &= ~(1u << I);
+        } else {
+          fail = 1;
+        }
+      }
+      __syncthreads();
+      if (fail) break;
+      yinv2r_tile<N, TW>(geo, buf(I), buf(D), tw, outp, outd, kfs, t);
+      __syncthreads();  // both buffers are free for later prefetches
+      I = F;
+    }
+    if (lead && fail) {
+      atomicAdd(&g_tile_load_failures, 1u);
+      for (int i = 0; i < 3; ++i)
+        if ((pend >> i) & 1u) bar_wait(&bars[i], (par >> i) & 1u);
+    }
+  } else {
+    load_tw(tw, twg, N);
+    int64_t t = blockIdx.x;
+    if (t < ntiles) {
       int o, c0;
       int64_t base, by;
-      geo.tile(tn, o, c0, base, by);
-      col_issue<N, TW, TW>(sm + N + F * B, 0, moved(in, by), base, geo.ra, geo.rb, c0);
+      geo.tile(t, o, c0, base, by);
+      col_issue<N, TW, TW>(buf(0), 0, moved(in, by), base, geo.ra, geo.rb, c0);
     }
     cp_async_commit();
-    cp_async_wait<1>();  // tile t's input has landed
-    __syncthreads();
-    float2* bi = sm + N + I * B;
-    float2* bd = sm + N + D * B;
-    int o, c0;
-    int64_t base, by;
-    geo.tile(t, o, c0, base, by);
-    if constexpr (Yinv2rCfg<N, TW>::ONE_CTA) {
-      // one CTA per SM: the derivative transform runs first, its first step
-      // reading the input (times i kfs f_n) from bi, which the plain transform
-      // then overwrites; both store straight to HBM
-      const ColOut o{nullptr, geo.ra, geo.rb, N / 2 + 1 - c0};
-      ColOut od = o, op = o;
-      od.g = moved(outd, by) + base;
-      op.g = moved(outp, by) + base;
-      fft_tile_call<N, TW, TW, NT, true, 1, DerivLoad<N>, ColOut>(bd, tw, DerivLoad<N>{bi, kfs}, od);
-      fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(bi, tw, TileLoad{}, op);
-    } else {
-      // two CTAs per SM (128 registers, where the load hook spills): a pass over the tile
-      const DerivLoad<N> dl{bi, kfs};
-      for (int e = threadIdx.x; e < N * TW; e += NT) bd[e] = dl(bd, e / TW, 0, e);
+    int I = 0;
+    for (; t < ntiles; t += gridDim.x) {
+      const int D = I == 2 ? 0 : I + 1, F = I == 0 ? 2 : I - 1;
+      const int64_t tn = t + gridDim.x;
+      if (tn < ntiles) {
+        int o, c0;
+        int64_t base, by;
+        geo.tile(tn, o, c0, base, by);
+        col_issue<N, TW, TW>(buf(F), 0, moved(in, by), base, geo.ra, geo.rb, c0);
+      }
+      cp_async_commit();
+      cp_async_wait<1>();  // tile t's input has landed
       __syncthreads();
-      const ColOut o{nullptr, geo.ra, geo.rb, N / 2 + 1 - c0};
-      ColOut od = o, op = o;
-      od.g = moved(outd, by) + base;
-      op.g = moved(outp, by) + base;
-      fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(bd, tw, TileLoad{}, od);
-      fft_tile_call<N, TW, TW, NT, true, 1, TileLoad, ColOut>(bi, tw, TileLoad{}, op);
+      yinv2r_tile<N, TW>(geo, buf(I), buf(D), tw, outp, outd, kfs, t);
+      __syncthreads();  // both buffers are free for later prefetches
+      I = F;
     }
-    __syncthreads();  // both buffers are free for later prefetches
-    I = F;
+    cp_async_wait<0>();
   }
-  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- screening field (z pass)
@@ -1811,14 +1872,23 @@ static cudaError_t launch_yinv2(const float2* in, float2* outp, float2* outd, fl
   if constexpr (N >= 512) {
     // one pass with three rotating single-array tile buffers (k_yinv2r)
     constexpr int TW = col_tw(N, 1);
-    constexpr size_t sm = yinv2r_smem<N, TW>();
     const int64_t ntiles = col_tiles<N, TW>() * m.nb;
-    auto k = k_yinv2r<N, TW>;
-    unsigned grid;
-    cudaError_t e = prep(k, sm, ntiles, grid);
-    if (e != cudaSuccess) return e;
-    k<<<grid, NT, sm, s>>>(geo_y<N, TW>(m), in, outp, outd, kfs, tw, ntiles);
-    return cudaGetLastError();
+    CUtensorMap map{};
+    const bool tma = tma_shape<N, TW>() && !m.shift && spectrum_map(map, in, N, TW, false);
+    auto go = [&](auto tma_c) {
+      constexpr bool TMA = decltype(tma_c)::value;
+      constexpr size_t sm = yinv2r_smem<N, TW>() + (TMA ? 4 * sizeof(uint64_t) : 0);
+      auto k = k_yinv2r<N, TW, TMA>;
+      unsigned grid;
+      cudaError_t e = prep(k, sm, ntiles, grid);
+      if (e != cudaSuccess) return e;
+      k<<<grid, NT, sm, s>>>(geo_y<N, TW>(m), in, outp, outd, kfs, tw, ntiles, map);
+      return cudaGetLastError();
+    };
+    if constexpr (tma_shape<N, TW>()) {
+      if (tma) return go(std::true_type{});
+    }
+    return go(std::false_type{});
   } else {
     constexpr int TW = col_tw(N, 2);
     constexpr size_t sm = col_smem<N, 2>();
