@@ -11,6 +11,12 @@
 // table length T (host-computed in double precision, rounded to float); a
 // length-L transform reads it with stride T / L.  INV selects exp(+...) (the
 // unnormalised inverse).
+//
+// The in-register DFTs are radix-2 decimation in time (inputs in bit-reversed
+// positions, placed there at compile time by the loads; outputs in natural
+// order): a twiddled butterfly a +- w b is four fused multiply-adds for a + w b
+// and one per component for 2a - (a + w b), six instructions where a multiply
+// by w after a decimation-in-frequency subtraction takes eight.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -48,29 +54,6 @@ __device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2&
   v3 = csub(t1, t3);
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft8(float2* v) {
-  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
-  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
-  dft4<INV>(e0, e1, e2, e3);
-  dft4<INV>(o0, o1, o2, o3);
-  const float r = 0.70710678118654752440f;
-  // o1 *= w8, o2 *= w8^2, o3 *= w8^3 with w8 = exp(-/+ i pi/4)
-  o1 = INV ? make_float2((o1.x - o1.y) * r, (o1.x + o1.y) * r)
-           : make_float2((o1.x + o1.y) * r, (o1.y - o1.x) * r);
-  o2 = rot_q<INV>(o2);
-  o3 = INV ? make_float2((-o3.x - o3.y) * r, (o3.x - o3.y) * r)
-           : make_float2((o3.y - o3.x) * r, (-o3.x - o3.y) * r);
-  v[0] = cadd(e0, o0);
-  v[4] = csub(e0, o0);
-  v[1] = cadd(e1, o1);
-  v[5] = csub(e1, o1);
-  v[2] = cadd(e2, o2);
-  v[6] = csub(e2, o2);
-  v[3] = cadd(e3, o3);
-  v[7] = csub(e3, o3);
-}
-
 // cos(2 pi m / 32) for m = 0..8 (standard values; sin(2 pi m/32) = cos32(8 - m)).
 __host__ __device__ constexpr float cos32(int m) {
   return m == 0 ? 1.0f
@@ -95,16 +78,63 @@ __device__ __forceinline__ float2 w32mul(float2 a, int m) {
              : make_float2(a.x * c + a.y * s, a.y * c - a.x * s);
 }
 
+// Decimation-in-time butterfly (a, b) <- (a + w b, a - w b) with
+// w = exp(-/+ 2 pi i m / 32), m in [0, 16) a compile-time constant after
+// unrolling: m = 0 and 8 are additions, the others four FMAs for a + w b and
+// one FMA per component for 2a - (a + w b).
+template <bool INV>
+__device__ __forceinline__ void bfly_tw(float2& a, float2& b, int m) {
+  if (m == 0) {
+    dft2<INV>(a, b);
+    return;
+  }
+  if (m == 8) {
+    const float2 wb = rot_q<INV>(b), t = a;
+    a = cadd(t, wb);
+    b = csub(t, wb);
+    return;
+  }
+  const float c = m <= 8 ? cos32(m) : -cos32(16 - m);
+  const float s = m <= 8 ? cos32(8 - m) : cos32(m - 8);  // sin(2 pi m / 32) >= 0
+  // forward w b = (c br + s bi, c bi - s br); inverse (c br - s bi, c bi + s br)
+  const float sg = INV ? -s : s;
+  const float2 x = make_float2(fmaf(c, b.x, fmaf(sg, b.y, a.x)), fmaf(c, b.y, fmaf(-sg, b.x, a.y)));
+  b = make_float2(fmaf(2.f, a.x, -x.x), fmaf(2.f, a.y, -x.y));
+  a = x;
+}
+
+// 8-point DFT, natural order in and out: two 4-point DFTs of the even and odd
+// inputs and one decimation-in-time layer.
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  bfly_tw<INV>(e0, o0, 0);
+  bfly_tw<INV>(e1, o1, 4);
+  bfly_tw<INV>(e2, o2, 8);
+  bfly_tw<INV>(e3, o3, 12);
+  v[0] = e0;
+  v[1] = e1;
+  v[2] = e2;
+  v[3] = e3;
+  v[4] = o0;
+  v[5] = o1;
+  v[6] = o2;
+  v[7] = o3;
+}
+
 // In-register DFT of R = 2..32 points on the strided view v[0], v[S], ...,
 // v[(R-1)S], in place.  R <= 8: natural order.  R = 16, 32: radix-2
-// decimation-in-frequency butterflies, so output k sits at position
-// pos_of<R>(k) (resolved at compile time by the caller).
+// decimation in time, so input n must sit at position pos_of<R>(n) (placed
+// there at compile time by the caller) and output k ends at position k.
 template <int R>
-__host__ __device__ constexpr int pos_of(int k) {
+__host__ __device__ constexpr int pos_of(int n) {
   if constexpr (R <= 8) {
-    return k;
+    return n;
   } else {
-    return (k % 2 == 0) ? pos_of<R / 2>(k / 2) : R / 2 + pos_of<R / 2>((k - 1) / 2);
+    return (n % 2 == 0) ? pos_of<R / 2>(n / 2) : R / 2 + pos_of<R / 2>((n - 1) / 2);
   }
 }
 
@@ -129,14 +159,12 @@ __device__ __forceinline__ void dftR(float2* v) {
     dft8s<INV, S>(v);
   } else {
     static_assert(R == 16 || R == 32, "radix");
-#pragma unroll
-    for (int k = 0; k < R / 2; ++k) {
-      const float2 a = v[k * S], b = v[(k + R / 2) * S];
-      v[k * S] = cadd(a, b);
-      v[(k + R / 2) * S] = w32mul<INV>(csub(a, b), k * (32 / R));
-    }
+    // even inputs in the first half, odd in the second (pos_of), each half a
+    // DFT of R / 2 points in natural order, then one butterfly layer
     dftR<R / 2, INV, S>(v);
     dftR<R / 2, INV, S>(v + (R / 2) * S);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) bfly_tw<INV>(v[k * S], v[(k + R / 2) * S], k * (32 / R));
   }
 }
 
@@ -144,19 +172,22 @@ __device__ __forceinline__ void dftR(float2* v) {
 // the thread with half = 0 holds x[0..15] in v, its partner x[16..31].  One
 // radix-2 decimation-in-frequency step exchanges the halves by shuffle (half 0
 // forms a[n] = x[n] + x[n + 16], half 1 b[n] = (x[n] - x[n + 16]) w32^n), then
-// each runs a 16-point DFT: half h ends with X[2k + h] at v[pos_of<16>(k)].
+// each runs a 16-point DFT: half h ends with X[2k + h] at v[k].
 template <bool INV>
 __device__ __forceinline__ void dft32_pair(float2 (&v)[16], int half) {
   const float sg = half ? -1.f : 1.f;
+  float2 u[16];
 #pragma unroll
   for (int n = 0; n < 16; ++n) {
     const float ox = __shfl_xor_sync(0xffffffffu, v[n].x, 16);
     const float oy = __shfl_xor_sync(0xffffffffu, v[n].y, 16);
     const float2 t = make_float2(fmaf(sg, v[n].x, ox), fmaf(sg, v[n].y, oy));
     const float2 tw = w32mul<INV>(t, n);
-    v[n] = half ? tw : t;
+    u[pos_of<16>(n)] = half ? tw : t;
   }
-  dftR<16, INV>(v);
+  dftR<16, INV>(u);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = u[k];
 }
 
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
@@ -220,14 +251,15 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
       if ((U1 % NT) == 0 || u < U1) {
         const int c = u % TW, n2 = u / TW;
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) v[i][n1] = ld(buf, R2 * n1 + n2, c, (R2 * n1 + n2) * PITCH + c);
+        for (int n1 = 0; n1 < R1; ++n1)
+          v[i][pos_of<R1>(n1)] = ld(buf, R2 * n1 + n2, c, (R2 * n1 + n2) * PITCH + c);
         dftR<R1, INV>(v[i]);
         if (n2 > 0) {
 #pragma unroll
           for (int k1 = 1; k1 < R1; ++k1) {
             float2 w = tw[n2 * k1 * TWS];
             if (INV) w.y = -w.y;
-            v[i][pos_of<R1>(k1)] = cmul(v[i][pos_of<R1>(k1)], w);
+            v[i][k1] = cmul(v[i][k1], w);
           }
         }
       }
@@ -240,7 +272,7 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
         const int c = u % TW, n2 = u / TW;
         float2* y = buf + n2 * (R1 + 1) * PITCH + c;
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) y[k1 * PITCH] = v[i][pos_of<R1>(k1)];
+        for (int k1 = 0; k1 < R1; ++k1) y[k1 * PITCH] = v[i][k1];
       }
     }
   }
@@ -255,7 +287,7 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
         const int c = u % TW, k1 = u / TW;
         const float2* yr = buf + k1 * PITCH + c;
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) y[i][n2] = yr[n2 * (R1 + 1) * PITCH];
+        for (int n2 = 0; n2 < R2; ++n2) y[i][pos_of<R2>(n2)] = yr[n2 * (R1 + 1) * PITCH];
         dftR<R2, INV>(y[i]);
       }
     }
@@ -268,7 +300,7 @@ __device__ __forceinline__ void fft_tile(float2* __restrict__ buf, const float2*
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) {
           const int n = k1 + R1 * k2;
-          const float2 o = st(y[i][pos_of<R2>(k2)], n, c, n * PITCH + c);
+          const float2 o = st(y[i][k2], n, c, n * PITCH + c);
           if constexpr (Store::kSmem) buf[n * PITCH + c] = o;
         }
       }
@@ -326,14 +358,14 @@ __device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const floa
         const int c = u / R2, n2 = u % R2;
         const float2* x = buf + c * CW + n2;
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) v[i][n1] = pre(x[R2 * n1], c, R2 * n1 + n2);
+        for (int n1 = 0; n1 < R1; ++n1) v[i][pos_of<R1>(n1)] = pre(x[R2 * n1], c, R2 * n1 + n2);
         dftR<R1, INV>(v[i]);
         if (n2 > 0) {
 #pragma unroll
           for (int k1 = 1; k1 < R1; ++k1) {
             float2 w = tw[n2 * k1 * TWS];
             if (INV) w.y = -w.y;
-            v[i][pos_of<R1>(k1)] = cmul(v[i][pos_of<R1>(k1)], w);
+            v[i][k1] = cmul(v[i][k1], w);
           }
         }
       }
@@ -346,7 +378,7 @@ __device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const floa
         const int c = u / R2, n2 = u % R2;
         float2* y = buf + c * CW + n2 * (R1 + 1);
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) y[k1] = v[i][pos_of<R1>(k1)];
+        for (int k1 = 0; k1 < R1; ++k1) y[k1] = v[i][k1];
       }
     }
   }
@@ -365,7 +397,7 @@ __device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const floa
     float2* X = buf + c * CW + k1 + R1 * half;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      const float2 o = st(y[pos_of<16>(k)], c, k1 + R1 * (2 * k + half));
+      const float2 o = st(y[k], c, k1 + R1 * (2 * k + half));
       if constexpr (Store::kSmem) X[2 * R1 * k] = o;
     }
   } else {
@@ -377,7 +409,7 @@ __device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const floa
         const int c = u / R1, k1 = u % R1;
         const float2* yr = buf + c * CW + k1;
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) y[i][n2] = yr[n2 * (R1 + 1)];
+        for (int n2 = 0; n2 < R2; ++n2) y[i][pos_of<R2>(n2)] = yr[n2 * (R1 + 1)];
         dftR<R2, INV>(y[i]);
       }
     }
@@ -390,7 +422,7 @@ __device__ __forceinline__ void fft_rowtile(float2* __restrict__ buf, const floa
         float2* X = buf + c * CW + k1;
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) {
-          const float2 o = st(y[i][pos_of<R2>(k2)], c, k1 + R1 * k2);
+          const float2 o = st(y[i][k2], c, k1 + R1 * k2);
           if constexpr (Store::kSmem) X[R1 * k2] = o;
         }
       }
