@@ -984,7 +984,8 @@ int ic_group(const Group& g, bool potentials) {
   if (!potentials) {
     CK(ic_noise(N, ctx->cfg.seed, ctx->lr[0], st, m, ctx->hdr));
     CHECK_RC(r2c3(ctx, N, ctx->lr[0], ctx->phi[0], ctx->tw_np, 1.f, 0.f, m));
-    CK(ic_phi1(N, ctx->phi[0], kf, eh_dev(ctx), st, m, ctx->hdr));
+    // lr[1] is free until the Hessians: the per-|n|^2 factor table
+    CK(ic_phi1(N, ctx->phi[0], kf, eh_dev(ctx), reinterpret_cast<double*>(ctx->lr[1]), st, m, ctx->hdr));
     const int ij[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
     for (int h = 0; h < 6; ++h) {
       CK(ic_hessian(N, ctx->phi[0], ctx->lc[0], ij[h][0], ij[h][1], kf, st, m));

@@ -289,8 +289,9 @@ cudaError_t pk_bin(int N, const float2* dk, int nbins, double* acc, double norm,
 cudaError_t ic_noise(int N, uint64_t seed, float* out, cudaStream_t s, Multi m = {},
                      const SimHeader* hdr = nullptr);
 // delta(k) = G(k) sqrt(P(k) N^3/L^3); phi1 = delta/k^2 (k = 0 -> 0), in place on c.
-cudaError_t ic_phi1(int N, float2* c, float kf, const EHDev& eh, cudaStream_t s, Multi m = {},
-                    const SimHeader* hdr = nullptr);
+// work: device scratch of 3 (N/2)^2 + 1 doubles per simulation (the factor per |n|^2).
+cudaError_t ic_phi1(int N, float2* c, float kf, const EHDev& eh, double* work, cudaStream_t s,
+                    Multi m = {}, const SimHeader* hdr = nullptr);
 // out = -k_i k_j / N^3 * phi1 with the Nyquist rule for i != j.
 cudaError_t ic_hessian(int N, const float2* phi1, float2* out, int i, int j, float kf,
                        cudaStream_t s, Multi m = {});

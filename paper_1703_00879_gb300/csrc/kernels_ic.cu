@@ -34,7 +34,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 
 // Unit Gaussian per lattice point: counter (idx lo, idx hi, 0, 0), key = seed,
-// u_i = (w_i + 1/2) / 2^32, g = sqrt(-2 ln u1) cos(2 pi u2) in double precision.
+// u_i = (w_i + 1/2) / 2^32, g = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller) in
+// single precision: ln u1 from u1 itself below 1/2 and as ln(1 - v) with
+// v = (2^32 - 1 - w_1 + 1/2) / 2^32 above, so that every u1 keeps its relative
+// precision; the result is within a few ulp of the double-precision formula
+// rounded to float (this GPU's double-precision rate made the double version
+// 15 ms for 512^3 points).
 // Multi-simulation kernels take the simulation from blockIdx.y and move every
 // buffer pointer by its shift; per-simulation values come from the header.
 __global__ void k_noise(int64_t n, uint32_t k0, uint32_t k1, float* __restrict__ out,
@@ -49,9 +54,9 @@ __global__ void k_noise(int64_t n, uint32_t k0, uint32_t k1, float* __restrict__
     k1 = (uint32_t)(sd >> 32);
   }
   const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 0u, 0u), k0, k1);
-  const double u1 = ((double)r.x + 0.5) * (1.0 / 4294967296.0);
-  const double u2 = ((double)r.y + 0.5) * (1.0 / 4294967296.0);
-  out[i] = (float)(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
+  const float lu = r.x < 0x80000000u ? logf(((float)r.x + 0.5f) * 0x1p-32f)
+                                      : log1pf(-((float)(0xFFFFFFFFu - r.x) + 0.5f) * 0x1p-32f);
+  out[i] = sqrtf(-2.f * lu) * cospif(((float)r.y + 0.5f) * 0x1p-31f);  // cos(pi * 2 u2)
 }
 
 struct Mode {
@@ -89,26 +94,39 @@ __device__ double eh_T(const EHDev& e, double k) {
   return L0 / (L0 + C0 * q * q);
 }
 
-__global__ void k_ic_phi1(int N, int64_t P, float2* __restrict__ c, float kf, EHDev eh,
-                          const SimHeader* __restrict__ hdr, Multi mm) {
+// The factor of phi1(k) = f(|n|^2) delta(k) (Sec. 3.1), f = sqrt(P(k) N^3 / L^3) / k^2
+// with k = kf |n|, depends on the integer |n|^2 only: one double-precision
+// evaluation per value 0 .. 3 (N/2)^2 into tab (each simulation its own table)
+// instead of one per mode.
+__global__ void k_ic_amp(int N, double* __restrict__ tab, float kf, EHDev eh,
+                         const SimHeader* __restrict__ hdr, Multi mm) {
+  const int64_t q = (int64_t)blockIdx.x * NTI + threadIdx.x;
+  if (q > 3LL * (N / 2) * (N / 2)) return;
+  const int64_t by = shift_of(mm, blockIdx.y);
+  tab = moved(tab, by);
+  if (hdr) eh = moved(hdr, by)->eh;
+  if (q == 0) {
+    tab[0] = 0.0;
+    return;
+  }
+  const double k = (double)kf * sqrt((double)q);
+  const double T = eh_T(eh, k);
+  const double pk = eh.amp * pow(k, eh.ns) * T * T;
+  tab[q] = sqrt(pk * eh.N3_over_L3) / (k * k);
+}
+
+__global__ void k_ic_phi1(int N, int64_t P, float2* __restrict__ c, const double* __restrict__ tab,
+                          Multi mm) {
   const int64_t m = (int64_t)blockIdx.x * NTI + threadIdx.x;
   if (m >= (int64_t)N * N * P) return;
   const int64_t by = shift_of(mm, blockIdx.y);
   c = moved(c, by);
-  if (hdr) eh = moved(hdr, by)->eh;
+  tab = moved(tab, by);
   bool valid;
   const Mode md = mode_of(m, N, P, valid);
   if (!valid) return;
-  const double n2 = (double)md.ix * md.ix + (double)md.fy * md.fy + (double)md.fz * md.fz;
-  float2 v = c[m];
-  if (n2 == 0.0) {
-    c[m] = make_float2(0.f, 0.f);
-    return;
-  }
-  const double k = (double)kf * sqrt(n2);
-  const double T = eh_T(eh, k);
-  const double pk = eh.amp * pow(k, eh.ns) * T * T;
-  const double f = sqrt(pk * eh.N3_over_L3) / (k * k);
+  const double f = tab[md.ix * md.ix + md.fy * md.fy + md.fz * md.fz];  // 0 at k = 0
+  const float2 v = c[m];
   c[m] = make_float2((float)(v.x * f), (float)(v.y * f));
 }
 
@@ -259,10 +277,12 @@ cudaError_t ic_noise(int N, uint64_t seed, float* out, cudaStream_t s, Multi m, 
   return cudaGetLastError();
 }
 
-cudaError_t ic_phi1(int N, float2* c, float kf, const EHDev& eh, cudaStream_t s, Multi m,
+cudaError_t ic_phi1(int N, float2* c, float kf, const EHDev& eh, double* work, cudaStream_t s, Multi m,
                     const SimHeader* hdr) {
+  const int64_t nq = 3LL * (N / 2) * (N / 2) + 1;
+  k_ic_amp<<<dim3(blocks_for(nq), m.nb), NTI, 0, s>>>(N, work, kf, eh, hdr, m);
   const int64_t n = half_elems(N);
-  k_ic_phi1<<<dim3(blocks_for(n), m.nb), NTI, 0, s>>>(N, half_pitch(N), c, kf, eh, hdr, m);
+  k_ic_phi1<<<dim3(blocks_for(n), m.nb), NTI, 0, s>>>(N, half_pitch(N), c, work, m);
   return cudaGetLastError();
 }
 
