@@ -300,11 +300,19 @@ class Simulation:
     def steps_done(self) -> int:
         return lib().cola_steps_done(self.ctx)
 
-    def snapshot(self, pos=True, vel=True):
-        """(positions [P,3], velocities [P,3]) as numpy float32 (host buffers)."""
+    def snapshot(self, pos=True, vel=True, out=None):
+        """(positions [P,3], velocities [P,3]) as numpy float32 (host buffers).  out: a pair of
+        C-contiguous float32 [P,3] arrays to fill instead (page-locked ones copy fastest)."""
         P = self.P
-        p = np.empty((P, 3), np.float32) if pos else None
-        v = np.empty((P, 3), np.float32) if vel else None
+        if out is not None:
+            for a in out:
+                if a is not None and (a.dtype != np.float32 or a.shape != (P, 3) or not a.flags.c_contiguous):
+                    raise ValueError("snapshot out arrays must be C-contiguous float32 [P, 3]")
+            p, v = (out[0] if pos else None), (out[1] if vel else None)
+            pos, vel = p is not None, v is not None
+        else:
+            p = np.empty((P, 3), np.float32) if pos else None
+            v = np.empty((P, 3), np.float32) if vel else None
         _check(lib().cola_snapshot(self.ctx, p.ctypes.data if pos else None,
                                    v.ctypes.data if vel else None, COLA_HOST), self.ctx)
         return p, v

@@ -1051,7 +1051,12 @@ int finish_ic(cola_ctx* ctx, bool potentials) {
 // copies without a wait limit go through the download ring, the rest through
 // cudaMemcpyAsync and a (bounded) wait.
 int copy_to_host(cola_ctx* ctx, void* dst, const void* src, size_t bytes) {
-  if (bytes >= ((size_t)64 << 20) && !(ctx->wait_limit_s > 0)) {
+  // page-locked destinations take the copy engine straight; large pageable ones go
+  // through the pinned download ring
+  cudaPointerAttributes at{};
+  const bool pinned = cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeHost;
+  if (!pinned) cudaGetLastError();
+  if (!pinned && bytes >= ((size_t)64 << 20) && !(ctx->wait_limit_s > 0)) {
     DownloadRing* r = download_ring();
     if (!r) return fail(ctx, COLA_ECUDA, "no current device");
     CK(r->copy(dst, src, bytes, ctx->st));

@@ -729,18 +729,21 @@ __global__ void __launch_bounds__(NTP) k_snapshot(
     const float* __restrict__ sz, const float* __restrict__ vx, const float* __restrict__ vy,
     const float* __restrict__ vz, const float* __restrict__ lx, const float* __restrict__ ly,
     const float* __restrict__ lz, float vscale, float* __restrict__ pos,
-    float* __restrict__ vel, int64_t P, LptMix mix) {
+    float* __restrict__ vel, int64_t P, LptMix mix, double dq, double invL) {
   const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
   if (p >= P) return;
   int li[3];
   lattice(pp, p, li[0], li[1], li[2]);
   const float sv[3] = {sx[p], sy[p], sz[p]};
   if (pos) {
+    // x = q + s wrapped into [0, L) in double precision; dq = L / Np and 1/L come from
+    // the host (no double division per particle: this GPU's double rate is low)
     const double L = pp.L;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      double x = (double)li[d] * (L / pp.Np) + (double)sv[d];
-      x -= L * floor(x / L);
+      double x = (double)li[d] * dq + (double)sv[d];
+      x -= L * floor(x * invL);
+      if (x < 0.0) x += L;
       if (x >= L) x -= L;
       pos[p * 3 + d] = (float)x;
     }
@@ -999,8 +1002,9 @@ cudaError_t part_snapshot(const PartParams& pp, const float* sx, const float* sy
                           const float* vx, const float* vy, const float* vz, const float* lx,
                           const float* ly, const float* lz, float vscale, float* pos, float* vel,
                           int64_t P, cudaStream_t s, LptMix mix) {
+  const double L = pp.L;
   k_snapshot<<<blocks_for(P), NTP, 0, s>>>(pp, sx, sy, sz, vx, vy, vz, lx, ly, lz, vscale, pos,
-                                           vel, P, mix);
+                                           vel, P, mix, L / pp.Np, 1.0 / L);
   return cudaGetLastError();
 }
 

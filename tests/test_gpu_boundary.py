@@ -232,3 +232,21 @@ def test_check_state_counts_non_finite_values(pkg):
         v[2, 7] = np.inf
         s.import_state(d, v, a, steps_done=2)
         assert s.check_state() == 2
+
+
+def test_snapshot_into_page_locked_buffers(pkg):
+    """A snapshot into caller-owned page-locked buffers (direct DMA) equals the pageable one
+    (staged through the download ring above 64 MB, plain copy below), at a size on each side."""
+    import torch
+    for run in (SMALL_F5.with_(nsteps=2), SMALL_F5.with_(Np=256, Nmesh=256, Lbox=256.0, nsteps=2)):
+        with pkg.Simulation(run) as s:
+            s.step(1)
+            p0, v0 = s.snapshot()
+            P = run.Np ** 3
+            out = tuple(torch.empty((P, 3), dtype=torch.float32, pin_memory=True).numpy() for _ in range(2))
+            p1, v1 = s.snapshot(out=out)
+            assert p1 is out[0] and v1 is out[1]
+            np.testing.assert_array_equal(p1, p0)
+            np.testing.assert_array_equal(v1, v0)
+            with pytest.raises(ValueError):
+                s.snapshot(out=(np.empty((P, 3), np.float64), None))
