@@ -238,6 +238,17 @@ int cola_check_state(cola_ctx* ctx, int64_t* nonfinite);
 int cola_set_wait_limit(cola_ctx* ctx, double seconds);
 int cola_wait(cola_ctx* ctx);
 
+/* Self-test of the one wait on the device.  The transform passes that stage their
+ * tiles with TMA wait on an mbarrier for each tile's copies, for one second at
+ * most; a CTA whose wait runs out is counted and stops, and cola_check_state
+ * reports COLA_ECUDA.  This call runs that wait, with limit `seconds`
+ * (0 < seconds <= 10), on a barrier phase that no copy completes, on the current
+ * device's per-thread default stream, and waits for it: *timed_out = 1 when the
+ * wait gave up (the expected result), 0 otherwise.  Nothing is allocated and no
+ * context is needed.  Errors: COLA_EINVAL (limit out of range, NULL timed_out),
+ * COLA_ECUDA. */
+int cola_selftest_wait(double seconds, int* timed_out);
+
 /* Current scale factor (NaN for a NULL context) and completed steps. */
 double cola_scale_factor(const cola_ctx* ctx);
 int32_t cola_steps_done(const cola_ctx* ctx);

@@ -101,6 +101,7 @@ _SIGS = {
     "cola_pk_result": (ctypes.c_int, [_P, _P, _P, _P]),
     "cola_set_stream": (ctypes.c_int, [_P, _P]),
     "cola_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_double]),
+    "cola_selftest_wait": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
     "cola_check_state": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "cola_wait": (ctypes.c_int, [_P]),
     "cola_batch_steps_done": (ctypes.c_int32, [_P]),
@@ -141,6 +142,14 @@ def _check(rc: int, ctx=None):
     if rc != COLA_OK:
         msg = lib().cola_last_error(ctx)
         raise ColaError(rc, msg.decode() if msg else "")
+
+
+def selftest_wait(seconds: float) -> bool:
+    """Runs the transform kernels' bounded device wait on a barrier phase that never completes
+    (cola_selftest_wait); True when it gave up within its limit."""
+    out = ctypes.c_int(-1)
+    _check(lib().cola_selftest_wait(float(seconds), ctypes.byref(out)))
+    return out.value == 1
 
 
 def make_config(run) -> cola_config:

@@ -1547,6 +1547,14 @@ int cola_wait(cola_ctx* ctx) {
   return host_wait(ctx);
 }
 
+int cola_selftest_wait(double seconds, int* timed_out) {
+  if (!timed_out) return fail(nullptr, COLA_EINVAL, "timed_out is NULL");
+  if (!(seconds > 0) || seconds > 10) return fail(nullptr, COLA_EINVAL, "limit out of range (0, 10] s");
+  const cudaError_t e = wait_probe(seconds, timed_out);
+  if (e != cudaSuccess) return fail(nullptr, COLA_ECUDA, std::string("cola_selftest_wait: ") + cudaGetErrorString(e));
+  return COLA_OK;
+}
+
 int cola_set_stream(cola_ctx* ctx, void* stream) {
   if (!ctx) return fail(nullptr, COLA_EINVAL, "ctx is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);

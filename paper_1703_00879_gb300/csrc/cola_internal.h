@@ -257,6 +257,9 @@ cudaError_t count_nonfinite(const float* const* f, int nf, int64_t n, unsigned l
 // *dst (host) = the number of transform CTAs on this device whose TMA tile-load
 // wait ran out (one second) since the library was loaded; stream-ordered copy.
 cudaError_t tile_load_failures(unsigned* dst, cudaStream_t s);
+// Runs the transform kernels' bounded mbarrier wait on a phase that never completes
+// (limit `seconds`, 0 < seconds <= 10, on the per-thread default stream; waits for it); *timed_out = 1 when it gave up.
+cudaError_t wait_probe(double seconds, int* timed_out);
 
 // hdr->step += 1 (end of a step)
 cudaError_t step_advance(SimHeader* hdr, cudaStream_t s, Multi m = {});

@@ -350,12 +350,13 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for phase `parity` of b to complete, for one second at most.
-__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
+// Wait for phase `parity` of b to complete, for limit_ns (one second) at most.
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity,
+                                         uint64_t limit_ns = 1000000000ull) {
   if (bar_try(b, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!bar_try(b, parity))
-    if (global_ns() - t0 > 1000000000ull) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
 }
 // orders this CTA's earlier generic-proxy accesses to shared memory before
@@ -489,6 +490,19 @@ __device__ __forceinline__ void col_pipeline_tma(Op op, const float2* __restrict
     for (int i = 0; i < 3; ++i)
       if ((pend >> i) & 1u) bar_wait(&bars[i], (par >> i) & 1u);  // bounded: copies in flight land before exit
   }
+}
+
+// Self-test of the bounded wait: one thread arms a barrier phase for 16 bytes
+// that no copy will deliver and waits on it with bar_wait; g_wait_probe = 1 when
+// the wait gave up after limit_ns, 0 if the phase completed.
+__device__ int g_wait_probe;
+__global__ void k_wait_probe(uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  bar_init(&bar);
+  fence_bar_init();
+  bar_expect(&bar, 16);
+  g_wait_probe = bar_wait(&bar, 0, limit_ns) ? 0 : 1;
 }
 
 // ---------------------------------------------------------------- plain column pass
@@ -2063,6 +2077,17 @@ cudaError_t lpt_z(int Nv, const void* phi1, const void* phi2, float2* o0, float2
   if (Nv > 512) return cudaErrorInvalidValue;  // four double-buffered 4-column tiles exceed shared memory
   COLA_SWITCH_N(Nv, return launch_lpt<N>(phi1, phi2, o0, o1, o2, o3, lp, tw, s, m));
   return cudaSuccess;
+}
+
+cudaError_t wait_probe(double seconds, int* timed_out) {
+  if (!(seconds > 0) || seconds > 10) return cudaErrorInvalidValue;
+  k_wait_probe<<<1, 32, 0, cudaStreamPerThread>>>((uint64_t)(seconds * 1e9));
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyFromSymbolAsync(timed_out, g_wait_probe, sizeof(int), 0, cudaMemcpyDeviceToHost,
+                                  cudaStreamPerThread);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamPerThread);
+  return e;
 }
 
 cudaError_t tile_load_failures(unsigned* dst, cudaStream_t s) {

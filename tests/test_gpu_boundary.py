@@ -250,3 +250,18 @@ def test_snapshot_into_page_locked_buffers(pkg):
             np.testing.assert_array_equal(v1, v0)
             with pytest.raises(ValueError):
                 s.snapshot(out=(np.empty((P, 3), np.float64), None))
+
+
+def test_device_wait_gives_up_at_its_limit(pkg):
+    """The one wait on the device (a TMA-staged transform's mbarrier wait for its tile) is bounded:
+    on a barrier phase that no copy completes it gives up after its limit and reports it, and the
+    device stays usable (a step runs afterwards)."""
+    t0 = time.perf_counter()
+    assert pkg.selftest_wait(0.02) is True
+    dt = time.perf_counter() - t0
+    assert 0.02 <= dt < 5.0
+    with pytest.raises(pkg.ColaError):
+        pkg.selftest_wait(0.0)
+    with pkg.Simulation(SMALL_F5.with_(nsteps=2)) as s:
+        s.step(1)
+        assert s.check_state() == 0
