@@ -777,7 +777,8 @@ int c2r3(cola_ctx* ctx, int N, float2* in, float* out, const float2* tw, Multi m
 // Sec. 4.1 / App. A: LPT fields at the lattice from the k-space seeds and one
 // row of table `vel` (0 displacement/acceleration, 1 velocity): row0, plus the
 // device step counter when add_step; over m's simulations (ctx is the first).
-int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}) {
+int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}, float* zero_dst = nullptr,
+            int64_t zero_floats = 0, bool* zeroed = nullptr) {
   LptParams lp{};
   lp.hdr = ctx->hdr;
   lp.vel = vel;
@@ -797,8 +798,11 @@ int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}) {
   const double H = (double)N * N * (N / 2 + 1) * 8.0, R = (double)N * N * N * 4.0;
   const double seedH = H * (lp.seed_prec ? 0.5 : 1.0);
   cudaEvent_t e = prof_begin(ctx, ST_LPT_Z);
-  CK(lpt_z(N, p1, p2, ctx->lc[0], ctx->lc[1], ctx->lc[2], ctx->lc[3], lp, ctx->tw_np, st, m));
-  prof_end(ctx, ST_LPT_Z, e, 1, m.nb * (2 * seedH + 4 * H));
+  bool zd = false;
+  CK(lpt_z(N, p1, p2, ctx->lc[0], ctx->lc[1], ctx->lc[2], ctx->lc[3], lp, ctx->tw_np, st, m, zero_dst,
+           zero_floats, &zd));
+  if (zeroed) *zeroed = zd;
+  prof_end(ctx, ST_LPT_Z, e, 1, m.nb * (2 * seedH + 4 * H + (zd ? 4.0 * (double)zero_floats : 0.0)));
   e = prof_begin(ctx, ST_LPT_Y);
   CK(fft_yinv2(N, ctx->lc[0], ctx->lc[0], ctx->lc[4], kf, ctx->tw_np, st, m));
   CK(fft_col(N, ctx->lc[1], 1, true, ctx->tw_np, st, m));
@@ -1104,7 +1108,9 @@ int enqueue_group_step(const Group& g, int n) {
   // the particle kernels (row 1 + step), no LPT transforms
   const bool fast = ctx->lpt_fast;
   const LptMix mix = fast ? lpt_mix_of(ctx, 1, 1, false) : LptMix{};
-  if (!fast) CHECK_RC(run_lpt(ctx, 0, 1, true, m));
+  // the density zero fill rides on the LPT z pass where that pass can take it
+  bool rho_zeroed = false;
+  if (!fast) CHECK_RC(run_lpt(ctx, 0, 1, true, m, ctx->rho, ctx->M, &rho_zeroed));
   // variant a.S1: the drift and kick read the 16-bit fields
   const int lq = (!fast && ctx->cfg.seed_precision) ? ctx->cfg.seed_precision : 0;
   StepDt dt = dt0;
@@ -1116,9 +1122,12 @@ int enqueue_group_step(const Group& g, int n) {
       ld[d] = reinterpret_cast<const float*>(ctx->lq[d]);
       lk[d] = reinterpret_cast<const float*>(ctx->lq[3 + d]);
     }
-  cudaEvent_t e = prof_begin(ctx, ST_RHO_ZERO);
-  CK(zero_f32(ctx->rho, ctx->M, ctx->st, m));
-  prof_end(ctx, ST_RHO_ZERO, e, 1, m.nb * 4.0 * Mb);
+  cudaEvent_t e = nullptr;
+  if (!rho_zeroed) {
+    e = prof_begin(ctx, ST_RHO_ZERO);
+    CK(zero_f32(ctx->rho, ctx->M, ctx->st, m));
+    prof_end(ctx, ST_RHO_ZERO, e, 1, m.nb * 4.0 * Mb);
+  }
   e = prof_begin(ctx, ST_DRIFT_DEPOSIT);
   CK(part_drift_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                         ctx->acc[0], ctx->acc[1], ctx->acc[2], ld[0], ld[1], ld[2], ctx->rho, dt,

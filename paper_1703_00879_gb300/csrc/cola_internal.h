@@ -190,9 +190,13 @@ cudaError_t mesh_z_force(int N, const float2* in, const float2* dk, float2* phi_
 // LPT: phi1, phi2 -> (c1 phi1 + c2 phi2), i kz (...), (e1 phi1 + e2 phi2), i kz (...),
 // each inverse-transformed along z.  phi1/phi2 point to float2 (fp32) or
 // 2 x 16-bit pairs (bf16/fp16) according to lp.seed_prec.
+// zero_dst: optionally also zero zero_floats floats at zero_dst (each simulation's, moved by
+// its shift) in the same launch, by bulk stores riding on the pass; *zeroed = whether it did
+// (it does where the pass runs one CTA per SM, N >= 512 on 4-column tiles).
 cudaError_t lpt_z(int N, const void* phi1, const void* phi2, float2* o0, float2* o1, float2* o2,
                   float2* o3, const LptParams& lp, const float2* tw, cudaStream_t s,
-                  Multi m = {});
+                  Multi m = {}, float* zero_dst = nullptr, int64_t zero_floats = 0,
+                  bool* zeroed = nullptr);
 
 // ------------------------------------------------------------------ particles
 cudaError_t part_deposit(const PartParams& pp, const float* sx, const float* sy, const float* sz,

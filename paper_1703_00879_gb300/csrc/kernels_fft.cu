@@ -386,6 +386,22 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       : "memory");
 }
 
+// Zero fill by bulk stores from a zeroed shared-memory region (thread 0): `bytes`
+// (a multiple of 16) at dst, in pieces of at most ZB bytes, one bulk group; at
+// most eight groups stay outstanding (the region is never written again, so
+// only the count is bounded).
+__device__ __forceinline__ void bulk_zero(char* dst, int64_t bytes, const void* zeros, uint32_t ZB) {
+  for (int64_t o = 0; o < bytes; o += ZB) {
+    const uint32_t len = (uint32_t)(bytes - o < (int64_t)ZB ? bytes - o : (int64_t)ZB);
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst + o),
+                 "r"(smem_u32(zeros)), "r"(len)
+                 : "memory");
+  }
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 8;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_store_drain() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
 // Issue the loads of column tile t of `geo` into buf (thread 0; buf 128-byte aligned).
 template <int N, int TW>
 __device__ __forceinline__ void tma_tile(const ColGeo<N, TW>& geo, const CUtensorMap* map, float2* buf,
@@ -989,7 +1005,13 @@ struct OpLptZ {
   float2 *o0, *o1, *o2, *o3;
   LptParams lp;
   int tab_smem;             // 1: the (single) table row is staged in extra once per CTA
+  // zero fill riding on this issue-bound pass: each tile clears its share (zchunk bytes)
+  // of zdst (zbytes per simulation, moved by the simulation's shift), by bulk stores
+  // from a zeroed 16 KB region after the table row; nullptr: none
+  char* zdst = nullptr;
+  int64_t zbytes = 0, zchunk = 0;
   float2* extra = nullptr;  // scratch after the stage buffers (set by col_pipeline)
+  static constexpr uint32_t kZero = 16384;
   __device__ __forceinline__ void issue_side(int64_t) const {}
   __device__ __forceinline__ void issue(float2* buf, int64_t t) const {
     int o, c0;
@@ -1020,6 +1042,19 @@ struct OpLptZ {
         __syncthreads();
       }
       tab = st;
+    }
+    if (zdst) {
+      float4* zr = reinterpret_cast<float4*>(extra) + (tab_smem ? lp.nk : 0);
+      if (t == blockIdx.x) {  // first tile: zero the region for the async proxy
+        for (int i = threadIdx.x; i < (int)(kZero / 16); i += NT) zr[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        fence_async_smem();
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) {
+        const int64_t tps = ColGeo<N, TW>::tps, tl = t % tps;
+        const int64_t a = tl * zchunk, b = a + zchunk < zbytes ? a + zchunk : zbytes;
+        if (a < b) bulk_zero(moved(zdst, by) + a, b - a, zr, kZero);
+      }
     }
     if constexpr (PREC != 0) {
       const uint32_t* rb = reinterpret_cast<const uint32_t*>(buf);
@@ -1075,6 +1110,7 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_c(N, 4), N)) k_lp
                                               const float2* __restrict__ twg, int64_t ntiles) {
   if (!op.geo.m.shift) resolve(op.lp, 0);  // one simulation: once per launch
   col_pipeline<N, fft_rows<N>() * 4 * TW>(op, twg, ntiles);
+  if (op.zdst && threadIdx.x == 0) bulk_store_drain();  // the zero fill completes with the kernel
 }
 
 // The LPT z pass with 8-column tiles (N = 256, 512), where four 4-column
@@ -2110,20 +2146,34 @@ cudaError_t mesh_z_force(int Nv, const float2* in, const float2* dk, float2* phi
 template <int N, int PREC>
 static cudaError_t launch_lpt_t(const void* p1, const void* p2, float2* o0, float2* o1,
                                 float2* o2, float2* o3, const LptParams& lp, const float2* tw,
-                                cudaStream_t s, Multi m) {
+                                cudaStream_t s, Multi m, float* zero_dst, int64_t zero_floats,
+                                bool* zeroed) {
   constexpr int TW = col_tw(N, 4);
   // one simulation at N >= 512 (one CTA per SM either way): the table row also
   // goes to shared memory
   const int tab_smem = (N >= 512 && !m.shift) ? 1 : 0;
-  const size_t sm = col_smem<N, 4>() + (tab_smem ? (size_t)lp.nk * sizeof(float4) : 0);
+  // the zero fill rides along where the pass runs one CTA per SM (N >= 512: room for the
+  // 16 KB zero region) on 16-byte aligned memory
+  const bool zf = zero_dst && zero_floats > 0 && N >= 512 && (zero_floats % 4) == 0 &&
+                  (reinterpret_cast<uintptr_t>(zero_dst) & 15) == 0;
+  using Op = OpLptZ<N, TW, PREC>;
+  const size_t sm = col_smem<N, 4>() + (tab_smem ? (size_t)lp.nk * sizeof(float4) : 0) + (zf ? Op::kZero : 0);
   const int64_t ntiles = col_tiles<N, TW>() * m.nb;
   auto k = k_lpt_z<N, TW, PREC>;
   unsigned grid;
   cudaError_t e = prep(k, sm, ntiles, grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, sm, s>>>(OpLptZ<N, TW, PREC>{geo_z<N, TW>(m), p1, p2, o0, o1, o2, o3, lp, tab_smem}, tw,
-                          ntiles);
-  return cudaGetLastError();
+  Op op{geo_z<N, TW>(m), p1, p2, o0, o1, o2, o3, lp, tab_smem};
+  if (zf) {
+    op.zdst = reinterpret_cast<char*>(zero_dst);
+    op.zbytes = zero_floats * (int64_t)sizeof(float);
+    const int64_t tps = col_tiles<N, TW>();
+    op.zchunk = ((op.zbytes + tps - 1) / tps + 15) / 16 * 16;
+  }
+  k<<<grid, NT, sm, s>>>(op, tw, ntiles);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && zeroed) *zeroed = zf;
+  return e;
 }
 
 template <int N, int PREC>
@@ -2141,7 +2191,7 @@ static cudaError_t launch_lpt8(const void* p1, const void* p2, float2* o0, float
 template <int N>
 static cudaError_t launch_lpt(const void* p1, const void* p2, float2* o0, float2* o1, float2* o2,
                               float2* o3, const LptParams& lp, const float2* tw,
-                              cudaStream_t s, Multi m) {
+                              cudaStream_t s, Multi m, float* zd, int64_t zn, bool* zeroed) {
   // measured on GB300 (ms per launch, 4-column -> 8-column tiles): N = 256 FP32 0.154 -> 0.144,
   // FP16 0.180 -> 0.143; N = 512 FP32 1.40 -> 1.46 (kept on 4 columns), FP16 1.55 -> 1.44
   if constexpr (N == 256 || N == 512) {
@@ -2149,15 +2199,17 @@ static cudaError_t launch_lpt(const void* p1, const void* p2, float2* o0, float2
     if (lp.seed_prec == 2) return launch_lpt8<N, 2>(p1, p2, o0, o1, o2, o3, lp, tw, s, m);
     if constexpr (N == 256) return launch_lpt8<N, 0>(p1, p2, o0, o1, o2, o3, lp, tw, s, m);
   }
-  if (lp.seed_prec == 1) return launch_lpt_t<N, 1>(p1, p2, o0, o1, o2, o3, lp, tw, s, m);
-  if (lp.seed_prec == 2) return launch_lpt_t<N, 2>(p1, p2, o0, o1, o2, o3, lp, tw, s, m);
-  return launch_lpt_t<N, 0>(p1, p2, o0, o1, o2, o3, lp, tw, s, m);
+  if (lp.seed_prec == 1) return launch_lpt_t<N, 1>(p1, p2, o0, o1, o2, o3, lp, tw, s, m, zd, zn, zeroed);
+  if (lp.seed_prec == 2) return launch_lpt_t<N, 2>(p1, p2, o0, o1, o2, o3, lp, tw, s, m, zd, zn, zeroed);
+  return launch_lpt_t<N, 0>(p1, p2, o0, o1, o2, o3, lp, tw, s, m, zd, zn, zeroed);
 }
 
 cudaError_t lpt_z(int Nv, const void* phi1, const void* phi2, float2* o0, float2* o1, float2* o2,
-                  float2* o3, const LptParams& lp, const float2* tw, cudaStream_t s, Multi m) {
+                  float2* o3, const LptParams& lp, const float2* tw, cudaStream_t s, Multi m,
+                  float* zero_dst, int64_t zero_floats, bool* zeroed) {
+  if (zeroed) *zeroed = false;
   if (Nv > 512) return cudaErrorInvalidValue;  // four double-buffered 4-column tiles exceed shared memory
-  COLA_SWITCH_N(Nv, return launch_lpt<N>(phi1, phi2, o0, o1, o2, o3, lp, tw, s, m));
+  COLA_SWITCH_N(Nv, return launch_lpt<N>(phi1, phi2, o0, o1, o2, o3, lp, tw, s, m, zero_dst, zero_floats, zeroed));
   return cudaSuccess;
 }
 
