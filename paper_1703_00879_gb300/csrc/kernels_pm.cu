@@ -780,11 +780,20 @@ __global__ void __launch_bounds__(NTP) k_pos_deposit(int Nm, float cellscale,
   cic_deposit(rho, Nm, c);
 }
 
-// P(k) estimator: per mode of the half spectrum, bin b = floor(|n| - 1/2) (decided
-// in double precision), weight 1 on the kx = 0, N/2 planes and 2 elsewhere,
-// |delta|^2 norm / W_CIC^2 with W_CIC = prod sinc^2(pi n_i/N) (the window in
-// single precision, a relative error ~1e-7 of P; sums in double).  acc holds
-// [count | sum P | sum |k| in units of k_F] per bin.
+// P(k) estimator: per mode of the half spectrum, bin b = floor(|n| - 1/2),
+// weight 1 on the kx = 0, N/2 planes and 2 elsewhere, |delta|^2 norm / W_CIC^2 with
+// W_CIC = prod sinc^2(pi n_i/N) (the window in single precision, a relative error
+// ~1e-7 of P).  acc holds [count | sum P | sum |k| in units of k_F] per bin, in
+// double precision.
+//
+// One warp per (z, y) row; lane l takes the run kx = l K .. l K + K - 1
+// (K = ceil((N/2 + 1) / 32)).  Along a run |n|^2 = kx^2 + ny^2 + nz^2 only grows,
+// so the bins are non-decreasing: a lane sums its modes in registers and adds to
+// the block's shared-memory bins once per bin it meets (and stops at the first
+// mode beyond the last bin).  The bin is decided exactly by integer comparisons,
+// 4 |n|^2 against (2b + 1)^2 and (2b + 3)^2.  |n| = s + r / (2 s) with s = sqrtf(|n|^2)
+// and r = |n|^2 - s^2 from one FMA (exact), summed in double: relative error
+// ~1e-14, with one double addition per mode (this GPU's double rate is low).
 __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, int N,
                                                 int64_t P, int nbins,
                                                 double* __restrict__ acc, double norm, Multi m,
@@ -795,47 +804,53 @@ __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, i
   acc = acc_stride > 0 ? acc + blockIdx.y * acc_stride : moved(acc, by);
   for (int i = threadIdx.x; i < 3 * nbins; i += NTP) sh[i] = 0.0;
   __syncthreads();
-  const int64_t nmodes = (int64_t)N * N * (N / 2 + 1);
-  for (int64_t m = (int64_t)blockIdx.x * NTP + threadIdx.x; m < nmodes;
-       m += (int64_t)gridDim.x * NTP) {
-    const int ix = (int)(m % (N / 2 + 1));
-    const int64_t rest = m / (N / 2 + 1);
-    const int iy = (int)(rest % N), iz = (int)(rest / N);
-    const int nx = ix, ny = iy < N / 2 ? iy : iy - N, nz = iz < N / 2 ? iz : iz - N;
-    // |n|^2 is an exact integer; the bin b = floor(|n| - 1/2) is decided exactly by
-    // integer comparisons, 4 |n|^2 against (2b + 1)^2 and (2b + 3)^2 (FP64 is slow
-    // on this GPU, so no double square root per mode)
-    const int64_t n2 = (int64_t)nx * nx + (int64_t)ny * ny + (int64_t)nz * nz;
-    if (4 * n2 < 1) continue;                            // |n| < 1/2: only n = 0
-    int b = (int)(sqrtf((float)n2) - 0.5f);
-    while (b > 0 && (int64_t)(2 * b + 1) * (2 * b + 1) > 4 * n2) --b;
-    while ((int64_t)(2 * b + 3) * (2 * b + 3) <= 4 * n2) ++b;
-    if (b >= nbins) continue;
-    // |n| in double: a float reciprocal square root and one Newton step in double
-    // (relative error ~1e-14)
-    const double nd = (double)n2;
-    double r = (double)rsqrtf((float)n2);
-    r = r * (1.5 - 0.5 * nd * r * r);
-    r = r * (1.5 - 0.5 * nd * r * r);
-    const double nmag = nd * r;
-    float wf = 1.f;
-    const int nn[3] = {nx, ny, nz};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if (nn[d] != 0) {
-        const float t = (float)nn[d] / (float)N;
-        const float sc = sinpif(t) / (3.14159265358979f * t);
-        wf *= sc * sc;
+  const int H = N / 2 + 1, K = (H + 31) / 32;
+  const int lane = threadIdx.x & 31, wpb = NTP / 32;
+  const float pi = 3.14159265358979f;
+  auto win = [&](int n) {
+    if (n == 0) return 1.f;
+    const float t = (float)n / (float)N;
+    const float sc = sinpif(t) / (pi * t);
+    return sc * sc;
+  };
+  for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < N * N; row += gridDim.x * wpb) {
+    const int iz = row / N, iy = row - iz * N;
+    const int ny = iy < N / 2 ? iy : iy - N, nz = iz < N / 2 ? iz : iz - N;
+    const int c = ny * ny + nz * nz;
+    const float wyz = win(ny) * win(nz);
+    int cur = -1;
+    double sw = 0.0, sp = 0.0, sn = 0.0;
+    auto flush = [&]() {
+      if (cur >= 0) {
+        atomicAdd(&sh[cur], sw);
+        atomicAdd(&sh[nbins + cur], sp * norm);
+        atomicAdd(&sh[2 * nbins + cur], sn);
       }
+    };
+    const int x0 = lane * K, x1 = min(x0 + K, H);
+    for (int ix = x0; ix < x1; ++ix) {
+      const int q = ix * ix + c;  // |n|^2 < 2^24 for N <= 4096
+      if (q == 0) continue;       // the k = 0 mode is in no bin
+      int b = (int)(sqrtf((float)q) - 0.5f);
+      while (b > 0 && (2 * b + 1) * (2 * b + 1) > 4 * q) --b;
+      while ((2 * b + 3) * (2 * b + 3) <= 4 * q) ++b;
+      if (b >= nbins) break;  // every later mode of the run is beyond the last bin too
+      if (b != cur) {
+        flush();
+        cur = b;
+        sw = sp = sn = 0.0;
+      }
+      const float qf = (float)q;
+      const float s = sqrtf(qf);
+      const float r = fmaf(-s, s, qf);
+      const float wt = (ix == 0 || ix == N / 2) ? 1.f : 2.f;
+      const float2 v = dk[hidx(iz, iy, ix, N, P)];
+      const float wf = win(ix) * wyz;
+      sw += (double)wt;
+      sp += (double)(wt * (v.x * v.x + v.y * v.y) / (wf * wf));
+      sn += (double)wt * ((double)s + (double)__fdividef(r, 2.f * s));
     }
-    const float2 v = dk[hidx(iz, iy, ix, N, P)];
-    // the power of the mode in float (relative error ~1e-7, far below the bins'
-    // 1e-4), accumulated in double
-    const double p2 = (double)((v.x * v.x + v.y * v.y) / (wf * wf)) * norm;
-    const double wt = (ix == 0 || ix == N / 2) ? 1.0 : 2.0;
-    atomicAdd(&sh[b], wt);
-    atomicAdd(&sh[nbins + b], wt * p2);
-    atomicAdd(&sh[2 * nbins + b], wt * nmag);
+    flush();
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 3 * nbins; i += NTP)
@@ -1097,8 +1112,9 @@ cudaError_t pk_bin(int N, const float2* dk, int nbins, double* acc, double norm,
                    cudaStream_t s, Multi m, int64_t acc_stride) {
   const size_t sm = 3 * (size_t)nbins * sizeof(double);
   if (sm > 48 * 1024) return cudaErrorInvalidValue;
-  const int64_t nmodes = (int64_t)N * N * (N / 2 + 1);
-  unsigned grid = (unsigned)std::min<int64_t>((nmodes + NTP - 1) / NTP, 152 * 8);
+  if (N > 4096) return cudaErrorInvalidValue;  // |n|^2 in 24 bits
+  const int64_t rows = (int64_t)N * N, wpb = NTP / 32;
+  unsigned grid = (unsigned)std::min<int64_t>((rows + wpb - 1) / wpb, 152 * 8);
   if (m.nb > 1) grid = std::max<unsigned>(1, grid / (unsigned)std::min(m.nb, 8));
   k_pk_bin<<<dim3(grid, m.nb), NTP, sm, s>>>(dk, N, half_pitch(N), nbins, acc, norm, m, acc_stride);
   return cudaGetLastError();
