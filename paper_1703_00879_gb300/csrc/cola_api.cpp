@@ -65,6 +65,11 @@ struct cola_ctx {
   // LPT work
   float2* lc[6] = {};
   float* lr[6] = {};
+  // second slot of the kick fields (FP32 runs): multi-step cola_step computes step n+1's
+  // LPT fields before step n's kick, so the two kick fields alternate; kslot = the slot
+  // holding the last step's (0: lr[3..5], 1: lrk)
+  float* lrk[3] = {};
+  int kslot = 0;
   // reduced-precision variant: the per-step drift (0..2) and kick (3..5) LPT
   // fields as 16-bit values with one FP32 scale per field (SimHeader lq_*)
   uint16_t* lq[6] = {};
@@ -128,12 +133,12 @@ constexpr int kMaxBins = 2000;
 enum Stage {
   ST_LPT_Z, ST_LPT_Y, ST_LPT_X, ST_RHO_ZERO, ST_DRIFT_DEPOSIT, ST_MESH_XR2C, ST_MESH_Y,
   ST_Z_SCREEN_FIELD, ST_X_SCREEN_SOURCE, ST_Z_FORCE, ST_MESH_YINV, ST_MESH_XC2R, ST_GATHER_KICK,
-  ST_COUNT
+  ST_KICK_DRIFT_DEPOSIT, ST_COUNT
 };
 const char* const kStageNames[ST_COUNT] = {
     "lpt_z_reweight", "lpt_y_inverse", "lpt_x_c2r", "rho_zero", "drift_deposit", "mesh_x_r2c",
     "mesh_y_forward", "z_screen_field", "x_screen_source", "z_force", "mesh_y_inverse",
-    "mesh_x_c2r", "gather_kick"};
+    "mesh_x_c2r", "gather_kick", "kick_drift_deposit"};
 
 cudaEvent_t take_event(cola_ctx* c) {
   if (!c->event_pool.empty()) {
@@ -699,6 +704,8 @@ void context_layout(cola_ctx* c, const cola_config& cfg, Layout& L) {
     L.add(&c->lr[i], P);
     if (cfg.seed_precision) L.add(&c->lq[i], P);
   }
+  if (!cfg.seed_precision)
+    for (int d = 0; d < 3; ++d) L.add(&c->lrk[d], P);
   L.add(&c->rho, M);
   L.add(&c->Cd, hm);
   L.add(&c->Ck, hm);
@@ -778,7 +785,7 @@ int c2r3(cola_ctx* ctx, int N, float2* in, float* out, const float2* tw, Multi m
 // row of table `vel` (0 displacement/acceleration, 1 velocity): row0, plus the
 // device step counter when add_step; over m's simulations (ctx is the first).
 int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}, float* zero_dst = nullptr,
-            int64_t zero_floats = 0, bool* zeroed = nullptr) {
+            int64_t zero_floats = 0, bool* zeroed = nullptr, int kslot = 0) {
   LptParams lp{};
   lp.hdr = ctx->hdr;
   lp.vel = vel;
@@ -821,7 +828,8 @@ int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}, float
       CK(fft_xc2r_multi16(N, 6, in6, out6, kfs6, lp.seed_prec, ctx->hdr, ctx->tw_np, st, m));
       CK(lq_update(ctx->hdr, lp.seed_prec, ctx->cfg.nsteps, st, m));
     } else {
-      float* out6[6] = {ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->lr[3], ctx->lr[4], ctx->lr[5]};
+      float* const* ko = kslot ? ctx->lrk : ctx->lr + 3;
+      float* out6[6] = {ctx->lr[0], ctx->lr[1], ctx->lr[2], ko[0], ko[1], ko[2]};
       CK(fft_xc2r_multi(N, 6, in6, out6, kfs6, ctx->tw_np, st, m));
     }
   }
@@ -1098,7 +1106,9 @@ int export_half(cola_ctx* ctx, int N, const float2* padded, float2* tmp, void* d
 // g.lead->st without touching the host step counters.  The step index comes
 // from each simulation's device header, so the launch sequence is the same for
 // every step.  n is the host's step index, used only for the model flags.
-int enqueue_group_step(const Group& g, int n) {
+int enqueue_group_tail(const Group& g, int kslot);
+
+int enqueue_group_step(const Group& g, int n, bool head_only = false) {
   cola_ctx* ctx = g.lead;
   const Multi m = g.all;
   const PartParams pp = part_params(ctx);
@@ -1134,7 +1144,28 @@ int enqueue_group_step(const Group& g, int n) {
                         ctx->P, ctx->st, m, mix));
   prof_end(ctx, ST_DRIFT_DEPOSIT, e, 1, m.nb * ((fast ? 84.0 : lq ? 66.0 : 72.0) * Pb + 8.0 * Mb));
   CHECK_RC(force_group(g, ctx->a[n + 1], true));
-  e = prof_begin(ctx, ST_GATHER_KICK);
+  if (head_only) return COLA_OK;
+  return enqueue_group_tail(g, 0);
+}
+
+// The kick that ends a step (the force of the step is in F) and the device step
+// advance; the step's kick fields are in slot kslot (see cola_ctx::lrk).
+int enqueue_group_tail(const Group& g, int kslot) {
+  cola_ctx* ctx = g.lead;
+  const Multi m = g.all;
+  const PartParams pp = part_params(ctx);
+  const double Pb = (double)ctx->P, Mb = (double)ctx->M;
+  const bool fast = ctx->lpt_fast;
+  const LptMix mix = fast ? lpt_mix_of(ctx, 1, 1, false) : LptMix{};
+  const int lq = (!fast && ctx->cfg.seed_precision) ? ctx->cfg.seed_precision : 0;
+  StepDt dt{ctx->hdr, 0.f, 0.f};
+  dt.lq = lq;
+  const float* lk[3] = {ctx->lr[3], ctx->lr[4], ctx->lr[5]};
+  if (kslot)
+    for (int d = 0; d < 3; ++d) lk[d] = ctx->lrk[d];
+  if (lq)
+    for (int d = 0; d < 3; ++d) lk[d] = reinterpret_cast<const float*>(ctx->lq[3 + d]);
+  cudaEvent_t e = prof_begin(ctx, ST_GATHER_KICK);
   if (fast)  // A_LPT: Psi1 (lr[0..2]) mixed with Psi2
     for (int d = 0; d < 3; ++d) lk[d] = ctx->lr[d];
   CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
@@ -1142,10 +1173,52 @@ int enqueue_group_step(const Group& g, int n) {
                       ctx->F[2], dt, ctx->P, ctx->st, m, mix));
   prof_end(ctx, ST_GATHER_KICK, e, 1, m.nb * ((fast ? 72.0 : lq ? 54.0 : 60.0) * Pb + 12.0 * Mb));
   CK(step_advance(ctx->hdr, ctx->st, m));
+  ctx->kslot = kslot;  // multi-simulation groups use slot 0 (their callers reset every member)
   return COLA_OK;
 }
 
 int enqueue_step(cola_ctx* ctx, int n) { return enqueue_group_step(single_group(ctx), n); }
+
+// K >= 2 consecutive steps of one simulation (Sec. 2) with the kick of each step
+// but the last and the drift + deposit of the next in one pass
+// (k_kick_drift_deposit): step n+1's LPT fields are formed before step n's kick,
+// its kick fields into the other slot.  The particle state after the K steps is
+// the one K separate steps leave.  FP32 fields, per-k LPT path.
+bool fused_steps_ok(const cola_ctx* ctx, int K) {
+  return K >= 2 && !ctx->lpt_fast && !ctx->cfg.seed_precision && ctx->lrk[0] != nullptr;
+}
+
+int enqueue_steps_fused(cola_ctx* ctx, int K) {
+  const Group g = single_group(ctx);
+  const Multi m = g.all;
+  const PartParams pp = part_params(ctx);
+  const double Pb = (double)ctx->P, Mb = (double)ctx->M;
+  CHECK_RC(enqueue_group_step(g, ctx->step, true));  // LPT, drift + deposit, force of the first step
+  int cur = 0;
+  for (int i = 1; i < K; ++i) {
+    // step n+1's LPT fields (table row 2 + device step n): drift into lr[0..2], kick into the other slot
+    bool zeroed = false;
+    CHECK_RC(run_lpt(ctx, 0, 2, true, m, ctx->rho, ctx->M, &zeroed, 1 - cur));
+    if (!zeroed) {
+      cudaEvent_t e = prof_begin(ctx, ST_RHO_ZERO);
+      CK(zero_f32(ctx->rho, ctx->M, ctx->st, m));
+      prof_end(ctx, ST_RHO_ZERO, e, 1, m.nb * 4.0 * Mb);
+    }
+    const float* const* ka = cur ? ctx->lrk : ctx->lr + 3;
+    cudaEvent_t e = prof_begin(ctx, ST_KICK_DRIFT_DEPOSIT);
+    CK(part_kick_drift_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2], ka[0],
+                               ka[1], ka[2], ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->F[0], ctx->F[1],
+                               ctx->F[2], ctx->rho, ctx->hdr, ctx->P, ctx->st, m));
+    prof_end(ctx, ST_KICK_DRIFT_DEPOSIT, e, 1, m.nb * (72.0 * Pb + 20.0 * Mb));
+    CK(step_advance(ctx->hdr, ctx->st, m));
+    ctx->step += 1;
+    cur = 1 - cur;
+    CHECK_RC(force_group(g, ctx->a[ctx->step + 1], true));
+  }
+  CHECK_RC(enqueue_group_tail(g, cur));
+  ctx->step += 1;
+  return COLA_OK;
+}
 
 }  // namespace
 
@@ -1393,6 +1466,7 @@ int cola_step(cola_ctx* ctx, int32_t nsteps) {
   if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "cola_step before cola_ic");
   if (nsteps < 0) nsteps = ctx->cfg.nsteps - ctx->step;
   if (ctx->step + nsteps > ctx->cfg.nsteps) return fail(ctx, COLA_EINVAL, "past the last step");
+  if (fused_steps_ok(ctx, nsteps)) return enqueue_steps_fused(ctx, nsteps);
   for (int it = 0; it < nsteps; ++it) {
     CHECK_RC(enqueue_step(ctx, ctx->step));
     ctx->step += 1;
@@ -1656,7 +1730,8 @@ int cola_export(cola_ctx* ctx, int32_t which, void* dst, int32_t where) {
         }
         return COLA_OK;
       }
-      for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * pb, ctx->lr[o + c], pb, where));
+      for (int c = 0; c < 3; ++c)
+        CHECK_RC(copy_out(ctx, d + c * pb, (o == 3 && ctx->kslot) ? ctx->lrk[c] : ctx->lr[o + c], pb, where));
       return COLA_OK;
     }
     default:
@@ -2033,12 +2108,14 @@ int cola_batch_step(cola_batch* b, int32_t nsteps) {
   const int total = b->ctx[0]->cfg.nsteps;
   if (nsteps < 0) nsteps = total - b->step;
   if (b->step + nsteps > total) return bfail(b, COLA_EINVAL, "past the last step");
+  for (cola_ctx* c : b->ctx) c->kslot = 0;  // batch steps keep the kick fields in lr[3..5]
   for (int i = 0; i < nsteps; ++i) CHECK_RC(batch_launch(b, b->plan));
   return COLA_OK;
 }
 
 int cola_batch_autotune(cola_batch* b, int32_t max_steps, cola_batch_plan* best_out) {
   if (!b) return fail(nullptr, COLA_EINVAL, "batch is NULL");
+  for (cola_ctx* c : b->ctx) c->kslot = 0;  // batch steps keep the kick fields in lr[3..5]
   const int n = (int)b->ctx.size();
   const int total = b->ctx[0]->cfg.nsteps;
   const int sms = 152;
@@ -2274,6 +2351,7 @@ int cola_step_many(cola_ctx* const* ctxs, int32_t n, void* stream) {
   for (int i = 0; i < n; ++i) {
     ctxs[i]->step += 1;
     ctxs[i]->hh.step = ctxs[i]->step;
+    ctxs[i]->kslot = 0;
   }
   return COLA_OK;
 }

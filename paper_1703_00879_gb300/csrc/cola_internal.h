@@ -241,6 +241,15 @@ cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float*
                              float* ay, float* az, const float* Ax, const float* Ay,
                              const float* Az, const float* Fx, const float* Fy, const float* Fz,
                              StepDt dt, int64_t P, cudaStream_t s, Multi m = {}, LptMix mix = {});
+// End of step n (hdr->step = n) and start of step n + 1 in one pass: kick with A_n,
+// closing half kick and drift of step n + 1 with its drift field dp, CIC deposit into rho
+// (zeroed by the caller); acc is not written.  FP32 fields, lattice of Np^3 particles.
+cudaError_t part_kick_drift_deposit(const PartParams& pp, float* sx, float* sy, float* sz, float* vx,
+                                    float* vy, float* vz, const float* Ax, const float* Ay,
+                                    const float* Az, const float* dpx, const float* dpy,
+                                    const float* dpz, const float* Fx, const float* Fy, const float* Fz,
+                                    float* rho, const SimHeader* hdr, int64_t P, cudaStream_t s,
+                                    Multi m = {});
 // Per simulation: lq_used = lq_scale (the scale the fields just written, table
 // row step + 1, carry), lq_scale = lq_amax x (growth of the next row over this
 // one, lqg) / target for the next pass (unchanged if nothing was written),
