@@ -1,0 +1,55 @@
+"""Multi-step cola_step joins the kick of each step but the last with the drift and
+deposit of the next (one pass over the particles, Sec. 2), forming the next step's
+LPT fields first.  The arithmetic per particle is that of separate steps; only the
+order of the float additions in the CIC deposit differs, so K steps in one call and
+K calls of one step agree to FP32 rounding, and both agree with the FP64 oracle."""
+import numpy as np
+import pytest
+
+from workloads import SMALL_F5
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1703_00879_gb300 as p
+    return p
+
+
+def _run(pkg, run, calls):
+    with pkg.Simulation(run) as s:
+        for k in calls:
+            s.step(k)
+        out = {w: s.export(w).astype(np.float64) for w in (pkg.COLA_F_DISP, pkg.COLA_F_DV, pkg.COLA_F_ACC,
+                                                              pkg.COLA_F_LPT_DISP, pkg.COLA_F_LPT_ACC)}
+        _, P, _ = s.pk()
+    return out, P
+
+
+@pytest.mark.parametrize("split", [[10], [2, 3, 5], [7, 1, 2]], ids=["one_call", "three_calls", "mixed"])
+def test_fused_steps_equal_single_steps(pkg, split):
+    run = SMALL_F5
+    ref, Pref = _run(pkg, run, [1] * 10)
+    got, P = _run(pkg, run, split)
+    cell = run.Lbox / run.Nmesh
+    for w in (pkg.COLA_F_DISP, pkg.COLA_F_DV, pkg.COLA_F_ACC):
+        scale = np.max(np.abs(ref[w])) or 1.0
+        err = np.max(np.abs(got[w] - ref[w]))
+        assert err <= 1e-4 * (cell if w == pkg.COLA_F_DISP else scale), (w, err)
+    # the last step's LPT fields (kick fields from whichever slot the last call left them in)
+    for w in (pkg.COLA_F_LPT_DISP, pkg.COLA_F_LPT_ACC):
+        np.testing.assert_allclose(got[w], ref[w], rtol=0, atol=1e-6 * np.max(np.abs(ref[w])))
+    assert np.max(np.abs(P / Pref - 1)) <= 1e-5
+
+
+def test_fused_steps_then_batch_step_use_the_right_kick_fields(pkg):
+    """A context stepped by a fused call (kick fields left in the second slot) and then by a
+    cola_step_many step exports the kick fields of its last step."""
+    run = SMALL_F5.with_(nsteps=4)
+    a, _ = _run(pkg, run, [1, 1, 1])
+    with pkg.Simulation(run) as s:
+        s.step(2)
+        pkg.step_many([s])
+        b = s.export(pkg.COLA_F_LPT_ACC).astype(np.float64)
+    np.testing.assert_allclose(b, a[pkg.COLA_F_LPT_ACC], rtol=0, atol=1e-6 * np.max(np.abs(b)))
