@@ -176,9 +176,13 @@ int cola_ic_from_potentials(cola_ctx* ctx, const float* phi1, const float* phi2,
 /* Advances `nsteps` COLA steps (Sec. 2, App. A; -1 = to z_final): per step the
  * LPT reweight and inverse FFTs of the displacement and acceleration fields,
  * the drift with CIC deposit, the forward FFT, the screened Poisson solve,
- * the force inverse FFTs and the CIC gather with the kick.  Asynchronous on
- * the stream.  Errors: COLA_ESTATE (before cola_ic), COLA_EINVAL (past the
- * last step), COLA_ECUDA. */
+ * the force inverse FFTs and the CIC gather with the kick.  Within one call of
+ * two or more steps (FP32 fields, per-k LPT path) the kick of each step but
+ * the last and the drift + deposit of the next run as one pass over the
+ * particles, with the next step's LPT fields formed first; the state after the
+ * call is that of the same number of single steps (up to the order of the
+ * deposit's float additions).  Asynchronous on the stream.  Errors:
+ * COLA_ESTATE (before cola_ic), COLA_EINVAL (past the last step), COLA_ECUDA. */
 int cola_step(cola_ctx* ctx, int32_t nsteps);
 
 /* Particle positions (wrapped into [0, Lbox), [Np^3][3] floats, Mpc/h) and
@@ -473,11 +477,9 @@ int cola_pk_noalloc(const float* pos, int64_t n, int32_t nmesh, double Lbox, int
 int cola_host_growth(const cola_config* cfg, const cola_model* model, double* out,
                      double* k_nodes);
 
-/* Device bytes cola_init allocates for cfg: one allocation holding every
- * per-context buffer (for admission control); -1 if cfg is invalid.  Not
- * counted: the read-only tables shared by all contexts of one configuration
- * and model (twiddles, growth tables, per-step parameters; about
- * 2 (nsteps+1) nk_table 16 bytes per distinct configuration and model). */
+/* Device bytes cola_init allocates for cfg: the one allocation holding every
+ * buffer of a context, its own copy of the twiddle, growth and per-step tables
+ * included (for admission control); -1 if cfg is invalid. */
 int64_t cola_device_bytes(const cola_config* cfg);
 
 /* Time integrals of the kick-drift-kick step (Sec. 2; dtau = dt/a^2):
