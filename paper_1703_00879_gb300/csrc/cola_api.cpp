@@ -883,12 +883,20 @@ int force_group(const Group& g, double a, bool device_params, bool ini = false) 
   auto st = ctx->st;
   const float2* tw = ctx->tw_nm;
   const double H = (double)N * N * (N / 2 + 1) * 8.0, R = (double)N * N * N * 4.0;
+  // up to 128 points the x and y steps of each transform run plane by plane in one pass
+  const bool plane = N <= 128;
   cudaEvent_t e = prof_begin(ctx, ST_MESH_XR2C);
-  CK(fft_xr2c(N, ctx->rho, ctx->Cd, fp.inv_rhobar, -1.f, tw, st, all));
+  if (plane) {
+    CK(fft_plane_r2c(N, ctx->rho, ctx->Cd, fp.inv_rhobar, -1.f, tw, st, all));
+  } else {
+    CK(fft_xr2c(N, ctx->rho, ctx->Cd, fp.inv_rhobar, -1.f, tw, st, all));
+  }
   prof_end(ctx, ST_MESH_XR2C, e, 1, all.nb * (R + H));
-  e = prof_begin(ctx, ST_MESH_Y);
-  CK(fft_col(N, ctx->Cd, 1, false, tw, st, all));
-  prof_end(ctx, ST_MESH_Y, e, 1, all.nb * 2 * H);
+  if (!plane) {
+    e = prof_begin(ctx, ST_MESH_Y);
+    CK(fft_col(N, ctx->Cd, 1, false, tw, st, all));
+    prof_end(ctx, ST_MESH_Y, e, 1, all.nb * 2 * H);
+  }
   if (const Group::Sub& sc = g.screened; sc.lead) {
     e = prof_begin(ctx, ST_Z_SCREEN_FIELD);
     for (const Group::Sub* sub : {&g.fr_screened, &g.dgp_screened})
@@ -921,18 +929,22 @@ int force_group(const Group& g, double a, bool device_params, bool ini = false) 
                     un.m));
     prof_end(ctx, ST_Z_FORCE, e, 1, un.m.nb * 3 * H);
   }
-  e = prof_begin(ctx, ST_MESH_YINV);
-  CK(fft_yinv2(N, ctx->Cphi, ctx->Cphi, ctx->Cw, -fp.kf, tw, st, all));
-  CK(fft_col(N, ctx->Cphz, 1, true, tw, st, all));
-  prof_end(ctx, ST_MESH_YINV, e, 2, all.nb * 5.0 * H);
-  e = prof_begin(ctx, ST_MESH_XC2R);
-  {
+  if (plane) {
+    e = prof_begin(ctx, ST_MESH_XC2R);
+    CK(fft_plane_force(N, ctx->Cphi, ctx->Cphz, ctx->F[0], ctx->F[1], ctx->F[2], -fp.kf, tw, st, all));
+    prof_end(ctx, ST_MESH_XC2R, e, 1, all.nb * (2 * H + 3 * R));
+  } else {
+    e = prof_begin(ctx, ST_MESH_YINV);
+    CK(fft_yinv2(N, ctx->Cphi, ctx->Cphi, ctx->Cw, -fp.kf, tw, st, all));
+    CK(fft_col(N, ctx->Cphz, 1, true, tw, st, all));
+    prof_end(ctx, ST_MESH_YINV, e, 2, all.nb * 5.0 * H);
+    e = prof_begin(ctx, ST_MESH_XC2R);
     const float2* in3[3] = {ctx->Cphi, ctx->Cw, ctx->Cphz};
     float* out3[3] = {ctx->F[0], ctx->F[1], ctx->F[2]};
     const float kfs3[3] = {-fp.kf, 0.f, 0.f};
     CK(fft_xc2r_multi(N, 3, in3, out3, kfs3, tw, st, all));
+    prof_end(ctx, ST_MESH_XC2R, e, 1, all.nb * 3 * (H + R));
   }
-  prof_end(ctx, ST_MESH_XC2R, e, 1, all.nb * 3 * (H + R));
   ctx->have_force = true;
   return COLA_OK;
 }

@@ -270,6 +270,15 @@ cudaError_t count_nonfinite(const float* const* f, int nf, int64_t n, unsigned l
 // *dst (host) = the number of transform CTAs on this device whose TMA tile-load
 // wait ran out (one second) since the library was loaded; stream-ordered copy.
 cudaError_t tile_load_failures(unsigned* dst, cudaStream_t s);
+// N <= 128: the x (r2c, in scale + offset) and y forward transforms of a real N^3 field
+// in one pass, one CTA per z-plane (out: interleaved half spectrum, z not transformed).
+cudaError_t fft_plane_r2c(int N, const float* in, float2* out, float scale, float offset, const float2* tw,
+                          cudaStream_t s, Multi m = {});
+// N <= 128: the force's y and x inverse steps in one pass per z-plane: from Phi and
+// -i kz Phi (z already inverse-transformed), fx = c2r(yinv(Phi)) with i kfs kx,
+// fy = c2r(yinv(i kfs ky Phi)), fz = c2r(yinv(-i kz Phi)).
+cudaError_t fft_plane_force(int N, const float2* phi, const float2* phiz, float* fx, float* fy, float* fz,
+                            float kfs, const float2* tw, cudaStream_t s, Multi m = {});
 // Runs the transform kernels' bounded mbarrier wait on a phase that never completes
 // (limit `seconds`, 0 < seconds <= 10, on the per-thread default stream; waits for it); *timed_out = 1 when it gave up.
 cudaError_t wait_probe(double seconds, int* timed_out);

@@ -1781,6 +1781,167 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------- plane passes (N <= 128)
+// Up to 128 points a whole z-plane of the half spectrum (N rows of M + 1 = N/2 + 1
+// values) fits in one CTA's shared memory, so the x and y steps of a 3-D
+// transform run as one pass over HBM: one CTA per plane (and simulation) stages
+// the plane, transforms its rows and then its columns in place, and writes it
+// back; the intermediate between the x and y steps never leaves the SM.  The
+// plane's rows have the row-transform pitch CW (>= M + R2 - 1, 8 mod 16, so the
+// row steps are conflict-free) and the column transforms run on chunks of
+// TWCOL columns at that pitch, with the padding rows of their intermediate
+// below the plane.
+template <int N>
+struct PlaneCfg {
+  static constexpr int M = N / 2;
+  static constexpr int CW = rowtile_pitch<M>();
+  static constexpr int ROWS = fft_rows<N>();
+  static constexpr int TWCOL = N == 128 ? 24 : CW;  // column chunk (a multiple of 8, CW = 3 x 24 at N = 128)
+  static constexpr size_t buf = (size_t)ROWS * CW;   // float2
+  static constexpr size_t smem = ((size_t)N + buf) * sizeof(float2);
+  static_assert(CW >= M + 1 && CW % 8 == 0 && CW % TWCOL == 0 && TWCOL % 8 == 0, "plane pitch");
+};
+
+// The N real rows of a plane (N floats each) as M complex values per row at pitch CW.
+template <int N>
+__device__ __forceinline__ void stage_real_plane(float2* buf, const float* __restrict__ src) {
+  constexpr int CH = N / 4, CW = PlaneCfg<N>::CW;  // 16-byte pieces per row
+  for (int e = threadIdx.x; e < N * CH; e += NT) {
+    const int y = e / CH, p = e - y * CH;
+    cp_async16(reinterpret_cast<float*>(buf + y * CW) + 4 * p, src + (int64_t)y * N + 4 * p, true);
+  }
+}
+
+// r2c split of every plane row in place (the split of row_r2c_store): from the
+// packed transform Z of row r, X[k] = (Z[k] + conj Z[M-k])/2 - i/2 w^k (Z[k] - conj Z[M-k])
+// for k = 0..M; a thread takes the pair (k, M - k) (k = 0: X[0] and X[M] from Z[0]).
+template <int N>
+__device__ __forceinline__ void plane_r2c_split(float2* buf, const float2* tw) {
+  constexpr int M = N / 2, CW = PlaneCfg<N>::CW, H = M / 2 + 1;
+  auto X = [&](float2 a, float2 bz, float2 w) {
+    const float2 b = cconj(bz);
+    const float2 E = cscale(cadd(a, b), 0.5f), D = csub(a, b);
+    return cadd(E, cmul(w, make_float2(0.5f * D.y, -0.5f * D.x)));
+  };
+  for (int e = threadIdx.x; e < N * H; e += NT) {
+    const int r = e / H, k = e - r * H;
+    float2* z = buf + r * CW;
+    const float2 zk = z[k], zm = z[(M - k) & (M - 1)];
+    const float2 xk = X(zk, zm, tw[k]), xm = X(zm, zk, tw[M - k]);
+    z[k] = xk;
+    if (k != M - k) z[M - k] = xm;
+  }
+  __syncthreads();
+}
+
+// Forward x (r2c, input scaled then offset) and y transforms of plane blockIdx.x of a
+// real N^3 field into the interleaved half spectrum (the z pass follows separately).
+template <int N>
+__global__ void __launch_bounds__(NT) k_plane_r2c(const float* __restrict__ in, float2* __restrict__ out,
+                                                  float scale, float offset, const float2* __restrict__ twg,
+                                                  Multi m) {
+  using C = PlaneCfg<N>;
+  extern __shared__ __align__(128) float2 sm[];
+  float2* tw = sm;
+  float2* buf = sm + N;
+  const int z = blockIdx.x;
+  const int64_t by = shift_of(m, blockIdx.y);
+  load_tw(tw, twg, N);
+  stage_real_plane<N>(buf, moved(in, by) + (int64_t)z * N * N);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  fft_rowtile<C::M, N, C::CW, NT, false, 2>(buf, tw, ScaleOffset{scale, offset});
+  plane_r2c_split<N>(buf, tw);
+  constexpr int64_t P = half_pitch(N);
+  float2* g = moved(out, by) + hrow(z, 0, N, P);
+#pragma unroll 1
+  for (int c0 = 0; c0 < C::CW; c0 += C::TWCOL)
+    fft_tile<N, C::TWCOL, C::CW, NT, false, 1, TileLoad, ColOut>(
+        buf + c0, tw, TileLoad{}, ColOut{g + hcol(c0), 4 * P, 2 * P, C::M + 1 - c0});
+}
+
+// Store hook of a plane's row transforms: real row r (M float2 = N reals) to g + r M.
+template <int M>
+struct PlaneRowOut {
+  static constexpr bool kSmem = false;
+  float2* g;
+  __device__ __forceinline__ float2 operator()(float2 v, int r, int k) const {
+    g[r * M + k] = v;
+    return v;
+  }
+};
+
+// The N complex rows (ky) of plane z of an interleaved half spectrum into buf (pitch CW).
+template <int N>
+__device__ __forceinline__ void stage_complex_plane(float2* buf, const float2* __restrict__ g, int z) {
+  constexpr int M = N / 2, CW = PlaneCfg<N>::CW;
+  constexpr int64_t P = half_pitch(N);
+  constexpr int CH = (M + 2) / 2;  // 16-byte pieces per row (kx = 0..M, staged as M + 2)
+  const float2* src = g + hrow(z, 0, N, P);
+  for (int e = threadIdx.x; e < N * CH; e += NT) {
+    const int y = e / CH, p = e - y * CH, kx = 2 * p;
+    cp_async16(buf + y * CW + kx, src + (int64_t)y * 2 * P + hcol(kx), true);
+  }
+}
+
+// y inverse of every column chunk of plane a, in place.
+template <int N>
+__device__ __forceinline__ void plane_yinv(float2* a, const float2* tw) {
+  using C = PlaneCfg<N>;
+#pragma unroll 1
+  for (int c0 = 0; c0 < C::CW; c0 += C::TWCOL) fft_tile<N, C::TWCOL, C::CW, NT, true>(a + c0, tw);
+}
+
+// c2r of the N rows of plane buffer a (x derivative i kfs kx applied on load when
+// kfs != 0) to the real plane at g (N x N floats).
+template <int N>
+__device__ __forceinline__ void plane_xc2r(float2* a, const float2* tw, float kfs, float* g) {
+  using C = PlaneCfg<N>;
+  row_c2r_combine<N, N>(a, tw, kfs);
+  fft_rowtile<C::M, N, C::CW, NT, true, 2, NoPre, false, PlaneRowOut<C::M>>(
+      a, tw, NoPre{}, PlaneRowOut<C::M>{reinterpret_cast<float2*>(g)});
+}
+
+// i kfs f_y times every value of plane buffer a (f_y the signed frequency of row y;
+// zero on the Nyquist row), in place.
+template <int N>
+__device__ __forceinline__ void plane_deriv_y(float2* a, float kfs) {
+  using C = PlaneCfg<N>;
+  for (int e = threadIdx.x; e < N * C::CW; e += NT) {
+    const int y = e / C::CW;
+    const float f = (y == N / 2) ? 0.f : kfs * (float)freq_index(y, N);
+    a[e] = cscale(cmul_i(a[e]), f);
+  }
+  __syncthreads();
+}
+
+// One force component's inverse y and x steps for one plane (App. B): from Phi
+// and -i kz Phi after their z inverse, F_x = c2r(yinv(Phi)) with i kfs kx on load,
+// F_y = c2r(yinv(i kfs ky Phi)), F_z = c2r(yinv(-i kz Phi)); kfs = -k_F.  CTA x
+// takes component x % 3 of plane x / 3, so the F_x and F_y CTAs of a plane run
+// side by side and the second read of Phi's plane comes from L2.
+template <int N>
+__global__ void __launch_bounds__(NT) k_plane_force(const float2* __restrict__ phi, const float2* __restrict__ phiz,
+                                                    float* __restrict__ fx, float* __restrict__ fy,
+                                                    float* __restrict__ fz, float kfs,
+                                                    const float2* __restrict__ twg, Multi m) {
+  using C = PlaneCfg<N>;
+  extern __shared__ __align__(128) float2 sm[];
+  float2* tw = sm;
+  float2* a = sm + N;
+  const int q = blockIdx.x % 3, z = blockIdx.x / 3;
+  const int64_t by = shift_of(m, blockIdx.y), off = (int64_t)z * N * N;
+  load_tw(tw, twg, N);
+  stage_complex_plane<N>(a, moved(q == 2 ? phiz : phi, by), z);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  if (q == 1) plane_deriv_y<N>(a, kfs);
+  plane_yinv<N>(a, tw);
+  plane_xc2r<N>(a, tw, q == 0 ? kfs : 0.f, moved(q == 0 ? fx : q == 1 ? fy : fz, by) + off);
+}
+
 // ---------------------------------------------------------------- launch helpers
 template <int N, int NBUF>
 constexpr size_t col_smem() {
@@ -2210,6 +2371,52 @@ cudaError_t lpt_z(int Nv, const void* phi1, const void* phi2, float2* o0, float2
   if (zeroed) *zeroed = false;
   if (Nv > 512) return cudaErrorInvalidValue;  // four double-buffered 4-column tiles exceed shared memory
   COLA_SWITCH_N(Nv, return launch_lpt<N>(phi1, phi2, o0, o1, o2, o3, lp, tw, s, m, zero_dst, zero_floats, zeroed));
+  return cudaSuccess;
+}
+
+template <int N>
+static cudaError_t launch_plane_r2c(const float* in, float2* out, float scale, float offset,
+                                    const float2* tw, cudaStream_t s, Multi m) {
+  if constexpr (N > 128) {
+    return cudaErrorInvalidValue;
+  } else {
+    constexpr size_t sm = PlaneCfg<N>::smem;
+    auto k = k_plane_r2c<N>;
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    k<<<dim3(N, m.nb), NT, sm, s>>>(in, out, scale, offset, tw, m);
+    return cudaGetLastError();
+  }
+}
+
+cudaError_t fft_plane_r2c(int Nv, const float* in, float2* out, float scale, float offset, const float2* tw,
+                          cudaStream_t s, Multi m) {
+  COLA_SWITCH_N(Nv, return launch_plane_r2c<N>(in, out, scale, offset, tw, s, m));
+  return cudaSuccess;
+}
+
+template <int N>
+static cudaError_t launch_plane_force(const float2* phi, const float2* phiz, float* fx, float* fy, float* fz,
+                                      float kfs, const float2* tw, cudaStream_t s, Multi m) {
+  if constexpr (N > 128) {
+    return cudaErrorInvalidValue;
+  } else {
+    constexpr size_t sm = PlaneCfg<N>::smem;
+    auto k = k_plane_force<N>;
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    k<<<dim3(3 * N, m.nb), NT, sm, s>>>(phi, phiz, fx, fy, fz, kfs, tw, m);
+    return cudaGetLastError();
+  }
+}
+
+cudaError_t fft_plane_force(int Nv, const float2* phi, const float2* phiz, float* fx, float* fy, float* fz,
+                            float kfs, const float2* tw, cudaStream_t s, Multi m) {
+  COLA_SWITCH_N(Nv, return launch_plane_force<N>(phi, phiz, fx, fy, fz, kfs, tw, s, m));
   return cudaSuccess;
 }
 
