@@ -810,6 +810,20 @@ int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}, float
            zero_floats, &zd));
   if (zeroed) *zeroed = zd;
   prof_end(ctx, ST_LPT_Z, e, 1, m.nb * (2 * seedH + 4 * H + (zd ? 4.0 * (double)zero_floats : 0.0)));
+  // variant a.S1: the per-step drift and kick fields leave the x pass as 16-bit
+  // values (one FP32 scale per field, delayed scaling)
+  const bool q16 = lp.seed_prec != 0 && vel == 0 && add_step;
+  if (N <= 128 && !q16) {
+    // y and x steps of the six outputs in one pass per (plane, field)
+    e = prof_begin(ctx, ST_LPT_X);
+    float* const* ko = kslot ? ctx->lrk : ctx->lr + 3;
+    const float2* in4[4] = {ctx->lc[0], ctx->lc[1], ctx->lc[2], ctx->lc[3]};
+    float* out6[6] = {ctx->lr[0], ctx->lr[1], ctx->lr[2], ko[0], ko[1], ko[2]};
+    CK(fft_plane_lpt(N, in4, out6, kf, ctx->tw_np, st, m));
+    prof_end(ctx, ST_LPT_X, e, 1, m.nb * (4 * H + 6 * R));
+    ctx->have_lpt = true;
+    return COLA_OK;
+  }
   e = prof_begin(ctx, ST_LPT_Y);
   CK(fft_yinv2(N, ctx->lc[0], ctx->lc[0], ctx->lc[4], kf, ctx->tw_np, st, m));
   CK(fft_col(N, ctx->lc[1], 1, true, ctx->tw_np, st, m));
@@ -817,9 +831,6 @@ int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}, float
   CK(fft_col(N, ctx->lc[3], 1, true, ctx->tw_np, st, m));
   prof_end(ctx, ST_LPT_Y, e, 4, m.nb * 10.0 * H);
   e = prof_begin(ctx, ST_LPT_X);
-  // variant a.S1: the per-step drift and kick fields leave the x pass as 16-bit
-  // values (one FP32 scale per field, delayed scaling)
-  const bool q16 = lp.seed_prec != 0 && vel == 0 && add_step;
   {
     const float2* in6[6] = {ctx->lc[0], ctx->lc[4], ctx->lc[1], ctx->lc[2], ctx->lc[5], ctx->lc[3]};
     const float kfs6[6] = {kf, 0.f, 0.f, kf, 0.f, 0.f};
@@ -905,19 +916,30 @@ int force_group(const Group& g, double a, bool device_params, bool ini = false) 
                                sub->m));
     prof_end(ctx, ST_Z_SCREEN_FIELD, e, (g.fr_screened.lead ? 1 : 0) + (g.dgp_screened.lead ? 1 : 0),
              sc.m.nb * 3 * H);
-    e = prof_begin(ctx, ST_MESH_YINV);
-    CK(fft_col(N, sc.lead->Cw, 1, true, tw, st, sc.m));
-    prof_end(ctx, ST_MESH_YINV, e, 1, sc.m.nb * 2 * H);
-    e = prof_begin(ctx, ST_X_SCREEN_SOURCE);
-    for (const Group::Sub* sub : {&g.fr_screened, &g.dgp_screened})
-      if (sub->lead)
-        CK(mesh_x_screen_source(N, sub->lead->Cw, sub->lead->rho, sub->lead->Cd, fp_of(sub->lead), tw,
-                                st, sub->m));
-    prof_end(ctx, ST_X_SCREEN_SOURCE, e, (g.fr_screened.lead ? 1 : 0) + (g.dgp_screened.lead ? 1 : 0),
-             sc.m.nb * (2 * H + R));
-    e = prof_begin(ctx, ST_MESH_Y);
-    CK(fft_col(N, sc.lead->Cd, 1, false, tw, st, sc.m));
-    prof_end(ctx, ST_MESH_Y, e, 1, sc.m.nb * 2 * H);
+    if (plane) {
+      // y inverse, x c2r, S = delta eps, x r2c and y forward in one pass per plane
+      e = prof_begin(ctx, ST_X_SCREEN_SOURCE);
+      for (const Group::Sub* sub : {&g.fr_screened, &g.dgp_screened})
+        if (sub->lead)
+          CK(fft_plane_screen(N, sub->lead->Cw, sub->lead->rho, sub->lead->Cd, fp_of(sub->lead), tw, st,
+                              sub->m));
+      prof_end(ctx, ST_X_SCREEN_SOURCE, e, (g.fr_screened.lead ? 1 : 0) + (g.dgp_screened.lead ? 1 : 0),
+               sc.m.nb * (2 * H + R));
+    } else {
+      e = prof_begin(ctx, ST_MESH_YINV);
+      CK(fft_col(N, sc.lead->Cw, 1, true, tw, st, sc.m));
+      prof_end(ctx, ST_MESH_YINV, e, 1, sc.m.nb * 2 * H);
+      e = prof_begin(ctx, ST_X_SCREEN_SOURCE);
+      for (const Group::Sub* sub : {&g.fr_screened, &g.dgp_screened})
+        if (sub->lead)
+          CK(mesh_x_screen_source(N, sub->lead->Cw, sub->lead->rho, sub->lead->Cd, fp_of(sub->lead), tw,
+                                  st, sub->m));
+      prof_end(ctx, ST_X_SCREEN_SOURCE, e, (g.fr_screened.lead ? 1 : 0) + (g.dgp_screened.lead ? 1 : 0),
+               sc.m.nb * (2 * H + R));
+      e = prof_begin(ctx, ST_MESH_Y);
+      CK(fft_col(N, sc.lead->Cd, 1, false, tw, st, sc.m));
+      prof_end(ctx, ST_MESH_Y, e, 1, sc.m.nb * 2 * H);
+    }
     e = prof_begin(ctx, ST_Z_FORCE);
     CK(mesh_z_force(N, sc.lead->Cd, sc.lead->Ck, sc.lead->Cphi, sc.lead->Cphz, fp_of(sc.lead), tw, st,
                     sc.m));

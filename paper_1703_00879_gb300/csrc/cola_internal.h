@@ -279,6 +279,16 @@ cudaError_t fft_plane_r2c(int N, const float* in, float2* out, float scale, floa
 // fy = c2r(yinv(i kfs ky Phi)), fz = c2r(yinv(-i kz Phi)).
 cudaError_t fft_plane_force(int N, const float2* phi, const float2* phiz, float* fx, float* fy, float* fz,
                             float kfs, const float2* tw, cudaStream_t s, Multi m = {});
+// N <= 128: the six LPT field outputs of run_lpt in one pass per (z-plane, field) from
+// lc[0..3] after the z inverse: out = {d_x lc0, d_y lc0, lc1, d_x lc2, d_y lc2, lc3}
+// (d_x, d_y: i kfs kx, i kfs ky), real N^3 fields.
+cudaError_t fft_plane_lpt(int N, const float2* const* lc, float* const* out, float kfs, const float2* tw,
+                          cudaStream_t s, Multi m = {});
+// N <= 128: the screening source in one pass per z-plane: from the screening field w
+// (z already inverse-transformed), y and x inverse, S = delta eps(w) with delta from
+// rho, x (r2c) and y forward into s_out (z not transformed).
+cudaError_t fft_plane_screen(int N, const float2* w_in, const float* rho, float2* s_out, const ForceParams& fp,
+                             const float2* tw, cudaStream_t s, Multi m = {});
 // Runs the transform kernels' bounded mbarrier wait on a phase that never completes
 // (limit `seconds`, 0 < seconds <= 10, on the per-thread default stream; waits for it); *timed_out = 1 when it gave up.
 cudaError_t wait_probe(double seconds, int* timed_out);

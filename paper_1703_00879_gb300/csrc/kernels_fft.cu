@@ -1707,12 +1707,13 @@ __device__ __forceinline__ float screen_eps(float w, float p) {
 // Load hook of the forward transform of the screening x pass: element j of
 // tile row r is S = delta eps(w), w the screening field (the tile value) and
 // delta = rho / rho_bar - 1 from the staged density row (M float2 per row).
-template <int M, int MODEL>
+// GLOBAL: the density rows are read from global memory (read-only path).
+template <int M, int MODEL, bool GLOBAL = false>
 struct ScreenSource {
   const float2* rho;
   float inv_rhobar, p;
   __device__ __forceinline__ float2 operator()(float2 w, int r, int j) const {
-    const float2 rv = rho[r * M + j];
+    const float2 rv = GLOBAL ? __ldg(rho + r * M + j) : rho[r * M + j];
     const float d0 = rv.x * inv_rhobar - 1.f, d1 = rv.y * inv_rhobar - 1.f;
     return make_float2(d0 * screen_eps<MODEL>(w.x, p), d1 * screen_eps<MODEL>(w.y, p));
   }
@@ -1916,30 +1917,80 @@ __device__ __forceinline__ void plane_deriv_y(float2* a, float kfs) {
   __syncthreads();
 }
 
-// One force component's inverse y and x steps for one plane (App. B): from Phi
-// and -i kz Phi after their z inverse, F_x = c2r(yinv(Phi)) with i kfs kx on load,
-// F_y = c2r(yinv(i kfs ky Phi)), F_z = c2r(yinv(-i kz Phi)); kfs = -k_F.  CTA x
-// takes component x % 3 of plane x / 3, so the F_x and F_y CTAs of a plane run
-// side by side and the second read of Phi's plane comes from L2.
+// Gradient components from spectra after their z inverse, one (plane, component)
+// per CTA: component q is c2r(yinv(in[q] times i kfs ky when bit q of dy)) with
+// i kfs kx applied on load when bit q of dx.  The CTAs of one plane are
+// consecutive (x = plane * n + q), so components that share an input spectrum
+// run side by side and the repeated reads of its plane come from L2.
+struct PlaneJobs {
+  const float2* in[6];
+  float* out[6];
+  int n, dx, dy;
+  float kfs;
+};
+
 template <int N>
-__global__ void __launch_bounds__(NT) k_plane_force(const float2* __restrict__ phi, const float2* __restrict__ phiz,
-                                                    float* __restrict__ fx, float* __restrict__ fy,
-                                                    float* __restrict__ fz, float kfs,
-                                                    const float2* __restrict__ twg, Multi m) {
+__global__ void __launch_bounds__(NT) k_plane_grad(PlaneJobs jobs, const float2* __restrict__ twg, Multi m) {
   using C = PlaneCfg<N>;
   extern __shared__ __align__(128) float2 sm[];
   float2* tw = sm;
   float2* a = sm + N;
-  const int q = blockIdx.x % 3, z = blockIdx.x / 3;
+  const int z = blockIdx.x / jobs.n, q = blockIdx.x - z * jobs.n;
   const int64_t by = shift_of(m, blockIdx.y), off = (int64_t)z * N * N;
+  const float2* in = jobs.in[0];
+  float* out = jobs.out[0];
+#pragma unroll
+  for (int i = 1; i < 6; ++i)  // selects, not an indexed copy of the parameters
+    if (i == q) {
+      in = jobs.in[i];
+      out = jobs.out[i];
+    }
   load_tw(tw, twg, N);
-  stage_complex_plane<N>(a, moved(q == 2 ? phiz : phi, by), z);
+  stage_complex_plane<N>(a, moved(in, by), z);
   cp_async_commit();
   cp_async_wait<0>();
   __syncthreads();
-  if (q == 1) plane_deriv_y<N>(a, kfs);
+  if ((jobs.dy >> q) & 1) plane_deriv_y<N>(a, jobs.kfs);
   plane_yinv<N>(a, tw);
-  plane_xc2r<N>(a, tw, q == 0 ? kfs : 0.f, moved(q == 0 ? fx : q == 1 ? fy : fz, by) + off);
+  plane_xc2r<N>(a, tw, ((jobs.dx >> q) & 1) ? jobs.kfs : 0.f, moved(out, by) + off);
+}
+
+// Screening source of plane blockIdx.x in one pass (Sec. 6.1, Sec. 6.2): the
+// screening field's plane after its z inverse is transformed back along y and x
+// (c2r), S = delta eps(w) is formed as the forward x transform loads it (delta
+// read from the density plane in global memory), and the forward x (r2c) and y
+// steps write S's plane of the interleaved half spectrum; the z pass follows.
+template <int N, int MODEL>
+__global__ void __launch_bounds__(NT) k_plane_screen(const float2* __restrict__ w_in,
+                                                     const float* __restrict__ rho,
+                                                     float2* __restrict__ s_out, ForceParams fp,
+                                                     const float2* __restrict__ twg, Multi m) {
+  using C = PlaneCfg<N>;
+  constexpr int M = C::M;
+  extern __shared__ __align__(128) float2 sm[];
+  float2* tw = sm;
+  float2* a = sm + N;
+  const int z = blockIdx.x;
+  const int64_t by = shift_of(m, blockIdx.y);
+  resolve(fp, by);
+  load_tw(tw, twg, N);
+  stage_complex_plane<N>(a, moved(w_in, by), z);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  plane_yinv<N>(a, tw);
+  row_c2r_combine<N, N>(a, tw, 0.f);
+  fft_rowtile<M, N, C::CW, NT, true, 2>(a, tw);
+  const ScreenSource<M, MODEL, true> src{reinterpret_cast<const float2*>(moved(rho, by) + (int64_t)z * N * N),
+                                         fp.inv_rhobar, MODEL == 1 ? fp.fr_thr : fp.dgp_coef};
+  fft_rowtile<M, N, C::CW, NT, false, 2, ScreenSource<M, MODEL, true>>(a, tw, src);
+  plane_r2c_split<N>(a, tw);
+  constexpr int64_t P = half_pitch(N);
+  float2* g = moved(s_out, by) + hrow(z, 0, N, P);
+#pragma unroll 1
+  for (int c0 = 0; c0 < C::CW; c0 += C::TWCOL)
+    fft_tile<N, C::TWCOL, C::CW, NT, false, 1, TileLoad, ColOut>(
+        a + c0, tw, TileLoad{}, ColOut{g + hcol(c0), 4 * P, 2 * P, C::M + 1 - c0});
 }
 
 // ---------------------------------------------------------------- launch helpers
@@ -2398,25 +2449,65 @@ cudaError_t fft_plane_r2c(int Nv, const float* in, float2* out, float scale, flo
 }
 
 template <int N>
-static cudaError_t launch_plane_force(const float2* phi, const float2* phiz, float* fx, float* fy, float* fz,
-                                      float kfs, const float2* tw, cudaStream_t s, Multi m) {
+static cudaError_t launch_plane_grad(const PlaneJobs& jobs, const float2* tw, cudaStream_t s, Multi m) {
   if constexpr (N > 128) {
     return cudaErrorInvalidValue;
   } else {
     constexpr size_t sm = PlaneCfg<N>::smem;
-    auto k = k_plane_force<N>;
+    auto k = k_plane_grad<N>;
     if (sm > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
     }
-    k<<<dim3(3 * N, m.nb), NT, sm, s>>>(phi, phiz, fx, fy, fz, kfs, tw, m);
+    k<<<dim3(jobs.n * N, m.nb), NT, sm, s>>>(jobs, tw, m);
     return cudaGetLastError();
   }
 }
 
+static cudaError_t plane_grad(int Nv, const PlaneJobs& jobs, const float2* tw, cudaStream_t s, Multi m) {
+  if (jobs.n < 1 || jobs.n > 6) return cudaErrorInvalidValue;
+  COLA_SWITCH_N(Nv, return launch_plane_grad<N>(jobs, tw, s, m));
+  return cudaSuccess;
+}
+
 cudaError_t fft_plane_force(int Nv, const float2* phi, const float2* phiz, float* fx, float* fy, float* fz,
                             float kfs, const float2* tw, cudaStream_t s, Multi m) {
-  COLA_SWITCH_N(Nv, return launch_plane_force<N>(phi, phiz, fx, fy, fz, kfs, tw, s, m));
+  const PlaneJobs jobs{{phi, phi, phiz}, {fx, fy, fz}, 3, 1, 2, kfs};
+  return plane_grad(Nv, jobs, tw, s, m);
+}
+
+cudaError_t fft_plane_lpt(int Nv, const float2* const* lc, float* const* out, float kfs, const float2* tw,
+                          cudaStream_t s, Multi m) {
+  const PlaneJobs jobs{{lc[0], lc[0], lc[1], lc[2], lc[2], lc[3]},
+                       {out[0], out[1], out[2], out[3], out[4], out[5]},
+                       6,
+                       0b001001,
+                       0b010010,
+                       kfs};
+  return plane_grad(Nv, jobs, tw, s, m);
+}
+
+template <int N>
+static cudaError_t launch_plane_screen(const float2* w_in, const float* rho, float2* s_out,
+                                       const ForceParams& fp, const float2* tw, cudaStream_t s, Multi m) {
+  if constexpr (N > 128) {
+    return cudaErrorInvalidValue;
+  } else {
+    constexpr size_t sm = PlaneCfg<N>::smem;
+    auto k = fp.model == 1 ? k_plane_screen<N, 1> : k_plane_screen<N, 2>;
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    k<<<dim3(N, m.nb), NT, sm, s>>>(w_in, rho, s_out, fp, tw, m);
+    return cudaGetLastError();
+  }
+}
+
+cudaError_t fft_plane_screen(int Nv, const float2* w_in, const float* rho, float2* s_out, const ForceParams& fp,
+                             const float2* tw, cudaStream_t s, Multi m) {
+  if (fp.model != 1 && fp.model != 2) return cudaErrorInvalidValue;
+  COLA_SWITCH_N(Nv, return launch_plane_screen<N>(w_in, rho, s_out, fp, tw, s, m));
   return cudaSuccess;
 }
 
