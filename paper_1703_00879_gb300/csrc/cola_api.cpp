@@ -120,7 +120,8 @@ struct cola_batch {
     void* shifts = nullptr;                // device shift arrays the graph's launches read
                                            // (through the first context's allocator, on cap_st)
   };
-  std::map<std::tuple<int, int, int, int, int>, Graph> graphs;  // plan -> graph serving every step
+  std::map<std::tuple<int, int, int, int, int, int>, Graph> graphs;  // (plan, launch sequence) -> graph
+                                                                     // serving every step
   double* pk_acc = nullptr;                // [n][3 * kMaxBins] + n shifts (batch P(k)), through
                                            // the first context's allocator, on st
   std::string err;
@@ -1222,36 +1223,59 @@ bool fused_steps_ok(const cola_ctx* ctx, int K) {
   return K >= 2 && !ctx->lpt_fast && !ctx->cfg.seed_precision && ctx->lrk[0] != nullptr;
 }
 
-int enqueue_steps_fused(cola_ctx* ctx, int K) {
-  const Group g = single_group(ctx);
+// The boundary between step n and step n + 1 of every simulation of g in the
+// fused form: step n+1's LPT fields (table row 2 + device step n; drift fields
+// into lr[0..2], kick fields into slot 1 - cur), the kick of step n (its kick
+// fields in slot cur) with the drift + deposit of step n + 1 in one pass, the
+// device step advance and the force of step n + 1.
+int enqueue_group_mid(const Group& g, int n, int cur) {
+  cola_ctx* ctx = g.lead;
   const Multi m = g.all;
   const PartParams pp = part_params(ctx);
   const double Pb = (double)ctx->P, Mb = (double)ctx->M;
+  bool zeroed = false;
+  CHECK_RC(run_lpt(ctx, 0, 2, true, m, ctx->rho, ctx->M, &zeroed, 1 - cur));
+  if (!zeroed) {
+    cudaEvent_t e = prof_begin(ctx, ST_RHO_ZERO);
+    CK(zero_f32(ctx->rho, ctx->M, ctx->st, m));
+    prof_end(ctx, ST_RHO_ZERO, e, 1, m.nb * 4.0 * Mb);
+  }
+  const float* const* ka = cur ? ctx->lrk : ctx->lr + 3;
+  cudaEvent_t e = prof_begin(ctx, ST_KICK_DRIFT_DEPOSIT);
+  CK(part_kick_drift_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2], ka[0], ka[1],
+                             ka[2], ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->F[0], ctx->F[1], ctx->F[2], ctx->rho,
+                             ctx->hdr, ctx->P, ctx->st, m));
+  prof_end(ctx, ST_KICK_DRIFT_DEPOSIT, e, 1, m.nb * (72.0 * Pb + 20.0 * Mb));
+  CK(step_advance(ctx->hdr, ctx->st, m));
+  return force_group(g, ctx->a[n + 2], true);
+}
+
+int enqueue_steps_fused(cola_ctx* ctx, int K) {
+  const Group g = single_group(ctx);
   CHECK_RC(enqueue_group_step(g, ctx->step, true));  // LPT, drift + deposit, force of the first step
   int cur = 0;
   for (int i = 1; i < K; ++i) {
-    // step n+1's LPT fields (table row 2 + device step n): drift into lr[0..2], kick into the other slot
-    bool zeroed = false;
-    CHECK_RC(run_lpt(ctx, 0, 2, true, m, ctx->rho, ctx->M, &zeroed, 1 - cur));
-    if (!zeroed) {
-      cudaEvent_t e = prof_begin(ctx, ST_RHO_ZERO);
-      CK(zero_f32(ctx->rho, ctx->M, ctx->st, m));
-      prof_end(ctx, ST_RHO_ZERO, e, 1, m.nb * 4.0 * Mb);
-    }
-    const float* const* ka = cur ? ctx->lrk : ctx->lr + 3;
-    cudaEvent_t e = prof_begin(ctx, ST_KICK_DRIFT_DEPOSIT);
-    CK(part_kick_drift_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2], ka[0],
-                               ka[1], ka[2], ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->F[0], ctx->F[1],
-                               ctx->F[2], ctx->rho, ctx->hdr, ctx->P, ctx->st, m));
-    prof_end(ctx, ST_KICK_DRIFT_DEPOSIT, e, 1, m.nb * (72.0 * Pb + 20.0 * Mb));
-    CK(step_advance(ctx->hdr, ctx->st, m));
+    CHECK_RC(enqueue_group_mid(g, ctx->step, cur));
     ctx->step += 1;
     cur = 1 - cur;
-    CHECK_RC(force_group(g, ctx->a[ctx->step + 1], true));
   }
   CHECK_RC(enqueue_group_tail(g, cur));
   ctx->step += 1;
   return COLA_OK;
+}
+
+// Launch sequences a batch graph holds: a whole step, or the pieces of a run of
+// fused steps (the first step's head; a boundary with the kick fields of the
+// ending step in slot 0 or 1; the last step's tail from slot 0 or 1).
+enum BatchKind { BK_STEP, BK_HEAD, BK_MID0, BK_MID1, BK_TAIL0, BK_TAIL1 };
+
+int enqueue_kind(const Group& g, int n, int kind) {
+  switch (kind) {
+    case BK_STEP: return enqueue_group_step(g, n);
+    case BK_HEAD: return enqueue_group_step(g, n, true);
+    case BK_MID0: case BK_MID1: return enqueue_group_mid(g, n, kind - BK_MID0);
+    default: return enqueue_group_tail(g, kind - BK_TAIL0);
+  }
 }
 
 }  // namespace
@@ -1947,7 +1971,7 @@ static void plan_groups(const std::vector<cola_ctx*>& ctxs, int group, std::vect
 
 // Captures one step of every context under plan p (the step index comes from
 // each context's device header, so the graph serves every step).
-static int batch_capture(cola_batch* b, int n, const cola_batch_plan& p, cola_batch::Graph* out) {
+static int batch_capture(cola_batch* b, int n, const cola_batch_plan& p, int kind, cola_batch::Graph* out) {
   std::vector<GroupPlan> groups;
   std::vector<int64_t> hsh;
   plan_groups(b->ctx, p.group, groups, hsh);
@@ -1979,7 +2003,7 @@ static int batch_capture(cola_batch* b, int n, const cola_batch_plan& p, cola_ba
     const bool prof = lead->prof;
     lead->st = b->chain_st[j % C];
     lead->prof = false;
-    rc = enqueue_group_step(groups[j].g, n);
+    rc = enqueue_kind(groups[j].g, n, kind);
     lead->st = saved;
     lead->prof = prof;
     if (rc != COLA_OK) b->err = lead->err;
@@ -2005,12 +2029,12 @@ static int batch_capture(cola_batch* b, int n, const cola_batch_plan& p, cola_ba
   return COLA_OK;
 }
 
-static int batch_graph(cola_batch* b, const cola_batch_plan& p, cudaGraphExec_t* ex) {
-  const auto key = std::make_tuple(p.group, p.chains, p.grid_cap, p.deposit_box, p.gather_box);
+static int batch_graph(cola_batch* b, const cola_batch_plan& p, cudaGraphExec_t* ex, int kind = BK_STEP) {
+  const auto key = std::make_tuple(p.group, p.chains, p.grid_cap, p.deposit_box, p.gather_box, kind);
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
     cola_batch::Graph g;
-    int rc = batch_capture(b, b->step, p, &g);
+    int rc = batch_capture(b, b->step, p, kind, &g);
     if (rc != COLA_OK) {
       if (g.shifts) dev_free_on(b->ctx[0], g.shifts, b->cap_st);
       return rc;
@@ -2024,7 +2048,7 @@ static int batch_graph(cola_batch* b, const cola_batch_plan& p, cudaGraphExec_t*
 // Profiling: when the first context has stage timing enabled, the groups of
 // the plan are launched directly (no graph) one after another on the batch's
 // stream, so the first group's stage events cover its multi-simulation launches.
-static int batch_eager(cola_batch* b, const cola_batch_plan& p, int n) {
+static int batch_eager(cola_batch* b, const cola_batch_plan& p, int n, int kind) {
   std::vector<GroupPlan> groups;
   std::vector<int64_t> hsh;
   plan_groups(b->ctx, p.group, groups, hsh);
@@ -2044,7 +2068,7 @@ static int batch_eager(cola_batch* b, const cola_batch_plan& p, int n) {
     lead->st = b->cap_st;
     set_grid_cap(p.grid_cap);
     set_particle_plan(p.deposit_box, p.gather_box);
-    rc = enqueue_group_step(gp.g, n);
+    rc = enqueue_kind(gp.g, n, kind);
     set_grid_cap(0);
     set_particle_plan(0, 0);
     lead->st = saved;
@@ -2057,22 +2081,25 @@ static int batch_eager(cola_batch* b, const cola_batch_plan& p, int n) {
   return rc == COLA_OK ? COLA_OK : bfail(b, rc, "batch step: " + b->err);
 }
 
-static int batch_launch(cola_batch* b, const cola_batch_plan& p) {
+// One launch sequence of `kind` (a whole step by default); every kind but the
+// head of a fused run ends one step.
+static int batch_launch(cola_batch* b, const cola_batch_plan& p, int kind = BK_STEP) {
   const int n = b->step;
   const bool eager = b->ctx[0]->prof;
   cudaGraphExec_t ex = nullptr;
-  if (!eager) CHECK_RC(batch_graph(b, p, &ex));
+  if (!eager) CHECK_RC(batch_graph(b, p, &ex, kind));
   // ordered after earlier work on the caller's stream, and before later work on it
   BCK(cudaEventRecord(b->ev_in, b->st));
   BCK(cudaStreamWaitEvent(b->cap_st, b->ev_in, 0));
-  if (eager) CHECK_RC(batch_eager(b, p, n));
+  if (eager) CHECK_RC(batch_eager(b, p, n, kind));
   else BCK(cudaGraphLaunch(ex, b->cap_st));
   BCK(cudaEventRecord(b->ev_out, b->cap_st));
   BCK(cudaStreamWaitEvent(b->st, b->ev_out, 0));
-  b->step = n + 1;
+  const int n1 = kind == BK_HEAD ? n : n + 1;
+  b->step = n1;
   for (cola_ctx* ctx : b->ctx) {
-    ctx->step = n + 1;
-    ctx->hh.step = n + 1;
+    ctx->step = n1;
+    ctx->hh.step = n1;
   }
   // later per-context calls on the contexts' own streams see the step
   for (cola_ctx* ctx : b->ctx)
@@ -2142,8 +2169,23 @@ int cola_batch_step(cola_batch* b, int32_t nsteps) {
   const int total = b->ctx[0]->cfg.nsteps;
   if (nsteps < 0) nsteps = total - b->step;
   if (b->step + nsteps > total) return bfail(b, COLA_EINVAL, "past the last step");
-  for (cola_ctx* c : b->ctx) c->kslot = 0;  // batch steps keep the kick fields in lr[3..5]
-  for (int i = 0; i < nsteps; ++i) CHECK_RC(batch_launch(b, b->plan));
+  for (cola_ctx* c : b->ctx) c->kslot = 0;  // single batch steps keep the kick fields in lr[3..5]
+  // two or more steps with the direct particle kernels: the kick of each step but
+  // the last and the drift + deposit of the next in one pass (enqueue_group_mid)
+  bool fused = nsteps >= 2 && b->plan.deposit_box == 0 && b->plan.gather_box == 0;
+  for (const cola_ctx* c : b->ctx) fused = fused && fused_steps_ok(c, nsteps);
+  if (!fused) {
+    for (int i = 0; i < nsteps; ++i) CHECK_RC(batch_launch(b, b->plan));
+    return COLA_OK;
+  }
+  CHECK_RC(batch_launch(b, b->plan, BK_HEAD));
+  int cur = 0;
+  for (int i = 1; i < nsteps; ++i) {
+    CHECK_RC(batch_launch(b, b->plan, cur ? BK_MID1 : BK_MID0));
+    cur = 1 - cur;
+  }
+  CHECK_RC(batch_launch(b, b->plan, cur ? BK_TAIL1 : BK_TAIL0));
+  for (cola_ctx* c : b->ctx) c->kslot = cur;  // the last step's kick fields
   return COLA_OK;
 }
 

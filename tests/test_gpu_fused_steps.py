@@ -53,3 +53,36 @@ def test_fused_steps_then_batch_step_use_the_right_kick_fields(pkg):
         pkg.step_many([s])
         b = s.export(pkg.COLA_F_LPT_ACC).astype(np.float64)
     np.testing.assert_allclose(b, a[pkg.COLA_F_LPT_ACC], rtol=0, atol=1e-6 * np.max(np.abs(b)))
+
+
+def _batch_run(pkg, runs, calls):
+    sims = [pkg.Simulation(r) for r in runs]
+    with pkg.Batch(sims) as b:
+        for k in calls:
+            b.step(k)
+        k, P, nm = b.pk()
+    out = []
+    for s in sims:
+        out.append({w: s.export(w).astype(np.float64) for w in (pkg.COLA_F_DISP, pkg.COLA_F_DV,
+                                                                pkg.COLA_F_LPT_ACC)})
+        s.close()
+    return out, P
+
+
+@pytest.mark.parametrize("split", [[6], [2, 1, 3]], ids=["one_call", "three_calls"])
+def test_fused_batch_steps_equal_single_batch_steps(pkg, split):
+    """A batch of the ensemble's model set stepped K at a time (fused boundaries, kick fields in
+    alternating slots) against the same batch stepped once per call: every member's state and
+    last kick fields agree to FP32 rounding, P(k) within 1e-5."""
+    from workloads import ENSEMBLE_MODELS, ensemble_run
+    runs = [ensemble_run(seed, Np=32, Nmesh=64, Lbox=64.0, nsteps=6) for seed in range(len(ENSEMBLE_MODELS))]
+    ref, Pref = _batch_run(pkg, runs, [1] * 6)
+    got, P = _batch_run(pkg, runs, split)
+    for r, a, b in zip(runs, ref, got):
+        cell = r.Lbox / r.Nmesh
+        assert np.max(np.abs(b[pkg.COLA_F_DISP] - a[pkg.COLA_F_DISP])) <= 1e-4 * cell
+        assert np.max(np.abs(b[pkg.COLA_F_DV] - a[pkg.COLA_F_DV])) <= 1e-4 * np.max(np.abs(a[pkg.COLA_F_DV]))
+        np.testing.assert_allclose(b[pkg.COLA_F_LPT_ACC], a[pkg.COLA_F_LPT_ACC], rtol=0,
+                                   atol=1e-6 * np.max(np.abs(a[pkg.COLA_F_LPT_ACC])))
+    ok = Pref > 0
+    assert np.max(np.abs(P[ok] / Pref[ok] - 1)) <= 1e-5
