@@ -820,8 +820,10 @@ int run_lpt(cola_ctx* ctx, int vel, int row0, bool add_step, Multi m = {}, float
     float* const* ko = kslot ? ctx->lrk : ctx->lr + 3;
     const float2* in4[4] = {ctx->lc[0], ctx->lc[1], ctx->lc[2], ctx->lc[3]};
     float* out6[6] = {ctx->lr[0], ctx->lr[1], ctx->lr[2], ko[0], ko[1], ko[2]};
-    CK(fft_plane_lpt(N, in4, out6, kf, ctx->tw_np, st, m));
-    prof_end(ctx, ST_LPT_X, e, 1, m.nb * (4 * H + 6 * R));
+    bool zp = false;
+    CK(fft_plane_lpt(N, in4, out6, kf, ctx->tw_np, st, m, zd ? nullptr : zero_dst, zero_floats, &zp));
+    if (zeroed) *zeroed = zd || zp;
+    prof_end(ctx, ST_LPT_X, e, 1, m.nb * (4 * H + 6 * R + (zp ? 4.0 * (double)zero_floats : 0.0)));
     ctx->have_lpt = true;
     return COLA_OK;
   }

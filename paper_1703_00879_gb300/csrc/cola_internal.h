@@ -281,9 +281,12 @@ cudaError_t fft_plane_force(int N, const float2* phi, const float2* phiz, float*
                             float kfs, const float2* tw, cudaStream_t s, Multi m = {});
 // N <= 128: the six LPT field outputs of run_lpt in one pass per (z-plane, field) from
 // lc[0..3] after the z inverse: out = {d_x lc0, d_y lc0, lc1, d_x lc2, d_y lc2, lc3}
-// (d_x, d_y: i kfs kx, i kfs ky), real N^3 fields.
+// (d_x, d_y: i kfs kx, i kfs ky), real N^3 fields.  With zero_dst, the launch also clears
+// zero_dst[0, zero_floats) of every simulation (*zeroed = true) when zero_floats is a
+// multiple of 4 and zero_dst is 16-byte aligned.
 cudaError_t fft_plane_lpt(int N, const float2* const* lc, float* const* out, float kfs, const float2* tw,
-                          cudaStream_t s, Multi m = {});
+                          cudaStream_t s, Multi m = {}, float* zero_dst = nullptr, int64_t zero_floats = 0,
+                          bool* zeroed = nullptr);
 // N <= 128: the screening source in one pass per z-plane: from the screening field w
 // (z already inverse-transformed), y and x inverse, S = delta eps(w) with delta from
 // rho, x (r2c) and y forward into s_out (z not transformed).

@@ -1927,6 +1927,9 @@ struct PlaneJobs {
   float* out[6];
   int n, dx, dy;
   float kfs;
+  float* zdst = nullptr;  // optional: zdst[0, zfloats) of each simulation is cleared, zchunk
+  int64_t zfloats = 0;    // floats (a multiple of 4) per CTA, by 16-byte stores
+  int64_t zchunk = 0;
 };
 
 template <int N>
@@ -1948,6 +1951,11 @@ __global__ void __launch_bounds__(NT) k_plane_grad(PlaneJobs jobs, const float2*
   load_tw(tw, twg, N);
   stage_complex_plane<N>(a, moved(in, by), z);
   cp_async_commit();
+  if (jobs.zdst) {  // this CTA's share of the zero fill while its plane lands
+    const int64_t lo = (int64_t)blockIdx.x * jobs.zchunk, hi = min(lo + jobs.zchunk, jobs.zfloats);
+    float4* d = reinterpret_cast<float4*>(moved(jobs.zdst, by));
+    for (int64_t i = lo / 4 + threadIdx.x; i < hi / 4; i += NT) d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   cp_async_wait<0>();
   __syncthreads();
   if ((jobs.dy >> q) & 1) plane_deriv_y<N>(a, jobs.kfs);
@@ -2477,14 +2485,24 @@ cudaError_t fft_plane_force(int Nv, const float2* phi, const float2* phiz, float
 }
 
 cudaError_t fft_plane_lpt(int Nv, const float2* const* lc, float* const* out, float kfs, const float2* tw,
-                          cudaStream_t s, Multi m) {
-  const PlaneJobs jobs{{lc[0], lc[0], lc[1], lc[2], lc[2], lc[3]},
-                       {out[0], out[1], out[2], out[3], out[4], out[5]},
-                       6,
-                       0b001001,
-                       0b010010,
-                       kfs};
-  return plane_grad(Nv, jobs, tw, s, m);
+                          cudaStream_t s, Multi m, float* zero_dst, int64_t zero_floats, bool* zeroed) {
+  PlaneJobs jobs{{lc[0], lc[0], lc[1], lc[2], lc[2], lc[3]},
+                 {out[0], out[1], out[2], out[3], out[4], out[5]},
+                 6,
+                 0b001001,
+                 0b010010,
+                 kfs};
+  const bool zf = zero_dst && zero_floats > 0 && (zero_floats % 4) == 0 &&
+                  (reinterpret_cast<uintptr_t>(zero_dst) & 15) == 0;
+  if (zf) {
+    const int64_t ctas = (int64_t)jobs.n * Nv;
+    jobs.zdst = zero_dst;
+    jobs.zfloats = zero_floats;
+    jobs.zchunk = (zero_floats + 4 * ctas - 1) / (4 * ctas) * 4;
+  }
+  const cudaError_t e = plane_grad(Nv, jobs, tw, s, m);
+  if (e == cudaSuccess && zeroed) *zeroed = zf;
+  return e;
 }
 
 template <int N>
