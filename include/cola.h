@@ -33,9 +33,11 @@
  *     so creating, stepping and freeing contexts never synchronises the
  *     device.  Buffers passed in by the caller stay owned by the caller.
  *   - Allocator contract: alloc(bytes, stream, user) returns memory usable on
- *     `stream`; free(ptr, stream, user) releases it in stream order (later
- *     work on `stream` may reuse it, earlier work still sees it), as PyTorch's
- *     caching allocator and cudaFreeAsync do.
+ *     `stream`, aligned to 256 bytes as cudaMalloc's is (cola_init releases a
+ *     misaligned block and fails with COLA_EINVAL); free(ptr, stream, user)
+ *     releases it in stream order (later work on `stream` may reuse it,
+ *     earlier work still sees it), as PyTorch's caching allocator and
+ *     cudaFreeAsync do.
  *   - Streams: all device work is enqueued on the stream given to cola_init
  *     (borrowed, never destroyed).  Calls that take or return HOST buffers
  *     wait on the host for that stream before returning (bounded by

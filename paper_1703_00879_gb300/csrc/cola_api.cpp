@@ -1356,6 +1356,11 @@ int cola_init(const cola_config* cfg, cola_alloc_fn alloc, cola_free_fn free_fn,
     void* slab = dev_alloc(ctx, lay.size);
     if (!slab) {
       rc = fail(ctx, COLA_ENOMEM, "device allocation of " + std::to_string(lay.size) + " bytes failed");
+    } else if (reinterpret_cast<uintptr_t>(slab) & 255) {
+      // the kernels' 16-byte vector accesses, bulk copies and tensor maps rely on
+      // every buffer starting on a 256-byte boundary (the slab's offsets keep it)
+      dev_free(ctx, slab);
+      rc = fail(ctx, COLA_EINVAL, "the allocator returned a block not aligned to 256 bytes");
     } else {
       ctx->allocs.push_back(slab);
       lay.place(static_cast<char*>(slab));

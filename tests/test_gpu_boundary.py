@@ -220,6 +220,32 @@ def test_failing_allocator_gives_enomem_and_leaks_nothing(pkg):
     assert cb.live == {}
 
 
+def test_misaligned_allocator_block_is_refused(pkg):
+    """An allocator whose block is not on a 256-byte boundary: cola_init releases it and fails
+    with COLA_EINVAL before any kernel touches it (the kernels' vector accesses need the
+    alignment)."""
+    import torch
+    L = pkg.lib()
+    st = torch.cuda.current_stream()
+    dev = torch.cuda.current_device()
+    live = {}
+
+    def _alloc(nbytes, stream, user):
+        base = torch.cuda.caching_allocator_alloc(int(nbytes) + 256, dev, int(stream or 0))
+        live[int(base) + 16] = int(base)
+        return int(base) + 16
+
+    def _free(ptr, stream, user):
+        torch.cuda.caching_allocator_delete(live.pop(int(ptr)))
+
+    cbs = (pkg.ALLOC_FN(_alloc), pkg.FREE_FN(_free))
+    cfg = pkg.make_config(SMALL_F5.with_(nsteps=3))
+    h = ctypes.c_void_p()
+    rc = L.cola_init(ctypes.byref(cfg), cbs[0], cbs[1], None, ctypes.c_void_p(st.cuda_stream), ctypes.byref(h))
+    torch.cuda.synchronize()
+    assert rc == pkg.COLA_EINVAL and not h.value and live == {}
+
+
 def test_check_state_counts_non_finite_values(pkg):
     """cola_check_state: 0 for a healthy run; a NaN and an Inf planted in the imported state are
     counted, and the next step's residual acceleration is checked as well."""
