@@ -190,7 +190,12 @@ int cola_step(cola_ctx* ctx, int32_t nsteps);
 /* Particle positions (wrapped into [0, Lbox), [Np^3][3] floats, Mpc/h) and
  * peculiar velocities ([Np^3][3] floats, km/s) at the current scale factor,
  * written to caller-owned buffers on the host or device; either pointer may
- * be NULL.  Host buffers wait for the stream (bounded by cola_set_wait_limit). */
+ * be NULL.  Host buffers wait for the stream (bounded by cola_set_wait_limit).
+ * Page-locked host buffers that the device can address (cudaHostAlloc, or
+ * registered and mapped) are written by the snapshot kernel directly, without
+ * a device staging buffer or a copy; other host buffers are staged and copied.
+ * If the wait gives up (COLA_ETIMEOUT) the device may still be writing the
+ * buffers: keep them until the stream has drained. */
 int cola_snapshot(cola_ctx* ctx, float* pos, float* vel, int32_t where);
 
 /* Matter power spectrum of the current particles: CIC on the Nmesh mesh,

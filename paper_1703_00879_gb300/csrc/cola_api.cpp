@@ -1096,6 +1096,18 @@ int finish_ic(cola_ctx* ctx, bool potentials) {
   return COLA_OK;
 }
 
+// The device address of page-locked host memory at p (registered or allocated by
+// cudaHostAlloc and mapped, as every such allocation is with unified addressing),
+// or nullptr for other memory.
+void* mapped_host(void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // Device-to-host copy into caller memory, synchronous for the caller: large
 // copies without a wait limit go through the download ring, the rest through
 // cudaMemcpyAsync and a (bounded) wait.
@@ -1556,15 +1568,20 @@ int cola_snapshot(cola_ctx* ctx, float* pos, float* vel, int32_t where) {
                      ctx->lr[0], ctx->lr[1], ctx->lr[2], vscale, pos, vel, ctx->P, ctx->st, mix));
     return COLA_OK;
   }
-  // host: stage through the (step-scratch) mesh force buffers when they are big enough
-  Temp tp(ctx, pos ? bytes : 0), tv(ctx, vel ? bytes : 0);
-  if ((pos && !tp.p) || (vel && !tv.p)) return fail(ctx, COLA_ENOMEM, "snapshot staging allocation failed");
+  // host: page-locked caller buffers the device can address are written by the
+  // snapshot kernel itself; the others are staged on the device and copied
+  float* mp = pos ? static_cast<float*>(mapped_host(pos)) : nullptr;
+  float* mv = vel ? static_cast<float*>(mapped_host(vel)) : nullptr;
+  Temp tp(ctx, pos && !mp ? bytes : 0), tv(ctx, vel && !mv ? bytes : 0);
+  if ((pos && !mp && !tp.p) || (vel && !mv && !tv.p))
+    return fail(ctx, COLA_ENOMEM, "snapshot staging allocation failed");
   CK(part_snapshot(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
-                   ctx->lr[0], ctx->lr[1], ctx->lr[2], vscale, static_cast<float*>(tp.p),
-                   static_cast<float*>(tv.p), ctx->P, ctx->st, mix));
-  if (pos) CHECK_RC(copy_to_host(ctx, pos, tp.p, bytes));
-  if (vel) CHECK_RC(copy_to_host(ctx, vel, tv.p, bytes));
-  return COLA_OK;
+                   ctx->lr[0], ctx->lr[1], ctx->lr[2], vscale, pos ? (mp ? mp : static_cast<float*>(tp.p)) : nullptr,
+                   vel ? (mv ? mv : static_cast<float*>(tv.p)) : nullptr, ctx->P, ctx->st, mix));
+  if (pos && !mp) CHECK_RC(copy_to_host(ctx, pos, tp.p, bytes));
+  if (vel && !mv) CHECK_RC(copy_to_host(ctx, vel, tv.p, bytes));
+  const bool copied = (pos && !mp) || (vel && !mv);  // a copy above already waited for the kernel
+  return copied ? COLA_OK : host_wait(ctx);
 }
 
 // Deposit, forward transform and binning of the current particles into

@@ -816,40 +816,59 @@ __global__ void __launch_bounds__(NTP, 2) k_gather_kick_box(
   }
 }
 
+// The [P][3] outputs leave through shared memory as whole 16-byte pieces (a CTA's
+// 256 particles are 3 KB of each array): the outputs may be page-locked host
+// memory written across the chip-to-host link, where partial lines cost most.
 __global__ void __launch_bounds__(NTP) k_snapshot(
     PartParams pp, const float* __restrict__ sx, const float* __restrict__ sy,
     const float* __restrict__ sz, const float* __restrict__ vx, const float* __restrict__ vy,
     const float* __restrict__ vz, const float* __restrict__ lx, const float* __restrict__ ly,
     const float* __restrict__ lz, float vscale, float* __restrict__ pos,
     float* __restrict__ vel, int64_t P, LptMix mix, double dq, double invL) {
-  const int64_t p = (int64_t)blockIdx.x * NTP + threadIdx.x;
-  if (p >= P) return;
-  int li[3];
-  lattice(pp, p, li[0], li[1], li[2]);
-  const float sv[3] = {sx[p], sy[p], sz[p]};
-  if (pos) {
-    // x = q + s wrapped into [0, L) in double precision; dq = L / Np and 1/L come from
-    // the host (no double division per particle: this GPU's double rate is low)
-    const double L = pp.L;
+  __shared__ __align__(16) float st[2][3 * NTP];
+  const int64_t base = (int64_t)blockIdx.x * NTP, p = base + threadIdx.x;
+  if (p < P) {
+    int li[3];
+    lattice(pp, p, li[0], li[1], li[2]);
+    const float sv[3] = {sx[p], sy[p], sz[p]};
+    if (pos) {
+      // x = q + s wrapped into [0, L) in double precision; dq = L / Np and 1/L come from
+      // the host (no double division per particle: this GPU's double rate is low)
+      const double L = pp.L;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      double x = (double)li[d] * dq + (double)sv[d];
-      x -= L * floor(x * invL);
-      if (x < 0.0) x += L;
-      if (x >= L) x -= L;
-      pos[p * 3 + d] = (float)x;
+      for (int d = 0; d < 3; ++d) {
+        double x = (double)li[d] * dq + (double)sv[d];
+        x -= L * floor(x * invL);
+        if (x < 0.0) x += L;
+        if (x >= L) x -= L;
+        st[0][3 * threadIdx.x + d] = (float)x;
+      }
+    }
+    if (vel) {
+      float l[3] = {lx[p], ly[p], lz[p]};
+      if (mix.on) {  // dPsi/dtau = dD1 Psi1 + dD2 Psi2
+        const float4 cf = mix_coeffs(mix, 0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) l[d] = cf.x * l[d] + cf.y * mix.q2[d][p];
+      }
+      st[1][3 * threadIdx.x + 0] = (vx[p] + l[0]) * vscale;
+      st[1][3 * threadIdx.x + 1] = (vy[p] + l[1]) * vscale;
+      st[1][3 * threadIdx.x + 2] = (vz[p] + l[2]) * vscale;
     }
   }
-  if (vel) {
-    float l[3] = {lx[p], ly[p], lz[p]};
-    if (mix.on) {  // dPsi/dtau = dD1 Psi1 + dD2 Psi2
-      const float4 cf = mix_coeffs(mix, 0);
+  __syncthreads();
+  const int n = (int)(3 * (P - base < NTP ? P - base : NTP));  // floats of this CTA per output
 #pragma unroll
-      for (int d = 0; d < 3; ++d) l[d] = cf.x * l[d] + cf.y * mix.q2[d][p];
+  for (int k = 0; k < 2; ++k) {
+    float* o = k ? vel : pos;
+    if (!o) continue;
+    o += 3 * base;
+    if (n == 3 * NTP && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+      for (int i = threadIdx.x; i < 3 * NTP / 4; i += NTP)
+        reinterpret_cast<float4*>(o)[i] = reinterpret_cast<const float4*>(st[k])[i];
+    } else {
+      for (int i = threadIdx.x; i < n; i += NTP) o[i] = st[k][i];
     }
-    vel[p * 3 + 0] = (vx[p] + l[0]) * vscale;
-    vel[p * 3 + 1] = (vy[p] + l[1]) * vscale;
-    vel[p * 3 + 2] = (vz[p] + l[2]) * vscale;
   }
 }
 
