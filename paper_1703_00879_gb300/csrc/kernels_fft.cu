@@ -1409,6 +1409,25 @@ __device__ __forceinline__ void row_c2r_combine(float2* buf, const float2* tw, f
   __syncthreads();
 }
 
+// The same pre-processing as the first step of the inverse row transform loads
+// element n of tile row r: its partner M - n is read from the staged row itself,
+// which no thread overwrites before every load of that step is done.  Saves the
+// separate pass over the tile (a write of every value and a barrier).  Pitch CW.
+template <int N, int CW>
+struct C2rCombine {
+  const float2* buf;
+  const float2* tw;
+  float kfs;
+  __device__ __forceinline__ float2 operator()(float2 zn, int r, int n) const {
+    constexpr int M = N / 2;
+    const float2 a = c2r_in<M>(zn, n, kfs);
+    const float2 b = cconj(c2r_in<M>(buf[r * CW + M - n], M - n, kfs));
+    const float2 E = cadd(a, b);
+    const float2 O = cmul(cconj(tw[n]), csub(a, b));
+    return cadd(E, cmul_i(O));
+  }
+};
+
 // Resident CTAs per SM for the plain row passes: 3 when three tiles fit in
 // shared memory and the transform is short enough (<= 256 points) to stay in
 // 85 registers, else 2.
@@ -1658,14 +1677,24 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
     cp_async_wait<1>();
     __syncthreads();
     float2* buf = cur ? st1 : st0;
-    row_c2r_combine<N, TWX>(buf, tw, jobs.kfs[j.job]);
+    // the c2r pre-processing rides on the transform's first loads (C2rCombine),
+    // except at N = 1024, where that costs this kernel spills and a separate
+    // pass over the tile measured faster
+    constexpr bool HOOK = N < 1024;
+    using Pre = std::conditional_t<HOOK, C2rCombine<N, C::CW>, NoPre>;
+    Pre pre{};
+    if constexpr (HOOK) {
+      pre = Pre{buf, tw, jobs.kfs[j.job]};
+    } else {
+      row_c2r_combine<N, TWX>(buf, tw, jobs.kfs[j.job]);
+    }
     // even tile rows go to one block of consecutive real rows, odd ones to
     // another, straight from the transform's last step
     if constexpr (OUT == 0) {
       float* out = moved(static_cast<float*>(jobs.out[j.job]), j.by);
       const RealRowOut<M> o{reinterpret_cast<float2*>(out + real_row_q(j.row0, N) * N),
                             reinterpret_cast<float2*>(out + real_row_q(j.row0 + 1, N) * N)};
-      fft_rowtile<M, TWX, C::CW, NT, true, 2, NoPre, false, RealRowOut<M>>(buf, tw, NoPre{}, o);
+      fft_rowtile<M, TWX, C::CW, NT, true, 2, Pre, false, RealRowOut<M>>(buf, tw, pre, o);
     } else {
       const SimHeader* h = moved(jobs.hdr, j.by);
       if (j.q != run_q) {  // the same for every thread of the CTA
@@ -1679,7 +1708,7 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
       float tile_max = 0.f;
       const RealRowOut16<M, OUT> o{out + real_row_q(j.row0, N) * M, out + real_row_q(j.row0 + 1, N) * M,
                                    1.f / h->lq_scale[j.job], &tile_max};
-      fft_rowtile<M, TWX, C::CW, NT, true, 2, NoPre, false, RealRowOut16<M, OUT>>(buf, tw, NoPre{}, o);
+      fft_rowtile<M, TWX, C::CW, NT, true, 2, Pre, false, RealRowOut16<M, OUT>>(buf, tw, pre, o);
       run_max = fmaxf(run_max, tile_max);
     }
     __syncthreads();
@@ -1767,8 +1796,8 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
       stage_complex_rows<N, TWX>(cur ? st0 : st1, moved(w_in, rn.by), rn.row0);
     }
     cp_async_commit();
-    row_c2r_combine<N, TWX>(buf, tw, 0.f);
-    fft_rowtile_call<M, TWX, C::CW, NT, true, 2, NoPre, true>(buf, tw);
+    fft_rowtile_call<M, TWX, C::CW, NT, true, 2, C2rCombine<N, C::CW>, true>(buf, tw,
+                                                                           C2rCombine<N, C::CW>{buf, tw, 0.f});
     cp_async_wait<1>();  // the density rows; the next tile's prefetch may still be in flight
     __syncthreads();
     // S = delta eps(w) is formed as the forward transform loads it
@@ -1899,9 +1928,8 @@ __device__ __forceinline__ void plane_yinv(float2* a, const float2* tw) {
 template <int N>
 __device__ __forceinline__ void plane_xc2r(float2* a, const float2* tw, float kfs, float* g) {
   using C = PlaneCfg<N>;
-  row_c2r_combine<N, N>(a, tw, kfs);
-  fft_rowtile<C::M, N, C::CW, NT, true, 2, NoPre, false, PlaneRowOut<C::M>>(
-      a, tw, NoPre{}, PlaneRowOut<C::M>{reinterpret_cast<float2*>(g)});
+  fft_rowtile<C::M, N, C::CW, NT, true, 2, C2rCombine<N, C::CW>, false, PlaneRowOut<C::M>>(
+      a, tw, C2rCombine<N, C::CW>{a, tw, kfs}, PlaneRowOut<C::M>{reinterpret_cast<float2*>(g)});
 }
 
 // i kfs f_y times every value of plane buffer a (f_y the signed frequency of row y;
@@ -1987,8 +2015,7 @@ __global__ void __launch_bounds__(NT) k_plane_screen(const float2* __restrict__ 
   cp_async_wait<0>();
   __syncthreads();
   plane_yinv<N>(a, tw);
-  row_c2r_combine<N, N>(a, tw, 0.f);
-  fft_rowtile<M, N, C::CW, NT, true, 2>(a, tw);
+  fft_rowtile<M, N, C::CW, NT, true, 2, C2rCombine<N, C::CW>>(a, tw, C2rCombine<N, C::CW>{a, tw, 0.f});
   const ScreenSource<M, MODEL, true> src{reinterpret_cast<const float2*>(moved(rho, by) + (int64_t)z * N * N),
                                          fp.inv_rhobar, MODEL == 1 ? fp.fr_thr : fp.dgp_coef};
   fft_rowtile<M, N, C::CW, NT, false, 2, ScreenSource<M, MODEL, true>>(a, tw, src);
