@@ -1365,47 +1365,36 @@ __device__ __forceinline__ float2 c2r_in(float2 x, int k, float kfs) {
 
 // c2r pre-processing in place on each staged row (unnormalised inverse, 2x
 // folded in): E = X[k] + conj X[M-k], O = w^-k (X[k] - conj X[M-k]),
-// Z[k] = E + i O, Z[M-k] = conj E + i conj O.
+// Z[k] = E + i O, Z[M-k] = conj E + i conj O.  A separate pass over the tile,
+// used by the 1024-point multi c2r; shorter rows take it on the transform's
+// first loads (C2rCombine below).  Warps take rows, lanes take k = lane,
+// lane + 32, ... <= M/2 (no division, the derivative test hoisted out of the loop).
 template <int N, int TWX>
 __device__ __forceinline__ void row_c2r_combine(float2* buf, const float2* tw, float kfs) {
   using C = RowCfg<N, TWX>;
   constexpr int M = N / 2;
-  if constexpr (M >= 256) {
-    // long rows: warps take rows, lanes take k = lane, lane + 32, ... <= M/2
-    // (no division, and the derivative test hoisted out of the loop)
-    auto pairs = [&](auto deriv) {
-      constexpr bool D = decltype(deriv)::value;
-      for (int r = threadIdx.x >> 5; r < TWX; r += NT / 32) {
-        float2* z = buf + r * C::CW;
-        for (int k = threadIdx.x & 31; k <= M / 2; k += 32) {
-          float2 a = z[k], b = z[M - k];
-          if (D) {
-            a = cscale(cmul_i(a), kfs * (float)k);
-            b = k == 0 ? make_float2(0.f, 0.f) : cscale(cmul_i(b), kfs * (float)(M - k));
-          }
-          if (k == 0) a.y = b.y = 0.f;  // X[0], X[M] real
-          b = cconj(b);
-          const float2 E = cadd(a, b);
-          const float2 O = cmul(cconj(tw[k]), csub(a, b));
-          z[k] = cadd(E, cmul_i(O));
-          if (k != 0 && k != M - k) z[M - k] = cadd(cconj(E), cmul_i(cconj(O)));
-        }
-      }
-    };
-    if (kfs != 0.f) pairs(std::true_type{});
-    else pairs(std::false_type{});
-  } else {
-    for (int e = threadIdx.x; e < TWX * (M / 2 + 1); e += NT) {
-      const int r = e / (M / 2 + 1), k = e - r * (M / 2 + 1);
+  static_assert(M >= 256, "long rows only");
+  auto pairs = [&](auto deriv) {
+    constexpr bool D = decltype(deriv)::value;
+    for (int r = threadIdx.x >> 5; r < TWX; r += NT / 32) {
       float2* z = buf + r * C::CW;
-      const float2 a = c2r_in<M>(z[k], k, kfs);
-      const float2 b = cconj(c2r_in<M>(z[M - k], M - k, kfs));
-      const float2 E = cadd(a, b);
-      const float2 O = cmul(cconj(tw[k]), csub(a, b));
-      z[k] = cadd(E, cmul_i(O));
-      if (k != 0 && k != M - k) z[M - k] = cadd(cconj(E), cmul_i(cconj(O)));
+      for (int k = threadIdx.x & 31; k <= M / 2; k += 32) {
+        float2 a = z[k], b = z[M - k];
+        if (D) {
+          a = cscale(cmul_i(a), kfs * (float)k);
+          b = k == 0 ? make_float2(0.f, 0.f) : cscale(cmul_i(b), kfs * (float)(M - k));
+        }
+        if (k == 0) a.y = b.y = 0.f;  // X[0], X[M] real
+        b = cconj(b);
+        const float2 E = cadd(a, b);
+        const float2 O = cmul(cconj(tw[k]), csub(a, b));
+        z[k] = cadd(E, cmul_i(O));
+        if (k != 0 && k != M - k) z[M - k] = cadd(cconj(E), cmul_i(cconj(O)));
+      }
     }
-  }
+  };
+  if (kfs != 0.f) pairs(std::true_type{});
+  else pairs(std::false_type{});
   __syncthreads();
 }
 
