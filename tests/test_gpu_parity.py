@@ -114,6 +114,22 @@ def test_force_from_density_vs_oracle(pkg, model, N):
         assert _relmax(F[i], ref[i]) < 3e-5, i
 
 
+@pytest.mark.parametrize("model", [LCDM_MODEL, F5, NDGP1], ids=["lcdm", "F5", "nDGP_screen"])
+def test_force_from_density_128_vs_oracle(pkg, model):
+    """N = 128, the largest mesh whose transforms run as plane passes (the x and y steps of a
+    z-plane in one CTA: density r2c, the screening source chain, the force inverses): the same
+    comparison and tolerance as above."""
+    N = 128
+    run = Run(Np=N, Nmesh=N, Lbox=16.0 * N, nsteps=4, model=model)
+    rho = _density(N, 3 + N).astype(np.float32)
+    a = 0.6
+    with pkg.Simulation(run, ic=False) as s:
+        F = s.force_from_density(rho, a)
+    ref = pm.force_mesh(rho.astype(np.float64), 1.0, N, run.Lbox, a, run.cosmo.Omega_m, model)
+    for i in range(3):
+        assert _relmax(F[i], ref[i]) < 3e-5, i
+
+
 def _sharp_k_modes_at_the_cut(N, L, R, rel=1e-5):
     """Lattice modes whose (kR)^2 lies within `rel` of 1: the FP64 oracle and the FP32 kernel may
     decide these either way (the sharp-k window of App. B).  Every other mode is decided alike."""
@@ -161,6 +177,27 @@ def test_ic_potentials_and_positions_vs_oracle(pkg, oracle_small):
     assert _relmax(d0.T, s0) < 2e-5
     # the initial residual acceleration is a small difference of two forces
     assert np.max(np.abs(a0.T - acc0)) < 2e-3 * np.max(np.abs(acc0)) + 1e-6
+
+
+@pytest.mark.parametrize("seed", [2, 4], ids=["F5", "nDGP_screen"])
+def test_ensemble_shape_run_vs_oracle(pkg, seed):
+    """The batched ensemble's simulation shape (64^3 particles, 128^3 mesh, 128 Mpc/h), three
+    steps in one cola_step call: the LPT fields, the density transform, the screening source and
+    the force inverses all run as plane passes, the step boundaries fused.  Displacements within
+    1e-4 cell of the FP64 oracle, P(k) within 1e-4 per bin."""
+    from workloads import ensemble_run
+    run = ensemble_run(seed, nsteps=3)
+    o = OracleSim(run).run_to_end()
+    with pkg.Simulation(run) as s:
+        s.run_to_end()
+        d = s.export(pkg.COLA_F_DISP).T.astype(np.float64)
+        k, P, nm = s.pk()
+    err = np.max(np.abs(d - o.s)) / (run.Lbox / run.Nmesh)
+    assert err <= 1e-4, err
+    ko, Po, nmo = o.power_spectrum(run.Nmesh // 2)
+    ok = nmo > 0
+    assert np.array_equal(nm[ok], nmo[ok].astype(np.int64))
+    assert np.max(np.abs(P[ok] / Po[ok] - 1)) <= 1e-4
 
 
 def _cell_err(run, s_gpu, s_ref):
