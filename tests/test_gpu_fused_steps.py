@@ -86,3 +86,22 @@ def test_fused_batch_steps_equal_single_batch_steps(pkg, split):
                                    atol=1e-6 * np.max(np.abs(a[pkg.COLA_F_LPT_ACC])))
     ok = Pref > 0
     assert np.max(np.abs(P[ok] / Pref[ok] - 1)) <= 1e-5
+
+
+def test_fused_batch_steps_eager_equal_graph(pkg):
+    """With stage timing on, batch steps launch eagerly (no graph) through the same launch
+    sequences, fused boundaries included: the state and the stage record agree with the graph
+    run (the fused particle pass appears in the record)."""
+    from workloads import ENSEMBLE_MODELS, ensemble_run
+    runs = [ensemble_run(seed, Np=32, Nmesh=64, Lbox=64.0, nsteps=4) for seed in range(len(ENSEMBLE_MODELS))]
+    ref, _ = _batch_run(pkg, runs, [4])
+    sims = [pkg.Simulation(r) for r in runs]
+    sims[0].profile(True)
+    with pkg.Batch(sims) as b:
+        b.step(4)
+    st = sims[0].profile_read()
+    assert st["kick_drift_deposit"][1] == 3 and st["drift_deposit"][1] == 1 and st["gather_kick"][1] == 1
+    for r, s, a in zip(runs, sims, ref):
+        d = s.export(pkg.COLA_F_DISP).astype(np.float64)
+        assert np.max(np.abs(d - a[pkg.COLA_F_DISP])) <= 1e-4 * r.Lbox / r.Nmesh
+        s.close()
