@@ -1722,27 +1722,42 @@ __device__ __forceinline__ float screen_eps(float w, float p) {
   }
 }
 
-// Load hook of the forward transform of the screening x pass: element j of
-// tile row r is S = delta eps(w), w the screening field (the tile value) and
-// delta = rho / rho_bar - 1 from the staged density row (M float2 per row).
-// GLOBAL: the density rows are read from global memory (read-only path).
-template <int M, int MODEL, bool GLOBAL = false>
+// Load hook of the forward transform of a screening pass: element j of tile row
+// r is S = delta eps(w), w the screening field (the tile value) and delta =
+// rho / rho_bar - 1 from consecutive density rows in global memory (M float2
+// per row, read-only path); used by the plane pass.
+template <int M, int MODEL>
 struct ScreenSource {
   const float2* rho;
   float inv_rhobar, p;
   __device__ __forceinline__ float2 operator()(float2 w, int r, int j) const {
-    const float2 rv = GLOBAL ? __ldg(rho + r * M + j) : rho[r * M + j];
+    const float2 rv = __ldg(rho + r * M + j);
+    const float d0 = rv.x * inv_rhobar - 1.f, d1 = rv.y * inv_rhobar - 1.f;
+    return make_float2(d0 * screen_eps<MODEL>(w.x, p), d1 * screen_eps<MODEL>(w.y, p));
+  }
+};
+
+// The same for an x-pass row tile, whose even rows are consecutive density rows
+// from `even` and odd rows from `odd`: each warp's loads of one transform step
+// cover 32 consecutive values of a row.
+template <int M, int MODEL>
+struct ScreenSourceRows {
+  const float2* even;
+  const float2* odd;
+  float inv_rhobar, p;
+  __device__ __forceinline__ float2 operator()(float2 w, int r, int j) const {
+    const float2 rv = __ldg((r & 1 ? odd : even) + (r >> 1) * M + j);
     const float d0 = rv.x * inv_rhobar - 1.f, d1 = rv.y * inv_rhobar - 1.f;
     return make_float2(d0 * screen_eps<MODEL>(w.x, p), d1 * screen_eps<MODEL>(w.y, p));
   }
 };
 
 // Screening source S = delta eps: c2r of the screening field rows, eps from the
-// field and delta from rho in the same tile, r2c.  Shared memory: twiddles, two
-// row tiles (double-buffered field rows), one tile of density rows.
+// field and delta from rho (read from global memory by the forward transform's
+// loads), r2c.  Shared memory: twiddles, two row tiles (double-buffered field rows).
 template <int N, int TWX>
 constexpr size_t xscreen_smem() {
-  return RowCfg<N, TWX>::smem + (size_t)TWX * N * sizeof(float);
+  return RowCfg<N, TWX>::smem;
 }
 
 template <int N, int TWX, int MODEL>
@@ -1758,7 +1773,6 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
   float2* tw = sm;
   float2* st0 = sm + N;
   float2* st1 = st0 + C::stage;
-  float* rr = reinterpret_cast<float*>(st1 + C::stage);  // density rows, TWX x N floats
   load_tw(tw, twg, N);
   int64_t t = blockIdx.x;
   if (t < ntiles) {
@@ -1776,10 +1790,7 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
     float2* buf = cur ? st1 : st0;
     cp_async_wait<0>();  // w rows of this tile (the only group in flight)
     __syncthreads();
-    // the density rows of this tile, then the next tile's w rows into the other
-    // buffer; both land while this tile's field is transformed
-    stage_real_rows<N, TWX>(rr, moved(rho, r.by), row0, N);
-    cp_async_commit();
+    // the next tile's w rows into the other buffer land while this tile is transformed
     if (tn < ntiles) {
       const RowTile rn = row_tile<N, TWX>(tn, m);
       stage_complex_rows<N, TWX>(cur ? st0 : st1, moved(w_in, rn.by), rn.row0);
@@ -1787,12 +1798,12 @@ __global__ void __launch_bounds__(NT, 2) k_x_screen(const float2* __restrict__ w
     cp_async_commit();
     fft_rowtile_call<M, TWX, C::CW, NT, true, 2, C2rCombine<N, C::CW>, true>(buf, tw,
                                                                            C2rCombine<N, C::CW>{buf, tw, 0.f});
-    cp_async_wait<1>();  // the density rows; the next tile's prefetch may still be in flight
-    __syncthreads();
     // S = delta eps(w) is formed as the forward transform loads it
-    const ScreenSource<M, MODEL> src{reinterpret_cast<const float2*>(rr), fp.inv_rhobar,
-                                     MODEL == 1 ? fp.fr_thr : fp.dgp_coef};
-    fft_rowtile_call<M, TWX, C::CW, NT, false, 2, ScreenSource<M, MODEL>, true>(buf, tw, src);
+    const float* rho_t = moved(rho, r.by);
+    const ScreenSourceRows<M, MODEL> src{reinterpret_cast<const float2*>(rho_t + real_row_q(row0, N) * N),
+                                         reinterpret_cast<const float2*>(rho_t + real_row_q(row0 + 1, N) * N),
+                                         fp.inv_rhobar, MODEL == 1 ? fp.fr_thr : fp.dgp_coef};
+    fft_rowtile_call<M, TWX, C::CW, NT, false, 2, ScreenSourceRows<M, MODEL>, true>(buf, tw, src);
     row_r2c_store<N, TWX>(buf, tw, moved(s_out, r.by), row0);
     __syncthreads();
     cur ^= 1;
@@ -2005,9 +2016,9 @@ __global__ void __launch_bounds__(NT) k_plane_screen(const float2* __restrict__ 
   __syncthreads();
   plane_yinv<N>(a, tw);
   fft_rowtile<M, N, C::CW, NT, true, 2, C2rCombine<N, C::CW>>(a, tw, C2rCombine<N, C::CW>{a, tw, 0.f});
-  const ScreenSource<M, MODEL, true> src{reinterpret_cast<const float2*>(moved(rho, by) + (int64_t)z * N * N),
+  const ScreenSource<M, MODEL> src{reinterpret_cast<const float2*>(moved(rho, by) + (int64_t)z * N * N),
                                          fp.inv_rhobar, MODEL == 1 ? fp.fr_thr : fp.dgp_coef};
-  fft_rowtile<M, N, C::CW, NT, false, 2, ScreenSource<M, MODEL, true>>(a, tw, src);
+  fft_rowtile<M, N, C::CW, NT, false, 2, ScreenSource<M, MODEL>>(a, tw, src);
   plane_r2c_split<N>(a, tw);
   constexpr int64_t P = half_pitch(N);
   float2* g = moved(s_out, by) + hrow(z, 0, N, P);
