@@ -367,8 +367,13 @@ int cola_batch_create(cola_ctx* const* ctxs, int32_t n, const cola_batch_plan* p
                       cola_batch** out);
 int cola_batch_set_plan(cola_batch* b, const cola_batch_plan* plan);
 int cola_batch_get_plan(const cola_batch* b, cola_batch_plan* out);
-/* Advances every context by nsteps (-1: to the last step).  When stage timing
- * is enabled on the first context (cola_profile_enable), the steps are
+/* Advances every context by nsteps (-1: to the last step).  With two or more
+ * steps, direct particle kernels (deposit_box = gather_box = 0) and every
+ * context on the FP32 per-k LPT path, the step boundaries are fused as in
+ * cola_step (the kick of each step but the last and the drift + deposit of
+ * the next in one pass): nsteps + 1 graph launches, the same state as nsteps
+ * single steps up to the order of the deposit's float additions.  When stage
+ * timing is enabled on the first context (cola_profile_enable), the steps are
  * launched without a graph, group after group on one stream, so that the
  * first group's stage timings (covering all of its simulations) are recorded. */
 int cola_batch_step(cola_batch* b, int32_t nsteps);
