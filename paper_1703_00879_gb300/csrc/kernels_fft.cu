@@ -856,10 +856,11 @@ __global__ void __launch_bounds__(NT, blocks_for_smem(col_smem_tw(N, TW), N) < 2
 }
 
 // ---------------------------------------------------------------- force (z pass)
-// One staged buffer per tile: the source (S, or delta when unscreened) is
-// transformed forward; delta(k) is read straight from global memory; Phi_tot(k)
-// is kept in registers while the two outputs (Phi and -i kz Phi) are inverse
-// transformed one after the other in the same buffer.
+// Per tile: the source (S, or delta when unscreened) is staged and transformed
+// forward while delta(k) lands in a second shared-memory tile (screened runs);
+// Phi_tot(k) is formed from both and kept in that second tile, and the two
+// outputs (Phi and -i kz Phi) are inverse transformed one after the other in
+// the staging buffer and stored to HBM.
 template <int N, int TW, bool SCREENED>
 struct OpZForce {
   // One CTA per SM (N >= 512, up to 255 registers): Phi_tot(k) is formed in the
