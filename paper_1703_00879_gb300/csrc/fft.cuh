@@ -14,22 +14,28 @@
 //
 // The in-register DFTs are radix-2 decimation in time (inputs in bit-reversed
 // positions, placed there at compile time by the loads; outputs in natural
-// order): a twiddled butterfly a +- w b is four fused multiply-adds for a + w b
-// and one per component for 2a - (a + w b), six instructions where a multiply
-// by w after a decimation-in-frequency subtraction takes eight.
+// order): a twiddled butterfly a +- w b is two fused multiply-adds per component
+// for a + w b and one for 2a - (a + w b), issued as paired (two-component)
+// FMAs; the decimation-in-frequency form (subtract, then multiply by w) takes
+// more.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace cola {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Additions, subtractions and scalings of complex values use the paired
+// single-precision instructions of this architecture (two components per
+// instruction, each rounded exactly as the scalar operation).  The complex
+// multiply stays scalar: its paired form (a multiply and an FMA on swapped
+// operands) measured no faster.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
 // multiply by +i
 __device__ __forceinline__ float2 cmul_i(float2 a) { return make_float2(-a.y, a.x); }
 // multiply by -i (forward) or +i (inverse)
@@ -80,8 +86,8 @@ __device__ __forceinline__ float2 w32mul(float2 a, int m) {
 
 // Decimation-in-time butterfly (a, b) <- (a + w b, a - w b) with
 // w = exp(-/+ 2 pi i m / 32), m in [0, 16) a compile-time constant after
-// unrolling: m = 0 and 8 are additions, the others four FMAs for a + w b and
-// one FMA per component for 2a - (a + w b).
+// unrolling: m = 0 and 8 are additions, the others two paired FMAs for a + w b
+// and one for 2a - (a + w b) (the same per-component FMAs as the scalar form).
 template <bool INV>
 __device__ __forceinline__ void bfly_tw(float2& a, float2& b, int m) {
   if (m == 0) {
@@ -98,8 +104,10 @@ __device__ __forceinline__ void bfly_tw(float2& a, float2& b, int m) {
   const float s = m <= 8 ? cos32(8 - m) : cos32(m - 8);  // sin(2 pi m / 32) >= 0
   // forward w b = (c br + s bi, c bi - s br); inverse (c br - s bi, c bi + s br)
   const float sg = INV ? -s : s;
-  const float2 x = make_float2(fmaf(c, b.x, fmaf(sg, b.y, a.x)), fmaf(c, b.y, fmaf(-sg, b.x, a.y)));
-  b = make_float2(fmaf(2.f, a.x, -x.x), fmaf(2.f, a.y, -x.y));
+  // x = (c br + (sg bi + ar), c bi + (-sg br + ai)), b <- 2a - x: paired FMAs
+  const float2 t = __ffma2_rn(make_float2(sg, -sg), make_float2(b.y, b.x), a);
+  const float2 x = __ffma2_rn(make_float2(c, c), b, t);
+  b = __ffma2_rn(make_float2(2.f, 2.f), a, make_float2(-x.x, -x.y));
   a = x;
 }
 
