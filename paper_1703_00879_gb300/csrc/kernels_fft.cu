@@ -1364,45 +1364,11 @@ __device__ __forceinline__ float2 c2r_in(float2 x, int k, float kfs) {
   return x;
 }
 
-// c2r pre-processing in place on each staged row (unnormalised inverse, 2x
-// folded in): E = X[k] + conj X[M-k], O = w^-k (X[k] - conj X[M-k]),
-// Z[k] = E + i O, Z[M-k] = conj E + i conj O.  A separate pass over the tile,
-// used by the 1024-point multi c2r; shorter rows take it on the transform's
-// first loads (C2rCombine below).  Warps take rows, lanes take k = lane,
-// lane + 32, ... <= M/2 (no division, the derivative test hoisted out of the loop).
-template <int N, int TWX>
-__device__ __forceinline__ void row_c2r_combine(float2* buf, const float2* tw, float kfs) {
-  using C = RowCfg<N, TWX>;
-  constexpr int M = N / 2;
-  static_assert(M >= 256, "long rows only");
-  auto pairs = [&](auto deriv) {
-    constexpr bool D = decltype(deriv)::value;
-    for (int r = threadIdx.x >> 5; r < TWX; r += NT / 32) {
-      float2* z = buf + r * C::CW;
-      for (int k = threadIdx.x & 31; k <= M / 2; k += 32) {
-        float2 a = z[k], b = z[M - k];
-        if (D) {
-          a = cscale(cmul_i(a), kfs * (float)k);
-          b = k == 0 ? make_float2(0.f, 0.f) : cscale(cmul_i(b), kfs * (float)(M - k));
-        }
-        if (k == 0) a.y = b.y = 0.f;  // X[0], X[M] real
-        b = cconj(b);
-        const float2 E = cadd(a, b);
-        const float2 O = cmul(cconj(tw[k]), csub(a, b));
-        z[k] = cadd(E, cmul_i(O));
-        if (k != 0 && k != M - k) z[M - k] = cadd(cconj(E), cmul_i(cconj(O)));
-      }
-    }
-  };
-  if (kfs != 0.f) pairs(std::true_type{});
-  else pairs(std::false_type{});
-  __syncthreads();
-}
-
-// The same pre-processing as the first step of the inverse row transform loads
-// element n of tile row r: its partner M - n is read from the staged row itself,
-// which no thread overwrites before every load of that step is done.  Saves the
-// separate pass over the tile (a write of every value and a barrier).  Pitch CW.
+// c2r pre-processing (unnormalised inverse, 2x folded in) as the first step of
+// the inverse row transform loads element n of tile row r: with E = X[n] +
+// conj X[M-n] and O = w^-n (X[n] - conj X[M-n]), Z[n] = E + i O.  The partner
+// M - n is read from the staged row itself, which no thread overwrites before
+// every load of that step is done (no separate pass over the tile).  Pitch CW.
 template <int N, int CW>
 struct C2rCombine {
   const float2* buf;
@@ -1667,17 +1633,9 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
     cp_async_wait<1>();
     __syncthreads();
     float2* buf = cur ? st1 : st0;
-    // the c2r pre-processing rides on the transform's first loads (C2rCombine),
-    // except at N = 1024, where that costs this kernel spills and a separate
-    // pass over the tile measured faster
-    constexpr bool HOOK = N < 1024;
-    using Pre = std::conditional_t<HOOK, C2rCombine<N, C::CW>, NoPre>;
-    Pre pre{};
-    if constexpr (HOOK) {
-      pre = Pre{buf, tw, jobs.kfs[j.job]};
-    } else {
-      row_c2r_combine<N, TWX>(buf, tw, jobs.kfs[j.job]);
-    }
+    // the c2r pre-processing rides on the transform's first loads
+    using Pre = C2rCombine<N, C::CW>;
+    const Pre pre{buf, tw, jobs.kfs[j.job]};
     // even tile rows go to one block of consecutive real rows, odd ones to
     // another, straight from the transform's last step
     if constexpr (OUT == 0) {
