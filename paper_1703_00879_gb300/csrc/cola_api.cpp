@@ -76,7 +76,11 @@ struct cola_ctx {
   // mesh
   float* rho = nullptr;
   float2 *Cd = nullptr, *Ck = nullptr, *Cw = nullptr, *Cphi = nullptr, *Cphz = nullptr;
+  // force mesh: F_x, F_y, F_z in F[0], F[1] = F[0] + M, F[2]; with fpairs (meshes
+  // above 128 points) F[0] holds the (F_x, F_y) pairs instead (2 floats per cell
+  // over F[0] and F[1]'s storage, read by the gather as one 8-byte load per corner)
   float* F[3] = {};
+  bool fpairs = false;
   float2 *tw_np = nullptr, *tw_nm = nullptr;
   char* tables = nullptr;      // tab, vtab, dfp, ddt: this context's copy of its key's tables
   size_t tables_bytes = 0;
@@ -713,7 +717,8 @@ void context_layout(cola_ctx* c, const cola_config& cfg, Layout& L) {
   L.add(&c->Cw, hm);
   L.add(&c->Cphi, hm);
   L.add(&c->Cphz, hm);
-  for (int d = 0; d < 3; ++d) L.add(&c->F[d], M);
+  L.add(&c->F[0], 2 * M);
+  L.add(&c->F[2], M);
   L.add(&c->pk_acc, 3 * kMaxBins);
   L.add(&c->hdr, 1);
   L.add(&c->scratch, 64);
@@ -965,9 +970,16 @@ int force_group(const Group& g, double a, bool device_params, bool ini = false) 
     prof_end(ctx, ST_MESH_YINV, e, 2, all.nb * 5.0 * H);
     e = prof_begin(ctx, ST_MESH_XC2R);
     const float2* in3[3] = {ctx->Cphi, ctx->Cw, ctx->Cphz};
-    float* out3[3] = {ctx->F[0], ctx->F[1], ctx->F[2]};
-    const float kfs3[3] = {-fp.kf, 0.f, 0.f};
-    CK(fft_xc2r_multi(N, 3, in3, out3, kfs3, tw, st, all));
+    if (ctx->fpairs) {
+      // F_x and F_y as the (x, y) pairs of the interleaved mesh in F[0]
+      CK(fft_xc2r_pair(N, ctx->Cphi, ctx->Cw, ctx->F[0], -fp.kf, tw, st, all));
+      const float kfs_z = 0.f;
+      CK(fft_xc2r_multi(N, 1, in3 + 2, ctx->F + 2, &kfs_z, tw, st, all));
+    } else {
+      float* out3[3] = {ctx->F[0], ctx->F[1], ctx->F[2]};
+      const float kfs3[3] = {-fp.kf, 0.f, 0.f};
+      CK(fft_xc2r_multi(N, 3, in3, out3, kfs3, tw, st, all));
+    }
     prof_end(ctx, ST_MESH_XC2R, e, 1, all.nb * 3 * (H + R));
   }
   ctx->have_force = true;
@@ -1066,7 +1078,8 @@ int ic_group(const Group& g, bool potentials) {
     CHECK_RC(force_group(g, ctx->a[0], true, true));
     CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                         ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[0], ctx->lr[1], ctx->lr[2],
-                        ctx->F[0], ctx->F[1], ctx->F[2], StepDt{nullptr, 0.f, 0.f}, ctx->P, st, m, mix));
+                        ctx->F[0], ctx->F[1], ctx->F[2], ctx->fpairs, StepDt{nullptr, 0.f, 0.f}, ctx->P, st, m,
+                        mix));
     return COLA_OK;
   }
   CHECK_RC(run_lpt(ctx, 0, 0, false, m));
@@ -1082,7 +1095,8 @@ int ic_group(const Group& g, bool potentials) {
   CHECK_RC(force_group(g, ctx->a[0], true, true));
   CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
                       ctx->acc[0], ctx->acc[1], ctx->acc[2], ctx->lr[3], ctx->lr[4], ctx->lr[5],
-                      ctx->F[0], ctx->F[1], ctx->F[2], StepDt{nullptr, 0.f, 0.f}, ctx->P, st, m));
+                      ctx->F[0], ctx->F[1], ctx->F[2], ctx->fpairs, StepDt{nullptr, 0.f, 0.f}, ctx->P, st,
+                      m));
   return COLA_OK;
 }
 
@@ -1131,6 +1145,28 @@ int copy_out(cola_ctx* ctx, void* dst, const void* src, size_t bytes, int where)
   if (where == COLA_HOST) return copy_to_host(ctx, dst, src, bytes);
   CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ctx->st));
   return COLA_OK;
+}
+
+// The force mesh as three component arrays of M floats at d (F_x, F_y, F_z), host
+// or device; pairs are split on the device (straight into device destinations,
+// through the free complex work buffers for host ones).
+int export_force(cola_ctx* ctx, char* d, int where) {
+  const size_t mb = (size_t)ctx->M * sizeof(float);
+  if (!ctx->fpairs) {
+    for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * mb, ctx->F[c], mb, where));
+    return COLA_OK;
+  }
+  const float2* fxy = reinterpret_cast<const float2*>(ctx->F[0]);
+  if (where == COLA_DEVICE) {
+    CK(split_pairs(fxy, reinterpret_cast<float*>(d), reinterpret_cast<float*>(d + mb), ctx->M, ctx->st));
+  } else {
+    float* x = reinterpret_cast<float*>(ctx->Cphi);
+    float* y = reinterpret_cast<float*>(ctx->Cphz);
+    CK(split_pairs(fxy, x, y, ctx->M, ctx->st));
+    CHECK_RC(copy_out(ctx, d, x, mb, where));
+    CHECK_RC(copy_out(ctx, d + mb, y, mb, where));
+  }
+  return copy_out(ctx, d + 2 * mb, ctx->F[2], mb, where);
 }
 
 int copy_in(cola_ctx* ctx, void* dst, const void* src, size_t bytes, int where) {
@@ -1218,8 +1254,8 @@ int enqueue_group_tail(const Group& g, int kslot) {
   if (fast)  // A_LPT: Psi1 (lr[0..2]) mixed with Psi2
     for (int d = 0; d < 3; ++d) lk[d] = ctx->lr[d];
   CK(part_gather_kick(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2],
-                      ctx->acc[0], ctx->acc[1], ctx->acc[2], lk[0], lk[1], lk[2], ctx->F[0], ctx->F[1],
-                      ctx->F[2], dt, ctx->P, ctx->st, m, mix));
+                      ctx->acc[0], ctx->acc[1], ctx->acc[2], lk[0], lk[1], lk[2], ctx->F[0],
+                      ctx->F[1], ctx->F[2], ctx->fpairs, dt, ctx->P, ctx->st, m, mix));
   prof_end(ctx, ST_GATHER_KICK, e, 1, m.nb * ((fast ? 72.0 : lq ? 54.0 : 60.0) * Pb + 12.0 * Mb));
   CK(step_advance(ctx->hdr, ctx->st, m));
   ctx->kslot = kslot;  // multi-simulation groups use slot 0 (their callers reset every member)
@@ -1257,7 +1293,8 @@ int enqueue_group_mid(const Group& g, int n, int cur) {
   const float* const* ka = cur ? ctx->lrk : ctx->lr + 3;
   cudaEvent_t e = prof_begin(ctx, ST_KICK_DRIFT_DEPOSIT);
   CK(part_kick_drift_deposit(pp, ctx->s[0], ctx->s[1], ctx->s[2], ctx->v[0], ctx->v[1], ctx->v[2], ka[0], ka[1],
-                             ka[2], ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->F[0], ctx->F[1], ctx->F[2], ctx->rho,
+                             ka[2], ctx->lr[0], ctx->lr[1], ctx->lr[2], ctx->F[0], ctx->F[1], ctx->F[2],
+                             ctx->fpairs, ctx->rho,
                              ctx->hdr, ctx->P, ctx->st, m));
   prof_end(ctx, ST_KICK_DRIFT_DEPOSIT, e, 1, m.nb * (72.0 * Pb + 20.0 * Mb));
   CK(step_advance(ctx->hdr, ctx->st, m));
@@ -1376,6 +1413,8 @@ int cola_init(const cola_config* cfg, cola_alloc_fn alloc, cola_free_fn free_fn,
     } else {
       ctx->allocs.push_back(slab);
       lay.place(static_cast<char*>(slab));
+      ctx->F[1] = ctx->F[0] + ctx->M;
+      ctx->fpairs = ctx->Nm > 128;  // the plane passes (N <= 128) write plain components
     }
   }
   if (!rc) rc = upload_twiddles(ctx, ctx->Np, ctx->tw_np);
@@ -1783,8 +1822,7 @@ int cola_export(cola_ctx* ctx, int32_t which, void* dst, int32_t where) {
     }
     case COLA_F_FORCE:
       if (!ctx->have_force) return fail(ctx, COLA_ESTATE, "no force yet");
-      for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * mb, ctx->F[c], mb, where));
-      return COLA_OK;
+      return export_force(ctx, d, where);
     case COLA_F_PHI1:
     case COLA_F_PHI2:
       if (!ctx->ic_done) return fail(ctx, COLA_ESTATE, "no seeds before cola_ic");
@@ -1897,9 +1935,7 @@ int cola_force_from_density(cola_ctx* ctx, const float* rho, double a, float* fo
   const size_t mb = (size_t)ctx->M * sizeof(float);
   CHECK_RC(copy_in(ctx, ctx->rho, rho, mb, where));
   CHECK_RC(run_force(ctx, a));
-  char* d = reinterpret_cast<char*>(force);
-  for (int c = 0; c < 3; ++c) CHECK_RC(copy_out(ctx, d + c * mb, ctx->F[c], mb, where));
-  return COLA_OK;
+  return export_force(ctx, reinterpret_cast<char*>(force), where);
 }
 
 // ---------------------------------------------------------------- batches

@@ -161,6 +161,10 @@ cudaError_t fft_xc2r(int N, const float2* in, float* out, float kfs, const float
 // up to six independent c2r row passes in one launch
 cudaError_t fft_xc2r_multi(int N, int njobs, const float2* const* in, float* const* out,
                            const float* kfs, const float2* tw, cudaStream_t s, Multi m = {});
+// N >= 256: c2r of the rows of a (x derivative i kfs kx on load) and of b into the
+// (x, y) pairs of one interleaved real field xy (2 floats per cell, N^3 cells).
+cudaError_t fft_xc2r_pair(int N, const float2* a, const float2* b, float* xy, float kfs, const float2* tw,
+                          cudaStream_t s, Multi m = {});
 // the same with 16-bit outputs (prec 1 bf16, 2 fp16): job j writes value / hdr->lq_scale[j]
 // and adds its largest |value| into hdr->lq_amax[j] (hdr moved per simulation)
 cudaError_t fft_xc2r_multi16(int N, int njobs, const float2* const* in, void* const* out,
@@ -236,10 +240,12 @@ cudaError_t part_drift_deposit(const PartParams& pp, float* sx, float* sy, float
                                const float* az, const float* dpx, const float* dpy,
                                const float* dpz, float* rho, StepDt dt, int64_t P,
                                cudaStream_t s, Multi m = {}, LptMix mix = {});
+// The force mesh: F_x, F_y in F0, F1, or (pairs) the (F_x, F_y) pairs interleaved in F0
+// (one float2 per cell; F1 unused); F_z in Fz.
 cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float* sy,
                              const float* sz, float* vx, float* vy, float* vz, float* ax,
                              float* ay, float* az, const float* Ax, const float* Ay,
-                             const float* Az, const float* Fx, const float* Fy, const float* Fz,
+                             const float* Az, const float* F0, const float* F1, const float* Fz, bool pairs,
                              StepDt dt, int64_t P, cudaStream_t s, Multi m = {}, LptMix mix = {});
 // End of step n (hdr->step = n) and start of step n + 1 in one pass: kick with A_n,
 // closing half kick and drift of step n + 1 with its drift field dp, CIC deposit into rho
@@ -247,9 +253,11 @@ cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float*
 cudaError_t part_kick_drift_deposit(const PartParams& pp, float* sx, float* sy, float* sz, float* vx,
                                     float* vy, float* vz, const float* Ax, const float* Ay,
                                     const float* Az, const float* dpx, const float* dpy,
-                                    const float* dpz, const float* Fx, const float* Fy, const float* Fz,
-                                    float* rho, const SimHeader* hdr, int64_t P, cudaStream_t s,
+                                    const float* dpz, const float* F0, const float* F1, const float* Fz,
+                                    bool pairs, float* rho, const SimHeader* hdr, int64_t P, cudaStream_t s,
                                     Multi m = {});
+// The (x, y) pairs of fxy (n cells) into x[0..n) and y[0..n) (either may be null).
+cudaError_t split_pairs(const float2* fxy, float* x, float* y, int64_t n, cudaStream_t s);
 // Per simulation: lq_used = lq_scale (the scale the fields just written, table
 // row step + 1, carry), lq_scale = lq_amax x (growth of the next row over this
 // one, lqg) / target for the next pass (unchanged if nothing was written),

@@ -1308,6 +1308,27 @@ __device__ __forceinline__ void stage_complex_rows(float2* st, const float2* __r
   });
 }
 
+// A pair tile: TWX/4 row pairs of a and the same row pairs of b (first pair-major
+// row q0), row pair i of a at tile rows 4i (plane z) and 4i + 2 (plane z + 1), of b
+// at 4i + 1 and 4i + 3, so that tile rows 2w and 2w + 1 are the same real row of a
+// and of b.
+template <int N, int TWX>
+__device__ __forceinline__ void stage_complex_rows_pair(float2* st, const float2* __restrict__ a,
+                                                        const float2* __restrict__ b, int64_t q0) {
+  using C = RowCfg<N, TWX>;
+  constexpr int P = (int)half_pitch(N);
+  const float2* srca = a + hrow_q(q0, P);
+  const float2* srcb = b + hrow_q(q0, P);
+  for_pairs<TWX / 2, P>([&](int pr, int p0, int p1) {
+    const int job = pr & 1, i = pr >> 1;
+    int k = (p0 >> 3) * 8 + 2 * (p0 & 3);
+    float2* d = st + (4 * i + 2 * ((p0 >> 2) & 1) + job) * C::CW + k;
+    const float2* g = (job ? srcb : srca) + (int64_t)i * 2 * P + 2 * p0;
+    for (int p = p0; p < p1; p += 32, k += 32, d += 32, g += 64)
+      if (k < C::M + 2) cp_async16(d, g, true);
+  });
+}
+
 // real rows of N floats: row r at floats [pitch r, pitch r + N), i.e. the M
 // complex values z[j] = x[2j] + i x[2j+1] at st[r * CW + j] when pitch = 2 CW
 template <int N, int TWX>
@@ -1663,6 +1684,90 @@ __global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r(const __grid_
     cur ^= 1;
   }
   if constexpr (OUT != 0) amax_flush(run_h, run_job, run_max);
+  cp_async_wait<0>();
+}
+
+// C2rCombine with the x-derivative factor of even tile rows (kfs) and of odd
+// ones (kfs1): a pair tile's rows of a and of b.
+template <int N, int CW>
+struct C2rCombine2 {
+  const float2* buf;
+  const float2* tw;
+  float kfs, kfs1;
+  __device__ __forceinline__ float2 operator()(float2 zn, int r, int n) const {
+    return C2rCombine<N, CW>{buf, tw, (r & 1) ? kfs1 : kfs}(zn, r, n);
+  }
+};
+
+// Store hook of a pair tile's c2r: the last transform step leaves output k of
+// tile rows 2w (a) and 2w + 1 (b) in lanes l and l ^ R1 of one warp (R1 = the
+// first-step radix, the outputs per row and lane group of that step); one
+// shuffle gives lane l (a) the pair (a, b) of real 2k and lane l ^ R1 (b) that
+// of real 2k + 1, and each writes one 8-byte pair, so a warp's stores cover
+// consecutive cells.  o0 / o1: cell 0 of the first real row of planes z / z + 1.
+template <int N, int R1>
+struct PairRowOut {
+  static constexpr bool kSmem = false;
+  float2 *o0, *o1;
+  __device__ __forceinline__ float2 operator()(float2 v, int r, int k) const {
+    const int isb = r & 1;
+    const float recv = __shfl_xor_sync(0xffffffffu, isb ? v.x : v.y, R1);
+    float2* row = (((r >> 1) & 1) ? o1 : o0) + (int64_t)(r >> 2) * N;
+    // one store instruction for the warp: cell 2k (a lanes) or 2k + 1 (b lanes)
+    row[2 * k + isb] = isb ? make_float2(recv, v.y) : make_float2(v.x, recv);
+    return v;
+  }
+};
+
+// c2r of the rows of a (x derivative i kfs kx on load) and of b into the (x, y)
+// pairs of one interleaved real field (App. B: F_x and F_y of the force mesh),
+// pair tiles of TWX/4 row pairs of each.
+template <int N, int TWX>
+__global__ void __launch_bounds__(NT, row_blocks<N, TWX>()) k_xc2r_pair(
+    const float2* __restrict__ a, const float2* __restrict__ b, float2* __restrict__ out, float kfs,
+    const float2* __restrict__ twg, int64_t tiles_per_sim, Multi m) {
+  using C = RowCfg<N, TWX>;
+  constexpr int M = N / 2, R1 = Split<M>::R1;
+  static_assert(R1 < 32 && TWX * R1 % 32 == 0, "pair lanes within whole warps");
+  extern __shared__ __align__(128) float2 sm[];
+  float2* tw = sm;
+  float2* st0 = sm + N;
+  float2* st1 = st0 + C::stage;
+  load_tw(tw, twg, N);
+  const int64_t ntiles = tiles_per_sim * m.nb;
+  auto tile = [&](int64_t t, int64_t& q0, int64_t& by) {
+    const int64_t s = t / tiles_per_sim;
+    q0 = (t - s * tiles_per_sim) * (TWX / 2);
+    by = shift_of(m, (int)s);
+  };
+  int64_t t = blockIdx.x;
+  if (t < ntiles) {
+    int64_t q0, by;
+    tile(t, q0, by);
+    stage_complex_rows_pair<N, TWX>(st0, moved(a, by), moved(b, by), q0);
+  }
+  cp_async_commit();
+  int cur = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    int64_t q0, by;
+    tile(t, q0, by);
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) {
+      int64_t qn, bn;
+      tile(tn, qn, bn);
+      stage_complex_rows_pair<N, TWX>(cur ? st0 : st1, moved(a, bn), moved(b, bn), qn);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    float2* buf = cur ? st1 : st0;
+    float2* o = moved(out, by);
+    const PairRowOut<N, R1> st{o + real_row_q(q0, N) * N, o + real_row_q(q0 + 1, N) * N};
+    fft_rowtile<M, TWX, C::CW, NT, true, 2, C2rCombine2<N, C::CW>, false, PairRowOut<N, R1>>(
+        buf, tw, C2rCombine2<N, C::CW>{buf, tw, kfs, 0.f}, st);
+    __syncthreads();
+    cur ^= 1;
+  }
   cp_async_wait<0>();
 }
 
@@ -2085,6 +2190,30 @@ cudaError_t fft_xc2r_multi(int Nv, int njobs, const float2* const* in, float* co
                            const float* kfs, const float2* tw, cudaStream_t s, Multi m) {
   if (njobs < 1 || njobs > 6) return cudaErrorInvalidValue;
   COLA_SWITCH_N(Nv, return launch_xc2r_multi<N>(njobs, in, out, kfs, tw, s, m));
+  return cudaSuccess;
+}
+
+template <int N>
+static cudaError_t launch_xc2r_pair(const float2* a, const float2* b, float* xy, float kfs, const float2* tw,
+                                   cudaStream_t s, Multi m) {
+  if constexpr (N < 256) {
+    return cudaErrorInvalidValue;
+  } else {
+    constexpr int TWX = row_tw(N);
+    const size_t sm = row_smem<N>();
+    const int64_t tps = (int64_t)N * N / (TWX / 2);
+    auto k = k_xc2r_pair<N, TWX>;
+    unsigned grid;
+    cudaError_t e = prep(k, sm, tps * m.nb, grid);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NT, sm, s>>>(a, b, reinterpret_cast<float2*>(xy), kfs, tw, tps, m);
+    return cudaGetLastError();
+  }
+}
+
+cudaError_t fft_xc2r_pair(int Nv, const float2* a, const float2* b, float* xy, float kfs, const float2* tw,
+                          cudaStream_t s, Multi m) {
+  COLA_SWITCH_N(Nv, return launch_xc2r_pair<N>(a, b, xy, kfs, tw, s, m));
   return cudaSuccess;
 }
 

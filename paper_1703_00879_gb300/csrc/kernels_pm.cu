@@ -139,6 +139,34 @@ __device__ __forceinline__ float cic_interp(const float* __restrict__ F, int Nm,
   return wz0 * (wy0 * a00 + wy1 * a01) + wz1 * (wy0 * a10 + wy1 * a11);
 }
 
+// (F_x, F_y) at the particle from the interleaved pair mesh Fxy (one float2 per
+// cell): the same weights and operation order as cic_interp per component, one
+// 8-byte load per corner instead of two 4-byte loads.
+__device__ __forceinline__ float2 cic_interp2(const float2* __restrict__ F, int Nm, const Cic& c) {
+  const float wx0 = 1.f - c.f[0], wx1 = c.f[0];
+  const float wy0 = 1.f - c.f[1], wy1 = c.f[1];
+  const float wz0 = 1.f - c.f[2], wz1 = c.f[2];
+  const int64_t z0 = (int64_t)c.i0[2] * Nm, z1 = (int64_t)c.i1[2] * Nm;
+  const int64_t r00 = (z0 + c.i0[1]) * Nm, r01 = (z0 + c.i1[1]) * Nm;
+  const int64_t r10 = (z1 + c.i0[1]) * Nm, r11 = (z1 + c.i1[1]) * Nm;
+  auto row = [&](int64_t r) {
+    const float2 a = __ldg(F + r + c.i0[0]), b = __ldg(F + r + c.i1[0]);
+    return make_float2(wx0 * a.x + wx1 * b.x, wx0 * a.y + wx1 * b.y);
+  };
+  const float2 a00 = row(r00), a01 = row(r01), a10 = row(r10), a11 = row(r11);
+  return make_float2(wz0 * (wy0 * a00.x + wy1 * a01.x) + wz1 * (wy0 * a10.x + wy1 * a11.x),
+                     wz0 * (wy0 * a00.y + wy1 * a01.y) + wz1 * (wy0 * a10.y + wy1 * a11.y));
+}
+
+__global__ void __launch_bounds__(NTP) k_split_pairs(const float2* __restrict__ fxy, float* __restrict__ x,
+                                                     float* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * NTP + threadIdx.x; i < n; i += (int64_t)gridDim.x * NTP) {
+    const float2 v = fxy[i];
+    if (x) x[i] = v.x;
+    if (y) y[i] = v.y;
+  }
+}
+
 __device__ __forceinline__ void lattice(const PartParams& pp, int64_t p, int& ix, int& iy, int& iz) {
   const int m = pp.Np - 1;
   ix = (int)(p & m);
@@ -254,12 +282,13 @@ __global__ void __launch_bounds__(NTP) k_drift_deposit(
 // (displacement load -> cell index -> 24 mesh loads) of different particles overlap.
 constexpr int PPT = 2;
 
+template <bool XY>
 __global__ void __launch_bounds__(NTP) k_gather_kick(
     PartParams pp, const float* __restrict__ sx, const float* __restrict__ sy,
     const float* __restrict__ sz, float* __restrict__ vx, float* __restrict__ vy,
     float* __restrict__ vz, float* __restrict__ ax, float* __restrict__ ay,
     float* __restrict__ az, const float* __restrict__ Ax, const float* __restrict__ Ay,
-    const float* __restrict__ Az, const float* __restrict__ Fx, const float* __restrict__ Fy,
+    const float* __restrict__ Az, const float* __restrict__ F0, const float* __restrict__ F1,
     const float* __restrict__ Fz, StepDt dt, int64_t P, Multi m, LptMix mix) {
   const int64_t p0 = (int64_t)blockIdx.x * NTP * PPT + threadIdx.x;
   const int64_t by = shift_of(m, blockIdx.y);
@@ -275,8 +304,8 @@ __global__ void __launch_bounds__(NTP) k_gather_kick(
   Ax = moved(Ax, by);
   Ay = moved(Ay, by);
   Az = moved(Az, by);
-  Fx = moved(Fx, by);
-  Fy = moved(Fy, by);
+  F0 = moved(F0, by);
+  F1 = moved(F1, by);
   Fz = moved(Fz, by);
   float dtk = dt.dtk;
   if (dt.hdr) {
@@ -301,8 +330,14 @@ __global__ void __launch_bounds__(NTP) k_gather_kick(
       int ix, iy, iz;
       lattice(pp, p, ix, iy, iz);
       const Cic c = cic_setup(pp, ix, iy, iz, px[u], py[u], pz[u]);
-      gx[u] = cic_interp(Fx, pp.Nm, c);
-      gy[u] = cic_interp(Fy, pp.Nm, c);
+      if constexpr (XY) {  // (F_x, F_y) pairs in F0
+        const float2 gxy = cic_interp2(reinterpret_cast<const float2*>(F0), pp.Nm, c);
+        gx[u] = gxy.x;
+        gy[u] = gxy.y;
+      } else {
+        gx[u] = cic_interp(F0, pp.Nm, c);
+        gy[u] = cic_interp(F1, pp.Nm, c);
+      }
       gz[u] = cic_interp(Fz, pp.Nm, c);
     }
   }
@@ -352,13 +387,13 @@ __global__ void __launch_bounds__(NTP) k_gather_kick(
 // is the same bit for bit; acc is not stored (the next gather forms it again)
 // and delta_v and s are read and written once instead of twice.  hdr->step = n.
 // Particles as in the gather (8 x 4 lattice patches per warp, PPT per thread).
-template <int Q, int MINB>
+template <int Q, int MINB, bool XY>
 __global__ void __launch_bounds__(NTP, MINB) k_kick_drift_deposit(
     PartParams pp, float* __restrict__ sx, float* __restrict__ sy, float* __restrict__ sz,
     float* __restrict__ vx, float* __restrict__ vy, float* __restrict__ vz,
     const float* __restrict__ Ax, const float* __restrict__ Ay, const float* __restrict__ Az,
     const float* __restrict__ dpx, const float* __restrict__ dpy, const float* __restrict__ dpz,
-    const float* __restrict__ Fx, const float* __restrict__ Fy, const float* __restrict__ Fz,
+    const float* __restrict__ F0, const float* __restrict__ F1, const float* __restrict__ Fz,
     float* __restrict__ rho, const SimHeader* __restrict__ hdr, int64_t P, Multi m) {
   const int64_t p0 = (int64_t)blockIdx.x * NTP * Q + threadIdx.x;
   const int64_t by = shift_of(m, blockIdx.y);
@@ -374,8 +409,8 @@ __global__ void __launch_bounds__(NTP, MINB) k_kick_drift_deposit(
   dpx = moved(dpx, by);
   dpy = moved(dpy, by);
   dpz = moved(dpz, by);
-  Fx = moved(Fx, by);
-  Fy = moved(Fy, by);
+  F0 = moved(F0, by);
+  F1 = moved(F1, by);
   Fz = moved(Fz, by);
   rho = moved(rho, by);
   const SimHeader* h = moved(hdr, by);
@@ -399,8 +434,14 @@ __global__ void __launch_bounds__(NTP, MINB) k_kick_drift_deposit(
       int ix, iy, iz;
       lattice(pp, p, ix, iy, iz);
       const Cic c = cic_setup(pp, ix, iy, iz, px[u], py[u], pz[u]);
-      gx[u] = cic_interp(Fx, pp.Nm, c);
-      gy[u] = cic_interp(Fy, pp.Nm, c);
+      if constexpr (XY) {  // (F_x, F_y) pairs in F0
+        const float2 gxy = cic_interp2(reinterpret_cast<const float2*>(F0), pp.Nm, c);
+        gx[u] = gxy.x;
+        gy[u] = gxy.y;
+      } else {
+        gx[u] = cic_interp(F0, pp.Nm, c);
+        gy[u] = cic_interp(F1, pp.Nm, c);
+      }
       gz[u] = cic_interp(Fz, pp.Nm, c);
     }
   }
@@ -586,6 +627,20 @@ __device__ __forceinline__ float box_interp(const float* __restrict__ q, int sy,
   return wz0 * (wy0 * a00 + wy1 * a01) + wz1 * (wy0 * a10 + wy1 * a11);
 }
 
+// The same for the (x, y) pairs of the interleaved box (one float2 per cell).
+__device__ __forceinline__ float2 box_interp2(const float2* __restrict__ q, int sy, int sz, const CicU& c) {
+  const float wx0 = 1.f - c.f[0], wx1 = c.f[0];
+  const float wy0 = 1.f - c.f[1], wy1 = c.f[1];
+  const float wz0 = 1.f - c.f[2], wz1 = c.f[2];
+  auto row = [&](int o) {
+    const float2 a = q[o], b = q[o + 1];
+    return make_float2(wx0 * a.x + wx1 * b.x, wx0 * a.y + wx1 * b.y);
+  };
+  const float2 a00 = row(0), a01 = row(sy), a10 = row(sz), a11 = row(sz + sy);
+  return make_float2(wz0 * (wy0 * a00.x + wy1 * a01.x) + wz1 * (wy0 * a10.x + wy1 * a11.x),
+                     wz0 * (wy0 * a00.y + wy1 * a01.y) + wz1 * (wy0 * a10.y + wy1 * a11.y));
+}
+
 __device__ __forceinline__ void cp_async16_pm(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -711,12 +766,13 @@ __global__ void __launch_bounds__(NTP, 3) k_drift_deposit_box(
 
 // Gather (three force components staged in a shared box of at most `cap`
 // cells) and kick, as k_gather_kick.
+template <bool XY>
 __global__ void __launch_bounds__(NTP, 2) k_gather_kick_box(
     PartParams pp, const float* __restrict__ sx, const float* __restrict__ sy,
     const float* __restrict__ sz, float* __restrict__ vx, float* __restrict__ vy,
     float* __restrict__ vz, float* __restrict__ ax, float* __restrict__ ay,
     float* __restrict__ az, const float* __restrict__ Ax, const float* __restrict__ Ay,
-    const float* __restrict__ Az, const float* __restrict__ Fx, const float* __restrict__ Fy,
+    const float* __restrict__ Az, const float* __restrict__ F0, const float* __restrict__ F1,
     const float* __restrict__ Fz, StepDt dt, Multi m, LptMix mix, int cap) {
   extern __shared__ __align__(16) float sbox[];
   __shared__ int red[NTP / 32][6];
@@ -733,8 +789,8 @@ __global__ void __launch_bounds__(NTP, 2) k_gather_kick_box(
   Ax = moved(Ax, by);
   Ay = moved(Ay, by);
   Az = moved(Az, by);
-  Fx = moved(Fx, by);
-  Fy = moved(Fy, by);
+  F0 = moved(F0, by);
+  F1 = moved(F1, by);
   Fz = moved(Fz, by);
   float dtk = dt.dtk;
   float qs[3] = {1.f, 1.f, 1.f};
@@ -764,8 +820,15 @@ __global__ void __launch_bounds__(NTP, 2) k_gather_kick_box(
       const int64_t gi = ((int64_t)((b.lo[2] + zz) & mask) * Nm + ((b.lo[1] + yy) & mask)) * Nm +
                          ((x0 + 4 * e) & mask);
       const int cell = r * ex + 4 * e;
-      cp_async16_pm(sbox + cell, Fx + gi);
-      cp_async16_pm(sbox + cap + cell, Fy + gi);
+      if constexpr (XY) {  // (x, y) pairs: 2 cap floats, then z
+        float2* sxy = reinterpret_cast<float2*>(sbox);
+        const float2* F2 = reinterpret_cast<const float2*>(F0);
+        cp_async16_pm(sxy + cell, F2 + gi);
+        cp_async16_pm(sxy + cell + 2, F2 + gi + 2);
+      } else {
+        cp_async16_pm(sbox + cell, F0 + gi);
+        cp_async16_pm(sbox + cap + cell, F1 + gi);
+      }
       cp_async16_pm(sbox + 2 * cap + cell, Fz + gi);
     });
     asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -774,15 +837,28 @@ __global__ void __launch_bounds__(NTP, 2) k_gather_kick_box(
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const int o = (c[k].i0[2] - b.lo[2]) * szb + (c[k].i0[1] - b.lo[1]) * syb + (c[k].i0[0] - x0);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) g[k][d] = box_interp(sbox + d * cap + o, syb, szb, c[k]);
+      if constexpr (XY) {
+        const float2 gxy = box_interp2(reinterpret_cast<const float2*>(sbox) + o, syb, szb, c[k]);
+        g[k][0] = gxy.x;
+        g[k][1] = gxy.y;
+      } else {
+        g[k][0] = box_interp(sbox + o, syb, szb, c[k]);
+        g[k][1] = box_interp(sbox + cap + o, syb, szb, c[k]);
+      }
+      g[k][2] = box_interp(sbox + 2 * cap + o, syb, szb, c[k]);
     }
   } else {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const Cic cw = wrap(c[k], pp.Nm);
-      g[k][0] = cic_interp(Fx, pp.Nm, cw);
-      g[k][1] = cic_interp(Fy, pp.Nm, cw);
+      if constexpr (XY) {
+        const float2 gxy = cic_interp2(reinterpret_cast<const float2*>(F0), pp.Nm, cw);
+        g[k][0] = gxy.x;
+        g[k][1] = gxy.y;
+      } else {
+        g[k][0] = cic_interp(F0, pp.Nm, cw);
+        g[k][1] = cic_interp(F1, pp.Nm, cw);
+      }
       g[k][2] = cic_interp(Fz, pp.Nm, cw);
     }
   }
@@ -1082,7 +1158,7 @@ cudaError_t box_smem_attr(K kernel, size_t max_bytes, bool& done) {
   if (e == cudaSuccess) done = true;
   return e;
 }
-bool g_dep_attr = false, g_gk_attr = false;
+bool g_dep_attr = false, g_gk_attr = false, g_gk_attr_xy = false;
 }  // namespace
 
 void set_particle_plan(int deposit_box, int gather_box) {
@@ -1110,30 +1186,41 @@ cudaError_t part_drift_deposit(const PartParams& pp, float* sx, float* sy, float
 cudaError_t part_gather_kick(const PartParams& pp, const float* sx, const float* sy,
                              const float* sz, float* vx, float* vy, float* vz, float* ax,
                              float* ay, float* az, const float* Ax, const float* Ay,
-                             const float* Az, const float* Fx, const float* Fy, const float* Fz,
+                             const float* Az, const float* F0, const float* F1, const float* Fz, bool pairs,
                              StepDt dt, int64_t P, cudaStream_t s, Multi m, LptMix mix) {
   if (g_gk_box > 0 && P == (int64_t)pp.Np * pp.Np * pp.Np && pp.Np >= LB) {
-    cudaError_t e = box_smem_attr(k_gather_kick_box, 3 * kMaxGatherBox * sizeof(float), g_gk_attr);
+    auto k = pairs ? k_gather_kick_box<true> : k_gather_kick_box<false>;
+    cudaError_t e = box_smem_attr(k, 3 * kMaxGatherBox * sizeof(float), pairs ? g_gk_attr_xy : g_gk_attr);
     if (e != cudaSuccess) return e;
-    k_gather_kick_box<<<dim3((unsigned)(P / LBP), m.nb), NTP, 3 * (size_t)g_gk_box * sizeof(float), s>>>(
-        pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, Fx, Fy, Fz, dt, m, mix, g_gk_box);
+    k<<<dim3((unsigned)(P / LBP), m.nb), NTP, 3 * (size_t)g_gk_box * sizeof(float), s>>>(
+        pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, F0, F1, Fz, dt, m, mix, g_gk_box);
     return cudaGetLastError();
   }
-  k_gather_kick<<<dim3((unsigned)((P + NTP * PPT - 1) / (NTP * PPT)), m.nb), NTP, 0, s>>>(
-      pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, Fx, Fy, Fz, dt, P, m, mix);
+  auto k = pairs ? k_gather_kick<true> : k_gather_kick<false>;
+  k<<<dim3((unsigned)((P + NTP * PPT - 1) / (NTP * PPT)), m.nb), NTP, 0, s>>>(
+      pp, sx, sy, sz, vx, vy, vz, ax, ay, az, Ax, Ay, Az, F0, F1, Fz, dt, P, m, mix);
+  return cudaGetLastError();
+}
+
+cudaError_t split_pairs(const float2* fxy, float* x, float* y, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + NTP - 1) / NTP, 152 * 8));
+  k_split_pairs<<<grid, NTP, 0, s>>>(fxy, x, y, n);
   return cudaGetLastError();
 }
 
 cudaError_t part_kick_drift_deposit(const PartParams& pp, float* sx, float* sy, float* sz, float* vx,
                                     float* vy, float* vz, const float* Ax, const float* Ay,
                                     const float* Az, const float* dpx, const float* dpy,
-                                    const float* dpz, const float* Fx, const float* Fy, const float* Fz,
-                                    float* rho, const SimHeader* hdr, int64_t P, cudaStream_t s, Multi m) {
+                                    const float* dpz, const float* F0, const float* F1, const float* Fz,
+                                    bool pairs, float* rho, const SimHeader* hdr, int64_t P, cudaStream_t s,
+                                    Multi m) {
   // two particles per thread at four CTAs per SM (64 registers); measured on the 512^3 / 1024^3
   // run (ms per launch): 8.9 against 9.5 at 76 registers, 10.4 at 119, 9.4 with one particle
   constexpr int Q = 2;
-  k_kick_drift_deposit<Q, 4><<<dim3((unsigned)((P + NTP * Q - 1) / (NTP * Q)), m.nb), NTP, 0, s>>>(
-      pp, sx, sy, sz, vx, vy, vz, Ax, Ay, Az, dpx, dpy, dpz, Fx, Fy, Fz, rho, hdr, P, m);
+  auto k = pairs ? k_kick_drift_deposit<Q, 4, true> : k_kick_drift_deposit<Q, 4, false>;
+  k<<<dim3((unsigned)((P + NTP * Q - 1) / (NTP * Q)), m.nb), NTP, 0, s>>>(
+      pp, sx, sy, sz, vx, vy, vz, Ax, Ay, Az, dpx, dpy, dpz, F0, F1, Fz, rho, hdr, P, m);
   return cudaGetLastError();
 }
 
