@@ -980,7 +980,7 @@ int force_group(const Group& g, double a, bool device_params, bool ini = false) 
       const float kfs3[3] = {-fp.kf, 0.f, 0.f};
       CK(fft_xc2r_multi(N, 3, in3, out3, kfs3, tw, st, all));
     }
-    prof_end(ctx, ST_MESH_XC2R, e, 1, all.nb * 3 * (H + R));
+    prof_end(ctx, ST_MESH_XC2R, e, ctx->fpairs ? 2 : 1, all.nb * 3 * (H + R));
   }
   ctx->have_force = true;
   return COLA_OK;
