@@ -979,20 +979,30 @@ __global__ void __launch_bounds__(NTP) k_pos_deposit(int Nm, float cellscale,
 // the block's shared-memory bins once per bin it meets (and stops at the first
 // mode beyond the last bin).  The bin is decided exactly by integer comparisons,
 // 4 |n|^2 against (2b + 1)^2 and (2b + 3)^2.  |n| = s + r / (2 s) with s = sqrtf(|n|^2)
-// and r = |n|^2 - s^2 from one FMA (exact), summed in double: relative error
-// ~1e-14, with one double addition per mode (this GPU's double rate is low).
+// and r = |n|^2 - s^2 from one FMA (exact).  Double precision stays out of the
+// per-mode work (this GPU's double rate is low, and a double atomic on shared
+// memory is a compare-and-swap loop): within a run the weights are an integer,
+// s an exact 64-bit integer count of 2^-23 (s >= 1 is a multiple of it), the
+// corrections r / (2 s) (below 2^-15 each) and the powers single precision; the
+// block's bins take them as 64-bit integer, float and (the power only) double
+// atomics once per bin met, and the launch's bins in double at the end: |k| with
+// a relative error ~1e-15.
 __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, int N,
                                                 int64_t P, int nbins,
                                                 double* __restrict__ acc, double norm, Multi m,
                                                 int64_t acc_stride) {
-  extern __shared__ double sh[];
+  // block bins: power (double), count and sum of s 2^23 (64-bit integers), sum of
+  // the corrections (float); then the CIC window per kx
+  extern __shared__ __align__(16) unsigned char pk_sh[];
+  double* bp = reinterpret_cast<double*>(pk_sh);
+  unsigned long long* bw = reinterpret_cast<unsigned long long*>(bp + nbins);
+  unsigned long long* bs = bw + nbins;
+  float* bc = reinterpret_cast<float*>(bs + nbins);
+  float* wx = bc + nbins;
   const int64_t by = shift_of(m, blockIdx.y);
   dk = moved(dk, by);
   acc = acc_stride > 0 ? acc + blockIdx.y * acc_stride : moved(acc, by);
-  for (int i = threadIdx.x; i < 3 * nbins; i += NTP) sh[i] = 0.0;
-  __syncthreads();
   const int H = N / 2 + 1, K = (H + 31) / 32;
-  const int lane = threadIdx.x & 31, wpb = NTP / 32;
   const float pi = 3.14159265358979f;
   auto win = [&](int n) {
     if (n == 0) return 1.f;
@@ -1000,18 +1010,29 @@ __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, i
     const float sc = sinpif(t) / (pi * t);
     return sc * sc;
   };
+  for (int i = threadIdx.x; i < nbins; i += NTP) {
+    bp[i] = 0.0;
+    bw[i] = bs[i] = 0ull;
+    bc[i] = 0.f;
+  }
+  for (int i = threadIdx.x; i < H; i += NTP) wx[i] = win(i);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wpb = NTP / 32;
   for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < N * N; row += gridDim.x * wpb) {
     const int iz = row / N, iy = row - iz * N;
     const int ny = iy < N / 2 ? iy : iy - N, nz = iz < N / 2 ? iz : iz - N;
     const int c = ny * ny + nz * nz;
     const float wyz = win(ny) * win(nz);
     int cur = -1;
-    double sw = 0.0, sp = 0.0, sn = 0.0;
+    int sw = 0;
+    float sp = 0.f, snc = 0.f;
+    long long sni = 0;
     auto flush = [&]() {
       if (cur >= 0) {
-        atomicAdd(&sh[cur], sw);
-        atomicAdd(&sh[nbins + cur], sp * norm);
-        atomicAdd(&sh[2 * nbins + cur], sn);
+        atomicAdd(&bp[cur], (double)sp * norm);
+        atomicAdd(&bw[cur], (unsigned long long)sw);
+        atomicAdd(&bs[cur], (unsigned long long)sni);
+        atomicAdd(&bc[cur], snc);
       }
     };
     const int x0 = lane * K, x1 = min(x0 + K, H);
@@ -1025,23 +1046,31 @@ __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, i
       if (b != cur) {
         flush();
         cur = b;
-        sw = sp = sn = 0.0;
+        sw = 0;
+        sp = snc = 0.f;
+        sni = 0;
       }
       const float qf = (float)q;
       const float s = sqrtf(qf);
       const float r = fmaf(-s, s, qf);
-      const float wt = (ix == 0 || ix == N / 2) ? 1.f : 2.f;
+      const int wi = (ix == 0 || ix == N / 2) ? 1 : 2;
+      const float wt = (float)wi;
       const float2 v = dk[hidx(iz, iy, ix, N, P)];
-      const float wf = win(ix) * wyz;
-      sw += (double)wt;
-      sp += (double)(wt * (v.x * v.x + v.y * v.y) / (wf * wf));
-      sn += (double)wt * ((double)s + (double)__fdividef(r, 2.f * s));
+      const float wf = wx[ix] * wyz;
+      sw += wi;
+      sp += wt * (v.x * v.x + v.y * v.y) / (wf * wf);
+      sni += (long long)wi * __float2ll_rn(s * 8388608.f);  // s 2^23, an integer
+      snc += wt * __fdividef(r, 2.f * s);
     }
     flush();
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 3 * nbins; i += NTP)
-    if (sh[i] != 0.0) atomicAdd(&acc[i], sh[i]);
+  for (int i = threadIdx.x; i < nbins; i += NTP)
+    if (bw[i] != 0ull) {
+      atomicAdd(&acc[i], (double)bw[i]);
+      atomicAdd(&acc[nbins + i], bp[i]);
+      atomicAdd(&acc[2 * nbins + i], (double)bs[i] * 0x1p-23 + (double)bc[i]);
+    }
 }
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + NTP - 1) / NTP); }
@@ -1321,9 +1350,15 @@ cudaError_t pos_deposit(int Nm, float cellscale, const float* pos, int64_t n, fl
 
 cudaError_t pk_bin(int N, const float2* dk, int nbins, double* acc, double norm,
                    cudaStream_t s, Multi m, int64_t acc_stride) {
-  const size_t sm = 3 * (size_t)nbins * sizeof(double);
-  if (sm > 48 * 1024) return cudaErrorInvalidValue;
-  if (N > 4096) return cudaErrorInvalidValue;  // |n|^2 in 24 bits
+  // bins (double, two 64-bit integers, float) and the window per kx
+  const size_t sm = (size_t)nbins * 28 + (size_t)(N / 2 + 1) * sizeof(float);
+  if (N > 4096 || sm > 200 * 1024) return cudaErrorInvalidValue;  // |n|^2 in 24 bits
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_pk_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   const int64_t rows = (int64_t)N * N, wpb = NTP / 32;
   unsigned grid = (unsigned)std::min<int64_t>((rows + wpb - 1) / wpb, 152 * 8);
   if (m.nb > 1) grid = std::max<unsigned>(1, grid / (unsigned)std::min(m.nb, 8));
