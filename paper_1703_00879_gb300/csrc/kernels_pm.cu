@@ -984,9 +984,10 @@ __global__ void __launch_bounds__(NTP) k_pos_deposit(int Nm, float cellscale,
 // memory is a compare-and-swap loop): within a run the weights are an integer,
 // s an exact 64-bit integer count of 2^-23 (s >= 1 is a multiple of it), the
 // corrections r / (2 s) (below 2^-15 each) and the powers single precision; the
-// block's bins take them as 64-bit integer, float and (the power only) double
-// atomics once per bin met, and the launch's bins in double at the end: |k| with
-// a relative error ~1e-15.
+// block's bins take them as 64-bit integer and float atomics once per bin met
+// (the power as a float pair: the sum and the exact rounding error of each
+// addition, recovered from the value the atomic returns), and the launch's bins
+// in double at the end: |k| with a relative error ~1e-15.
 __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, int N,
                                                 int64_t P, int nbins,
                                                 double* __restrict__ acc, double norm, Multi m,
@@ -994,10 +995,11 @@ __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, i
   // block bins: power (double), count and sum of s 2^23 (64-bit integers), sum of
   // the corrections (float); then the CIC window per kx
   extern __shared__ __align__(16) unsigned char pk_sh[];
-  double* bp = reinterpret_cast<double*>(pk_sh);
-  unsigned long long* bw = reinterpret_cast<unsigned long long*>(bp + nbins);
+  unsigned long long* bw = reinterpret_cast<unsigned long long*>(pk_sh);
   unsigned long long* bs = bw + nbins;
-  float* bc = reinterpret_cast<float*>(bs + nbins);
+  float* bp = reinterpret_cast<float*>(bs + nbins);  // power: value and rounding error
+  float* bq = bp + nbins;
+  float* bc = bq + nbins;
   float* wx = bc + nbins;
   const int64_t by = shift_of(m, blockIdx.y);
   dk = moved(dk, by);
@@ -1011,9 +1013,8 @@ __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, i
     return sc * sc;
   };
   for (int i = threadIdx.x; i < nbins; i += NTP) {
-    bp[i] = 0.0;
     bw[i] = bs[i] = 0ull;
-    bc[i] = 0.f;
+    bp[i] = bq[i] = bc[i] = 0.f;
   }
   for (int i = threadIdx.x; i < H; i += NTP) wx[i] = win(i);
   __syncthreads();
@@ -1029,7 +1030,11 @@ __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, i
     long long sni = 0;
     auto flush = [&]() {
       if (cur >= 0) {
-        atomicAdd(&bp[cur], (double)sp * norm);
+        // power: the float bin and, from the value the atomic replaced, the exact
+        // rounding error of that addition into a second float (two-sum)
+        const float old = atomicAdd(&bp[cur], sp), sum = old + sp;
+        const float bv = sum - old;
+        atomicAdd(&bq[cur], (old - (sum - bv)) + (sp - bv));
         atomicAdd(&bw[cur], (unsigned long long)sw);
         atomicAdd(&bs[cur], (unsigned long long)sni);
         atomicAdd(&bc[cur], snc);
@@ -1068,7 +1073,7 @@ __global__ void __launch_bounds__(NTP) k_pk_bin(const float2* __restrict__ dk, i
   for (int i = threadIdx.x; i < nbins; i += NTP)
     if (bw[i] != 0ull) {
       atomicAdd(&acc[i], (double)bw[i]);
-      atomicAdd(&acc[nbins + i], bp[i]);
+      atomicAdd(&acc[nbins + i], ((double)bp[i] + (double)bq[i]) * norm);
       atomicAdd(&acc[2 * nbins + i], (double)bs[i] * 0x1p-23 + (double)bc[i]);
     }
 }
@@ -1350,7 +1355,7 @@ cudaError_t pos_deposit(int Nm, float cellscale, const float* pos, int64_t n, fl
 
 cudaError_t pk_bin(int N, const float2* dk, int nbins, double* acc, double norm,
                    cudaStream_t s, Multi m, int64_t acc_stride) {
-  // bins (double, two 64-bit integers, float) and the window per kx
+  // bins (two 64-bit integers, three floats) and the window per kx
   const size_t sm = (size_t)nbins * 28 + (size_t)(N / 2 + 1) * sizeof(float);
   if (N > 4096 || sm > 200 * 1024) return cudaErrorInvalidValue;  // |n|^2 in 24 bits
   static bool attr = false;
