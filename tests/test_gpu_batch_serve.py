@@ -49,6 +49,25 @@ def test_batch_equals_solo(plan):
         s.close()
 
 
+def test_batch_with_boxes_on_paired_force_mesh_equals_solo():
+    """Meshes above 128 points keep F_x and F_y as interleaved pairs: the shared-memory box
+    gather stages and interpolates the pairs.  Two F5 / nDGP members (32^3 particles on a 256^3
+    mesh) with deposit bins and gather boxes against their solo runs."""
+    import paper_1703_00879_gb300 as pkg
+    runs = [ensemble_run(seed, Np=32, Nmesh=256, Lbox=64.0, nsteps=3) for seed in (2, 4)]
+    solo = [_solo(pkg, r) for r in runs]
+    sims = [pkg.Simulation(r) for r in runs]
+    with pkg.Batch(sims, plan=(2, 1, 0, 16384, 8192)) as b:
+        b.step(-1)
+        k, P, nm = b.pk()
+    for i, (r, s, (d0, (k0, P0, nm0))) in enumerate(zip(runs, sims, solo)):
+        d = s.export(pkg.COLA_F_DISP)
+        assert np.max(np.abs(d - d0)) / (r.Lbox / r.Nmesh) <= 1e-4
+        ok = nm0 > 0
+        assert np.max(np.abs(P[i][ok] / P0[ok] - 1)) <= 1e-4
+        s.close()
+
+
 def test_batch_members_vs_oracle():
     """One member of every model class of the ensemble (LCDM, f(R) 1e-6/1e-5/1e-4, nDGP r_c H0 = 1
     and 5, each screened) advanced together in one batch, against the FP64 oracle run of the same
