@@ -81,6 +81,22 @@ def test_fr_with_tiny_fR0_equals_lcdm_run():
     assert np.allclose(a.s, b.s, rtol=0, atol=1e-9 * np.abs(a.s).max())
 
 
+@pytest.mark.parametrize("model", [
+    Model(kind=1, fR0=1e-14, screening=1),
+    Model(kind=2, rcH0=1e7, screening=0),
+    Model(kind=2, rcH0=1e7, screening=1, R_smooth=1.0),
+], ids=["fR_screened", "nDGP", "nDGP_screened"])
+def test_mg_limits_with_and_without_screening_equal_lcdm_run(model):
+    """Sec. 5 limits with the screening passes in the path: chameleon screening with |f_R0| -> 0
+    (threshold and fifth-force range both -> 0) and nDGP with r_c H0 -> infinity (the fifth-force
+    coefficient 1/(3 beta) -> 0, eps finite) leave the LCDM trajectory; mu - 1 < 1e-7 here, so
+    the displacements agree to 1e-6 of their largest value."""
+    base = SMALL_F5.with_(Np=16, Nmesh=16, Lbox=32.0, nsteps=3)
+    a = Simulation(base.with_model(Model())).run_to_end()
+    b = Simulation(base.with_model(model)).run_to_end()
+    assert np.allclose(a.s, b.s, rtol=0, atol=1e-6 * np.abs(a.s).max())
+
+
 def test_small_config_runs_and_boost_positive():
     """F5 boost B(k) = P_MG/P_LCDM > 1 and growing with k at the small scales of config 1."""
     sim = Simulation(SMALL_F5).run_to_end()
