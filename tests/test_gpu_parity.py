@@ -244,6 +244,37 @@ def test_small_config_boost_vs_oracle(pkg, oracle_small):
     assert np.max(np.abs(B - Bo)) <= 1e-4
 
 
+@pytest.fixture(scope="module")
+def oracle_small_lcdm():
+    return OracleSim(SMALL_F5.with_model(LCDM_MODEL)).run_to_end()
+
+
+@pytest.mark.parametrize("model", [
+    Model(kind=1, fR0=1e-14, screening=1),
+    Model(kind=1, fR0=1e-14, screening=0),
+    Model(kind=2, rcH0=1e7, screening=1, R_smooth=1.0),
+    Model(kind=2, rcH0=1e7, screening=0),
+], ids=["fR_tiny_screened", "fR_tiny", "nDGP_large_rc_screened", "nDGP_large_rc"])
+def test_mg_limits_reduce_to_lcdm(pkg, oracle_small_lcdm, model):
+    """G_eff -> 1 limits (Sec. 5): f(R) with |f_R0| -> 0 (the scalaron mass a m -> infinity, so
+    mu - 1 = k^2/(3(k^2 + a^2 m^2)) < 1e-12 here) and nDGP with r_c H0 -> infinity (1/(3 beta)
+    ~ 2e-8), with and without screening, run on the GPU's modified-gravity kernels (per-k growth
+    tables, screening passes, fifth-force Green's function).  They must reproduce the FP64
+    oracle's LCDM run: displacements within 1e-4 cell, P(k) within 1e-4 per bin."""
+    run = SMALL_F5.with_model(model)
+    o = oracle_small_lcdm
+    with pkg.Simulation(run) as s:
+        s.run_to_end()
+        disp = s.export(pkg.COLA_F_DISP).T
+        _, P, nm = s.pk()
+    mx, rms = _cell_err(run, disp, o.s)
+    assert mx <= 1e-4, (mx, rms)
+    _, Po, nmo = o.power_spectrum()
+    ok = nmo > 0
+    assert np.array_equal(nm, nmo.astype(np.int64))
+    assert np.max(np.abs(P[ok] / Po[ok] - 1)) <= 1e-4
+
+
 @pytest.mark.parametrize("run", [
     SMALL_F5.with_(Nmesh=64, nsteps=5),                       # mesh finer than particles
     SMALL_F5.with_(model=NDGP1, nsteps=5),                     # Vainshtein screening
