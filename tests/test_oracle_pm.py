@@ -29,6 +29,29 @@ def test_rfft_convention_against_direct_sum():
                        atol=1e-12)
 
 
+def test_rfft_every_mode_against_direct_sum_on_8_cubed():
+    """The whole half spectrum of the forward transform against the defining sum
+    X[kz, ky, kx] = sum_n x[n] exp(-2 pi i k.n / N), and the inverse against the synthesis
+    x[n] = N^-3 sum over all k of X[k] exp(+2 pi i k.n / N), the missing half from X(-k) = X(k)*."""
+    N = 8
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((N, N, N))
+    n = np.arange(N)
+    E = np.exp(-2j * np.pi * np.outer(n, n) / N)               # E[k, n]
+    full = np.einsum("az,by,cx,zyx->abc", E, E, E, x)          # all N^3 modes by the direct sum
+    X = ics.rfft3(x)
+    assert X.shape == (N, N, N // 2 + 1)
+    assert np.allclose(X, full[:, :, : N // 2 + 1], rtol=0, atol=1e-12 * np.abs(full).max())
+    neg = (-n) % N
+    rebuilt = np.empty_like(full)
+    rebuilt[:, :, : N // 2 + 1] = X
+    for kx in range(N // 2 + 1, N):
+        rebuilt[:, :, kx] = np.conj(X[np.ix_(neg, neg, [(-kx) % N])][:, :, 0])
+    y = np.einsum("az,by,cx,abc->zyx", E.conj(), E.conj(), E.conj(), rebuilt).real / N**3
+    assert np.allclose(ics.irfft3(X, N), y, rtol=0, atol=1e-12)
+    assert np.allclose(y, x, rtol=0, atol=1e-12)
+
+
 # ------------------------------------------------------------------ 2LPT source
 def _phi1_from_real(phi_real):
     return ics.rfft3(phi_real)
